@@ -1,0 +1,412 @@
+"""Benchmark of the SHGEMM random projection on GB300 (one JSON line on stdout).
+
+Workload (one step): the SHGEMM sweep Y_k = A * Omega_k at m = n = 16384,
+k in {64, 128, 256, 512}; A i.i.d. U[-1, 1] FP32 (seed 2, 1 GiB, larger than
+L2), Omega N(0,1) FP16 16384 x 512 (seed 1), Omega_k its first k columns.
+value = sum of 2 m n k over the step / step time (TFLOP/s, the paper's
+2mnk/t convention).
+
+Also reported (outside the timed steps): the FP32 SIMT path and the BF16x3
+split on the same sweep, sampled-row errors against the FP64 oracle, the
+4096^2 / 8192^2 points (L2 flushed between repetitions), the randomized SVD
+of the 1024^2 planted matrix and RP-HOSVD of the 512^3 Tucker tensor with
+the SHGEMM path vs the FP32 path, the roofline of the dominant kernel, the
+end-to-end number through host buffers and the oracle's CPU time.
+
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference] [--quick]
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import subprocess
+import sys
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "RSVD/RP-HOSVD time & SHGEMM TFLOP/s vs FP32 path, same GB300, matched error"
+KS = (64, 128, 256, 512)
+M = N = 16384
+
+
+def peaks():
+    try:
+        return json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))
+    except Exception:
+        return {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0, "bf16_tflops_sustained": 1700.0, "_fallback": True}
+
+
+class ClockSampler:
+    """nvidia-smi clocks and throttle reasons sampled during the timed region."""
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+         "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index: int):
+        self.idx = gpu_index
+        self.proc = None
+        self.lines = []
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", f"--id={self.idx}", f"--query-gpu={self.Q}",
+                                          "--format=csv,noheader,nounits", "-lms", "100"],
+                                         stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.t = threading.Thread(target=self._read, daemon=True)
+            self.t.start()
+        except Exception:
+            self.proc = None
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def stop(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        sm, mx, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            f = [x.strip() for x in ln.split(",")]
+            if len(f) < 9:
+                continue
+            try:
+                sm.append(float(f[1]))
+                mx.append(float(f[2]))
+            except ValueError:
+                continue
+            for nm, v in zip(names, f[5:9]):
+                if v.lower() == "active":
+                    reasons.add(nm)
+        return {"sm_mhz": float(np.median(sm)) if sm else None, "sm_max_mhz": max(mx) if mx else None,
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+def dist_env():
+    ws = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return ws, rank, local
+
+
+def oracle_rate(A_host, Om_host, budget_s=10.0, ks=KS):
+    """Oracle (FP64 CPU) throughput on a bounded row sample of the sweep."""
+    from oracle import shgemm as OS
+    rows, flops, t0 = 0, 0.0, time.perf_counter()
+    step = 512
+    while time.perf_counter() - t0 < budget_s and rows < A_host.shape[0]:
+        blk = A_host[rows:rows + step]
+        for k in ks:
+            OS.project_exact(blk, Om_host[:, :k])
+            flops += 2.0 * blk.shape[0] * A_host.shape[1] * k
+        rows += blk.shape[0]
+    dt = time.perf_counter() - t0
+    return flops / dt / 1e12, rows, dt
+
+
+def run_reference(args):
+    ws, rank, _ = dist_env()
+    if rank != 0:
+        return
+    from synth import omega_f16
+    rng = np.random.default_rng(2)
+    rows = 1024
+    A = rng.uniform(-1.0, 1.0, size=(rows, N)).astype(np.float32)   # rows of the same U[-1,1] matrix
+    Om = omega_f16(N, max(KS), seed=1)
+    for _ in range(args.warmup):
+        oracle_rate(A[:256], Om, budget_s=0.0)
+    times = []
+    for _ in range(args.steps):
+        t0 = time.perf_counter()
+        rate, r, dt = oracle_rate(A, Om, budget_s=1e9)
+        times.append(time.perf_counter() - t0)
+    flops = 2.0 * rows * N * sum(KS)
+    value = flops * len(times) / sum(times) / 1e12
+    cores = os.cpu_count()
+    line = {"impl": "reference", "metric": METRIC, "value": value, "unit": "TFLOP/s", "n_gpus": ws,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * sum(times) / len(times),
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+            "data": "synthetic",
+            "config": {"workload": "shgemm_sweep m=n=16384 k=64,128,256,512 (oracle: 1024-row sample)",
+                       "sample_rows": rows},
+            "cpu_baseline": {"value": value, "unit": "TFLOP/s", "cores": cores, "kind": "oracle",
+                             "sample": f"rows 0..{rows} of A (U[-1,1], 16384 cols) times Omega_k, all four k"},
+            "e2e": {"value": value, "unit": "TFLOP/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--quick", action="store_true", help="skip the side measurements")
+    args = ap.parse_args()
+    if args.impl == "reference":
+        run_reference(args)
+        return
+
+    import torch
+    ws, rank, local = dist_env()
+    torch.cuda.set_device(local)
+    if ws > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl")
+    import __graft_entry__ as g
+    g.build()
+    import paper_2304_04612_gb300 as shg
+    from synth import omega_f16
+    from oracle import shgemm as OS
+
+    pk = peaks()
+    dev = torch.device("cuda", local)
+    # ---------------------------------------------------------------- inputs
+    rng = np.random.default_rng(2)
+    A_host = rng.uniform(-1.0, 1.0, size=(M, N)).astype(np.float32)
+    Om_host = omega_f16(N, max(KS), seed=1)
+    A = torch.from_numpy(A_host).to(dev)
+    Om = torch.from_numpy(Om_host).to(dev)
+    Ys = {k: torch.empty(M, k, dtype=torch.float32, device=dev) for k in KS}
+    flags = shg.new_flags(dev)
+    stream = torch.cuda.current_stream(dev)
+
+    def step(variant="f16", events=None):
+        for k in KS:
+            if events is not None:
+                events[k][0].record(stream)
+            shg.shgemm_project(A, Om[:, :k], variant, out=Ys[k], flags=flags, check=False, stream=stream)
+            if events is not None:
+                events[k][1].record(stream)
+
+    for _ in range(args.warmup):
+        step()
+    torch.cuda.synchronize()
+    shg.check_flags(flags, "warmup")
+
+    ev = {k: [] for k in KS}
+    clocks = ClockSampler(local)
+    clocks.start()
+    time.sleep(0.3)
+    if ws > 1:
+        torch.distributed.barrier()
+    torch.cuda.synchronize()
+    t0 = torch.cuda.Event(enable_timing=True)
+    t1 = torch.cuda.Event(enable_timing=True)
+    t0.record(stream)
+    for _ in range(args.steps):
+        e = {k: (torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for k in KS}
+        step(events=e)
+        for k in KS:
+            ev[k].append(e[k])
+    t1.record(stream)
+    torch.cuda.synchronize()
+    ms_total = t0.elapsed_time(t1)
+    if ws > 1:
+        tt = torch.tensor([ms_total], device=dev)
+        torch.distributed.all_reduce(tt, op=torch.distributed.ReduceOp.MAX)
+        ms_total = float(tt.item())
+    clk = clocks.stop()
+    ms_step = ms_total / args.steps
+    flop_step = sum(2.0 * M * N * k for k in KS)
+    value = flop_step * args.steps * ws / (ms_total * 1e-3) / 1e12
+    per_k_ms = {k: float(np.mean([a.elapsed_time(b) for a, b in ev[k]])) for k in KS}
+    shg.check_flags(flags, "timed steps")
+
+    # -------------------------------------------------------------- roofline
+    bw = pk["hbm_gbs"] * 1e9
+    tc = pk["bf16_tflops"] * 1e12
+    roof = {}
+    for k in KS:
+        byts = 4.0 * M * N + 2.0 * N * k + 4.0 * M * k
+        fl = 4.0 * M * N * k
+        t = per_k_ms[k] * 1e-3
+        floor = max(byts / bw, fl / tc)
+        roof[k] = {"ms": per_k_ms[k], "tflops_2mnk": 2.0 * M * N * k / t / 1e12,
+                   "achieved_gbs": byts / t / 1e9, "tensor_tflops_4mnk": fl / t / 1e12,
+                   "bound": "hbm" if byts / bw >= fl / tc else "tensor", "frac_of_floor": floor / t}
+    k0 = 256
+    b0 = 4.0 * M * N + 2.0 * N * k0 + 4.0 * M * k0
+    roofline = {"bound": "hbm", "achieved": b0 / (per_k_ms[k0] * 1e-3) / 1e9, "peak": pk["hbm_gbs"],
+                "unit": "GB/s", "frac": b0 / (per_k_ms[k0] * 1e-3) / 1e9 / pk["hbm_gbs"], "traffic": None,
+                "kernel": "tc_gemm_kernel<K-major A, FP16 Omega> (SHGEMM-FP16), m=n=16384, k=256",
+                "peak_source": "MEASURED_PEAKS.json hbm_gbs (burst copy)" if "_fallback" not in pk else "fallback",
+                "per_k": {str(k): roof[k] for k in KS}}
+
+    line = {"metric": METRIC, "value": value, "unit": "TFLOP/s", "n_gpus": ws, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": ms_step, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f16x2-split/f32-acc", "data": "synthetic",
+            "config": {"workload": "shgemm_sweep m=n=16384 k=64,128,256,512 (SHGEMM-FP16, tcgen05)",
+                       "A": "16384x16384 FP32 U[-1,1] seed 2", "omega": "16384x512 FP16 N(0,1) seed 1",
+                       "l2": "inputs larger than L2 (A = 1 GiB per projection)",
+                       "parallelism": f"replicas x{ws}" if ws > 1 else "single GPU"},
+            "gpu_launches": len(KS) * args.steps, "clocks": clk, "roofline": roofline}
+
+    if rank == 0 and not args.quick:
+        side = side_measurements(shg, OS, torch, dev, A, A_host, Om, Om_host, Ys, flags, stream, pk)
+        line.update(side)
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+    if ws > 1:
+        torch.distributed.destroy_process_group()
+
+
+def time_ms(torch, stream, fn, reps=5, flush=None):
+    ts = []
+    for _ in range(reps):
+        if flush is not None:
+            flush()
+        a = torch.cuda.Event(enable_timing=True)
+        b = torch.cuda.Event(enable_timing=True)
+        a.record(stream)
+        fn()
+        b.record(stream)
+        torch.cuda.synchronize()
+        ts.append(a.elapsed_time(b))
+    return float(np.median(ts))
+
+
+def side_measurements(shg, OS, torch, dev, A, A_host, Om, Om_host, Ys, flags, stream, pk):
+    out = {}
+    flush_buf = torch.empty(512 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)
+
+    def flush():
+        flush_buf.zero_()
+
+    # FP32 SIMT path and BF16x3 on the same sweep
+    from oracle.lowp import encode_bf16
+    cmp = {}
+    Omb = torch.from_numpy(encode_bf16(OS.bf16_omega(Om_host)).view(np.int16)).to(dev).view(torch.bfloat16)
+    for variant, om in (("fp32", Om), ("bf16x3", Omb), ("f16", Om)):
+        per = {}
+        for k in KS:
+            reps = 2 if variant == "fp32" else 5
+            ms = time_ms(torch, stream, lambda: shg.shgemm_project(A, om[:, :k], variant, out=Ys[k], flags=flags,
+                                                                    check=False, stream=stream), reps=reps)
+            per[str(k)] = {"ms": ms, "tflops_2mnk": 2.0 * M * N * k / (ms * 1e-3) / 1e12}
+        cmp[variant] = per
+    out["sweep_16384"] = cmp
+    out["speedup_vs_fp32_simt"] = {str(k): cmp["fp32"][str(k)]["ms"] / cmp["f16"][str(k)]["ms"] for k in KS}
+
+    # sampled-row error vs the FP64 oracle (same inputs), per variant
+    rows = np.random.default_rng(0).choice(M, 128, replace=False)
+    errs = {}
+    for variant, om in (("f16", Om), ("fp32", Om), ("bf16x3", Omb)):
+        e = {}
+        for k in KS:
+            Y = shg.shgemm_project(A, om[:, :k], variant, out=Ys[k], flags=flags, check=True, stream=stream)
+            ref = OS.project_exact(A_host[rows], Om_host[:, :k]) if variant != "bf16x3" else \
+                A_host[rows].astype(np.float64) @ OS.bf16_omega(Om_host[:, :k])
+            e[str(k)] = OS.rel_fro_error(Y[rows].cpu().numpy(), ref)
+        errs[variant] = e
+    out["rel_err_sampled_rows"] = errs
+
+    # smaller square sizes, L2 flushed before each repetition
+    small = {}
+    for mm in (4096, 8192):
+        As = A[:mm, :mm]
+        per = {}
+        for variant in ("f16", "fp32"):
+            for k in KS:
+                ms = time_ms(torch, stream, lambda: shg.shgemm_project(As, Om[:mm, :k], variant, out=Ys[k][:mm],
+                                                                        flags=flags, check=False, stream=stream),
+                             reps=3 if variant == "fp32" else 5, flush=flush)
+                per[f"{variant}_k{k}"] = {"ms": ms, "tflops_2mnk": 2.0 * mm * mm * k / (ms * 1e-3) / 1e12}
+        small[str(mm)] = per
+    out["sweep_small"] = small
+
+    # end to end through host buffers: H2D of A and Omega, the sweep, D2H of Y
+    A_pin = torch.from_numpy(A_host).pin_memory()
+    Om_pin = torch.from_numpy(Om_host).pin_memory()
+    Yh = {k: torch.empty(M, k, dtype=torch.float32).pin_memory() for k in KS}
+
+    def e2e_step():
+        A.copy_(A_pin, non_blocking=True)
+        Om.copy_(Om_pin, non_blocking=True)
+        for k in KS:
+            shg.shgemm_project(A, Om[:, :k], "f16", out=Ys[k], flags=flags, check=False, stream=stream)
+            Yh[k].copy_(Ys[k], non_blocking=True)
+    e2e_step()
+    ms = time_ms(torch, stream, e2e_step, reps=3)
+    h2d = A_host.nbytes + Om_host.nbytes
+    d2h = sum(M * k * 4 for k in KS)
+    out["e2e"] = {"value": sum(2.0 * M * N * k for k in KS) / (ms * 1e-3) / 1e12, "unit": "TFLOP/s",
+                  "ms_per_step": ms, "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h}
+
+    # randomized SVD of the planted 1024^2 matrix and RP-HOSVD of the 512^3 tensor
+    out["rsvd_1024"] = rsvd_times(shg, torch, dev, stream)
+    out["rp_hosvd_512"] = hosvd_times(shg, torch, dev, stream)
+
+    # CPU baseline: the oracle on a bounded row sample of the same sweep
+    rate, rows_done, dt = oracle_rate(A_host, Om_host, budget_s=10.0)
+    out["cpu_baseline"] = {"value": rate, "unit": "TFLOP/s", "cores": os.cpu_count(), "kind": "oracle",
+                           "sample": f"first {rows_done} rows of A times Omega_k for all four k ({dt:.1f} s, "
+                                     "numpy float64)"}
+    return out
+
+
+def rsvd_times(shg, torch, dev, stream):
+    from synth import rsvd_planted
+    from oracle import rsvd as OR
+    A_h, Om_h = rsvd_planted(1024, 1024, rate=8.0, seed_a=0, seed_omega=1, k=64)
+    A = torch.from_numpy(A_h).to(dev)
+    Om = torch.from_numpy(Om_h).to(dev)
+    ws = torch.empty(shg.rsvd_workspace_size(1024, 1024, 32, 32, 0), dtype=torch.uint8, device=dev)
+    fl = shg.new_flags(dev)
+    res = {}
+    ref = OR.rsvd(A_h, Om_h, p=32)
+    for v in ("f16", "fp32"):
+        outs = (torch.empty(1024, 32, device=dev), torch.empty(32, device=dev), torch.empty(1024, 32, device=dev),
+                None)
+        fn = lambda: shg.shg_rsvd(A, Om, 32, 32, 0, v, workspace=ws, out=outs, flags=fl, check=False, stream=stream)
+        fn()
+        ms = time_ms(torch, stream, fn, reps=10)
+        U, S, V = (t.cpu().numpy().astype(np.float64) for t in outs[:3])
+        A64 = A_h.astype(np.float64)
+        r_p = np.linalg.norm(A64 - (U * S) @ V.T) / np.linalg.norm(A64)
+        res[v] = {"ms": ms, "sigma_max_rel_err": float(np.max(np.abs(S - ref["S"]) / ref["S"])),
+                  "residual": float(r_p), "oracle_residual": ref["r_p"]}
+    res["speedup_f16_vs_fp32"] = res["fp32"]["ms"] / res["f16"]["ms"]
+    return res
+
+
+def hosvd_times(shg, torch, dev, stream):
+    from synth import tucker, hosvd_omegas
+    dims, J = (512, 512, 512), (48, 48, 48)
+    A_h, _, _ = tucker(dims, (32, 32, 32), seed=3, noise_std=1e-4)
+    oms_h = hosvd_omegas(dims, J, seed=3)
+    X = torch.from_numpy(A_h).to(dev)
+    oms = [torch.from_numpy(o).to(dev) for o in oms_h]
+    ws = torch.empty(shg.rp_hosvd_workspace_size(dims, J), dtype=torch.uint8, device=dev)
+    fl = shg.new_flags(dev)
+    res = {}
+    for v in ("f16", "fp32"):
+        core = torch.empty(*J, device=dev)
+        facs = [torch.empty(512, 48, device=dev) for _ in range(3)]
+        fn = lambda: shg.shg_rp_hosvd(X, oms, J, v, workspace=ws, out=(core, facs), flags=fl, check=False,
+                                      stream=stream)
+        fn()
+        shg.check_flags(fl, "rp_hosvd")
+        ms = time_ms(torch, stream, fn, reps=5)
+        c = core.double()
+        Fs = [f.double() for f in facs]
+        rec = torch.einsum("abc,ia,jb,kc->ijk", c, Fs[0], Fs[1], Fs[2])
+        err = float(torch.linalg.norm(X.double() - rec) / torch.linalg.norm(X.double()))
+        res[v] = {"ms": ms, "rel_err": err}
+    res["speedup_f16_vs_fp32"] = res["fp32"]["ms"] / res["f16"]["ms"]
+    return res
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,187 @@
+/*
+ * shg.h - C ABI of libshg.so: mixed-precision random projection (SHGEMM) on
+ * GB300 tensor cores and the randomized factorizations built on it.
+ *
+ * Method: Ootomo & Yokota, "Mixed-Precision Random Projection for RandNLA on
+ * Tensor Cores", arXiv 2304.04612.  Section / equation / algorithm numbers
+ * below refer to that paper.
+ *
+ * Conventions shared by every entry point
+ * ---------------------------------------
+ * - Matrices are row-major.  "ld" arguments are leading dimensions in
+ *   elements (the distance between consecutive rows).
+ * - Every pointer to matrix data is a DEVICE pointer owned by the caller; the
+ *   library never allocates device memory.  Entry points that need scratch
+ *   memory take a caller-provided workspace whose size a *_workspace_size
+ *   query returns.
+ * - FP16 / BF16 data is passed as uint16_t bit patterns.
+ * - `stream` is a cudaStream_t (NULL = legacy default stream).  Calls are
+ *   asynchronous on it; nothing synchronises the stream.
+ * - Argument errors are detected on the host before any launch and returned
+ *   as SHG_ERR_INVALID_ARG.  CUDA launch errors return SHG_ERR_CUDA.
+ * - Conditions only the device can detect are OR-ed, as SHG_FLAG_* bits, into
+ *   the caller's device word `d_flags` (int32, caller zeroes it; must not be
+ *   NULL).  Read it back after the stream work finished and convert it with
+ *   shg_flags_status().  On any set flag the outputs are undefined.
+ * - Tensor-core paths stage operands with TMA: A / B base pointers must be
+ *   16-byte aligned and lda * sizeof(float), ldo * 2 multiples of 16 bytes
+ *   (lda % 4 == 0, ldo % 8 == 0); otherwise SHG_ERR_INVALID_ARG.
+ * - One GPU: the current CUDA device of the calling thread.
+ */
+#ifndef SHG_H
+#define SHG_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum shg_status {
+  SHG_OK = 0,
+  SHG_ERR_INVALID_ARG = 1,
+  SHG_ERR_RANGE = 2,        /* |a| >= 65520: A outside the FP16 range of SHGEMM-FP16 (Sec. 4.2) */
+  SHG_ERR_NOT_SPD = 3,      /* non-positive pivot in a CholeskyQR Gram factorisation */
+  SHG_ERR_WORKSPACE = 4,    /* workspace too small */
+  SHG_ERR_CUDA = 5,         /* a CUDA runtime call failed */
+  SHG_ERR_TIMEOUT = 6,      /* a bounded device-side wait gave up */
+  SHG_ERR_UNSUPPORTED = 7   /* valid request this build does not implement */
+} shg_status;
+
+/* Device flag bits written to *d_flags. */
+#define SHG_FLAG_RANGE   1
+#define SHG_FLAG_NOT_SPD 2
+#define SHG_FLAG_TIMEOUT 4
+
+typedef enum shg_variant {
+  SHG_SPLIT_F16 = 0,    /* SHGEMM-FP16: A -> FP16 hi + 2^11-scaled FP16 lo, two tensor-core products (Eqs. shgemm-1..3) */
+  SHG_SPLIT_BF16X3 = 1, /* A -> three BF16 pieces at 2^0, 2^-8, 2^-16; Omega must be BF16 (RN of the FP16 Omega) */
+  SHG_SPLIT_BF16X2 = 2, /* A -> two BF16 pieces; Omega BF16 */
+  SHG_FP32_SIMT = 3     /* plain FP32 SIMT SGEMM with FP16 Omega widened exactly to FP32 (the single-precision baseline) */
+} shg_variant;
+
+/* Human-readable name of a shg_status value. Never NULL. */
+const char* shg_status_string(int status);
+
+/* Library ABI version (major * 100 + minor). */
+int shg_version(void);
+
+/* Map d_flags bits to the most severe status (TIMEOUT > NOT_SPD > RANGE > OK). */
+int shg_flags_status(int32_t flags);
+
+/*
+ * A1. Gaussian test matrix (Sec. 3.1; Sec. 3.3 generates N(0,1) in FP32 and
+ * rounds it RN to the low format).  out[r*ld + c], 0 <= r < rows,
+ * 0 <= c < cols, receives RN_fp16(z_e) where e = r*cols + c and z_e is
+ * normal (e mod 4) of the Box-Muller pairs of Philox4x32-10 block
+ * (e div 4) + offset under key (seed lo, seed hi).  Deterministic; the same
+ * element always gets the same value whatever the launch shape.
+ * Errors: rows, cols < 0, ld < cols, out == NULL (when rows*cols > 0).
+ */
+int shg_gaussian_f16(uint64_t seed, uint64_t offset, int64_t rows, int64_t cols,
+                     uint16_t* out, int64_t ld, void* stream);
+
+/*
+ * A2-A4. Random projection Y = op(A) * Omega (Eq. rp-vec) by SHGEMM
+ * (Sec. 4.1, Eqs. shgemm-1..3): A is split in shared memory into
+ * hi = RN_fp16(a) and lo = RN_fp16((a - hi) * 2^11), both multiplied with the
+ * FP16 Omega on tcgen05 tensor cores into FP32 TMEM accumulators, and
+ * recombined as Y = acc_hi + 2^-11 acc_lo in FP32.
+ *
+ *   trans_a = 0: A is m x n (lda >= n), Y = A * Omega.
+ *   trans_a = 1: A is n x m (lda >= m), Y = A^T * Omega.
+ *   Omega: n x k (ldo >= k), FP16 bits (BF16 bits for SHG_SPLIT_BF16X*).
+ *   Y: m x k FP32 (ldy >= k), overwritten.
+ * variant: shg_variant.  SHG_SPLIT_BF16X* support trans_a = 0 only.
+ * Device flags: SHG_FLAG_RANGE when some |a| >= 65520 under SHG_SPLIT_F16.
+ * m, n, k >= 1 and < 2^31.
+ */
+int shgemm_project(int64_t m, int64_t n, int64_t k,
+                   const float* A, int64_t lda, int trans_a,
+                   const uint16_t* omega, int64_t ldo,
+                   float* Y, int64_t ldy,
+                   int variant, int32_t* d_flags, void* stream);
+
+/*
+ * FP32-accurate product C (+)= op(A) * B of two FP32 matrices by the
+ * TCEC split (Eq. tcec-5): hiA*hiB + (loA*hiB + hiA*loB) * 2^-11 on FP16
+ * tensor cores.  Used for B = Q^T A of Algorithm 1 (line 3) and the core
+ * contraction of Algorithm 2 (line 5).
+ *   trans_a = 0: A m x kk (lda >= kk); trans_a = 1: A kk x m (lda >= m).
+ *   B: kk x n (ldb >= n, ldb % 4 == 0).  C: m x n (ldc >= n).
+ *   accumulate = 0: C = op(A) B; 1: C += op(A) B.
+ * Device flags: SHG_FLAG_RANGE when a value of A or B is >= 65520 in magnitude.
+ */
+int shg_gemm_split3(int64_t m, int64_t n, int64_t kk,
+                    const float* A, int64_t lda, int trans_a,
+                    const float* B, int64_t ldb,
+                    float* C, int64_t ldc, int accumulate,
+                    int32_t* d_flags, void* stream);
+
+/*
+ * Plain FP32 SIMT GEMM C (+)= op(A) * B (the single-precision baseline the
+ * paper compares with, Sec. 4.4).  Each output is accumulated sequentially
+ * in FP32 by FMA.  B is FP32 (b_f16 = 0) or FP16 bits widened exactly to
+ * FP32 (b_f16 = 1).  Shapes as in shg_gemm_split3.
+ */
+int shg_sgemm(int64_t m, int64_t n, int64_t kk,
+              const float* A, int64_t lda, int trans_a,
+              const void* B, int64_t ldb, int b_f16,
+              float* C, int64_t ldc, int accumulate, void* stream);
+
+/*
+ * CholeskyQR2 (orthonormal basis of Algorithm 1 line 2 / Algorithm 2 line 4):
+ * twice { G = X^T X (FP64 accumulation), G = R^T R (FP64 Cholesky),
+ * X <- X R^-1 }.  X: m x k FP32 (ldx >= k), overwritten by Q with
+ * Q^T Q = I and X_in = Q R, diag(R) > 0.  k <= m, k <= 1024.
+ * Device flags: SHG_FLAG_NOT_SPD on a non-positive pivot.
+ */
+int shg_cholqr2_workspace_size(int64_t m, int64_t k, size_t* bytes);
+int shg_cholqr2(int64_t m, int64_t k, float* X, int64_t ldx,
+                void* workspace, size_t ws_bytes, int32_t* d_flags, void* stream);
+
+/*
+ * Randomized SVD, Algorithm 1 with the power scheme of Sec. 2.1:
+ *   Y = A Omega; Q = orth(Y); q times { Z = orth(A^T fp16(Q)); Q = orth(A fp16(Z)) };
+ *   B = Q^T A; U' S V'^T = tSVD(B, rank); U = Q U'.
+ * k = rank + oversampling (p-hat of Sec. 2.2), 1 <= rank, k <= min(m, n), k <= 1024.
+ *   A: m x n FP32 (lda >= n).  omega: n x k FP16 bits (BF16 bits for the BF16
+ *   variants), ldo >= k.
+ *   U: m x rank (ld rank), S: rank (descending), V: n x rank (ld rank), all FP32,
+ *   A ~= U diag(S) V^T.  Q_out: NULL or m x k FP32 (ld k), receives Q.
+ * variant selects how the projections (Y = A Omega and the power-scheme
+ * products) are computed: SHG_SPLIT_F16 / BF16X* (tensor cores, B = Q^T A by
+ * the TCEC split) or SHG_FP32_SIMT (every GEMM in FP32 SIMT: the
+ * single-precision baseline).  Gram matrices and Cholesky are FP64, the
+ * k x k eigensolver of B B^T is FP32 Jacobi refined by FP64 Rayleigh
+ * quotients.
+ * Device flags: RANGE, NOT_SPD, TIMEOUT.
+ */
+int shg_rsvd_workspace_size(int64_t m, int64_t n, int64_t rank, int64_t oversampling,
+                            int power_iters, size_t* bytes);
+int shg_rsvd(int64_t m, int64_t n, int64_t rank, int64_t oversampling, int power_iters,
+             const float* A, int64_t lda, const uint16_t* omega, int64_t ldo,
+             float* U, float* S, float* V, float* Q_out,
+             void* workspace, size_t ws_bytes, int variant, int32_t* d_flags, void* stream);
+
+/*
+ * Random-projection HOSVD, Algorithm 2 (Sec. 5.2), for a 3-way tensor
+ * X[i0][i1][i2] (row-major, last index fastest, dims[0..2]).
+ *   ranks[i] = J_i (target rank plus oversampling), 1 <= J_i <= dims[i], J_i <= 256.
+ *   omegas[i]: FP16 bits, (prod_{j != i} dims[j]) x J_i, ld J_i; its row index
+ *   is the row-major linear index of the other modes (i0*I2 + i2 for mode 1).
+ *   W_i = X_(i) Omega_i; Q_i = CholeskyQR2(W_i) -> factors[i] (dims[i] x J_i, ld J_i).
+ *   core (J0 x J1 x J2, row-major) = X x_0 Q_0^T x_1 Q_1^T x_2 Q_2^T.
+ * variant: SHG_SPLIT_F16 (SHGEMM projections, TCEC-split first core
+ * contraction) or SHG_FP32_SIMT (FP32 baseline).
+ */
+int shg_rp_hosvd_workspace_size(int ndim, const int64_t* dims, const int64_t* ranks, size_t* bytes);
+int shg_rp_hosvd(int ndim, const int64_t* dims, const int64_t* ranks, const float* X,
+                 const uint16_t* const* omegas, float* core, float* const* factors,
+                 void* workspace, size_t ws_bytes, int variant, int32_t* d_flags, void* stream);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* SHG_H */

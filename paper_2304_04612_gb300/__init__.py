@@ -1,0 +1,246 @@
+"""GB300-native mixed-precision random projection (SHGEMM) and the randomized
+factorizations built on it (Ootomo & Yokota, arXiv 2304.04612).
+
+This module is a thin binding over the C ABI of ``libshg.so``
+(include/shg.h): it checks tensors, passes device pointers, leading
+dimensions and the current CUDA stream, and turns status codes into
+exceptions.  Every computation runs in the library's CUDA kernels; PyTorch
+only provides device memory and streams.
+
+Functions (same names as the C entry points)
+--------------------------------------------
+shg_gaussian_f16   FP16 Gaussian test matrix (Philox4x32-10 + Box-Muller, RN)
+shgemm_project     Y = op(A) Omega by SHGEMM (or the BF16 / FP32 SIMT variants)
+shg_gemm_split3    FP32-accurate op(A) B of two FP32 matrices (TCEC split)
+shg_sgemm          plain FP32 SIMT GEMM (the single-precision baseline)
+shg_cholqr2        CholeskyQR2 orthonormalisation (in place)
+shg_rsvd           randomized SVD (Algorithm 1, power scheme of Sec. 2.1)
+shg_rp_hosvd       random-projection HOSVD of a 3-way tensor (Algorithm 2)
+"""
+from __future__ import annotations
+
+import ctypes
+
+import torch
+
+from . import _lib
+
+VARIANTS = {"f16": 0, "bf16x3": 1, "bf16x2": 2, "fp32": 3}
+FLAG_RANGE, FLAG_NOT_SPD, FLAG_TIMEOUT = 1, 2, 4
+
+
+class ShgError(RuntimeError):
+    def __init__(self, status: int, where: str):
+        self.status = status
+        msg = _lib.load().shg_status_string(status).decode()
+        super().__init__(f"{where}: {msg} (status {status})")
+
+
+def _check(rc: int, where: str):
+    if rc != 0:
+        raise ShgError(rc, where)
+
+
+def _stream(stream):
+    s = stream if stream is not None else torch.cuda.current_stream()
+    return ctypes.c_void_p(s.cuda_stream)
+
+
+def _ptr(t):
+    return ctypes.c_void_p(t.data_ptr()) if t is not None else ctypes.c_void_p(0)
+
+
+def _mat(t: torch.Tensor, name: str, dtypes):
+    if not isinstance(t, torch.Tensor) or not t.is_cuda:
+        raise TypeError(f"{name} must be a CUDA tensor")
+    if t.dtype not in dtypes:
+        raise TypeError(f"{name} must have dtype in {dtypes}, got {t.dtype}")
+    if t.dim() != 2 or t.stride(1) != 1:
+        raise ValueError(f"{name} must be a 2-D row-major tensor (unit column stride)")
+    return t.stride(0) if t.shape[0] > 1 else max(t.shape[1], t.stride(0))
+
+
+def _variant(v):
+    if isinstance(v, str):
+        return VARIANTS[v]
+    return int(v)
+
+
+def new_flags(device=None) -> torch.Tensor:
+    """A zeroed device word for the SHG_FLAG_* bits."""
+    return torch.zeros(1, dtype=torch.int32, device=device or "cuda")
+
+
+def check_flags(flags: torch.Tensor, where: str = "shg"):
+    """Synchronise on the flags word and raise ShgError when a bit is set."""
+    f = int(flags.item())
+    _check(_lib.load().shg_flags_status(f), where)
+
+
+def shg_gaussian_f16(seed: int, offset: int, rows: int, cols: int, out: torch.Tensor | None = None,
+                     stream=None) -> torch.Tensor:
+    if out is None:
+        out = torch.empty(rows, cols, dtype=torch.float16, device="cuda")
+    ld = _mat(out, "out", (torch.float16,))
+    _check(_lib.load().shg_gaussian_f16(seed, offset, rows, cols, _ptr(out), ld, _stream(stream)),
+           "shg_gaussian_f16")
+    return out
+
+
+def shgemm_project(A: torch.Tensor, omega: torch.Tensor, variant="f16", trans_a: bool = False,
+                   out: torch.Tensor | None = None, flags: torch.Tensor | None = None,
+                   check: bool = True, stream=None) -> torch.Tensor:
+    """Y = A @ omega (trans_a: A.T @ omega).  omega: float16 (bfloat16 for the
+    BF16 variants).  With check=True the call synchronises and raises on a
+    device flag (e.g. SHG_ERR_RANGE)."""
+    v = _variant(variant)
+    lda = _mat(A, "A", (torch.float32,))
+    ldo = _mat(omega, "omega", (torch.bfloat16,) if v in (1, 2) else (torch.float16,))
+    m = A.shape[1] if trans_a else A.shape[0]
+    n = A.shape[0] if trans_a else A.shape[1]
+    k = omega.shape[1]
+    if omega.shape[0] != n:
+        raise ValueError(f"omega has {omega.shape[0]} rows, expected {n}")
+    if out is None:
+        out = torch.empty(m, k, dtype=torch.float32, device=A.device)
+    ldy = _mat(out, "out", (torch.float32,))
+    fl = flags if flags is not None else new_flags(A.device)
+    _check(_lib.load().shgemm_project(m, n, k, _ptr(A), lda, int(trans_a), _ptr(omega), ldo, _ptr(out), ldy,
+                                      v, _ptr(fl), _stream(stream)), "shgemm_project")
+    if check:
+        check_flags(fl, "shgemm_project")
+    return out
+
+
+def shg_gemm_split3(A: torch.Tensor, B: torch.Tensor, trans_a: bool = False, out: torch.Tensor | None = None,
+                    accumulate: bool = False, flags: torch.Tensor | None = None, check: bool = True,
+                    stream=None) -> torch.Tensor:
+    lda = _mat(A, "A", (torch.float32,))
+    ldb = _mat(B, "B", (torch.float32,))
+    m = A.shape[1] if trans_a else A.shape[0]
+    kk = A.shape[0] if trans_a else A.shape[1]
+    n = B.shape[1]
+    if B.shape[0] != kk:
+        raise ValueError("inner dimensions differ")
+    if out is None:
+        out = torch.empty(m, n, dtype=torch.float32, device=A.device)
+    ldc = _mat(out, "out", (torch.float32,))
+    fl = flags if flags is not None else new_flags(A.device)
+    _check(_lib.load().shg_gemm_split3(m, n, kk, _ptr(A), lda, int(trans_a), _ptr(B), ldb, _ptr(out), ldc,
+                                       int(accumulate), _ptr(fl), _stream(stream)), "shg_gemm_split3")
+    if check:
+        check_flags(fl, "shg_gemm_split3")
+    return out
+
+
+def shg_sgemm(A: torch.Tensor, B: torch.Tensor, trans_a: bool = False, out: torch.Tensor | None = None,
+              accumulate: bool = False, stream=None) -> torch.Tensor:
+    lda = _mat(A, "A", (torch.float32,))
+    ldb = _mat(B, "B", (torch.float32, torch.float16))
+    m = A.shape[1] if trans_a else A.shape[0]
+    kk = A.shape[0] if trans_a else A.shape[1]
+    n = B.shape[1]
+    if B.shape[0] != kk:
+        raise ValueError("inner dimensions differ")
+    if out is None:
+        out = torch.empty(m, n, dtype=torch.float32, device=A.device)
+    ldc = _mat(out, "out", (torch.float32,))
+    _check(_lib.load().shg_sgemm(m, n, kk, _ptr(A), lda, int(trans_a), _ptr(B), ldb,
+                                 int(B.dtype == torch.float16), _ptr(out), ldc, int(accumulate), _stream(stream)),
+           "shg_sgemm")
+    return out
+
+
+def shg_cholqr2(X: torch.Tensor, workspace: torch.Tensor | None = None, flags: torch.Tensor | None = None,
+                check: bool = True, stream=None) -> torch.Tensor:
+    ldx = _mat(X, "X", (torch.float32,))
+    m, k = X.shape
+    lib = _lib.load()
+    need = ctypes.c_size_t()
+    _check(lib.shg_cholqr2_workspace_size(m, k, ctypes.byref(need)), "shg_cholqr2_workspace_size")
+    ws = workspace if workspace is not None else torch.empty(need.value, dtype=torch.uint8, device=X.device)
+    fl = flags if flags is not None else new_flags(X.device)
+    _check(lib.shg_cholqr2(m, k, _ptr(X), ldx, _ptr(ws), ws.numel(), _ptr(fl), _stream(stream)), "shg_cholqr2")
+    if check:
+        check_flags(fl, "shg_cholqr2")
+    return X
+
+
+def rsvd_workspace_size(m: int, n: int, rank: int, oversampling: int, power_iters: int = 0) -> int:
+    need = ctypes.c_size_t()
+    _check(_lib.load().shg_rsvd_workspace_size(m, n, rank, oversampling, power_iters, ctypes.byref(need)),
+           "shg_rsvd_workspace_size")
+    return need.value
+
+
+def shg_rsvd(A: torch.Tensor, omega: torch.Tensor, rank: int, oversampling: int, power_iters: int = 0,
+             variant="f16", want_q: bool = False, workspace: torch.Tensor | None = None,
+             out=None, flags: torch.Tensor | None = None, check: bool = True, stream=None):
+    """Randomized SVD (Algorithm 1).  Returns (U, S, V[, Q]) with A ~= U diag(S) V^T."""
+    v = _variant(variant)
+    lda = _mat(A, "A", (torch.float32,))
+    ldo = _mat(omega, "omega", (torch.bfloat16,) if v in (1, 2) else (torch.float16,))
+    m, n = A.shape
+    k = rank + oversampling
+    if omega.shape != (n, k):
+        raise ValueError(f"omega must be {n} x {k}")
+    dev = A.device
+    if out is None:
+        U = torch.empty(m, rank, dtype=torch.float32, device=dev)
+        S = torch.empty(rank, dtype=torch.float32, device=dev)
+        V = torch.empty(n, rank, dtype=torch.float32, device=dev)
+        Q = torch.empty(m, k, dtype=torch.float32, device=dev) if want_q else None
+    else:
+        U, S, V, Q = out
+    need = rsvd_workspace_size(m, n, rank, oversampling, power_iters)
+    ws = workspace if workspace is not None else torch.empty(need, dtype=torch.uint8, device=dev)
+    fl = flags if flags is not None else new_flags(dev)
+    _check(_lib.load().shg_rsvd(m, n, rank, oversampling, power_iters, _ptr(A), lda, _ptr(omega), ldo,
+                                _ptr(U), _ptr(S), _ptr(V), _ptr(Q), _ptr(ws), ws.numel(), v, _ptr(fl),
+                                _stream(stream)), "shg_rsvd")
+    if check:
+        check_flags(fl, "shg_rsvd")
+    return (U, S, V, Q) if want_q else (U, S, V)
+
+
+def rp_hosvd_workspace_size(dims, ranks) -> int:
+    d = (ctypes.c_int64 * 3)(*dims)
+    r = (ctypes.c_int64 * 3)(*ranks)
+    need = ctypes.c_size_t()
+    _check(_lib.load().shg_rp_hosvd_workspace_size(3, d, r, ctypes.byref(need)), "shg_rp_hosvd_workspace_size")
+    return need.value
+
+
+def shg_rp_hosvd(X: torch.Tensor, omegas, ranks, variant="f16", workspace: torch.Tensor | None = None,
+                 out=None, flags: torch.Tensor | None = None, check: bool = True, stream=None):
+    """RP-HOSVD (Algorithm 2) of a contiguous 3-way float32 tensor.  Returns
+    (core J0 x J1 x J2, [Q_0, Q_1, Q_2])."""
+    if X.dim() != 3 or not X.is_contiguous() or X.dtype != torch.float32 or not X.is_cuda:
+        raise ValueError("X must be a contiguous 3-way float32 CUDA tensor")
+    dims = list(X.shape)
+    ranks = [int(r) for r in ranks]
+    for i, om in enumerate(omegas):
+        rows = 1
+        for j, d in enumerate(dims):
+            if j != i:
+                rows *= d
+        if om.dtype != torch.float16 or tuple(om.shape) != (rows, ranks[i]) or not om.is_contiguous():
+            raise ValueError(f"omega {i} must be a contiguous float16 {rows} x {ranks[i]} tensor")
+    dev = X.device
+    if out is None:
+        core = torch.empty(*ranks, dtype=torch.float32, device=dev)
+        facs = [torch.empty(dims[i], ranks[i], dtype=torch.float32, device=dev) for i in range(3)]
+    else:
+        core, facs = out
+    need = rp_hosvd_workspace_size(dims, ranks)
+    ws = workspace if workspace is not None else torch.empty(need, dtype=torch.uint8, device=dev)
+    fl = flags if flags is not None else new_flags(dev)
+    d = (ctypes.c_int64 * 3)(*dims)
+    r = (ctypes.c_int64 * 3)(*ranks)
+    om_ptrs = (ctypes.c_void_p * 3)(*[o.data_ptr() for o in omegas])
+    f_ptrs = (ctypes.c_void_p * 3)(*[f.data_ptr() for f in facs])
+    _check(_lib.load().shg_rp_hosvd(3, d, r, _ptr(X), om_ptrs, _ptr(core), f_ptrs, _ptr(ws), ws.numel(),
+                                    _variant(variant), _ptr(fl), _stream(stream)), "shg_rp_hosvd")
+    if check:
+        check_flags(fl, "shg_rp_hosvd")
+    return core, facs

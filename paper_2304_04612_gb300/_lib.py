@@ -1,0 +1,61 @@
+"""ctypes loader of libshg.so and the raw C signatures of include/shg.h.
+
+The library is built in-tree by ``paper_2304_04612_gb300.build``; loading
+fails loudly when it is missing.  There is no other implementation to fall
+back to.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "libshg.so")
+
+c_i64 = ctypes.c_int64
+c_int = ctypes.c_int
+c_u64 = ctypes.c_uint64
+c_vp = ctypes.c_void_p
+c_sz = ctypes.c_size_t
+
+# name -> (restype, argtypes), mirroring include/shg.h
+SIGNATURES = {
+    "shg_status_string": (ctypes.c_char_p, [c_int]),
+    "shg_version": (c_int, []),
+    "shg_flags_status": (c_int, [ctypes.c_int32]),
+    "shg_gaussian_f16": (c_int, [c_u64, c_u64, c_i64, c_i64, c_vp, c_i64, c_vp]),
+    "shgemm_project": (c_int, [c_i64, c_i64, c_i64, c_vp, c_i64, c_int, c_vp, c_i64, c_vp, c_i64,
+                               c_int, c_vp, c_vp]),
+    "shg_gemm_split3": (c_int, [c_i64, c_i64, c_i64, c_vp, c_i64, c_int, c_vp, c_i64, c_vp, c_i64,
+                                c_int, c_vp, c_vp]),
+    "shg_sgemm": (c_int, [c_i64, c_i64, c_i64, c_vp, c_i64, c_int, c_vp, c_i64, c_int, c_vp, c_i64,
+                          c_int, c_vp]),
+    "shg_cholqr2_workspace_size": (c_int, [c_i64, c_i64, ctypes.POINTER(c_sz)]),
+    "shg_cholqr2": (c_int, [c_i64, c_i64, c_vp, c_i64, c_vp, c_sz, c_vp, c_vp]),
+    "shg_rsvd_workspace_size": (c_int, [c_i64, c_i64, c_i64, c_i64, c_int, ctypes.POINTER(c_sz)]),
+    "shg_rsvd": (c_int, [c_i64, c_i64, c_i64, c_i64, c_int, c_vp, c_i64, c_vp, c_i64, c_vp, c_vp, c_vp,
+                         c_vp, c_vp, c_sz, c_int, c_vp, c_vp]),
+    "shg_rp_hosvd_workspace_size": (c_int, [c_int, ctypes.POINTER(c_i64), ctypes.POINTER(c_i64),
+                                            ctypes.POINTER(c_sz)]),
+    "shg_rp_hosvd": (c_int, [c_int, ctypes.POINTER(c_i64), ctypes.POINTER(c_i64), c_vp,
+                             ctypes.POINTER(c_vp), c_vp, ctypes.POINTER(c_vp), c_vp, c_sz, c_int, c_vp, c_vp]),
+}
+
+_lib = None
+
+
+def load() -> ctypes.CDLL:
+    """Load libshg.so (once) and attach the argument types."""
+    global _lib
+    if _lib is None:
+        if not os.path.exists(LIB_PATH):
+            raise RuntimeError(
+                f"{LIB_PATH} is missing: build it with `python -m paper_2304_04612_gb300.build` "
+                "(or __graft_entry__.build()); there is no fallback implementation")
+        lib = ctypes.CDLL(LIB_PATH)
+        for name, (res, args) in SIGNATURES.items():
+            f = getattr(lib, name)
+            f.restype = res
+            f.argtypes = args
+        _lib = lib
+    return _lib

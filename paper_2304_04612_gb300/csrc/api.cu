@@ -1,0 +1,315 @@
+// extern "C" entry points of libshg.so (declared in include/shg.h):
+// argument validation on the host, then the launches of Algorithm 1
+// (randomized SVD) and Algorithm 2 (RP-HOSVD) on the caller's stream.
+#include <cstring>
+
+#include "internal.h"
+#include "linalg.h"
+
+namespace shg {
+
+int sm_count() {
+  static int cache[64] = {0};
+  int dev = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess || dev < 0) return -1;
+  if (dev < 64 && cache[dev] > 0) return cache[dev];
+  int n = 0;
+  if (cudaDeviceGetAttribute(&n, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess) return -1;
+  if (dev < 64) cache[dev] = n;
+  return n;
+}
+
+int ceil_div_i(int64_t a, int64_t b) { return static_cast<int>((a + b - 1) / b); }
+
+namespace {
+
+inline int64_t round8(int64_t x) { return (x + 7) / 8 * 8; }
+
+bool tc_variant(int v) { return v == SHG_SPLIT_F16 || v == SHG_SPLIT_BF16X3 || v == SHG_SPLIT_BF16X2; }
+
+// Workspace layout of shg_rsvd.
+struct RsvdLayout {
+  size_t Y, T, Z, H, Bt, small, Vk, lam, Up, Ups, total;
+};
+RsvdLayout rsvd_layout(int64_t m, int64_t n, int64_t k, int64_t rank) {
+  const int64_t ldk = round8(k), mx = m > n ? m : n;
+  RsvdLayout L{};
+  size_t off = 0;
+  auto take = [&](size_t bytes) {
+    const size_t o = off;
+    off += align256(bytes);
+    return o;
+  };
+  L.Y = take(m * ldk * 4);
+  L.T = take(mx * ldk * 4);
+  L.Z = take(n * ldk * 4);
+  L.H = take(mx * ldk * 2);
+  L.Bt = take(n * ldk * 4);
+  L.small = take(cholqr_small_bytes(k));
+  L.Vk = take(k * k * 4);
+  L.lam = take(k * 8);
+  L.Up = take(k * rank * 4);
+  L.Ups = take(k * rank * 4);
+  L.total = off;
+  return L;
+}
+
+struct HosvdLayout {
+  size_t W[3], T, T1, T2, small, total;
+  int64_t ld[3];
+};
+HosvdLayout hosvd_layout(const int64_t* d, const int64_t* J) {
+  HosvdLayout L{};
+  size_t off = 0;
+  auto take = [&](size_t bytes) {
+    const size_t o = off;
+    off += align256(bytes);
+    return o;
+  };
+  int64_t maxI = 0, maxL = 0, maxJ = 0;
+  for (int i = 0; i < 3; ++i) {
+    L.ld[i] = round8(J[i]);
+    L.W[i] = take(d[i] * L.ld[i] * 4);
+    maxI = d[i] > maxI ? d[i] : maxI;
+    maxL = L.ld[i] > maxL ? L.ld[i] : maxL;
+    maxJ = J[i] > maxJ ? J[i] : maxJ;
+  }
+  L.T = take(maxI * maxL * 4);
+  L.T1 = take(d[0] * d[1] * L.ld[2] * 4);
+  L.T2 = take(d[0] * J[1] * J[2] * 4);
+  L.small = take(cholqr_small_bytes(maxJ));
+  L.total = off;
+  return L;
+}
+
+#define SHG_TRY(x)            \
+  do {                        \
+    const int rc_ = (x);      \
+    if (rc_ != SHG_OK) return rc_; \
+  } while (0)
+
+}  // namespace
+}  // namespace shg
+
+using namespace shg;
+
+extern "C" {
+
+const char* shg_status_string(int s) {
+  switch (s) {
+    case SHG_OK: return "SHG_OK";
+    case SHG_ERR_INVALID_ARG: return "SHG_ERR_INVALID_ARG";
+    case SHG_ERR_RANGE: return "SHG_ERR_RANGE: |A| exceeds the FP16 range of SHGEMM-FP16";
+    case SHG_ERR_NOT_SPD: return "SHG_ERR_NOT_SPD: non-positive pivot in CholeskyQR";
+    case SHG_ERR_WORKSPACE: return "SHG_ERR_WORKSPACE: workspace too small";
+    case SHG_ERR_CUDA: return "SHG_ERR_CUDA";
+    case SHG_ERR_TIMEOUT: return "SHG_ERR_TIMEOUT: a bounded device wait gave up";
+    case SHG_ERR_UNSUPPORTED: return "SHG_ERR_UNSUPPORTED";
+    default: return "unknown shg_status";
+  }
+}
+
+int shg_version(void) { return 100; }
+
+int shg_flags_status(int32_t f) {
+  if (f & SHG_FLAG_TIMEOUT) return SHG_ERR_TIMEOUT;
+  if (f & SHG_FLAG_NOT_SPD) return SHG_ERR_NOT_SPD;
+  if (f & SHG_FLAG_RANGE) return SHG_ERR_RANGE;
+  return SHG_OK;
+}
+
+int shgemm_project(int64_t m, int64_t n, int64_t k, const float* A, int64_t lda, int trans_a,
+                   const uint16_t* omega, int64_t ldo, float* Y, int64_t ldy, int variant, int32_t* d_flags,
+                   void* stream) {
+  if (m < 1 || n < 1 || k < 1 || !A || !omega || !Y || !d_flags) return SHG_ERR_INVALID_ARG;
+  if (lda < (trans_a ? m : n) || ldo < k || ldy < k) return SHG_ERR_INVALID_ARG;
+  cudaStream_t st = static_cast<cudaStream_t>(stream);
+  switch (variant) {
+    case SHG_SPLIT_F16:
+      return tc_gemm(trans_a ? A_MNMAJ : A_KMAJ, B_F16, 2, m, k, n, 1, A, lda, 0, omega, ldo, Y, ldy, 0,
+                     d_flags, st);
+    case SHG_SPLIT_BF16X3:
+    case SHG_SPLIT_BF16X2:
+      if (trans_a) return SHG_ERR_UNSUPPORTED;
+      return tc_gemm(A_KMAJ, B_BF16, variant == SHG_SPLIT_BF16X3 ? 3 : 2, m, k, n, 1, A, lda, 0, omega, ldo, Y,
+                     ldy, 0, d_flags, st);
+    case SHG_FP32_SIMT:
+      return simt_gemm(m, k, n, A, lda, trans_a, omega, ldo, 1, Y, ldy, 0, 1, 0, 0, 0, st);
+    default:
+      return SHG_ERR_INVALID_ARG;
+  }
+}
+
+int shg_gemm_split3(int64_t m, int64_t n, int64_t kk, const float* A, int64_t lda, int trans_a, const float* B,
+                    int64_t ldb, float* C, int64_t ldc, int accumulate, int32_t* d_flags, void* stream) {
+  if (m < 1 || n < 1 || kk < 1 || !A || !B || !C || !d_flags) return SHG_ERR_INVALID_ARG;
+  if (lda < (trans_a ? m : kk) || ldb < n || ldc < n) return SHG_ERR_INVALID_ARG;
+  return tc_gemm(trans_a ? A_MNMAJ : A_KMAJ, B_SPLIT, 2, m, n, kk, 1, A, lda, 0, B, ldb, C, ldc, accumulate,
+                 d_flags, static_cast<cudaStream_t>(stream));
+}
+
+int shg_sgemm(int64_t m, int64_t n, int64_t kk, const float* A, int64_t lda, int trans_a, const void* B,
+              int64_t ldb, int b_f16, float* C, int64_t ldc, int accumulate, void* stream) {
+  if (m < 1 || n < 1 || kk < 1 || !A || !B || !C) return SHG_ERR_INVALID_ARG;
+  if (lda < (trans_a ? m : kk) || ldb < n || ldc < n) return SHG_ERR_INVALID_ARG;
+  return simt_gemm(m, n, kk, A, lda, trans_a, B, ldb, b_f16, C, ldc, accumulate, 1, 0, 0, 0,
+                   static_cast<cudaStream_t>(stream));
+}
+
+int shg_cholqr2_workspace_size(int64_t m, int64_t k, size_t* bytes) {
+  if (!bytes || k < 1 || m < k || k > 1024) return SHG_ERR_INVALID_ARG;
+  *bytes = align256(static_cast<size_t>(m) * k * 4) + cholqr_small_bytes(k);
+  return SHG_OK;
+}
+
+int shg_cholqr2(int64_t m, int64_t k, float* X, int64_t ldx, void* ws, size_t ws_bytes, int32_t* d_flags,
+                void* stream) {
+  size_t need = 0;
+  if (shg_cholqr2_workspace_size(m, k, &need) != SHG_OK) return SHG_ERR_INVALID_ARG;
+  if (!X || ldx < k || !d_flags || !ws) return SHG_ERR_INVALID_ARG;
+  if (ws_bytes < need) return SHG_ERR_WORKSPACE;
+  cudaStream_t st = static_cast<cudaStream_t>(stream);
+  float* T = static_cast<float*>(ws);
+  void* small = static_cast<uint8_t*>(ws) + align256(static_cast<size_t>(m) * k * 4);
+  return cholqr2(m, k, X, ldx, T, k, small, d_flags, st);
+}
+
+int shg_rsvd_workspace_size(int64_t m, int64_t n, int64_t rank, int64_t oversampling, int power_iters,
+                            size_t* bytes) {
+  if (!bytes || m < 1 || n < 1 || rank < 1 || oversampling < 0 || power_iters < 0) return SHG_ERR_INVALID_ARG;
+  const int64_t k = rank + oversampling;
+  if (k > m || k > n || k > 1024) return SHG_ERR_INVALID_ARG;
+  *bytes = rsvd_layout(m, n, k, rank).total;
+  return SHG_OK;
+}
+
+int shg_rsvd(int64_t m, int64_t n, int64_t rank, int64_t oversampling, int power_iters, const float* A,
+             int64_t lda, const uint16_t* omega, int64_t ldo, float* U, float* S, float* V, float* Q_out,
+             void* ws, size_t ws_bytes, int variant, int32_t* d_flags, void* stream) {
+  size_t need = 0;
+  if (shg_rsvd_workspace_size(m, n, rank, oversampling, power_iters, &need) != SHG_OK) return SHG_ERR_INVALID_ARG;
+  if (!A || !omega || !U || !S || !V || !ws || !d_flags || lda < n) return SHG_ERR_INVALID_ARG;
+  if (variant < SHG_SPLIT_F16 || variant > SHG_FP32_SIMT) return SHG_ERR_INVALID_ARG;
+  const int64_t k = rank + oversampling;
+  if (ldo < k) return SHG_ERR_INVALID_ARG;
+  if (ws_bytes < need) return SHG_ERR_WORKSPACE;
+  cudaStream_t st = static_cast<cudaStream_t>(stream);
+  const RsvdLayout L = rsvd_layout(m, n, k, rank);
+  uint8_t* w = static_cast<uint8_t*>(ws);
+  float* Y = reinterpret_cast<float*>(w + L.Y);
+  float* T = reinterpret_cast<float*>(w + L.T);
+  float* Z = reinterpret_cast<float*>(w + L.Z);
+  uint16_t* H = reinterpret_cast<uint16_t*>(w + L.H);
+  float* Bt = reinterpret_cast<float*>(w + L.Bt);
+  void* small = w + L.small;
+  float* Vk = reinterpret_cast<float*>(w + L.Vk);
+  double* lam = reinterpret_cast<double*>(w + L.lam);
+  float* Up = reinterpret_cast<float*>(w + L.Up);
+  float* Ups = reinterpret_cast<float*>(w + L.Ups);
+  const int64_t ldk = round8(k);
+  const bool tc = tc_variant(variant);
+
+  // line 1: Y = A Omega
+  SHG_TRY(shgemm_project(m, n, k, A, lda, 0, omega, ldo, Y, ldk, variant, d_flags, stream));
+  // line 2: Q = orth(Y)
+  SHG_TRY(cholqr2(m, k, Y, ldk, T, ldk, small, d_flags, st));
+  // power scheme (Sec. 2.1): the FP16-rounded basis is the next test matrix
+  for (int it = 0; it < power_iters; ++it) {
+    if (tc) {
+      SHG_TRY(to_f16(m, k, Y, ldk, H, ldk, st));
+      SHG_TRY(tc_gemm(A_MNMAJ, B_F16, 2, n, k, m, 1, A, lda, 0, H, ldk, Z, ldk, 0, d_flags, st));
+    } else {
+      SHG_TRY(simt_gemm(n, k, m, A, lda, 1, Y, ldk, 0, Z, ldk, 0, 1, 0, 0, 0, st));
+    }
+    SHG_TRY(cholqr2(n, k, Z, ldk, T, ldk, small, d_flags, st));
+    if (tc) {
+      SHG_TRY(to_f16(n, k, Z, ldk, H, ldk, st));
+      SHG_TRY(tc_gemm(A_KMAJ, B_F16, 2, m, k, n, 1, A, lda, 0, H, ldk, Y, ldk, 0, d_flags, st));
+    } else {
+      SHG_TRY(simt_gemm(m, k, n, A, lda, 0, Z, ldk, 0, Y, ldk, 0, 1, 0, 0, 0, st));
+    }
+    SHG_TRY(cholqr2(m, k, Y, ldk, T, ldk, small, d_flags, st));
+  }
+  // line 3: B^T = A^T Q (FP32-accurate)
+  if (tc)
+    SHG_TRY(tc_gemm(A_MNMAJ, B_SPLIT, 2, n, k, m, 1, A, lda, 0, Y, ldk, Bt, ldk, 0, d_flags, st));
+  else
+    SHG_TRY(simt_gemm(n, k, m, A, lda, 1, Y, ldk, 0, Bt, ldk, 0, 1, 0, 0, 0, st));
+  // line 4: tSVD(B) through the eigendecomposition of B B^T = Bt^T Bt
+  uint8_t* sw = static_cast<uint8_t*>(small);
+  double* G = reinterpret_cast<double*>(sw);
+  float* jscratch = reinterpret_cast<float*>(sw + 3 * align256(k * k * 8) + align256(k * k * 4));
+  SHG_TRY(gram_f64(n, k, Bt, ldk, G, st));
+  SHG_TRY(jacobi_eig(k, G, Vk, jscratch, st));
+  SHG_TRY(rayleigh_sort(k, rank, G, Vk, lam, S, Up, Ups, st));
+  // line 5: U = Q U'; V = B^T U' Sigma^-1
+  SHG_TRY(simt_gemm(m, rank, k, Y, ldk, 0, Up, rank, 0, U, rank, 0, 1, 0, 0, 0, st));
+  SHG_TRY(simt_gemm(n, rank, k, Bt, ldk, 0, Ups, rank, 0, V, rank, 0, 1, 0, 0, 0, st));
+  if (Q_out) {
+    if (cudaMemcpy2DAsync(Q_out, k * 4, Y, ldk * 4, k * 4, m, cudaMemcpyDeviceToDevice, st) != cudaSuccess)
+      return SHG_ERR_CUDA;
+  }
+  return SHG_OK;
+}
+
+int shg_rp_hosvd_workspace_size(int ndim, const int64_t* dims, const int64_t* ranks, size_t* bytes) {
+  if (!bytes || !dims || !ranks) return SHG_ERR_INVALID_ARG;
+  if (ndim != 3) return SHG_ERR_UNSUPPORTED;
+  for (int i = 0; i < 3; ++i)
+    if (dims[i] < 1 || ranks[i] < 1 || ranks[i] > dims[i] || ranks[i] > 1024) return SHG_ERR_INVALID_ARG;
+  *bytes = hosvd_layout(dims, ranks).total;
+  return SHG_OK;
+}
+
+int shg_rp_hosvd(int ndim, const int64_t* dims, const int64_t* ranks, const float* X,
+                 const uint16_t* const* omegas, float* core, float* const* factors, void* ws, size_t ws_bytes,
+                 int variant, int32_t* d_flags, void* stream) {
+  size_t need = 0;
+  const int rc0 = shg_rp_hosvd_workspace_size(ndim, dims, ranks, &need);
+  if (rc0 != SHG_OK) return rc0;
+  if (!X || !omegas || !core || !factors || !ws || !d_flags) return SHG_ERR_INVALID_ARG;
+  for (int i = 0; i < 3; ++i)
+    if (!omegas[i] || !factors[i]) return SHG_ERR_INVALID_ARG;
+  if (variant != SHG_SPLIT_F16 && variant != SHG_FP32_SIMT) return SHG_ERR_UNSUPPORTED;
+  if (ws_bytes < need) return SHG_ERR_WORKSPACE;
+  cudaStream_t st = static_cast<cudaStream_t>(stream);
+  const HosvdLayout L = hosvd_layout(dims, ranks);
+  uint8_t* w = static_cast<uint8_t*>(ws);
+  float* W[3];
+  for (int i = 0; i < 3; ++i) W[i] = reinterpret_cast<float*>(w + L.W[i]);
+  float* T = reinterpret_cast<float*>(w + L.T);
+  float* T1 = reinterpret_cast<float*>(w + L.T1);
+  float* T2 = reinterpret_cast<float*>(w + L.T2);
+  void* small = w + L.small;
+  const int64_t I0 = dims[0], I1 = dims[1], I2 = dims[2];
+  const int64_t J0 = ranks[0], J1 = ranks[1], J2 = ranks[2];
+  const bool tc = (variant == SHG_SPLIT_F16);
+
+  // lines 1-3: W_i = X_(i) Omega_(i), Q_i = orth(W_i)
+  if (tc) {
+    SHG_TRY(tc_gemm(A_KMAJ, B_F16, 2, I0, J0, I1 * I2, 1, X, I1 * I2, 0, omegas[0], J0, W[0], L.ld[0], 0, d_flags, st));
+    SHG_TRY(tc_gemm(A_KMAJ, B_F16, 2, I1, J1, I2, I0, X, I2, I1 * I2, omegas[1], J1, W[1], L.ld[1], 0, d_flags, st));
+    SHG_TRY(tc_gemm(A_MNMAJ, B_F16, 2, I2, J2, I0 * I1, 1, X, I2, 0, omegas[2], J2, W[2], L.ld[2], 0, d_flags, st));
+  } else {
+    SHG_TRY(simt_gemm(I0, J0, I1 * I2, X, I1 * I2, 0, omegas[0], J0, 1, W[0], L.ld[0], 0, 1, 0, 0, 0, st));
+    if (cudaMemsetAsync(W[1], 0, I1 * L.ld[1] * 4, st) != cudaSuccess) return SHG_ERR_CUDA;
+    SHG_TRY(simt_gemm(I1, J1, I2, X, I2, 0, omegas[1], J1, 1, W[1], L.ld[1], 1, I0, I1 * I2, I2 * J1, 0, st));
+    SHG_TRY(simt_gemm(I2, J2, I0 * I1, X, I2, 1, omegas[2], J2, 1, W[2], L.ld[2], 0, 1, 0, 0, 0, st));
+  }
+  for (int i = 0; i < 3; ++i) {
+    SHG_TRY(cholqr2(dims[i], ranks[i], W[i], L.ld[i], T, L.ld[i], small, d_flags, st));
+    if (cudaMemcpy2DAsync(factors[i], ranks[i] * 4, W[i], L.ld[i] * 4, ranks[i] * 4, dims[i],
+                          cudaMemcpyDeviceToDevice, st) != cudaSuccess)
+      return SHG_ERR_CUDA;
+  }
+  // line 5: core = X x_2 Q_2^T x_1 Q_1^T x_0 Q_0^T
+  if (tc)
+    SHG_TRY(tc_gemm(A_KMAJ, B_SPLIT, 2, I0 * I1, J2, I2, 1, X, I2, 0, W[2], L.ld[2], T1, L.ld[2], 0, d_flags, st));
+  else
+    SHG_TRY(simt_gemm(I0 * I1, J2, I2, X, I2, 0, W[2], L.ld[2], 0, T1, L.ld[2], 0, 1, 0, 0, 0, st));
+  SHG_TRY(simt_gemm(J1, J2, I1, W[1], L.ld[1], 1, T1, L.ld[2], 0, T2, J2, 0, I0, 0, I1 * L.ld[2], J1 * J2, st));
+  SHG_TRY(simt_gemm(J0, J1 * J2, I0, W[0], L.ld[0], 1, T2, J1 * J2, 0, core, J1 * J2, 0, 1, 0, 0, 0, st));
+  return SHG_OK;
+}
+
+}  // extern "C"

@@ -1,0 +1,85 @@
+// FP16 Gaussian test matrix (Sec. 3.1; Sec. 3.3 draws N(0,1) in FP32 and
+// rounds RN to the low format) from the counter-based Philox4x32-10
+// generator (Salmon et al., SC'11) and the Box-Muller transform.
+//
+// Element e = r * cols + c takes normal (e mod 4) of Philox block
+// (e div 4) + offset under key (seed lo, seed hi): the value depends only on
+// the element's logical index, never on the launch shape.
+#include <cuda_fp16.h>
+
+#include "internal.h"
+
+namespace shg {
+namespace {
+
+__device__ __forceinline__ uint4 philox4x32_10(uint4 c, uint2 k) {
+  constexpr uint32_t M0 = 0xD2511F53u, M1 = 0xCD9E8D57u;
+  constexpr uint32_t W0 = 0x9E3779B9u, W1 = 0xBB67AE85u;
+#pragma unroll
+  for (int r = 0; r < 10; ++r) {
+    const uint32_t hi0 = __umulhi(M0, c.x), lo0 = M0 * c.x;
+    const uint32_t hi1 = __umulhi(M1, c.z), lo1 = M1 * c.z;
+    c = make_uint4(hi1 ^ c.y ^ k.x, lo1, hi0 ^ c.w ^ k.y, lo0);
+    k.x += W0;
+    k.y += W1;
+  }
+  return c;
+}
+
+// (x + 1/2) * 2^-32 in (0, 1]
+__device__ __forceinline__ float to_unit(uint32_t x) {
+  return fmaf(static_cast<float>(x), 2.3283064365386963e-10f, 1.1641532182693481e-10f);
+}
+
+__global__ void gaussian_f16_kernel(uint2 key, unsigned long long offset, long long rows, long long cols,
+                                    __half* out, long long ld) {
+  const long long n = rows * cols;
+  const long long nblk = (n + 3) / 4;
+  for (long long b = blockIdx.x * static_cast<long long>(blockDim.x) + threadIdx.x; b < nblk;
+       b += static_cast<long long>(gridDim.x) * blockDim.x) {
+    const unsigned long long ctr = b + offset;
+    const uint4 x = philox4x32_10(make_uint4(static_cast<uint32_t>(ctr), static_cast<uint32_t>(ctr >> 32), 0u, 0u), key);
+    float z[4];
+    {
+      const float r = sqrtf(-2.0f * logf(to_unit(x.x)));
+      float s, c;
+      sincospif(2.0f * to_unit(x.y), &s, &c);
+      z[0] = r * c;
+      z[1] = r * s;
+    }
+    {
+      const float r = sqrtf(-2.0f * logf(to_unit(x.z)));
+      float s, c;
+      sincospif(2.0f * to_unit(x.w), &s, &c);
+      z[2] = r * c;
+      z[3] = r * s;
+    }
+#pragma unroll
+    for (int j = 0; j < 4; ++j) {
+      const long long e = 4 * b + j;
+      if (e < n) {
+        const long long r = e / cols, c = e - r * cols;
+        out[r * ld + c] = __float2half_rn(z[j]);
+      }
+    }
+  }
+}
+
+}  // namespace
+}  // namespace shg
+
+extern "C" int shg_gaussian_f16(uint64_t seed, uint64_t offset, int64_t rows, int64_t cols, uint16_t* out,
+                                int64_t ld, void* stream) {
+  if (rows < 0 || cols < 0 || ld < cols) return SHG_ERR_INVALID_ARG;
+  if (rows == 0 || cols == 0) return SHG_OK;
+  if (!out) return SHG_ERR_INVALID_ARG;
+  const long long nblk = (rows * cols + 3) / 4;
+  const int sms = shg::sm_count();
+  if (sms <= 0) return SHG_ERR_CUDA;
+  const long long want = (nblk + 255) / 256;
+  const int grid = static_cast<int>(want < 8ll * sms ? want : 8ll * sms);
+  const uint2 key = make_uint2(static_cast<uint32_t>(seed), static_cast<uint32_t>(seed >> 32));
+  shg::gaussian_f16_kernel<<<grid, 256, 0, static_cast<cudaStream_t>(stream)>>>(
+      key, offset, rows, cols, reinterpret_cast<__half*>(out), ld);
+  return shg::cuda_status(cudaGetLastError());
+}

@@ -1,0 +1,41 @@
+// Host-side declarations shared by the library's translation units.
+#pragma once
+#include <cstddef>
+#include <cstdint>
+#include <cuda_runtime.h>
+
+#include "../../include/shg.h"
+
+namespace shg {
+
+enum AMajor : int { A_KMAJ = 0, A_MNMAJ = 1 };
+enum BMode : int { B_F16 = 0, B_BF16 = 1, B_SPLIT = 2 };
+
+// Test hooks of the tensor-core GEMM (never set by the public entry points).
+struct TcTestHooks {
+  unsigned long long wait_ns = 2000000000ull;  // bound of every device-side wait
+  int drop_commit = 0;                         // 1: never signal "accumulator ready"
+};
+
+// C (+)= op(A) * B on tcgen05 tensor cores with A split in shared memory.
+//   amaj = A_KMAJ : A is M x K, A[m][k] at A + (p * p_stride) + m * lda + s
+//                   where the K index is (p, s), p < P, s < S_k (K = P * S_k);
+//                   B row of K index (p, s) is p * S_k + s.
+//   amaj = A_MNMAJ: A is K x M (A[k][m] at A + k * lda + m), P = 1.
+//   bmode: B_F16 / B_BF16 (B already 16-bit, `pieces` A pieces of that type)
+//          or B_SPLIT (B FP32 split into FP16 hi/lo, TCEC products).
+int tc_gemm(int amaj, int bmode, int pieces, int64_t M, int64_t N, int64_t S_k, int64_t P,
+            const float* A, int64_t lda, int64_t p_stride, const void* B, int64_t ldb, float* C,
+            int64_t ldc, int accumulate, int32_t* d_flags, cudaStream_t stream,
+            const TcTestHooks* hooks = nullptr);
+
+// FP32 SIMT GEMM, batched over gridDim.z with element strides.
+int simt_gemm(int64_t M, int64_t N, int64_t K, const float* A, int64_t lda, int trans_a, const void* B,
+              int64_t ldb, int b_f16, float* C, int64_t ldc, int accumulate, int64_t batch,
+              int64_t stride_a, int64_t stride_b, int64_t stride_c, cudaStream_t stream);
+
+int sm_count();
+int ceil_div_i(int64_t a, int64_t b);
+inline int cuda_status(cudaError_t e) { return e == cudaSuccess ? SHG_OK : SHG_ERR_CUDA; }
+
+}  // namespace shg

@@ -1,0 +1,23 @@
+// Host launchers of the k x k linear algebra (see linalg.cu).
+#pragma once
+#include <cstddef>
+#include <cstdint>
+#include <cuda_runtime.h>
+
+namespace shg {
+
+size_t align256(size_t x);
+// Bytes of the small (k-sized) scratch one CholeskyQR2 / eigensolve needs.
+size_t cholqr_small_bytes(int64_t k);
+
+int gram_f64(int64_t m, int64_t k, const float* X, int64_t ldx, double* G, cudaStream_t st);
+int cholesky_f64(int64_t k, const double* G, double* R, double* scratch, int32_t* flags, cudaStream_t st);
+int tri_inv(int64_t k, const double* R, double* X, float* Xf, cudaStream_t st);
+int jacobi_eig(int64_t k, const double* G, float* V, float* scratch, cudaStream_t st);
+int rayleigh_sort(int64_t k, int64_t p, const double* G, const float* V, double* lam, float* S, float* Up,
+                  float* Ups, cudaStream_t st);
+int to_f16(int64_t rows, int64_t cols, const float* x, int64_t ldx, uint16_t* y, int64_t ldy, cudaStream_t st);
+int cholqr2(int64_t m, int64_t k, float* X, int64_t ldx, float* T, int64_t ldt, void* small, int32_t* flags,
+            cudaStream_t st);
+
+}  // namespace shg

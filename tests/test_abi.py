@@ -1,0 +1,67 @@
+"""CPU-only checks of the C ABI: libshg.so loads, exports every symbol that
+include/shg.h declares, and rejects bad arguments on the host (no GPU work)."""
+import ctypes
+import os
+import re
+
+import pytest
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+HEADER = os.path.join(ROOT, "include", "shg.h")
+
+
+def declared_functions():
+    src = open(HEADER).read()
+    src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
+    return sorted(set(re.findall(r"^\s*(?:const\s+)?\w+\*?\s+\**(shg\w+|shgemm\w+)\s*\(", src, flags=re.M)))
+
+
+@pytest.fixture(scope="module")
+def lib():
+    from paper_2304_04612_gb300 import build as b
+    b.build()
+    from paper_2304_04612_gb300 import _lib
+    return _lib.load()
+
+
+def test_header_declares_the_paper_entry_points():
+    names = declared_functions()
+    for want in ("shgemm_project", "shg_rsvd", "shg_rp_hosvd", "shg_gaussian_f16", "shg_gemm_split3",
+                 "shg_sgemm", "shg_cholqr2"):
+        assert want in names
+
+
+def test_every_declared_symbol_is_exported(lib):
+    from paper_2304_04612_gb300 import _lib
+    for name in declared_functions():
+        assert hasattr(lib, name), name
+        assert name in _lib.SIGNATURES, f"binding lacks a signature for {name}"
+
+
+def test_status_strings(lib):
+    for s in range(8):
+        assert lib.shg_status_string(s)
+    assert lib.shg_status_string(99) == b"unknown shg_status"
+    assert lib.shg_flags_status(0) == 0
+    assert lib.shg_flags_status(1) == 2      # RANGE
+    assert lib.shg_flags_status(3) == 3      # NOT_SPD outranks RANGE
+    assert lib.shg_flags_status(7) == 6      # TIMEOUT outranks all
+
+
+def test_host_argument_validation(lib):
+    null = ctypes.c_void_p(0)
+    # m = 0 is rejected before any CUDA call
+    assert lib.shgemm_project(0, 8, 8, null, 8, 0, null, 8, null, 8, 0, null, null) == 1
+    # ld smaller than the row length
+    one = ctypes.c_void_p(16)
+    assert lib.shgemm_project(8, 8, 8, one, 4, 0, one, 8, one, 8, 0, one, null) == 1
+    assert lib.shg_gaussian_f16(0, 0, -1, 4, null, 4, null) == 1
+    assert lib.shg_gaussian_f16(0, 0, 0, 4, null, 4, null) == 0       # empty is a no-op
+    sz = ctypes.c_size_t()
+    assert lib.shg_rsvd_workspace_size(100, 100, 90, 20, 0, ctypes.byref(sz)) == 1   # k > min(m, n)
+    assert lib.shg_rsvd_workspace_size(1024, 1024, 32, 32, 0, ctypes.byref(sz)) == 0
+    assert sz.value > 1024 * 64 * 4
+    d = (ctypes.c_int64 * 3)(8, 8, 8)
+    r = (ctypes.c_int64 * 3)(4, 9, 4)                                 # J > I
+    assert lib.shg_rp_hosvd_workspace_size(3, d, r, ctypes.byref(sz)) == 1
+    assert lib.shg_rp_hosvd_workspace_size(4, d, r, ctypes.byref(sz)) == 7

@@ -1,0 +1,136 @@
+"""GPU parity of CholeskyQR2, the randomized SVD (Algorithm 1) and RP-HOSVD
+(Algorithm 2) against the FP64 oracle fed the same FP32 A and FP16 Omega.
+
+Tolerances: leading singular values within 1e-5 relative, the rank-p
+residual ||A - U S V^T||_F / ||A||_F within 1% of the oracle's, Q^T Q = I
+within 1e-5 (Frobenius), and the basis itself within the perturbation that
+the FP32 rounding of Y allows (cond(Y) * relative error of Y).
+"""
+import numpy as np
+import pytest
+import torch
+
+from oracle import rsvd as OR
+from oracle import hosvd as OH  # noqa: F401  (rp_hosvd reference)
+from oracle import shgemm as OS
+from synth import rsvd_planted, omega_f16, planted_svd, sigma_exp, uniform, tucker, hosvd_omegas
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def shg():
+    import __graft_entry__ as g
+    g.build()
+    import paper_2304_04612_gb300 as m
+    return m
+
+
+def dev(x):
+    return torch.from_numpy(np.ascontiguousarray(x)).cuda()
+
+
+def residual(A, U, S, V):
+    A = A.astype(np.float64)
+    return np.linalg.norm(A - (U.astype(np.float64) * S.astype(np.float64)) @ V.astype(np.float64).T) / np.linalg.norm(A)
+
+
+def test_cholqr2_orthonormal_and_matches_householder(shg):
+    rng = np.random.default_rng(0)
+    m, k = 3000, 72
+    U = np.linalg.qr(rng.standard_normal((m, k)))[0]
+    V = np.linalg.qr(rng.standard_normal((k, k)))[0]
+    X = ((U * np.logspace(0, -4, k)) @ V.T).astype(np.float32)    # cond ~ 1e4
+    Q = shg.shg_cholqr2(dev(X)).cpu().numpy().astype(np.float64)
+    assert np.linalg.norm(Q.T @ Q - np.eye(k)) < 1e-5
+    Qr, _ = OR.qr_pos(X.astype(np.float64))
+    assert np.linalg.norm(Q - Qr) < 1e4 * 1e-6 * np.sqrt(k)
+
+
+def test_cholqr2_not_spd_flag(shg):
+    X = uniform(500, 16, seed=1)
+    X[:, 5] = 0.0                               # exactly singular Gram matrix
+    with pytest.raises(shg.ShgError) as ei:
+        shg.shg_cholqr2(dev(X))
+    assert ei.value.status == 3
+
+
+@pytest.mark.parametrize("variant", ["f16", "fp32"])
+def test_rsvd_planted_1024(shg, variant):
+    """The randomized-SVD accuracy workload: 1024 x 1024, sigma_i = 2^(-i/8),
+    rank 32, oversampling 32, q = 0."""
+    A, Om = rsvd_planted(1024, 1024, rate=8.0, seed_a=0, seed_omega=1, k=64)
+    U, S, V, Q = shg.shg_rsvd(dev(A), dev(Om), rank=32, oversampling=32, variant=variant, want_q=True)
+    U, S, V, Q = (t.cpu().numpy() for t in (U, S, V, Q))
+    ref = OR.rsvd(A, Om, p=32)
+    rel_s = np.abs(S.astype(np.float64) - ref["S"]) / ref["S"]
+    assert rel_s.max() <= 1e-5, rel_s.max()
+    r_p = residual(A, U, S, V)
+    assert abs(r_p - ref["r_p"]) <= 0.01 * ref["r_p"], (r_p, ref["r_p"])
+    Q64 = Q.astype(np.float64)
+    assert np.linalg.norm(Q64.T @ Q64 - np.eye(64)) <= 1e-5
+    # basis: perturbation bound cond(Y) * ||dY|| / ||Y|| with ||dY||/||Y|| <= 1e-5
+    condY = np.linalg.cond(ref["Y"])
+    assert np.linalg.norm(Q64 - ref["Q"]) <= 10 * condY * 1e-6 * np.sqrt(64)
+    # U, V orthonormal columns
+    assert np.linalg.norm(U.T.astype(np.float64) @ U - np.eye(32)) < 1e-4
+    assert np.linalg.norm(V.T.astype(np.float64) @ V - np.eye(32)) < 1e-4
+
+
+def test_rsvd_shgemm_no_worse_than_fp32(shg):
+    A, Om = rsvd_planted(1024, 1024, rate=8.0, seed_a=0, seed_omega=1, k=64)
+    ref = OR.rsvd(A, Om, p=32)
+    out = {}
+    for v in ("f16", "fp32"):
+        U, S, V = shg.shg_rsvd(dev(A), dev(Om), rank=32, oversampling=32, variant=v)
+        out[v] = residual(A, U.cpu().numpy(), S.cpu().numpy(), V.cpu().numpy())
+    assert out["f16"] <= out["fp32"] * 1.01 + 1e-7
+    assert abs(out["f16"] - ref["r_p"]) <= 0.01 * ref["r_p"]
+
+
+@pytest.mark.parametrize("m,n,rank,s,q", [(700, 1200, 20, 12, 0), (1500, 600, 40, 16, 1), (512, 512, 16, 16, 2)])
+def test_rsvd_shapes_and_power_scheme(shg, m, n, rank, s, q):
+    A = planted_svd(m, n, sigma_exp(min(m, n), 16.0), seed=4)
+    Om = omega_f16(n, rank + s, seed=5)
+    U, S, V = shg.shg_rsvd(dev(A), dev(Om), rank=rank, oversampling=s, power_iters=q)
+    U, S, V = U.cpu().numpy(), S.cpu().numpy(), V.cpu().numpy()
+    ref = OR.rsvd(A, Om, p=rank, q=q, fp16_basis=True)
+    rel_s = np.abs(S.astype(np.float64) - ref["S"]) / ref["S"]
+    assert rel_s.max() <= 1e-5, rel_s.max()
+    r_p = residual(A, U, S, V)
+    assert abs(r_p - ref["r_p"]) <= 0.01 * ref["r_p"]
+
+
+def test_rsvd_bf16_variant(shg):
+    A, Om = rsvd_planted(1024, 1024, rate=8.0, seed_a=0, seed_omega=1, k=64)
+    Wb = OS.bf16_omega(Om)
+    from oracle.lowp import encode_bf16
+    om_b = torch.from_numpy(encode_bf16(Wb).view(np.int16)).cuda().view(torch.bfloat16)
+    U, S, V = shg.shg_rsvd(dev(A), om_b, rank=32, oversampling=32, variant="bf16x3")
+    ref = OR.rsvd(A, Wb, p=32)
+    rel_s = np.abs(S.cpu().numpy().astype(np.float64) - ref["S"]) / ref["S"]
+    assert rel_s.max() <= 1e-5
+
+
+def test_rp_hosvd_small(shg):
+    dims, J = (64, 48, 40), (12, 12, 12)
+    A, _, _ = tucker(dims, (8, 8, 8), seed=3, noise_std=1e-4)
+    oms = hosvd_omegas(dims, J, seed=4)
+    ref = OH.rp_hosvd(A, oms)
+    for variant in ("f16", "fp32"):
+        core, facs = shg.shg_rp_hosvd(dev(A), [dev(o) for o in oms], J, variant=variant)
+        core = core.cpu().numpy().astype(np.float64)
+        facs = [f.cpu().numpy().astype(np.float64) for f in facs]
+        for i in range(3):
+            assert np.linalg.norm(facs[i].T @ facs[i] - np.eye(J[i])) < 1e-5
+            # same subspaces as the oracle (up to the FP32 rounding of W_i)
+            Pq = facs[i] @ facs[i].T
+            Pr = ref["Q"][i] @ ref["Q"][i].T
+            assert np.linalg.norm(Pq - Pr) < 1e-3
+        # properties of the returned factorization, in plain float64 numpy
+        rec = np.einsum("abc,ia,jb,kc->ijk", core, facs[0], facs[1], facs[2])
+        err = np.linalg.norm(A.astype(np.float64) - rec) / np.linalg.norm(A)
+        assert abs(err - ref["err"]) <= 0.01 * ref["err"], (variant, err, ref["err"])
+        # the core is the projection of A on the returned factors (line 5)
+        proj = np.einsum("ijk,ia,jb,kc->abc", A.astype(np.float64), facs[0], facs[1], facs[2])
+        assert np.linalg.norm(core - proj) / np.linalg.norm(proj) < 1e-5

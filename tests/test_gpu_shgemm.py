@@ -1,0 +1,171 @@
+"""GPU parity of the projection kernels against the FP64 oracle.
+
+Tolerances (from the method, Sec. 4.3 / 4.4.1):
+* SHGEMM-FP16: relative Frobenius error <= 1e-5 and <= 2x the FP32 SIMT
+  error on the same inputs; every element within the paper's bound
+  (1/8) n u |A||Omega| plus the split's representation bound u16^2 |A||Omega|.
+* BF16x3: same FP32-level bound; BF16x2: 2^-16-level (two 8-bit pieces).
+* TCEC split product: FP32-level relative error <= 1e-5.
+"""
+import numpy as np
+import pytest
+import torch
+
+from oracle import shgemm as OS
+from oracle import gaussian as OG
+from oracle.lowp import FP16, BF16, round_rn, encode_bf16
+from synth import uniform, omega_f16
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def shg():
+    import __graft_entry__ as g
+    g.build()
+    import paper_2304_04612_gb300 as m
+    return m
+
+
+def dev(x):
+    return torch.from_numpy(np.ascontiguousarray(x)).cuda()
+
+
+def padded_f32(A):
+    """FP32 matrix stored with a leading dimension rounded up to a multiple of 4
+    (the 16-byte TMA stride rule); returns the (rows x cols) view."""
+    r, c = A.shape
+    buf = torch.zeros(r, (c + 3) // 4 * 4, dtype=torch.float32, device="cuda")
+    buf[:, :c] = dev(A)
+    return buf[:, :c]
+
+
+def padded_omega(Om, ld):
+    """n x k FP16 Omega stored with leading dimension ld (TMA wants ld % 8 == 0)."""
+    n, k = Om.shape
+    buf = torch.zeros(n, ld, dtype=torch.float16, device="cuda")
+    buf[:, :k] = dev(Om)
+    return buf[:, :k]
+
+
+SHAPES = [(300, 1000, 64), (129, 67, 1), (256, 512, 200), (1000, 300, 256), (200, 640, 512),
+          (64, 4096, 48), (1, 130, 8), (513, 2048, 96), (128, 64, 128), (77, 1536, 144)]
+
+
+@pytest.mark.parametrize("m,n,k", SHAPES)
+@pytest.mark.parametrize("trans", [False, True])
+def test_shgemm_f16_parity(shg, m, n, k, trans):
+    A = uniform(n, m, seed=2) if trans else uniform(m, n, seed=2)
+    Om = omega_f16(n, k, seed=1)
+    om_t = padded_omega(Om, (k + 7) // 8 * 8)
+    At = padded_f32(A)
+    Y = shg.shgemm_project(At, om_t, "f16", trans_a=trans).cpu().numpy()
+    A_op = A.T.copy() if trans else A
+    ref = OS.project_exact(A_op, Om)
+    err = OS.rel_fro_error(Y, ref)
+    Ys = shg.shgemm_project(At, om_t, "fp32", trans_a=trans).cpu().numpy()
+    err_simt = OS.rel_fro_error(Ys, ref)
+    assert err <= 1e-5, (err, err_simt)
+    assert err <= max(2.0 * err_simt, 2e-7), (err, err_simt)
+    bound = OS.elementwise_bound(A_op, Om) * (1 if n >= 8 else 8.0 / n) + \
+        OS.U_FP16 ** 2 * (np.abs(A_op.astype(np.float64)) @ np.abs(Om.astype(np.float64)))
+    viol = np.abs(Y - ref) > bound * (1 + 1e-6) + 1e-30
+    assert not viol.any(), f"{viol.sum()} elements exceed the Sec. 4.3 bound"
+
+
+def test_shgemm_ld_and_offsets(shg):
+    """Leading dimensions larger than the row length on A, Omega and Y."""
+    m, n, k = 200, 700, 40
+    A = uniform(m, n + 12, seed=5)
+    Om = omega_f16(n, k, seed=6)
+    At = dev(A)[:, :n]
+    Yb = torch.full((m, k + 9), 7.0, device="cuda")
+    shg.shgemm_project(At, padded_omega(Om, 56), out=Yb[:, :k])
+    Y = Yb.cpu().numpy()
+    assert OS.rel_fro_error(Y[:, :k], OS.project_exact(A[:, :n], Om)) < 1e-5
+    assert np.all(Y[:, k:] == 7.0)              # nothing written past the row
+
+
+@pytest.mark.parametrize("pieces,tol", [(3, 1e-5), (2, 2e-4)])
+def test_shgemm_bf16_parity(shg, pieces, tol):
+    m, n, k = 300, 1000, 64
+    A = uniform(m, n, seed=2)
+    Om = omega_f16(n, k, seed=1)
+    Wb = OS.bf16_omega(Om)                      # RN_bf16 of the FP16 values
+    om_b = torch.from_numpy(encode_bf16(Wb).view(np.int16)).cuda().view(torch.bfloat16)
+    Y = shg.shgemm_project(dev(A), om_b, "bf16x3" if pieces == 3 else "bf16x2").cpu().numpy()
+    ref = A.astype(np.float64) @ Wb
+    err = OS.rel_fro_error(Y, ref)
+    assert err <= tol, err
+    emu = OS.shgemm_bf16_emulated(A, Om, pieces)
+    assert OS.rel_fro_error(emu, ref) <= tol
+
+
+@pytest.mark.parametrize("m,n,kk,trans", [(300, 64, 1000, False), (1000, 48, 300, True), (130, 200, 257, False),
+                                          (1024, 64, 1024, True), (96, 136, 640, True)])
+def test_split3_parity(shg, m, n, kk, trans):
+    A = uniform(kk, m, seed=3) if trans else uniform(m, kk, seed=3)
+    B = uniform(kk, n, seed=4)
+    C = shg.shg_gemm_split3(padded_f32(A), padded_f32(B), trans_a=trans).cpu().numpy()
+    A_op = A.T if trans else A
+    ref = A_op.astype(np.float64) @ B.astype(np.float64)
+    assert OS.rel_fro_error(C, ref) <= 1e-5
+
+
+def test_split3_accumulate(shg):
+    A = uniform(200, 300, seed=7)
+    B = uniform(300, 64, seed=8)
+    C0 = uniform(200, 64, seed=9)
+    C = dev(C0)
+    shg.shg_gemm_split3(dev(A), dev(B), out=C, accumulate=True)
+    ref = C0.astype(np.float64) + A.astype(np.float64) @ B.astype(np.float64)
+    assert OS.rel_fro_error(C.cpu().numpy(), ref) < 1e-6
+
+
+@pytest.mark.parametrize("trans,bf16", [(False, False), (True, False), (False, True), (True, True)])
+def test_sgemm_parity(shg, trans, bf16):
+    m, n, kk = 257, 70, 900
+    A = uniform(kk, m, seed=3) if trans else uniform(m, kk, seed=3)
+    if bf16:
+        Bn = omega_f16(kk, n, seed=4)
+        Bt = dev(Bn)
+        Bref = Bn.astype(np.float64)
+    else:
+        Bn = uniform(kk, n, seed=4)
+        Bt = dev(Bn)
+        Bref = Bn.astype(np.float64)
+    C = shg.shg_sgemm(dev(A), Bt, trans_a=trans).cpu().numpy()
+    ref = (A.T if trans else A).astype(np.float64) @ Bref
+    assert OS.rel_fro_error(C, ref) < 1e-5
+
+
+def test_range_flag_raises(shg):
+    A = uniform(256, 512, seed=1)
+    A[17, 33] = 70000.0
+    Om = omega_f16(512, 64, seed=1)
+    with pytest.raises(shg.ShgError) as ei:
+        shg.shgemm_project(dev(A), dev(Om), "f16")
+    assert ei.value.status == 2
+    # the FP32 path and the BF16 split have the full exponent range
+    shg.shgemm_project(dev(A), dev(Om), "fp32")
+    A[17, 33] = 65519.0                    # still rounds to a finite FP16 value
+    shg.shgemm_project(dev(A), dev(Om), "f16")
+
+
+def test_gaussian_generator_matches_philox_oracle(shg):
+    rows, cols = 333, 77
+    g = shg.shg_gaussian_f16(seed=1234, offset=5, rows=rows, cols=cols).cpu().numpy().astype(np.float64)
+    ref = OG.gaussian_f16(1234, 5, rows, cols)
+    same = g == ref
+    assert same.mean() > 0.999
+    # the rest differs only by FP16 rounding of FP32 vs FP64 Box-Muller values
+    d = np.abs(g - ref)[~same]
+    assert np.all(d <= 2.0 ** -10 * np.maximum(np.abs(ref[~same]), 2.0 ** -14))
+
+
+def test_gaussian_generator_layout_independent(shg):
+    a = shg.shg_gaussian_f16(7, 0, 40, 30).cpu()
+    buf = torch.zeros(40, 64, dtype=torch.float16, device="cuda")
+    shg.shg_gaussian_f16(7, 0, 40, 30, out=buf[:, :30])
+    assert torch.equal(a, buf[:, :30].cpu())
+    assert torch.count_nonzero(buf[:, 30:]) == 0
