@@ -153,9 +153,15 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--quick", action="store_true", help="skip the side measurements")
+    ap.add_argument("--case", type=int, nargs=2, metavar=("MN", "K"),
+                    help="profiling case: only W + K launches of one m=n=MN, k=K SHGEMM (no JSON contract line)")
+    ap.add_argument("--variant", default="f16", help="variant for --case")
     args = ap.parse_args()
     if args.impl == "reference":
         run_reference(args)
+        return
+    if args.case:
+        run_case(args)
         return
 
     import torch
@@ -260,6 +266,37 @@ def main():
         print(json.dumps(line), flush=True)
     if ws > 1:
         torch.distributed.destroy_process_group()
+
+
+def run_case(args):
+    """A single SHGEMM shape, for ncu captures: W warm-up launches then K timed ones."""
+    import torch
+    import __graft_entry__ as g
+    g.build()
+    import paper_2304_04612_gb300 as shg
+    mn, k = args.case
+    dev = torch.device("cuda", 0)
+    gen = torch.Generator(device=dev).manual_seed(2)
+    A = torch.rand(mn, mn, device=dev, generator=gen) * 2 - 1
+    Om = torch.randn(mn, k, device=dev, generator=gen).half()
+    if args.variant.startswith("bf16"):
+        Om = Om.bfloat16()
+    Y = torch.empty(mn, k, device=dev)
+    fl = shg.new_flags(dev)
+    for _ in range(args.warmup):
+        shg.shgemm_project(A, Om, args.variant, out=Y, flags=fl, check=False)
+    torch.cuda.synchronize()
+    a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    a.record()
+    for _ in range(args.steps):
+        shg.shgemm_project(A, Om, args.variant, out=Y, flags=fl, check=False)
+    b.record()
+    torch.cuda.synchronize()
+    shg.check_flags(fl, "case")
+    ms = a.elapsed_time(b) / args.steps
+    print(json.dumps({"case": [mn, k], "variant": args.variant, "ms": ms,
+                      "tflops_2mnk": 2.0 * mn * mn * k / (ms * 1e-3) / 1e12,
+                      "gbs": (4.0 * mn * mn + 2.0 * mn * k + 4.0 * mn * k) / (ms * 1e-3) / 1e9}))
 
 
 def time_ms(torch, stream, fn, reps=5, flush=None):

@@ -169,8 +169,11 @@ int shg_rsvd(int64_t m, int64_t n, int64_t rank, int64_t oversampling, int power
  * Random-projection HOSVD, Algorithm 2 (Sec. 5.2), for a 3-way tensor
  * X[i0][i1][i2] (row-major, last index fastest, dims[0..2]).
  *   ranks[i] = J_i (target rank plus oversampling), 1 <= J_i <= dims[i], J_i <= 256.
- *   omegas[i]: FP16 bits, (prod_{j != i} dims[j]) x J_i, ld J_i; its row index
- *   is the row-major linear index of the other modes (i0*I2 + i2 for mode 1).
+ *   omegas[i]: FP16 bits, (prod_{j != i} dims[j]) x J_i with leading dimension
+ *   omega_lds[i] (omega_lds NULL: J_i; the tensor-core path needs
+ *   omega_lds[i] % 8 == 0); its row index is the row-major linear index of the
+ *   other modes (i0*I2 + i2 for mode 1).  The tensor-core path also needs
+ *   dims[2] % 4 == 0 (TMA row stride).
  *   W_i = X_(i) Omega_i; Q_i = CholeskyQR2(W_i) -> factors[i] (dims[i] x J_i, ld J_i).
  *   core (J0 x J1 x J2, row-major) = X x_0 Q_0^T x_1 Q_1^T x_2 Q_2^T.
  * variant: SHG_SPLIT_F16 (SHGEMM projections, TCEC-split first core
@@ -178,7 +181,7 @@ int shg_rsvd(int64_t m, int64_t n, int64_t rank, int64_t oversampling, int power
  */
 int shg_rp_hosvd_workspace_size(int ndim, const int64_t* dims, const int64_t* ranks, size_t* bytes);
 int shg_rp_hosvd(int ndim, const int64_t* dims, const int64_t* ranks, const float* X,
-                 const uint16_t* const* omegas, float* core, float* const* factors,
+                 const uint16_t* const* omegas, const int64_t* omega_lds, float* core, float* const* factors,
                  void* workspace, size_t ws_bytes, int variant, int32_t* d_flags, void* stream);
 
 #ifdef __cplusplus

@@ -224,8 +224,8 @@ def shg_rp_hosvd(X: torch.Tensor, omegas, ranks, variant="f16", workspace: torch
         for j, d in enumerate(dims):
             if j != i:
                 rows *= d
-        if om.dtype != torch.float16 or tuple(om.shape) != (rows, ranks[i]) or not om.is_contiguous():
-            raise ValueError(f"omega {i} must be a contiguous float16 {rows} x {ranks[i]} tensor")
+        if om.dtype != torch.float16 or tuple(om.shape) != (rows, ranks[i]) or om.stride(1) != 1:
+            raise ValueError(f"omega {i} must be a row-major float16 {rows} x {ranks[i]} tensor")
     dev = X.device
     if out is None:
         core = torch.empty(*ranks, dtype=torch.float32, device=dev)
@@ -238,8 +238,9 @@ def shg_rp_hosvd(X: torch.Tensor, omegas, ranks, variant="f16", workspace: torch
     d = (ctypes.c_int64 * 3)(*dims)
     r = (ctypes.c_int64 * 3)(*ranks)
     om_ptrs = (ctypes.c_void_p * 3)(*[o.data_ptr() for o in omegas])
+    om_lds = (ctypes.c_int64 * 3)(*[o.stride(0) for o in omegas])
     f_ptrs = (ctypes.c_void_p * 3)(*[f.data_ptr() for f in facs])
-    _check(_lib.load().shg_rp_hosvd(3, d, r, _ptr(X), om_ptrs, _ptr(core), f_ptrs, _ptr(ws), ws.numel(),
+    _check(_lib.load().shg_rp_hosvd(3, d, r, _ptr(X), om_ptrs, om_lds, _ptr(core), f_ptrs, _ptr(ws), ws.numel(),
                                     _variant(variant), _ptr(fl), _stream(stream)), "shg_rp_hosvd")
     if check:
         check_flags(fl, "shg_rp_hosvd")

@@ -38,7 +38,8 @@ SIGNATURES = {
     "shg_rp_hosvd_workspace_size": (c_int, [c_int, ctypes.POINTER(c_i64), ctypes.POINTER(c_i64),
                                             ctypes.POINTER(c_sz)]),
     "shg_rp_hosvd": (c_int, [c_int, ctypes.POINTER(c_i64), ctypes.POINTER(c_i64), c_vp,
-                             ctypes.POINTER(c_vp), c_vp, ctypes.POINTER(c_vp), c_vp, c_sz, c_int, c_vp, c_vp]),
+                             ctypes.POINTER(c_vp), ctypes.POINTER(c_i64), c_vp, ctypes.POINTER(c_vp), c_vp, c_sz,
+                             c_int, c_vp, c_vp]),
 }
 
 _lib = None

@@ -47,7 +47,7 @@ RsvdLayout rsvd_layout(int64_t m, int64_t n, int64_t k, int64_t rank) {
   L.Bt = take(n * ldk * 4);
   L.small = take(cholqr_small_bytes(k));
   L.Vk = take(k * k * 4);
-  L.lam = take(k * 8);
+  L.lam = take(2 * k * 8);
   L.Up = take(k * rank * 4);
   L.Ups = take(k * rank * 4);
   L.total = off;
@@ -262,14 +262,18 @@ int shg_rp_hosvd_workspace_size(int ndim, const int64_t* dims, const int64_t* ra
 }
 
 int shg_rp_hosvd(int ndim, const int64_t* dims, const int64_t* ranks, const float* X,
-                 const uint16_t* const* omegas, float* core, float* const* factors, void* ws, size_t ws_bytes,
-                 int variant, int32_t* d_flags, void* stream) {
+                 const uint16_t* const* omegas, const int64_t* omega_lds, float* core, float* const* factors,
+                 void* ws, size_t ws_bytes, int variant, int32_t* d_flags, void* stream) {
   size_t need = 0;
   const int rc0 = shg_rp_hosvd_workspace_size(ndim, dims, ranks, &need);
   if (rc0 != SHG_OK) return rc0;
   if (!X || !omegas || !core || !factors || !ws || !d_flags) return SHG_ERR_INVALID_ARG;
-  for (int i = 0; i < 3; ++i)
+  int64_t ldo[3];
+  for (int i = 0; i < 3; ++i) {
     if (!omegas[i] || !factors[i]) return SHG_ERR_INVALID_ARG;
+    ldo[i] = omega_lds ? omega_lds[i] : ranks[i];
+    if (ldo[i] < ranks[i]) return SHG_ERR_INVALID_ARG;
+  }
   if (variant != SHG_SPLIT_F16 && variant != SHG_FP32_SIMT) return SHG_ERR_UNSUPPORTED;
   if (ws_bytes < need) return SHG_ERR_WORKSPACE;
   cudaStream_t st = static_cast<cudaStream_t>(stream);
@@ -287,14 +291,16 @@ int shg_rp_hosvd(int ndim, const int64_t* dims, const int64_t* ranks, const floa
 
   // lines 1-3: W_i = X_(i) Omega_(i), Q_i = orth(W_i)
   if (tc) {
-    SHG_TRY(tc_gemm(A_KMAJ, B_F16, 2, I0, J0, I1 * I2, 1, X, I1 * I2, 0, omegas[0], J0, W[0], L.ld[0], 0, d_flags, st));
-    SHG_TRY(tc_gemm(A_KMAJ, B_F16, 2, I1, J1, I2, I0, X, I2, I1 * I2, omegas[1], J1, W[1], L.ld[1], 0, d_flags, st));
-    SHG_TRY(tc_gemm(A_MNMAJ, B_F16, 2, I2, J2, I0 * I1, 1, X, I2, 0, omegas[2], J2, W[2], L.ld[2], 0, d_flags, st));
+    SHG_TRY(tc_gemm(A_KMAJ, B_F16, 2, I0, J0, I1 * I2, 1, X, I1 * I2, 0, omegas[0], ldo[0], W[0], L.ld[0], 0, d_flags, st));
+    SHG_TRY(tc_gemm(A_KMAJ, B_F16, 2, I1, J1, I2, I0, X, I2, I1 * I2, omegas[1], ldo[1], W[1], L.ld[1], 0, d_flags,
+                    st));
+    SHG_TRY(tc_gemm(A_MNMAJ, B_F16, 2, I2, J2, I0 * I1, 1, X, I2, 0, omegas[2], ldo[2], W[2], L.ld[2], 0, d_flags,
+                    st));
   } else {
-    SHG_TRY(simt_gemm(I0, J0, I1 * I2, X, I1 * I2, 0, omegas[0], J0, 1, W[0], L.ld[0], 0, 1, 0, 0, 0, st));
+    SHG_TRY(simt_gemm(I0, J0, I1 * I2, X, I1 * I2, 0, omegas[0], ldo[0], 1, W[0], L.ld[0], 0, 1, 0, 0, 0, st));
     if (cudaMemsetAsync(W[1], 0, I1 * L.ld[1] * 4, st) != cudaSuccess) return SHG_ERR_CUDA;
-    SHG_TRY(simt_gemm(I1, J1, I2, X, I2, 0, omegas[1], J1, 1, W[1], L.ld[1], 1, I0, I1 * I2, I2 * J1, 0, st));
-    SHG_TRY(simt_gemm(I2, J2, I0 * I1, X, I2, 1, omegas[2], J2, 1, W[2], L.ld[2], 0, 1, 0, 0, 0, st));
+    SHG_TRY(simt_gemm(I1, J1, I2, X, I2, 0, omegas[1], ldo[1], 1, W[1], L.ld[1], 1, I0, I1 * I2, I2 * ldo[1], 0, st));
+    SHG_TRY(simt_gemm(I2, J2, I0 * I1, X, I2, 1, omegas[2], ldo[2], 1, W[2], L.ld[2], 0, 1, 0, 0, 0, st));
   }
   for (int i = 0; i < 3; ++i) {
     SHG_TRY(cholqr2(dims[i], ranks[i], W[i], L.ld[i], T, L.ld[i], small, d_flags, st));

@@ -227,32 +227,50 @@ __global__ void __launch_bounds__(1024) jacobi_kernel(int k, const double* __res
   }
 }
 
-// lambda_i = v_i^T G v_i (FP64, G symmetric from its upper triangle); one CTA per i.
+// lambda_i = v_i^T G v_i / v_i^T v_i (FP64 Rayleigh quotient, G symmetric
+// from its upper triangle; the FP32 rotations leave |v_i| = 1 only to
+// ~1e-5); one CTA per i.  nrm[i] = |v_i| (FP64).
 __global__ void rayleigh_kernel(int k, const double* __restrict__ G, const float* __restrict__ V,
-                                double* __restrict__ lam) {
+                                double* __restrict__ lam, double* __restrict__ nrm) {
   const int i = blockIdx.x;
-  __shared__ double red[32];
-  double s = 0.0;
+  __shared__ double red[2][32];
+  double s = 0.0, q = 0.0;
   for (int e = threadIdx.x; e < k * k; e += blockDim.x) {
     const int a = e / k, b = e - a * k;
     const double g = G[min(a, b) * k + max(a, b)];
     s = fma(static_cast<double>(V[a * k + i]) * g, static_cast<double>(V[b * k + i]), s);
   }
+  for (int a = threadIdx.x; a < k; a += blockDim.x) {
+    const double v = V[a * k + i];
+    q = fma(v, v, q);
+  }
 #pragma unroll
-  for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
-  if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = s;
+  for (int o = 16; o > 0; o >>= 1) {
+    s += __shfl_xor_sync(0xffffffffu, s, o);
+    q += __shfl_xor_sync(0xffffffffu, q, o);
+  }
+  if ((threadIdx.x & 31) == 0) {
+    red[0][threadIdx.x >> 5] = s;
+    red[1][threadIdx.x >> 5] = q;
+  }
   __syncthreads();
   if (threadIdx.x == 0) {
-    double t = 0.0;
-    for (int w = 0; w < (blockDim.x + 31) / 32; ++w) t += red[w];
-    lam[i] = t;
+    double t = 0.0, u = 0.0;
+    for (int w = 0; w < (blockDim.x + 31) / 32; ++w) {
+      t += red[0][w];
+      u += red[1][w];
+    }
+    lam[i] = t / u;
+    nrm[i] = sqrt(u);
   }
 }
 
 // Sort eigenvalues descending (ties by index), S[j] = sqrt(lambda) for the
-// top p, Up = V[:, perm[:p]] and Ups = Up / S (k x p, FP32).
-__global__ void sort_select_kernel(int k, int p, const double* __restrict__ lam, const float* __restrict__ V,
-                                   float* __restrict__ S, float* __restrict__ Up, float* __restrict__ Ups) {
+// top p, Up = V[:, perm[:p]] normalised to unit length and Ups = Up / S
+// (k x p, FP32).
+__global__ void sort_select_kernel(int k, int p, const double* __restrict__ lam, const double* __restrict__ nrm,
+                                   const float* __restrict__ V, float* __restrict__ S, float* __restrict__ Up,
+                                   float* __restrict__ Ups) {
   extern __shared__ int rank_of[];
   for (int i = threadIdx.x; i < k; i += blockDim.x) {
     const double li = lam[i];
@@ -269,11 +287,12 @@ __global__ void sort_select_kernel(int k, int p, const double* __restrict__ lam,
     if (r < p) {
       const double sg = sqrt(fmax(lam[i], 0.0));
       S[r] = static_cast<float>(sg);
-      const float inv = sg > 0.0 ? static_cast<float>(1.0 / sg) : 0.0f;
+      const double inv_n = 1.0 / nrm[i];
+      const double inv_s = sg > 0.0 ? inv_n / sg : 0.0;
       for (int a = 0; a < k; ++a) {
-        const float v = V[a * k + i];
-        Up[a * p + r] = v;
-        Ups[a * p + r] = v * inv;
+        const double v = V[a * k + i];
+        Up[a * p + r] = static_cast<float>(v * inv_n);
+        Ups[a * p + r] = static_cast<float>(v * inv_s);
       }
     }
   }
@@ -348,9 +367,11 @@ int jacobi_eig(int64_t k, const double* G, float* V, float* scratch, cudaStream_
 
 int rayleigh_sort(int64_t k, int64_t p, const double* G, const float* V, double* lam, float* S, float* Up,
                   float* Ups, cudaStream_t st) {
-  rayleigh_kernel<<<static_cast<unsigned>(k), 256, 0, st>>>(static_cast<int>(k), G, V, lam);
+  double* nrm = lam + k;  // lam holds 2k doubles
+  rayleigh_kernel<<<static_cast<unsigned>(k), 256, 0, st>>>(static_cast<int>(k), G, V, lam, nrm);
   if (cudaGetLastError() != cudaSuccess) return SHG_ERR_CUDA;
-  sort_select_kernel<<<1, 256, k * sizeof(int), st>>>(static_cast<int>(k), static_cast<int>(p), lam, V, S, Up, Ups);
+  sort_select_kernel<<<1, 256, k * sizeof(int), st>>>(static_cast<int>(k), static_cast<int>(p), lam, nrm, V, S, Up,
+                                                      Ups);
   return cuda_status(cudaGetLastError());
 }
 

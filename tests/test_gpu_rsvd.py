@@ -118,7 +118,13 @@ def test_rp_hosvd_small(shg):
     oms = hosvd_omegas(dims, J, seed=4)
     ref = OH.rp_hosvd(A, oms)
     for variant in ("f16", "fp32"):
-        core, facs = shg.shg_rp_hosvd(dev(A), [dev(o) for o in oms], J, variant=variant)
+        # Omega stored with leading dimension 16 (the TMA row stride rule)
+        om_d = []
+        for o in oms:
+            buf = torch.zeros(o.shape[0], 16, dtype=torch.float16, device="cuda")
+            buf[:, :o.shape[1]] = dev(o)
+            om_d.append(buf[:, :o.shape[1]])
+        core, facs = shg.shg_rp_hosvd(dev(A), om_d, J, variant=variant)
         core = core.cpu().numpy().astype(np.float64)
         facs = [f.cpu().numpy().astype(np.float64) for f in facs]
         for i in range(3):
