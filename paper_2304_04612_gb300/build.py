@@ -35,7 +35,8 @@ def sources():
 
 def _compile(src: str, ptxas_verbose: bool) -> tuple[str, str]:
     obj = os.path.join(BUILD, os.path.basename(src)[:-3] + ".o")
-    cmd = [nvcc(), *ARCH, *FLAGS, "-c", src, "-o", obj]
+    extra = os.environ.get("SHG_NVCC_FLAGS", "").split()   # tuning experiments only
+    cmd = [nvcc(), *ARCH, *FLAGS, *extra, "-c", src, "-o", obj]
     if ptxas_verbose:
         cmd += ["-Xptxas", "-v"]
     r = subprocess.run(cmd, capture_output=True, text=True)
