@@ -5,6 +5,10 @@
 #include <cstdint>
 #include <cuda.h>
 
+#ifndef SHG_WAIT_HINT_NS
+#define SHG_WAIT_HINT_NS 20000
+#endif
+
 namespace shg {
 
 __device__ __forceinline__ uint32_t smem_u32(const void* p) {
@@ -63,7 +67,11 @@ __device__ __forceinline__ bool mbar_wait(uint32_t bar, uint32_t parity, volatil
   if (mbar_try_wait(bar, parity)) return true;
   const uint64_t t0 = globaltimer_ns();
   for (;;) {
-    if (mbar_try_wait_sleep(bar, parity, 20000u)) return true;
+#if SHG_WAIT_HINT_NS > 0
+    if (mbar_try_wait_sleep(bar, parity, SHG_WAIT_HINT_NS)) return true;
+#else
+    if (mbar_try_wait(bar, parity)) return true;
+#endif
     if (*abort) return false;
     if (globaltimer_ns() - t0 > limit_ns) {
       *abort = 1;
@@ -91,6 +99,19 @@ __device__ __forceinline__ void tma_load_3d(uint32_t dst, const CUtensorMap* map
       "%5}], [%2];" ::"r"(dst),
       "l"(reinterpret_cast<uint64_t>(map)), "r"(bar), "r"(x), "r"(y), "r"(z)
       : "memory");
+}
+// Prefetch a tensor box into L2 (no shared-memory destination, no barrier).
+__device__ __forceinline__ void tma_prefetch_2d(const CUtensorMap* map, int x, int y) {
+  asm volatile("cp.async.bulk.prefetch.tensor.2d.L2.global.tile [%0, {%1, %2}];" ::"l"(
+                   reinterpret_cast<uint64_t>(map)),
+               "r"(x), "r"(y)
+               : "memory");
+}
+__device__ __forceinline__ void tma_prefetch_3d(const CUtensorMap* map, int x, int y, int z) {
+  asm volatile("cp.async.bulk.prefetch.tensor.3d.L2.global.tile [%0, {%1, %2, %3}];" ::"l"(
+                   reinterpret_cast<uint64_t>(map)),
+               "r"(x), "r"(y), "r"(z)
+               : "memory");
 }
 // Make generic-proxy shared-memory writes visible to the async proxy
 // (tensor-core operand reads).

@@ -1,12 +1,13 @@
 // SHGEMM on tcgen05 tensor cores (Sec. 4.1, Eqs. shgemm-1..3), its BF16
 // analogue, and the TCEC split product (Eq. tcec-5) for two FP32 operands.
 //
-// One CTA = 10 warps, one CTA per SM, persistent over a contiguous range of
+// One CTA = 11 warps, one CTA per SM, persistent over a contiguous range of
 // work units (stream-K).  A unit is one (N tile <= 128, 128-row M tile,
 // 64-deep K block).
-//   warp 0      TMA producer: FP32 A tile (128 x 64, 32 KB) into a shared-
-//               memory staging ring; B tile (16-bit Omega, or the FP32 B
-//               tile of the TCEC product) into a second ring
+//   warp 0      TMA producer of A: FP32 tile (128 x 64, 32 KB) into a shared-
+//               memory staging ring, running ahead independently of B
+//   warp 10     TMA producer of B: 16-bit Omega tile (or the FP32 B tile of
+//               the TCEC product) into a second ring, freed by the MMAs
 //   warp 1      TMEM owner + single-thread tcgen05.mma issuer; the A operand
 //               is read from tensor memory, B from shared memory
 //   warps 2..5  split warps: thread r of the CTA's 128 reads row r of the
@@ -48,9 +49,10 @@ namespace shg {
 
 namespace {
 
-constexpr int kThreads = 320;
+constexpr int kThreads = 352;
 constexpr int kFirstSplitWarp = 2;
 constexpr int kFirstEpiWarp = 6;
+constexpr int kBProducerWarp = 10;
 constexpr int kBM = 128;  // rows of the output tile (tcgen05 M)
 constexpr int kBK = 64;   // K depth per unit
 constexpr uint32_t kMaxSmem = 232448;
@@ -69,6 +71,7 @@ struct TcArgs {
   int sa, sb, st;  // ring depths: A staging, B tiles, TMEM A stages
   uint32_t tmem_cols, b_bytes;
   int kc;
+  int prefetch;  // L2 prefetch group size in units (0: off)
   unsigned long long wait_ns;
   int drop_commit;
 };
@@ -298,13 +301,32 @@ __global__ void __launch_bounds__(kThreads, 1)
   long long issued_a = 0, issued_b = 0;
 
   if (warp == 0) {
-    // ---------------------------------------------------------- TMA producer
+    // ---------------------------------------------------------- A producer
+    // The A stream runs ahead on its own: loaded TMA latency is several
+    // microseconds, so A must never wait behind the B ring (which frees
+    // only when the MMAs complete).
     if (lane == 0) {
-      const uint32_t b_tx = kSplitB ? N * 256u : N * 128u;
+      // L2 prefetch in groups: every `pf` units the next `pf` units' boxes
+      // are requested back to back, so each row of A is fetched from DRAM in
+      // runs of pf x 256 contiguous bytes; the shared-memory loads then hit L2.
+      const int pf = args.prefetch;
       long long i = 0;
       for (long long u = u0; u < u1; ++u, ++i) {
-        const int sa = static_cast<int>(i % SA), sb = static_cast<int>(i % SB);
-        const uint32_t pa = static_cast<uint32_t>((i / SA) & 1), pb = static_cast<uint32_t>((i / SB) & 1);
+        const int sa = static_cast<int>(i % SA);
+        const uint32_t pa = static_cast<uint32_t>((i / SA) & 1);
+        if (pf > 0 && (i % pf) == 0) {
+          for (long long v = u + pf; v < u + 2 * pf && v < u1; ++v) {
+            const UnitPos q = decode(v, args);
+            const int qp = q.kb / args.kb_per_p;
+            const int qk = q.kb - qp * args.kb_per_p;
+            if (AMAJ == A_KMAJ) {
+              tma_prefetch_3d(&tmA, qk * kBK, q.mt * kBM, qp);
+              tma_prefetch_3d(&tmA, qk * kBK + 32, q.mt * kBM, qp);
+            } else {
+              for (int j = 0; j < 4; ++j) tma_prefetch_2d(&tmA, q.mt * kBM + 32 * j, q.kb * kBK);
+            }
+          }
+        }
         const UnitPos p = decode(u, args);
         const int pp = p.kb / args.kb_per_p;
         const int sk = p.kb - pp * args.kb_per_p;
@@ -319,6 +341,20 @@ __global__ void __launch_bounds__(kThreads, 1)
           for (int j = 0; j < 4; ++j) tma_load_2d(adst + j * 8192, &tmA, afull, p.mt * kBM + 32 * j, p.kb * kBK);
         }
         issued_a = i + 1;
+      }
+    }
+    __syncwarp();
+  } else if (warp == kBProducerWarp) {
+    // ---------------------------------------------------------- B producer
+    if (lane == 0) {
+      const uint32_t b_tx = kSplitB ? N * 256u : N * 128u;
+      long long i = 0;
+      for (long long u = u0; u < u1; ++u, ++i) {
+        const int sb = static_cast<int>(i % SB);
+        const uint32_t pb = static_cast<uint32_t>((i / SB) & 1);
+        const UnitPos p = decode(u, args);
+        const int pp = p.kb / args.kb_per_p;
+        const int sk = p.kb - pp * args.kb_per_p;
         if (!mbar_wait(bar_bempty + 8 * sb, pb ^ 1u, abort_flag, lim)) break;
         const uint32_t bfull = bar_bfull + 8 * sb;
         const uint32_t bdst = smem_u32(b_ring + sb * args.b_bytes);
@@ -368,13 +404,17 @@ __global__ void __launch_bounds__(kThreads, 1)
             tc_fence_after();
             const uint32_t sbm = smem_u32(b_ring + sb * args.b_bytes);
             const uint32_t ta = tm_a + st * (PIECES * 32);
+            // K step ks advances the start address by 16 rows of 128 B; the
+            // address field holds bytes >> 4, so that is + ks * 128
+            const uint64_t bh0 = smem_desc_sw128(sbm, 8192, 1024);
+            const uint64_t bl0 = smem_desc_sw128(sbm + b_piece, 8192, 1024);
 #pragma unroll
             for (int ks = 0; ks < kBK / 16; ++ks) {
               const uint32_t acc_d = (u == chunk_start && ks == 0) ? 0u : 1u;
               const uint32_t acc_l = (first_in_seg && ks == 0) ? 0u : 1u;
-              const uint64_t bh = smem_desc_sw128(sbm + ks * 2048, 8192, 1024);
+              const uint64_t bh = bh0 + static_cast<uint64_t>(ks * 128);
               if (kSplitB) {
-                const uint64_t bl = smem_desc_sw128(sbm + b_piece + ks * 2048, 8192, 1024);
+                const uint64_t bl = bl0 + static_cast<uint64_t>(ks * 128);
                 tc_mma_f16_tmem_a(tm_d, ta + ks * 8, bh, idesc, acc_d);       // hiA * hiB (RN drained)
                 tc_mma_f16_tmem_a(tm_l, ta + 32 + ks * 8, bh, idesc, acc_l);  // loA * hiB
                 tc_mma_f16_tmem_a(tm_l, ta + ks * 8, bl, idesc, 1u);          // hiA * loB
@@ -535,10 +575,12 @@ __global__ void __launch_bounds__(kThreads, 1)
 
   __syncthreads();
   if (*abort_flag) {
+    // wait (bounded) for this CTA's TMA copies still in flight
     if (warp == 0 && lane == 0) {
-      // wait (bounded) for this CTA's TMA copies still in flight
       for (long long j = (issued_a > SA ? issued_a - SA : 0); j < issued_a; ++j)
         wait_time_only(bar_afull + 8 * static_cast<int>(j % SA), static_cast<uint32_t>((j / SA) & 1), lim);
+    }
+    if (warp == kBProducerWarp && lane == 0) {
       for (long long j = (issued_b > SB ? issued_b - SB : 0); j < issued_b; ++j)
         wait_time_only(bar_bfull + 8 * static_cast<int>(j % SB), static_cast<uint32_t>((j / SB) & 1), lim);
     }
@@ -591,26 +633,32 @@ bool make_map(CUtensorMap* map, CUtensorMapDataType dt, int rank, const void* pt
              CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
 }
 
+int env_int(const char* name, int dflt) {
+  const char* e = std::getenv(name);
+  return e ? std::atoi(e) : dflt;
+}
+
 template <int AMAJ, int BMODE, int PIECES>
 int launch(const CUtensorMap& ta, const CUtensorMap& tb, const TcArgs& a, int grid, size_t smem,
            cudaStream_t st) {
   auto k = tc_gemm_kernel<AMAJ, BMODE, PIECES>;
-  static bool configured[64] = {};  // one attribute call per instantiation and device
+  // The shared-memory carve-out is sized to what the rings need; the rest of
+  // the SM's 256 KB stays L1.  One attribute update per instantiation,
+  // device and size.
+  static size_t configured[64] = {};
   int dev = 0;
   if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 64) return SHG_ERR_CUDA;
-  if (!configured[dev]) {
-    if (cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, static_cast<int>(kMaxSmem)) !=
-        cudaSuccess)
+  if (configured[dev] != smem) {
+    const int carve = static_cast<int>((smem * 100 + kMaxSmem - 1) / kMaxSmem);
+    if (cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, static_cast<int>(smem)) !=
+            cudaSuccess ||
+        (env_int("SHG_CARVE", 1) &&
+         cudaFuncSetAttribute(k, cudaFuncAttributePreferredSharedMemoryCarveout, carve) != cudaSuccess))
       return SHG_ERR_CUDA;
-    configured[dev] = true;
+    configured[dev] = smem;
   }
   k<<<grid, kThreads, smem, st>>>(ta, tb, a);
   return cuda_status(cudaGetLastError());
-}
-
-int env_int(const char* name, int dflt) {
-  const char* e = std::getenv(name);
-  return e ? std::atoi(e) : dflt;
 }
 
 }  // namespace
