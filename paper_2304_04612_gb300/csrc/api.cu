@@ -236,11 +236,10 @@ int shg_rsvd(int64_t m, int64_t n, int64_t rank, int64_t oversampling, int power
   else
     SHG_TRY(simt_gemm(n, k, m, A, lda, 1, Y, ldk, 0, Bt, ldk, 0, 1, 0, 0, 0, st));
   // line 4: tSVD(B) through the eigendecomposition of B B^T = Bt^T Bt
-  uint8_t* sw = static_cast<uint8_t*>(small);
-  double* G = reinterpret_cast<double*>(sw);
-  float* jscratch = reinterpret_cast<float*>(sw + 3 * align256(k * k * 8) + align256(k * k * 4));
+  const SmallWs sw = small_ws(small, k);
+  double* G = sw.G;
   SHG_TRY(gram_f64(n, k, Bt, ldk, G, st));
-  SHG_TRY(jacobi_eig(k, G, Vk, jscratch, st));
+  SHG_TRY(jacobi_eig(k, G, Vk, sw.jac, st));
   SHG_TRY(rayleigh_sort(k, rank, G, Vk, lam, S, Up, Ups, st));
   // line 5: U = Q U'; V = B^T U' Sigma^-1
   SHG_TRY(simt_gemm(m, rank, k, Y, ldk, 0, Up, rank, 0, U, rank, 0, 1, 0, 0, 0, st));

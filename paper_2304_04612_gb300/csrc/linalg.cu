@@ -1,16 +1,17 @@
 // k x k linear algebra of the randomized factorizations (k = rank +
-// oversampling, small): FP64 Gram matrices, FP64 Cholesky, triangular
-// inverse, and the eigendecomposition of B B^T for the small SVD of
+// oversampling, small): FP64 Gram matrices, FP64 Cholesky with the inverse
+// of its factor, and the eigendecomposition of B B^T for the small SVD of
 // Algorithm 1 (line 4).
 //
 // CholeskyQR2 replaces the QR factorization of Algorithm 1 (line 2) and
 // Algorithm 2 (line 4): twice { G = X^T X, G = R^T R, X <- X R^-1 }.  The
 // Gram matrix is accumulated in FP64 from exact FP32 x FP32 products, the
-// Cholesky factor is FP64, X R^-1 is an FP32 GEMM with R^-1 rounded to FP32.
+// Cholesky factor and its inverse are FP64, X R^-1 is an FP32 GEMM with R^-1
+// rounded to FP32.
 //
 // The eigensolver is a parallel cyclic Jacobi method (round-robin pairing)
 // in FP32 on the scaled Gram matrix; eigenvalues are then refined as FP64
-// Rayleigh quotients v^T G v with the FP64 Gram matrix.
+// Rayleigh quotients v^T G v / v^T v with the FP64 Gram matrix.
 #include <cuda_fp16.h>
 
 #include "internal.h"
@@ -59,171 +60,324 @@ __global__ void __launch_bounds__(256) gram_f64_kernel(int m, int k, const float
   }
 }
 
-// ------------------------------------------------------------- Cholesky FP64
-// Upper Cholesky G = R^T R of the k x k matrix whose upper triangle is in G
-// (row-major, ld k).  One CTA; the matrix lives in shared memory when it
-// fits, else in `scratch` (global, k*k doubles).  R (upper, zero below) is
-// written to R.  A non-positive pivot raises SHG_FLAG_NOT_SPD and is replaced
-// by the smallest positive double so that the factor stays finite.
-__global__ void __launch_bounds__(1024) cholesky_kernel(int k, const double* __restrict__ G, double* __restrict__ R,
-                                                       double* scratch, int in_smem, int* flags) {
-  extern __shared__ double sm[];
-  double* a = in_smem ? sm : scratch;
-  const int tid = threadIdx.x, nt = blockDim.x;
-  for (int e = tid; e < k * k; e += nt) {
-    const int i = e / k, j = e - i * k;
-    a[e] = (j >= i) ? G[e] : 0.0;
-  }
+// ------------------------------------------------ Cholesky + inverse
+// FP64 on this part has a 64-cycle dependent latency and under 2 FMA per
+// clock per SM, so the k x k kernels keep FP64 off their serial chains
+// wherever FP32 carries enough precision.
+
+// Largest diagonal entry of the k x k FP64 matrix G (one CTA, result to
+// *out, valid after the next barrier).
+__device__ void diag_max(int k, const double* __restrict__ G, double* red, double* out) {
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5, nw = blockDim.x >> 5;
+  double m = 0.0;
+  for (int i = tid; i < k; i += blockDim.x) m = fmax(m, fabs(G[i * k + i]));
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) m = fmax(m, __shfl_xor_sync(0xffffffffu, m, o));
+  if (lane == 0) red[warp] = m;
   __syncthreads();
-  __shared__ double inv_piv;
-  for (int j = 0; j < k; ++j) {
-    if (tid == 0) {
-      double d = a[j * k + j];
-      if (!(d > 0.0)) {
-        atomicOr(flags, SHG_FLAG_NOT_SPD);
-        d = 2.2250738585072014e-308;
-      }
-      const double r = sqrt(d);
-      a[j * k + j] = r;
-      inv_piv = 1.0 / r;
-    }
-    __syncthreads();
-    for (int l = j + 1 + tid; l < k; l += nt) a[j * k + l] *= inv_piv;
-    __syncthreads();
-    const int w = k - j - 1;  // trailing size
-    const int tot = w * w;
-    for (int e = tid; e < tot; e += nt) {
-      const int l = j + 1 + e / w, lp = j + 1 + e % w;
-      if (lp >= l) a[l * k + lp] -= a[j * k + l] * a[j * k + lp];
-    }
-    __syncthreads();
-  }
-  for (int e = tid; e < k * k; e += nt) {
-    const int i = e / k, j = e - i * k;
-    R[e] = (j >= i) ? a[e] : 0.0;
+  if (tid == 0) {
+    double t = 0.0;
+    for (int w = 0; w < nw; ++w) t = fmax(t, red[w]);
+    *out = t;
   }
 }
 
-// ------------------------------------------------------- triangular inverse
-// X = R^-1 for upper-triangular R (k x k, FP64).  One warp per column j:
-// X[j][j] = 1/R[j][j]; X[i][j] = -(sum_{l=i+1..j} R[i][l] X[l][j]) / R[i][i].
-// Writes the FP32 rounding of X to Xf (k x k, zero below the diagonal).
-__global__ void tri_inv_kernel(int k, const double* __restrict__ R, double* __restrict__ X, float* __restrict__ Xf) {
-  const int warp = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
-  const int lane = threadIdx.x & 31;
-  if (warp >= k) return;
-  const int j = warp;
-  for (int i = lane; i < k; i += 32) {
-    if (i > j) {
-      X[i * k + j] = 0.0;
-      Xf[i * k + j] = 0.0f;
+// Upper Cholesky G = R^T R of the k x k matrix whose upper triangle is in G
+// (row-major, ld k), then X = R^-1; writes X in FP32 (upper, zero below the
+// diagonal) to Xf.  One CTA.
+//   G is scaled by sigma = 4^-e (e = floor(log2(max diag) / 2)), an exact
+//   power of two, so that pivots lie near [0, 4] and sqrt(sigma) = 2^-e is
+//   exact: R^-1 = 2^-e R_s^-1.
+//   Elimination (FP64) keeps rows unscaled: after column j,
+//   a[j][l] = R[j][j] R[j][l] and d_j = a[j][j] = R[j][j]^2, so the trailing
+//   update a[l][l'] -= (a[j][l] / d_j) a[j][l'] needs only 1/d_j, which the
+//   thread owning a[j+1][j+1] forms as soon as it has updated it (an FP32
+//   reciprocal refined by one Newton-Raphson step r (2 - d r), relative
+//   error about 2^-48): one barrier per column.
+//   Inverse (FP32, from R rounded to FP32): X[j][j] = 1/R[j][j],
+//   X[i][j] = -(1/R[i][i]) sum_{l=i+1..j} R[i][l] X[l][j]; thread j
+//   back-substitutes column j alone.  Its rounding is of the same order as
+//   that of the FP32 product X R^-1 which follows.
+// `a` (k^2 doubles) and the FP32 R and X (k^2 floats each) live in shared
+// memory when they fit, else in `scratch` (2 k^2 doubles).  A non-positive
+// pivot raises SHG_FLAG_NOT_SPD and is replaced by the smallest positive
+// normal double so that R stays finite.
+// SMEM selects the shared-memory layout at compile time, so that the
+// accesses compile to shared loads and stores rather than generic ones.
+template <bool SMEM>
+__global__ void __launch_bounds__(1024) chol_inv_kernel(int k, const double* __restrict__ G, float* __restrict__ Xf,
+                                                       double* scratch, int* flags) {
+  extern __shared__ double sm[];
+  double* a = SMEM ? sm : scratch;
+  float* rf = reinterpret_cast<float*>(a + k * k);
+  float* xf = rf + k * k;
+  __shared__ double dinv[1024];
+  __shared__ float rinv[1024];
+  __shared__ double red[32];
+  __shared__ double dmax;
+  const int tid = threadIdx.x, nt = blockDim.x;
+  const int lane = tid & 31, warp = tid >> 5, nw = nt >> 5;
+  diag_max(k, G, red, &dmax);
+  __syncthreads();
+  const int e2 = (dmax > 0.0) ? (ilogb(dmax) >> 1) : 0;
+  const double sigma = ldexp(1.0, -2 * e2);
+  for (int e = tid; e < k * k; e += nt) {
+    const int i = e / k, j = e - i * k;
+    a[e] = (j >= i) ? G[e] * sigma : 0.0;
+  }
+  __syncthreads();
+  auto pivot = [&](int j) {
+    double d = a[j * k + j];
+    if (!(d > 0.0)) {
+      atomicOr(flags, SHG_FLAG_NOT_SPD);
+      d = 2.2250738585072014e-308;
+      a[j * k + j] = d;
+    }
+    double r;
+    if (d >= 1e-37 && d <= 1e37) {
+      r = static_cast<double>(1.0f / static_cast<float>(d));
+      r = r * fma(-d, r, 2.0);
+    } else {
+      r = 1.0 / d;
+    }
+    dinv[j] = r;
+  };
+  if (tid == 0) pivot(0);
+  __syncthreads();
+  for (int j = 0; j < k - 1; ++j) {
+    const double dj = dinv[j];
+    const double* rowj = a + j * k;
+    for (int l = j + 1 + warp; l < k; l += nw) {
+      const double t = rowj[l] * dj;
+      double* rowl = a + l * k;
+      for (int lp = l + lane; lp < k; lp += 32) rowl[lp] = fma(-t, rowj[lp], rowl[lp]);
+    }
+    // warp 0 lane 0 owns a[j+1][j+1] (row j+1, first column)
+    if (tid == 0) pivot(j + 1);
+    __syncthreads();
+  }
+  // R in FP32: R[i][l] = a[i][l] / R[i][i], 1/R[i][i] = sqrt(1/d_i)
+  for (int i = tid; i < k; i += nt) rinv[i] = static_cast<float>(sqrt(dinv[i]));
+  for (int e = tid; e < k * k; e += nt) {
+    const int i = e / k, l = e - i * k;
+    if (l > i) rf[e] = static_cast<float>(a[e] * sqrt(dinv[i]));
+  }
+  __syncthreads();
+  for (int j = tid; j < k; j += nt) {
+    xf[j * k + j] = rinv[j];
+    for (int i = j - 1; i >= 0; --i) {
+      float s8[8] = {0, 0, 0, 0, 0, 0, 0, 0};
+      int l = i + 1;
+      for (; l + 7 <= j; l += 8) {
+#pragma unroll
+        for (int u = 0; u < 8; ++u) s8[u] = fmaf(rf[i * k + l + u], xf[(l + u) * k + j], s8[u]);
+      }
+      for (; l <= j; ++l) s8[7] = fmaf(rf[i * k + l], xf[l * k + j], s8[7]);
+      const float t = ((s8[0] + s8[1]) + (s8[2] + s8[3])) + ((s8[4] + s8[5]) + (s8[6] + s8[7]));
+      xf[i * k + j] = -t * rinv[i];
     }
   }
-  if (lane == 0) X[j * k + j] = 1.0 / R[j * k + j];
-  __syncwarp();
-  for (int i = j - 1; i >= 0; --i) {
-    double s = 0.0;
-    for (int l = i + 1 + lane; l <= j; l += 32) s = fma(R[i * k + l], X[l * k + j], s);
-#pragma unroll
-    for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
-    if (lane == 0) X[i * k + j] = -s / R[i * k + i];
-    __syncwarp();
+  __syncthreads();
+  const float unscale = ldexpf(1.0f, -e2);
+  for (int e = tid; e < k * k; e += nt) {
+    const int i = e / k, j = e - i * k;
+    Xf[e] = (j >= i) ? xf[e] * unscale : 0.0f;
   }
-  for (int i = lane; i <= j; i += 32) Xf[i * k + j] = static_cast<float>(X[i * k + j]);
 }
 
 // --------------------------------------------------------------- Jacobi FP32
+// One pair of a round: rows/columns p < q rotated by (c, s).
+struct __align__(16) JPair {
+  int p, q;
+  float c, s;
+};
+
+// The 2 x 2 block of J^T A J at pair rows (c, s) and pair columns
+// (c2, s2) from the old block m: rows first (new p = c p - s q,
+// new q = s p + c q), then columns the same way.  The products are rounded
+// separately so that every caller gets the same bits.
+__device__ __forceinline__ void jac_block(float m00, float m01, float m10, float m11, float c, float s, float c2,
+                                          float s2, float& n00, float& n01, float& n10, float& n11) {
+  const float l00 = __fmaf_rn(-s, m10, __fmul_rn(c, m00));
+  const float l01 = __fmaf_rn(-s, m11, __fmul_rn(c, m01));
+  const float l10 = __fmaf_rn(s, m00, __fmul_rn(c, m10));
+  const float l11 = __fmaf_rn(s, m01, __fmul_rn(c, m11));
+  n00 = __fmaf_rn(-s2, l01, __fmul_rn(c2, l00));
+  n01 = __fmaf_rn(s2, l00, __fmul_rn(c2, l01));
+  n10 = __fmaf_rn(-s2, l11, __fmul_rn(c2, l10));
+  n11 = __fmaf_rn(s2, l10, __fmul_rn(c2, l11));
+}
+
+// Element (x, y) of J^T A J where x is side sx of pair P1 and y side sy of
+// pair P2 (P1 == P2 allowed: the rotated pair's off-diagonal is exactly 0).
+__device__ __forceinline__ float jac_elem(const float* A, int ld, const JPair& P1, int sx, const JPair& P2, int sy,
+                                          bool same) {
+  float n00, n01, n10, n11;
+  jac_block(A[P1.p * ld + P2.p], A[P1.p * ld + P2.q], A[P1.q * ld + P2.p], A[P1.q * ld + P2.q], P1.c, P1.s, P2.c,
+            P2.s, n00, n01, n10, n11);
+  if (same && sx != sy && P1.s != 0.0f) return 0.0f;
+  return sx ? (sy ? n11 : n10) : (sy ? n01 : n00);
+}
+
+// Rotation annihilating a_pq of the 2 x 2 block [[app, apq], [apq, aqq]]
+// (t = tan of the angle, the smaller root); skipped (c = 1, s = 0) when
+// |a_pq| <= 2^-23 sqrt(|a_pp a_qq|).  c = 1/sqrt(1 + t^2) and s = t c keep
+// c^2 + s^2 = 1 to rounding whatever the accuracy of t.
+__device__ __forceinline__ bool jac_rot(float app, float aqq, float apq, float& c, float& s) {
+  c = 1.0f;
+  s = 0.0f;
+  if (!(fabsf(apq) > 1.1920929e-7f * sqrtf(fabsf(app * aqq))) || !(fabsf(apq) > 1e-30f)) return false;
+  const float tau = __fdividef(aqq - app, 2.0f * apq);
+  const float t = __fdividef(tau >= 0.0f ? 1.0f : -1.0f, fabsf(tau) + sqrtf(fmaf(tau, tau, 1.0f)));
+  c = rsqrtf(fmaf(t, t, 1.0f));
+  s = t * c;
+  return true;
+}
+
 // Eigendecomposition of the symmetric k x k matrix whose upper triangle is
-// in G (FP64): A = G / max diag in FP32, V = I, then sweeps of the parallel
-// cyclic Jacobi method until no rotation is needed (or 30 sweeps).  Writes
-// V (k x k FP32, columns = eigenvectors).  Matrices live in shared memory
-// when they fit, else in `scratch` (2 * kp * kp floats, kp = k rounded up to
-// even).
+// in G (FP64): A = sigma G in FP32 (sigma a power of two near 1 / max diag),
+// V = I, then sweeps of the parallel cyclic Jacobi method (circle-method
+// pairing: kp - 1 rounds of kp / 2 disjoint pairs, position 0 fixed, the
+// others turn) until a sweep applies no rotation (at most 40 sweeps).
+// Writes V (k x k FP32, columns = eigenvectors).
+//   One barrier per round: every thread forms 2 x 2 blocks of J^T A J for
+//   pair blocks (t, u), u >= t, into the second buffer (each block also to
+//   its mirror, so A stays exactly symmetric) and rotates column pairs of V
+//   (kept transposed, float4 rows); threads t < kp/2 also form the three
+//   entries of round r+1's pair t from the same old A and build its
+//   rotation into the other parameter buffer.  last_rot holds the latest
+//   sweep that applies a rotation; sweep s ends the loop when last_rot < s.
+// Shared layout: two JPair[kp/2] buffers, two {pair, side}[kp] index maps,
+// then A, its second buffer (kp (kp + 1) floats each, leading dimension
+// kp + 1) and V^T (kp x ldv, ldv = kp rounded up to 4); the matrices move to
+// `scratch` when they do not fit.
+template <bool SMEM>
 __global__ void __launch_bounds__(1024) jacobi_kernel(int k, const double* __restrict__ G, float* __restrict__ Vout,
-                                                     float* scratch, int in_smem) {
-  extern __shared__ float smf[];
+                                                     float* scratch) {
+  extern __shared__ __align__(16) int smi[];
   const int kp = k + (k & 1);
-  float* A = in_smem ? smf : scratch;
-  float* V = A + kp * kp;
-  __shared__ int pp[512], qq[512];
-  __shared__ float cc[512], ss[512];
-  __shared__ int rotated;
+  const int half = kp / 2, n1 = kp - 1;
+  const int ld = kp + 1, ldv = (kp + 3) & ~3;
+  JPair* pairs = reinterpret_cast<JPair*>(smi);  // [2][half]
+  int* tmap = smi + 8 * kp;                      // [2][kp]: pair of index
+  int* smap = tmap + 2 * kp;                     // [2][kp]: side of index
+  float* A = SMEM ? reinterpret_cast<float*>(smap + 2 * kp) : scratch;
+  float* B = A + kp * ld;
+  float* Vt = B + kp * ld;
+  __shared__ int last_rot;
+  __shared__ double red[32];
   __shared__ double dmax;
   const int tid = threadIdx.x, nt = blockDim.x;
-  if (tid == 0) {
-    double mx = 0.0;
-    for (int i = 0; i < k; ++i) mx = fmax(mx, fabs(G[i * k + i]));
-    dmax = mx > 0.0 ? mx : 1.0;
-  }
+  const int lane = tid & 31, warp = tid >> 5, nw = nt >> 5;
+  diag_max(k, G, red, &dmax);
+  if (tid == 0) last_rot = -1;
   __syncthreads();
+  const double sigma = ldexp(1.0, -((dmax > 0.0) ? ilogb(dmax) : 0));
   for (int e = tid; e < kp * kp; e += nt) {
     const int i = e / kp, j = e - i * kp;
     float v = 0.0f;
-    if (i < k && j < k) v = static_cast<float>(G[min(i, j) * k + max(i, j)] / dmax);
-    A[e] = v;
-    V[e] = (i == j) ? 1.0f : 0.0f;
+    if (i < k && j < k) v = static_cast<float>(G[min(i, j) * k + max(i, j)] * sigma);
+    A[i * ld + j] = v;
+  }
+  for (int e = tid; e < kp * ldv; e += nt) {
+    const int i = e / ldv, j = e - i * ldv;
+    Vt[e] = (i == j) ? 1.0f : 0.0f;
+  }
+  // pairing of round 0 and, per rotation thread, its running positions
+  int pa = 0, pb = 0;
+  if (tid < half) {
+    pa = (tid == 0) ? 0 : tid;                   // ((0 + i - 1) mod n1) + 1
+    pb = ((n1 - 1 - tid) % n1 + n1) % n1 + 1;    // ((0 - 1 - i) mod n1) + 1
   }
   __syncthreads();
-  const int half = kp / 2;
-  for (int sweep = 0; sweep < 30; ++sweep) {
-    if (tid == 0) rotated = 0;
-    __syncthreads();
-    for (int r = 0; r < kp - 1; ++r) {
-      // circle method: position 0 fixed, the others rotate by r
-      for (int i = tid; i < half; i += nt) {
-        const int a = (i == 0) ? 0 : ((r + i - 1) % (kp - 1)) + 1;
-        const int bpos = kp - 1 - i;
-        const int b = ((r + bpos - 1) % (kp - 1)) + 1;
-        const int p = min(a, b), q = max(a, b);
-        const float app = A[p * kp + p], aqq = A[q * kp + q], apq = A[p * kp + q];
-        float c = 1.0f, s = 0.0f;
-        if (fabsf(apq) > 1e-7f * sqrtf(fabsf(app * aqq)) && fabsf(apq) > 1e-30f) {
-          const float tau = (aqq - app) / (2.0f * apq);
-          const float t = (tau >= 0.0f ? 1.0f : -1.0f) / (fabsf(tau) + sqrtf(1.0f + tau * tau));
-          c = rsqrtf(1.0f + t * t);
-          s = t * c;
-          rotated = 1;
-        }
-        pp[i] = p;
-        qq[i] = q;
-        cc[i] = c;
-        ss[i] = s;
-      }
-      __syncthreads();
-      // rows p, q <- J^T A
-      for (int e = tid; e < half * kp; e += nt) {
-        const int i = e / kp, j = e - i * kp;
-        const float c = cc[i], s = ss[i];
-        if (s != 0.0f) {
-          const int p = pp[i], q = qq[i];
-          const float x = A[p * kp + j], y = A[q * kp + j];
-          A[p * kp + j] = c * x - s * y;
-          A[q * kp + j] = s * x + c * y;
-        }
-      }
-      __syncthreads();
-      // columns p, q <- A J and V J
-      for (int e = tid; e < half * kp; e += nt) {
-        const int i = e / kp, j = e - i * kp;
-        const float c = cc[i], s = ss[i];
-        if (s != 0.0f) {
-          const int p = pp[i], q = qq[i];
-          const float x = A[j * kp + p], y = A[j * kp + q];
-          A[j * kp + p] = c * x - s * y;
-          A[j * kp + q] = s * x + c * y;
-          const float vx = V[j * kp + p], vy = V[j * kp + q];
-          V[j * kp + p] = c * vx - s * vy;
-          V[j * kp + q] = s * vx + c * vy;
+  if (tid < half) {
+    const int p = min(pa, pb), q = max(pa, pb);
+    float c, s;
+    if (jac_rot(A[p * ld + p], A[q * ld + q], A[p * ld + q], c, s)) last_rot = 0;
+    pairs[tid] = JPair{p, q, c, s};
+    tmap[p] = tid;
+    tmap[q] = tid;
+    smap[p] = 0;
+    smap[q] = 1;
+  }
+  __syncthreads();
+  int buf = 0;
+  for (int sweep = 0; sweep < 40; ++sweep) {
+    for (int r = 0; r < n1; ++r) {
+      const JPair* cur = pairs + buf * half;
+      const int* ct = tmap + buf * kp;
+      const int* cs = smap + buf * kp;
+      // J^T A J by pair blocks
+      for (int t = warp; t < half; t += nw) {
+        const JPair P1 = cur[t];
+        for (int u = t + lane; u < half; u += 32) {
+          const JPair P2 = cur[u];
+          float n00, n01, n10, n11;
+          jac_block(A[P1.p * ld + P2.p], A[P1.p * ld + P2.q], A[P1.q * ld + P2.p], A[P1.q * ld + P2.q], P1.c, P1.s,
+                    P2.c, P2.s, n00, n01, n10, n11);
+          if (u == t) {
+            if (P1.s != 0.0f) n01 = 0.0f;
+            B[P1.p * ld + P1.p] = n00;
+            B[P1.q * ld + P1.q] = n11;
+            B[P1.p * ld + P1.q] = n01;
+            B[P1.q * ld + P1.p] = n01;
+          } else {
+            B[P1.p * ld + P2.p] = n00;
+            B[P2.p * ld + P1.p] = n00;
+            B[P1.p * ld + P2.q] = n01;
+            B[P2.q * ld + P1.p] = n01;
+            B[P1.q * ld + P2.p] = n10;
+            B[P2.p * ld + P1.q] = n10;
+            B[P1.q * ld + P2.q] = n11;
+            B[P2.q * ld + P1.q] = n11;
+          }
         }
       }
+      // V <- V J on the transposed rows p, q
+      const int nv4 = ldv >> 2;
+      for (int w = tid; w < half * nv4; w += nt) {
+        const int t = w / nv4, c4 = (w - t * nv4) * 4;
+        const JPair P = cur[t];
+        float4* vp = reinterpret_cast<float4*>(Vt + P.p * ldv + c4);
+        float4* vq = reinterpret_cast<float4*>(Vt + P.q * ldv + c4);
+        const float4 x = *vp, y = *vq;
+        *vp = make_float4(__fmaf_rn(-P.s, y.x, __fmul_rn(P.c, x.x)), __fmaf_rn(-P.s, y.y, __fmul_rn(P.c, x.y)),
+                          __fmaf_rn(-P.s, y.z, __fmul_rn(P.c, x.z)), __fmaf_rn(-P.s, y.w, __fmul_rn(P.c, x.w)));
+        *vq = make_float4(__fmaf_rn(P.s, x.x, __fmul_rn(P.c, y.x)), __fmaf_rn(P.s, x.y, __fmul_rn(P.c, y.y)),
+                          __fmaf_rn(P.s, x.z, __fmul_rn(P.c, y.z)), __fmaf_rn(P.s, x.w, __fmul_rn(P.c, y.w)));
+      }
+      // rotations of the next round from the same old A
+      if (tid < half) {
+        pa = (tid == 0) ? 0 : (pa == n1 ? 1 : pa + 1);
+        pb = (pb == n1) ? 1 : pb + 1;
+        const int p = min(pa, pb), q = max(pa, pb);
+        const int tp = ct[p], tq = ct[q], sp = cs[p], sq = cs[q];
+        const JPair Pp = cur[tp], Pq = cur[tq];
+        const float app = jac_elem(A, ld, Pp, sp, Pp, sp, true);
+        const float aqq = jac_elem(A, ld, Pq, sq, Pq, sq, true);
+        const float apq = (tp <= tq) ? jac_elem(A, ld, Pp, sp, Pq, sq, tp == tq) : jac_elem(A, ld, Pq, sq, Pp, sp, false);
+        float c, s;
+        if (jac_rot(app, aqq, apq, c, s)) last_rot = (r + 1 == n1) ? sweep + 1 : sweep;
+        JPair* nxt = pairs + (buf ^ 1) * half;
+        int* nt_ = tmap + (buf ^ 1) * kp;
+        int* ns_ = smap + (buf ^ 1) * kp;
+        nxt[tid] = JPair{p, q, c, s};
+        nt_[p] = tid;
+        nt_[q] = tid;
+        ns_[p] = 0;
+        ns_[q] = 1;
+      }
       __syncthreads();
+      float* t = A;
+      A = B;
+      B = t;
+      buf ^= 1;
     }
-    if (!rotated) break;
-    __syncthreads();
+    if (last_rot < sweep) break;
   }
   for (int e = tid; e < k * k; e += nt) {
     const int i = e / k, j = e - i * k;
-    Vout[e] = V[i * kp + j];
+    Vout[e] = Vt[j * ldv + i];
   }
 }
 
@@ -308,14 +462,58 @@ __global__ void f32_to_f16_kernel(long long rows, long long cols, const float* _
   }
 }
 
+int smem_fits(size_t bytes) { return bytes <= 200 * 1024 ? 1 : 0; }
+
+// Floats of the Jacobi matrices: A and its second buffer (kp (kp + 1) each)
+// and V^T (kp x ldv).
+size_t jacobi_scratch_floats(int64_t k) {
+  const int64_t kp = k + (k & 1), ldv = (kp + 3) & ~int64_t(3);
+  return static_cast<size_t>(2 * kp * (kp + 1) + kp * ldv);
+}
+
+// One-CTA kernels: about `work` elements per barrier phase, a few per thread.
+int block_threads(int64_t work) {
+  int64_t t = (work + 31) / 32 * 32;
+  if (t < 128) t = 128;
+  if (t > 1024) t = 1024;
+  return static_cast<int>(t);
+}
+
 }  // namespace
 
 // ------------------------------------------------------------------ host API
 size_t align256(size_t x) { return (x + 255) & ~size_t(255); }
 
-size_t cholqr_small_bytes(int64_t k) {
+namespace {
+// Byte offsets of the pieces of the small scratch: FP64 Gram (k^2), the
+// Cholesky/inverse spill area (2 k^2 doubles), R^-1 in FP32 (k^2) and the
+// Jacobi spill area.
+void small_offsets(int64_t k, size_t off[5]) {
   const int64_t kp = k + (k & 1);
-  return align256(k * k * 8) * 3 + align256(k * k * 4) + align256(2 * kp * kp * 4) + align256(k * 8);
+  off[0] = 0;
+  off[1] = off[0] + align256(static_cast<size_t>(k * k) * 8);
+  off[2] = off[1] + align256(static_cast<size_t>(2 * k * k) * 8);
+  off[3] = off[2] + align256(static_cast<size_t>(k * k) * 4);
+  off[4] = off[3] + align256(jacobi_scratch_floats(k) * 4);
+}
+}  // namespace
+
+SmallWs small_ws(void* base, int64_t k) {
+  size_t off[5];
+  small_offsets(k, off);
+  uint8_t* w = static_cast<uint8_t*>(base);
+  SmallWs s;
+  s.G = reinterpret_cast<double*>(w + off[0]);
+  s.chol = reinterpret_cast<double*>(w + off[1]);
+  s.Rf = reinterpret_cast<float*>(w + off[2]);
+  s.jac = reinterpret_cast<float*>(w + off[3]);
+  return s;
+}
+
+size_t cholqr_small_bytes(int64_t k) {
+  size_t off[5];
+  small_offsets(k, off);
+  return off[4];
 }
 
 int gram_f64(int64_t m, int64_t k, const float* X, int64_t ldx, double* G, cudaStream_t st) {
@@ -323,10 +521,11 @@ int gram_f64(int64_t m, int64_t k, const float* X, int64_t ldx, double* G, cudaS
   const int t = static_cast<int>((k + 31) / 32);
   const long long tiles = static_cast<long long>(t) * (t + 1) / 2;
   const int sms = sm_count();
-  long long chunks = (4ll * sms + tiles - 1) / tiles;
+  // enough row chunks that about two CTAs per SM share the FP64 work
+  long long chunks = (2ll * sms + tiles - 1) / tiles;
   long long rows = (m + chunks - 1) / chunks;
   rows = ((rows + 31) / 32) * 32;
-  if (rows < 64) rows = 64;
+  if (rows < 32) rows = 32;
   chunks = (m + rows - 1) / rows;
   if (chunks > 65535) return SHG_ERR_UNSUPPORTED;
   dim3 grid(t, t, static_cast<unsigned>(chunks));
@@ -334,34 +533,42 @@ int gram_f64(int64_t m, int64_t k, const float* X, int64_t ldx, double* G, cudaS
   return cuda_status(cudaGetLastError());
 }
 
-int cholesky_f64(int64_t k, const double* G, double* R, double* scratch, int32_t* flags, cudaStream_t st) {
-  const size_t need = static_cast<size_t>(k) * k * sizeof(double);
-  const int in_smem = need <= 200 * 1024 ? 1 : 0;
+int chol_inv(int64_t k, const double* G, float* Rinv, double* scratch, int32_t* flags, cudaStream_t st) {
+  if (k > 1024) return SHG_ERR_UNSUPPORTED;
+  const size_t need = static_cast<size_t>(2 * k * k) * sizeof(double);
+  const int in_smem = smem_fits(need);
   const size_t smem = in_smem ? need : 0;
-  if (in_smem && cudaFuncSetAttribute(cholesky_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                      static_cast<int>(smem)) != cudaSuccess)
-    return SHG_ERR_CUDA;
-  cholesky_kernel<<<1, 1024, smem, st>>>(static_cast<int>(k), G, R, scratch, in_smem, flags);
-  return cuda_status(cudaGetLastError());
-}
-
-int tri_inv(int64_t k, const double* R, double* X, float* Xf, cudaStream_t st) {
-  const int warps_per_block = 8;
-  const int blocks = static_cast<int>((k + warps_per_block - 1) / warps_per_block);
-  tri_inv_kernel<<<blocks, 32 * warps_per_block, 0, st>>>(static_cast<int>(k), R, X, Xf);
+  const int threads = block_threads(k * k / 4);
+  if (in_smem) {
+    if (cudaFuncSetAttribute(chol_inv_kernel<true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             static_cast<int>(smem)) != cudaSuccess)
+      return SHG_ERR_CUDA;
+    chol_inv_kernel<true><<<1, threads, smem, st>>>(static_cast<int>(k), G, Rinv, scratch, flags);
+  } else {
+    chol_inv_kernel<false><<<1, threads, 0, st>>>(static_cast<int>(k), G, Rinv, scratch, flags);
+  }
   return cuda_status(cudaGetLastError());
 }
 
 int jacobi_eig(int64_t k, const double* G, float* V, float* scratch, cudaStream_t st) {
   if (k > 1024) return SHG_ERR_UNSUPPORTED;
   const int64_t kp = k + (k & 1);
-  const size_t need = static_cast<size_t>(2 * kp * kp) * sizeof(float);
-  const int in_smem = need <= 200 * 1024 ? 1 : 0;
-  const size_t smem = in_smem ? need : 0;
-  if (in_smem && cudaFuncSetAttribute(jacobi_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                      static_cast<int>(smem)) != cudaSuccess)
-    return SHG_ERR_CUDA;
-  jacobi_kernel<<<1, 1024, smem, st>>>(static_cast<int>(k), G, V, scratch, in_smem);
+  const size_t prm = static_cast<size_t>(8 * kp + 4 * kp) * sizeof(int);
+  const size_t mats = jacobi_scratch_floats(k) * sizeof(float);
+  const int in_smem = smem_fits(prm + mats);
+  const size_t smem = in_smem ? prm + mats : prm;
+  const int threads = block_threads(kp * kp / 8);
+  if (in_smem) {
+    if (cudaFuncSetAttribute(jacobi_kernel<true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             static_cast<int>(smem)) != cudaSuccess)
+      return SHG_ERR_CUDA;
+    jacobi_kernel<true><<<1, threads, smem, st>>>(static_cast<int>(k), G, V, scratch);
+  } else {
+    if (cudaFuncSetAttribute(jacobi_kernel<false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             static_cast<int>(smem)) != cudaSuccess)
+      return SHG_ERR_CUDA;
+    jacobi_kernel<false><<<1, threads, smem, st>>>(static_cast<int>(k), G, V, scratch);
+  }
   return cuda_status(cudaGetLastError());
 }
 
@@ -388,26 +595,16 @@ int to_f16(int64_t rows, int64_t cols, const float* x, int64_t ldx, uint16_t* y,
 // small = cholqr_small_bytes(k).
 int cholqr2(int64_t m, int64_t k, float* X, int64_t ldx, float* T, int64_t ldt, void* small, int32_t* flags,
             cudaStream_t st) {
-  uint8_t* w = static_cast<uint8_t*>(small);
-  double* G = reinterpret_cast<double*>(w);
-  w += align256(k * k * 8);
-  double* R = reinterpret_cast<double*>(w);
-  w += align256(k * k * 8);
-  double* Ri = reinterpret_cast<double*>(w);
-  w += align256(k * k * 8);
-  float* Rf = reinterpret_cast<float*>(w);
-  w += align256(k * k * 4);
-  double* chol_scratch = reinterpret_cast<double*>(w);  // k*k doubles fit in the 2*kp*kp floats region
+  const SmallWs w = small_ws(small, k);
   int rc;
   float* src = X;
   int64_t lds = ldx;
   for (int pass = 0; pass < 2; ++pass) {
     float* dst = (pass == 0) ? T : X;
     const int64_t ldd = (pass == 0) ? ldt : ldx;
-    if ((rc = gram_f64(m, k, src, lds, G, st))) return rc;
-    if ((rc = cholesky_f64(k, G, R, chol_scratch, flags, st))) return rc;
-    if ((rc = tri_inv(k, R, Ri, Rf, st))) return rc;
-    if ((rc = simt_gemm(m, k, k, src, lds, 0, Rf, k, 0, dst, ldd, 0, 1, 0, 0, 0, st))) return rc;
+    if ((rc = gram_f64(m, k, src, lds, w.G, st))) return rc;
+    if ((rc = chol_inv(k, w.G, w.Rf, w.chol, flags, st))) return rc;
+    if ((rc = simt_gemm(m, k, k, src, lds, 0, w.Rf, k, 0, dst, ldd, 0, 1, 0, 0, 0, st))) return rc;
     src = dst;
     lds = ldd;
   }

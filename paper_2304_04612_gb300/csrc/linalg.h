@@ -9,10 +9,18 @@ namespace shg {
 size_t align256(size_t x);
 // Bytes of the small (k-sized) scratch one CholeskyQR2 / eigensolve needs.
 size_t cholqr_small_bytes(int64_t k);
+// Pieces of that scratch (base must be 256-byte aligned).
+struct SmallWs {
+  double* G;     // k x k FP64 Gram matrix (upper triangle)
+  double* chol;  // 2 k^2 doubles: Cholesky factor and inverse when not in shared memory
+  float* Rf;     // k x k FP32 R^-1
+  float* jac;    // Jacobi matrices when not in shared memory
+};
+SmallWs small_ws(void* base, int64_t k);
 
 int gram_f64(int64_t m, int64_t k, const float* X, int64_t ldx, double* G, cudaStream_t st);
-int cholesky_f64(int64_t k, const double* G, double* R, double* scratch, int32_t* flags, cudaStream_t st);
-int tri_inv(int64_t k, const double* R, double* X, float* Xf, cudaStream_t st);
+// Rinv = FP32(R^-1) with G = R^T R (FP64, upper Cholesky).
+int chol_inv(int64_t k, const double* G, float* Rinv, double* scratch, int32_t* flags, cudaStream_t st);
 int jacobi_eig(int64_t k, const double* G, float* V, float* scratch, cudaStream_t st);
 int rayleigh_sort(int64_t k, int64_t p, const double* G, const float* V, double* lam, float* S, float* Up,
                   float* Ups, cudaStream_t st);
