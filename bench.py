@@ -34,6 +34,25 @@ METRIC = "RSVD/RP-HOSVD time & SHGEMM TFLOP/s vs FP32 path, same GB300, matched 
 KS = (64, 128, 256, 512)
 M = N = 16384
 
+# DRAM bytes (dram__bytes_read.sum + dram__bytes_write.sum) of one SHGEMM-FP16
+# launch at m = n = 16384, from the ncu captures summarised in
+# profiles/tc_gemm_kernel_shgemm_f16.md, with the SHA-256 of the kernel
+# sources they were taken on; reported only while the sources are unchanged.
+TRAFFIC = {
+    "sources": ["paper_2304_04612_gb300/csrc/shgemm_tc.cu", "paper_2304_04612_gb300/csrc/ptx.cuh"],
+    "sha256": None,
+    "bytes_per_launch": {},
+}
+
+
+def kernel_sha() -> str:
+    import hashlib
+    h = hashlib.sha256()
+    for f in TRAFFIC["sources"]:
+        with open(os.path.join(ROOT, f), "rb") as fh:
+            h.update(fh.read())
+    return h.hexdigest()
+
 
 def peaks():
     try:
@@ -242,13 +261,28 @@ def main():
         roof[k] = {"ms": per_k_ms[k], "tflops_2mnk": 2.0 * M * N * k / t / 1e12,
                    "achieved_gbs": byts / t / 1e9, "tensor_tflops_4mnk": fl / t / 1e12,
                    "bound": "hbm" if byts / bw >= fl / tc else "tensor", "frac_of_floor": floor / t}
-    k0 = 256
+    # the dominant launch: the largest share of the step
+    k0 = max(KS, key=lambda k: per_k_ms[k])
     b0 = 4.0 * M * N + 2.0 * N * k0 + 4.0 * M * k0
-    roofline = {"bound": "hbm", "achieved": b0 / (per_k_ms[k0] * 1e-3) / 1e9, "peak": pk["hbm_gbs"],
-                "unit": "GB/s", "frac": b0 / (per_k_ms[k0] * 1e-3) / 1e9 / pk["hbm_gbs"], "traffic": None,
-                "kernel": "tc_gemm_kernel<K-major A, FP16 Omega> (SHGEMM-FP16), m=n=16384, k=256",
-                "peak_source": "MEASURED_PEAKS.json hbm_gbs (burst copy)" if "_fallback" not in pk else "fallback",
-                "per_k": {str(k): roof[k] for k in KS}}
+    f0 = 4.0 * M * N * k0
+    t0s = per_k_ms[k0] * 1e-3
+    traffic = None
+    if TRAFFIC["sha256"] is not None and kernel_sha() == TRAFFIC["sha256"]:
+        traffic = TRAFFIC["bytes_per_launch"].get(str(k0))
+    src = "MEASURED_PEAKS.json" if "_fallback" not in pk else "fallback"
+    if roof[k0]["bound"] == "hbm":
+        roofline = {"bound": "hbm", "achieved": b0 / t0s / 1e9, "peak": pk["hbm_gbs"], "unit": "GB/s",
+                    "frac": b0 / t0s / 1e9 / pk["hbm_gbs"], "traffic": traffic,
+                    "peak_source": f"{src} hbm_gbs (burst copy)"}
+    else:
+        roofline = {"bound": "tensor", "achieved": f0 / t0s / 1e12, "peak": pk["bf16_tflops"],
+                    "unit": "TFLOP/s", "frac": f0 / t0s / 1e12 / pk["bf16_tflops"], "traffic": traffic,
+                    "peak_source": f"{src} bf16_tflops (burst; FP16 and BF16 dense rates are equal)"}
+    roofline.update({
+        "kernel": f"tc_gemm_kernel<K-major A, FP16 Omega> (SHGEMM-FP16), m=n={M}, k={k0}",
+        "share_of_step": per_k_ms[k0] / sum(per_k_ms.values()),
+        "algorithmic": {"bytes": b0, "tensor_flops_4mnk": f0},
+        "per_k": {str(k): roof[k] for k in KS}})
 
     line = {"metric": METRIC, "value": value, "unit": "TFLOP/s", "n_gpus": ws, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": ms_step, "higher_is_better": True,

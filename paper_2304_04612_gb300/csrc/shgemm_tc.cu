@@ -72,6 +72,7 @@ struct TcArgs {
   uint32_t tmem_cols, b_bytes;
   int kc;
   int prefetch;  // L2 prefetch group size in units (0: off)
+  int groups;    // CTA groups, one per run of N tiles (divides n_tiles and gridDim.x)
   unsigned long long wait_ns;
   int drop_commit;
 };
@@ -215,6 +216,20 @@ __device__ __forceinline__ void split_inplace_b(uint8_t* tile, int G, int t, flo
 struct UnitPos {
   int nt, mt, kb;
 };
+
+// Units of this CTA.  The grid is split into `groups` equal groups, group g
+// owning N tiles [g, g + 1) x n_tiles / groups; the i-th CTAs of all groups
+// cover the same (M tile, K block) range, so the groups read the same A
+// tiles at about the same time and all but the first read come from L2:
+// A streams from HBM about once for any number of N tiles.
+__device__ __forceinline__ void cta_range(const TcArgs& a, long long& u0, long long& u1) {
+  const int G = a.groups;
+  const int g = static_cast<int>(blockIdx.x) % G, i = static_cast<int>(blockIdx.x) / G;
+  const int C = static_cast<int>(gridDim.x) / G;
+  const long long per = a.units / G;
+  u0 = g * per + static_cast<long long>(i) * per / C;
+  u1 = g * per + static_cast<long long>(i + 1) * per / C;
+}
 __device__ __forceinline__ UnitPos decode(long long u, const TcArgs& a) {
   const long long per_n = static_cast<long long>(a.m_tiles) * a.kblocks;
   UnitPos p;
@@ -295,8 +310,8 @@ __global__ void __launch_bounds__(kThreads, 1)
   const uint32_t tm_l = tmem_base + 2 * N;
   const uint32_t tm_a = tmem_base + (2 + kNumL) * N;
 
-  const long long u0 = static_cast<long long>(blockIdx.x) * args.units / gridDim.x;
-  const long long u1 = static_cast<long long>(blockIdx.x + 1) * args.units / gridDim.x;
+  long long u0, u1;
+  cta_range(args, u0, u1);
   const uint64_t lim = args.wait_ns;
   long long issued_a = 0, issued_b = 0;
 
@@ -754,10 +769,14 @@ int tc_gemm(int amaj, int bmode, int pieces, int64_t M, int64_t N, int64_t S_k, 
   // stream-K grid: at most one CTA per SM, at least one unit per CTA
   const int sms = sm_count();
   if (sms <= 0) return SHG_ERR_CUDA;
-  const int grid = static_cast<int>(std::min<long long>(sms, a.units));
+  // one CTA group per N tile when there are few N tiles (see cta_range)
+  a.groups = (a.n_tiles > 1 && a.n_tiles <= 8 && env_int("SHG_NGROUPS", 1) != 0) ? a.n_tiles : 1;
+  const long long per_group = a.units / a.groups;
+  const int grid = static_cast<int>(std::min<long long>(sms / a.groups, per_group)) * a.groups;
+  const int per_cta = grid / a.groups;
   bool split = false;
-  for (int c = 1; c < grid && !split; ++c)
-    if ((static_cast<long long>(c) * a.units / grid) % a.kblocks != 0) split = true;
+  for (int c = 1; c < per_cta && !split; ++c)
+    if ((static_cast<long long>(c) * per_group / per_cta) % a.kblocks != 0) split = true;
   if (split && !accumulate) {
     if (cudaMemset2DAsync(C, ldc * sizeof(float), 0, N * sizeof(float), M, stream) != cudaSuccess)
       return SHG_ERR_CUDA;
