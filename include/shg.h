@@ -142,6 +142,29 @@ int shg_cholqr2(int64_t m, int64_t k, float* X, int64_t ldx,
                 void* workspace, size_t ws_bytes, int32_t* d_flags, void* stream);
 
 /*
+ * shg_cholqr2 without a caller workspace: the scratch is a fixed 32 MiB
+ * array compiled into the library, so the call allocates no device memory.
+ * It exists for callers that may not allocate while they run (a serving
+ * loop whose device memory all belongs to its own pool, a latency-critical
+ * path where an allocation could wait on other device work).  The paper has
+ * no counterpart; its computation is exactly that of shg_cholqr2.
+ *   Limit: the bytes shg_cholqr2_workspace_size(m, k) reports, plus 256,
+ *   at most 32 MiB (m k up to about 8.3e6 at k = 64); larger sizes return
+ *   SHG_ERR_WORKSPACE before any launch.
+ *   d_flags: a device word that must be zero on entry (as for shg_cholqr2),
+ *   or NULL, in which case a word inside the static scratch is cleared on
+ *   the stream and the device flags are not reported.  Everything else the
+ *   call needs zeroed it clears itself on the stream.
+ *   The scratch address is resolved on the first call on each device, with
+ *   that device current: make that first call before any stream capture on
+ *   the device begins.
+ *   One scratch serves every call on a device: calls that overlap in time
+ *   (different streams, or different host threads without ordering) race on
+ *   it and give wrong results.  Order them on one stream or synchronise.
+ */
+int shg_cholqr2_static(int64_t m, int64_t k, float* X, int64_t ldx, int32_t* d_flags, void* stream);
+
+/*
  * Randomized SVD, Algorithm 1 with the power scheme of Sec. 2.1:
  *   Y = A Omega; Q = orth(Y); q times { Z = orth(A^T fp16(Q)); Q = orth(A fp16(Z)) };
  *   B = Q^T A; U' S V'^T = tSVD(B, rank); U = Q U'.

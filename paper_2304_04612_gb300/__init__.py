@@ -14,6 +14,7 @@ shgemm_project     Y = op(A) Omega by SHGEMM (or the BF16 / FP32 SIMT variants)
 shg_gemm_split3    FP32-accurate op(A) B of two FP32 matrices (TCEC split)
 shg_sgemm          plain FP32 SIMT GEMM (the single-precision baseline)
 shg_cholqr2        CholeskyQR2 orthonormalisation (in place)
+shg_cholqr2_static the same on the library's static scratch (allocates nothing)
 shg_rsvd           randomized SVD (Algorithm 1, power scheme of Sec. 2.1)
 shg_rp_hosvd       random-projection HOSVD of a 3-way tensor (Algorithm 2)
 """
@@ -163,6 +164,19 @@ def shg_cholqr2(X: torch.Tensor, workspace: torch.Tensor | None = None, flags: t
     _check(lib.shg_cholqr2(m, k, _ptr(X), ldx, _ptr(ws), ws.numel(), _ptr(fl), _stream(stream)), "shg_cholqr2")
     if check:
         check_flags(fl, "shg_cholqr2")
+    return X
+
+
+def shg_cholqr2_static(X: torch.Tensor, flags: torch.Tensor | None = None, check: bool = True,
+                       stream=None) -> torch.Tensor:
+    """shg_cholqr2 on the library's static scratch (no workspace argument)."""
+    ldx = _mat(X, "X", (torch.float32,))
+    m, k = X.shape
+    lib = _lib.load()
+    _check(lib.shg_cholqr2_static(m, k, _ptr(X), ldx, _ptr(flags) if flags is not None else None,
+                                  _stream(stream)), "shg_cholqr2_static")
+    if check and flags is not None:
+        check_flags(flags, "shg_cholqr2_static")
     return X
 
 
