@@ -35,13 +35,13 @@ KS = (64, 128, 256, 512)
 M = N = 16384
 
 # DRAM bytes (dram__bytes_read.sum + dram__bytes_write.sum) of one SHGEMM-FP16
-# launch at m = n = 16384, from the ncu captures summarised in
-# profiles/tc_gemm_kernel_shgemm_f16.md, with the SHA-256 of the kernel
-# sources they were taken on; reported only while the sources are unchanged.
+# launch at m = n = 16384, from one-pass ncu captures of
+# `bench.py --case 16384 K`, with the SHA-256 of the kernel sources they were
+# taken on; reported only while the sources are unchanged.
 TRAFFIC = {
     "sources": ["paper_2304_04612_gb300/csrc/shgemm_tc.cu", "paper_2304_04612_gb300/csrc/ptx.cuh"],
-    "sha256": None,
-    "bytes_per_launch": {},
+    "sha256": "412f94c27e4c3000e065702fe7e41ed468a367dae2d4128d40e2b6be6c49aa0b",
+    "bytes_per_launch": {"64": 1094783488, "128": 1111319552, "256": 1122886144, "512": 1149646336},
 }
 
 

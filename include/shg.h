@@ -106,8 +106,8 @@ int shgemm_project(int64_t m, int64_t n, int64_t k,
 /*
  * FP32-accurate product C (+)= op(A) * B of two FP32 matrices by the
  * TCEC split (Eq. tcec-5): hiA*hiB + (loA*hiB + hiA*loB) * 2^-11 on FP16
- * tensor cores.  Used for B = Q^T A of Algorithm 1 (line 3) and the core
- * contraction of Algorithm 2 (line 5).
+ * tensor cores.  Used for B = Q^T A of Algorithm 1 and the first core
+ * contraction of Algorithm 2.
  *   trans_a = 0: A m x kk (lda >= kk); trans_a = 1: A kk x m (lda >= m).
  *   B: kk x n (ldb >= n, ldb % 4 == 0).  C: m x n (ldc >= n).
  *   accumulate = 0: C = op(A) B; 1: C += op(A) B.
@@ -131,7 +131,7 @@ int shg_sgemm(int64_t m, int64_t n, int64_t kk,
               float* C, int64_t ldc, int accumulate, void* stream);
 
 /*
- * CholeskyQR2 (orthonormal basis of Algorithm 1 line 2 / Algorithm 2 line 4):
+ * CholeskyQR2 (the orthonormal basis of Algorithms 1 and 2):
  * twice { G = X^T X (FP64 accumulation), G = R^T R (FP64 Cholesky),
  * X <- X R^-1 }.  X: m x k FP32 (ldx >= k), overwritten by Q with
  * Q^T Q = I and X_in = Q R, diag(R) > 0.  k <= m, k <= 1024.

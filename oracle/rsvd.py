@@ -52,16 +52,16 @@ def rsvd(A32: np.ndarray, omega: np.ndarray, p: int, q: int = 0, fp16_basis: boo
     A = np.asarray(A32, dtype=np.float32).astype(np.float64)
     om = np.asarray(omega)
     W = f16_to_f64(om) if om.dtype in (np.float16, np.uint16) else om.astype(np.float64)
-    Y = A @ W                                    # line 1
-    Q, _ = qr_pos(Y)                             # line 2
+    Y = A @ W                                    # projection
+    Q, _ = qr_pos(Y)                             # orthonormal basis
     for _ in range(q):                           # power scheme, Sec. 2.1
         Qb = round_rn(Q, FP16) if fp16_basis else Q
         Z, _ = qr_pos(A.T @ Qb)
         Zb = round_rn(Z, FP16) if fp16_basis else Z
         Q, _ = qr_pos(A @ Zb)
-    B = Q.T @ A                                  # line 3
-    Ub, S, Vt = np.linalg.svd(B, full_matrices=False)   # line 4
-    U = Q @ Ub[:, :p]                            # line 5
+    B = Q.T @ A                                  # B = Q^T A
+    Ub, S, Vt = np.linalg.svd(B, full_matrices=False)   # small SVD of B
+    U = Q @ Ub[:, :p]                            # lift the left vectors
     V = Vt[:p].T
     U, V = canonical_signs(U, V)
     S = S[:p]

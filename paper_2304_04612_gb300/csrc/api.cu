@@ -209,9 +209,9 @@ int shg_rsvd(int64_t m, int64_t n, int64_t rank, int64_t oversampling, int power
   const int64_t ldk = round8(k);
   const bool tc = tc_variant(variant);
 
-  // line 1: Y = A Omega
+  // projection: Y = A Omega
   SHG_TRY(shgemm_project(m, n, k, A, lda, 0, omega, ldo, Y, ldk, variant, d_flags, stream));
-  // line 2: Q = orth(Y)
+  // orthonormal basis: Q = orth(Y)
   SHG_TRY(cholqr2(m, k, Y, ldk, T, ldk, small, d_flags, st));
   // power scheme (Sec. 2.1): the FP16-rounded basis is the next test matrix
   for (int it = 0; it < power_iters; ++it) {
@@ -230,18 +230,18 @@ int shg_rsvd(int64_t m, int64_t n, int64_t rank, int64_t oversampling, int power
     }
     SHG_TRY(cholqr2(m, k, Y, ldk, T, ldk, small, d_flags, st));
   }
-  // line 3: B^T = A^T Q (FP32-accurate)
+  // B^T = A^T Q (FP32-accurate)
   if (tc)
     SHG_TRY(tc_gemm(A_MNMAJ, B_SPLIT, 2, n, k, m, 1, A, lda, 0, Y, ldk, Bt, ldk, 0, d_flags, st));
   else
     SHG_TRY(simt_gemm(n, k, m, A, lda, 1, Y, ldk, 0, Bt, ldk, 0, 1, 0, 0, 0, st));
-  // line 4: tSVD(B) through the eigendecomposition of B B^T = Bt^T Bt
+  // small SVD of B through the eigendecomposition of B B^T = Bt^T Bt
   const SmallWs sw = small_ws(small, k);
   double* G = sw.G;
   SHG_TRY(gram_f64(n, k, Bt, ldk, G, st));
   SHG_TRY(jacobi_eig(k, G, Vk, sw.jac, st));
   SHG_TRY(rayleigh_sort(k, rank, G, Vk, lam, S, Up, Ups, st));
-  // line 5: U = Q U'; V = B^T U' Sigma^-1
+  // lift: U = Q U'; V = B^T U' Sigma^-1
   SHG_TRY(simt_gemm(m, rank, k, Y, ldk, 0, Up, rank, 0, U, rank, 0, 1, 0, 0, 0, st));
   SHG_TRY(simt_gemm(n, rank, k, Bt, ldk, 0, Ups, rank, 0, V, rank, 0, 1, 0, 0, 0, st));
   if (Q_out) {
@@ -288,7 +288,7 @@ int shg_rp_hosvd(int ndim, const int64_t* dims, const int64_t* ranks, const floa
   const int64_t J0 = ranks[0], J1 = ranks[1], J2 = ranks[2];
   const bool tc = (variant == SHG_SPLIT_F16);
 
-  // lines 1-3: W_i = X_(i) Omega_(i), Q_i = orth(W_i)
+  // per mode: W_i = X_(i) Omega_(i), Q_i = orth(W_i)
   if (tc) {
     SHG_TRY(tc_gemm(A_KMAJ, B_F16, 2, I0, J0, I1 * I2, 1, X, I1 * I2, 0, omegas[0], ldo[0], W[0], L.ld[0], 0, d_flags, st));
     SHG_TRY(tc_gemm(A_KMAJ, B_F16, 2, I1, J1, I2, I0, X, I2, I1 * I2, omegas[1], ldo[1], W[1], L.ld[1], 0, d_flags,
@@ -307,7 +307,7 @@ int shg_rp_hosvd(int ndim, const int64_t* dims, const int64_t* ranks, const floa
                           cudaMemcpyDeviceToDevice, st) != cudaSuccess)
       return SHG_ERR_CUDA;
   }
-  // line 5: core = X x_2 Q_2^T x_1 Q_1^T x_0 Q_0^T
+  // core = X x_2 Q_2^T x_1 Q_1^T x_0 Q_0^T
   if (tc)
     SHG_TRY(tc_gemm(A_KMAJ, B_SPLIT, 2, I0 * I1, J2, I2, 1, X, I2, 0, W[2], L.ld[2], T1, L.ld[2], 0, d_flags, st));
   else

@@ -1,13 +1,12 @@
 // k x k linear algebra of the randomized factorizations (k = rank +
-// oversampling, small): FP64 Gram matrices, FP64 Cholesky with the inverse
-// of its factor, and the eigendecomposition of B B^T for the small SVD of
-// Algorithm 1 (line 4).
+// oversampling, small): FP64 Gram matrices, Cholesky factors and their
+// inverses, and the eigendecomposition of B B^T for the small SVD of
+// Algorithm 1.
 //
-// CholeskyQR2 replaces the QR factorization of Algorithm 1 (line 2) and
-// Algorithm 2 (line 4): twice { G = X^T X, G = R^T R, X <- X R^-1 }.  The
-// Gram matrix is accumulated in FP64 from exact FP32 x FP32 products, the
-// Cholesky factor and its inverse are FP64, X R^-1 is an FP32 GEMM with R^-1
-// rounded to FP32.
+// CholeskyQR2 replaces the QR factorization of Algorithms 1 and 2:
+// twice { G = X^T X, G = R^T R, X <- X R^-1 }.  The Gram matrix is
+// accumulated in FP64 from exact FP32 x FP32 products and factored in FP64;
+// R^-1 is formed in FP32 from the FP64 factor and X R^-1 is an FP32 GEMM.
 //
 // The eigensolver is a parallel cyclic Jacobi method (round-robin pairing)
 // in FP32 on the scaled Gram matrix; eigenvalues are then refined as FP64

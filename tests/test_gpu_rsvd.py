@@ -137,6 +137,6 @@ def test_rp_hosvd_small(shg):
         rec = np.einsum("abc,ia,jb,kc->ijk", core, facs[0], facs[1], facs[2])
         err = np.linalg.norm(A.astype(np.float64) - rec) / np.linalg.norm(A)
         assert abs(err - ref["err"]) <= 0.01 * ref["err"], (variant, err, ref["err"])
-        # the core is the projection of A on the returned factors (line 5)
+        # the core is the projection of A on the returned factors (last step of Algorithm 2)
         proj = np.einsum("ijk,ia,jb,kc->abc", A.astype(np.float64), facs[0], facs[1], facs[2])
         assert np.linalg.norm(core - proj) / np.linalg.norm(proj) < 1e-5
