@@ -207,6 +207,64 @@ int shg_rp_hosvd(int ndim, const int64_t* dims, const int64_t* ranks, const floa
                  const uint16_t* const* omegas, const int64_t* omega_lds, float* core, float* const* factors,
                  void* workspace, size_t ws_bytes, int variant, int32_t* d_flags, void* stream);
 
+/*
+ * alpha_Y of FP16 (Sec. 3.2): E[RN_fp16(g)^2] for g ~ N(0,1), the variance
+ * of an FP16-rounded standard Gaussian entry, computed on the host from its
+ * definition (each finite FP16 value weighted by the normal probability of
+ * its round-to-nearest interval).  About 1 - 4.4e-8.
+ */
+double shg_alpha_y_f16(void);
+
+/*
+ * y = RN_fp16(x) element-wise (round to nearest even, subnormals kept), the
+ * rounding of Sec. 3.1 applied to an FP32 matrix: rows x cols, x with leading
+ * dimension ldx, y (FP16 bits) with ldy.  Used to round a trained FP32 sketch
+ * to the FP16 test matrix of the projection.
+ */
+int shg_round_f16(int64_t rows, int64_t cols, const float* x, int64_t ldx,
+                  uint16_t* y, int64_t ldy, void* stream);
+
+/*
+ * A14. A-posteriori residual estimate of a basis Q of the range of A
+ * (Theorems 1 and 3: for G with i.i.d. entries of variance alpha,
+ * E ||S G||_F^2 = alpha t ||S||_F^2):
+ *   G: n x t probes, element (r, c) = RN_fp16 of normal r*t + c of the
+ *      Philox stream (seed, offset) exactly as shg_gaussian_f16 generates it;
+ *   d_out[0] = est = sqrt(||(I - Q Q^T) A G||_F^2 / (alpha t)) / ||A||_F,
+ *   d_out[1] = ||(I - Q Q^T) A G||_F^2, d_out[2] = ||A||_F^2 (device doubles).
+ * A: m x n FP32 (lda >= n, lda % 4 == 0, 16-byte aligned); Q: m x k FP32
+ * with orthonormal columns (ldq >= k), k <= m.  alpha <= 0 selects
+ * shg_alpha_y_f16().  A G is an SHGEMM product; the projection uses FP32
+ * GEMMs and FP64 sums.  Workspace from shg_residual_estimate_workspace_size.
+ * Device flags: RANGE (A outside the FP16 split range), TIMEOUT.
+ */
+int shg_residual_estimate_workspace_size(int64_t m, int64_t n, int64_t k, int64_t t, size_t* bytes);
+int shg_residual_estimate(int64_t m, int64_t n, int64_t k, int64_t t,
+                          const float* A, int64_t lda, const float* Q, int64_t ldq,
+                          uint64_t seed, uint64_t offset, double alpha, double* d_out,
+                          void* workspace, size_t ws_bytes, int32_t* d_flags, void* stream);
+
+/*
+ * A13. Loss and gradient of a sketch for the range finder of Algorithm 1
+ * (the quantity ||A - Q Q^T A||_F of Sec. 2.2, relative to ||A||_F):
+ *   Y = A fp16(Omega) (computed by the caller with shgemm_project),
+ *   Q R = Y (CholeskyQR2, diag(R) > 0),
+ *   *d_loss = 1 - ||A^T Q||_F^2 / ||A||_F^2   (device double),
+ *   want_grad != 0: d_omega (n x k FP32, ldd >= k) =
+ *       A^T [ -(2 / ||A||_F^2) (I - Q Q^T) A A^T Q R^-T ],
+ *   the gradient of the loss with respect to the FP16 values of Omega (the
+ *   gradient passed straight through to FP32 master weights).
+ * A: m x n FP32 (lda >= n, lda % 4 == 0, 16-byte aligned); Y: m x k FP32
+ * (ldy >= k); 1 <= k <= min(m, 1024).  A^T Q, A (A^T Q) and A^T dY are
+ * FP32-accurate products by the TCEC split (Eq. tcec-5).  Workspace from
+ * shg_sketch_loss_grad_workspace_size.
+ * Device flags: NOT_SPD (Y rank-deficient), RANGE, TIMEOUT.
+ */
+int shg_sketch_loss_grad_workspace_size(int64_t m, int64_t n, int64_t k, size_t* bytes);
+int shg_sketch_loss_grad(int64_t m, int64_t n, int64_t k, const float* A, int64_t lda,
+                         const float* Y, int64_t ldy, int want_grad, float* d_omega, int64_t ldd,
+                         double* d_loss, void* workspace, size_t ws_bytes, int32_t* d_flags, void* stream);
+
 #ifdef __cplusplus
 }
 #endif

@@ -17,6 +17,11 @@ shg_cholqr2        CholeskyQR2 orthonormalisation (in place)
 shg_cholqr2_static the same on the library's static scratch (allocates nothing)
 shg_rsvd           randomized SVD (Algorithm 1, power scheme of Sec. 2.1)
 shg_rp_hosvd       random-projection HOSVD of a 3-way tensor (Algorithm 2)
+shg_alpha_y_f16    variance of an FP16-rounded N(0,1) value (alpha_Y, Sec. 3.2)
+shg_round_f16      RN_fp16 of an FP32 matrix
+shg_residual_estimate   a-posteriori range-finder residual with FP16 probes (Thms. 1, 3)
+shg_sketch_loss_grad    loss and gradient of a learned sketch
+sketch.SketchFn    torch.autograd.Function over the two above; sketch.choose_sketch
 """
 from __future__ import annotations
 
@@ -178,6 +183,70 @@ def shg_cholqr2_static(X: torch.Tensor, flags: torch.Tensor | None = None, check
     if check and flags is not None:
         check_flags(flags, "shg_cholqr2_static")
     return X
+
+
+def shg_alpha_y_f16() -> float:
+    """Variance of an FP16-rounded N(0,1) value (alpha_Y of Sec. 3.2)."""
+    return float(_lib.load().shg_alpha_y_f16())
+
+
+def shg_round_f16(x: torch.Tensor, out: torch.Tensor | None = None, stream=None) -> torch.Tensor:
+    """RN_fp16 of an FP32 matrix, in the library's kernel."""
+    ldx = _mat(x, "x", (torch.float32,))
+    rows, cols = x.shape
+    y = out if out is not None else torch.empty(rows, cols, dtype=torch.float16, device=x.device)
+    ldy = _mat(y, "out", (torch.float16,))
+    _check(_lib.load().shg_round_f16(rows, cols, _ptr(x), ldx, _ptr(y), ldy, _stream(stream)), "shg_round_f16")
+    return y
+
+
+def shg_residual_estimate(A: torch.Tensor, Q: torch.Tensor, t: int = 16, seed: int = 0, offset: int = 0,
+                          alpha: float = 0.0, flags: torch.Tensor | None = None, check: bool = True,
+                          stream=None) -> torch.Tensor:
+    """Device doubles [est, ||(I - QQ^T) A G||_F^2, ||A||_F^2] with t FP16 Gaussian probes."""
+    lda = _mat(A, "A", (torch.float32,))
+    ldq = _mat(Q, "Q", (torch.float32,))
+    m, n = A.shape
+    k = Q.shape[1]
+    if Q.shape[0] != m:
+        raise ValueError("Q must have as many rows as A")
+    lib = _lib.load()
+    need = ctypes.c_size_t()
+    _check(lib.shg_residual_estimate_workspace_size(m, n, k, t, ctypes.byref(need)),
+           "shg_residual_estimate_workspace_size")
+    ws = torch.empty(need.value, dtype=torch.uint8, device=A.device)
+    out = torch.empty(3, dtype=torch.float64, device=A.device)
+    fl = flags if flags is not None else new_flags(A.device)
+    _check(lib.shg_residual_estimate(m, n, k, t, _ptr(A), lda, _ptr(Q), ldq, seed, offset, float(alpha), _ptr(out),
+                                     _ptr(ws), ws.numel(), _ptr(fl), _stream(stream)), "shg_residual_estimate")
+    if check:
+        check_flags(fl, "shg_residual_estimate")
+    return out
+
+
+def shg_sketch_loss_grad(A: torch.Tensor, Y: torch.Tensor, want_grad: bool = True,
+                         flags: torch.Tensor | None = None, check: bool = True, stream=None):
+    """(loss as a device double, dloss/dOmega n x k FP32 or None) for Y = A fp16(Omega)."""
+    lda = _mat(A, "A", (torch.float32,))
+    ldy = _mat(Y, "Y", (torch.float32,))
+    m, n = A.shape
+    k = Y.shape[1]
+    if Y.shape[0] != m:
+        raise ValueError("Y must have as many rows as A")
+    lib = _lib.load()
+    need = ctypes.c_size_t()
+    _check(lib.shg_sketch_loss_grad_workspace_size(m, n, k, ctypes.byref(need)),
+           "shg_sketch_loss_grad_workspace_size")
+    ws = torch.empty(need.value, dtype=torch.uint8, device=A.device)
+    loss = torch.empty((), dtype=torch.float64, device=A.device)
+    grad = torch.empty(n, k, dtype=torch.float32, device=A.device) if want_grad else None
+    fl = flags if flags is not None else new_flags(A.device)
+    _check(lib.shg_sketch_loss_grad(m, n, k, _ptr(A), lda, _ptr(Y), ldy, int(want_grad), _ptr(grad),
+                                    k if want_grad else 0, _ptr(loss), _ptr(ws), ws.numel(), _ptr(fl),
+                                    _stream(stream)), "shg_sketch_loss_grad")
+    if check:
+        check_flags(fl, "shg_sketch_loss_grad")
+    return loss, grad
 
 
 def rsvd_workspace_size(m: int, n: int, rank: int, oversampling: int, power_iters: int = 0) -> int:

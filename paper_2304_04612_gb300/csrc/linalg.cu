@@ -488,7 +488,6 @@ namespace {
 // Cholesky/inverse spill area (2 k^2 doubles), R^-1 in FP32 (k^2) and the
 // Jacobi spill area.
 void small_offsets(int64_t k, size_t off[5]) {
-  const int64_t kp = k + (k & 1);
   off[0] = 0;
   off[1] = off[0] + align256(static_cast<size_t>(k * k) * 8);
   off[2] = off[1] + align256(static_cast<size_t>(2 * k * k) * 8);

@@ -1,0 +1,344 @@
+// Learned sketch (loss and gradient of a test matrix) and the a-posteriori
+// residual estimator with FP16 Gaussian probes.
+//
+// Loss of a sketch Omega on A (m x n), Y = A fp16(Omega), Q = orth(Y):
+//   l = ||A - Q Q^T A||_F^2 / ||A||_F^2 = 1 - ||A^T Q||_F^2 / ||A||_F^2.
+// Gradient (Y = Q R):
+//   dl/dY     = -(2 / ||A||_F^2) (I - Q Q^T) A A^T Q R^-T
+//   dl/dOmega = A^T dl/dY.
+// Residual estimate (Theorems 1 and 3: E ||S G||_F^2 = alpha t ||S||_F^2 for
+// G with i.i.d. entries of variance alpha):
+//   est = sqrt(||(I - Q Q^T) A G||_F^2 / (alpha t)) / ||A||_F.
+// Every product with A runs on the tensor cores (SHGEMM for A G; the TCEC
+// split for A^T Q, A (A^T Q) and A^T dY, which need FP32 accuracy in both
+// operands); the m x k and k x k steps use the FP32 SIMT GEMM and the FP64
+// Gram / Cholesky kernels of CholeskyQR2.
+#include <cmath>
+#include <cuda_fp16.h>
+
+#include "internal.h"
+#include "linalg.h"
+
+namespace shg {
+namespace {
+
+inline int64_t round8(int64_t x) { return (x + 7) / 8 * 8; }
+
+// out += sum of squares of the rows x cols FP32 matrix X (leading dimension
+// ld).  Each thread squares and adds up to 8 values in FP32, then adds that
+// partial sum in FP64 (few FP64 operations: GB300's FP64 rate is low).
+__global__ void sumsq_kernel(long long rows, long long cols, const float* __restrict__ X, long long ld,
+                             double* out) {
+  __shared__ double red[32];
+  const long long n = rows * cols;
+  const long long stride = static_cast<long long>(gridDim.x) * blockDim.x * 8;
+  double acc = 0.0;
+  for (long long e0 = (static_cast<long long>(blockIdx.x) * blockDim.x + threadIdx.x) * 8; e0 < n; e0 += stride) {
+    float s = 0.0f;
+#pragma unroll
+    for (int u = 0; u < 8; ++u) {
+      const long long e = e0 + u;
+      if (e < n) {
+        const long long r = e / cols, c = e - r * cols;
+        const float v = X[r * ld + c];
+        s = fmaf(v, v, s);
+      }
+    }
+    acc += static_cast<double>(s);
+  }
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
+  if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = acc;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    double t = 0.0;
+    for (int w = 0; w < static_cast<int>(blockDim.x >> 5); ++w) t += red[w];
+    atomicAdd(out, t);
+  }
+}
+
+// Same for a row-major matrix whose column count is a multiple of 4 and whose
+// rows start 16-byte aligned: float4 loads.
+__global__ void sumsq4_kernel(long long rows, long long cols4, const float4* __restrict__ X, long long ld4,
+                              double* out) {
+  __shared__ double red[32];
+  const long long n = rows * cols4;
+  const long long stride = static_cast<long long>(gridDim.x) * blockDim.x * 2;
+  double acc = 0.0;
+  for (long long e0 = (static_cast<long long>(blockIdx.x) * blockDim.x + threadIdx.x) * 2; e0 < n; e0 += stride) {
+    float s = 0.0f;
+#pragma unroll
+    for (int u = 0; u < 2; ++u) {
+      const long long e = e0 + u;
+      if (e < n) {
+        const long long r = e / cols4, c = e - r * cols4;
+        const float4 v = X[r * ld4 + c];
+        s = fmaf(v.x, v.x, s);
+        s = fmaf(v.y, v.y, s);
+        s = fmaf(v.z, v.z, s);
+        s = fmaf(v.w, v.w, s);
+      }
+    }
+    acc += static_cast<double>(s);
+  }
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
+  if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = acc;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    double t = 0.0;
+    for (int w = 0; w < static_cast<int>(blockDim.x >> 5); ++w) t += red[w];
+    atomicAdd(out, t);
+  }
+}
+
+// C = -C for the k x n block (leading dimension ld).
+__global__ void negate_kernel(int rows, int cols, float* C, int ld) {
+  for (int e = blockIdx.x * blockDim.x + threadIdx.x; e < rows * cols; e += gridDim.x * blockDim.x) {
+    const int r = e / cols, c = e - r * cols;
+    C[r * ld + c] = -C[r * ld + c];
+  }
+}
+
+// Rit[i][j] = s * Rinv[j][i] with s = -2 / ||A||_F^2 read from the device
+// (k x k, leading dimensions ld).
+__global__ void scaled_transpose_kernel(int k, const float* __restrict__ Rinv, int ld, const double* nA2,
+                                        float* __restrict__ Rit) {
+  const float s = static_cast<float>(-2.0 / *nA2);
+  for (int e = blockIdx.x * blockDim.x + threadIdx.x; e < k * k; e += gridDim.x * blockDim.x) {
+    const int i = e / k, j = e - i * k;
+    Rit[i * ld + j] = s * Rinv[j * ld + i];
+  }
+}
+
+// acc = {||A||^2, ||A^T Q||^2} -> loss = 1 - acc[1] / acc[0].
+__global__ void loss_kernel(const double* acc, double* loss) { *loss = 1.0 - acc[1] / acc[0]; }
+
+// acc = {||A||^2, ||(I - QQ^T) A G||^2} -> out = {est, acc[1], acc[0]}.
+__global__ void estimate_kernel(const double* acc, double alpha, int t, double* out) {
+  out[0] = sqrt(acc[1] / (alpha * t)) / sqrt(acc[0]);
+  out[1] = acc[1];
+  out[2] = acc[0];
+}
+
+int sumsq(int64_t rows, int64_t cols, const float* X, int64_t ld, double* out, cudaStream_t st) {
+  const int sms = sm_count();
+  if (sms <= 0) return SHG_ERR_CUDA;
+  const bool vec = (cols % 4 == 0) && (ld % 4 == 0) && (reinterpret_cast<uintptr_t>(X) % 16 == 0);
+  const long long per = vec ? 8 : 8;  // values per thread per step
+  const long long want = (rows * cols + 256 * per - 1) / (256 * per);
+  const int grid = static_cast<int>(want < 4ll * sms ? (want > 0 ? want : 1) : 4ll * sms);
+  if (vec)
+    sumsq4_kernel<<<grid, 256, 0, st>>>(rows, cols / 4, reinterpret_cast<const float4*>(X), ld / 4, out);
+  else
+    sumsq_kernel<<<grid, 256, 0, st>>>(rows, cols, X, ld, out);
+  return cuda_status(cudaGetLastError());
+}
+
+int negate(int64_t rows, int64_t cols, float* C, int64_t ld, cudaStream_t st) {
+  const int n = static_cast<int>(rows * cols);
+  negate_kernel<<<(n + 255) / 256, 256, 0, st>>>(static_cast<int>(rows), static_cast<int>(cols), C,
+                                                  static_cast<int>(ld));
+  return cuda_status(cudaGetLastError());
+}
+
+#define SHG_TRY(x)                  \
+  do {                              \
+    const int rc_ = (x);            \
+    if (rc_ != SHG_OK) return rc_;  \
+  } while (0)
+
+// Workspace of shg_sketch_loss_grad: Q, T (m x ldk), W1 (n x ldk), W (m x ldk),
+// C, X1, X2, Rinv, Rit (k x ldk), the CholeskyQR scratch, two doubles.
+struct SketchLayout {
+  size_t Q, T, W1, W, C, X1, X2, Rinv, Rit, small, acc, total;
+};
+SketchLayout sketch_layout(int64_t m, int64_t n, int64_t k) {
+  const int64_t ldk = round8(k);
+  SketchLayout L{};
+  size_t off = 0;
+  auto take = [&](size_t bytes) {
+    const size_t o = off;
+    off += align256(bytes);
+    return o;
+  };
+  L.Q = take(m * ldk * 4);
+  L.T = take(m * ldk * 4);
+  L.W1 = take(n * ldk * 4);
+  L.W = take(m * ldk * 4);
+  L.C = take(k * ldk * 4);
+  L.X1 = take(k * ldk * 4);
+  L.X2 = take(k * ldk * 4);
+  L.Rinv = take(k * ldk * 4);
+  L.Rit = take(k * ldk * 4);
+  L.small = take(cholqr_small_bytes(k));
+  L.acc = take(2 * sizeof(double));
+  L.total = off;
+  return L;
+}
+
+// Workspace of shg_residual_estimate: probes G (n x ldt FP16), Z (m x ldt),
+// C (k x ldt), two doubles.
+struct EstLayout {
+  size_t G, Z, C, acc, total;
+};
+EstLayout est_layout(int64_t m, int64_t n, int64_t k, int64_t t) {
+  const int64_t ldt = round8(t);
+  EstLayout L{};
+  size_t off = 0;
+  auto take = [&](size_t bytes) {
+    const size_t o = off;
+    off += align256(bytes);
+    return o;
+  };
+  L.G = take(n * ldt * 2);
+  L.Z = take(m * ldt * 4);
+  L.C = take(k * ldt * 4);
+  L.acc = take(2 * sizeof(double));
+  L.total = off;
+  return L;
+}
+
+// Copy the k x k block of a row-major matrix with leading dimension k into
+// one with leading dimension ld (ld >= k).
+int widen(int64_t k, const float* src, float* dst, int64_t ld, cudaStream_t st) {
+  return cuda_status(cudaMemcpy2DAsync(dst, ld * 4, src, k * 4, k * 4, k, cudaMemcpyDeviceToDevice, st));
+}
+
+bool aligned16(const void* p) { return reinterpret_cast<uintptr_t>(p) % 16 == 0; }
+
+}  // namespace
+}  // namespace shg
+
+using namespace shg;
+
+// alpha_Y of FP16 (Sec. 3.2): E[RN_fp16(g)^2] for g ~ N(0,1).  Every finite
+// non-negative FP16 value v receives the normal probability of its RN
+// interval, whose ends are the midpoints to its neighbours; the largest
+// finite value keeps everything below the overflow threshold 65520.
+extern "C" double shg_alpha_y_f16(void) {
+  double prev = 0.0, sum = 0.0;
+  auto f16 = [](int bits) {
+    const int e = (bits >> 10) & 31, f = bits & 1023;
+    return e == 0 ? std::ldexp(static_cast<double>(f), -24) : std::ldexp(1.0 + f / 1024.0, e - 15);
+  };
+  const double inv_sqrt2 = 0.70710678118654752440;
+  for (int bits = 0; bits <= 0x7BFF; ++bits) {
+    const double v = f16(bits);
+    const double lo = (bits == 0) ? 0.0 : 0.5 * (prev + v);
+    const double hi = (bits == 0x7BFF) ? v + 0.5 * (v - prev) : 0.5 * (v + f16(bits + 1));
+    // P(lo < g < hi) = (erfc(lo / sqrt 2) - erfc(hi / sqrt 2)) / 2 for 0 <= lo < hi
+    const double mass = 0.5 * (std::erfc(lo * inv_sqrt2) - std::erfc(hi * inv_sqrt2));
+    sum += v * v * mass;
+    prev = v;
+  }
+  return 2.0 * sum;
+}
+
+extern "C" int shg_round_f16(int64_t rows, int64_t cols, const float* x, int64_t ldx, uint16_t* y, int64_t ldy,
+                             void* stream) {
+  if (rows < 0 || cols < 0 || ldx < cols || ldy < cols) return SHG_ERR_INVALID_ARG;
+  if (rows * cols > 0 && (!x || !y)) return SHG_ERR_INVALID_ARG;
+  return to_f16(rows, cols, x, ldx, y, ldy, static_cast<cudaStream_t>(stream));
+}
+
+extern "C" int shg_residual_estimate_workspace_size(int64_t m, int64_t n, int64_t k, int64_t t, size_t* bytes) {
+  if (!bytes || m < 1 || n < 1 || k < 1 || t < 1 || k > m) return SHG_ERR_INVALID_ARG;
+  *bytes = est_layout(m, n, k, t).total;
+  return SHG_OK;
+}
+
+extern "C" int shg_residual_estimate(int64_t m, int64_t n, int64_t k, int64_t t, const float* A, int64_t lda,
+                                     const float* Q, int64_t ldq, uint64_t seed, uint64_t offset, double alpha,
+                                     double* d_out, void* ws, size_t ws_bytes, int32_t* d_flags, void* stream) {
+  size_t need = 0;
+  if (shg_residual_estimate_workspace_size(m, n, k, t, &need) != SHG_OK) return SHG_ERR_INVALID_ARG;
+  if (!A || !Q || !d_out || !ws || !d_flags || lda < n || ldq < k) return SHG_ERR_INVALID_ARG;
+  if (lda % 4 != 0 || !aligned16(A)) return SHG_ERR_INVALID_ARG;
+  if (ws_bytes < need) return SHG_ERR_WORKSPACE;
+  if (!(alpha > 0.0)) alpha = shg_alpha_y_f16();
+  cudaStream_t st = static_cast<cudaStream_t>(stream);
+  const EstLayout L = est_layout(m, n, k, t);
+  const int64_t ldt = round8(t);
+  uint8_t* w = static_cast<uint8_t*>(ws);
+  uint16_t* G = reinterpret_cast<uint16_t*>(w + L.G);
+  float* Z = reinterpret_cast<float*>(w + L.Z);
+  float* C = reinterpret_cast<float*>(w + L.C);
+  double* acc = reinterpret_cast<double*>(w + L.acc);
+  if (cudaMemsetAsync(acc, 0, 2 * sizeof(double), st) != cudaSuccess) return SHG_ERR_CUDA;
+  // t fresh probes, RN-rounded to FP16, and Z = A G by SHGEMM
+  SHG_TRY(shg_gaussian_f16(seed, offset, n, t, G, ldt, st));
+  SHG_TRY(tc_gemm(A_KMAJ, B_F16, 2, m, t, n, 1, A, lda, 0, G, ldt, Z, ldt, 0, d_flags, st));
+  // Z <- (I - Q Q^T) Z: C = Q^T Z, Z += Q (-C)
+  SHG_TRY(simt_gemm(k, t, m, Q, ldq, 1, Z, ldt, 0, C, ldt, 0, 1, 0, 0, 0, st));
+  SHG_TRY(negate(k, t, C, ldt, st));
+  SHG_TRY(simt_gemm(m, t, k, Q, ldq, 0, C, ldt, 0, Z, ldt, 1, 1, 0, 0, 0, st));
+  SHG_TRY(sumsq(m, n, A, lda, acc, st));
+  SHG_TRY(sumsq(m, t, Z, ldt, acc + 1, st));
+  estimate_kernel<<<1, 1, 0, st>>>(acc, alpha, static_cast<int>(t), d_out);
+  return cuda_status(cudaGetLastError());
+}
+
+extern "C" int shg_sketch_loss_grad_workspace_size(int64_t m, int64_t n, int64_t k, size_t* bytes) {
+  if (!bytes || m < 1 || n < 1 || k < 1 || k > m || k > 1024) return SHG_ERR_INVALID_ARG;
+  *bytes = sketch_layout(m, n, k).total;
+  return SHG_OK;
+}
+
+extern "C" int shg_sketch_loss_grad(int64_t m, int64_t n, int64_t k, const float* A, int64_t lda, const float* Y,
+                                    int64_t ldy, int want_grad, float* d_omega, int64_t ldd, double* d_loss,
+                                    void* ws, size_t ws_bytes, int32_t* d_flags, void* stream) {
+  size_t need = 0;
+  if (shg_sketch_loss_grad_workspace_size(m, n, k, &need) != SHG_OK) return SHG_ERR_INVALID_ARG;
+  if (!A || !Y || !d_loss || !ws || !d_flags || lda < n || ldy < k) return SHG_ERR_INVALID_ARG;
+  if (lda % 4 != 0 || !aligned16(A)) return SHG_ERR_INVALID_ARG;
+  if (want_grad && (!d_omega || ldd < k)) return SHG_ERR_INVALID_ARG;
+  if (ws_bytes < need) return SHG_ERR_WORKSPACE;
+  cudaStream_t st = static_cast<cudaStream_t>(stream);
+  const SketchLayout L = sketch_layout(m, n, k);
+  const int64_t ldk = round8(k);
+  uint8_t* w = static_cast<uint8_t*>(ws);
+  float* Q = reinterpret_cast<float*>(w + L.Q);
+  float* T = reinterpret_cast<float*>(w + L.T);
+  float* W1 = reinterpret_cast<float*>(w + L.W1);
+  float* W = reinterpret_cast<float*>(w + L.W);
+  float* C = reinterpret_cast<float*>(w + L.C);
+  float* X1 = reinterpret_cast<float*>(w + L.X1);
+  float* X2 = reinterpret_cast<float*>(w + L.X2);
+  float* Rinv = reinterpret_cast<float*>(w + L.Rinv);
+  float* Rit = reinterpret_cast<float*>(w + L.Rit);
+  const SmallWs sw = small_ws(w + L.small, k);
+  double* acc = reinterpret_cast<double*>(w + L.acc);
+  if (cudaMemsetAsync(acc, 0, 2 * sizeof(double), st) != cudaSuccess) return SHG_ERR_CUDA;
+  // Q = CholeskyQR2(Y) keeping both inverse factors: Y = Q R, R^-1 = X1 X2
+  if (cudaMemcpy2DAsync(Q, ldk * 4, Y, ldy * 4, k * 4, m, cudaMemcpyDeviceToDevice, st) != cudaSuccess)
+    return SHG_ERR_CUDA;
+  SHG_TRY(gram_f64(m, k, Q, ldk, sw.G, st));
+  SHG_TRY(chol_inv(k, sw.G, sw.Rf, sw.chol, d_flags, st));
+  SHG_TRY(widen(k, sw.Rf, X1, ldk, st));
+  SHG_TRY(simt_gemm(m, k, k, Q, ldk, 0, X1, ldk, 0, T, ldk, 0, 1, 0, 0, 0, st));
+  SHG_TRY(gram_f64(m, k, T, ldk, sw.G, st));
+  SHG_TRY(chol_inv(k, sw.G, sw.Rf, sw.chol, d_flags, st));
+  SHG_TRY(widen(k, sw.Rf, X2, ldk, st));
+  SHG_TRY(simt_gemm(m, k, k, T, ldk, 0, X2, ldk, 0, Q, ldk, 0, 1, 0, 0, 0, st));
+  // loss = 1 - ||A^T Q||^2 / ||A||^2, A^T Q FP32-accurate by the TCEC split
+  SHG_TRY(sumsq(m, n, A, lda, acc, st));
+  SHG_TRY(tc_gemm(A_MNMAJ, B_SPLIT, 2, n, k, m, 1, A, lda, 0, Q, ldk, W1, ldk, 0, d_flags, st));
+  SHG_TRY(sumsq(n, k, W1, ldk, acc + 1, st));
+  loss_kernel<<<1, 1, 0, st>>>(acc, d_loss);
+  SHG_TRY(cuda_status(cudaGetLastError()));
+  if (!want_grad) return SHG_OK;
+  // W = A (A^T Q); P = (I - Q Q^T) W = W + Q (-(Q^T W))
+  SHG_TRY(tc_gemm(A_KMAJ, B_SPLIT, 2, m, k, n, 1, A, lda, 0, W1, ldk, W, ldk, 0, d_flags, st));
+  SHG_TRY(simt_gemm(k, k, m, Q, ldk, 1, W, ldk, 0, C, ldk, 0, 1, 0, 0, 0, st));
+  SHG_TRY(negate(k, k, C, ldk, st));
+  SHG_TRY(simt_gemm(m, k, k, Q, ldk, 0, C, ldk, 0, W, ldk, 1, 1, 0, 0, 0, st));
+  // dl/dY = P R^-T (-2 / ||A||^2), R^-1 = X1 X2
+  SHG_TRY(simt_gemm(k, k, k, X1, ldk, 0, X2, ldk, 0, Rinv, ldk, 0, 1, 0, 0, 0, st));
+  scaled_transpose_kernel<<<(static_cast<int>(k * k) + 255) / 256, 256, 0, st>>>(static_cast<int>(k), Rinv,
+                                                                                  static_cast<int>(ldk), acc, Rit);
+  SHG_TRY(cuda_status(cudaGetLastError()));
+  SHG_TRY(simt_gemm(m, k, k, W, ldk, 0, Rit, ldk, 0, T, ldk, 0, 1, 0, 0, 0, st));
+  // dl/dOmega = A^T dl/dY (TCEC split, TN)
+  return tc_gemm(A_MNMAJ, B_SPLIT, 2, n, k, m, 1, A, lda, 0, T, ldk, d_omega, ldd, 0, d_flags, st);
+}

@@ -65,3 +65,29 @@ def test_host_argument_validation(lib):
     r = (ctypes.c_int64 * 3)(4, 9, 4)                                 # J > I
     assert lib.shg_rp_hosvd_workspace_size(3, d, r, ctypes.byref(sz)) == 1
     assert lib.shg_rp_hosvd_workspace_size(4, d, r, ctypes.byref(sz)) == 7
+
+
+def test_alpha_y_f16_matches_the_oracle(lib):
+    # the library computes alpha_Y (Sec. 3.2) on the host from its definition;
+    # the oracle computes it independently in numpy / scipy
+    from oracle.gaussian import FP16, alpha_Y
+    a = lib.shg_alpha_y_f16()
+    assert abs(a - alpha_Y(FP16)) <= 1e-13
+    assert 0.99999990 < a < 1.0
+
+
+def test_sketch_and_estimator_host_validation(lib):
+    null = ctypes.c_void_p(0)
+    sz = ctypes.c_size_t()
+    assert lib.shg_residual_estimate_workspace_size(100, 80, 120, 16, ctypes.byref(sz)) == 1   # k > m
+    assert lib.shg_residual_estimate_workspace_size(100, 80, 20, 0, ctypes.byref(sz)) == 1     # t < 1
+    assert lib.shg_residual_estimate_workspace_size(100, 80, 20, 16, ctypes.byref(sz)) == 0
+    assert sz.value >= 100 * 16 * 4 + 80 * 16 * 2
+    assert lib.shg_sketch_loss_grad_workspace_size(100, 80, 2000, ctypes.byref(sz)) == 1       # k > m
+    assert lib.shg_sketch_loss_grad_workspace_size(2048, 2048, 96, ctypes.byref(sz)) == 0
+    # NULL operands are rejected before any CUDA call
+    assert lib.shg_residual_estimate(100, 80, 20, 16, null, 80, null, 20, 0, 0, 0.0, null, null, 0, null,
+                                     null) == 1
+    assert lib.shg_sketch_loss_grad(100, 80, 20, null, 80, null, 20, 1, null, 20, null, null, 0, null, null) == 1
+    assert lib.shg_round_f16(-1, 4, null, 4, null, 4, null) == 1
+    assert lib.shg_round_f16(0, 4, null, 4, null, 4, null) == 0
