@@ -418,6 +418,7 @@ def side_measurements(shg, OS, torch, dev, A, A_host, Om, Om_host, Ys, flags, st
     # randomized SVD of the planted 1024^2 matrix and RP-HOSVD of the 512^3 tensor
     out["rsvd_1024"] = rsvd_times(shg, torch, dev, stream)
     out["rp_hosvd_512"] = hosvd_times(shg, torch, dev, stream)
+    out["rsvd_batched_256"] = batched_times(shg, torch, dev, stream)
 
     # CPU baseline: the oracle on a bounded row sample of the same sweep
     rate, rows_done, dt = oracle_rate(A_host, Om_host, budget_s=10.0)
@@ -449,6 +450,59 @@ def rsvd_times(shg, torch, dev, stream):
         res[v] = {"ms": ms, "sigma_max_rel_err": float(np.max(np.abs(S - ref["S"]) / ref["S"])),
                   "residual": float(r_p), "oracle_residual": ref["r_p"]}
     res["speedup_f16_vs_fp32"] = res["fp32"]["ms"] / res["f16"]["ms"]
+    return res
+
+
+def batched_times(shg, torch, dev, stream):
+    """256 uneven randomized SVDs (m in [256, 4096], n in [256, 2048], rank in
+    {16, 32, 64, 128}, s = 16, q = 1, sigma_i = 2^(-i/rate), rate in [8, 64]).
+    The matrices are built on the GPU from seeded Gaussians as
+    Q1 diag(sigma) Q2^T with Q1, Q2 orthonormal bases of 256 columns (the
+    spectrum beyond 256 is below 2^-4 at the slowest decay and is dropped):
+    input generation only, outside every timed region."""
+    from synth import batch_specs
+    specs = batch_specs(256, seed=4)
+    g = torch.Generator(device=dev).manual_seed(4)
+    As, ranks = [], []
+    for sp in specs:
+        m, n = sp["m"], sp["n"]
+        r = min(m, n, 256)
+        sig = torch.pow(2.0, -torch.arange(1, r + 1, device=dev, dtype=torch.float32) / sp["rate"])
+        q1 = torch.linalg.qr(torch.randn(m, r, device=dev, generator=g))[0]
+        q2 = torch.linalg.qr(torch.randn(n, r, device=dev, generator=g))[0]
+        ld = (n + 3) // 4 * 4
+        buf = torch.zeros(m, ld, device=dev)
+        buf[:, :n] = (q1 * sig) @ q2.T
+        As.append(buf[:, :n])
+        ranks.append(sp["rank"])
+    s, q = 16, 1
+    ms_, ns_ = [A.shape[0] for A in As], [A.shape[1] for A in As]
+    ws = torch.empty(shg.rsvd_batched_workspace_size(ms_, ns_, ranks, s, q), dtype=torch.uint8, device=dev)
+    out = ([torch.empty(m, r, device=dev) for m, r in zip(ms_, ranks)], [torch.empty(r, device=dev) for r in ranks],
+           [torch.empty(n, r, device=dev) for n, r in zip(ns_, ranks)])
+    fl = shg.new_flags(dev)
+    res = {"problems": 256, "bytes_of_A": int(sum(4 * m * n for m, n in zip(ms_, ns_)))}
+    for mode, use_graph in (("graph", True), ("streams", False)):
+        fn = lambda: shg.shg_rsvd_batched(As, ranks, s, q, omegas=None, seed=4, use_graph=use_graph, out=out,
+                                          workspace=ws, flags=fl, check=False, stream=stream)
+        fn()
+        ms = time_ms(torch, stream, fn, reps=5)
+        res[mode] = {"ms": ms, "problems_per_s": 256 / (ms * 1e-3)}
+    # the same problems one after another through shg_rsvd on one stream
+    oms = [shg.shg_gaussian_f16(4, i << 32, n, r + s,
+                                out=torch.empty(n, (r + s + 7) // 8 * 8, dtype=torch.float16, device=dev)[:, :r + s])
+           for i, (n, r) in enumerate(zip(ns_, ranks))]
+    ws1 = torch.empty(max(shg.rsvd_workspace_size(m, n, r, s, q) for m, n, r in zip(ms_, ns_, ranks)),
+                      dtype=torch.uint8, device=dev)
+
+    def seq():
+        for i in range(256):
+            shg.shg_rsvd(As[i], oms[i], ranks[i], s, q, "f16", workspace=ws1,
+                         out=(out[0][i], out[1][i], out[2][i], None), flags=fl, check=False, stream=stream)
+    seq()
+    ms = time_ms(torch, stream, seq, reps=2)
+    res["sequential"] = {"ms": ms, "problems_per_s": 256 / (ms * 1e-3)}
+    res["device_flags"] = int(fl.item())
     return res
 
 

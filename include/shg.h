@@ -208,6 +208,35 @@ int shg_rp_hosvd(int ndim, const int64_t* dims, const int64_t* ranks, const floa
                  void* workspace, size_t ws_bytes, int variant, int32_t* d_flags, void* stream);
 
 /*
+ * A12. Batched randomized SVD: problem i (0 <= i < batch) is Algorithm 1 on
+ * A[i] (m[i] x n[i], lda[i]) with rank[i], the common oversampling and
+ * power_iters, exactly as shg_rsvd computes it, into U[i] (m[i] x rank[i]),
+ * S[i] (rank[i]) and V[i] (n[i] x rank[i]).  Batching is not in the paper.
+ *   omegas: NULL, or per problem an FP16 n[i] x (rank[i] + oversampling)
+ *   test matrix (ldo[i], multiple of 8) or NULL; a NULL Omega is generated
+ *   as shg_gaussian_f16(seed, offset = i * 2^32) would generate it.
+ *   All arrays of sizes and pointers are HOST arrays of `batch` entries; the
+ *   pointers in them are device pointers.  Workspace from
+ *   shg_rsvd_batched_workspace_size (one slice per concurrent branch).
+ * Problems run concurrently on up to 32 streams owned by the library
+ * (created on the first call on a device), forked from and joined back to
+ * `stream`.  use_graph != 0: the first call with a given set of arguments
+ * captures this fork/join into a CUDA graph, later calls with identical
+ * arguments (same pointers and sizes) replay it with one graph launch; up to
+ * 16 graphs are kept per process.  Calls are serialised by a mutex.
+ * Device flags: as shg_rsvd (OR-ed over all problems).
+ */
+int shg_rsvd_batched_workspace_size(int batch, const int64_t* m, const int64_t* n, const int64_t* rank,
+                                    int64_t oversampling, int power_iters, size_t* bytes);
+int shg_rsvd_batched(int batch, const int64_t* m, const int64_t* n, const int64_t* rank,
+                     int64_t oversampling, int power_iters,
+                     const float* const* A, const int64_t* lda,
+                     const uint16_t* const* omegas, const int64_t* ldo, uint64_t seed,
+                     float* const* U, float* const* S, float* const* V,
+                     void* workspace, size_t ws_bytes, int variant, int use_graph,
+                     int32_t* d_flags, void* stream);
+
+/*
  * alpha_Y of FP16 (Sec. 3.2): E[RN_fp16(g)^2] for g ~ N(0,1), the variance
  * of an FP16-rounded standard Gaussian entry, computed on the host from its
  * definition (each finite FP16 value weighted by the normal probability of

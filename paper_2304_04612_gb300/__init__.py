@@ -17,6 +17,7 @@ shg_cholqr2        CholeskyQR2 orthonormalisation (in place)
 shg_cholqr2_static the same on the library's static scratch (allocates nothing)
 shg_rsvd           randomized SVD (Algorithm 1, power scheme of Sec. 2.1)
 shg_rp_hosvd       random-projection HOSVD of a 3-way tensor (Algorithm 2)
+shg_rsvd_batched   many uneven randomized SVDs at once (concurrent branches, CUDA graph)
 shg_alpha_y_f16    variance of an FP16-rounded N(0,1) value (alpha_Y, Sec. 3.2)
 shg_round_f16      RN_fp16 of an FP32 matrix
 shg_residual_estimate   a-posteriori range-finder residual with FP16 probes (Thms. 1, 3)
@@ -183,6 +184,59 @@ def shg_cholqr2_static(X: torch.Tensor, flags: torch.Tensor | None = None, check
     if check and flags is not None:
         check_flags(flags, "shg_cholqr2_static")
     return X
+
+
+def _host_array(ctype, values):
+    return (ctype * len(values))(*values)
+
+
+def rsvd_batched_workspace_size(ms, ns, ranks, oversampling: int, power_iters: int = 0) -> int:
+    b = len(ms)
+    need = ctypes.c_size_t()
+    _check(_lib.load().shg_rsvd_batched_workspace_size(
+        b, _host_array(ctypes.c_int64, ms), _host_array(ctypes.c_int64, ns), _host_array(ctypes.c_int64, ranks),
+        oversampling, power_iters, ctypes.byref(need)), "shg_rsvd_batched_workspace_size")
+    return need.value
+
+
+def shg_rsvd_batched(As, ranks, oversampling: int, power_iters: int = 0, omegas=None, seed: int = 0,
+                     variant="f16", use_graph: bool = True, out=None, workspace: torch.Tensor | None = None,
+                     flags: torch.Tensor | None = None, check: bool = True, stream=None):
+    """Randomized SVD of every A in As (Algorithm 1 per problem, run concurrently).
+
+    omegas: None (all generated from ``seed``) or a list whose entries are FP16
+    tensors or None.  Returns (Us, Ss, Vs) lists; ``out`` may pass them in
+    (needed for graph replay, which is keyed on the output pointers).
+    """
+    b = len(As)
+    ms, ns = [int(A.shape[0]) for A in As], [int(A.shape[1]) for A in As]
+    ldas = [_mat(A, f"A[{i}]", (torch.float32,)) for i, A in enumerate(As)]
+    dev_ = As[0].device
+    if out is None:
+        Us = [torch.empty(m, r, device=dev_) for m, r in zip(ms, ranks)]
+        Ss = [torch.empty(r, device=dev_) for r in ranks]
+        Vs = [torch.empty(n, r, device=dev_) for n, r in zip(ns, ranks)]
+    else:
+        Us, Ss, Vs = out
+    lib = _lib.load()
+    need = rsvd_batched_workspace_size(ms, ns, ranks, oversampling, power_iters)
+    ws = workspace if workspace is not None else torch.empty(need, dtype=torch.uint8, device=dev_)
+    fl = flags if flags is not None else new_flags(dev_)
+    if omegas is None:
+        om_arr, ldo_arr = None, None
+    else:
+        om_arr = _host_array(ctypes.c_void_p, [o.data_ptr() if o is not None else 0 for o in omegas])
+        ldo_arr = _host_array(ctypes.c_int64, [o.stride(0) if o is not None else 0 for o in omegas])
+    _check(lib.shg_rsvd_batched(
+        b, _host_array(ctypes.c_int64, ms), _host_array(ctypes.c_int64, ns), _host_array(ctypes.c_int64, ranks),
+        oversampling, power_iters, _host_array(ctypes.c_void_p, [A.data_ptr() for A in As]),
+        _host_array(ctypes.c_int64, ldas), om_arr, ldo_arr, seed,
+        _host_array(ctypes.c_void_p, [U.data_ptr() for U in Us]), _host_array(ctypes.c_void_p, [S.data_ptr() for S in Ss]),
+        _host_array(ctypes.c_void_p, [V.data_ptr() for V in Vs]), _ptr(ws), ws.numel(), _variant(variant),
+        int(use_graph), _ptr(fl), _stream(stream)), "shg_rsvd_batched")
+    if check:
+        check_flags(fl, "shg_rsvd_batched")
+    return Us, Ss, Vs
 
 
 def shg_alpha_y_f16() -> float:

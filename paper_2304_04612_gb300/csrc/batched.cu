@@ -1,0 +1,249 @@
+// Batched randomized SVD: one call for many uneven problems.
+//
+// Problem i runs Algorithm 1 (shg_rsvd) on branch i mod B of a fork/join
+// over B library-owned streams; each branch reuses its own slice of the
+// workspace, so problems on one branch run in order and problems on
+// different branches run concurrently (their single-CTA k x k kernels and
+// small projections fill the GPU together).  With use_graph the whole
+// fork/join is captured once into a CUDA graph, cached by the call's
+// arguments, and replayed with one graph launch on the caller's stream.
+#include <cstring>
+#include <mutex>
+#include <vector>
+
+#include "internal.h"
+
+namespace shg {
+namespace {
+
+inline int64_t round8(int64_t x) { return (x + 7) / 8 * 8; }
+
+constexpr int kMaxBranches = 32;
+constexpr int kMaxDevices = 64;
+constexpr int kMaxGraphs = 16;
+
+// Streams and fork/join events of one device, created on first use.
+struct Pool {
+  cudaStream_t s[kMaxBranches] = {};
+  cudaEvent_t done[kMaxBranches] = {};
+  cudaEvent_t fork = nullptr;
+  cudaStream_t capture = nullptr;  // graphs are captured here, never on the caller's stream
+  bool ready = false;
+};
+Pool g_pool[kMaxDevices];
+
+struct GraphEntry {
+  std::vector<uint8_t> key;
+  cudaGraphExec_t exec = nullptr;
+  int dev = -1;
+  unsigned long long last_use = 0;
+};
+std::vector<GraphEntry> g_graphs;
+unsigned long long g_tick = 0;
+std::mutex g_mu;
+
+int pool_for_device(Pool** out, int* dev_out) {
+  int dev = -1;
+  if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= kMaxDevices) return SHG_ERR_CUDA;
+  Pool& p = g_pool[dev];
+  if (!p.ready) {
+    for (int b = 0; b < kMaxBranches; ++b) {
+      if (cudaStreamCreateWithFlags(&p.s[b], cudaStreamNonBlocking) != cudaSuccess) return SHG_ERR_CUDA;
+      if (cudaEventCreateWithFlags(&p.done[b], cudaEventDisableTiming) != cudaSuccess) return SHG_ERR_CUDA;
+    }
+    if (cudaEventCreateWithFlags(&p.fork, cudaEventDisableTiming) != cudaSuccess) return SHG_ERR_CUDA;
+    if (cudaStreamCreateWithFlags(&p.capture, cudaStreamNonBlocking) != cudaSuccess) return SHG_ERR_CUDA;
+    p.ready = true;
+  }
+  *out = &p;
+  *dev_out = dev;
+  return SHG_OK;
+}
+
+int branches_for(int batch) { return batch < kMaxBranches ? batch : kMaxBranches; }
+
+// Largest per-problem need: the shg_rsvd workspace plus an FP16 Omega
+// (n x round8(k)) for problems whose Omega is generated.
+int branch_bytes(int batch, const int64_t* m, const int64_t* n, const int64_t* rank, int64_t s, int q,
+                 size_t* out) {
+  size_t mx = 0;
+  for (int i = 0; i < batch; ++i) {
+    size_t b = 0;
+    const int rc = shg_rsvd_workspace_size(m[i], n[i], rank[i], s, q, &b);
+    if (rc != SHG_OK) return rc;
+    b = (b + 255) & ~size_t(255);
+    b += (static_cast<size_t>(n[i]) * round8(rank[i] + s) * 2 + 255) & ~size_t(255);
+    if (b > mx) mx = b;
+  }
+  *out = mx;
+  return SHG_OK;
+}
+
+template <typename T>
+void put(std::vector<uint8_t>& key, const T& v) {
+  const uint8_t* p = reinterpret_cast<const uint8_t*>(&v);
+  key.insert(key.end(), p, p + sizeof(T));
+}
+
+struct Args {
+  int batch;
+  const int64_t *m, *n, *rank;
+  int64_t s;
+  int q;
+  const float* const* A;
+  const int64_t* lda;
+  const uint16_t* const* omegas;
+  const int64_t* ldo;
+  uint64_t seed;
+  float* const* U;
+  float* const* S;
+  float* const* V;
+  uint8_t* ws;
+  size_t ws_bytes;
+  int variant;
+  int32_t* flags;
+};
+
+std::vector<uint8_t> make_key(const Args& a, int dev) {
+  std::vector<uint8_t> key;
+  put(key, dev);
+  put(key, a.batch);
+  put(key, a.s);
+  put(key, a.q);
+  put(key, a.seed);
+  put(key, a.ws);
+  put(key, a.ws_bytes);
+  put(key, a.variant);
+  put(key, a.flags);
+  for (int i = 0; i < a.batch; ++i) {
+    put(key, a.m[i]);
+    put(key, a.n[i]);
+    put(key, a.rank[i]);
+    put(key, a.A[i]);
+    put(key, a.lda[i]);
+    const uint16_t* om = a.omegas ? a.omegas[i] : nullptr;
+    put(key, om);
+    put(key, om ? a.ldo[i] : int64_t(0));
+    put(key, a.U[i]);
+    put(key, a.S[i]);
+    put(key, a.V[i]);
+  }
+  return key;
+}
+
+// The fork/join itself: problems on branch streams, joined back to `st`.
+int enqueue(const Args& a, Pool& p, size_t per_branch, cudaStream_t st) {
+  const int nb = branches_for(a.batch);
+  if (cudaEventRecord(p.fork, st) != cudaSuccess) return SHG_ERR_CUDA;
+  for (int b = 0; b < nb; ++b)
+    if (cudaStreamWaitEvent(p.s[b], p.fork, 0) != cudaSuccess) return SHG_ERR_CUDA;
+  for (int i = 0; i < a.batch; ++i) {
+    const int b = i % nb;
+    uint8_t* w = a.ws + static_cast<size_t>(b) * per_branch;
+    const int64_t k = a.rank[i] + a.s;
+    const uint16_t* om = a.omegas ? a.omegas[i] : nullptr;
+    int64_t ldo = om ? a.ldo[i] : round8(k);
+    size_t need = 0;
+    int rc = shg_rsvd_workspace_size(a.m[i], a.n[i], a.rank[i], a.s, a.q, &need);
+    if (rc != SHG_OK) return rc;
+    need = (need + 255) & ~size_t(255);
+    if (!om) {
+      uint16_t* gen = reinterpret_cast<uint16_t*>(w + need);
+      // Philox stream of problem i: counter blocks from i * 2^32 on
+      rc = shg_gaussian_f16(a.seed, static_cast<uint64_t>(i) << 32, a.n[i], k, gen, ldo, p.s[b]);
+      if (rc != SHG_OK) return rc;
+      om = gen;
+    }
+    rc = shg_rsvd(a.m[i], a.n[i], a.rank[i], a.s, a.q, a.A[i], a.lda[i], om, ldo, a.U[i], a.S[i], a.V[i], nullptr,
+                  w, need, a.variant, a.flags, p.s[b]);
+    if (rc != SHG_OK) return rc;
+  }
+  for (int b = 0; b < nb; ++b) {
+    if (cudaEventRecord(p.done[b], p.s[b]) != cudaSuccess) return SHG_ERR_CUDA;
+    if (cudaStreamWaitEvent(st, p.done[b], 0) != cudaSuccess) return SHG_ERR_CUDA;
+  }
+  return SHG_OK;
+}
+
+}  // namespace
+}  // namespace shg
+
+using namespace shg;
+
+extern "C" int shg_rsvd_batched_workspace_size(int batch, const int64_t* m, const int64_t* n, const int64_t* rank,
+                                               int64_t oversampling, int power_iters, size_t* bytes) {
+  if (!bytes || batch < 1 || !m || !n || !rank) return SHG_ERR_INVALID_ARG;
+  size_t per = 0;
+  const int rc = branch_bytes(batch, m, n, rank, oversampling, power_iters, &per);
+  if (rc != SHG_OK) return rc;
+  *bytes = per * branches_for(batch);
+  return SHG_OK;
+}
+
+extern "C" int shg_rsvd_batched(int batch, const int64_t* m, const int64_t* n, const int64_t* rank,
+                                int64_t oversampling, int power_iters, const float* const* A, const int64_t* lda,
+                                const uint16_t* const* omegas, const int64_t* ldo, uint64_t seed, float* const* U,
+                                float* const* S, float* const* V, void* ws, size_t ws_bytes, int variant,
+                                int use_graph, int32_t* d_flags, void* stream) {
+  size_t need = 0;
+  int rc = shg_rsvd_batched_workspace_size(batch, m, n, rank, oversampling, power_iters, &need);
+  if (rc != SHG_OK) return rc;
+  if (!A || !lda || !U || !S || !V || !ws || !d_flags) return SHG_ERR_INVALID_ARG;
+  if (omegas && !ldo) return SHG_ERR_INVALID_ARG;
+  for (int i = 0; i < batch; ++i) {
+    if (!A[i] || !U[i] || !S[i] || !V[i] || lda[i] < n[i]) return SHG_ERR_INVALID_ARG;
+    if (omegas && omegas[i] && ldo[i] < rank[i] + oversampling) return SHG_ERR_INVALID_ARG;
+  }
+  if (ws_bytes < need) return SHG_ERR_WORKSPACE;
+  Args a{batch, m, n, rank, oversampling, power_iters, A, lda, omegas, ldo, seed, U, S, V,
+         static_cast<uint8_t*>(ws), ws_bytes, variant, d_flags};
+  size_t per = 0;
+  rc = branch_bytes(batch, m, n, rank, oversampling, power_iters, &per);
+  if (rc != SHG_OK) return rc;
+  cudaStream_t st = static_cast<cudaStream_t>(stream);
+  std::lock_guard<std::mutex> lock(g_mu);
+  Pool* p = nullptr;
+  int dev = -1;
+  if ((rc = pool_for_device(&p, &dev)) != SHG_OK) return rc;
+  cudaStreamCaptureStatus cap = cudaStreamCaptureStatusNone;
+  if (cudaStreamIsCapturing(st, &cap) != cudaSuccess) return SHG_ERR_CUDA;
+  if (!use_graph || cap != cudaStreamCaptureStatusNone) return enqueue(a, *p, per, st);
+
+  std::vector<uint8_t> key = make_key(a, dev);
+  for (GraphEntry& e : g_graphs) {
+    if (e.dev == dev && e.key == key) {
+      e.last_use = ++g_tick;
+      return cuda_status(cudaGraphLaunch(e.exec, st));
+    }
+  }
+  // capture the fork/join once on the library's capture stream (the caller's
+  // stream may be the legacy default stream, which cannot be captured); the
+  // graph launch then orders it after the caller's earlier work
+  if (cudaStreamBeginCapture(p->capture, cudaStreamCaptureModeRelaxed) != cudaSuccess) return SHG_ERR_CUDA;
+  rc = enqueue(a, *p, per, p->capture);
+  cudaGraph_t graph = nullptr;
+  const cudaError_t end = cudaStreamEndCapture(p->capture, &graph);
+  if (rc != SHG_OK) {
+    if (graph) cudaGraphDestroy(graph);
+    return rc;
+  }
+  if (end != cudaSuccess || !graph) return SHG_ERR_CUDA;
+  cudaGraphExec_t exec = nullptr;
+  const cudaError_t inst = cudaGraphInstantiate(&exec, graph, 0);
+  cudaGraphDestroy(graph);
+  if (inst != cudaSuccess) return SHG_ERR_CUDA;
+  if (static_cast<int>(g_graphs.size()) >= kMaxGraphs) {
+    size_t old = 0;
+    for (size_t j = 1; j < g_graphs.size(); ++j)
+      if (g_graphs[j].last_use < g_graphs[old].last_use) old = j;
+    cudaGraphExecDestroy(g_graphs[old].exec);
+    g_graphs.erase(g_graphs.begin() + static_cast<long>(old));
+  }
+  GraphEntry e;
+  e.key = std::move(key);
+  e.exec = exec;
+  e.dev = dev;
+  e.last_use = ++g_tick;
+  g_graphs.push_back(std::move(e));
+  return cuda_status(cudaGraphLaunch(exec, st));
+}
