@@ -71,7 +71,6 @@ struct TcArgs {
   int sa, sb, st;  // ring depths: A staging, B tiles, TMEM A stages
   uint32_t tmem_cols, b_bytes;
   int kc;
-  int prefetch;  // L2 prefetch group size in units (0: off)
   int groups;    // CTA groups, one per run of N tiles (divides n_tiles and gridDim.x)
   unsigned long long wait_ns;
   int drop_commit;
@@ -217,6 +216,59 @@ struct UnitPos {
   int nt, mt, kb;
 };
 
+__device__ __forceinline__ UnitPos decode(long long u, const TcArgs& a) {
+  const long long per_n = static_cast<long long>(a.m_tiles) * a.kblocks;
+  UnitPos p;
+  p.nt = static_cast<int>(u / per_n);
+  const long long r = u - static_cast<long long>(p.nt) * per_n;
+  p.mt = static_cast<int>(r / a.kblocks);
+  p.kb = static_cast<int>(r - static_cast<long long>(p.mt) * a.kblocks);
+  return p;
+}
+
+// Slot and phase parity in a ring of n slots, advanced one unit at a time:
+// the per-unit path of every role does no integer division (a 64-bit
+// division by a run-time value is a long dependent instruction sequence).
+struct Ring {
+  int s = 0;
+  uint32_t ph = 0;
+  __device__ __forceinline__ void next(int n) {
+    if (++s == n) {
+      s = 0;
+      ph ^= 1u;
+    }
+  }
+};
+
+// Position of consecutive units: N tile, M tile, K block and its split into
+// (K piece pp, block sk within the piece), advanced without division.
+struct UnitWalk {
+  int nt, mt, kb, pp, sk;
+  __device__ __forceinline__ void init(long long u, const TcArgs& a) {
+    const UnitPos p = decode(u, a);
+    nt = p.nt;
+    mt = p.mt;
+    kb = p.kb;
+    pp = kb / a.kb_per_p;
+    sk = kb - pp * a.kb_per_p;
+  }
+  __device__ __forceinline__ void next(const TcArgs& a) {
+    if (++sk == a.kb_per_p) {
+      sk = 0;
+      ++pp;
+    }
+    if (++kb == a.kblocks) {
+      kb = 0;
+      pp = 0;
+      sk = 0;
+      if (++mt == a.m_tiles) {
+        mt = 0;
+        ++nt;
+      }
+    }
+  }
+};
+
 // Units of this CTA.  The grid is split into `groups` equal groups, group g
 // owning N tiles [g, g + 1) x n_tiles / groups; the i-th CTAs of all groups
 // cover the same (M tile, K block) range, so the groups read the same A
@@ -229,15 +281,6 @@ __device__ __forceinline__ void cta_range(const TcArgs& a, long long& u0, long l
   const long long per = a.units / G;
   u0 = g * per + static_cast<long long>(i) * per / C;
   u1 = g * per + static_cast<long long>(i + 1) * per / C;
-}
-__device__ __forceinline__ UnitPos decode(long long u, const TcArgs& a) {
-  const long long per_n = static_cast<long long>(a.m_tiles) * a.kblocks;
-  UnitPos p;
-  p.nt = static_cast<int>(u / per_n);
-  const long long r = u - static_cast<long long>(p.nt) * per_n;
-  p.mt = static_cast<int>(r / a.kblocks);
-  p.kb = static_cast<int>(r - static_cast<long long>(p.mt) * a.kblocks);
-  return p;
 }
 
 template <int AMAJ, int BMODE, int PIECES>
@@ -321,39 +364,20 @@ __global__ void __launch_bounds__(kThreads, 1)
     // microseconds, so A must never wait behind the B ring (which frees
     // only when the MMAs complete).
     if (lane == 0) {
-      // L2 prefetch in groups: every `pf` units the next `pf` units' boxes
-      // are requested back to back, so each row of A is fetched from DRAM in
-      // runs of pf x 256 contiguous bytes; the shared-memory loads then hit L2.
-      const int pf = args.prefetch;
+      Ring ra;
+      UnitWalk w;
+      w.init(u0, args);
       long long i = 0;
-      for (long long u = u0; u < u1; ++u, ++i) {
-        const int sa = static_cast<int>(i % SA);
-        const uint32_t pa = static_cast<uint32_t>((i / SA) & 1);
-        if (pf > 0 && (i % pf) == 0) {
-          for (long long v = u + pf; v < u + 2 * pf && v < u1; ++v) {
-            const UnitPos q = decode(v, args);
-            const int qp = q.kb / args.kb_per_p;
-            const int qk = q.kb - qp * args.kb_per_p;
-            if (AMAJ == A_KMAJ) {
-              tma_prefetch_3d(&tmA, qk * kBK, q.mt * kBM, qp);
-              tma_prefetch_3d(&tmA, qk * kBK + 32, q.mt * kBM, qp);
-            } else {
-              for (int j = 0; j < 4; ++j) tma_prefetch_2d(&tmA, q.mt * kBM + 32 * j, q.kb * kBK);
-            }
-          }
-        }
-        const UnitPos p = decode(u, args);
-        const int pp = p.kb / args.kb_per_p;
-        const int sk = p.kb - pp * args.kb_per_p;
-        if (!mbar_wait(bar_aempty + 8 * sa, pa ^ 1u, abort_flag, lim)) break;
-        const uint32_t afull = bar_afull + 8 * sa;
-        const uint32_t adst = smem_u32(a_ring + sa * kABytes);
+      for (long long u = u0; u < u1; ++u, ++i, ra.next(SA), w.next(args)) {
+        if (!mbar_wait(bar_aempty + 8 * ra.s, ra.ph ^ 1u, abort_flag, lim)) break;
+        const uint32_t afull = bar_afull + 8 * ra.s;
+        const uint32_t adst = smem_u32(a_ring + ra.s * kABytes);
         mbar_expect_tx(afull, kABytes);
         if (AMAJ == A_KMAJ) {
-          tma_load_3d(adst, &tmA, afull, sk * kBK, p.mt * kBM, pp);
-          tma_load_3d(adst + 16384, &tmA, afull, sk * kBK + 32, p.mt * kBM, pp);
+          tma_load_3d(adst, &tmA, afull, w.sk * kBK, w.mt * kBM, w.pp);
+          tma_load_3d(adst + 16384, &tmA, afull, w.sk * kBK + 32, w.mt * kBM, w.pp);
         } else {
-          for (int j = 0; j < 4; ++j) tma_load_2d(adst + j * 8192, &tmA, afull, p.mt * kBM + 32 * j, p.kb * kBK);
+          for (int j = 0; j < 4; ++j) tma_load_2d(adst + j * 8192, &tmA, afull, w.mt * kBM + 32 * j, w.kb * kBK);
         }
         issued_a = i + 1;
       }
@@ -363,22 +387,20 @@ __global__ void __launch_bounds__(kThreads, 1)
     // ---------------------------------------------------------- B producer
     if (lane == 0) {
       const uint32_t b_tx = kSplitB ? N * 256u : N * 128u;
+      Ring rb;
+      UnitWalk w;
+      w.init(u0, args);
       long long i = 0;
-      for (long long u = u0; u < u1; ++u, ++i) {
-        const int sb = static_cast<int>(i % SB);
-        const uint32_t pb = static_cast<uint32_t>((i / SB) & 1);
-        const UnitPos p = decode(u, args);
-        const int pp = p.kb / args.kb_per_p;
-        const int sk = p.kb - pp * args.kb_per_p;
-        if (!mbar_wait(bar_bempty + 8 * sb, pb ^ 1u, abort_flag, lim)) break;
-        const uint32_t bfull = bar_bfull + 8 * sb;
-        const uint32_t bdst = smem_u32(b_ring + sb * args.b_bytes);
-        const int brow = pp * args.S_k + sk * kBK;
+      for (long long u = u0; u < u1; ++u, ++i, rb.next(SB), w.next(args)) {
+        if (!mbar_wait(bar_bempty + 8 * rb.s, rb.ph ^ 1u, abort_flag, lim)) break;
+        const uint32_t bfull = bar_bfull + 8 * rb.s;
+        const uint32_t bdst = smem_u32(b_ring + rb.s * args.b_bytes);
+        const int brow = w.pp * args.S_k + w.sk * kBK;
         mbar_expect_tx(bfull, b_tx);
         if (kSplitB) {
-          for (int j = 0; j < N / 32; ++j) tma_load_2d(bdst + j * 8192, &tmB, bfull, p.nt * N + 32 * j, brow);
+          for (int j = 0; j < N / 32; ++j) tma_load_2d(bdst + j * 8192, &tmB, bfull, w.nt * N + 32 * j, brow);
         } else {
-          for (int j = 0; j < N / 64; ++j) tma_load_2d(bdst + j * 8192, &tmB, bfull, p.nt * N + 64 * j, brow);
+          for (int j = 0; j < N / 64; ++j) tma_load_2d(bdst + j * 8192, &tmB, bfull, w.nt * N + 64 * j, brow);
         }
         issued_b = i + 1;
       }
@@ -391,6 +413,7 @@ __global__ void __launch_bounds__(kThreads, 1)
       const uint32_t idesc = idesc_f16(kFmt, 0u, 1u, kBM, N);
       const uint32_t b_piece = static_cast<uint32_t>(N / 64) * 8192u;
       long long u = u0, i = 0, cc = 0;
+      Ring rt, rb;
       int seg = 0;
       bool ok = true;
       while (ok && u < u1) {
@@ -408,11 +431,10 @@ __global__ void __launch_bounds__(kThreads, 1)
           tc_fence_after();
           const uint32_t tm_d = tmem_base + d * N;
           const long long chunk_start = u;
-          for (; u < chunk_end; ++u, ++i) {
-            const int st = static_cast<int>(i % ST), sb = static_cast<int>(i % SB);
-            const uint32_t pt = static_cast<uint32_t>((i / ST) & 1), pb = static_cast<uint32_t>((i / SB) & 1);
-            if (!mbar_wait(bar_tfull + 8 * st, pt, abort_flag, lim) ||
-                !mbar_wait((kSplitB ? bar_bready : bar_bfull) + 8 * sb, pb, abort_flag, lim)) {
+          for (; u < chunk_end; ++u, ++i, rt.next(ST), rb.next(SB)) {
+            const int st = rt.s, sb = rb.s;
+            if (!mbar_wait(bar_tfull + 8 * st, rt.ph, abort_flag, lim) ||
+                !mbar_wait((kSplitB ? bar_bready : bar_bfull) + 8 * sb, rb.ph, abort_flag, lim)) {
               ok = false;
               break;
             }
@@ -458,11 +480,10 @@ __global__ void __launch_bounds__(kThreads, 1)
     const int r = 32 * q + lane;  // tile row == TMEM lane of this thread
     const uint32_t lane_off = static_cast<uint32_t>(32 * q) << 16;
     float vmax = 0.0f;
-    long long i = 0;
-    for (long long u = u0; u < u1; ++u, ++i) {
-      const int sa = static_cast<int>(i % SA), sb = static_cast<int>(i % SB), st = static_cast<int>(i % ST);
-      const uint32_t pa = static_cast<uint32_t>((i / SA) & 1), pb = static_cast<uint32_t>((i / SB) & 1);
-      const uint32_t pt = static_cast<uint32_t>((i / ST) & 1);
+    Ring ra, rb, rt;
+    for (long long u = u0; u < u1; ++u, ra.next(SA), rb.next(SB), rt.next(ST)) {
+      const int sa = ra.s, sb = rb.s, st = rt.s;
+      const uint32_t pa = ra.ph, pb = rb.ph, pt = rt.ph;
       if (kSplitB) {
         if (!warp_wait(bar_bfull + 8 * sb, pb, abort_flag, lim, lane)) {
           *abort_flag = 1;
