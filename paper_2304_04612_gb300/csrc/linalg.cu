@@ -155,11 +155,17 @@ __global__ void __launch_bounds__(1024) chol_inv_kernel(int k, const double* __r
     if (tid == 0) pivot(j + 1);
     __syncthreads();
   }
-  // R in FP32: R[i][l] = a[i][l] / R[i][i], 1/R[i][i] = sqrt(1/d_i)
-  for (int i = tid; i < k; i += nt) rinv[i] = static_cast<float>(sqrt(dinv[i]));
-  for (int e = tid; e < k * k; e += nt) {
-    const int i = e / k, l = e - i * k;
-    if (l > i) rf[e] = static_cast<float>(a[e] * sqrt(dinv[i]));
+  // R in FP32: R[i][l] = a[i][l] / R[i][i], 1/R[i][i] = sqrt(1/d_i) (one
+  // FP64 square root per row, kept in dinv)
+  for (int i = tid; i < k; i += nt) {
+    const double r = sqrt(dinv[i]);
+    rinv[i] = static_cast<float>(r);
+    dinv[i] = r;
+  }
+  __syncthreads();
+  for (int i = warp; i < k; i += nw) {
+    const double r = dinv[i];
+    for (int l = i + 1 + lane; l < k; l += 32) rf[i * k + l] = static_cast<float>(a[i * k + l] * r);
   }
   __syncthreads();
   for (int j = tid; j < k; j += nt) {
@@ -260,9 +266,12 @@ __global__ void __launch_bounds__(1024) jacobi_kernel(int k, const double* __res
   JPair* pairs = reinterpret_cast<JPair*>(smi);  // [2][half]
   int* tmap = smi + 8 * kp;                      // [2][kp]: pair of index
   int* smap = tmap + 2 * kp;                     // [2][kp]: side of index
-  float* A = SMEM ? reinterpret_cast<float*>(smap + 2 * kp) : scratch;
-  float* B = A + kp * ld;
-  float* Vt = B + kp * ld;
+  // One fixed base; the two A buffers alternate by an integer index (no
+  // loop-carried pointer swap, so shared accesses stay shared accesses).
+  float* const M0 = SMEM ? reinterpret_cast<float*>(smap + 2 * kp) : scratch;
+  float* const Vt = M0 + 2 * kp * ld;
+  int abuf = 0;
+  float* A = M0;
   __shared__ int last_rot;
   __shared__ double red[32];
   __shared__ double dmax;
@@ -282,20 +291,27 @@ __global__ void __launch_bounds__(1024) jacobi_kernel(int k, const double* __res
     const int i = e / ldv, j = e - i * ldv;
     Vt[e] = (i == j) ? 1.0f : 0.0f;
   }
+  // The last ceil(kp/2 / 32) warps only build rotations (rotation thread rt
+  // owns pair rt); the others only apply them, so a round costs the longer
+  // of the two instead of their sum.
+  const int rot_warps = (half + 31) / 32;
+  const int upd_warps = nw - rot_warps;
+  const int rt = tid - upd_warps * 32;
+  const bool rotor = rt >= 0 && rt < half;
   // pairing of round 0 and, per rotation thread, its running positions
   int pa = 0, pb = 0;
-  if (tid < half) {
-    pa = (tid == 0) ? 0 : tid;                   // ((0 + i - 1) mod n1) + 1
-    pb = ((n1 - 1 - tid) % n1 + n1) % n1 + 1;    // ((0 - 1 - i) mod n1) + 1
+  if (rotor) {
+    pa = (rt == 0) ? 0 : rt;                    // ((0 + i - 1) mod n1) + 1
+    pb = ((n1 - 1 - rt) % n1 + n1) % n1 + 1;    // ((0 - 1 - i) mod n1) + 1
   }
   __syncthreads();
-  if (tid < half) {
+  if (rotor) {
     const int p = min(pa, pb), q = max(pa, pb);
     float c, s;
     if (jac_rot(A[p * ld + p], A[q * ld + q], A[p * ld + q], c, s)) last_rot = 0;
-    pairs[tid] = JPair{p, q, c, s};
-    tmap[p] = tid;
-    tmap[q] = tid;
+    pairs[rt] = JPair{p, q, c, s};
+    tmap[p] = rt;
+    tmap[q] = rt;
     smap[p] = 0;
     smap[q] = 1;
   }
@@ -303,11 +319,13 @@ __global__ void __launch_bounds__(1024) jacobi_kernel(int k, const double* __res
   int buf = 0;
   for (int sweep = 0; sweep < 40; ++sweep) {
     for (int r = 0; r < n1; ++r) {
+      A = M0 + abuf * (kp * ld);
+      float* const B = M0 + (abuf ^ 1) * (kp * ld);
       const JPair* cur = pairs + buf * half;
       const int* ct = tmap + buf * kp;
       const int* cs = smap + buf * kp;
       // J^T A J by pair blocks
-      for (int t = warp; t < half; t += nw) {
+      for (int t = warp; t < half && warp < upd_warps; t += upd_warps) {
         const JPair P1 = cur[t];
         for (int u = t + lane; u < half; u += 32) {
           const JPair P2 = cur[u];
@@ -334,7 +352,7 @@ __global__ void __launch_bounds__(1024) jacobi_kernel(int k, const double* __res
       }
       // V <- V J on the transposed rows p, q
       const int nv4 = ldv >> 2;
-      for (int w = tid; w < half * nv4; w += nt) {
+      for (int w = tid; w < half * nv4 && warp < upd_warps; w += upd_warps * 32) {
         const int t = w / nv4, c4 = (w - t * nv4) * 4;
         const JPair P = cur[t];
         float4* vp = reinterpret_cast<float4*>(Vt + P.p * ldv + c4);
@@ -346,8 +364,8 @@ __global__ void __launch_bounds__(1024) jacobi_kernel(int k, const double* __res
                           __fmaf_rn(P.s, x.z, __fmul_rn(P.c, y.z)), __fmaf_rn(P.s, x.w, __fmul_rn(P.c, y.w)));
       }
       // rotations of the next round from the same old A
-      if (tid < half) {
-        pa = (tid == 0) ? 0 : (pa == n1 ? 1 : pa + 1);
+      if (rotor) {
+        pa = (rt == 0) ? 0 : (pa == n1 ? 1 : pa + 1);
         pb = (pb == n1) ? 1 : pb + 1;
         const int p = min(pa, pb), q = max(pa, pb);
         const int tp = ct[p], tq = ct[q], sp = cs[p], sq = cs[q];
@@ -360,16 +378,14 @@ __global__ void __launch_bounds__(1024) jacobi_kernel(int k, const double* __res
         JPair* nxt = pairs + (buf ^ 1) * half;
         int* nt_ = tmap + (buf ^ 1) * kp;
         int* ns_ = smap + (buf ^ 1) * kp;
-        nxt[tid] = JPair{p, q, c, s};
-        nt_[p] = tid;
-        nt_[q] = tid;
+        nxt[rt] = JPair{p, q, c, s};
+        nt_[p] = rt;
+        nt_[q] = rt;
         ns_[p] = 0;
         ns_[q] = 1;
       }
       __syncthreads();
-      float* t = A;
-      A = B;
-      B = t;
+      abuf ^= 1;
       buf ^= 1;
     }
     if (last_rot < sweep) break;
@@ -555,7 +571,11 @@ int jacobi_eig(int64_t k, const double* G, float* V, float* scratch, cudaStream_
   const size_t mats = jacobi_scratch_floats(k) * sizeof(float);
   const int in_smem = smem_fits(prm + mats);
   const size_t smem = in_smem ? prm + mats : prm;
-  const int threads = block_threads(kp * kp / 8);
+  // update warps for about 8 elements per thread, plus the rotation warps
+  const int rot = static_cast<int>((kp / 2 + 31) / 32) * 32;
+  int threads = block_threads(kp * kp / 16) + rot;
+  if (threads > 1024) threads = 1024;
+  if (threads - rot < 64) return SHG_ERR_UNSUPPORTED;
   if (in_smem) {
     if (cudaFuncSetAttribute(jacobi_kernel<true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                              static_cast<int>(smem)) != cudaSuccess)
