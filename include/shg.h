@@ -254,6 +254,20 @@ int shg_round_f16(int64_t rows, int64_t cols, const float* x, int64_t ldx,
                   uint16_t* y, int64_t ldy, void* stream);
 
 /*
+ * Diagnostic of the failure path of the tensor-core kernel (not part of the
+ * method).  Runs the SHGEMM-FP16 kernel of shgemm_project on (m, n, k) with
+ * the "hi accumulator ready" signal suppressed, so one of its waits can never
+ * be satisfied, and every device-side wait limited to wait_ns nanoseconds
+ * (1e5 <= wait_ns <= 2e9).  The kernel gives up, lets its outstanding TMA
+ * loads and MMAs finish, releases its tensor memory, sets SHG_FLAG_TIMEOUT
+ * in *d_flags and returns; the context stays usable.  Y receives undefined
+ * values.  Arguments as for shgemm_project with trans_a = 0.
+ */
+int shg_diag_wait_timeout(int64_t m, int64_t n, int64_t k, const float* A, int64_t lda,
+                          const uint16_t* omega, int64_t ldo, float* Y, int64_t ldy,
+                          uint64_t wait_ns, int32_t* d_flags, void* stream);
+
+/*
  * A14. A-posteriori residual estimate of a basis Q of the range of A
  * (Theorems 1 and 3: for G with i.i.d. entries of variance alpha,
  * E ||S G||_F^2 = alpha t ||S||_F^2):

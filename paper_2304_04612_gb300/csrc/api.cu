@@ -140,6 +140,18 @@ int shgemm_project(int64_t m, int64_t n, int64_t k, const float* A, int64_t lda,
   }
 }
 
+int shg_diag_wait_timeout(int64_t m, int64_t n, int64_t k, const float* A, int64_t lda, const uint16_t* omega,
+                          int64_t ldo, float* Y, int64_t ldy, uint64_t wait_ns, int32_t* d_flags, void* stream) {
+  if (m < 1 || n < 1 || k < 1 || !A || !omega || !Y || !d_flags) return SHG_ERR_INVALID_ARG;
+  if (lda < n || ldo < k || ldy < k) return SHG_ERR_INVALID_ARG;
+  if (wait_ns < 100000ull || wait_ns > 2000000000ull) return SHG_ERR_INVALID_ARG;
+  TcTestHooks h;
+  h.wait_ns = wait_ns;
+  h.drop_commit = 1;
+  return tc_gemm(A_KMAJ, B_F16, 2, m, k, n, 1, A, lda, 0, omega, ldo, Y, ldy, 0, d_flags,
+                 static_cast<cudaStream_t>(stream), &h);
+}
+
 int shg_gemm_split3(int64_t m, int64_t n, int64_t kk, const float* A, int64_t lda, int trans_a, const float* B,
                     int64_t ldb, float* C, int64_t ldc, int accumulate, int32_t* d_flags, void* stream) {
   if (m < 1 || n < 1 || kk < 1 || !A || !B || !C || !d_flags) return SHG_ERR_INVALID_ARG;
