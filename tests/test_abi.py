@@ -91,3 +91,25 @@ def test_sketch_and_estimator_host_validation(lib):
     assert lib.shg_sketch_loss_grad(100, 80, 20, null, 80, null, 20, 1, null, 20, null, null, 0, null, null) == 1
     assert lib.shg_round_f16(-1, 4, null, 4, null, 4, null) == 1
     assert lib.shg_round_f16(0, 4, null, 4, null, 4, null) == 0
+
+
+def test_batched_workspace_host_validation(lib):
+    sz = ctypes.c_size_t()
+    m = (ctypes.c_int64 * 3)(512, 300, 2048)
+    n = (ctypes.c_int64 * 3)(256, 300, 1024)
+    r = (ctypes.c_int64 * 3)(32, 16, 64)
+    assert lib.shg_rsvd_batched_workspace_size(3, m, n, r, 16, 1, ctypes.byref(sz)) == 0
+    one = ctypes.c_size_t()
+    assert lib.shg_rsvd_workspace_size(2048, 1024, 64, 16, 1, ctypes.byref(one)) == 0
+    # one slice per branch (3 branches here), each at least the largest problem's need
+    assert sz.value >= 3 * one.value
+    bad = (ctypes.c_int64 * 3)(32, 300, 64)                          # rank + s > min(m, n)
+    assert lib.shg_rsvd_batched_workspace_size(3, m, n, bad, 16, 1, ctypes.byref(sz)) == 1
+    assert lib.shg_rsvd_batched_workspace_size(0, m, n, r, 16, 1, ctypes.byref(sz)) == 1
+    null = ctypes.c_void_p(0)
+    # NULL pointer arrays are rejected before any CUDA call
+    assert lib.shg_rsvd_batched(3, m, n, r, 16, 1, null, null, null, null, 0, null, null, null, null, 0, 0, 0,
+                                null, null) == 1
+    # diagnostic entry: out-of-range wait limit rejected on the host
+    assert lib.shg_diag_wait_timeout(8, 8, 8, ctypes.c_void_p(16), 8, ctypes.c_void_p(16), 8, ctypes.c_void_p(16), 8,
+                                     10, ctypes.c_void_p(16), null) == 1
