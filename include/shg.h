@@ -83,6 +83,21 @@ int shg_gaussian_f16(uint64_t seed, uint64_t offset, int64_t rows, int64_t cols,
                      uint16_t* out, int64_t ld, void* stream);
 
 /*
+ * Sparse sign test matrix (Sec. 3.4: Eq. sp-rand of Sec. 2.2 without the
+ * sqrt(s) factor, which the range finder does not need).  out[r*ld + c]
+ * receives +1, 0 or -1 (exact FP16 bits 0x3C00, 0, 0xBC00) from 32-bit word
+ * e mod 4 (e = r*cols + c) of Philox4x32-10 block (e div 4) + offset under
+ * key (seed lo, seed hi), the stream of shg_gaussian_f16: +1 when the word is
+ * below T, -1 when it is at least 2^32 - T, 0 otherwise, with
+ * T = min(2^31, floor(2^32 / (2 s) + 1/2)); s >= 1 (1: Rademacher signs,
+ * 3: Achlioptas, sqrt(n): very sparse).  The result feeds shgemm_project
+ * unchanged: its values are exact in FP16.
+ * Errors: rows, cols < 0, ld < cols, s < 1, out == NULL (when rows*cols > 0).
+ */
+int shg_sparse_sign_f16(uint64_t seed, uint64_t offset, int64_t rows, int64_t cols, double s,
+                        uint16_t* out, int64_t ld, void* stream);
+
+/*
  * A2-A4. Random projection Y = op(A) * Omega (Eq. rp-vec) by SHGEMM
  * (Sec. 4.1, Eqs. shgemm-1..3): A is split in shared memory into
  * hi = RN_fp16(a) and lo = RN_fp16((a - hi) * 2^11), both multiplied with the

@@ -10,6 +10,7 @@ only provides device memory and streams.
 Functions (same names as the C entry points)
 --------------------------------------------
 shg_gaussian_f16   FP16 Gaussian test matrix (Philox4x32-10 + Box-Muller, RN)
+shg_sparse_sign_f16  sparse {-1, 0, +1} test matrix (Sec. 3.4), same Philox stream
 shgemm_project     Y = op(A) Omega by SHGEMM (or the BF16 / FP32 SIMT variants)
 shg_gemm_split3    FP32-accurate op(A) B of two FP32 matrices (TCEC split)
 shg_sgemm          plain FP32 SIMT GEMM (the single-precision baseline)
@@ -91,6 +92,17 @@ def shg_gaussian_f16(seed: int, offset: int, rows: int, cols: int, out: torch.Te
     ld = _mat(out, "out", (torch.float16,))
     _check(_lib.load().shg_gaussian_f16(seed, offset, rows, cols, _ptr(out), ld, _stream(stream)),
            "shg_gaussian_f16")
+    return out
+
+
+def shg_sparse_sign_f16(seed: int, offset: int, rows: int, cols: int, s: float = 3.0,
+                        out: torch.Tensor | None = None, stream=None) -> torch.Tensor:
+    """Sparse sign test matrix of {-1, 0, +1} in FP16 (Sec. 3.4), P(nonzero) ~ 1/s."""
+    if out is None:
+        out = torch.empty(rows, cols, dtype=torch.float16, device="cuda")
+    ld = _mat(out, "out", (torch.float16,))
+    _check(_lib.load().shg_sparse_sign_f16(seed, offset, rows, cols, float(s), _ptr(out), ld, _stream(stream)),
+           "shg_sparse_sign_f16")
     return out
 
 

@@ -24,6 +24,7 @@ SIGNATURES = {
     "shg_version": (c_int, []),
     "shg_flags_status": (c_int, [ctypes.c_int32]),
     "shg_gaussian_f16": (c_int, [c_u64, c_u64, c_i64, c_i64, c_vp, c_i64, c_vp]),
+    "shg_sparse_sign_f16": (c_int, [c_u64, c_u64, c_i64, c_i64, ctypes.c_double, c_vp, c_i64, c_vp]),
     "shgemm_project": (c_int, [c_i64, c_i64, c_i64, c_vp, c_i64, c_int, c_vp, c_i64, c_vp, c_i64,
                                c_int, c_vp, c_vp]),
     "shg_gemm_split3": (c_int, [c_i64, c_i64, c_i64, c_vp, c_i64, c_int, c_vp, c_i64, c_vp, c_i64,

@@ -4,7 +4,9 @@
 //
 // Element e = r * cols + c takes normal (e mod 4) of Philox block
 // (e div 4) + offset under key (seed lo, seed hi): the value depends only on
-// the element's logical index, never on the launch shape.
+// the element's logical index, never on the launch shape.  The sparse sign
+// matrix of Sec. 3.4 uses the raw 32-bit words of the same stream.
+#include <cmath>
 #include <cuda_fp16.h>
 
 #include "internal.h"
@@ -65,8 +67,53 @@ __global__ void gaussian_f16_kernel(uint2 key, unsigned long long offset, long l
   }
 }
 
+// Sparse sign test matrix (Sec. 3.4): element e takes 32-bit word e mod 4 of
+// the same Philox block (e div 4) + offset and becomes +1 below t, -1 at or
+// above 2^32 - t, 0 otherwise (exact FP16 values 0x3C00, 0xBC00, 0).
+__global__ void sparse_sign_f16_kernel(uint2 key, unsigned long long offset, long long rows, long long cols,
+                                       uint32_t t, __half* out, long long ld) {
+  const long long n = rows * cols;
+  const long long nblk = (n + 3) / 4;
+  const uint32_t hi = 0xFFFFFFFFu - t;  // w >= 2^32 - t  <=>  w > 2^32 - 1 - t
+  for (long long b = blockIdx.x * static_cast<long long>(blockDim.x) + threadIdx.x; b < nblk;
+       b += static_cast<long long>(gridDim.x) * blockDim.x) {
+    const unsigned long long ctr = b + offset;
+    const uint4 x = philox4x32_10(make_uint4(static_cast<uint32_t>(ctr), static_cast<uint32_t>(ctr >> 32), 0u, 0u), key);
+    const uint32_t w[4] = {x.x, x.y, x.z, x.w};
+#pragma unroll
+    for (int j = 0; j < 4; ++j) {
+      const long long e = 4 * b + j;
+      if (e < n) {
+        const long long r = e / cols, c = e - r * cols;
+        const unsigned short bits = (w[j] < t) ? 0x3C00u : (w[j] > hi ? 0xBC00u : 0u);
+        out[r * ld + c] = __ushort_as_half(bits);
+      }
+    }
+  }
+}
+
 }  // namespace
 }  // namespace shg
+
+extern "C" int shg_sparse_sign_f16(uint64_t seed, uint64_t offset, int64_t rows, int64_t cols, double s,
+                                   uint16_t* out, int64_t ld, void* stream) {
+  if (rows < 0 || cols < 0 || ld < cols || !(s >= 1.0)) return SHG_ERR_INVALID_ARG;
+  if (rows == 0 || cols == 0) return SHG_OK;
+  if (!out) return SHG_ERR_INVALID_ARG;
+  // T = floor(2^32 / (2 s) + 1/2), at most 2^31
+  double td = std::floor(4294967296.0 / (2.0 * s) + 0.5);
+  if (td > 2147483648.0) td = 2147483648.0;
+  const uint32_t t = static_cast<uint32_t>(td);
+  const long long nblk = (rows * cols + 3) / 4;
+  const int sms = shg::sm_count();
+  if (sms <= 0) return SHG_ERR_CUDA;
+  const long long want = (nblk + 255) / 256;
+  const int grid = static_cast<int>(want < 8ll * sms ? want : 8ll * sms);
+  const uint2 key = make_uint2(static_cast<uint32_t>(seed), static_cast<uint32_t>(seed >> 32));
+  shg::sparse_sign_f16_kernel<<<grid, 256, 0, static_cast<cudaStream_t>(stream)>>>(
+      key, offset, rows, cols, t, reinterpret_cast<__half*>(out), ld);
+  return shg::cuda_status(cudaGetLastError());
+}
 
 extern "C" int shg_gaussian_f16(uint64_t seed, uint64_t offset, int64_t rows, int64_t cols, uint16_t* out,
                                 int64_t ld, void* stream) {
