@@ -175,12 +175,18 @@ def main():
     ap.add_argument("--case", type=int, nargs=2, metavar=("MN", "K"),
                     help="profiling case: only W + K launches of one m=n=MN, k=K SHGEMM (no JSON contract line)")
     ap.add_argument("--variant", default="f16", help="variant for --case")
+    ap.add_argument("--factor", choices=["rsvd", "hosvd"],
+                    help="profiling case: W + K calls of the randomized SVD of the 1024^2 planted matrix "
+                         "or of RP-HOSVD of the 512^3 Tucker tensor (no JSON contract line)")
     args = ap.parse_args()
     if args.impl == "reference":
         run_reference(args)
         return
     if args.case:
         run_case(args)
+        return
+    if args.factor:
+        run_factor(args)
         return
 
     import torch
@@ -300,6 +306,39 @@ def main():
         print(json.dumps(line), flush=True)
     if ws > 1:
         torch.distributed.destroy_process_group()
+
+
+def run_factor(args):
+    """One factorization workload, for ncu launch lists: W warm-up calls then K timed ones."""
+    import torch
+    import __graft_entry__ as g
+    g.build()
+    import paper_2304_04612_gb300 as shg
+    from synth import rsvd_planted, tucker, hosvd_omegas
+    dev = torch.device("cuda", 0)
+    fl = shg.new_flags(dev)
+    if args.factor == "rsvd":
+        A_h, Om_h = rsvd_planted(1024, 1024, rate=8.0, seed_a=0, seed_omega=1, k=64)
+        A, Om = torch.from_numpy(A_h).to(dev), torch.from_numpy(Om_h).to(dev)
+        ws = torch.empty(shg.rsvd_workspace_size(1024, 1024, 32, 32, 0), dtype=torch.uint8, device=dev)
+        fn = lambda: shg.shg_rsvd(A, Om, 32, 32, 0, args.variant, workspace=ws, flags=fl, check=False)
+    else:
+        dims, J = (512, 512, 512), (48, 48, 48)
+        X_h, _, _ = tucker(dims, (32, 32, 32), seed=3, noise_std=1e-4)
+        X = torch.from_numpy(X_h).to(dev)
+        oms = [torch.from_numpy(o).to(dev) for o in hosvd_omegas(dims, J, seed=3)]
+        fn = lambda: shg.shg_rp_hosvd(X, oms, J, args.variant, flags=fl, check=False)
+    for _ in range(args.warmup):
+        fn()
+    torch.cuda.synchronize()
+    a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    a.record()
+    for _ in range(args.steps):
+        fn()
+    b.record()
+    torch.cuda.synchronize()
+    shg.check_flags(fl, args.factor)
+    print(json.dumps({"factor": args.factor, "variant": args.variant, "ms": a.elapsed_time(b) / args.steps}))
 
 
 def run_case(args):
