@@ -11,6 +11,7 @@
 // The eigensolver is a parallel cyclic Jacobi method (round-robin pairing)
 // in FP32 on the scaled Gram matrix; eigenvalues are then refined as FP64
 // Rayleigh quotients v^T G v / v^T v with the FP64 Gram matrix.
+#include <cooperative_groups.h>
 #include <cuda_fp16.h>
 
 #include "internal.h"
@@ -396,6 +397,160 @@ __global__ void __launch_bounds__(1024) jacobi_kernel(int k, const double* __res
   }
 }
 
+// The same Jacobi method for k too large for one SM's shared memory: A (two
+// buffers), V^T and the round parameters live in global memory (they stay in
+// L2), every round is spread over the whole grid of a cooperative launch and
+// ends with one grid barrier.  Shared data is read with ld.global.cg (L2,
+// never a stale L1 line written by another SM in an earlier round).  Layout
+// of `scratch`: A buffers (2 kp (kp + 1) floats), V^T (kp x ldv), then the
+// parameters: JPair[2][kp/2], pair-of-index[2][kp], side-of-index[2][kp],
+// last_rot.
+__global__ void __launch_bounds__(256) jacobi_grid_kernel(int k, const double* __restrict__ G,
+                                                         float* __restrict__ Vout, float* scratch) {
+  namespace cg = cooperative_groups;
+  cg::grid_group grid = cg::this_grid();
+  const int kp = k + (k & 1);
+  const int half = kp / 2, n1 = kp - 1;
+  const int ld = kp + 1, ldv = (kp + 3) & ~3;
+  float* const M0 = scratch;
+  float* const Vt = M0 + 2 * kp * ld;
+  JPair* const pairs = reinterpret_cast<JPair*>(Vt + kp * ldv);  // 16-byte aligned: offsets are multiples of 4 floats
+  int* const tmap = reinterpret_cast<int*>(pairs + 2 * half);
+  int* const smap = tmap + 2 * kp;
+  volatile int* const last_rot = smap + 2 * kp;
+  const long long gtid = static_cast<long long>(blockIdx.x) * blockDim.x + threadIdx.x;
+  const long long gnt = static_cast<long long>(gridDim.x) * blockDim.x;
+  __shared__ double red[32];
+  __shared__ double dmax;
+  diag_max(k, G, red, &dmax);  // every block forms the scale itself
+  __syncthreads();
+  const double sigma = ldexp(1.0, -((dmax > 0.0) ? ilogb(dmax) : 0));
+  for (long long e = gtid; e < static_cast<long long>(kp) * kp; e += gnt) {
+    const int i = static_cast<int>(e / kp), j = static_cast<int>(e - static_cast<long long>(i) * kp);
+    float v = 0.0f;
+    if (i < k && j < k) v = static_cast<float>(G[min(i, j) * k + max(i, j)] * sigma);
+    M0[i * ld + j] = v;
+  }
+  for (long long e = gtid; e < static_cast<long long>(kp) * ldv; e += gnt) {
+    const int i = static_cast<int>(e / ldv), j = static_cast<int>(e - static_cast<long long>(i) * ldv);
+    Vt[e] = (i == j) ? 1.0f : 0.0f;
+  }
+  if (gtid == 0) *last_rot = -1;
+  // rotation thread rt = gtid < half owns pair rt; its running circle positions
+  const bool rotor = gtid < half;
+  const int rt = static_cast<int>(gtid);
+  int pa = 0, pb = 0;
+  if (rotor) {
+    pa = (rt == 0) ? 0 : rt;
+    pb = ((n1 - 1 - rt) % n1 + n1) % n1 + 1;
+  }
+  grid.sync();
+  if (rotor) {
+    const int p = min(pa, pb), q = max(pa, pb);
+    float c, s;
+    if (jac_rot(__ldcg(M0 + p * ld + p), __ldcg(M0 + q * ld + q), __ldcg(M0 + p * ld + q), c, s)) *last_rot = 0;
+    pairs[rt] = JPair{p, q, c, s};
+    tmap[p] = rt;
+    tmap[q] = rt;
+    smap[p] = 0;
+    smap[q] = 1;
+  }
+  grid.sync();
+  int abuf = 0, buf = 0;
+  const int nv4 = ldv >> 2;
+  for (int sweep = 0; sweep < 40; ++sweep) {
+    for (int r = 0; r < n1; ++r) {
+      const float* A = M0 + abuf * (kp * ld);
+      float* B = M0 + (abuf ^ 1) * (kp * ld);
+      const JPair* cur = pairs + buf * half;
+      const int* ct = tmap + buf * kp;
+      const int* cs = smap + buf * kp;
+      auto ldp = [&](int t) {
+        JPair P;
+        const int4 v = __ldcg(reinterpret_cast<const int4*>(cur + t));
+        P.p = v.x;
+        P.q = v.y;
+        P.c = __int_as_float(v.z);
+        P.s = __int_as_float(v.w);
+        return P;
+      };
+      // J^T A J by pair blocks (t, u), u >= t
+      for (long long idx = gtid; idx < static_cast<long long>(half) * half; idx += gnt) {
+        const int t = static_cast<int>(idx / half), u = static_cast<int>(idx - static_cast<long long>(t) * half);
+        if (u < t) continue;
+        const JPair P1 = ldp(t), P2 = ldp(u);
+        float n00, n01, n10, n11;
+        jac_block(__ldcg(A + P1.p * ld + P2.p), __ldcg(A + P1.p * ld + P2.q), __ldcg(A + P1.q * ld + P2.p),
+                  __ldcg(A + P1.q * ld + P2.q), P1.c, P1.s, P2.c, P2.s, n00, n01, n10, n11);
+        if (u == t) {
+          if (P1.s != 0.0f) n01 = 0.0f;
+          B[P1.p * ld + P1.p] = n00;
+          B[P1.q * ld + P1.q] = n11;
+          B[P1.p * ld + P1.q] = n01;
+          B[P1.q * ld + P1.p] = n01;
+        } else {
+          B[P1.p * ld + P2.p] = n00;
+          B[P2.p * ld + P1.p] = n00;
+          B[P1.p * ld + P2.q] = n01;
+          B[P2.q * ld + P1.p] = n01;
+          B[P1.q * ld + P2.p] = n10;
+          B[P2.p * ld + P1.q] = n10;
+          B[P1.q * ld + P2.q] = n11;
+          B[P2.q * ld + P1.q] = n11;
+        }
+      }
+      // V <- V J on the transposed rows p, q
+      for (long long w = gtid; w < static_cast<long long>(half) * nv4; w += gnt) {
+        const int t = static_cast<int>(w / nv4), c4 = static_cast<int>(w - static_cast<long long>(t) * nv4) * 4;
+        const JPair P = ldp(t);
+        float4* vp = reinterpret_cast<float4*>(Vt + P.p * ldv + c4);
+        float4* vq = reinterpret_cast<float4*>(Vt + P.q * ldv + c4);
+        const float4 x = __ldcg(vp), y = __ldcg(vq);
+        *vp = make_float4(__fmaf_rn(-P.s, y.x, __fmul_rn(P.c, x.x)), __fmaf_rn(-P.s, y.y, __fmul_rn(P.c, x.y)),
+                          __fmaf_rn(-P.s, y.z, __fmul_rn(P.c, x.z)), __fmaf_rn(-P.s, y.w, __fmul_rn(P.c, x.w)));
+        *vq = make_float4(__fmaf_rn(P.s, x.x, __fmul_rn(P.c, y.x)), __fmaf_rn(P.s, x.y, __fmul_rn(P.c, y.y)),
+                          __fmaf_rn(P.s, x.z, __fmul_rn(P.c, y.z)), __fmaf_rn(P.s, x.w, __fmul_rn(P.c, y.w)));
+      }
+      // rotations of the next round from the same old A
+      if (rotor) {
+        pa = (rt == 0) ? 0 : (pa == n1 ? 1 : pa + 1);
+        pb = (pb == n1) ? 1 : pb + 1;
+        const int p = min(pa, pb), q = max(pa, pb);
+        const int tp = __ldcg(ct + p), tq = __ldcg(ct + q), sp = __ldcg(cs + p), sq = __ldcg(cs + q);
+        const JPair Pp = ldp(tp), Pq = ldp(tq);
+        auto elem = [&](const JPair& P1, int sx, const JPair& P2, int sy, bool same) {
+          float n00, n01, n10, n11;
+          jac_block(__ldcg(A + P1.p * ld + P2.p), __ldcg(A + P1.p * ld + P2.q), __ldcg(A + P1.q * ld + P2.p),
+                    __ldcg(A + P1.q * ld + P2.q), P1.c, P1.s, P2.c, P2.s, n00, n01, n10, n11);
+          if (same && sx != sy && P1.s != 0.0f) return 0.0f;
+          return sx ? (sy ? n11 : n10) : (sy ? n01 : n00);
+        };
+        const float app = elem(Pp, sp, Pp, sp, true);
+        const float aqq = elem(Pq, sq, Pq, sq, true);
+        const float apq = (tp <= tq) ? elem(Pp, sp, Pq, sq, tp == tq) : elem(Pq, sq, Pp, sp, false);
+        float c, s;
+        if (jac_rot(app, aqq, apq, c, s)) *last_rot = (r + 1 == n1) ? sweep + 1 : sweep;
+        JPair* nxt = pairs + (buf ^ 1) * half;
+        int* nt_ = tmap + (buf ^ 1) * kp;
+        int* ns_ = smap + (buf ^ 1) * kp;
+        nxt[rt] = JPair{p, q, c, s};
+        nt_[p] = rt;
+        nt_[q] = rt;
+        ns_[p] = 0;
+        ns_[q] = 1;
+      }
+      grid.sync();
+      abuf ^= 1;
+      buf ^= 1;
+    }
+    if (*last_rot < sweep) break;
+  }
+  for (long long e = gtid; e < static_cast<long long>(k) * k; e += gnt) {
+    const int i = static_cast<int>(e / k), j = static_cast<int>(e - static_cast<long long>(i) * k);
+    Vout[e] = __ldcg(Vt + j * ldv + i);
+  }
+}
+
 // lambda_i = v_i^T G v_i / v_i^T v_i (FP64 Rayleigh quotient, G symmetric
 // from its upper triangle; the FP32 rotations leave |v_i| = 1 only to
 // ~1e-5); one CTA per i.  nrm[i] = |v_i| (FP64).
@@ -483,7 +638,9 @@ int smem_fits(size_t bytes) { return bytes <= 200 * 1024 ? 1 : 0; }
 // and V^T (kp x ldv).
 size_t jacobi_scratch_floats(int64_t k) {
   const int64_t kp = k + (k & 1), ldv = (kp + 3) & ~int64_t(3);
-  return static_cast<size_t>(2 * kp * (kp + 1) + kp * ldv);
+  // matrices, then (grid version) JPair[2][kp/2] (4 kp floats), the two index
+  // maps (2 x 2 kp ints) and the flag
+  return static_cast<size_t>(2 * kp * (kp + 1) + kp * ldv + 8 * kp + 64);
 }
 
 // One-CTA kernels: about `work` elements per barrier phase, a few per thread.
@@ -582,10 +739,24 @@ int jacobi_eig(int64_t k, const double* G, float* V, float* scratch, cudaStream_
       return SHG_ERR_CUDA;
     jacobi_kernel<true><<<1, threads, smem, st>>>(static_cast<int>(k), G, V, scratch);
   } else {
-    if (cudaFuncSetAttribute(jacobi_kernel<false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                             static_cast<int>(smem)) != cudaSuccess)
+    // too large for one SM: the whole grid works on every round (cooperative launch)
+    static int blocks_per_sm = 0;
+    if (blocks_per_sm == 0 &&
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&blocks_per_sm, jacobi_grid_kernel, 256, 0) != cudaSuccess)
       return SHG_ERR_CUDA;
-    jacobi_kernel<false><<<1, threads, smem, st>>>(static_cast<int>(k), G, V, scratch);
+    const int sms = sm_count();
+    if (sms <= 0 || blocks_per_sm <= 0) return SHG_ERR_CUDA;
+    const long long work = (kp / 2) * (kp / 2);
+    long long want = (work + 255) / 256;
+    if (want > static_cast<long long>(sms) * blocks_per_sm) want = static_cast<long long>(sms) * blocks_per_sm;
+    if (want < 1) want = 1;
+    int kk = static_cast<int>(k);
+    const double* g = G;
+    float* v = V;
+    float* sc = scratch;
+    void* argv[] = {&kk, &g, &v, &sc};
+    return cuda_status(cudaLaunchCooperativeKernel(reinterpret_cast<const void*>(jacobi_grid_kernel),
+                                                   dim3(static_cast<unsigned>(want)), dim3(256), argv, 0, st));
   }
   return cuda_status(cudaGetLastError());
 }

@@ -140,3 +140,20 @@ def test_rp_hosvd_small(shg):
         # the core is the projection of A on the returned factors (last step of Algorithm 2)
         proj = np.einsum("ijk,ia,jb,kc->abc", A.astype(np.float64), facs[0], facs[1], facs[2])
         assert np.linalg.norm(core - proj) / np.linalg.norm(proj) < 1e-5
+
+
+def test_rsvd_large_k_grid_eigensolver(shg):
+    """k = rank + s = 160 exceeds one SM's shared memory: the eigensolver runs
+    on the whole grid (cooperative launch).  Same tolerances as the other
+    randomized-SVD cases (slower decay keeps sigma_128 / sigma_1 = 2^-4)."""
+    m, n, rank, s = 1200, 1000, 128, 32
+    A = planted_svd(m, n, sigma_exp(min(m, n), 32.0), seed=8)
+    Om = omega_f16(n, rank + s, seed=9)
+    U, S, V = shg.shg_rsvd(dev(A), dev(Om), rank=rank, oversampling=s)
+    U, S, V = (t.cpu().numpy() for t in (U, S, V))
+    ref = OR.rsvd(A, Om, p=rank)
+    rel_s = np.abs(S.astype(np.float64) - ref["S"]) / ref["S"]
+    assert rel_s.max() <= 1e-5, rel_s.max()
+    r_p = residual(A, U, S, V)
+    assert abs(r_p - ref["r_p"]) <= 0.01 * ref["r_p"], (r_p, ref["r_p"])
+    assert np.linalg.norm(U.T.astype(np.float64) @ U - np.eye(rank)) < 1e-4
