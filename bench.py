@@ -175,7 +175,7 @@ def main():
     ap.add_argument("--case", type=int, nargs=2, metavar=("MN", "K"),
                     help="profiling case: only W + K launches of one m=n=MN, k=K SHGEMM (no JSON contract line)")
     ap.add_argument("--variant", default="f16", help="variant for --case")
-    ap.add_argument("--factor", choices=["rsvd", "hosvd"],
+    ap.add_argument("--factor", choices=["rsvd", "hosvd", "rsvd4096"],
                     help="profiling case: W + K calls of the randomized SVD of the 1024^2 planted matrix "
                          "or of RP-HOSVD of the 512^3 Tucker tensor (no JSON contract line)")
     args = ap.parse_args()
@@ -308,6 +308,26 @@ def main():
         torch.distributed.destroy_process_group()
 
 
+def paper_rsvd_inputs(torch, dev):
+    """The randomized-SVD shape of the paper's throughput study (Sec. 5.1):
+    N = 4096, p = 256, s = 10, A_exp-like spectrum sigma_i = 2^(-i a) with
+    sigma_p = 1e-3.  Built as Q1 diag(sigma) Q2^T with Q1, Q2 orthonormal bases
+    of seeded Gaussians (512 leading singular values; input generation only)."""
+    from synth import omega_f16
+    N, p, s = 4096, 256, 10
+    k = p + s
+    rng = np.random.default_rng(7)
+    r = 512
+    sig = 2.0 ** (-np.arange(1, r + 1) * (np.log2(1e3) / p))
+    q1 = np.linalg.qr(rng.standard_normal((N, r)))[0]
+    q2 = np.linalg.qr(rng.standard_normal((N, r)))[0]
+    A = torch.from_numpy(((q1 * sig) @ q2.T).astype(np.float32)).to(dev)
+    ldo = (k + 7) // 8 * 8
+    Om = torch.zeros(N, ldo, dtype=torch.float16, device=dev)
+    Om[:, :k] = torch.from_numpy(omega_f16(N, k, seed=1)).to(dev)
+    return A, Om[:, :k], p, s
+
+
 def run_factor(args):
     """One factorization workload, for ncu launch lists: W warm-up calls then K timed ones."""
     import torch
@@ -317,7 +337,11 @@ def run_factor(args):
     from synth import rsvd_planted, tucker, hosvd_omegas
     dev = torch.device("cuda", 0)
     fl = shg.new_flags(dev)
-    if args.factor == "rsvd":
+    if args.factor == "rsvd4096":
+        A, Om, p, s_ = paper_rsvd_inputs(torch, dev)
+        ws = torch.empty(shg.rsvd_workspace_size(4096, 4096, p, s_, 0), dtype=torch.uint8, device=dev)
+        fn = lambda: shg.shg_rsvd(A, Om, p, s_, 0, args.variant, workspace=ws, flags=fl, check=False)
+    elif args.factor == "rsvd":
         A_h, Om_h = rsvd_planted(1024, 1024, rate=8.0, seed_a=0, seed_omega=1, k=64)
         A, Om = torch.from_numpy(A_h).to(dev), torch.from_numpy(Om_h).to(dev)
         ws = torch.empty(shg.rsvd_workspace_size(1024, 1024, 32, 32, 0), dtype=torch.uint8, device=dev)
