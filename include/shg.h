@@ -146,8 +146,24 @@ int shg_sgemm(int64_t m, int64_t n, int64_t kk,
               float* C, int64_t ldc, int accumulate, void* stream);
 
 /*
+ * Gram matrix G = X^T X of an m x k FP32 matrix, the first step of every
+ * CholeskyQR pass (Algorithms 1 and 2 orthonormalise with QR; the library
+ * uses CholeskyQR2).  The products x_ri x_rj are exact; they are summed
+ * with compensated FP32 arithmetic (Ogita, Rump and Oishi's dot product:
+ * TwoProduct by FMA, TwoSum) in blocks of 128 rows whose sums meet in FP64,
+ * so each entry is within gamma_128^2 (|X|^T |X|)_ij (about 6e-11 of it,
+ * gamma_n = n u / (1 - n u), u = 2^-24) of the exact value.
+ *   X: m x k row-major FP32 (ldx >= k).  G: k x k row-major FP64, caller-
+ *   owned; the upper triangle (j >= i) is written, the rest is zeroed.
+ *   1 <= k <= 1024, m >= 1.  Invalid arguments return SHG_ERR_INVALID_ARG
+ *   before any launch.  Asynchronous on `stream`.
+ */
+int shg_gram(int64_t m, int64_t k, const float* X, int64_t ldx, double* G, void* stream);
+
+/*
  * CholeskyQR2 (the orthonormal basis of Algorithms 1 and 2):
- * twice { G = X^T X (FP64 accumulation), G = R^T R (FP64 Cholesky),
+ * twice { G = X^T X (compensated FP32 sums, FP64 result, as shg_gram),
+ * G = R^T R (FP64 Cholesky),
  * X <- X R^-1 }.  X: m x k FP32 (ldx >= k), overwritten by Q with
  * Q^T Q = I and X_in = Q R, diag(R) > 0.  k <= m, k <= 1024.
  * Device flags: SHG_FLAG_NOT_SPD on a non-positive pivot.

@@ -170,6 +170,18 @@ def shg_sgemm(A: torch.Tensor, B: torch.Tensor, trans_a: bool = False, out: torc
     return out
 
 
+def shg_gram(X: torch.Tensor, out: torch.Tensor | None = None, stream=None) -> torch.Tensor:
+    """G = X^T X (k x k FP64; upper triangle, zeros below)."""
+    ldx = _mat(X, "X", (torch.float32,))
+    m, k = X.shape
+    if out is None:
+        out = torch.empty(k, k, dtype=torch.float64, device=X.device)
+    if out.dtype != torch.float64 or tuple(out.shape) != (k, k) or not out.is_contiguous():
+        raise ValueError("out must be a contiguous k x k float64 tensor")
+    _check(_lib.load().shg_gram(m, k, _ptr(X), ldx, _ptr(out), _stream(stream)), "shg_gram")
+    return out
+
+
 def shg_cholqr2(X: torch.Tensor, workspace: torch.Tensor | None = None, flags: torch.Tensor | None = None,
                 check: bool = True, stream=None) -> torch.Tensor:
     ldx = _mat(X, "X", (torch.float32,))

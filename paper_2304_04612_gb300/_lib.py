@@ -32,6 +32,7 @@ SIGNATURES = {
     "shg_sgemm": (c_int, [c_i64, c_i64, c_i64, c_vp, c_i64, c_int, c_vp, c_i64, c_int, c_vp, c_i64,
                           c_int, c_vp]),
     "shg_cholqr2_workspace_size": (c_int, [c_i64, c_i64, ctypes.POINTER(c_sz)]),
+    "shg_gram": (c_int, [c_i64, c_i64, c_vp, c_i64, c_vp, c_vp]),
     "shg_cholqr2": (c_int, [c_i64, c_i64, c_vp, c_i64, c_vp, c_sz, c_vp, c_vp]),
     "shg_cholqr2_static": (c_int, [c_i64, c_i64, c_vp, c_i64, c_vp, c_vp]),
     "shg_alpha_y_f16": (ctypes.c_double, []),

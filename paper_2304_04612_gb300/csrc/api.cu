@@ -168,6 +168,11 @@ int shg_sgemm(int64_t m, int64_t n, int64_t kk, const float* A, int64_t lda, int
                    static_cast<cudaStream_t>(stream));
 }
 
+int shg_gram(int64_t m, int64_t k, const float* X, int64_t ldx, double* G, void* stream) {
+  if (m < 1 || k < 1 || k > 1024 || !X || !G || ldx < k || m >= (1ll << 31)) return SHG_ERR_INVALID_ARG;
+  return gram_f64(m, k, X, ldx, G, static_cast<cudaStream_t>(stream));
+}
+
 int shg_cholqr2_workspace_size(int64_t m, int64_t k, size_t* bytes) {
   if (!bytes || k < 1 || m < k || k > 1024) return SHG_ERR_INVALID_ARG;
   *bytes = align256(static_cast<size_t>(m) * k * 4) + cholqr_small_bytes(k);

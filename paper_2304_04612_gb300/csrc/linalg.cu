@@ -4,9 +4,10 @@
 // Algorithm 1.
 //
 // CholeskyQR2 replaces the QR factorization of Algorithms 1 and 2:
-// twice { G = X^T X, G = R^T R, X <- X R^-1 }.  The Gram matrix is
-// accumulated in FP64 from exact FP32 x FP32 products and factored in FP64;
-// R^-1 is formed in FP32 from the FP64 factor and X R^-1 is an FP32 GEMM.
+// twice { G = X^T X, G = R^T R, X <- X R^-1 }.  The Gram matrix is summed
+// from exact FP32 x FP32 products with compensated FP32 arithmetic (about
+// twice FP32's precision), delivered in FP64 and factored in FP64; R^-1 is
+// formed in FP32 from the FP64 factor and X R^-1 is an FP32 GEMM.
 //
 // The eigensolver is a parallel cyclic Jacobi method (round-robin pairing)
 // in FP32 on the scaled Gram matrix; eigenvalues are then refined as FP64
@@ -20,43 +21,90 @@
 namespace shg {
 namespace {
 
-// ---------------------------------------------------------------- Gram FP64
+// ---------------------------------------------------------------- Gram
 // G[i][j] += sum_r X[r][i] X[r][j] for the upper 32 x 32 tiles (ti <= tj);
 // blockIdx.z selects a chunk of rows.  G must be zeroed first.
-__global__ void __launch_bounds__(256) gram_f64_kernel(int m, int k, const float* __restrict__ X, long long ldx,
-                                                      double* __restrict__ G, int rows_per_chunk) {
+//
+// GB300 issues FP64 at about 1/64 of its FP32 rate, so the sums run on the
+// FP32 pipe with error-free transformations (the compensated dot product of
+// Ogita, Rump and Oishi, "Accurate sum and dot product", 2005): each product
+// is split exactly into p + e with p = fl(x y) and e = fma(x, y, -p); the p
+// are summed with Knuth's TwoSum into s, whose rounding errors t collect with
+// the e in a second word c.  Every kFlushRows rows the pair is added to an
+// FP64 accumulator and restarted, which bounds the error of a 128-row block
+// by gamma_128^2 sum |x_ri x_rj| (about 6e-11 of it, 4e-14 for random signs);
+// the chunk sums meet in FP64 atomics.  The _rn intrinsics keep the compiler
+// from contracting the transformations into FMAs.
+constexpr int kFlushRows = 128;
+
+__device__ __forceinline__ void dot2_step(float x, float y, float& s, float& c) {
+  const float p = __fmul_rn(x, y);
+  const float e = __fmaf_rn(x, y, -p);
+  const float t = __fadd_rn(s, p);
+  const float z = __fsub_rn(t, s);
+  const float r = __fadd_rn(__fsub_rn(s, __fsub_rn(t, z)), __fsub_rn(p, z));
+  s = t;
+  c = __fadd_rn(c, __fadd_rn(r, e));
+}
+
+__global__ void __launch_bounds__(256) gram_kernel(int m, int k, const float* __restrict__ X, long long ldx,
+                                                   double* __restrict__ G, int rows_per_chunk) {
   const int ti = blockIdx.y, tj = blockIdx.x;
   if (ti > tj) return;
   __shared__ float Xi[32][33], Xj[32][33];
   const int tid = threadIdx.x;
   const int a = tid >> 3;        // 0..31: row of the G tile
   const int b4 = (tid & 7) * 4;  // 4 columns
+  const int ci = ti * 32 + (tid & 31), cj = tj * 32 + (tid & 31);
+  const int lr = tid >> 5;  // this thread loads rows lr, lr + 8, lr + 16, lr + 24 of a 32-row slab
   double acc[4] = {0, 0, 0, 0};
+  float s[4] = {0, 0, 0, 0}, c[4] = {0, 0, 0, 0};
   const int r0 = blockIdx.z * rows_per_chunk;
   const int r1 = min(m, r0 + rows_per_chunk);
-  for (int rb = r0; rb < r1; rb += 32) {
-    for (int e = tid; e < 32 * 32; e += 256) {
-      const int rr = e >> 5, cc = e & 31;
-      const int gr = rb + rr;
-      const int ci = ti * 32 + cc, cj = tj * 32 + cc;
-      Xi[rr][cc] = (gr < r1 && ci < k) ? X[gr * ldx + ci] : 0.0f;
-      Xj[rr][cc] = (gr < r1 && cj < k) ? X[gr * ldx + cj] : 0.0f;
-    }
-    __syncthreads();
-#pragma unroll 8
-    for (int rr = 0; rr < 32; ++rr) {
-      const double xa = Xi[rr][a];
+  float pi[4], pj[4];
+  auto fetch = [&](int rb) {
 #pragma unroll
-      for (int c = 0; c < 4; ++c) acc[c] = fma(xa, static_cast<double>(Xj[rr][b4 + c]), acc[c]);
+    for (int u = 0; u < 4; ++u) {
+      const int gr = rb + lr + 8 * u;
+      const bool in = gr < r1;
+      pi[u] = (in && ci < k) ? X[gr * ldx + ci] : 0.0f;
+      pj[u] = (in && cj < k) ? X[gr * ldx + cj] : 0.0f;
+    }
+  };
+  if (r0 < r1) fetch(r0);
+  int since = 0;
+  for (int rb = r0; rb < r1; rb += 32) {
+#pragma unroll
+    for (int u = 0; u < 4; ++u) {
+      Xi[lr + 8 * u][tid & 31] = pi[u];
+      Xj[lr + 8 * u][tid & 31] = pj[u];
     }
     __syncthreads();
+    if (rb + 32 < r1) fetch(rb + 32);  // the next slab's loads overlap this slab's sums
+#pragma unroll 4
+    for (int rr = 0; rr < 32; ++rr) {
+      const float xa = Xi[rr][a];
+#pragma unroll
+      for (int q = 0; q < 4; ++q) dot2_step(xa, Xj[rr][b4 + q], s[q], c[q]);
+    }
+    __syncthreads();
+    since += 32;
+    if (since == kFlushRows) {
+#pragma unroll
+      for (int q = 0; q < 4; ++q) {
+        acc[q] += static_cast<double>(s[q]) + static_cast<double>(c[q]);
+        s[q] = c[q] = 0.0f;
+      }
+      since = 0;
+    }
   }
   const int gi = ti * 32 + a;
   if (gi >= k) return;
 #pragma unroll
-  for (int c = 0; c < 4; ++c) {
-    const int gj = tj * 32 + b4 + c;
-    if (gj < k && gj >= gi) atomicAdd(&G[gi * k + gj], acc[c]);
+  for (int q = 0; q < 4; ++q) {
+    const int gj = tj * 32 + b4 + q;
+    if (gj < k && gj >= gi)
+      atomicAdd(&G[gi * k + gj], acc[q] + (static_cast<double>(s[q]) + static_cast<double>(c[q])));
   }
 }
 
@@ -692,15 +740,15 @@ int gram_f64(int64_t m, int64_t k, const float* X, int64_t ldx, double* G, cudaS
   const int t = static_cast<int>((k + 31) / 32);
   const long long tiles = static_cast<long long>(t) * (t + 1) / 2;
   const int sms = sm_count();
-  // enough row chunks that about two CTAs per SM share the FP64 work
-  long long chunks = (2ll * sms + tiles - 1) / tiles;
+  // enough row chunks that about four CTAs per SM share the work
+  long long chunks = (4ll * sms + tiles - 1) / tiles;
   long long rows = (m + chunks - 1) / chunks;
   rows = ((rows + 31) / 32) * 32;
   if (rows < 32) rows = 32;
   chunks = (m + rows - 1) / rows;
   if (chunks > 65535) return SHG_ERR_UNSUPPORTED;
   dim3 grid(t, t, static_cast<unsigned>(chunks));
-  gram_f64_kernel<<<grid, 256, 0, st>>>(static_cast<int>(m), static_cast<int>(k), X, ldx, G, static_cast<int>(rows));
+  gram_kernel<<<grid, 256, 0, st>>>(static_cast<int>(m), static_cast<int>(k), X, ldx, G, static_cast<int>(rows));
   return cuda_status(cudaGetLastError());
 }
 

@@ -65,6 +65,10 @@ def test_host_argument_validation(lib):
     r = (ctypes.c_int64 * 3)(4, 9, 4)                                 # J > I
     assert lib.shg_rp_hosvd_workspace_size(3, d, r, ctypes.byref(sz)) == 1
     assert lib.shg_rp_hosvd_workspace_size(4, d, r, ctypes.byref(sz)) == 7
+    # Gram matrix: k = 0, k > 1024 and ldx < k are rejected before any launch
+    assert lib.shg_gram(8, 0, one, 8, one, null) == 1
+    assert lib.shg_gram(8, 1025, one, 1025, one, null) == 1
+    assert lib.shg_gram(8, 8, one, 4, one, null) == 1
 
 
 def test_alpha_y_f16_matches_the_oracle(lib):
