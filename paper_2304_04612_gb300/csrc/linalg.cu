@@ -130,36 +130,82 @@ __device__ void diag_max(int k, const double* __restrict__ G, double* red, doubl
   }
 }
 
+// Double-float arithmetic on the FP32 pipe: a value is the unevaluated sum
+// hi + lo with |lo| <= ulp(hi) / 2 (about 48 significant bits, 44 after the
+// operations below).  Error-free steps: Dekker's Fast2Sum, Knuth's TwoSum
+// and the FMA TwoProduct (Ogita, Rump and Oishi 2005 collect them); the
+// _rn intrinsics keep the compiler from contracting them.
+__device__ __forceinline__ float2 fast_two_sum(float a, float b) {  // needs |a| >= |b|
+  const float s = __fadd_rn(a, b);
+  return make_float2(s, __fsub_rn(b, __fsub_rn(s, a)));
+}
+__device__ __forceinline__ float2 two_sum(float a, float b) {
+  const float s = __fadd_rn(a, b);
+  const float bb = __fsub_rn(s, a);
+  return make_float2(s, __fadd_rn(__fsub_rn(a, __fsub_rn(s, bb)), __fsub_rn(b, bb)));
+}
+// x * y
+__device__ __forceinline__ float2 df_mul(float2 x, float2 y) {
+  const float p = __fmul_rn(x.x, y.x);
+  float e = __fmaf_rn(x.x, y.x, -p);
+  e = __fmaf_rn(x.x, y.y, e);
+  e = __fmaf_rn(x.y, y.x, e);
+  return fast_two_sum(p, e);
+}
+// a - t * b
+__device__ __forceinline__ float2 df_sub_mul(float2 a, float2 t, float2 b) {
+  const float p = __fmul_rn(t.x, b.x);
+  float pe = __fmaf_rn(t.x, b.x, -p);
+  pe = __fmaf_rn(t.x, b.y, pe);
+  pe = __fmaf_rn(t.y, b.x, pe);
+  const float2 s = two_sum(a.x, -p);
+  return two_sum(s.x, __fadd_rn(s.y, __fsub_rn(a.y, pe)));
+}
+// 1 / d for d > 0: r = fl(1 / d.hi), e = 1 - d r in double-float (1 - p is
+// exact, p being within an ulp of 1), then r + r e
+__device__ __forceinline__ float2 df_recip(float2 d) {
+  const float r = 1.0f / d.x;
+  const float p = __fmul_rn(d.x, r);
+  float pe = __fmaf_rn(d.x, r, -p);
+  pe = __fmaf_rn(d.y, r, pe);
+  const float e = __fsub_rn(__fsub_rn(1.0f, p), pe);
+  return fast_two_sum(r, __fmul_rn(r, e));
+}
+
 // Upper Cholesky G = R^T R of the k x k matrix whose upper triangle is in G
 // (row-major, ld k), then X = R^-1; writes X in FP32 (upper, zero below the
 // diagonal) to Xf.  One CTA.
 //   G is scaled by sigma = 4^-e (e = floor(log2(max diag) / 2)), an exact
 //   power of two, so that pivots lie near [0, 4] and sqrt(sigma) = 2^-e is
 //   exact: R^-1 = 2^-e R_s^-1.
-//   Elimination (FP64) keeps rows unscaled: after column j,
-//   a[j][l] = R[j][j] R[j][l] and d_j = a[j][j] = R[j][j]^2, so the trailing
-//   update a[l][l'] -= (a[j][l] / d_j) a[j][l'] needs only 1/d_j, which the
-//   thread owning a[j+1][j+1] forms as soon as it has updated it (an FP32
-//   reciprocal refined by one Newton-Raphson step r (2 - d r), relative
-//   error about 2^-48): one barrier per column.
+//   Elimination in double-float (FP64 on this part issues at about 1/64 of
+//   the FP32 rate, so the 44-bit arithmetic of pairs of floats is several
+//   times faster than FP64 and close to its accuracy).  Rows stay unscaled:
+//   after column j, a[j][l] = R[j][j] R[j][l] and d_j = a[j][j] = R[j][j]^2,
+//   so the trailing update a[l][l'] -= (a[j][l] / d_j) a[j][l'] needs only
+//   1/d_j, which thread 0 forms right after it has updated a[j+1][j+1]: one
+//   barrier per column.  The trailing triangle of n = k - j - 1 rows is
+//   folded into ceil(n / 2) rows of n + 1 elements (rows r and n - 1 - r
+//   together), warps over those rows and lanes along them, so the lanes stay
+//   busy as the triangle shrinks.
 //   Inverse (FP32, from R rounded to FP32): X[j][j] = 1/R[j][j],
 //   X[i][j] = -(1/R[i][i]) sum_{l=i+1..j} R[i][l] X[l][j]; thread j
 //   back-substitutes column j alone.  Its rounding is of the same order as
 //   that of the FP32 product X R^-1 which follows.
-// `a` (k^2 doubles) and the FP32 R and X (k^2 floats each) live in shared
-// memory when they fit, else in `scratch` (2 k^2 doubles).  A non-positive
-// pivot raises SHG_FLAG_NOT_SPD and is replaced by the smallest positive
-// normal double so that R stays finite.
+// `a` (k^2 double-floats) and the FP32 R and X (k^2 floats each) live in
+// shared memory when they fit, else in `scratch` (2 k^2 doubles).  A
+// non-positive pivot raises SHG_FLAG_NOT_SPD and is replaced by the smallest
+// positive normal float so that R stays finite.
 // SMEM selects the shared-memory layout at compile time, so that the
 // accesses compile to shared loads and stores rather than generic ones.
 template <bool SMEM>
 __global__ void __launch_bounds__(1024) chol_inv_kernel(int k, const double* __restrict__ G, float* __restrict__ Xf,
                                                        double* scratch, int* flags) {
-  extern __shared__ double sm[];
-  double* a = SMEM ? sm : scratch;
+  extern __shared__ __align__(16) float2 smd[];
+  float2* a = SMEM ? smd : reinterpret_cast<float2*>(scratch);
   float* rf = reinterpret_cast<float*>(a + k * k);
   float* xf = rf + k * k;
-  __shared__ double dinv[1024];
+  __shared__ float2 dinv[1024];
   __shared__ float rinv[1024];
   __shared__ double red[32];
   __shared__ double dmax;
@@ -171,50 +217,58 @@ __global__ void __launch_bounds__(1024) chol_inv_kernel(int k, const double* __r
   const double sigma = ldexp(1.0, -2 * e2);
   for (int e = tid; e < k * k; e += nt) {
     const int i = e / k, j = e - i * k;
-    a[e] = (j >= i) ? G[e] * sigma : 0.0;
+    float2 v = make_float2(0.0f, 0.0f);
+    if (j >= i) {
+      const double g = G[e] * sigma;
+      v.x = static_cast<float>(g);
+      v.y = static_cast<float>(g - static_cast<double>(v.x));
+    }
+    a[e] = v;
   }
   __syncthreads();
   auto pivot = [&](int j) {
-    double d = a[j * k + j];
-    if (!(d > 0.0)) {
+    float2 d = a[j * k + j];
+    if (!(d.x > 0.0f)) {
       atomicOr(flags, SHG_FLAG_NOT_SPD);
-      d = 2.2250738585072014e-308;
+      d = make_float2(1.17549435e-38f, 0.0f);
       a[j * k + j] = d;
     }
-    double r;
-    if (d >= 1e-37 && d <= 1e37) {
-      r = static_cast<double>(1.0f / static_cast<float>(d));
-      r = r * fma(-d, r, 2.0);
-    } else {
-      r = 1.0 / d;
-    }
-    dinv[j] = r;
+    dinv[j] = df_recip(d);
   };
   if (tid == 0) pivot(0);
   __syncthreads();
   for (int j = 0; j < k - 1; ++j) {
-    const double dj = dinv[j];
-    const double* rowj = a + j * k;
-    for (int l = j + 1 + warp; l < k; l += nw) {
-      const double t = rowj[l] * dj;
-      double* rowl = a + l * k;
-      for (int lp = l + lane; lp < k; lp += 32) rowl[lp] = fma(-t, rowj[lp], rowl[lp]);
+    const float2 dj = dinv[j];
+    const float2* rowj = a + j * k;
+    const int n = k - j - 1;
+    const int rows = (n + 1) >> 1;
+    for (int i = warp; i < rows; i += nw) {
+      for (int c = lane; c <= n; c += 32) {
+        int r = i, cc = i + c;
+        if (c >= n - i) {
+          r = n - 1 - i;
+          cc = c - 1;
+          if (r == i) continue;  // odd n: the middle row has no second half
+        }
+        const int l = j + 1 + r, lp = j + 1 + cc;
+        const float2 t = df_mul(rowj[l], dj);
+        a[l * k + lp] = df_sub_mul(a[l * k + lp], t, rowj[lp]);
+      }
     }
-    // warp 0 lane 0 owns a[j+1][j+1] (row j+1, first column)
+    // thread 0 (folded row 0, element 0) owns a[j+1][j+1]
     if (tid == 0) pivot(j + 1);
     __syncthreads();
   }
-  // R in FP32: R[i][l] = a[i][l] / R[i][i], 1/R[i][i] = sqrt(1/d_i) (one
-  // FP64 square root per row, kept in dinv)
-  for (int i = tid; i < k; i += nt) {
-    const double r = sqrt(dinv[i]);
-    rinv[i] = static_cast<float>(r);
-    dinv[i] = r;
-  }
+  // R in FP32: R[i][l] = a[i][l] / R[i][i], 1/R[i][i] = sqrt(1/d_i)
+  for (int i = tid; i < k; i += nt)
+    rinv[i] = static_cast<float>(sqrt(static_cast<double>(dinv[i].x) + static_cast<double>(dinv[i].y)));
   __syncthreads();
   for (int i = warp; i < k; i += nw) {
-    const double r = dinv[i];
-    for (int l = i + 1 + lane; l < k; l += 32) rf[i * k + l] = static_cast<float>(a[i * k + l] * r);
+    const float r = rinv[i];
+    for (int l = i + 1 + lane; l < k; l += 32) {
+      const float2 v = a[i * k + l];
+      rf[i * k + l] = __fmaf_rn(v.y, r, __fmul_rn(v.x, r));
+    }
   }
   __syncthreads();
   for (int j = tid; j < k; j += nt) {
@@ -290,42 +344,45 @@ __device__ __forceinline__ bool jac_rot(float app, float aqq, float apq, float& 
 
 // Eigendecomposition of the symmetric k x k matrix whose upper triangle is
 // in G (FP64): A = sigma G in FP32 (sigma a power of two near 1 / max diag),
-// V = I, then sweeps of the parallel cyclic Jacobi method (circle-method
-// pairing: kp - 1 rounds of kp / 2 disjoint pairs, position 0 fixed, the
-// others turn) until a sweep applies no rotation (at most 40 sweeps).
-// Writes V (k x k FP32, columns = eigenvectors).
-//   One barrier per round: every thread forms 2 x 2 blocks of J^T A J for
-//   pair blocks (t, u), u >= t, into the second buffer (each block also to
-//   its mirror, so A stays exactly symmetric) and rotates column pairs of V
-//   (kept transposed, float4 rows); threads t < kp/2 also form the three
-//   entries of round r+1's pair t from the same old A and build its
-//   rotation into the other parameter buffer.  last_rot holds the latest
-//   sweep that applies a rotation; sweep s ends the loop when last_rot < s.
-// Shared layout: two JPair[kp/2] buffers, two {pair, side}[kp] index maps,
-// then A, its second buffer (kp (kp + 1) floats each, leading dimension
-// kp + 1) and V^T (kp x ldv, ldv = kp rounded up to 4); the matrices move to
-// `scratch` when they do not fit.
-template <bool SMEM>
+// V = I, then sweeps of the parallel cyclic Jacobi method until a sweep
+// applies no rotation (at most 40 sweeps).  Writes V (k x k FP32, columns =
+// eigenvectors).  One CTA; everything lives in shared memory.
+//   Pairing (the round-robin "circle" order, kp = k rounded up to even,
+//   h = kp / 2 slots, n1 = kp - 1): at round r slot i holds
+//     a_i(r) = 0 (i = 0) or ((r + i - 1) mod n1) + 1,  b_i(r) = ((r - 1 - i) mod n1) + 1,
+//   so between rounds a_i <- a_{i+1} (1 <= i < h - 1), a_{h-1} <- b_{h-1},
+//   b_i <- b_{i-1} (i >= 1) and b_0 <- a_1.  The slot of round r that each
+//   index of round r + 1 comes from is therefore fixed, and no thread needs
+//   an index table.
+//   Roles (whole warps): block threads own fixed pair blocks (t, u), t <= u,
+//   and write each 2 x 2 block of J^T A J to the second buffer (and to its
+//   mirror, so A stays exactly symmetric); V threads own fixed (slot,
+//   8-column) pieces of V^T and rotate them; rotation threads (one per
+//   slot) build round r + 1's rotations from the old A at the same time.
+//   One barrier per round.  last_rot holds the latest sweep that applies a
+//   rotation; sweep s ends the loop when last_rot < s.
+// Shared layout: JPair[2][h], the two A buffers (kp x (kp + 1) floats each),
+// V^T (kp x ldv, ldv = kp rounded up to 8).
+constexpr int kJacItems = 8;  // most blocks (or V pieces) one thread owns
+
+__host__ __device__ inline int jac_ldv(int kp) { return (kp + 7) & ~7; }
+__host__ __device__ inline size_t jac_cta_floats(int kp) {
+  return static_cast<size_t>(4 * kp) + 2 * static_cast<size_t>(kp) * (kp + 1) + static_cast<size_t>(kp) * jac_ldv(kp);
+}
+
 __global__ void __launch_bounds__(1024) jacobi_kernel(int k, const double* __restrict__ G, float* __restrict__ Vout,
-                                                     float* scratch) {
-  extern __shared__ __align__(16) int smi[];
+                                                     int TB, int TV) {
+  extern __shared__ __align__(16) float smf[];
   const int kp = k + (k & 1);
-  const int half = kp / 2, n1 = kp - 1;
-  const int ld = kp + 1, ldv = (kp + 3) & ~3;
-  JPair* pairs = reinterpret_cast<JPair*>(smi);  // [2][half]
-  int* tmap = smi + 8 * kp;                      // [2][kp]: pair of index
-  int* smap = tmap + 2 * kp;                     // [2][kp]: side of index
-  // One fixed base; the two A buffers alternate by an integer index (no
-  // loop-carried pointer swap, so shared accesses stay shared accesses).
-  float* const M0 = SMEM ? reinterpret_cast<float*>(smap + 2 * kp) : scratch;
+  const int h = kp / 2, n1 = kp - 1;
+  const int ld = kp + 1, ldv = jac_ldv(kp);
+  JPair* pairs = reinterpret_cast<JPair*>(smf);  // [2][h]
+  float* const M0 = smf + 8 * h;
   float* const Vt = M0 + 2 * kp * ld;
-  int abuf = 0;
-  float* A = M0;
   __shared__ int last_rot;
   __shared__ double red[32];
   __shared__ double dmax;
   const int tid = threadIdx.x, nt = blockDim.x;
-  const int lane = tid & 31, warp = tid >> 5, nw = nt >> 5;
   diag_max(k, G, red, &dmax);
   if (tid == 0) last_rot = -1;
   __syncthreads();
@@ -334,104 +391,128 @@ __global__ void __launch_bounds__(1024) jacobi_kernel(int k, const double* __res
     const int i = e / kp, j = e - i * kp;
     float v = 0.0f;
     if (i < k && j < k) v = static_cast<float>(G[min(i, j) * k + max(i, j)] * sigma);
-    A[i * ld + j] = v;
+    M0[i * ld + j] = v;
   }
   for (int e = tid; e < kp * ldv; e += nt) {
     const int i = e / ldv, j = e - i * ldv;
     Vt[e] = (i == j) ? 1.0f : 0.0f;
   }
-  // The last ceil(kp/2 / 32) warps only build rotations (rotation thread rt
-  // owns pair rt); the others only apply them, so a round costs the longer
-  // of the two instead of their sum.
-  const int rot_warps = (half + 31) / 32;
-  const int upd_warps = nw - rot_warps;
-  const int rt = tid - upd_warps * 32;
-  const bool rotor = rt >= 0 && rt < half;
-  // pairing of round 0 and, per rotation thread, its running positions
+  const int nblk = h * (h + 1) / 2, nc8 = ldv / 8, nv = h * nc8;
+  const bool is_blk = tid < TB;
+  const bool is_v = !is_blk && tid < TB + TV;
+  const int rt = tid - TB - TV;
+  const bool rotor = rt >= 0 && rt < h;
+  // fixed items: blocks in folded-triangle order (rectangle row i = rows i
+  // and h - 1 - i of the triangle, h + 1 blocks), or V pieces (slot, chunk)
+  int it_a[kJacItems], it_b[kJacItems];
+#pragma unroll
+  for (int c = 0; c < kJacItems; ++c) {
+    it_a[c] = -1;
+    it_b[c] = 0;
+    if (is_blk) {
+      const int bi = tid + c * TB;
+      if (bi < nblk) {
+        const int i = bi / (h + 1), j = bi - i * (h + 1);
+        if (j < h - i) {
+          it_a[c] = i;
+          it_b[c] = i + j;
+        } else {
+          it_a[c] = h - 1 - i;
+          it_b[c] = j - 1;
+        }
+      }
+    } else if (is_v) {
+      const int vi = tid - TB + c * TV;
+      if (vi < nv) {
+        it_a[c] = vi / nc8;
+        it_b[c] = (vi - (vi / nc8) * nc8) * 8;
+      }
+    }
+  }
+  // slot rt's indices (round 0, then advanced) and the slots of the previous
+  // round its a- and b-index come from
   int pa = 0, pb = 0;
+  const int srcA = (rt <= 0) ? 0 : min(rt + 1, h - 1);
+  const int srcB = (rt >= 1) ? rt - 1 : (h >= 2 ? 1 : 0);
   if (rotor) {
-    pa = (rt == 0) ? 0 : rt;                    // ((0 + i - 1) mod n1) + 1
-    pb = ((n1 - 1 - rt) % n1 + n1) % n1 + 1;    // ((0 - 1 - i) mod n1) + 1
+    pa = (rt == 0) ? 0 : rt;
+    pb = ((n1 - 1 - rt) % n1 + n1) % n1 + 1;
   }
   __syncthreads();
   if (rotor) {
     const int p = min(pa, pb), q = max(pa, pb);
     float c, s;
-    if (jac_rot(A[p * ld + p], A[q * ld + q], A[p * ld + q], c, s)) last_rot = 0;
+    if (jac_rot(M0[p * ld + p], M0[q * ld + q], M0[p * ld + q], c, s)) last_rot = 0;
     pairs[rt] = JPair{p, q, c, s};
-    tmap[p] = rt;
-    tmap[q] = rt;
-    smap[p] = 0;
-    smap[q] = 1;
   }
   __syncthreads();
-  int buf = 0;
+  int buf = 0, abuf = 0;
   for (int sweep = 0; sweep < 40; ++sweep) {
     for (int r = 0; r < n1; ++r) {
-      A = M0 + abuf * (kp * ld);
+      const float* const A = M0 + abuf * (kp * ld);
       float* const B = M0 + (abuf ^ 1) * (kp * ld);
-      const JPair* cur = pairs + buf * half;
-      const int* ct = tmap + buf * kp;
-      const int* cs = smap + buf * kp;
-      // J^T A J by pair blocks
-      for (int t = warp; t < half && warp < upd_warps; t += upd_warps) {
-        const JPair P1 = cur[t];
-        for (int u = t + lane; u < half; u += 32) {
-          const JPair P2 = cur[u];
-          float n00, n01, n10, n11;
-          jac_block(A[P1.p * ld + P2.p], A[P1.p * ld + P2.q], A[P1.q * ld + P2.p], A[P1.q * ld + P2.q], P1.c, P1.s,
-                    P2.c, P2.s, n00, n01, n10, n11);
-          if (u == t) {
-            if (P1.s != 0.0f) n01 = 0.0f;
-            B[P1.p * ld + P1.p] = n00;
-            B[P1.q * ld + P1.q] = n11;
-            B[P1.p * ld + P1.q] = n01;
-            B[P1.q * ld + P1.p] = n01;
-          } else {
-            B[P1.p * ld + P2.p] = n00;
-            B[P2.p * ld + P1.p] = n00;
-            B[P1.p * ld + P2.q] = n01;
-            B[P2.q * ld + P1.p] = n01;
-            B[P1.q * ld + P2.p] = n10;
-            B[P2.p * ld + P1.q] = n10;
-            B[P1.q * ld + P2.q] = n11;
-            B[P2.q * ld + P1.q] = n11;
+      const JPair* cur = pairs + buf * h;
+      if (is_blk) {
+#pragma unroll
+        for (int c = 0; c < kJacItems; ++c) {
+          if (it_a[c] >= 0) {
+            const int t = it_a[c], u = it_b[c];
+            const JPair P1 = cur[t], P2 = cur[u];
+            float n00, n01, n10, n11;
+            jac_block(A[P1.p * ld + P2.p], A[P1.p * ld + P2.q], A[P1.q * ld + P2.p], A[P1.q * ld + P2.q], P1.c,
+                      P1.s, P2.c, P2.s, n00, n01, n10, n11);
+            if (t == u) {
+              if (P1.s != 0.0f) n01 = 0.0f;
+              B[P1.p * ld + P1.p] = n00;
+              B[P1.q * ld + P1.q] = n11;
+              B[P1.p * ld + P1.q] = n01;
+              B[P1.q * ld + P1.p] = n01;
+            } else {
+              B[P1.p * ld + P2.p] = n00;
+              B[P2.p * ld + P1.p] = n00;
+              B[P1.p * ld + P2.q] = n01;
+              B[P2.q * ld + P1.p] = n01;
+              B[P1.q * ld + P2.p] = n10;
+              B[P2.p * ld + P1.q] = n10;
+              B[P1.q * ld + P2.q] = n11;
+              B[P2.q * ld + P1.q] = n11;
+            }
           }
         }
-      }
-      // V <- V J on the transposed rows p, q
-      const int nv4 = ldv >> 2;
-      for (int w = tid; w < half * nv4 && warp < upd_warps; w += upd_warps * 32) {
-        const int t = w / nv4, c4 = (w - t * nv4) * 4;
-        const JPair P = cur[t];
-        float4* vp = reinterpret_cast<float4*>(Vt + P.p * ldv + c4);
-        float4* vq = reinterpret_cast<float4*>(Vt + P.q * ldv + c4);
-        const float4 x = *vp, y = *vq;
-        *vp = make_float4(__fmaf_rn(-P.s, y.x, __fmul_rn(P.c, x.x)), __fmaf_rn(-P.s, y.y, __fmul_rn(P.c, x.y)),
-                          __fmaf_rn(-P.s, y.z, __fmul_rn(P.c, x.z)), __fmaf_rn(-P.s, y.w, __fmul_rn(P.c, x.w)));
-        *vq = make_float4(__fmaf_rn(P.s, x.x, __fmul_rn(P.c, y.x)), __fmaf_rn(P.s, x.y, __fmul_rn(P.c, y.y)),
-                          __fmaf_rn(P.s, x.z, __fmul_rn(P.c, y.z)), __fmaf_rn(P.s, x.w, __fmul_rn(P.c, y.w)));
-      }
-      // rotations of the next round from the same old A
-      if (rotor) {
+      } else if (is_v) {
+        // V <- V J on the transposed rows p, q
+#pragma unroll
+        for (int c = 0; c < kJacItems; ++c) {
+          if (it_a[c] >= 0) {
+            const JPair P = cur[it_a[c]];
+            float4* vp = reinterpret_cast<float4*>(Vt + P.p * ldv + it_b[c]);
+            float4* vq = reinterpret_cast<float4*>(Vt + P.q * ldv + it_b[c]);
+#pragma unroll
+            for (int hh = 0; hh < 2; ++hh) {
+              const float4 x = vp[hh], y = vq[hh];
+              vp[hh] = make_float4(__fmaf_rn(-P.s, y.x, __fmul_rn(P.c, x.x)), __fmaf_rn(-P.s, y.y, __fmul_rn(P.c, x.y)),
+                                   __fmaf_rn(-P.s, y.z, __fmul_rn(P.c, x.z)), __fmaf_rn(-P.s, y.w, __fmul_rn(P.c, x.w)));
+              vq[hh] = make_float4(__fmaf_rn(P.s, x.x, __fmul_rn(P.c, y.x)), __fmaf_rn(P.s, x.y, __fmul_rn(P.c, y.y)),
+                                   __fmaf_rn(P.s, x.z, __fmul_rn(P.c, y.z)), __fmaf_rn(P.s, x.w, __fmul_rn(P.c, y.w)));
+            }
+          }
+        }
+      } else if (rotor) {
+        // rotation of slot rt for round r + 1 from the same old A
         pa = (rt == 0) ? 0 : (pa == n1 ? 1 : pa + 1);
         pb = (pb == n1) ? 1 : pb + 1;
-        const int p = min(pa, pb), q = max(pa, pb);
-        const int tp = ct[p], tq = ct[q], sp = cs[p], sq = cs[q];
-        const JPair Pp = cur[tp], Pq = cur[tq];
+        const JPair PA = cur[srcA], PB = cur[srcB];
+        const int sxa = (pa == PA.p) ? 0 : 1, sxb = (pb == PB.p) ? 0 : 1;
+        const bool a_low = pa < pb;
+        const JPair Pp = a_low ? PA : PB, Pq = a_low ? PB : PA;
+        const int sp = a_low ? sxa : sxb, sq = a_low ? sxb : sxa;
+        const int tp = a_low ? srcA : srcB, tq = a_low ? srcB : srcA;
         const float app = jac_elem(A, ld, Pp, sp, Pp, sp, true);
         const float aqq = jac_elem(A, ld, Pq, sq, Pq, sq, true);
         const float apq = (tp <= tq) ? jac_elem(A, ld, Pp, sp, Pq, sq, tp == tq) : jac_elem(A, ld, Pq, sq, Pp, sp, false);
         float c, s;
         if (jac_rot(app, aqq, apq, c, s)) last_rot = (r + 1 == n1) ? sweep + 1 : sweep;
-        JPair* nxt = pairs + (buf ^ 1) * half;
-        int* nt_ = tmap + (buf ^ 1) * kp;
-        int* ns_ = smap + (buf ^ 1) * kp;
-        nxt[rt] = JPair{p, q, c, s};
-        nt_[p] = rt;
-        nt_[q] = rt;
-        ns_[p] = 0;
-        ns_[q] = 1;
+        pairs[(buf ^ 1) * h + rt] = JPair{min(pa, pb), max(pa, pb), c, s};
       }
       __syncthreads();
       abuf ^= 1;
@@ -772,20 +853,28 @@ int chol_inv(int64_t k, const double* G, float* Rinv, double* scratch, int32_t* 
 int jacobi_eig(int64_t k, const double* G, float* V, float* scratch, cudaStream_t st) {
   if (k > 1024) return SHG_ERR_UNSUPPORTED;
   const int64_t kp = k + (k & 1);
-  const size_t prm = static_cast<size_t>(8 * kp + 4 * kp) * sizeof(int);
-  const size_t mats = jacobi_scratch_floats(k) * sizeof(float);
-  const int in_smem = smem_fits(prm + mats);
-  const size_t smem = in_smem ? prm + mats : prm;
-  // update warps for about 8 elements per thread, plus the rotation warps
-  const int rot = static_cast<int>((kp / 2 + 31) / 32) * 32;
-  int threads = block_threads(kp * kp / 16) + rot;
-  if (threads > 1024) threads = 1024;
-  if (threads - rot < 64) return SHG_ERR_UNSUPPORTED;
-  if (in_smem) {
-    if (cudaFuncSetAttribute(jacobi_kernel<true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                             static_cast<int>(smem)) != cudaSuccess)
+  const size_t smem = jac_cta_floats(static_cast<int>(kp)) * sizeof(float);
+  if (smem_fits(smem)) {
+    // one CTA: whole warps of block threads and V threads with about the
+    // same number of items each, then one rotation thread per slot
+    const int h = static_cast<int>(kp / 2);
+    const int nblk = h * (h + 1) / 2, nv = h * (jac_ldv(static_cast<int>(kp)) / 8);
+    const int rot = (h + 31) / 32 * 32;
+    const int avail = 1024 - rot;
+    int TB = 0, TV = 0;
+    for (int per = 1; per <= kJacItems; ++per) {
+      TB = (nblk + per - 1) / per;
+      TV = (nv + per - 1) / per;
+      TB = (TB + 31) / 32 * 32;
+      TV = (TV + 31) / 32 * 32;
+      if (TB + TV <= avail) break;
+    }
+    if (TB + TV > avail || (nblk + TB - 1) / TB > kJacItems || (nv + TV - 1) / TV > kJacItems)
+      return SHG_ERR_UNSUPPORTED;
+    if (cudaFuncSetAttribute(jacobi_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, static_cast<int>(smem)) !=
+        cudaSuccess)
       return SHG_ERR_CUDA;
-    jacobi_kernel<true><<<1, threads, smem, st>>>(static_cast<int>(k), G, V, scratch);
+    jacobi_kernel<<<1, TB + TV + rot, smem, st>>>(static_cast<int>(k), G, V, TB, TV);
   } else {
     // too large for one SM: the whole grid works on every round (cooperative launch)
     static int blocks_per_sm = 0;
