@@ -29,7 +29,7 @@ bool tc_variant(int v) { return v == SHG_SPLIT_F16 || v == SHG_SPLIT_BF16X3 || v
 
 // Workspace layout of shg_rsvd.
 struct RsvdLayout {
-  size_t Y, T, Z, H, Bt, small, Vk, lam, Up, Ups, total;
+  size_t Y, T, Z, H, Bt, small, eig, Vk, lam, Up, Ups, total;
 };
 RsvdLayout rsvd_layout(int64_t m, int64_t n, int64_t k, int64_t rank) {
   const int64_t ldk = round8(k), mx = m > n ? m : n;
@@ -46,6 +46,7 @@ RsvdLayout rsvd_layout(int64_t m, int64_t n, int64_t k, int64_t rank) {
   L.H = take(mx * ldk * 2);
   L.Bt = take(n * ldk * 4);
   L.small = take(cholqr_small_bytes(k));
+  L.eig = take(jacobi_log_bytes(k));
   L.Vk = take(k * k * 4);
   L.lam = take(2 * k * 8);
   L.Up = take(k * rank * 4);
@@ -256,7 +257,7 @@ int shg_rsvd(int64_t m, int64_t n, int64_t rank, int64_t oversampling, int power
   const SmallWs sw = small_ws(small, k);
   double* G = sw.G;
   SHG_TRY(gram_f64(n, k, Bt, ldk, G, st));
-  SHG_TRY(jacobi_eig(k, G, Vk, sw.jac, st));
+  SHG_TRY(jacobi_eig(k, G, Vk, sw.jac, jacobi_log_bytes(k) ? w + L.eig : nullptr, st));
   SHG_TRY(rayleigh_sort(k, rank, G, Vk, lam, S, Up, Ups, st));
   // lift: U = Q U'; V = B^T U' Sigma^-1
   SHG_TRY(simt_gemm(m, rank, k, Y, ldk, 0, Up, rank, 0, U, rank, 0, 1, 0, 0, 0, st));

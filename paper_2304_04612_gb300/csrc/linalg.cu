@@ -342,43 +342,77 @@ __device__ __forceinline__ bool jac_rot(float app, float aqq, float apq, float& 
   return true;
 }
 
-// Eigendecomposition of the symmetric k x k matrix whose upper triangle is
-// in G (FP64): A = sigma G in FP32 (sigma a power of two near 1 / max diag),
-// V = I, then sweeps of the parallel cyclic Jacobi method until a sweep
-// applies no rotation (at most 40 sweeps).  Writes V (k x k FP32, columns =
-// eigenvectors).  One CTA; everything lives in shared memory.
-//   Pairing (the round-robin "circle" order, kp = k rounded up to even,
-//   h = kp / 2 slots, n1 = kp - 1): at round r slot i holds
-//     a_i(r) = 0 (i = 0) or ((r + i - 1) mod n1) + 1,  b_i(r) = ((r - 1 - i) mod n1) + 1,
-//   so between rounds a_i <- a_{i+1} (1 <= i < h - 1), a_{h-1} <- b_{h-1},
-//   b_i <- b_{i-1} (i >= 1) and b_0 <- a_1.  The slot of round r that each
-//   index of round r + 1 comes from is therefore fixed, and no thread needs
-//   an index table.
-//   Roles (whole warps): block threads own fixed pair blocks (t, u), t <= u,
-//   and write each 2 x 2 block of J^T A J to the second buffer (and to its
-//   mirror, so A stays exactly symmetric); V threads own fixed (slot,
-//   8-column) pieces of V^T and rotate them; rotation threads (one per
-//   slot) build round r + 1's rotations from the old A at the same time.
-//   One barrier per round.  last_rot holds the latest sweep that applies a
-//   rotation; sweep s ends the loop when last_rot < s.
-// Shared layout: JPair[2][h], the two A buffers (kp x (kp + 1) floats each),
-// V^T (kp x ldv, ldv = kp rounded up to 8).
-constexpr int kJacItems = 8;  // most blocks (or V pieces) one thread owns
-
-__host__ __device__ inline int jac_ldv(int kp) { return (kp + 7) & ~7; }
-__host__ __device__ inline size_t jac_cta_floats(int kp) {
-  return static_cast<size_t>(4 * kp) + 2 * static_cast<size_t>(kp) * (kp + 1) + static_cast<size_t>(kp) * jac_ldv(kp);
+// Indices (a, b) of slot t at round r of the round-robin ("circle")
+// pairing of kp = n1 + 1 indices: a = 0 (t = 0) or ((r + t - 1) mod n1) + 1,
+// b = ((r - 1 - t) mod n1) + 1, for 0 <= r <= n1 and 0 <= t < kp / 2.
+__device__ __forceinline__ void circle_ab(int t, int r, int n1, int& a, int& b) {
+  a = r + t - 1;
+  if (a >= n1) a -= n1;
+  a = (t == 0) ? 0 : a + 1;
+  b = r - 1 - t;
+  if (b < 0) b += n1;
+  b += 1;
 }
 
-__global__ void __launch_bounds__(1024) jacobi_kernel(int k, const double* __restrict__ G, float* __restrict__ Vout,
-                                                     int TB, int TV) {
+// Element (x, y) of a symmetric matrix kept as its upper triangle.
+__device__ __forceinline__ int sym_at(int x, int y, int ld) { return min(x, y) * ld + max(x, y); }
+
+// Element (x, y) of J^T A J (A symmetric, upper triangle) where x is side sx
+// of pair (p1, q1, c1, s1) and y side sy of pair (p2, q2, c2, s2); same:
+// both are the same pair, whose rotated off-diagonal is exactly 0.
+__device__ __forceinline__ float jac_elem_sym(const float* A, int ld, int p1, int q1, float2 r1, int sx, int p2,
+                                              int q2, float2 r2, int sy, bool same) {
+  float n00, n01, n10, n11;
+  jac_block(A[sym_at(p1, p2, ld)], A[sym_at(p1, q2, ld)], A[sym_at(q1, p2, ld)], A[sym_at(q1, q2, ld)], r1.x, r1.y,
+            r2.x, r2.y, n00, n01, n10, n11);
+  if (same && sx != sy && r1.y != 0.0f) return 0.0f;
+  return sx ? (sy ? n11 : n10) : (sy ? n01 : n00);
+}
+
+// Eigenvalues of the symmetric k x k matrix whose upper triangle is in G
+// (FP64), by the parallel cyclic Jacobi method: A = sigma G in FP32 (sigma a
+// power of two near 1 / max diag), then sweeps until a sweep applies no
+// rotation (at most kJacSweeps).  One CTA; A lives in shared memory, and a
+// round is bound by shared-memory traffic, which the layout keeps low.  The
+// eigenvectors are not accumulated here: every round's rotations (c, s) go
+// to `log` (round rho, slot t at rho * h + t) and *rounds_out receives the
+// number of rounds that count; jac_apply_v_kernel multiplies them out.
+//   Pairing: the circle order of circle_ab (kp = k rounded up to even,
+//   h = kp / 2 slots, n1 = kp - 1).  Between rounds a_i <- a_{i+1}
+//   (1 <= i < h - 1), a_{h-1} <- b_{h-1}, b_i <- b_{i-1} (i >= 1) and
+//   b_0 <- a_1, so the slot of round r that each index of round r + 1 comes
+//   from is fixed; every thread computes slot indices, and only the
+//   rotations (c, s) go through shared memory.
+//   A is kept as its upper triangle (each element read and written once per
+//   round).
+//   Roles (whole warps): block threads own fixed pair blocks (t, u), t <= u,
+//   in folded-triangle order (rows i and h - 1 - i of the triangle form one
+//   row of h + 1 blocks) and write each 2 x 2 block of J^T A J to the second
+//   buffer; rotation threads (one per slot) build round r + 1's rotations
+//   from the old A at the same time.  The rotation chain (about 200
+//   dependent instructions) sets the length of a round, so the rotation
+//   warps get a warp scheduler to themselves: warp w issues from scheduler
+//   w mod 4, the rotation warps are warps 0, 4, 8, ... and the other warps
+//   on that scheduler only wait at the barrier.  One barrier per round.
+//   last_rot holds the latest sweep that applies a rotation; sweep s ends
+//   the loop when last_rot < s, and the rounds of sweeps 0 .. s - 1 count.
+// Shared layout: (c, s)[2][h], then the two A buffers (kp x (kp + 1) floats
+// each, upper triangles).
+constexpr int kJacSweeps = 40;
+constexpr int kJacItems = 6;  // most blocks (or V pieces) one thread owns
+
+__host__ __device__ inline size_t jac_cta_floats(int kp) {
+  return static_cast<size_t>(2 * kp) + 2 * static_cast<size_t>(kp) * (kp + 1);
+}
+
+__global__ void __launch_bounds__(768) jacobi_kernel(int k, const double* __restrict__ G, float2* __restrict__ log,
+                                                    int* __restrict__ rounds_out, int TB) {
   extern __shared__ __align__(16) float smf[];
   const int kp = k + (k & 1);
   const int h = kp / 2, n1 = kp - 1;
-  const int ld = kp + 1, ldv = jac_ldv(kp);
-  JPair* pairs = reinterpret_cast<JPair*>(smf);  // [2][h]
-  float* const M0 = smf + 8 * h;
-  float* const Vt = M0 + 2 * kp * ld;
+  const int ld = kp + 1;
+  float2* rots = reinterpret_cast<float2*>(smf);  // [2][h]
+  float* const M0 = smf + 4 * h;
   __shared__ int last_rot;
   __shared__ double red[32];
   __shared__ double dmax;
@@ -389,140 +423,220 @@ __global__ void __launch_bounds__(1024) jacobi_kernel(int k, const double* __res
   const double sigma = ldexp(1.0, -((dmax > 0.0) ? ilogb(dmax) : 0));
   for (int e = tid; e < kp * kp; e += nt) {
     const int i = e / kp, j = e - i * kp;
-    float v = 0.0f;
-    if (i < k && j < k) v = static_cast<float>(G[min(i, j) * k + max(i, j)] * sigma);
-    M0[i * ld + j] = v;
+    if (j >= i) M0[i * ld + j] = (j < k) ? static_cast<float>(G[i * k + j] * sigma) : 0.0f;
   }
-  for (int e = tid; e < kp * ldv; e += nt) {
-    const int i = e / ldv, j = e - i * ldv;
-    Vt[e] = (i == j) ? 1.0f : 0.0f;
-  }
-  const int nblk = h * (h + 1) / 2, nc8 = ldv / 8, nv = h * nc8;
-  const bool is_blk = tid < TB;
-  const bool is_v = !is_blk && tid < TB + TV;
-  const int rt = tid - TB - TV;
+  const int nblk = h * (h + 1) / 2;
+  // warps 0, 4, 8, ...: rotation warps (then idle); the others: block warps
+  const int warp = tid >> 5, lane = tid & 31;
+  const bool sched0 = (warp & 3) == 0;
+  const int wt = sched0 ? -1 : ((warp >> 2) * 3 + (warp & 3) - 1) * 32 + lane;  // worker thread index
+  const bool is_blk = !sched0 && wt < TB;
+  const int rt = sched0 ? (warp >> 2) * 32 + lane : -1;
   const bool rotor = rt >= 0 && rt < h;
-  // fixed items: blocks in folded-triangle order (rectangle row i = rows i
-  // and h - 1 - i of the triangle, h + 1 blocks), or V pieces (slot, chunk)
-  int it_a[kJacItems], it_b[kJacItems];
+  // fixed blocks (t, u) in folded-triangle order
+  int it[kJacItems];  // t | u << 16, or -1
 #pragma unroll
   for (int c = 0; c < kJacItems; ++c) {
-    it_a[c] = -1;
-    it_b[c] = 0;
-    if (is_blk) {
-      const int bi = tid + c * TB;
-      if (bi < nblk) {
-        const int i = bi / (h + 1), j = bi - i * (h + 1);
-        if (j < h - i) {
-          it_a[c] = i;
-          it_b[c] = i + j;
-        } else {
-          it_a[c] = h - 1 - i;
-          it_b[c] = j - 1;
-        }
-      }
-    } else if (is_v) {
-      const int vi = tid - TB + c * TV;
-      if (vi < nv) {
-        it_a[c] = vi / nc8;
-        it_b[c] = (vi - (vi / nc8) * nc8) * 8;
-      }
+    it[c] = -1;
+    const int bi = wt + c * TB;
+    if (is_blk && bi < nblk) {
+      const int i = bi / (h + 1), j = bi - i * (h + 1);
+      it[c] = (j < h - i) ? (i | ((i + j) << 16)) : ((h - 1 - i) | ((j - 1) << 16));
     }
   }
-  // slot rt's indices (round 0, then advanced) and the slots of the previous
-  // round its a- and b-index come from
-  int pa = 0, pb = 0;
+  // the slots of the previous round that slot rt's a- and b-index come from
   const int srcA = (rt <= 0) ? 0 : min(rt + 1, h - 1);
   const int srcB = (rt >= 1) ? rt - 1 : (h >= 2 ? 1 : 0);
-  if (rotor) {
-    pa = (rt == 0) ? 0 : rt;
-    pb = ((n1 - 1 - rt) % n1 + n1) % n1 + 1;
-  }
   __syncthreads();
   if (rotor) {
+    int pa, pb;
+    circle_ab(rt, 0, n1, pa, pb);
     const int p = min(pa, pb), q = max(pa, pb);
     float c, s;
     if (jac_rot(M0[p * ld + p], M0[q * ld + q], M0[p * ld + q], c, s)) last_rot = 0;
-    pairs[rt] = JPair{p, q, c, s};
+    rots[rt] = make_float2(c, s);
+    log[rt] = make_float2(c, s);
   }
   __syncthreads();
-  int buf = 0, abuf = 0;
-  for (int sweep = 0; sweep < 40; ++sweep) {
+  // Rotation thread: the ten elements of the old A its next rotation needs
+  // (the diagonal 2 x 2 blocks of its two source slots and their common
+  // block) are addressed one round ahead, so that its loads are the first
+  // in the shared-memory queue when the round starts.
+  int rix[10], rfl = 0;
+  auto plan = [&](int r) {
+    int pa, pb, aA, bA, aB, bB;
+    circle_ab(rt, r + 1, n1, pa, pb);
+    circle_ab(srcA, r, n1, aA, bA);
+    circle_ab(srcB, r, n1, aB, bB);
+    const int pA = min(aA, bA), qA = max(aA, bA), pB = min(aB, bB), qB = max(aB, bB);
+    const int sxa = (pa == pA) ? 0 : 1, sxb = (pb == pB) ? 0 : 1;
+    const bool a_low = pa < pb;
+    const int tp = a_low ? srcA : srcB, tq = a_low ? srcB : srcA;
+    const int pp = a_low ? pA : pB, qp = a_low ? qA : qB, pq = a_low ? pB : pA, qq = a_low ? qB : qA;
+    const int sp = a_low ? sxa : sxb, sq = a_low ? sxb : sxa;
+    const bool pfirst = tp <= tq;
+    const int p1 = pfirst ? pp : pq, q1 = pfirst ? qp : qq, p2 = pfirst ? pq : pp, q2 = pfirst ? qq : qp;
+    rix[0] = pp * ld + pp;
+    rix[1] = pp * ld + qp;
+    rix[2] = qp * ld + qp;
+    rix[3] = pq * ld + pq;
+    rix[4] = pq * ld + qq;
+    rix[5] = qq * ld + qq;
+    rix[6] = sym_at(p1, p2, ld);
+    rix[7] = sym_at(p1, q2, ld);
+    rix[8] = sym_at(q1, p2, ld);
+    rix[9] = sym_at(q1, q2, ld);
+    rfl = sp | (sq << 1) | (pfirst ? 4 : 0) | (tp == tq ? 8 : 0) | (a_low ? 16 : 0);
+  };
+  if (rotor) plan(0);
+  int buf = 0;
+  int sweeps = kJacSweeps;
+  for (int sweep = 0; sweep < kJacSweeps; ++sweep) {
     for (int r = 0; r < n1; ++r) {
-      const float* const A = M0 + abuf * (kp * ld);
-      float* const B = M0 + (abuf ^ 1) * (kp * ld);
-      const JPair* cur = pairs + buf * h;
+      const float* const A = M0 + buf * (kp * ld);
+      float* const B = M0 + (buf ^ 1) * (kp * ld);
+      const float2* cur = rots + buf * h;
       if (is_blk) {
+        // two blocks at a time: all loads, then all arithmetic and stores
 #pragma unroll
-        for (int c = 0; c < kJacItems; ++c) {
-          if (it_a[c] >= 0) {
-            const int t = it_a[c], u = it_b[c];
-            const JPair P1 = cur[t], P2 = cur[u];
-            float n00, n01, n10, n11;
-            jac_block(A[P1.p * ld + P2.p], A[P1.p * ld + P2.q], A[P1.q * ld + P2.p], A[P1.q * ld + P2.q], P1.c,
-                      P1.s, P2.c, P2.s, n00, n01, n10, n11);
-            if (t == u) {
-              if (P1.s != 0.0f) n01 = 0.0f;
-              B[P1.p * ld + P1.p] = n00;
-              B[P1.q * ld + P1.q] = n11;
-              B[P1.p * ld + P1.q] = n01;
-              B[P1.q * ld + P1.p] = n01;
-            } else {
-              B[P1.p * ld + P2.p] = n00;
-              B[P2.p * ld + P1.p] = n00;
-              B[P1.p * ld + P2.q] = n01;
-              B[P2.q * ld + P1.p] = n01;
-              B[P1.q * ld + P2.p] = n10;
-              B[P2.p * ld + P1.q] = n10;
-              B[P1.q * ld + P2.q] = n11;
-              B[P2.q * ld + P1.q] = n11;
+        for (int g = 0; g < kJacItems; g += 2) {
+          int ix[2][4];
+          float v[2][4];
+          float2 R1[2], R2[2];
+#pragma unroll
+          for (int e = 0; e < 2; ++e) {
+            if (it[g + e] >= 0) {
+              const int t = it[g + e] & 0xffff, u = it[g + e] >> 16;
+              int a1, b1, a2, b2;
+              circle_ab(t, r, n1, a1, b1);
+              circle_ab(u, r, n1, a2, b2);
+              const int p1 = min(a1, b1), q1 = max(a1, b1), p2 = min(a2, b2), q2 = max(a2, b2);
+              ix[e][0] = sym_at(p1, p2, ld);
+              ix[e][1] = sym_at(p1, q2, ld);
+              ix[e][2] = sym_at(q1, p2, ld);
+              ix[e][3] = sym_at(q1, q2, ld);
+              R1[e] = cur[t];
+              R2[e] = cur[u];
+#pragma unroll
+              for (int z = 0; z < 4; ++z) v[e][z] = A[ix[e][z]];
             }
           }
-        }
-      } else if (is_v) {
-        // V <- V J on the transposed rows p, q
 #pragma unroll
-        for (int c = 0; c < kJacItems; ++c) {
-          if (it_a[c] >= 0) {
-            const JPair P = cur[it_a[c]];
-            float4* vp = reinterpret_cast<float4*>(Vt + P.p * ldv + it_b[c]);
-            float4* vq = reinterpret_cast<float4*>(Vt + P.q * ldv + it_b[c]);
-#pragma unroll
-            for (int hh = 0; hh < 2; ++hh) {
-              const float4 x = vp[hh], y = vq[hh];
-              vp[hh] = make_float4(__fmaf_rn(-P.s, y.x, __fmul_rn(P.c, x.x)), __fmaf_rn(-P.s, y.y, __fmul_rn(P.c, x.y)),
-                                   __fmaf_rn(-P.s, y.z, __fmul_rn(P.c, x.z)), __fmaf_rn(-P.s, y.w, __fmul_rn(P.c, x.w)));
-              vq[hh] = make_float4(__fmaf_rn(P.s, x.x, __fmul_rn(P.c, y.x)), __fmaf_rn(P.s, x.y, __fmul_rn(P.c, y.y)),
-                                   __fmaf_rn(P.s, x.z, __fmul_rn(P.c, y.z)), __fmaf_rn(P.s, x.w, __fmul_rn(P.c, y.w)));
+          for (int e = 0; e < 2; ++e) {
+            if (it[g + e] >= 0) {
+              float n00, n01, n10, n11;
+              jac_block(v[e][0], v[e][1], v[e][2], v[e][3], R1[e].x, R1[e].y, R2[e].x, R2[e].y, n00, n01, n10, n11);
+              if ((it[g + e] & 0xffff) == (it[g + e] >> 16)) {
+                if (R1[e].y != 0.0f) n01 = 0.0f;
+                n10 = n01;  // the same element as n01 on the diagonal block
+              }
+              B[ix[e][0]] = n00;
+              B[ix[e][1]] = n01;
+              B[ix[e][2]] = n10;
+              B[ix[e][3]] = n11;
             }
           }
         }
       } else if (rotor) {
         // rotation of slot rt for round r + 1 from the same old A
-        pa = (rt == 0) ? 0 : (pa == n1 ? 1 : pa + 1);
-        pb = (pb == n1) ? 1 : pb + 1;
-        const JPair PA = cur[srcA], PB = cur[srcB];
-        const int sxa = (pa == PA.p) ? 0 : 1, sxb = (pb == PB.p) ? 0 : 1;
-        const bool a_low = pa < pb;
-        const JPair Pp = a_low ? PA : PB, Pq = a_low ? PB : PA;
-        const int sp = a_low ? sxa : sxb, sq = a_low ? sxb : sxa;
-        const int tp = a_low ? srcA : srcB, tq = a_low ? srcB : srcA;
-        const float app = jac_elem(A, ld, Pp, sp, Pp, sp, true);
-        const float aqq = jac_elem(A, ld, Pq, sq, Pq, sq, true);
-        const float apq = (tp <= tq) ? jac_elem(A, ld, Pp, sp, Pq, sq, tp == tq) : jac_elem(A, ld, Pq, sq, Pp, sp, false);
+        float ev[10];
+#pragma unroll
+        for (int z = 0; z < 10; ++z) ev[z] = A[rix[z]];
+        const float2 RA = cur[srcA], RB = cur[srcB];
+        const int sp = rfl & 1, sq = (rfl >> 1) & 1;
+        const bool pfirst = (rfl & 4) != 0, same = (rfl & 8) != 0, a_low = (rfl & 16) != 0;
+        const float2 Rp = a_low ? RA : RB, Rq = a_low ? RB : RA;
+        float n00, n01, n10, n11;
+        jac_block(ev[0], ev[1], ev[1], ev[2], Rp.x, Rp.y, Rp.x, Rp.y, n00, n01, n10, n11);
+        const float app = sp ? n11 : n00;
+        jac_block(ev[3], ev[4], ev[4], ev[5], Rq.x, Rq.y, Rq.x, Rq.y, n00, n01, n10, n11);
+        const float aqq = sq ? n11 : n00;
+        const float2 R1 = pfirst ? Rp : Rq, R2 = pfirst ? Rq : Rp;
+        const int sx = pfirst ? sp : sq, sy = pfirst ? sq : sp;
+        jac_block(ev[6], ev[7], ev[8], ev[9], R1.x, R1.y, R2.x, R2.y, n00, n01, n10, n11);
+        const float apq = (same && sx != sy && R1.y != 0.0f) ? 0.0f : (sx ? (sy ? n11 : n10) : (sy ? n01 : n00));
         float c, s;
         if (jac_rot(app, aqq, apq, c, s)) last_rot = (r + 1 == n1) ? sweep + 1 : sweep;
-        pairs[(buf ^ 1) * h + rt] = JPair{min(pa, pb), max(pa, pb), c, s};
+        rots[(buf ^ 1) * h + rt] = make_float2(c, s);
+        if (sweep * n1 + r + 1 < kJacSweeps * n1) log[static_cast<size_t>(sweep * n1 + r + 1) * h + rt] = make_float2(c, s);
+        plan(r + 1 == n1 ? 0 : r + 1);
       }
       __syncthreads();
-      abuf ^= 1;
       buf ^= 1;
     }
-    if (last_rot < sweep) break;
+    if (last_rot < sweep) {
+      sweeps = sweep;
+      break;
+    }
   }
-  for (int e = tid; e < k * k; e += nt) {
+  if (tid == 0) *rounds_out = sweeps * n1;
+}
+
+// V = J_0 J_1 ... J_{R-1} from the rotation log of jacobi_kernel (round rho
+// rotates, in every slot t, columns (p, q) of V by (c, s) of log[rho h + t]).
+// Rows of V are independent under V <- V J, so CTA b builds rows
+// [b RB, b RB + RB) in shared memory from identity rows, thread t applying
+// slot t's rotation to all of them (loads first), one barrier per round (a
+// warp barrier when one warp covers the slots).  The log is read eight
+// rounds ahead.  Writes Vout (k x k, row-major, columns = eigenvectors).
+template <int RB>
+__global__ void __launch_bounds__(128) jac_apply_v_kernel(int k, const float2* __restrict__ log,
+                                                          const int* __restrict__ rounds, float* __restrict__ Vout) {
+  extern __shared__ float vs[];  // RB x kp
+  const int kp = k + (k & 1), h = kp / 2, n1 = kp - 1;
+  const int row0 = blockIdx.x * RB;
+  const int t = threadIdx.x, nt = blockDim.x;
+  const bool one_warp = nt == 32;
+  for (int e = t; e < RB * kp; e += nt) {
+    const int i = e / kp, j = e - i * kp;
+    vs[e] = (row0 + i == j) ? 1.0f : 0.0f;
+  }
+  __syncthreads();
+  const int R = *rounds;
+  const bool on = t < h;
+  float2 cur[8], nxt[8];
+#pragma unroll
+  for (int u = 0; u < 8; ++u)
+    cur[u] = (on && u < R) ? log[static_cast<size_t>(u) * h + t] : make_float2(1.0f, 0.0f);
+  int rm = 0;  // round mod n1
+  for (int g = 0; g < R; g += 8) {
+#pragma unroll
+    for (int u = 0; u < 8; ++u)
+      nxt[u] = (on && g + 8 + u < R) ? log[static_cast<size_t>(g + 8 + u) * h + t] : make_float2(1.0f, 0.0f);
+#pragma unroll
+    for (int u = 0; u < 8; ++u) {
+      if (g + u < R) {
+        if (on) {
+          int a, b;
+          circle_ab(t, rm, n1, a, b);
+          const int p = min(a, b), q = max(a, b);
+          const float c = cur[u].x, sn = cur[u].y;
+          float x[RB], y[RB];
+#pragma unroll
+          for (int i = 0; i < RB; ++i) {
+            x[i] = vs[i * kp + p];
+            y[i] = vs[i * kp + q];
+          }
+#pragma unroll
+          for (int i = 0; i < RB; ++i) {
+            vs[i * kp + p] = __fmaf_rn(-sn, y[i], __fmul_rn(c, x[i]));
+            vs[i * kp + q] = __fmaf_rn(sn, x[i], __fmul_rn(c, y[i]));
+          }
+        }
+        if (++rm == n1) rm = 0;
+        if (one_warp)
+          __syncwarp();
+        else
+          __syncthreads();
+      }
+    }
+#pragma unroll
+    for (int u = 0; u < 8; ++u) cur[u] = nxt[u];
+  }
+  __syncthreads();
+  for (int e = t; e < RB * k; e += nt) {
     const int i = e / k, j = e - i * k;
-    Vout[e] = Vt[j * ldv + i];
+    if (row0 + i < k) Vout[static_cast<size_t>(row0 + i) * k + j] = vs[i * kp + j];
   }
 }
 
@@ -783,6 +897,12 @@ int block_threads(int64_t work) {
 }  // namespace
 
 // ------------------------------------------------------------------ host API
+size_t jacobi_log_bytes(int64_t k) {
+  const int64_t kp = k + (k & 1);
+  if (jac_cta_floats(static_cast<int>(kp)) * sizeof(float) > 200 * 1024) return 0;
+  return 256 + static_cast<size_t>(kJacSweeps) * (kp - 1) * (kp / 2) * sizeof(float2);
+}
+
 size_t align256(size_t x) { return (x + 255) & ~size_t(255); }
 
 namespace {
@@ -850,31 +970,35 @@ int chol_inv(int64_t k, const double* G, float* Rinv, double* scratch, int32_t* 
   return cuda_status(cudaGetLastError());
 }
 
-int jacobi_eig(int64_t k, const double* G, float* V, float* scratch, cudaStream_t st) {
+int jacobi_eig(int64_t k, const double* G, float* V, float* scratch, void* eig, cudaStream_t st) {
   if (k > 1024) return SHG_ERR_UNSUPPORTED;
   const int64_t kp = k + (k & 1);
   const size_t smem = jac_cta_floats(static_cast<int>(kp)) * sizeof(float);
-  if (smem_fits(smem)) {
-    // one CTA: whole warps of block threads and V threads with about the
-    // same number of items each, then one rotation thread per slot
-    const int h = static_cast<int>(kp / 2);
-    const int nblk = h * (h + 1) / 2, nv = h * (jac_ldv(static_cast<int>(kp)) / 8);
-    const int rot = (h + 31) / 32 * 32;
-    const int avail = 1024 - rot;
-    int TB = 0, TV = 0;
-    for (int per = 1; per <= kJacItems; ++per) {
-      TB = (nblk + per - 1) / per;
-      TV = (nv + per - 1) / per;
-      TB = (TB + 31) / 32 * 32;
-      TV = (TV + 31) / 32 * 32;
-      if (TB + TV <= avail) break;
-    }
-    if (TB + TV > avail || (nblk + TB - 1) / TB > kJacItems || (nv + TV - 1) / TV > kJacItems)
-      return SHG_ERR_UNSUPPORTED;
+  // one CTA: whole warps of block threads with at most kJacItems blocks each
+  // on schedulers 1-3, the rotation warps on scheduler 0 (at most 768
+  // threads: 18 worker warps, 6 warps on scheduler 0)
+  const int h = static_cast<int>(kp / 2);
+  const int nblk = h * (h + 1) / 2;
+  const int rot_warps = (h + 31) / 32;
+  int TB = 0;
+  for (int per = 1; per <= kJacItems; ++per) {
+    TB = ((nblk + per - 1) / per + 31) / 32 * 32;
+    if (TB <= 18 * 32) break;
+  }
+  if (eig && smem_fits(smem) && h <= 128 && TB <= 18 * 32 && rot_warps <= 6 && (nblk + TB - 1) / TB <= kJacItems) {
+    const int groups = std::max(rot_warps, TB / 32 / 3 + ((TB / 32) % 3 ? 1 : 0));
+    int* rounds = static_cast<int*>(eig);
+    float2* log = reinterpret_cast<float2*>(static_cast<uint8_t*>(eig) + 256);
     if (cudaFuncSetAttribute(jacobi_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, static_cast<int>(smem)) !=
         cudaSuccess)
       return SHG_ERR_CUDA;
-    jacobi_kernel<<<1, TB + TV + rot, smem, st>>>(static_cast<int>(k), G, V, TB, TV);
+    jacobi_kernel<<<1, groups * 128, smem, st>>>(static_cast<int>(k), G, log, rounds, TB);
+    if (cudaGetLastError() != cudaSuccess) return SHG_ERR_CUDA;
+    // V: eight rows per CTA, one thread per slot
+    constexpr int rb = 8;
+    const int threads = (h + 31) / 32 * 32;
+    jac_apply_v_kernel<rb><<<static_cast<unsigned>((k + rb - 1) / rb), threads, rb * kp * sizeof(float), st>>>(
+        static_cast<int>(k), log, rounds, V);
   } else {
     // too large for one SM: the whole grid works on every round (cooperative launch)
     static int blocks_per_sm = 0;

@@ -21,7 +21,12 @@ SmallWs small_ws(void* base, int64_t k);
 int gram_f64(int64_t m, int64_t k, const float* X, int64_t ldx, double* G, cudaStream_t st);
 // Rinv = FP32(R^-1) with G = R^T R (FP64, upper Cholesky).
 int chol_inv(int64_t k, const double* G, float* Rinv, double* scratch, int32_t* flags, cudaStream_t st);
-int jacobi_eig(int64_t k, const double* G, float* V, float* scratch, cudaStream_t st);
+// Eigenvectors V (k x k FP32, columns) of the symmetric matrix whose upper
+// triangle is G.  `scratch`: jacobi_scratch_floats(k) floats; `eig`:
+// jacobi_log_bytes(k) bytes (the rotation log of the single-CTA solver; it
+// is used when non-null and non-zero in size, else the grid solver runs).
+int jacobi_eig(int64_t k, const double* G, float* V, float* scratch, void* eig, cudaStream_t st);
+size_t jacobi_log_bytes(int64_t k);
 int rayleigh_sort(int64_t k, int64_t p, const double* G, const float* V, double* lam, float* S, float* Up,
                   float* Ups, cudaStream_t st);
 int to_f16(int64_t rows, int64_t cols, const float* x, int64_t ldx, uint16_t* y, int64_t ldy, cudaStream_t st);
