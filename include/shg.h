@@ -146,6 +146,42 @@ int shg_sgemm(int64_t m, int64_t n, int64_t kk,
               float* C, int64_t ldc, int accumulate, void* stream);
 
 /*
+ * Autotuner of the tensor-core projection (not in the paper).  A launch of
+ * the split-precision GEMM has a few free parameters: the depths of its
+ * FP32 A staging ring and of its B tile ring (2..6), the number of K blocks
+ * between round-to-nearest drains of the hi product (2, 4 or 8) and whether
+ * the grid runs one CTA group per N tile.  Calls of one shape class (the
+ * variant and transposition, the N tiling, and m and n to within a factor
+ * of two) share a configuration.
+ *   shg_autotune_project times every candidate on the caller's operands
+ *   (arguments as in shgemm_project; Y is overwritten; `reps` timed launches
+ *   per candidate, 1..100), synchronising `stream`, and caches the fastest
+ *   for the class; later projections of the class (shgemm_project, the
+ *   projections of shg_rsvd and shg_rsvd_batched) use it.  A class that is
+ *   already cached is not timed again.  It may not run while `stream` is
+ *   being captured (SHG_ERR_UNSUPPORTED), nor for SHG_FP32_SIMT.
+ *   config_out (host, nullable): {A stages, B stages, drain K blocks,
+ *   grouping, 1 if the class was cached before the call}.
+ *   shg_autotune_lookup reports the cached configuration of a class
+ *   (config_out[4] = 0 when it has none; the other entries are then the
+ *   built-in defaults).  shg_autotune_clear empties the cache.
+ *   shg_rsvd_batched_autotune tunes the projection Y_i = A_i Omega_i of
+ *   every shape class in a batch (arguments as in shg_rsvd_batched, with the
+ *   batch's workspace as scratch; Omega_i is the Philox stream the batched
+ *   call generates from `seed`); *tuned_out (nullable) receives the number
+ *   of classes it timed.
+ */
+int shg_autotune_project(int64_t m, int64_t n, int64_t k, const float* A, int64_t lda, int trans_a,
+                         const uint16_t* omega, int64_t ldo, float* Y, int64_t ldy, int variant, int reps,
+                         int32_t* d_flags, void* stream, int32_t* config_out);
+int shg_autotune_lookup(int64_t m, int64_t n, int64_t k, int trans_a, int variant, int32_t* config_out);
+int shg_autotune_clear(void);
+int shg_rsvd_batched_autotune(int batch, const int64_t* m, const int64_t* n, const int64_t* rank,
+                              int64_t oversampling, const float* const* A, const int64_t* lda, uint64_t seed,
+                              void* workspace, size_t ws_bytes, int reps, int32_t* d_flags, void* stream,
+                              int32_t* tuned_out);
+
+/*
  * Gram matrix G = X^T X of an m x k FP32 matrix, the first step of every
  * CholeskyQR pass (Algorithms 1 and 2 orthonormalise with QR; the library
  * uses CholeskyQR2).  The products x_ri x_rj are exact; they are summed

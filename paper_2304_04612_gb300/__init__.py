@@ -131,6 +131,63 @@ def shgemm_project(A: torch.Tensor, omega: torch.Tensor, variant="f16", trans_a:
     return out
 
 
+def _config(arr) -> dict:
+    return {"a_stages": arr[0], "b_stages": arr[1], "drain_kblocks": arr[2], "n_groups": bool(arr[3]),
+            "cached": bool(arr[4])}
+
+
+def shg_autotune_project(A: torch.Tensor, omega: torch.Tensor, variant="f16", trans_a: bool = False, reps: int = 3,
+                         out: torch.Tensor | None = None, flags: torch.Tensor | None = None, stream=None) -> dict:
+    """Time the launch configurations of the projection A @ omega and cache
+    the fastest for its shape class (synchronises; ``out`` is overwritten)."""
+    v = _variant(variant)
+    lda = _mat(A, "A", (torch.float32,))
+    ldo = _mat(omega, "omega", (torch.bfloat16,) if v in (1, 2) else (torch.float16,))
+    m = A.shape[1] if trans_a else A.shape[0]
+    n = A.shape[0] if trans_a else A.shape[1]
+    k = omega.shape[1]
+    if omega.shape[0] != n:
+        raise ValueError(f"omega has {omega.shape[0]} rows, expected {n}")
+    if out is None:
+        out = torch.empty(m, k, dtype=torch.float32, device=A.device)
+    ldy = _mat(out, "out", (torch.float32,))
+    fl = flags if flags is not None else new_flags(A.device)
+    cfg = (ctypes.c_int32 * 5)()
+    _check(_lib.load().shg_autotune_project(m, n, k, _ptr(A), lda, int(trans_a), _ptr(omega), ldo, _ptr(out), ldy,
+                                            v, reps, _ptr(fl), _stream(stream), cfg), "shg_autotune_project")
+    return _config(cfg)
+
+
+def shg_autotune_lookup(m: int, n: int, k: int, trans_a: bool = False, variant="f16") -> dict:
+    cfg = (ctypes.c_int32 * 5)()
+    _check(_lib.load().shg_autotune_lookup(m, n, k, int(trans_a), _variant(variant), cfg), "shg_autotune_lookup")
+    return _config(cfg)
+
+
+def shg_autotune_clear() -> None:
+    _check(_lib.load().shg_autotune_clear(), "shg_autotune_clear")
+
+
+def shg_rsvd_batched_autotune(As, ranks, oversampling: int, seed: int = 0, reps: int = 3,
+                              workspace: torch.Tensor | None = None, flags: torch.Tensor | None = None,
+                              stream=None) -> int:
+    """Tune the projection of every shape class of a batch; returns the
+    number of classes timed."""
+    b = len(As)
+    ms, ns = [int(A.shape[0]) for A in As], [int(A.shape[1]) for A in As]
+    ldas = [_mat(A, f"A[{i}]", (torch.float32,)) for i, A in enumerate(As)]
+    dev_ = As[0].device
+    need = rsvd_batched_workspace_size(ms, ns, ranks, oversampling, 0)
+    ws = workspace if workspace is not None else torch.empty(need, dtype=torch.uint8, device=dev_)
+    fl = flags if flags is not None else new_flags(dev_)
+    tuned = ctypes.c_int32()
+    _check(_lib.load().shg_rsvd_batched_autotune(
+        b, _host_array(ctypes.c_int64, ms), _host_array(ctypes.c_int64, ns), _host_array(ctypes.c_int64, ranks),
+        oversampling, _host_array(ctypes.c_void_p, [A.data_ptr() for A in As]), _host_array(ctypes.c_int64, ldas),
+        seed, _ptr(ws), ws.numel(), reps, _ptr(fl), _stream(stream), ctypes.byref(tuned)), "shg_rsvd_batched_autotune")
+    return tuned.value
+
+
 def shg_gemm_split3(A: torch.Tensor, B: torch.Tensor, trans_a: bool = False, out: torch.Tensor | None = None,
                     accumulate: bool = False, flags: torch.Tensor | None = None, check: bool = True,
                     stream=None) -> torch.Tensor:

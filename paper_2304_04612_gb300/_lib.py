@@ -38,6 +38,12 @@ SIGNATURES = {
     "shg_alpha_y_f16": (ctypes.c_double, []),
     "shg_diag_wait_timeout": (c_int, [c_i64, c_i64, c_i64, c_vp, c_i64, c_vp, c_i64, c_vp, c_i64, c_u64, c_vp, c_vp]),
     "shg_rsvd_batched_workspace_size": (c_int, [c_int, c_vp, c_vp, c_vp, c_i64, c_int, ctypes.POINTER(c_sz)]),
+    "shg_autotune_project": (c_int, [c_i64, c_i64, c_i64, c_vp, c_i64, c_int, c_vp, c_i64, c_vp, c_i64, c_int,
+                                     c_int, c_vp, c_vp, c_vp]),
+    "shg_autotune_lookup": (c_int, [c_i64, c_i64, c_i64, c_int, c_int, c_vp]),
+    "shg_autotune_clear": (c_int, []),
+    "shg_rsvd_batched_autotune": (c_int, [c_int, c_vp, c_vp, c_vp, c_i64, c_vp, c_vp, c_u64, c_vp, c_sz, c_int,
+                                          c_vp, c_vp, c_vp]),
     "shg_rsvd_batched": (c_int, [c_int, c_vp, c_vp, c_vp, c_i64, c_int, c_vp, c_vp, c_vp, c_vp, c_u64, c_vp, c_vp,
                                  c_vp, c_vp, c_sz, c_int, c_int, c_vp, c_vp]),
     "shg_round_f16": (c_int, [c_i64, c_i64, c_vp, c_i64, c_vp, c_i64, c_vp]),

@@ -141,6 +141,61 @@ int shgemm_project(int64_t m, int64_t n, int64_t k, const float* A, int64_t lda,
   }
 }
 
+// (amaj, bmode, pieces) of a projection variant; false for the SIMT path.
+static bool tc_layout(int variant, int trans_a, int* amaj, int* bmode, int* pieces) {
+  *amaj = trans_a ? A_MNMAJ : A_KMAJ;
+  if (variant == SHG_SPLIT_F16) {
+    *bmode = B_F16;
+    *pieces = 2;
+    return true;
+  }
+  if ((variant == SHG_SPLIT_BF16X3 || variant == SHG_SPLIT_BF16X2) && !trans_a) {
+    *bmode = B_BF16;
+    *pieces = variant == SHG_SPLIT_BF16X3 ? 3 : 2;
+    return true;
+  }
+  return false;
+}
+
+static void put_config(const TcConfig& c, int found, int32_t* out) {
+  if (!out) return;
+  out[0] = c.sa;
+  out[1] = c.sb;
+  out[2] = c.kc;
+  out[3] = c.groups;
+  out[4] = found;
+}
+
+int shg_autotune_project(int64_t m, int64_t n, int64_t k, const float* A, int64_t lda, int trans_a,
+                         const uint16_t* omega, int64_t ldo, float* Y, int64_t ldy, int variant, int reps,
+                         int32_t* d_flags, void* stream, int32_t* config_out) {
+  if (m < 1 || n < 1 || k < 1 || !A || !omega || !Y || !d_flags || reps < 1 || reps > 100) return SHG_ERR_INVALID_ARG;
+  if (lda < (trans_a ? m : n) || ldo < k || ldy < k) return SHG_ERR_INVALID_ARG;
+  int amaj, bmode, pieces;
+  if (!tc_layout(variant, trans_a, &amaj, &bmode, &pieces)) return SHG_ERR_UNSUPPORTED;
+  TcConfig best;
+  int found = 0;
+  const int rc = tc_autotune(amaj, bmode, pieces, m, k, n, 1, A, lda, 0, omega, ldo, Y, ldy, d_flags,
+                             static_cast<cudaStream_t>(stream), reps, &best, &found);
+  if (rc == SHG_OK) put_config(best, found, config_out);
+  return rc;
+}
+
+int shg_autotune_lookup(int64_t m, int64_t n, int64_t k, int trans_a, int variant, int32_t* config_out) {
+  if (m < 1 || n < 1 || k < 1 || !config_out) return SHG_ERR_INVALID_ARG;
+  int amaj, bmode, pieces;
+  if (!tc_layout(variant, trans_a, &amaj, &bmode, &pieces)) return SHG_ERR_UNSUPPORTED;
+  TcConfig c;
+  const bool found = tc_tuned(amaj, bmode, pieces, m, k, n, 1, &c);
+  put_config(c, found ? 1 : 0, config_out);
+  return SHG_OK;
+}
+
+int shg_autotune_clear(void) {
+  tc_tune_clear();
+  return SHG_OK;
+}
+
 int shg_diag_wait_timeout(int64_t m, int64_t n, int64_t k, const float* A, int64_t lda, const uint16_t* omega,
                           int64_t ldo, float* Y, int64_t ldy, uint64_t wait_ns, int32_t* d_flags, void* stream) {
   if (m < 1 || n < 1 || k < 1 || !A || !omega || !Y || !d_flags) return SHG_ERR_INVALID_ARG;

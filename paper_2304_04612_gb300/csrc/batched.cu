@@ -247,3 +247,39 @@ extern "C" int shg_rsvd_batched(int batch, const int64_t* m, const int64_t* n, c
   g_graphs.push_back(std::move(e));
   return cuda_status(cudaGraphLaunch(exec, st));
 }
+
+extern "C" int shg_rsvd_batched_autotune(int batch, const int64_t* m, const int64_t* n, const int64_t* rank,
+                                         int64_t oversampling, const float* const* A, const int64_t* lda,
+                                         uint64_t seed, void* ws, size_t ws_bytes, int reps, int32_t* d_flags,
+                                         void* stream, int32_t* tuned_out) {
+  size_t need = 0;
+  int rc = shg_rsvd_batched_workspace_size(batch, m, n, rank, oversampling, 0, &need);
+  if (rc != SHG_OK) return rc;
+  if (!A || !lda || !ws || !d_flags || reps < 1 || reps > 100) return SHG_ERR_INVALID_ARG;
+  if (ws_bytes < need) return SHG_ERR_WORKSPACE;
+  cudaStream_t st = static_cast<cudaStream_t>(stream);
+  uint8_t* w = static_cast<uint8_t*>(ws);
+  int tuned = 0;
+  for (int i = 0; i < batch; ++i) {
+    if (!A[i] || lda[i] < n[i]) return SHG_ERR_INVALID_ARG;
+    const int64_t k = rank[i] + oversampling, ldk = round8(k);
+    if (tc_tuned(A_KMAJ, B_F16, 2, m[i], k, n[i], 1, nullptr)) continue;
+    // problem i stands for its shape class: Omega_i (its Philox stream) and
+    // a scratch Y in the workspace, which holds both (it holds the FP16
+    // Omega and the FP32 Y of a whole randomized SVD)
+    const size_t om_bytes = (static_cast<size_t>(n[i]) * ldk * 2 + 255) & ~size_t(255);
+    if (om_bytes + static_cast<size_t>(m[i]) * ldk * 4 > ws_bytes) return SHG_ERR_WORKSPACE;
+    uint16_t* om = reinterpret_cast<uint16_t*>(w);
+    float* y = reinterpret_cast<float*>(w + om_bytes);
+    rc = shg_gaussian_f16(seed, static_cast<uint64_t>(i) << 32, n[i], k, om, ldk, st);
+    if (rc != SHG_OK) return rc;
+    TcConfig best;
+    int found = 0;
+    rc = tc_autotune(A_KMAJ, B_F16, 2, m[i], k, n[i], 1, A[i], lda[i], 0, om, ldk, y, ldk, d_flags, st, reps, &best,
+                     &found);
+    if (rc != SHG_OK) return rc;
+    tuned += found ? 0 : 1;
+  }
+  if (tuned_out) *tuned_out = tuned;
+  return SHG_OK;
+}

@@ -24,10 +24,28 @@ struct TcTestHooks {
 //   amaj = A_MNMAJ: A is K x M (A[k][m] at A + k * lda + m), P = 1.
 //   bmode: B_F16 / B_BF16 (B already 16-bit, `pieces` A pieces of that type)
 //          or B_SPLIT (B FP32 split into FP16 hi/lo, TCEC products).
+//   The launch configuration comes from `force` when given, else from the
+//   autotuner's cache for the call's shape class, else from the defaults.
+struct TcConfig {
+  int sa = 4;      // depth of the FP32 A staging ring
+  int sb = 4;      // depth of the B tile ring
+  int kc = 4;      // K blocks per RN drain of the hi product
+  int groups = 1;  // 1: one CTA group per N tile when there are 2..8 N tiles; 0: a single group
+};
 int tc_gemm(int amaj, int bmode, int pieces, int64_t M, int64_t N, int64_t S_k, int64_t P,
             const float* A, int64_t lda, int64_t p_stride, const void* B, int64_t ldb, float* C,
             int64_t ldc, int accumulate, int32_t* d_flags, cudaStream_t stream,
-            const TcTestHooks* hooks = nullptr);
+            const TcTestHooks* hooks = nullptr, const TcConfig* force = nullptr);
+// Times the candidate configurations of this tc_gemm call (C is
+// overwritten; synchronises `stream`) and caches the fastest for the call's
+// shape class.  *best receives it; *found_before tells whether the class was
+// already tuned (then nothing runs).
+int tc_autotune(int amaj, int bmode, int pieces, int64_t M, int64_t N, int64_t S_k, int64_t P, const float* A,
+                int64_t lda, int64_t p_stride, const void* B, int64_t ldb, float* C, int64_t ldc,
+                int32_t* d_flags, cudaStream_t stream, int reps, TcConfig* best, int* found_before);
+// Cached configuration of a shape class (returns false when untuned).
+bool tc_tuned(int amaj, int bmode, int pieces, int64_t M, int64_t N, int64_t K, int64_t P, TcConfig* out);
+void tc_tune_clear();
 
 // FP32 SIMT GEMM, batched over gridDim.z with element strides.
 int simt_gemm(int64_t M, int64_t N, int64_t K, const float* A, int64_t lda, int trans_a, const void* B,

@@ -41,6 +41,7 @@
 #include <algorithm>
 #include <cstdlib>
 #include <mutex>
+#include <vector>
 
 #include "internal.h"
 #include "ptx.cuh"
@@ -697,11 +698,154 @@ int launch(const CUtensorMap& ta, const CUtensorMap& tb, const TcArgs& a, int gr
   return cuda_status(cudaGetLastError());
 }
 
+
+// ------------------------------------------------------------ autotuner
+// Shape class: operand layout and piece type, the N tiling, and M and K to
+// within a factor of two.  The cache is small (one entry per class seen).
+struct TuneKey {
+  int amaj, bmode, pieces, nt, n_tiles, mlog, klog, pmulti;
+  bool operator==(const TuneKey& o) const {
+    return amaj == o.amaj && bmode == o.bmode && pieces == o.pieces && nt == o.nt && n_tiles == o.n_tiles &&
+           mlog == o.mlog && klog == o.klog && pmulti == o.pmulti;
+  }
+};
+std::mutex g_tune_mu;
+std::vector<std::pair<TuneKey, TcConfig>> g_tune;
+
+int floor_log2(int64_t x) {
+  int l = 0;
+  while (l < 62 && (int64_t(1) << (l + 1)) <= x) ++l;
+  return l;
+}
+
+// N tiling of a call: tile width (a multiple of 64, at most 128 when the
+// accumulators and two A stages fit in TMEM) and the number of tiles.
+void n_tiling(int bmode, int pieces, int64_t N, int* nt_out, int* tiles_out) {
+  const int n_lo = (bmode == B_SPLIT) ? 1 : pieces - 1;
+  const int max_tile = ((2 + n_lo) * 128 + 2 * pieces * 32 <= 512) ? 128 : 64;
+  int nt = static_cast<int>(((N + 63) / 64) * 64);
+  if (nt > max_tile) {
+    const int tiles = static_cast<int>((N + max_tile - 1) / max_tile);
+    nt = static_cast<int>(((N + tiles - 1) / tiles + 63) / 64 * 64);
+  }
+  *nt_out = nt;
+  *tiles_out = static_cast<int>((N + nt - 1) / nt);
+}
+
+TuneKey tune_key(int amaj, int bmode, int pieces, int64_t M, int64_t N, int64_t K, int64_t P) {
+  TuneKey k{};
+  k.amaj = amaj;
+  k.bmode = bmode;
+  k.pieces = pieces;
+  n_tiling(bmode, pieces, N, &k.nt, &k.n_tiles);
+  k.mlog = floor_log2(M);
+  k.klog = floor_log2(K);
+  k.pmulti = P > 1;
+  return k;
+}
+
+TcConfig default_config() {
+  TcConfig c;
+  c.sa = env_int("SHG_A_STAGES", 4);
+  c.sb = env_int("SHG_B_STAGES", 4);
+  c.kc = env_int("SHG_DRAIN_KBLOCKS", 4);
+  c.groups = env_int("SHG_NGROUPS", 1) != 0 ? 1 : 0;
+  return c;
+}
+
 }  // namespace
 
-int tc_gemm(int amaj, int bmode, int pieces, int64_t M, int64_t N, int64_t S_k, int64_t P, const float* A,
-            int64_t lda, int64_t p_stride, const void* B, int64_t ldb, float* C, int64_t ldc, int accumulate,
-            int32_t* d_flags, cudaStream_t stream, const TcTestHooks* hooks) {
+bool tc_tuned(int amaj, int bmode, int pieces, int64_t M, int64_t N, int64_t K, int64_t P, TcConfig* out) {
+  const TuneKey key = tune_key(amaj, bmode, pieces, M, N, K, P);
+  std::lock_guard<std::mutex> lock(g_tune_mu);
+  for (const auto& e : g_tune)
+    if (e.first == key) {
+      if (out) *out = e.second;
+      return true;
+    }
+  return false;
+}
+
+void tc_tune_clear() {
+  std::lock_guard<std::mutex> lock(g_tune_mu);
+  g_tune.clear();
+}
+
+int tc_autotune(int amaj, int bmode, int pieces, int64_t M, int64_t N, int64_t S_k, int64_t P, const float* A,
+                int64_t lda, int64_t p_stride, const void* B, int64_t ldb, float* C, int64_t ldc,
+                int32_t* d_flags, cudaStream_t stream, int reps, TcConfig* best, int* found_before) {
+  if (reps < 1 || reps > 100) return SHG_ERR_INVALID_ARG;
+  if (found_before) *found_before = 0;
+  if (tc_tuned(amaj, bmode, pieces, M, N, S_k * P, P, best)) {
+    if (found_before) *found_before = 1;
+    return SHG_OK;
+  }
+  cudaStreamCaptureStatus cap = cudaStreamCaptureStatusNone;
+  if (cudaStreamIsCapturing(stream, &cap) != cudaSuccess) return SHG_ERR_CUDA;
+  if (cap != cudaStreamCaptureStatusNone) return SHG_ERR_UNSUPPORTED;  // timing needs synchronisation
+  const TuneKey key = tune_key(amaj, bmode, pieces, M, N, S_k * P, P);
+  // candidates: staging depths, drain interval (2..8 K blocks keeps the
+  // error of the hi product's TMEM accumulation below that of 16 blocks
+  // by a factor >= 2) and the N-tile grouping
+  std::vector<TcConfig> cand;
+  for (int sa : {2, 4, 6})
+    for (int sb : {2, 4})
+      for (int kc : {2, 4, 8})
+        for (int g : {1, 0}) {
+          if (g == 0 && (key.n_tiles < 2 || key.n_tiles > 8)) continue;
+          TcConfig c;
+          c.sa = sa;
+          c.sb = sb;
+          c.kc = kc;
+          c.groups = g;
+          cand.push_back(c);
+        }
+  cudaEvent_t e0 = nullptr, e1 = nullptr;
+  if (cudaEventCreate(&e0) != cudaSuccess || cudaEventCreate(&e1) != cudaSuccess) {
+    if (e0) cudaEventDestroy(e0);
+    return SHG_ERR_CUDA;
+  }
+  float best_ms = 1e30f;
+  TcConfig win = cand.front();
+  int rc = SHG_OK;
+  for (const TcConfig& c : cand) {
+    rc = tc_gemm(amaj, bmode, pieces, M, N, S_k, P, A, lda, p_stride, B, ldb, C, ldc, 0, d_flags, stream, nullptr,
+                 &c);  // warm-up (and validation of the configuration)
+    if (rc != SHG_OK) break;
+    if (cudaEventRecord(e0, stream) != cudaSuccess) { rc = SHG_ERR_CUDA; break; }
+    for (int r = 0; r < reps && rc == SHG_OK; ++r)
+      rc = tc_gemm(amaj, bmode, pieces, M, N, S_k, P, A, lda, p_stride, B, ldb, C, ldc, 0, d_flags, stream,
+                   nullptr, &c);
+    if (rc != SHG_OK) break;
+    if (cudaEventRecord(e1, stream) != cudaSuccess || cudaEventSynchronize(e1) != cudaSuccess) {
+      rc = SHG_ERR_CUDA;
+      break;
+    }
+    float ms = 0.0f;
+    if (cudaEventElapsedTime(&ms, e0, e1) != cudaSuccess) { rc = SHG_ERR_CUDA; break; }
+    if (ms < best_ms) {
+      best_ms = ms;
+      win = c;
+    }
+  }
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  if (rc != SHG_OK) return rc;
+  {
+    std::lock_guard<std::mutex> lock(g_tune_mu);
+    bool have = false;
+    for (const auto& e : g_tune) have = have || (e.first == key);
+    if (!have) g_tune.emplace_back(key, win);
+  }
+  if (best) *best = win;
+  return SHG_OK;
+}
+
+namespace {
+
+int tc_gemm_impl(int amaj, int bmode, int pieces, int64_t M, int64_t N, int64_t S_k, int64_t P, const float* A,
+                 int64_t lda, int64_t p_stride, const void* B, int64_t ldb, float* C, int64_t ldc, int accumulate,
+                 int32_t* d_flags, cudaStream_t stream, const TcTestHooks* hooks, const TcConfig* force) {
   if (M <= 0 || N <= 0 || S_k <= 0 || P <= 0) return SHG_ERR_INVALID_ARG;
   if (M >= (1ll << 31) || N >= (1ll << 31) || S_k * P >= (1ll << 31)) return SHG_ERR_INVALID_ARG;
   if (amaj == A_MNMAJ && P != 1) return SHG_ERR_INVALID_ARG;
@@ -718,14 +862,12 @@ int tc_gemm(int amaj, int bmode, int pieces, int64_t M, int64_t N, int64_t S_k, 
   a.N = static_cast<int>(N);
   const int n_lo = (bmode == B_SPLIT) ? 1 : pieces - 1;
   // TMEM: D0, D1, lo accumulator(s), then at least two A stages of pieces x 32 columns
-  const int max_tile = ((2 + n_lo) * 128 + 2 * pieces * 32 <= 512) ? 128 : 64;
-  int nt = static_cast<int>(((N + 63) / 64) * 64);
-  if (nt > max_tile) {
-    const int tiles = static_cast<int>((N + max_tile - 1) / max_tile);
-    nt = static_cast<int>(((N + tiles - 1) / tiles + 63) / 64 * 64);
-  }
+  int nt = 0;
+  n_tiling(bmode, pieces, N, &nt, &a.n_tiles);
   a.n_tile = nt;
-  a.n_tiles = static_cast<int>((N + nt - 1) / nt);
+  TcConfig cfg = default_config();
+  if (force) cfg = *force;
+  else tc_tuned(amaj, bmode, pieces, M, N, K, P, &cfg);
   a.m_tiles = static_cast<int>((M + kBM - 1) / kBM);
   a.kb_per_p = static_cast<int>((S_k + kBK - 1) / kBK);
   a.kblocks = a.kb_per_p * static_cast<int>(P);
@@ -743,15 +885,14 @@ int tc_gemm(int amaj, int bmode, int pieces, int64_t M, int64_t N, int64_t S_k, 
   a.tmem_cols = cols;
   a.b_bytes = (bmode == B_SPLIT) ? static_cast<uint32_t>(nt) * 256u : static_cast<uint32_t>(nt) * 128u;
   const uint32_t bar_bytes = 1024;
-  a.sa = std::max(2, std::min(env_int("SHG_A_STAGES", 4), 6));
-  a.sb = std::max(2, std::min(env_int("SHG_B_STAGES", 4), 6));
+  a.sa = std::max(2, std::min(cfg.sa, 6));
+  a.sb = std::max(2, std::min(cfg.sb, 6));
   while (a.sa * kABytes + a.sb * a.b_bytes + 1024 + bar_bytes > kMaxSmem) {
     if (a.sb > 2 && a.sb >= a.sa) --a.sb;
     else if (a.sa > 2) --a.sa;
     else return SHG_ERR_UNSUPPORTED;
   }
-  const int kc = env_int("SHG_DRAIN_KBLOCKS", 4);
-  a.kc = kc > 0 ? kc : a.kblocks;  // 0: accumulate a whole segment in TMEM
+  a.kc = cfg.kc > 0 ? cfg.kc : a.kblocks;  // 0: accumulate a whole segment in TMEM
   TcTestHooks h;
   if (hooks) h = *hooks;
   a.wait_ns = h.wait_ns;
@@ -791,7 +932,7 @@ int tc_gemm(int amaj, int bmode, int pieces, int64_t M, int64_t N, int64_t S_k, 
   const int sms = sm_count();
   if (sms <= 0) return SHG_ERR_CUDA;
   // one CTA group per N tile when there are few N tiles (see cta_range)
-  a.groups = (a.n_tiles > 1 && a.n_tiles <= 8 && env_int("SHG_NGROUPS", 1) != 0) ? a.n_tiles : 1;
+  a.groups = (a.n_tiles > 1 && a.n_tiles <= 8 && cfg.groups != 0) ? a.n_tiles : 1;
   const long long per_group = a.units / a.groups;
   const int grid = static_cast<int>(std::min<long long>(sms / a.groups, per_group)) * a.groups;
   const int per_cta = grid / a.groups;
@@ -812,6 +953,15 @@ int tc_gemm(int amaj, int bmode, int pieces, int64_t M, int64_t N, int64_t S_k, 
   if (bmode == B_F16) return launch<A_MNMAJ, B_F16, 2>(ta, tb, a, grid, smem, stream);
   if (bmode == B_SPLIT) return launch<A_MNMAJ, B_SPLIT, 2>(ta, tb, a, grid, smem, stream);
   return SHG_ERR_UNSUPPORTED;
+}
+
+}  // namespace
+
+int tc_gemm(int amaj, int bmode, int pieces, int64_t M, int64_t N, int64_t S_k, int64_t P, const float* A,
+            int64_t lda, int64_t p_stride, const void* B, int64_t ldb, float* C, int64_t ldc, int accumulate,
+            int32_t* d_flags, cudaStream_t stream, const TcTestHooks* hooks, const TcConfig* force) {
+  return tc_gemm_impl(amaj, bmode, pieces, M, N, S_k, P, A, lda, p_stride, B, ldb, C, ldc, accumulate, d_flags,
+                      stream, hooks, force);
 }
 
 }  // namespace shg

@@ -65,6 +65,15 @@ def test_host_argument_validation(lib):
     r = (ctypes.c_int64 * 3)(4, 9, 4)                                 # J > I
     assert lib.shg_rp_hosvd_workspace_size(3, d, r, ctypes.byref(sz)) == 1
     assert lib.shg_rp_hosvd_workspace_size(4, d, r, ctypes.byref(sz)) == 7
+    # autotuner: bad shapes, reps out of range and the SIMT variant (nothing
+    # to tune) are rejected before any launch; lookup of an untuned class
+    cfg = (ctypes.c_int32 * 5)()
+    assert lib.shg_autotune_project(0, 8, 8, one, 8, 0, one, 8, one, 8, 0, 3, one, null, cfg) == 1
+    assert lib.shg_autotune_project(8, 8, 8, one, 8, 0, one, 8, one, 8, 0, 0, one, null, cfg) == 1
+    assert lib.shg_autotune_project(8, 8, 8, one, 8, 0, one, 8, one, 8, 3, 3, one, null, cfg) == 7
+    assert lib.shg_autotune_clear() == 0
+    assert lib.shg_autotune_lookup(4096, 4096, 64, 0, 0, cfg) == 0 and cfg[4] == 0
+    assert lib.shg_autotune_lookup(4096, 4096, 64, 0, 3, cfg) == 7
     # Gram matrix: k = 0, k > 1024 and ldx < k are rejected before any launch
     assert lib.shg_gram(8, 0, one, 8, one, null) == 1
     assert lib.shg_gram(8, 1025, one, 1025, one, null) == 1
