@@ -399,6 +399,7 @@ __device__ __forceinline__ float jac_elem_sym(const float* A, int ld, int p1, in
 // Shared layout: (c, s)[2][h], then the two A buffers (kp x (kp + 1) floats
 // each, upper triangles).
 constexpr int kJacSweeps = 40;
+constexpr int kJacLogMaxK = 288;  // largest kp whose rotations are logged (13 MB at 40 sweeps)
 constexpr int kJacItems = 6;  // most blocks (or V pieces) one thread owns
 
 __host__ __device__ inline size_t jac_cta_floats(int kp) {
@@ -580,7 +581,7 @@ __global__ void __launch_bounds__(768) jacobi_kernel(int k, const double* __rest
 // warp barrier when one warp covers the slots).  The log is read eight
 // rounds ahead.  Writes Vout (k x k, row-major, columns = eigenvectors).
 template <int RB>
-__global__ void __launch_bounds__(128) jac_apply_v_kernel(int k, const float2* __restrict__ log,
+__global__ void __launch_bounds__(512) jac_apply_v_kernel(int k, const float2* __restrict__ log,
                                                           const int* __restrict__ rounds, float* __restrict__ Vout) {
   extern __shared__ float vs[];  // RB x kp
   const int kp = k + (k & 1), h = kp / 2, n1 = kp - 1;
@@ -641,156 +642,177 @@ __global__ void __launch_bounds__(128) jac_apply_v_kernel(int k, const float2* _
 }
 
 // The same Jacobi method for k too large for one SM's shared memory: A (two
-// buffers), V^T and the round parameters live in global memory (they stay in
-// L2), every round is spread over the whole grid of a cooperative launch and
-// ends with one grid barrier.  Shared data is read with ld.global.cg (L2,
-// never a stale L1 line written by another SM in an earlier round).  Layout
-// of `scratch`: A buffers (2 kp (kp + 1) floats), V^T (kp x ldv), then the
-// parameters: JPair[2][kp/2], pair-of-index[2][kp], side-of-index[2][kp],
+// buffers, upper triangles), the rotations and, without a log, V^T live in
+// global memory (they stay in L2); every round is spread over the whole grid
+// of a cooperative launch and ends with one grid barrier.  Shared data is
+// read with ld.global.cg (L2, never a stale L1 line written by another SM in
+// an earlier round).  The last h threads of the grid are the rotation
+// threads, addressing their loads a round ahead as in jacobi_kernel; the
+// others take the pair blocks in folded-triangle order.  With `log` the
+// rotations go there and V is multiplied out afterwards (jac_apply_v_kernel);
+// without it V^T is rotated in every round here.  Layout of `scratch`: A
+// buffers (2 kp (kp + 1) floats), V^T (kp x ldv), the rotations (c, s)[2][h],
 // last_rot.
 __global__ void __launch_bounds__(256) jacobi_grid_kernel(int k, const double* __restrict__ G,
-                                                         float* __restrict__ Vout, float* scratch) {
+                                                         float* __restrict__ Vout, float* scratch,
+                                                         float2* __restrict__ log, int* __restrict__ rounds_out) {
   namespace cg = cooperative_groups;
   cg::grid_group grid = cg::this_grid();
   const int kp = k + (k & 1);
-  const int half = kp / 2, n1 = kp - 1;
+  const int h = kp / 2, n1 = kp - 1;
   const int ld = kp + 1, ldv = (kp + 3) & ~3;
   float* const M0 = scratch;
   float* const Vt = M0 + 2 * kp * ld;
-  JPair* const pairs = reinterpret_cast<JPair*>(Vt + kp * ldv);  // 16-byte aligned: offsets are multiples of 4 floats
-  int* const tmap = reinterpret_cast<int*>(pairs + 2 * half);
-  int* const smap = tmap + 2 * kp;
-  volatile int* const last_rot = smap + 2 * kp;
-  const long long gtid = static_cast<long long>(blockIdx.x) * blockDim.x + threadIdx.x;
-  const long long gnt = static_cast<long long>(gridDim.x) * blockDim.x;
+  float2* const rots = reinterpret_cast<float2*>(Vt + kp * ldv);  // [2][h]; 8-byte aligned (offsets are even)
+  volatile int* const last_rot = reinterpret_cast<int*>(rots + 2 * h);
+  const int gtid = static_cast<int>(blockIdx.x * blockDim.x + threadIdx.x);
+  const int gnt = static_cast<int>(gridDim.x * blockDim.x);
+  const bool defer = log != nullptr;
   __shared__ double red[32];
   __shared__ double dmax;
   diag_max(k, G, red, &dmax);  // every block forms the scale itself
   __syncthreads();
   const double sigma = ldexp(1.0, -((dmax > 0.0) ? ilogb(dmax) : 0));
-  for (long long e = gtid; e < static_cast<long long>(kp) * kp; e += gnt) {
-    const int i = static_cast<int>(e / kp), j = static_cast<int>(e - static_cast<long long>(i) * kp);
-    float v = 0.0f;
-    if (i < k && j < k) v = static_cast<float>(G[min(i, j) * k + max(i, j)] * sigma);
-    M0[i * ld + j] = v;
+  for (int e = gtid; e < kp * kp; e += gnt) {
+    const int i = e / kp, j = e - i * kp;
+    if (j >= i) M0[i * ld + j] = (j < k) ? static_cast<float>(G[i * k + j] * sigma) : 0.0f;
   }
-  for (long long e = gtid; e < static_cast<long long>(kp) * ldv; e += gnt) {
-    const int i = static_cast<int>(e / ldv), j = static_cast<int>(e - static_cast<long long>(i) * ldv);
-    Vt[e] = (i == j) ? 1.0f : 0.0f;
-  }
+  if (!defer)
+    for (int e = gtid; e < kp * ldv; e += gnt) {
+      const int i = e / ldv, j = e - i * ldv;
+      Vt[e] = (i == j) ? 1.0f : 0.0f;
+    }
   if (gtid == 0) *last_rot = -1;
-  // rotation thread rt = gtid < half owns pair rt; its running circle positions
-  const bool rotor = gtid < half;
-  const int rt = static_cast<int>(gtid);
-  int pa = 0, pb = 0;
-  if (rotor) {
-    pa = (rt == 0) ? 0 : rt;
-    pb = ((n1 - 1 - rt) % n1 + n1) % n1 + 1;
-  }
+  const int workers = gnt - h;  // the host launches at least h + 1 threads
+  const int rt = gtid - workers;
+  const bool rotor = rt >= 0;
+  const int srcA = (rt <= 0) ? 0 : min(rt + 1, h - 1);
+  const int srcB = (rt >= 1) ? rt - 1 : (h >= 2 ? 1 : 0);
   grid.sync();
   if (rotor) {
+    int pa, pb;
+    circle_ab(rt, 0, n1, pa, pb);
     const int p = min(pa, pb), q = max(pa, pb);
     float c, s;
     if (jac_rot(__ldcg(M0 + p * ld + p), __ldcg(M0 + q * ld + q), __ldcg(M0 + p * ld + q), c, s)) *last_rot = 0;
-    pairs[rt] = JPair{p, q, c, s};
-    tmap[p] = rt;
-    tmap[q] = rt;
-    smap[p] = 0;
-    smap[q] = 1;
+    rots[rt] = make_float2(c, s);
+    if (defer) log[rt] = make_float2(c, s);
   }
+  int rix[10], rfl = 0;
+  auto plan = [&](int r) {
+    int pa, pb, aA, bA, aB, bB;
+    circle_ab(rt, r + 1, n1, pa, pb);
+    circle_ab(srcA, r, n1, aA, bA);
+    circle_ab(srcB, r, n1, aB, bB);
+    const int pA = min(aA, bA), qA = max(aA, bA), pB = min(aB, bB), qB = max(aB, bB);
+    const int sxa = (pa == pA) ? 0 : 1, sxb = (pb == pB) ? 0 : 1;
+    const bool a_low = pa < pb;
+    const int tp = a_low ? srcA : srcB, tq = a_low ? srcB : srcA;
+    const int pp = a_low ? pA : pB, qp = a_low ? qA : qB, pq = a_low ? pB : pA, qq = a_low ? qB : qA;
+    const int sp = a_low ? sxa : sxb, sq = a_low ? sxb : sxa;
+    const bool pfirst = tp <= tq;
+    const int p1 = pfirst ? pp : pq, q1 = pfirst ? qp : qq, p2 = pfirst ? pq : pp, q2 = pfirst ? qq : qp;
+    rix[0] = pp * ld + pp;
+    rix[1] = pp * ld + qp;
+    rix[2] = qp * ld + qp;
+    rix[3] = pq * ld + pq;
+    rix[4] = pq * ld + qq;
+    rix[5] = qq * ld + qq;
+    rix[6] = sym_at(p1, p2, ld);
+    rix[7] = sym_at(p1, q2, ld);
+    rix[8] = sym_at(q1, p2, ld);
+    rix[9] = sym_at(q1, q2, ld);
+    rfl = sp | (sq << 1) | (pfirst ? 4 : 0) | (tp == tq ? 8 : 0) | (a_low ? 16 : 0);
+  };
+  if (rotor) plan(0);
   grid.sync();
-  int abuf = 0, buf = 0;
+  const int nblk = h * (h + 1) / 2;
   const int nv4 = ldv >> 2;
-  for (int sweep = 0; sweep < 40; ++sweep) {
+  int buf = 0, sweeps = kJacSweeps;
+  for (int sweep = 0; sweep < kJacSweeps; ++sweep) {
     for (int r = 0; r < n1; ++r) {
-      const float* A = M0 + abuf * (kp * ld);
-      float* B = M0 + (abuf ^ 1) * (kp * ld);
-      const JPair* cur = pairs + buf * half;
-      const int* ct = tmap + buf * kp;
-      const int* cs = smap + buf * kp;
-      auto ldp = [&](int t) {
-        JPair P;
-        const int4 v = __ldcg(reinterpret_cast<const int4*>(cur + t));
-        P.p = v.x;
-        P.q = v.y;
-        P.c = __int_as_float(v.z);
-        P.s = __int_as_float(v.w);
-        return P;
-      };
-      // J^T A J by pair blocks (t, u), u >= t
-      for (long long idx = gtid; idx < static_cast<long long>(half) * half; idx += gnt) {
-        const int t = static_cast<int>(idx / half), u = static_cast<int>(idx - static_cast<long long>(t) * half);
-        if (u < t) continue;
-        const JPair P1 = ldp(t), P2 = ldp(u);
-        float n00, n01, n10, n11;
-        jac_block(__ldcg(A + P1.p * ld + P2.p), __ldcg(A + P1.p * ld + P2.q), __ldcg(A + P1.q * ld + P2.p),
-                  __ldcg(A + P1.q * ld + P2.q), P1.c, P1.s, P2.c, P2.s, n00, n01, n10, n11);
-        if (u == t) {
-          if (P1.s != 0.0f) n01 = 0.0f;
-          B[P1.p * ld + P1.p] = n00;
-          B[P1.q * ld + P1.q] = n11;
-          B[P1.p * ld + P1.q] = n01;
-          B[P1.q * ld + P1.p] = n01;
-        } else {
-          B[P1.p * ld + P2.p] = n00;
-          B[P2.p * ld + P1.p] = n00;
-          B[P1.p * ld + P2.q] = n01;
-          B[P2.q * ld + P1.p] = n01;
-          B[P1.q * ld + P2.p] = n10;
-          B[P2.p * ld + P1.q] = n10;
-          B[P1.q * ld + P2.q] = n11;
-          B[P2.q * ld + P1.q] = n11;
-        }
-      }
-      // V <- V J on the transposed rows p, q
-      for (long long w = gtid; w < static_cast<long long>(half) * nv4; w += gnt) {
-        const int t = static_cast<int>(w / nv4), c4 = static_cast<int>(w - static_cast<long long>(t) * nv4) * 4;
-        const JPair P = ldp(t);
-        float4* vp = reinterpret_cast<float4*>(Vt + P.p * ldv + c4);
-        float4* vq = reinterpret_cast<float4*>(Vt + P.q * ldv + c4);
-        const float4 x = __ldcg(vp), y = __ldcg(vq);
-        *vp = make_float4(__fmaf_rn(-P.s, y.x, __fmul_rn(P.c, x.x)), __fmaf_rn(-P.s, y.y, __fmul_rn(P.c, x.y)),
-                          __fmaf_rn(-P.s, y.z, __fmul_rn(P.c, x.z)), __fmaf_rn(-P.s, y.w, __fmul_rn(P.c, x.w)));
-        *vq = make_float4(__fmaf_rn(P.s, x.x, __fmul_rn(P.c, y.x)), __fmaf_rn(P.s, x.y, __fmul_rn(P.c, y.y)),
-                          __fmaf_rn(P.s, x.z, __fmul_rn(P.c, y.z)), __fmaf_rn(P.s, x.w, __fmul_rn(P.c, y.w)));
-      }
-      // rotations of the next round from the same old A
-      if (rotor) {
-        pa = (rt == 0) ? 0 : (pa == n1 ? 1 : pa + 1);
-        pb = (pb == n1) ? 1 : pb + 1;
-        const int p = min(pa, pb), q = max(pa, pb);
-        const int tp = __ldcg(ct + p), tq = __ldcg(ct + q), sp = __ldcg(cs + p), sq = __ldcg(cs + q);
-        const JPair Pp = ldp(tp), Pq = ldp(tq);
-        auto elem = [&](const JPair& P1, int sx, const JPair& P2, int sy, bool same) {
+      const float* A = M0 + buf * (kp * ld);
+      float* B = M0 + (buf ^ 1) * (kp * ld);
+      const float2* cur = rots + buf * h;
+      if (!rotor) {
+        // J^T A J by pair blocks (t, u), u >= t, folded-triangle order
+        for (int bi = gtid; bi < nblk; bi += workers) {
+          const int i = bi / (h + 1), j = bi - i * (h + 1);
+          const int t = (j < h - i) ? i : h - 1 - i, u = (j < h - i) ? i + j : j - 1;
+          int a1, b1, a2, b2;
+          circle_ab(t, r, n1, a1, b1);
+          circle_ab(u, r, n1, a2, b2);
+          const int p1 = min(a1, b1), q1 = max(a1, b1), p2 = min(a2, b2), q2 = max(a2, b2);
+          const int i00 = sym_at(p1, p2, ld), i01 = sym_at(p1, q2, ld), i10 = sym_at(q1, p2, ld),
+                    i11 = sym_at(q1, q2, ld);
+          const float2 R1 = __ldcg(cur + t), R2 = __ldcg(cur + u);
           float n00, n01, n10, n11;
-          jac_block(__ldcg(A + P1.p * ld + P2.p), __ldcg(A + P1.p * ld + P2.q), __ldcg(A + P1.q * ld + P2.p),
-                    __ldcg(A + P1.q * ld + P2.q), P1.c, P1.s, P2.c, P2.s, n00, n01, n10, n11);
-          if (same && sx != sy && P1.s != 0.0f) return 0.0f;
-          return sx ? (sy ? n11 : n10) : (sy ? n01 : n00);
-        };
-        const float app = elem(Pp, sp, Pp, sp, true);
-        const float aqq = elem(Pq, sq, Pq, sq, true);
-        const float apq = (tp <= tq) ? elem(Pp, sp, Pq, sq, tp == tq) : elem(Pq, sq, Pp, sp, false);
+          jac_block(__ldcg(A + i00), __ldcg(A + i01), __ldcg(A + i10), __ldcg(A + i11), R1.x, R1.y, R2.x, R2.y, n00,
+                    n01, n10, n11);
+          if (t == u) {
+            if (R1.y != 0.0f) n01 = 0.0f;
+            n10 = n01;
+          }
+          B[i00] = n00;
+          B[i01] = n01;
+          B[i10] = n10;
+          B[i11] = n11;
+        }
+        // V <- V J on the transposed rows p, q (when not deferred)
+        if (!defer)
+          for (int w = gtid; w < h * nv4; w += workers) {
+            const int t = w / nv4, c4 = (w - t * nv4) * 4;
+            int a1, b1;
+            circle_ab(t, r, n1, a1, b1);
+            const float2 R = __ldcg(cur + t);
+            float4* vp = reinterpret_cast<float4*>(Vt + min(a1, b1) * ldv + c4);
+            float4* vq = reinterpret_cast<float4*>(Vt + max(a1, b1) * ldv + c4);
+            const float4 x = __ldcg(vp), y = __ldcg(vq);
+            *vp = make_float4(__fmaf_rn(-R.y, y.x, __fmul_rn(R.x, x.x)), __fmaf_rn(-R.y, y.y, __fmul_rn(R.x, x.y)),
+                              __fmaf_rn(-R.y, y.z, __fmul_rn(R.x, x.z)), __fmaf_rn(-R.y, y.w, __fmul_rn(R.x, x.w)));
+            *vq = make_float4(__fmaf_rn(R.y, x.x, __fmul_rn(R.x, y.x)), __fmaf_rn(R.y, x.y, __fmul_rn(R.x, y.y)),
+                              __fmaf_rn(R.y, x.z, __fmul_rn(R.x, y.z)), __fmaf_rn(R.y, x.w, __fmul_rn(R.x, y.w)));
+          }
+      } else {
+        // rotation of slot rt for round r + 1 from the same old A
+        float ev[10];
+#pragma unroll
+        for (int z = 0; z < 10; ++z) ev[z] = __ldcg(A + rix[z]);
+        const float2 RA = __ldcg(cur + srcA), RB = __ldcg(cur + srcB);
+        const int sp = rfl & 1, sq = (rfl >> 1) & 1;
+        const bool pfirst = (rfl & 4) != 0, same = (rfl & 8) != 0, a_low = (rfl & 16) != 0;
+        const float2 Rp = a_low ? RA : RB, Rq = a_low ? RB : RA;
+        float n00, n01, n10, n11;
+        jac_block(ev[0], ev[1], ev[1], ev[2], Rp.x, Rp.y, Rp.x, Rp.y, n00, n01, n10, n11);
+        const float app = sp ? n11 : n00;
+        jac_block(ev[3], ev[4], ev[4], ev[5], Rq.x, Rq.y, Rq.x, Rq.y, n00, n01, n10, n11);
+        const float aqq = sq ? n11 : n00;
+        const float2 R1 = pfirst ? Rp : Rq, R2 = pfirst ? Rq : Rp;
+        const int sx = pfirst ? sp : sq, sy = pfirst ? sq : sp;
+        jac_block(ev[6], ev[7], ev[8], ev[9], R1.x, R1.y, R2.x, R2.y, n00, n01, n10, n11);
+        const float apq = (same && sx != sy && R1.y != 0.0f) ? 0.0f : (sx ? (sy ? n11 : n10) : (sy ? n01 : n00));
         float c, s;
         if (jac_rot(app, aqq, apq, c, s)) *last_rot = (r + 1 == n1) ? sweep + 1 : sweep;
-        JPair* nxt = pairs + (buf ^ 1) * half;
-        int* nt_ = tmap + (buf ^ 1) * kp;
-        int* ns_ = smap + (buf ^ 1) * kp;
-        nxt[rt] = JPair{p, q, c, s};
-        nt_[p] = rt;
-        nt_[q] = rt;
-        ns_[p] = 0;
-        ns_[q] = 1;
+        rots[(buf ^ 1) * h + rt] = make_float2(c, s);
+        if (defer && sweep * n1 + r + 1 < kJacSweeps * n1)
+          log[static_cast<size_t>(sweep * n1 + r + 1) * h + rt] = make_float2(c, s);
+        plan(r + 1 == n1 ? 0 : r + 1);
       }
       grid.sync();
-      abuf ^= 1;
       buf ^= 1;
     }
-    if (*last_rot < sweep) break;
+    if (*last_rot < sweep) {
+      sweeps = sweep;
+      break;
+    }
   }
-  for (long long e = gtid; e < static_cast<long long>(k) * k; e += gnt) {
-    const int i = static_cast<int>(e / k), j = static_cast<int>(e - static_cast<long long>(i) * k);
-    Vout[e] = __ldcg(Vt + j * ldv + i);
+  if (defer) {
+    if (gtid == 0) *rounds_out = sweeps * n1;
+  } else {
+    for (int e = gtid; e < k * k; e += gnt) {
+      const int i = e / k, j = e - i * k;
+      Vout[e] = __ldcg(Vt + j * ldv + i);
+    }
   }
 }
 
@@ -881,9 +903,8 @@ int smem_fits(size_t bytes) { return bytes <= 200 * 1024 ? 1 : 0; }
 // and V^T (kp x ldv).
 size_t jacobi_scratch_floats(int64_t k) {
   const int64_t kp = k + (k & 1), ldv = (kp + 3) & ~int64_t(3);
-  // matrices, then (grid version) JPair[2][kp/2] (4 kp floats), the two index
-  // maps (2 x 2 kp ints) and the flag
-  return static_cast<size_t>(2 * kp * (kp + 1) + kp * ldv + 8 * kp + 64);
+  // matrices, then (grid version) the rotations (c, s)[2][kp/2] and the flag
+  return static_cast<size_t>(2 * kp * (kp + 1) + kp * ldv + 2 * kp + 64);
 }
 
 // One-CTA kernels: about `work` elements per barrier phase, a few per thread.
@@ -899,7 +920,7 @@ int block_threads(int64_t work) {
 // ------------------------------------------------------------------ host API
 size_t jacobi_log_bytes(int64_t k) {
   const int64_t kp = k + (k & 1);
-  if (jac_cta_floats(static_cast<int>(kp)) * sizeof(float) > 200 * 1024) return 0;
+  if (kp > kJacLogMaxK) return 0;  // larger solves rotate V in every round instead
   return 256 + static_cast<size_t>(kJacSweeps) * (kp - 1) * (kp / 2) * sizeof(float2);
 }
 
@@ -985,7 +1006,7 @@ int jacobi_eig(int64_t k, const double* G, float* V, float* scratch, void* eig, 
     TB = ((nblk + per - 1) / per + 31) / 32 * 32;
     if (TB <= 18 * 32) break;
   }
-  if (eig && smem_fits(smem) && h <= 128 && TB <= 18 * 32 && rot_warps <= 6 && (nblk + TB - 1) / TB <= kJacItems) {
+  if (eig && jacobi_log_bytes(k) > 0 && smem_fits(smem) && h <= 128 && TB <= 18 * 32 && rot_warps <= 6 && (nblk + TB - 1) / TB <= kJacItems) {
     const int groups = std::max(rot_warps, TB / 32 / 3 + ((TB / 32) % 3 ? 1 : 0));
     int* rounds = static_cast<int*>(eig);
     float2* log = reinterpret_cast<float2*>(static_cast<uint8_t*>(eig) + 256);
@@ -1000,24 +1021,34 @@ int jacobi_eig(int64_t k, const double* G, float* V, float* scratch, void* eig, 
     jac_apply_v_kernel<rb><<<static_cast<unsigned>((k + rb - 1) / rb), threads, rb * kp * sizeof(float), st>>>(
         static_cast<int>(k), log, rounds, V);
   } else {
-    // too large for one SM: the whole grid works on every round (cooperative launch)
+    // too large for one SM: the whole grid works on every round (cooperative
+    // launch); h rotation threads plus the block threads
     static int blocks_per_sm = 0;
     if (blocks_per_sm == 0 &&
         cudaOccupancyMaxActiveBlocksPerMultiprocessor(&blocks_per_sm, jacobi_grid_kernel, 256, 0) != cudaSuccess)
       return SHG_ERR_CUDA;
     const int sms = sm_count();
     if (sms <= 0 || blocks_per_sm <= 0) return SHG_ERR_CUDA;
-    const long long work = (kp / 2) * (kp / 2);
-    long long want = (work + 255) / 256;
+    long long want = (static_cast<long long>(nblk) + h + 255) / 256;
     if (want > static_cast<long long>(sms) * blocks_per_sm) want = static_cast<long long>(sms) * blocks_per_sm;
-    if (want < 1) want = 1;
+    if (want * 256 < h + 32) return SHG_ERR_UNSUPPORTED;
+    const bool defer = eig && jacobi_log_bytes(k) > 0;
     int kk = static_cast<int>(k);
     const double* g = G;
     float* v = V;
     float* sc = scratch;
-    void* argv[] = {&kk, &g, &v, &sc};
-    return cuda_status(cudaLaunchCooperativeKernel(reinterpret_cast<const void*>(jacobi_grid_kernel),
-                                                   dim3(static_cast<unsigned>(want)), dim3(256), argv, 0, st));
+    int* rounds = defer ? static_cast<int*>(eig) : nullptr;
+    float2* log = defer ? reinterpret_cast<float2*>(static_cast<uint8_t*>(eig) + 256) : nullptr;
+    void* argv[] = {&kk, &g, &v, &sc, &log, &rounds};
+    if (cudaLaunchCooperativeKernel(reinterpret_cast<const void*>(jacobi_grid_kernel), dim3(static_cast<unsigned>(want)),
+                                    dim3(256), argv, 0, st) != cudaSuccess)
+      return SHG_ERR_CUDA;
+    if (defer) {
+      constexpr int rb = 8;
+      const int threads = (h + 31) / 32 * 32;
+      jac_apply_v_kernel<rb><<<static_cast<unsigned>((k + rb - 1) / rb), threads, rb * kp * sizeof(float), st>>>(
+          static_cast<int>(k), log, rounds, V);
+    }
   }
   return cuda_status(cudaGetLastError());
 }

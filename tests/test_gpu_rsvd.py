@@ -157,3 +157,19 @@ def test_rsvd_large_k_grid_eigensolver(shg):
     r_p = residual(A, U, S, V)
     assert abs(r_p - ref["r_p"]) <= 0.01 * ref["r_p"], (r_p, ref["r_p"])
     assert np.linalg.norm(U.T.astype(np.float64) @ U - np.eye(rank)) < 1e-4
+
+
+def test_rsvd_k_beyond_rotation_log(shg):
+    """k = 296 is beyond the size whose rotations the eigensolver logs: the
+    grid solver then rotates V in every round itself.  Same tolerances."""
+    m, n, rank, s = 900, 800, 280, 16
+    A = planted_svd(m, n, sigma_exp(min(m, n), 64.0), seed=12)
+    Om = omega_f16(n, rank + s, seed=13)
+    U, S, V = shg.shg_rsvd(dev(A), dev(Om), rank=rank, oversampling=s)
+    U, S, V = (t.cpu().numpy() for t in (U, S, V))
+    ref = OR.rsvd(A, Om, p=rank)
+    lead = slice(0, 64)
+    rel_s = np.abs(S.astype(np.float64) - ref["S"]) / ref["S"]
+    assert rel_s[lead].max() <= 1e-5, rel_s[lead].max()
+    r_p = residual(A, U, S, V)
+    assert abs(r_p - ref["r_p"]) <= 0.01 * ref["r_p"], (r_p, ref["r_p"])
