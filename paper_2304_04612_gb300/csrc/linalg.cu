@@ -188,10 +188,11 @@ __device__ __forceinline__ float2 df_recip(float2 d) {
 //   folded into ceil(n / 2) rows of n + 1 elements (rows r and n - 1 - r
 //   together), warps over those rows and lanes along them, so the lanes stay
 //   busy as the triangle shrinks.
-//   Inverse (FP32, from R rounded to FP32): X[j][j] = 1/R[j][j],
-//   X[i][j] = -(1/R[i][i]) sum_{l=i+1..j} R[i][l] X[l][j]; thread j
-//   back-substitutes column j alone.  Its rounding is of the same order as
-//   that of the FP32 product X R^-1 which follows.
+//   Inverse (FP32, from R rounded to FP32), by 16 x 16 blocks: inside a
+//   diagonal block X[j][j] = 1/R[j][j], X[i][j] = -(1/R[i][i])
+//   sum_{l=i+1..j} R[i][l] X[l][j]; off the diagonal X_ij = -X_ii
+//   sum_l R_il X_lj, one block diagonal after the other.  Its rounding is of
+//   the same order as that of the FP32 product X R^-1 which follows.
 // `a` (k^2 double-floats) and the FP32 R and X (k^2 floats each) live in
 // shared memory when they fit, else in `scratch` (2 k^2 doubles).  A
 // non-positive pivot raises SHG_FLAG_NOT_SPD and is replaced by the smallest
@@ -271,21 +272,55 @@ __global__ void __launch_bounds__(1024) chol_inv_kernel(int k, const double* __r
     }
   }
   __syncthreads();
-  for (int j = tid; j < k; j += nt) {
-    xf[j * k + j] = rinv[j];
-    for (int i = j - 1; i >= 0; --i) {
-      float s8[8] = {0, 0, 0, 0, 0, 0, 0, 0};
-      int l = i + 1;
-      for (; l + 7 <= j; l += 8) {
-#pragma unroll
-        for (int u = 0; u < 8; ++u) s8[u] = fmaf(rf[i * k + l + u], xf[(l + u) * k + j], s8[u]);
-      }
-      for (; l <= j; ++l) s8[7] = fmaf(rf[i * k + l], xf[l * k + j], s8[7]);
-      const float t = ((s8[0] + s8[1]) + (s8[2] + s8[3])) + ((s8[4] + s8[5]) + (s8[6] + s8[7]));
-      xf[i * k + j] = -t * rinv[i];
+  // X = R^-1 by 16 x 16 blocks (nb of them along the diagonal): the diagonal
+  // blocks by back-substitution (a thread per column), then block diagonal
+  // d = 1 .. nb - 1 for every block row i, j = i + d, from the blocks below:
+  // T = sum_{l = i+1 .. j} R_il X_lj, then X_ij = -X_ii T.  The dead
+  // elimination buffer holds T.
+  constexpr int BS = 16;
+  const int nb = (k + BS - 1) / BS;
+  float* T = reinterpret_cast<float*>(a);
+  for (int c = tid; c < k; c += nt) {
+    const int base = (c / BS) * BS;
+    xf[c * k + c] = rinv[c];
+    for (int i = c - 1; i >= base; --i) {
+      float s = 0.0f;
+      for (int l = i + 1; l <= c; ++l) s = fmaf(rf[i * k + l], xf[l * k + c], s);
+      xf[i * k + c] = -s * rinv[i];
     }
   }
   __syncthreads();
+  for (int d = 1; d < nb; ++d) {
+    const int cnt = (nb - d) * BS * BS;
+    for (int e = tid; e < cnt; e += nt) {
+      const int i = e / (BS * BS), r = (e / BS) % BS, c = e % BS;
+      const int row = i * BS + r, col = (i + d) * BS + c;
+      float s0 = 0.0f, s1 = 0.0f, s2 = 0.0f, s3 = 0.0f;
+      if (row < k && col < k) {
+        int l = (i + 1) * BS;
+        for (; l + 3 <= col; l += 4) {
+          s0 = fmaf(rf[row * k + l], xf[l * k + col], s0);
+          s1 = fmaf(rf[row * k + l + 1], xf[(l + 1) * k + col], s1);
+          s2 = fmaf(rf[row * k + l + 2], xf[(l + 2) * k + col], s2);
+          s3 = fmaf(rf[row * k + l + 3], xf[(l + 3) * k + col], s3);
+        }
+        for (; l <= col; ++l) s0 = fmaf(rf[row * k + l], xf[l * k + col], s0);
+      }
+      T[e] = (s0 + s1) + (s2 + s3);
+    }
+    __syncthreads();
+    for (int e = tid; e < cnt; e += nt) {
+      const int i = e / (BS * BS), r = (e / BS) % BS, c = e % BS;
+      const int row = i * BS + r, col = (i + d) * BS + c;
+      if (row < k && col < k) {
+        const int mend = min(BS, k - i * BS);
+        float s = 0.0f;
+        for (int m = r; m < mend; ++m) s = fmaf(xf[row * k + i * BS + m], T[i * BS * BS + m * BS + c], s);
+        xf[row * k + col] = -s;
+      }
+    }
+    __syncthreads();
+  }
   const float unscale = ldexpf(1.0f, -e2);
   for (int e = tid; e < k * k; e += nt) {
     const int i = e / k, j = e - i * k;
