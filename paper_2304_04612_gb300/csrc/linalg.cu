@@ -434,6 +434,7 @@ __device__ __forceinline__ float jac_elem_sym(const float* A, int ld, int p1, in
 // Shared layout: (c, s)[2][h], then the two A buffers (kp x (kp + 1) floats
 // each, upper triangles).
 constexpr int kJacSweeps = 40;
+constexpr int kJacChunk = 64;  // rotation rounds staged in shared memory at a time
 constexpr int kJacLogMaxK = 288;  // largest kp whose rotations are logged (13 MB at 40 sweeps)
 constexpr int kJacItems = 6;  // most blocks (or V pieces) one thread owns
 
@@ -613,13 +614,15 @@ __global__ void __launch_bounds__(768) jacobi_kernel(int k, const double* __rest
 // Rows of V are independent under V <- V J, so CTA b builds rows
 // [b RB, b RB + RB) in shared memory from identity rows, thread t applying
 // slot t's rotation to all of them (loads first), one barrier per round (a
-// warp barrier when one warp covers the slots).  The log is read eight
-// rounds ahead.  Writes Vout (k x k, row-major, columns = eigenvectors).
+// warp barrier when one warp covers the slots).  The log is staged
+// kJacChunk rounds at a time in shared memory.  Writes Vout (k x k,
+// row-major, columns = eigenvectors).
 template <int RB>
 __global__ void __launch_bounds__(512) jac_apply_v_kernel(int k, const float2* __restrict__ log,
                                                           const int* __restrict__ rounds, float* __restrict__ Vout) {
-  extern __shared__ float vs[];  // RB x kp
+  extern __shared__ __align__(16) float vs[];  // RB x kp rows, then kJacChunk x h rotations
   const int kp = k + (k & 1), h = kp / 2, n1 = kp - 1;
+  float2* lc = reinterpret_cast<float2*>(vs + RB * kp + (RB * kp & 1));
   const int row0 = blockIdx.x * RB;
   const int t = threadIdx.x, nt = blockDim.x;
   const bool one_warp = nt == 32;
@@ -627,47 +630,39 @@ __global__ void __launch_bounds__(512) jac_apply_v_kernel(int k, const float2* _
     const int i = e / kp, j = e - i * kp;
     vs[e] = (row0 + i == j) ? 1.0f : 0.0f;
   }
-  __syncthreads();
   const int R = *rounds;
   const bool on = t < h;
-  float2 cur[8], nxt[8];
-#pragma unroll
-  for (int u = 0; u < 8; ++u)
-    cur[u] = (on && u < R) ? log[static_cast<size_t>(u) * h + t] : make_float2(1.0f, 0.0f);
   int rm = 0;  // round mod n1
-  for (int g = 0; g < R; g += 8) {
+  for (int g = 0; g < R; g += kJacChunk) {
+    const int cnt = min(kJacChunk, R - g);
+    __syncthreads();  // the previous chunk is consumed (and the identity rows are written)
+    if (on)
+      for (int u = 0; u < cnt; ++u) lc[u * h + t] = log[static_cast<size_t>(g + u) * h + t];
+    __syncthreads();
+    for (int u = 0; u < cnt; ++u) {
+      if (on) {
+        int a, b;
+        circle_ab(t, rm, n1, a, b);
+        const int p = min(a, b), q = max(a, b);
+        const float2 cs = lc[u * h + t];
+        float x[RB], y[RB];
 #pragma unroll
-    for (int u = 0; u < 8; ++u)
-      nxt[u] = (on && g + 8 + u < R) ? log[static_cast<size_t>(g + 8 + u) * h + t] : make_float2(1.0f, 0.0f);
-#pragma unroll
-    for (int u = 0; u < 8; ++u) {
-      if (g + u < R) {
-        if (on) {
-          int a, b;
-          circle_ab(t, rm, n1, a, b);
-          const int p = min(a, b), q = max(a, b);
-          const float c = cur[u].x, sn = cur[u].y;
-          float x[RB], y[RB];
-#pragma unroll
-          for (int i = 0; i < RB; ++i) {
-            x[i] = vs[i * kp + p];
-            y[i] = vs[i * kp + q];
-          }
-#pragma unroll
-          for (int i = 0; i < RB; ++i) {
-            vs[i * kp + p] = __fmaf_rn(-sn, y[i], __fmul_rn(c, x[i]));
-            vs[i * kp + q] = __fmaf_rn(sn, x[i], __fmul_rn(c, y[i]));
-          }
+        for (int i = 0; i < RB; ++i) {
+          x[i] = vs[i * kp + p];
+          y[i] = vs[i * kp + q];
         }
-        if (++rm == n1) rm = 0;
-        if (one_warp)
-          __syncwarp();
-        else
-          __syncthreads();
-      }
-    }
 #pragma unroll
-    for (int u = 0; u < 8; ++u) cur[u] = nxt[u];
+        for (int i = 0; i < RB; ++i) {
+          vs[i * kp + p] = __fmaf_rn(-cs.y, y[i], __fmul_rn(cs.x, x[i]));
+          vs[i * kp + q] = __fmaf_rn(cs.y, x[i], __fmul_rn(cs.x, y[i]));
+        }
+      }
+      if (++rm == n1) rm = 0;
+      if (one_warp)
+        __syncwarp();
+      else
+        __syncthreads();
+    }
   }
   __syncthreads();
   for (int e = t; e < RB * k; e += nt) {
@@ -891,11 +886,13 @@ __global__ void rayleigh_kernel(int k, const double* __restrict__ G, const float
 
 // Sort eigenvalues descending (ties by index), S[j] = sqrt(lambda) for the
 // top p, Up = V[:, perm[:p]] normalised to unit length and Ups = Up / S
-// (k x p, FP32).
+// (k x p, FP32).  Ranks by counting (thread per eigenvalue), then all
+// threads write Up and Ups element by element.
 __global__ void sort_select_kernel(int k, int p, const double* __restrict__ lam, const double* __restrict__ nrm,
                                    const float* __restrict__ V, float* __restrict__ S, float* __restrict__ Up,
                                    float* __restrict__ Ups) {
-  extern __shared__ int rank_of[];
+  extern __shared__ double sel[];          // [p] 1 / ||v||, [p] 1 / (||v|| sigma)
+  int* perm = reinterpret_cast<int*>(sel + 2 * p);  // [p] column of rank r
   for (int i = threadIdx.x; i < k; i += blockDim.x) {
     const double li = lam[i];
     int r = 0;
@@ -903,22 +900,21 @@ __global__ void sort_select_kernel(int k, int p, const double* __restrict__ lam,
       const double lj = lam[j];
       r += (lj > li) || (lj == li && j < i);
     }
-    rank_of[i] = r;
-  }
-  __syncthreads();
-  for (int i = threadIdx.x; i < k; i += blockDim.x) {
-    const int r = rank_of[i];
     if (r < p) {
-      const double sg = sqrt(fmax(lam[i], 0.0));
+      const double sg = sqrt(fmax(li, 0.0));
       S[r] = static_cast<float>(sg);
       const double inv_n = 1.0 / nrm[i];
-      const double inv_s = sg > 0.0 ? inv_n / sg : 0.0;
-      for (int a = 0; a < k; ++a) {
-        const double v = V[a * k + i];
-        Up[a * p + r] = static_cast<float>(v * inv_n);
-        Ups[a * p + r] = static_cast<float>(v * inv_s);
-      }
+      sel[r] = inv_n;
+      sel[p + r] = sg > 0.0 ? inv_n / sg : 0.0;
+      perm[r] = i;
     }
+  }
+  __syncthreads();
+  for (int e = threadIdx.x; e < k * p; e += blockDim.x) {
+    const int a = e / p, r = e - a * p;
+    const double v = V[a * k + perm[r]];
+    Up[e] = static_cast<float>(v * sel[r]);
+    Ups[e] = static_cast<float>(v * sel[p + r]);
   }
 }
 
@@ -953,6 +949,10 @@ int block_threads(int64_t work) {
 }  // namespace
 
 // ------------------------------------------------------------------ host API
+static size_t apply_smem(int64_t kp, int rb) {
+  return (static_cast<size_t>(rb * kp + 1) & ~size_t(1)) * sizeof(float) + static_cast<size_t>(kJacChunk) * (kp / 2) * sizeof(float2);
+}
+
 size_t jacobi_log_bytes(int64_t k) {
   const int64_t kp = k + (k & 1);
   if (kp > kJacLogMaxK) return 0;  // larger solves rotate V in every round instead
@@ -1053,7 +1053,10 @@ int jacobi_eig(int64_t k, const double* G, float* V, float* scratch, void* eig, 
     // V: eight rows per CTA, one thread per slot
     constexpr int rb = 8;
     const int threads = (h + 31) / 32 * 32;
-    jac_apply_v_kernel<rb><<<static_cast<unsigned>((k + rb - 1) / rb), threads, rb * kp * sizeof(float), st>>>(
+    if (cudaFuncSetAttribute(jac_apply_v_kernel<rb>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             static_cast<int>(apply_smem(kp, rb))) != cudaSuccess)
+      return SHG_ERR_CUDA;
+    jac_apply_v_kernel<rb><<<static_cast<unsigned>((k + rb - 1) / rb), threads, apply_smem(kp, rb), st>>>(
         static_cast<int>(k), log, rounds, V);
   } else {
     // too large for one SM: the whole grid works on every round (cooperative
@@ -1081,7 +1084,10 @@ int jacobi_eig(int64_t k, const double* G, float* V, float* scratch, void* eig, 
     if (defer) {
       constexpr int rb = 8;
       const int threads = (h + 31) / 32 * 32;
-      jac_apply_v_kernel<rb><<<static_cast<unsigned>((k + rb - 1) / rb), threads, rb * kp * sizeof(float), st>>>(
+      if (cudaFuncSetAttribute(jac_apply_v_kernel<rb>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                               static_cast<int>(apply_smem(kp, rb))) != cudaSuccess)
+        return SHG_ERR_CUDA;
+      jac_apply_v_kernel<rb><<<static_cast<unsigned>((k + rb - 1) / rb), threads, apply_smem(kp, rb), st>>>(
           static_cast<int>(k), log, rounds, V);
     }
   }
@@ -1093,8 +1099,8 @@ int rayleigh_sort(int64_t k, int64_t p, const double* G, const float* V, double*
   double* nrm = lam + k;  // lam holds 2k doubles
   rayleigh_kernel<<<static_cast<unsigned>(k), 256, 0, st>>>(static_cast<int>(k), G, V, lam, nrm);
   if (cudaGetLastError() != cudaSuccess) return SHG_ERR_CUDA;
-  sort_select_kernel<<<1, 256, k * sizeof(int), st>>>(static_cast<int>(k), static_cast<int>(p), lam, nrm, V, S, Up,
-                                                      Ups);
+  sort_select_kernel<<<1, 1024, p * (2 * sizeof(double) + sizeof(int)), st>>>(static_cast<int>(k), static_cast<int>(p),
+                                                                              lam, nrm, V, S, Up, Ups);
   return cuda_status(cudaGetLastError());
 }
 
