@@ -285,7 +285,7 @@ int shg_rp_hosvd(int ndim, const int64_t* dims, const int64_t* ranks, const floa
  *   All arrays of sizes and pointers are HOST arrays of `batch` entries; the
  *   pointers in them are device pointers.  Workspace from
  *   shg_rsvd_batched_workspace_size (one slice per concurrent branch).
- * Problems run concurrently on up to 32 streams owned by the library
+ * Problems run concurrently on up to 128 streams owned by the library
  * (created on the first call on a device), forked from and joined back to
  * `stream`.  use_graph != 0: the first call with a given set of arguments
  * captures this fork/join into a CUDA graph, later calls with identical

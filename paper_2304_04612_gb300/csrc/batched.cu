@@ -18,7 +18,7 @@ namespace {
 
 inline int64_t round8(int64_t x) { return (x + 7) / 8 * 8; }
 
-constexpr int kMaxBranches = 32;
+constexpr int kMaxBranches = 128;
 constexpr int kMaxDevices = 64;
 constexpr int kMaxGraphs = 16;
 
