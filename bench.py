@@ -487,6 +487,7 @@ def side_measurements(shg, OS, torch, dev, A, A_host, Om, Om_host, Ys, flags, st
     out["rp_hosvd_512"] = hosvd_times(shg, torch, dev, stream)
     out["rsvd_batched_256"] = batched_times(shg, torch, dev, stream)
     out["rsvd_4096_p256"] = rsvd4096_times(shg, torch, dev, stream)
+    out["learned_sketch_2048"] = sketch_times(shg, torch, dev, stream)
 
     # CPU baseline: the oracle on a bounded row sample of the same sweep
     rate, rows_done, dt = oracle_rate(A_host, Om_host, budget_s=10.0)
@@ -544,6 +545,67 @@ def rsvd4096_times(shg, torch, dev, stream):
     res["optimal_residual"] = float(np.sqrt(np.sum(sig[p:] ** 2) / np.sum(sig ** 2)))
     res["l2"] = "A (64 MiB) stays in L2 between calls; the k x k steps dominate"
     return res
+
+
+def sketch_times(shg, torch, dev, stream, n_train=4096, n_test=512, k=96):
+    """Learned FP16 sketch for the 2048 x 2048 family A = U diag(sigma) (V0 cos T +
+    W sin T)^T + E (r = 64, sigma_j = 2^(-j/8), theta_j ~ U[0, 0.2], ||E|| = 1e-3
+    ||signal||): Omega (FP32 master, 2048 x 96) trained with Adam through SketchFn
+    (the library's SHGEMM projection and loss / gradient kernels) on n_train
+    generated matrices, one pass, batch 1; then the mean test loss
+    ||A - QQ^T A||_F^2 / ||A||_F^2 on n_test fresh matrices against a Gaussian
+    Omega of the same k, and the estimator's choice (choose_sketch, 16 probes)
+    on the first 64 test matrices.  The matrices are generated on the GPU from
+    seeded Gaussians in batches of 16 (input generation, not timed)."""
+    from paper_2304_04612_gb300.sketch import SketchFn, choose_sketch
+    n, r = 2048, 64
+    g = torch.Generator(device=dev).manual_seed(5)
+    V0 = torch.linalg.qr(torch.randn(n, r, device=dev, generator=g))[0]
+    sig = torch.pow(2.0, -torch.arange(1, r + 1, device=dev, dtype=torch.float32) / 8.0)
+
+    def family(count):
+        U = torch.linalg.qr(torch.randn(count, n, r, device=dev, generator=g))[0]
+        W = torch.randn(count, n, r, device=dev, generator=g)
+        W = torch.linalg.qr(W - V0 @ (V0.T @ W))[0]
+        th = torch.rand(count, 1, r, device=dev, generator=g) * 0.2
+        S = (U * sig) @ (V0 * torch.cos(th) + W * torch.sin(th)).transpose(1, 2)
+        E = torch.randn(count, n, n, device=dev, generator=g)
+        E *= (1e-3 * torch.linalg.norm(S, dim=(1, 2)) / torch.linalg.norm(E, dim=(1, 2)))[:, None, None]
+        return (S + E).contiguous()
+
+    omega = torch.randn(n, k, device=dev, generator=g).requires_grad_(True)
+    gauss = omega.detach().clone()
+    opt = torch.optim.Adam([omega], lr=0.01)
+    step_ms = []
+    for b in range(n_train // 16):
+        As = family(16)
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        for A in As:
+            opt.zero_grad()
+            SketchFn.apply(A, omega).backward()
+            opt.step()
+        e1.record(stream)
+        torch.cuda.synchronize()
+        step_ms.append(e0.elapsed_time(e1) / 16)
+    learned, base, better, used = [], [], 0, 0
+    with torch.no_grad():
+        for b in range(n_test // 16):
+            As = family(16)
+            for j, A in enumerate(As):
+                ll = SketchFn.apply(A, omega.detach()).item()
+                lg = SketchFn.apply(A, gauss).item()
+                learned.append(ll)
+                base.append(lg)
+                better += ll < lg
+                if b * 16 + j < 64:
+                    used += bool(choose_sketch(A, omega.detach(), seed=1000 + b * 16 + j, probes=16)[3])
+    return {"n": n, "k": k, "train_matrices": n_train, "test_matrices": n_test,
+            "train_step_ms": float(np.median(step_ms)),
+            "test_loss_learned": float(np.mean(learned)), "test_loss_gaussian": float(np.mean(base)),
+            "loss_ratio_learned_over_gaussian": float(np.mean(learned) / np.mean(base)),
+            "learned_better_fraction": better / len(learned),
+            "estimator_keeps_learned_of_64": used}
 
 
 def batched_times(shg, torch, dev, stream):
