@@ -268,6 +268,10 @@ int shg_rsvd(int64_t m, int64_t n, int64_t rank, int64_t oversampling, int power
  *   core (J0 x J1 x J2, row-major) = X x_0 Q_0^T x_1 Q_1^T x_2 Q_2^T.
  * variant: SHG_SPLIT_F16 (SHGEMM projections, TCEC-split first core
  * contraction) or SHG_FP32_SIMT (FP32 baseline).
+ * The three modes' projections and CholeskyQR2 run on three streams owned
+ * by the library (created on the first call on a device), forked from and
+ * joined back to `stream`; the call stays asynchronous and ordered on
+ * `stream`, also under stream capture.
  */
 int shg_rp_hosvd_workspace_size(int ndim, const int64_t* dims, const int64_t* ranks, size_t* bytes);
 int shg_rp_hosvd(int ndim, const int64_t* dims, const int64_t* ranks, const float* X,

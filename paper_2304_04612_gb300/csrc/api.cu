@@ -2,6 +2,7 @@
 // argument validation on the host, then the launches of Algorithm 1
 // (randomized SVD) and Algorithm 2 (RP-HOSVD) on the caller's stream.
 #include <cstring>
+#include <mutex>
 
 #include "internal.h"
 #include "linalg.h"
@@ -55,8 +56,37 @@ RsvdLayout rsvd_layout(int64_t m, int64_t n, int64_t k, int64_t rank) {
   return L;
 }
 
+// Three library streams per device for the independent per-mode work of
+// RP-HOSVD, with fork / join events; created on first use.
+struct ModePool {
+  cudaStream_t s[3] = {};
+  cudaEvent_t done[3] = {};
+  cudaEvent_t fork = nullptr;
+  bool ready = false;
+};
+ModePool g_mode_pool[64];
+std::mutex g_mode_mu;
+
+// The caller holds g_mode_mu (the pool's events are shared by every call on
+// the device, so a fork / join is enqueued by one host thread at a time).
+int mode_pool(ModePool** out) {
+  int dev = -1;
+  if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 64) return SHG_ERR_CUDA;
+  ModePool& p = g_mode_pool[dev];
+  if (!p.ready) {
+    for (int i = 0; i < 3; ++i) {
+      if (cudaStreamCreateWithFlags(&p.s[i], cudaStreamNonBlocking) != cudaSuccess) return SHG_ERR_CUDA;
+      if (cudaEventCreateWithFlags(&p.done[i], cudaEventDisableTiming) != cudaSuccess) return SHG_ERR_CUDA;
+    }
+    if (cudaEventCreateWithFlags(&p.fork, cudaEventDisableTiming) != cudaSuccess) return SHG_ERR_CUDA;
+    p.ready = true;
+  }
+  *out = &p;
+  return SHG_OK;
+}
+
 struct HosvdLayout {
-  size_t W[3], T, T1, T2, small, total;
+  size_t W[3], T[3], T1, T2, small[3], total;
   int64_t ld[3];
 };
 HosvdLayout hosvd_layout(const int64_t* d, const int64_t* J) {
@@ -75,10 +105,10 @@ HosvdLayout hosvd_layout(const int64_t* d, const int64_t* J) {
     maxL = L.ld[i] > maxL ? L.ld[i] : maxL;
     maxJ = J[i] > maxJ ? J[i] : maxJ;
   }
-  L.T = take(maxI * maxL * 4);
+  for (int i = 0; i < 3; ++i) L.T[i] = take(maxI * maxL * 4);  // one per mode: the modes run concurrently
   L.T1 = take(d[0] * d[1] * L.ld[2] * 4);
   L.T2 = take(d[0] * J[1] * J[2] * 4);
-  L.small = take(cholqr_small_bytes(maxJ));
+  for (int i = 0; i < 3; ++i) L.small[i] = take(cholqr_small_bytes(maxJ));
   L.total = off;
   return L;
 }
@@ -353,33 +383,53 @@ int shg_rp_hosvd(int ndim, const int64_t* dims, const int64_t* ranks, const floa
   uint8_t* w = static_cast<uint8_t*>(ws);
   float* W[3];
   for (int i = 0; i < 3; ++i) W[i] = reinterpret_cast<float*>(w + L.W[i]);
-  float* T = reinterpret_cast<float*>(w + L.T);
   float* T1 = reinterpret_cast<float*>(w + L.T1);
   float* T2 = reinterpret_cast<float*>(w + L.T2);
-  void* small = w + L.small;
   const int64_t I0 = dims[0], I1 = dims[1], I2 = dims[2];
   const int64_t J0 = ranks[0], J1 = ranks[1], J2 = ranks[2];
   const bool tc = (variant == SHG_SPLIT_F16);
 
-  // per mode: W_i = X_(i) Omega_(i), Q_i = orth(W_i)
-  if (tc) {
-    SHG_TRY(tc_gemm(A_KMAJ, B_F16, 2, I0, J0, I1 * I2, 1, X, I1 * I2, 0, omegas[0], ldo[0], W[0], L.ld[0], 0, d_flags, st));
-    SHG_TRY(tc_gemm(A_KMAJ, B_F16, 2, I1, J1, I2, I0, X, I2, I1 * I2, omegas[1], ldo[1], W[1], L.ld[1], 0, d_flags,
-                    st));
-    SHG_TRY(tc_gemm(A_MNMAJ, B_F16, 2, I2, J2, I0 * I1, 1, X, I2, 0, omegas[2], ldo[2], W[2], L.ld[2], 0, d_flags,
-                    st));
-  } else {
-    SHG_TRY(simt_gemm(I0, J0, I1 * I2, X, I1 * I2, 0, omegas[0], ldo[0], 1, W[0], L.ld[0], 0, 1, 0, 0, 0, st));
-    if (cudaMemsetAsync(W[1], 0, I1 * L.ld[1] * 4, st) != cudaSuccess) return SHG_ERR_CUDA;
-    SHG_TRY(simt_gemm(I1, J1, I2, X, I2, 0, omegas[1], ldo[1], 1, W[1], L.ld[1], 1, I0, I1 * I2, I2 * ldo[1], 0, st));
-    SHG_TRY(simt_gemm(I2, J2, I0 * I1, X, I2, 1, omegas[2], ldo[2], 1, W[2], L.ld[2], 0, 1, 0, 0, 0, st));
-  }
+  // per mode: W_i = X_(i) Omega_(i), Q_i = orth(W_i).  The three modes are
+  // independent: they run on three library streams forked from and joined
+  // back to `stream` (their single-CTA k x k steps then overlap).
+  std::unique_lock<std::mutex> pool_lock(g_mode_mu);
+  ModePool* mp = nullptr;
+  SHG_TRY(mode_pool(&mp));
+  if (cudaEventRecord(mp->fork, st) != cudaSuccess) return SHG_ERR_CUDA;
   for (int i = 0; i < 3; ++i) {
-    SHG_TRY(cholqr2(dims[i], ranks[i], W[i], L.ld[i], T, L.ld[i], small, d_flags, st));
+    cudaStream_t ms = mp->s[i];
+    if (cudaStreamWaitEvent(ms, mp->fork, 0) != cudaSuccess) return SHG_ERR_CUDA;
+    if (i == 0) {
+      if (tc)
+        SHG_TRY(tc_gemm(A_KMAJ, B_F16, 2, I0, J0, I1 * I2, 1, X, I1 * I2, 0, omegas[0], ldo[0], W[0], L.ld[0], 0,
+                        d_flags, ms));
+      else
+        SHG_TRY(simt_gemm(I0, J0, I1 * I2, X, I1 * I2, 0, omegas[0], ldo[0], 1, W[0], L.ld[0], 0, 1, 0, 0, 0, ms));
+    } else if (i == 1) {
+      if (tc) {
+        SHG_TRY(tc_gemm(A_KMAJ, B_F16, 2, I1, J1, I2, I0, X, I2, I1 * I2, omegas[1], ldo[1], W[1], L.ld[1], 0,
+                        d_flags, ms));
+      } else {
+        if (cudaMemsetAsync(W[1], 0, I1 * L.ld[1] * 4, ms) != cudaSuccess) return SHG_ERR_CUDA;
+        SHG_TRY(simt_gemm(I1, J1, I2, X, I2, 0, omegas[1], ldo[1], 1, W[1], L.ld[1], 1, I0, I1 * I2, I2 * ldo[1], 0,
+                          ms));
+      }
+    } else {
+      if (tc)
+        SHG_TRY(tc_gemm(A_MNMAJ, B_F16, 2, I2, J2, I0 * I1, 1, X, I2, 0, omegas[2], ldo[2], W[2], L.ld[2], 0,
+                        d_flags, ms));
+      else
+        SHG_TRY(simt_gemm(I2, J2, I0 * I1, X, I2, 1, omegas[2], ldo[2], 1, W[2], L.ld[2], 0, 1, 0, 0, 0, ms));
+    }
+    float* T = reinterpret_cast<float*>(w + L.T[i]);
+    SHG_TRY(cholqr2(dims[i], ranks[i], W[i], L.ld[i], T, L.ld[i], w + L.small[i], d_flags, ms));
     if (cudaMemcpy2DAsync(factors[i], ranks[i] * 4, W[i], L.ld[i] * 4, ranks[i] * 4, dims[i],
-                          cudaMemcpyDeviceToDevice, st) != cudaSuccess)
+                          cudaMemcpyDeviceToDevice, ms) != cudaSuccess)
       return SHG_ERR_CUDA;
+    if (cudaEventRecord(mp->done[i], ms) != cudaSuccess) return SHG_ERR_CUDA;
+    if (cudaStreamWaitEvent(st, mp->done[i], 0) != cudaSuccess) return SHG_ERR_CUDA;
   }
+  pool_lock.unlock();
   // core = X x_2 Q_2^T x_1 Q_1^T x_0 Q_0^T
   if (tc)
     SHG_TRY(tc_gemm(A_KMAJ, B_SPLIT, 2, I0 * I1, J2, I2, 1, X, I2, 0, W[2], L.ld[2], T1, L.ld[2], 0, d_flags, st));
