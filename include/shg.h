@@ -109,7 +109,9 @@ int shg_sparse_sign_f16(uint64_t seed, uint64_t offset, int64_t rows, int64_t co
  *   Omega: n x k (ldo >= k), FP16 bits (BF16 bits for SHG_SPLIT_BF16X*).
  *   Y: m x k FP32 (ldy >= k), overwritten.
  * variant: shg_variant.  SHG_SPLIT_BF16X* support trans_a = 0 only.
- * Device flags: SHG_FLAG_RANGE when some |a| >= 65520 under SHG_SPLIT_F16.
+ * Device flags: SHG_FLAG_RANGE when some |a| >= 65520 under SHG_SPLIT_F16
+ * (its hi piece overflows to infinity; the kernel detects the non-finite
+ * output row, so a NaN or infinite input raises the flag as well).
  * m, n, k >= 1 and < 2^31.
  */
 int shgemm_project(int64_t m, int64_t n, int64_t k,
@@ -126,7 +128,8 @@ int shgemm_project(int64_t m, int64_t n, int64_t k,
  *   trans_a = 0: A m x kk (lda >= kk); trans_a = 1: A kk x m (lda >= m).
  *   B: kk x n (ldb >= n, ldb % 4 == 0).  C: m x n (ldc >= n).
  *   accumulate = 0: C = op(A) B; 1: C += op(A) B.
- * Device flags: SHG_FLAG_RANGE when a value of A or B is >= 65520 in magnitude.
+ * Device flags: SHG_FLAG_RANGE when a value of A or B is >= 65520 in magnitude
+ * (B checked when it is split, A through the non-finite output it causes).
  */
 int shg_gemm_split3(int64_t m, int64_t n, int64_t kk,
                     const float* A, int64_t lda, int trans_a,

@@ -14,6 +14,8 @@
 //               staged FP32 tile, splits hi = RN_f16(a),
 //               lo = RN_f16((a - hi) * 2^11) (or BF16 pieces) and writes
 //               the pieces into TMEM lane r with tcgen05.st (the A operand)
+//               (an FP16 overflow, |a| >= 65520, makes hi infinite; the
+//               epilogue sees it as a non-finite Y and raises the range flag)
 //   warps 6..9  epilogue: drains the hi product every `kc` K blocks from
 //               TMEM into an FP32 running sum held in registers (RN adds);
 //               at the end of a segment Y = sum + 2^-11 acc_lo
@@ -132,14 +134,13 @@ __device__ __forceinline__ void read_row(const uint8_t* tile, int r, float (&a)[
 // the lower half), and store them at TMEM columns taddr + 32 * piece of this
 // thread's lane.
 template <bool BF16, int PIECES>
-__device__ __forceinline__ void split_to_tmem(const float (&a)[64], uint32_t taddr, float& vmax) {
+__device__ __forceinline__ void split_to_tmem(const float (&a)[64], uint32_t taddr) {
 #pragma unroll
   for (int h = 0; h < 4; ++h) {  // 8 columns (16 values) per store
     uint32_t out[PIECES][8];
 #pragma unroll
     for (int j = 0; j < 8; ++j) {
       const float x0 = a[16 * h + 2 * j], x1 = a[16 * h + 2 * j + 1];
-      vmax = fmaxf(vmax, fmaxf(fabsf(x0), fabsf(x1)));
       if constexpr (!BF16) {
         // hi = RN_f16(a); lo = RN_f16((a - hi) * 2^11): a - hi and the scaling are exact
         const __half2 hi = __floats2half2_rn(x0, x1);
@@ -508,19 +509,20 @@ __global__ void __launch_bounds__(kThreads, 1)
         break;
       }
       tc_fence_after();
-      split_to_tmem<kBF16, PIECES>(a, tm_a + lane_off + st * (PIECES * 32), vmax);
+      split_to_tmem<kBF16, PIECES>(a, tm_a + lane_off + st * (PIECES * 32));
       tc_wait_st();
       tc_fence_before();
       __syncwarp();
       if (lane == 0) mbar_arrive(bar_tfull + 8 * st);
     }
-    if (!kBF16 && vmax >= 65520.0f) atomicOr(args.flags, SHG_FLAG_RANGE);
+    if (kSplitB && vmax >= 65520.0f) atomicOr(args.flags, SHG_FLAG_RANGE);  // the FP32 B operand
   } else {
     // ---------------------------------------------------------- epilogue
     const int q = warp & 3;  // TMEM lane quadrant this warp may access
     const uint32_t lane_off = static_cast<uint32_t>(32 * q) << 16;
     long long u = u0, cc = 0;
     bool ok = true;
+    float nonfinite = 0.0f;  // FP16 split overflow (|a| >= 65520 makes hi infinite) shows as a non-finite Y
     float S[kMaxN];
     while (ok && u < u1) {
       const UnitPos p0 = decode(u, args);
@@ -576,6 +578,10 @@ __global__ void __launch_bounds__(kThreads, 1)
               v[j] = fmaf(t1, 0.00390625f, S[c0 + j]);
             }
           }
+          // an infinite hi piece makes every column of its row non-finite,
+          // so the row's first column tells (0, or NaN from inf / NaN)
+          if constexpr (!kBF16)
+            if (c0 == 0) nonfinite = __fmaf_rn(v[0], 0.0f, nonfinite);
           const int col0 = p0.nt * N + c0;
           if (row_ok && col0 < args.N) {
             if (vec && col0 + 16 <= args.N) {
@@ -608,6 +614,7 @@ __global__ void __launch_bounds__(kThreads, 1)
       u = seg_end;
     }
     if (!ok) *abort_flag = 1;
+    if (nonfinite != 0.0f) atomicOr(args.flags, SHG_FLAG_RANGE);
   }
 
   __syncthreads();
