@@ -30,7 +30,7 @@ bool tc_variant(int v) { return v == SHG_SPLIT_F16 || v == SHG_SPLIT_BF16X3 || v
 
 // Workspace layout of shg_rsvd.
 struct RsvdLayout {
-  size_t Y, T, Z, H, Bt, small, eig, Vk, lam, Up, Ups, total;
+  size_t Y, T, Z, H, Hlo, Bt, small, eig, Vk, lam, Up, Ups, total;
 };
 RsvdLayout rsvd_layout(int64_t m, int64_t n, int64_t k, int64_t rank) {
   const int64_t ldk = round8(k), mx = m > n ? m : n;
@@ -45,6 +45,7 @@ RsvdLayout rsvd_layout(int64_t m, int64_t n, int64_t k, int64_t rank) {
   L.T = take(mx * ldk * 4);
   L.Z = take(n * ldk * 4);
   L.H = take(mx * ldk * 2);
+  L.Hlo = take(m * ldk * 2);
   L.Bt = take(n * ldk * 4);
   L.small = take(cholqr_small_bytes(k));
   L.eig = take(jacobi_log_bytes(k));
@@ -86,7 +87,7 @@ int mode_pool(ModePool** out) {
 }
 
 struct HosvdLayout {
-  size_t W[3], T[3], T1, T2, small[3], total;
+  size_t W[3], T[3], T1, T2, small[3], Bhi, Blo, total;
   int64_t ld[3];
 };
 HosvdLayout hosvd_layout(const int64_t* d, const int64_t* J) {
@@ -109,6 +110,8 @@ HosvdLayout hosvd_layout(const int64_t* d, const int64_t* J) {
   L.T1 = take(d[0] * d[1] * L.ld[2] * 4);
   L.T2 = take(d[0] * J[1] * J[2] * 4);
   for (int i = 0; i < 3; ++i) L.small[i] = take(cholqr_small_bytes(maxJ));
+  L.Bhi = take(d[2] * L.ld[2] * 2);  // Q_2 split into FP16 hi / lo for the first core contraction
+  L.Blo = take(d[2] * L.ld[2] * 2);
   L.total = off;
   return L;
 }
@@ -334,8 +337,13 @@ int shg_rsvd(int64_t m, int64_t n, int64_t rank, int64_t oversampling, int power
     SHG_TRY(cholqr2(m, k, Y, ldk, T, ldk, small, d_flags, st));
   }
   // B^T = A^T Q (FP32-accurate)
-  if (tc)
-    SHG_TRY(tc_gemm(A_MNMAJ, B_SPLIT, 2, n, k, m, 1, A, lda, 0, Y, ldk, Bt, ldk, 0, d_flags, st));
+  if (tc) {
+    // Q split into FP16 hi / lo once (the TCEC B operand), then the TN product
+    uint16_t* Hlo = reinterpret_cast<uint16_t*>(w + L.Hlo);
+    SHG_TRY(split_f16(m, k, Y, ldk, H, Hlo, ldk, d_flags, st));
+    SHG_TRY(tc_gemm(A_MNMAJ, B_SPLIT_PRE, 2, n, k, m, 1, A, lda, 0, H, ldk, Bt, ldk, 0, d_flags, st, nullptr, nullptr,
+                    Hlo));
+  }
   else
     SHG_TRY(simt_gemm(n, k, m, A, lda, 1, Y, ldk, 0, Bt, ldk, 0, 1, 0, 0, 0, st));
   // small SVD of B through the eigendecomposition of B B^T = Bt^T Bt
@@ -431,8 +439,13 @@ int shg_rp_hosvd(int ndim, const int64_t* dims, const int64_t* ranks, const floa
   }
   pool_lock.unlock();
   // core = X x_2 Q_2^T x_1 Q_1^T x_0 Q_0^T
-  if (tc)
-    SHG_TRY(tc_gemm(A_KMAJ, B_SPLIT, 2, I0 * I1, J2, I2, 1, X, I2, 0, W[2], L.ld[2], T1, L.ld[2], 0, d_flags, st));
+  if (tc) {
+    uint16_t* Bhi = reinterpret_cast<uint16_t*>(w + L.Bhi);
+    uint16_t* Blo = reinterpret_cast<uint16_t*>(w + L.Blo);
+    SHG_TRY(split_f16(I2, J2, W[2], L.ld[2], Bhi, Blo, L.ld[2], d_flags, st));
+    SHG_TRY(tc_gemm(A_KMAJ, B_SPLIT_PRE, 2, I0 * I1, J2, I2, 1, X, I2, 0, Bhi, L.ld[2], T1, L.ld[2], 0, d_flags, st,
+                    nullptr, nullptr, Blo));
+  }
   else
     SHG_TRY(simt_gemm(I0 * I1, J2, I2, X, I2, 0, W[2], L.ld[2], 0, T1, L.ld[2], 0, 1, 0, 0, 0, st));
   SHG_TRY(simt_gemm(J1, J2, I1, W[1], L.ld[1], 1, T1, L.ld[2], 0, T2, J2, 0, I0, 0, I1 * L.ld[2], J1 * J2, st));

@@ -9,7 +9,7 @@
 namespace shg {
 
 enum AMajor : int { A_KMAJ = 0, A_MNMAJ = 1 };
-enum BMode : int { B_F16 = 0, B_BF16 = 1, B_SPLIT = 2 };
+enum BMode : int { B_F16 = 0, B_BF16 = 1, B_SPLIT = 2, B_SPLIT_PRE = 3 };
 
 // Test hooks of the tensor-core GEMM (never set by the public entry points).
 struct TcTestHooks {
@@ -22,8 +22,11 @@ struct TcTestHooks {
 //                   where the K index is (p, s), p < P, s < S_k (K = P * S_k);
 //                   B row of K index (p, s) is p * S_k + s.
 //   amaj = A_MNMAJ: A is K x M (A[k][m] at A + k * lda + m), P = 1.
-//   bmode: B_F16 / B_BF16 (B already 16-bit, `pieces` A pieces of that type)
-//          or B_SPLIT (B FP32 split into FP16 hi/lo, TCEC products).
+//   bmode: B_F16 / B_BF16 (B already 16-bit, `pieces` A pieces of that type),
+//          B_SPLIT (B FP32, split into FP16 hi/lo in every tile, TCEC
+//          products) or B_SPLIT_PRE (the same products with B split
+//          beforehand by split_f16: B = hi pieces, B_lo = lo pieces, FP16,
+//          leading dimension ldb).
 //   The launch configuration comes from `force` when given, else from the
 //   autotuner's cache for the call's shape class, else from the defaults.
 struct TcConfig {
@@ -35,7 +38,12 @@ struct TcConfig {
 int tc_gemm(int amaj, int bmode, int pieces, int64_t M, int64_t N, int64_t S_k, int64_t P,
             const float* A, int64_t lda, int64_t p_stride, const void* B, int64_t ldb, float* C,
             int64_t ldc, int accumulate, int32_t* d_flags, cudaStream_t stream,
-            const TcTestHooks* hooks = nullptr, const TcConfig* force = nullptr);
+            const TcTestHooks* hooks = nullptr, const TcConfig* force = nullptr, const void* B_lo = nullptr);
+// hi = RN_f16(b), lo = RN_f16((b - hi) 2^11) of a rows x cols FP32 matrix
+// (the TCEC split of the B operand, done once per call); raises
+// SHG_FLAG_RANGE when some |b| >= 65520.
+int split_f16(int64_t rows, int64_t cols, const float* B, int64_t ldb, uint16_t* hi, uint16_t* lo, int64_t ldo,
+              int32_t* d_flags, cudaStream_t stream);
 // Times the candidate configurations of this tc_gemm call (C is
 // overwritten; synchronises `stream`) and caches the fastest for the call's
 // shape class.  *best receives it; *found_before tells whether the class was

@@ -288,9 +288,11 @@ __device__ __forceinline__ void cta_range(const TcArgs& a, long long& u0, long l
 template <int AMAJ, int BMODE, int PIECES>
 __global__ void __launch_bounds__(kThreads, 1)
     tc_gemm_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmB,
-                   const TcArgs args) {
+                   const __grid_constant__ CUtensorMap tmB2, const TcArgs args) {
   constexpr bool kBF16 = (BMODE == B_BF16);
-  constexpr bool kSplitB = (BMODE == B_SPLIT);
+  constexpr bool kInplaceB = (BMODE == B_SPLIT);  // FP32 B split by the split warps in every tile
+  constexpr bool kPreB = (BMODE == B_SPLIT_PRE);  // hi / lo pieces of B loaded from two FP16 matrices
+  constexpr bool kSplitB = kInplaceB || kPreB;    // TCEC products
   constexpr int kNumL = kSplitB ? 1 : PIECES - 1;  // lo accumulators
   extern __shared__ uint8_t smem_raw[];
   uint8_t* smem = reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
@@ -343,6 +345,7 @@ __global__ void __launch_bounds__(kThreads, 1)
   if (warp == 0 && lane == 0) {
     tma_prefetch_desc(&tmA);
     tma_prefetch_desc(&tmB);
+    if (kPreB) tma_prefetch_desc(&tmB2);
   }
   if (warp == 1) {
     tmem_alloc(smem_u32(tmem_slot), args.tmem_cols);
@@ -399,8 +402,14 @@ __global__ void __launch_bounds__(kThreads, 1)
         const uint32_t bdst = smem_u32(b_ring + rb.s * args.b_bytes);
         const int brow = w.pp * args.S_k + w.sk * kBK;
         mbar_expect_tx(bfull, b_tx);
-        if (kSplitB) {
+        if (kInplaceB) {
           for (int j = 0; j < N / 32; ++j) tma_load_2d(bdst + j * 8192, &tmB, bfull, w.nt * N + 32 * j, brow);
+        } else if (kPreB) {
+          // the layout the in-place split would produce: hi blocks, then lo
+          for (int j = 0; j < N / 64; ++j) {
+            tma_load_2d(bdst + j * 8192, &tmB, bfull, w.nt * N + 64 * j, brow);
+            tma_load_2d(bdst + N * 128 + j * 8192, &tmB2, bfull, w.nt * N + 64 * j, brow);
+          }
         } else {
           for (int j = 0; j < N / 64; ++j) tma_load_2d(bdst + j * 8192, &tmB, bfull, w.nt * N + 64 * j, brow);
         }
@@ -436,7 +445,7 @@ __global__ void __launch_bounds__(kThreads, 1)
           for (; u < chunk_end; ++u, ++i, rt.next(ST), rb.next(SB)) {
             const int st = rt.s, sb = rb.s;
             if (!mbar_wait(bar_tfull + 8 * st, rt.ph, abort_flag, lim) ||
-                !mbar_wait((kSplitB ? bar_bready : bar_bfull) + 8 * sb, rb.ph, abort_flag, lim)) {
+                !mbar_wait((kInplaceB ? bar_bready : bar_bfull) + 8 * sb, rb.ph, abort_flag, lim)) {
               ok = false;
               break;
             }
@@ -486,7 +495,7 @@ __global__ void __launch_bounds__(kThreads, 1)
     for (long long u = u0; u < u1; ++u, ra.next(SA), rb.next(SB), rt.next(ST)) {
       const int sa = ra.s, sb = rb.s, st = rt.s;
       const uint32_t pa = ra.ph, pb = rb.ph, pt = rt.ph;
-      if (kSplitB) {
+      if (kInplaceB) {
         if (!warp_wait(bar_bfull + 8 * sb, pb, abort_flag, lim, lane)) {
           *abort_flag = 1;
           break;
@@ -515,7 +524,7 @@ __global__ void __launch_bounds__(kThreads, 1)
       __syncwarp();
       if (lane == 0) mbar_arrive(bar_tfull + 8 * st);
     }
-    if (kSplitB && vmax >= 65520.0f) atomicOr(args.flags, SHG_FLAG_RANGE);  // the FP32 B operand
+    if (kInplaceB && vmax >= 65520.0f) atomicOr(args.flags, SHG_FLAG_RANGE);  // the FP32 B operand
   } else {
     // ---------------------------------------------------------- epilogue
     const int q = warp & 3;  // TMEM lane quadrant this warp may access
@@ -683,8 +692,8 @@ int env_int(const char* name, int dflt) {
 }
 
 template <int AMAJ, int BMODE, int PIECES>
-int launch(const CUtensorMap& ta, const CUtensorMap& tb, const TcArgs& a, int grid, size_t smem,
-           cudaStream_t st) {
+int launch(const CUtensorMap& ta, const CUtensorMap& tb, const CUtensorMap& tb2, const TcArgs& a, int grid,
+           size_t smem, cudaStream_t st) {
   auto k = tc_gemm_kernel<AMAJ, BMODE, PIECES>;
   // The shared-memory carve-out is sized to what the rings need; the rest of
   // the SM's 256 KB stays L1.  One attribute update per instantiation,
@@ -701,7 +710,7 @@ int launch(const CUtensorMap& ta, const CUtensorMap& tb, const TcArgs& a, int gr
       return SHG_ERR_CUDA;
     configured[dev] = smem;
   }
-  k<<<grid, kThreads, smem, st>>>(ta, tb, a);
+  k<<<grid, kThreads, smem, st>>>(ta, tb, tb2, a);
   return cuda_status(cudaGetLastError());
 }
 
@@ -728,7 +737,7 @@ int floor_log2(int64_t x) {
 // N tiling of a call: tile width (a multiple of 64, at most 128 when the
 // accumulators and two A stages fit in TMEM) and the number of tiles.
 void n_tiling(int bmode, int pieces, int64_t N, int* nt_out, int* tiles_out) {
-  const int n_lo = (bmode == B_SPLIT) ? 1 : pieces - 1;
+  const int n_lo = (bmode == B_SPLIT || bmode == B_SPLIT_PRE) ? 1 : pieces - 1;
   const int max_tile = ((2 + n_lo) * 128 + 2 * pieces * 32 <= 512) ? 128 : 64;
   int nt = static_cast<int>(((N + 63) / 64) * 64);
   if (nt > max_tile) {
@@ -852,11 +861,13 @@ namespace {
 
 int tc_gemm_impl(int amaj, int bmode, int pieces, int64_t M, int64_t N, int64_t S_k, int64_t P, const float* A,
                  int64_t lda, int64_t p_stride, const void* B, int64_t ldb, float* C, int64_t ldc, int accumulate,
-                 int32_t* d_flags, cudaStream_t stream, const TcTestHooks* hooks, const TcConfig* force) {
+                 int32_t* d_flags, cudaStream_t stream, const TcTestHooks* hooks, const TcConfig* force,
+                 const void* B_lo) {
   if (M <= 0 || N <= 0 || S_k <= 0 || P <= 0) return SHG_ERR_INVALID_ARG;
   if (M >= (1ll << 31) || N >= (1ll << 31) || S_k * P >= (1ll << 31)) return SHG_ERR_INVALID_ARG;
   if (amaj == A_MNMAJ && P != 1) return SHG_ERR_INVALID_ARG;
-  if (bmode == B_SPLIT && pieces != 2) return SHG_ERR_INVALID_ARG;
+  if ((bmode == B_SPLIT || bmode == B_SPLIT_PRE) && pieces != 2) return SHG_ERR_INVALID_ARG;
+  if (bmode == B_SPLIT_PRE && (!B_lo || (reinterpret_cast<uintptr_t>(B_lo) & 15))) return SHG_ERR_INVALID_ARG;
   if (bmode == B_F16 && pieces != 2) return SHG_ERR_INVALID_ARG;
   if (bmode == B_BF16 && (pieces < 2 || pieces > 3 || amaj != A_KMAJ)) return SHG_ERR_UNSUPPORTED;
   const size_t bsz = (bmode == B_SPLIT) ? 4 : 2;
@@ -867,7 +878,7 @@ int tc_gemm_impl(int amaj, int bmode, int pieces, int64_t M, int64_t N, int64_t 
   TcArgs a{};
   a.M = static_cast<int>(M);
   a.N = static_cast<int>(N);
-  const int n_lo = (bmode == B_SPLIT) ? 1 : pieces - 1;
+  const int n_lo = (bmode == B_SPLIT || bmode == B_SPLIT_PRE) ? 1 : pieces - 1;
   // TMEM: D0, D1, lo accumulator(s), then at least two A stages of pieces x 32 columns
   int nt = 0;
   n_tiling(bmode, pieces, N, &nt, &a.n_tiles);
@@ -890,7 +901,8 @@ int tc_gemm_impl(int amaj, int bmode, int pieces, int64_t M, int64_t N, int64_t 
   uint32_t cols = 32;
   while (cols < static_cast<uint32_t>(acc_cols + a.st * pieces * 32)) cols <<= 1;
   a.tmem_cols = cols;
-  a.b_bytes = (bmode == B_SPLIT) ? static_cast<uint32_t>(nt) * 256u : static_cast<uint32_t>(nt) * 128u;
+  a.b_bytes = (bmode == B_SPLIT || bmode == B_SPLIT_PRE) ? static_cast<uint32_t>(nt) * 256u
+                                                        : static_cast<uint32_t>(nt) * 128u;
   const uint32_t bar_bytes = 1024;
   a.sa = std::max(2, std::min(cfg.sa, 6));
   a.sb = std::max(2, std::min(cfg.sb, 6));
@@ -906,7 +918,7 @@ int tc_gemm_impl(int amaj, int bmode, int pieces, int64_t M, int64_t N, int64_t 
   a.drop_commit = h.drop_commit;
   const size_t smem = 1024 + static_cast<size_t>(a.sa) * kABytes + static_cast<size_t>(a.sb) * a.b_bytes + bar_bytes;
 
-  CUtensorMap ta, tb;
+  CUtensorMap ta, tb, tb2;
   bool ok;
   if (amaj == A_KMAJ) {
     const uint64_t dims[3] = {static_cast<uint64_t>(S_k), static_cast<uint64_t>(M), static_cast<uint64_t>(P)};
@@ -927,6 +939,10 @@ int tc_gemm_impl(int amaj, int bmode, int pieces, int64_t M, int64_t N, int64_t 
     if (bmode == B_SPLIT) {
       const uint32_t box[2] = {32, 64};
       ok = make_map(&tb, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 2, B, dims, strides, box);
+    } else if (bmode == B_SPLIT_PRE) {
+      const uint32_t box[2] = {64, 64};
+      ok = make_map(&tb, CU_TENSOR_MAP_DATA_TYPE_FLOAT16, 2, B, dims, strides, box) &&
+           make_map(&tb2, CU_TENSOR_MAP_DATA_TYPE_FLOAT16, 2, B_lo, dims, strides, box);
     } else {
       const uint32_t box[2] = {64, 64};
       ok = make_map(&tb, bmode == B_BF16 ? CU_TENSOR_MAP_DATA_TYPE_BFLOAT16 : CU_TENSOR_MAP_DATA_TYPE_FLOAT16, 2,
@@ -934,6 +950,7 @@ int tc_gemm_impl(int amaj, int bmode, int pieces, int64_t M, int64_t N, int64_t 
     }
   }
   if (!ok) return SHG_ERR_CUDA;
+  if (bmode != B_SPLIT_PRE) tb2 = tb;  // unused by the other instances
 
   // stream-K grid: at most one CTA per SM, at least one unit per CTA
   const int sms = sm_count();
@@ -952,13 +969,15 @@ int tc_gemm_impl(int amaj, int bmode, int pieces, int64_t M, int64_t N, int64_t 
   }
 
   if (amaj == A_KMAJ) {
-    if (bmode == B_F16) return launch<A_KMAJ, B_F16, 2>(ta, tb, a, grid, smem, stream);
-    if (bmode == B_BF16 && pieces == 2) return launch<A_KMAJ, B_BF16, 2>(ta, tb, a, grid, smem, stream);
-    if (bmode == B_BF16 && pieces == 3) return launch<A_KMAJ, B_BF16, 3>(ta, tb, a, grid, smem, stream);
-    return launch<A_KMAJ, B_SPLIT, 2>(ta, tb, a, grid, smem, stream);
+    if (bmode == B_F16) return launch<A_KMAJ, B_F16, 2>(ta, tb, tb2, a, grid, smem, stream);
+    if (bmode == B_BF16 && pieces == 2) return launch<A_KMAJ, B_BF16, 2>(ta, tb, tb2, a, grid, smem, stream);
+    if (bmode == B_BF16 && pieces == 3) return launch<A_KMAJ, B_BF16, 3>(ta, tb, tb2, a, grid, smem, stream);
+    if (bmode == B_SPLIT_PRE) return launch<A_KMAJ, B_SPLIT_PRE, 2>(ta, tb, tb2, a, grid, smem, stream);
+    return launch<A_KMAJ, B_SPLIT, 2>(ta, tb, tb2, a, grid, smem, stream);
   }
-  if (bmode == B_F16) return launch<A_MNMAJ, B_F16, 2>(ta, tb, a, grid, smem, stream);
-  if (bmode == B_SPLIT) return launch<A_MNMAJ, B_SPLIT, 2>(ta, tb, a, grid, smem, stream);
+  if (bmode == B_F16) return launch<A_MNMAJ, B_F16, 2>(ta, tb, tb2, a, grid, smem, stream);
+  if (bmode == B_SPLIT) return launch<A_MNMAJ, B_SPLIT, 2>(ta, tb, tb2, a, grid, smem, stream);
+  if (bmode == B_SPLIT_PRE) return launch<A_MNMAJ, B_SPLIT_PRE, 2>(ta, tb, tb2, a, grid, smem, stream);
   return SHG_ERR_UNSUPPORTED;
 }
 
@@ -966,9 +985,39 @@ int tc_gemm_impl(int amaj, int bmode, int pieces, int64_t M, int64_t N, int64_t 
 
 int tc_gemm(int amaj, int bmode, int pieces, int64_t M, int64_t N, int64_t S_k, int64_t P, const float* A,
             int64_t lda, int64_t p_stride, const void* B, int64_t ldb, float* C, int64_t ldc, int accumulate,
-            int32_t* d_flags, cudaStream_t stream, const TcTestHooks* hooks, const TcConfig* force) {
+            int32_t* d_flags, cudaStream_t stream, const TcTestHooks* hooks, const TcConfig* force,
+            const void* B_lo) {
   return tc_gemm_impl(amaj, bmode, pieces, M, N, S_k, P, A, lda, p_stride, B, ldb, C, ldc, accumulate, d_flags,
-                      stream, hooks, force);
+                      stream, hooks, force, B_lo);
+}
+
+// ------------------------------------------------------ B split, once
+namespace {
+__global__ void split_f16_kernel(long long rows, long long cols, const float* __restrict__ B, long long ldb,
+                                 __half* __restrict__ hi, __half* __restrict__ lo, long long ldo, int* flags) {
+  const long long n = rows * cols;
+  bool big = false;
+  for (long long e = blockIdx.x * static_cast<long long>(blockDim.x) + threadIdx.x; e < n;
+       e += static_cast<long long>(gridDim.x) * blockDim.x) {
+    const long long r = e / cols, c = e - r * cols;
+    const float b = B[r * ldb + c];
+    const __half h = __float2half_rn(b);
+    hi[r * ldo + c] = h;
+    lo[r * ldo + c] = __float2half_rn((b - __half2float(h)) * 2048.0f);  // b - hi and the scaling are exact
+    big |= fabsf(b) >= 65520.0f;
+  }
+  if (big) atomicOr(flags, SHG_FLAG_RANGE);
+}
+}  // namespace
+
+int split_f16(int64_t rows, int64_t cols, const float* B, int64_t ldb, uint16_t* hi, uint16_t* lo, int64_t ldo,
+              int32_t* d_flags, cudaStream_t stream) {
+  if (rows < 1 || cols < 1 || ldb < cols || ldo < cols) return SHG_ERR_INVALID_ARG;
+  const long long n = rows * cols;
+  const int blocks = static_cast<int>(std::min<long long>((n + 255) / 256, 4LL * sm_count()));
+  split_f16_kernel<<<blocks, 256, 0, stream>>>(rows, cols, B, ldb, reinterpret_cast<__half*>(hi),
+                                              reinterpret_cast<__half*>(lo), ldo, d_flags);
+  return cuda_status(cudaGetLastError());
 }
 
 }  // namespace shg
