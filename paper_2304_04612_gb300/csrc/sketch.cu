@@ -149,9 +149,10 @@ int negate(int64_t rows, int64_t cols, float* C, int64_t ld, cudaStream_t st) {
   } while (0)
 
 // Workspace of shg_sketch_loss_grad: Q, T (m x ldk), W1 (n x ldk), W (m x ldk),
-// C, X1, X2, Rinv, Rit (k x ldk), the CholeskyQR scratch, two doubles.
+// C, X1, X2, Rinv, Rit (k x ldk), the CholeskyQR scratch, two doubles, and
+// the FP16 hi / lo pieces of the TCEC products' B operand (max(m, n) x ldk).
 struct SketchLayout {
-  size_t Q, T, W1, W, C, X1, X2, Rinv, Rit, small, acc, total;
+  size_t Q, T, W1, W, C, X1, X2, Rinv, Rit, small, acc, Bhi, Blo, total;
 };
 SketchLayout sketch_layout(int64_t m, int64_t n, int64_t k) {
   const int64_t ldk = round8(k);
@@ -173,6 +174,8 @@ SketchLayout sketch_layout(int64_t m, int64_t n, int64_t k) {
   L.Rit = take(k * ldk * 4);
   L.small = take(cholqr_small_bytes(k));
   L.acc = take(2 * sizeof(double));
+  L.Bhi = take((m > n ? m : n) * ldk * 2);
+  L.Blo = take((m > n ? m : n) * ldk * 2);
   L.total = off;
   return L;
 }
@@ -323,13 +326,21 @@ extern "C" int shg_sketch_loss_grad(int64_t m, int64_t n, int64_t k, const float
   SHG_TRY(simt_gemm(m, k, k, T, ldk, 0, X2, ldk, 0, Q, ldk, 0, 1, 0, 0, 0, st));
   // loss = 1 - ||A^T Q||^2 / ||A||^2, A^T Q FP32-accurate by the TCEC split
   SHG_TRY(sumsq(m, n, A, lda, acc, st));
-  SHG_TRY(tc_gemm(A_MNMAJ, B_SPLIT, 2, n, k, m, 1, A, lda, 0, Q, ldk, W1, ldk, 0, d_flags, st));
+  uint16_t* Bhi = reinterpret_cast<uint16_t*>(w + L.Bhi);
+  uint16_t* Blo = reinterpret_cast<uint16_t*>(w + L.Blo);
+  // TCEC product with the FP32 B operand split into FP16 hi / lo once
+  auto tcec = [&](int amaj, int64_t M, int64_t K, const float* B, float* C_, int64_t ldc) {
+    SHG_TRY(split_f16(K, k, B, ldk, Bhi, Blo, ldk, d_flags, st));
+    return tc_gemm(amaj, B_SPLIT_PRE, 2, M, k, K, 1, A, lda, 0, Bhi, ldk, C_, ldc, 0, d_flags, st, nullptr,
+                   nullptr, Blo);
+  };
+  SHG_TRY(tcec(A_MNMAJ, n, m, Q, W1, ldk));
   SHG_TRY(sumsq(n, k, W1, ldk, acc + 1, st));
   loss_kernel<<<1, 1, 0, st>>>(acc, d_loss);
   SHG_TRY(cuda_status(cudaGetLastError()));
   if (!want_grad) return SHG_OK;
   // W = A (A^T Q); P = (I - Q Q^T) W = W + Q (-(Q^T W))
-  SHG_TRY(tc_gemm(A_KMAJ, B_SPLIT, 2, m, k, n, 1, A, lda, 0, W1, ldk, W, ldk, 0, d_flags, st));
+  SHG_TRY(tcec(A_KMAJ, m, n, W1, W, ldk));
   SHG_TRY(simt_gemm(k, k, m, Q, ldk, 1, W, ldk, 0, C, ldk, 0, 1, 0, 0, 0, st));
   SHG_TRY(negate(k, k, C, ldk, st));
   SHG_TRY(simt_gemm(m, k, k, Q, ldk, 0, C, ldk, 0, W, ldk, 1, 1, 0, 0, 0, st));
@@ -340,5 +351,5 @@ extern "C" int shg_sketch_loss_grad(int64_t m, int64_t n, int64_t k, const float
   SHG_TRY(cuda_status(cudaGetLastError()));
   SHG_TRY(simt_gemm(m, k, k, W, ldk, 0, Rit, ldk, 0, T, ldk, 0, 1, 0, 0, 0, st));
   // dl/dOmega = A^T dl/dY (TCEC split, TN)
-  return tc_gemm(A_MNMAJ, B_SPLIT, 2, n, k, m, 1, A, lda, 0, T, ldk, d_omega, ldd, 0, d_flags, st);
+  return tcec(A_MNMAJ, n, m, T, d_omega, ldd);
 }
