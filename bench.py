@@ -40,8 +40,8 @@ M = N = 16384
 # taken on; reported only while the sources are unchanged.
 TRAFFIC = {
     "sources": ["paper_2304_04612_gb300/csrc/shgemm_tc.cu", "paper_2304_04612_gb300/csrc/ptx.cuh"],
-    "sha256": "e1a424181065cf1abd7d38642e5ee0f80bf2bad0c1e7fd3977f1d0757a5a8aad",
-    "bytes_per_launch": {"64": 1093550080, "128": 1109739520, "256": 1123002112, "512": 1153815552},
+    "sha256": "25998ac94bf82907cedfc2f61f604ee7e7e1846daa3221ba569562bdd39bc4fd",
+    "bytes_per_launch": {"64": 1093532416, "128": 1111054336, "256": 1123832320, "512": 1153206016},
 }
 
 

@@ -434,7 +434,6 @@ __device__ __forceinline__ float jac_elem_sym(const float* A, int ld, int p1, in
 // Shared layout: (c, s)[2][h], then the two A buffers (kp x (kp + 1) floats
 // each, upper triangles).
 constexpr int kJacSweeps = 40;
-constexpr int kJacChunk = 64;  // rotation rounds staged in shared memory at a time
 constexpr int kJacLogMaxK = 288;  // largest kp whose rotations are logged (13 MB at 40 sweeps)
 constexpr int kJacItems = 6;  // most blocks (or V pieces) one thread owns
 
@@ -614,15 +613,13 @@ __global__ void __launch_bounds__(768) jacobi_kernel(int k, const double* __rest
 // Rows of V are independent under V <- V J, so CTA b builds rows
 // [b RB, b RB + RB) in shared memory from identity rows, thread t applying
 // slot t's rotation to all of them (loads first), one barrier per round (a
-// warp barrier when one warp covers the slots).  The log is staged
-// kJacChunk rounds at a time in shared memory.  Writes Vout (k x k,
-// row-major, columns = eigenvectors).
+// warp barrier when one warp covers the slots).  The log is read eight
+// rounds ahead.  Writes Vout (k x k, row-major, columns = eigenvectors).
 template <int RB>
 __global__ void __launch_bounds__(512) jac_apply_v_kernel(int k, const float2* __restrict__ log,
                                                           const int* __restrict__ rounds, float* __restrict__ Vout) {
-  extern __shared__ __align__(16) float vs[];  // RB x kp rows, then kJacChunk x h rotations
+  extern __shared__ float vs[];  // RB x kp
   const int kp = k + (k & 1), h = kp / 2, n1 = kp - 1;
-  float2* lc = reinterpret_cast<float2*>(vs + RB * kp + (RB * kp & 1));
   const int row0 = blockIdx.x * RB;
   const int t = threadIdx.x, nt = blockDim.x;
   const bool one_warp = nt == 32;
@@ -630,39 +627,47 @@ __global__ void __launch_bounds__(512) jac_apply_v_kernel(int k, const float2* _
     const int i = e / kp, j = e - i * kp;
     vs[e] = (row0 + i == j) ? 1.0f : 0.0f;
   }
+  __syncthreads();
   const int R = *rounds;
   const bool on = t < h;
+  float2 cur[8], nxt[8];
+#pragma unroll
+  for (int u = 0; u < 8; ++u)
+    cur[u] = (on && u < R) ? log[static_cast<size_t>(u) * h + t] : make_float2(1.0f, 0.0f);
   int rm = 0;  // round mod n1
-  for (int g = 0; g < R; g += kJacChunk) {
-    const int cnt = min(kJacChunk, R - g);
-    __syncthreads();  // the previous chunk is consumed (and the identity rows are written)
-    if (on)
-      for (int u = 0; u < cnt; ++u) lc[u * h + t] = log[static_cast<size_t>(g + u) * h + t];
-    __syncthreads();
-    for (int u = 0; u < cnt; ++u) {
-      if (on) {
-        int a, b;
-        circle_ab(t, rm, n1, a, b);
-        const int p = min(a, b), q = max(a, b);
-        const float2 cs = lc[u * h + t];
-        float x[RB], y[RB];
+  for (int g = 0; g < R; g += 8) {
 #pragma unroll
-        for (int i = 0; i < RB; ++i) {
-          x[i] = vs[i * kp + p];
-          y[i] = vs[i * kp + q];
-        }
+    for (int u = 0; u < 8; ++u)
+      nxt[u] = (on && g + 8 + u < R) ? log[static_cast<size_t>(g + 8 + u) * h + t] : make_float2(1.0f, 0.0f);
 #pragma unroll
-        for (int i = 0; i < RB; ++i) {
-          vs[i * kp + p] = __fmaf_rn(-cs.y, y[i], __fmul_rn(cs.x, x[i]));
-          vs[i * kp + q] = __fmaf_rn(cs.y, x[i], __fmul_rn(cs.x, y[i]));
+    for (int u = 0; u < 8; ++u) {
+      if (g + u < R) {
+        if (on) {
+          int a, b;
+          circle_ab(t, rm, n1, a, b);
+          const int p = min(a, b), q = max(a, b);
+          const float c = cur[u].x, sn = cur[u].y;
+          float x[RB], y[RB];
+#pragma unroll
+          for (int i = 0; i < RB; ++i) {
+            x[i] = vs[i * kp + p];
+            y[i] = vs[i * kp + q];
+          }
+#pragma unroll
+          for (int i = 0; i < RB; ++i) {
+            vs[i * kp + p] = __fmaf_rn(-sn, y[i], __fmul_rn(c, x[i]));
+            vs[i * kp + q] = __fmaf_rn(sn, x[i], __fmul_rn(c, y[i]));
+          }
         }
+        if (++rm == n1) rm = 0;
+        if (one_warp)
+          __syncwarp();
+        else
+          __syncthreads();
       }
-      if (++rm == n1) rm = 0;
-      if (one_warp)
-        __syncwarp();
-      else
-        __syncthreads();
     }
+#pragma unroll
+    for (int u = 0; u < 8; ++u) cur[u] = nxt[u];
   }
   __syncthreads();
   for (int e = t; e < RB * k; e += nt) {
@@ -949,10 +954,6 @@ int block_threads(int64_t work) {
 }  // namespace
 
 // ------------------------------------------------------------------ host API
-static size_t apply_smem(int64_t kp, int rb) {
-  return (static_cast<size_t>(rb * kp + 1) & ~size_t(1)) * sizeof(float) + static_cast<size_t>(kJacChunk) * (kp / 2) * sizeof(float2);
-}
-
 size_t jacobi_log_bytes(int64_t k) {
   const int64_t kp = k + (k & 1);
   if (kp > kJacLogMaxK) return 0;  // larger solves rotate V in every round instead
@@ -1053,10 +1054,7 @@ int jacobi_eig(int64_t k, const double* G, float* V, float* scratch, void* eig, 
     // V: eight rows per CTA, one thread per slot
     constexpr int rb = 8;
     const int threads = (h + 31) / 32 * 32;
-    if (cudaFuncSetAttribute(jac_apply_v_kernel<rb>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                             static_cast<int>(apply_smem(kp, rb))) != cudaSuccess)
-      return SHG_ERR_CUDA;
-    jac_apply_v_kernel<rb><<<static_cast<unsigned>((k + rb - 1) / rb), threads, apply_smem(kp, rb), st>>>(
+    jac_apply_v_kernel<rb><<<static_cast<unsigned>((k + rb - 1) / rb), threads, rb * kp * sizeof(float), st>>>(
         static_cast<int>(k), log, rounds, V);
   } else {
     // too large for one SM: the whole grid works on every round (cooperative
@@ -1084,10 +1082,7 @@ int jacobi_eig(int64_t k, const double* G, float* V, float* scratch, void* eig, 
     if (defer) {
       constexpr int rb = 8;
       const int threads = (h + 31) / 32 * 32;
-      if (cudaFuncSetAttribute(jac_apply_v_kernel<rb>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                               static_cast<int>(apply_smem(kp, rb))) != cudaSuccess)
-        return SHG_ERR_CUDA;
-      jac_apply_v_kernel<rb><<<static_cast<unsigned>((k + rb - 1) / rb), threads, apply_smem(kp, rb), st>>>(
+      jac_apply_v_kernel<rb><<<static_cast<unsigned>((k + rb - 1) / rb), threads, rb * kp * sizeof(float), st>>>(
           static_cast<int>(k), log, rounds, V);
     }
   }
