@@ -194,14 +194,17 @@ __device__ __forceinline__ float2 df_recip(float2 d) {
 //   sum_l R_il X_lj, one block diagonal after the other.  Its rounding is of
 //   the same order as that of the FP32 product X R^-1 which follows.
 // `a` (k^2 double-floats) and the FP32 R and X (k^2 floats each) live in
-// shared memory when they fit, else in `scratch` (2 k^2 doubles).  A
+// shared memory when they fit, else in `scratch` (2 k^2 doubles, then k
+// double-float pivot reciprocals); there the elimination has run in panels
+// before (pre_dinv: the reciprocals) and this kernel only forms R^-1.  A
 // non-positive pivot raises SHG_FLAG_NOT_SPD and is replaced by the smallest
 // positive normal float so that R stays finite.
 // SMEM selects the shared-memory layout at compile time, so that the
 // accesses compile to shared loads and stores rather than generic ones.
 template <bool SMEM>
 __global__ void __launch_bounds__(1024) chol_inv_kernel(int k, const double* __restrict__ G, float* __restrict__ Xf,
-                                                       double* scratch, int* flags) {
+                                                       double* scratch, int* flags,
+                                                       const float2* __restrict__ pre_dinv) {
   extern __shared__ __align__(16) float2 smd[];
   float2* a = SMEM ? smd : reinterpret_cast<float2*>(scratch);
   float* rf = reinterpret_cast<float*>(a + k * k);
@@ -216,6 +219,11 @@ __global__ void __launch_bounds__(1024) chol_inv_kernel(int k, const double* __r
   __syncthreads();
   const int e2 = (dmax > 0.0) ? (ilogb(dmax) >> 1) : 0;
   const double sigma = ldexp(1.0, -2 * e2);
+  if (pre_dinv) {
+    // eliminated already (chol_panel_kernel / chol_trail_kernel): the
+    // unscaled rows are in `a`, the pivot reciprocals in pre_dinv
+    for (int j = tid; j < k; j += nt) dinv[j] = pre_dinv[j];
+  } else {
   for (int e = tid; e < k * k; e += nt) {
     const int i = e / k, j = e - i * k;
     float2 v = make_float2(0.0f, 0.0f);
@@ -260,6 +268,8 @@ __global__ void __launch_bounds__(1024) chol_inv_kernel(int k, const double* __r
     if (tid == 0) pivot(j + 1);
     __syncthreads();
   }
+  }
+  __syncthreads();
   // R in FP32: R[i][l] = a[i][l] / R[i][i], 1/R[i][i] = sqrt(1/d_i)
   for (int i = tid; i < k; i += nt)
     rinv[i] = static_cast<float>(sqrt(static_cast<double>(dinv[i].x) + static_cast<double>(dinv[i].y)));
@@ -325,6 +335,99 @@ __global__ void __launch_bounds__(1024) chol_inv_kernel(int k, const double* __r
   for (int e = tid; e < k * k; e += nt) {
     const int i = e / k, j = e - i * k;
     Xf[e] = (j >= i) ? xf[e] * unscale : 0.0f;
+  }
+}
+
+// The same elimination for k too large for shared memory, in panels of
+// kCholPanel columns over the whole GPU (the matrix stays in L2):
+// chol_scale_kernel writes the scaled double-float upper triangle,
+// chol_panel_kernel (one CTA) eliminates the panel's own rows column by
+// column, chol_trail_kernel applies the panel to the trailing triangle,
+// a 32 x 32 tile per CTA:
+//   a[l][l'] -= sum_{j in panel} (a[j][l] / d_j) a[j][l'],
+// the same operations in the same order as the one-CTA elimination.
+// chol_inv_kernel<false> with pre_dinv then forms R^-1.
+constexpr int kCholPanel = 32;
+
+__global__ void __launch_bounds__(256) chol_scale_kernel(int k, const double* __restrict__ G, float2* __restrict__ a) {
+  __shared__ double red[32];
+  __shared__ double dmax;
+  diag_max(k, G, red, &dmax);  // every block forms the scale itself
+  __syncthreads();
+  const int e2 = (dmax > 0.0) ? (ilogb(dmax) >> 1) : 0;
+  const double sigma = ldexp(1.0, -2 * e2);
+  for (long long e = blockIdx.x * 256LL + threadIdx.x; e < static_cast<long long>(k) * k; e += gridDim.x * 256LL) {
+    const int i = static_cast<int>(e / k), j = static_cast<int>(e - static_cast<long long>(i) * k);
+    float2 v = make_float2(0.0f, 0.0f);
+    if (j >= i) {
+      const double g = G[e] * sigma;
+      v.x = static_cast<float>(g);
+      v.y = static_cast<float>(g - static_cast<double>(v.x));
+    }
+    a[e] = v;
+  }
+}
+
+__global__ void __launch_bounds__(1024) chol_panel_kernel(int k, int j0, int j1, float2* a, float2* dinv_g,
+                                                         int* flags) {
+  __shared__ float2 dj_s;
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5, nw = blockDim.x >> 5;
+  for (int j = j0; j < j1; ++j) {
+    if (tid == 0) {
+      float2 d = a[static_cast<size_t>(j) * k + j];
+      if (!(d.x > 0.0f)) {
+        atomicOr(flags, SHG_FLAG_NOT_SPD);
+        d = make_float2(1.17549435e-38f, 0.0f);
+        a[static_cast<size_t>(j) * k + j] = d;
+      }
+      dj_s = df_recip(d);
+      dinv_g[j] = dj_s;
+    }
+    __syncthreads();
+    const float2 dj = dj_s;
+    const float2* rowj = a + static_cast<size_t>(j) * k;
+    for (int l = j + 1 + warp; l < j1; l += nw) {
+      const float2 t = df_mul(rowj[l], dj);
+      float2* rowl = a + static_cast<size_t>(l) * k;
+      for (int lp = l + lane; lp < k; lp += 32) rowl[lp] = df_sub_mul(rowl[lp], t, rowj[lp]);
+    }
+    __syncthreads();
+  }
+}
+
+__global__ void __launch_bounds__(256) chol_trail_kernel(int k, int j0, int j1, float2* a,
+                                                        const float2* __restrict__ dinv_g) {
+  // tile (ti, tj), ti <= tj, of the trailing triangle rows / columns [j1, k)
+  const int t = (k - j1 + 31) / 32;
+  int ti = 0, rem = blockIdx.x;
+  while (rem >= t - ti) {
+    rem -= t - ti;
+    ++ti;
+  }
+  const int tj = ti + rem;
+  __shared__ float2 T[kCholPanel][33];   // a[j][l] / d_j for the tile's rows l
+  __shared__ float2 P[kCholPanel][33];   // a[j][l'] for the tile's columns l'
+  const int np = j1 - j0;
+  const int l0 = j1 + ti * 32, c0 = j1 + tj * 32;
+  for (int e = threadIdx.x; e < np * 32; e += 256) {
+    const int j = e >> 5, x = e & 31;
+    const float2* rowj = a + static_cast<size_t>(j0 + j) * k;
+    const float2 dj = dinv_g[j0 + j];
+    T[j][x] = (l0 + x < k) ? df_mul(rowj[l0 + x], dj) : make_float2(0.0f, 0.0f);
+    P[j][x] = (c0 + x < k) ? rowj[c0 + x] : make_float2(0.0f, 0.0f);
+  }
+  __syncthreads();
+  const int r = threadIdx.x >> 3, cb = (threadIdx.x & 7) * 4;
+  const int l = l0 + r;
+  if (l >= k) return;
+#pragma unroll
+  for (int q = 0; q < 4; ++q) {
+    const int lp = c0 + cb + q;
+    if (lp < k && lp >= l) {
+      float2 v = a[static_cast<size_t>(l) * k + lp];
+      for (int j = 0; j < np; ++j) v = df_sub_mul(v, T[j][r], P[j][cb + q]);
+      a[static_cast<size_t>(l) * k + lp] = v;
+    }
   }
 }
 
@@ -969,7 +1072,7 @@ namespace {
 void small_offsets(int64_t k, size_t off[5]) {
   off[0] = 0;
   off[1] = off[0] + align256(static_cast<size_t>(k * k) * 8);
-  off[2] = off[1] + align256(static_cast<size_t>(2 * k * k) * 8);
+  off[2] = off[1] + align256(static_cast<size_t>(2 * k * k + k) * 8);
   off[3] = off[2] + align256(static_cast<size_t>(k * k) * 4);
   off[4] = off[3] + align256(jacobi_scratch_floats(k) * 4);
 }
@@ -1014,16 +1117,36 @@ int chol_inv(int64_t k, const double* G, float* Rinv, double* scratch, int32_t* 
   if (k > 1024) return SHG_ERR_UNSUPPORTED;
   const size_t need = static_cast<size_t>(2 * k * k) * sizeof(double);
   const int in_smem = smem_fits(need);
-  const size_t smem = in_smem ? need : 0;
   const int threads = block_threads(k * k / 4);
+  const int kk = static_cast<int>(k);
   if (in_smem) {
     if (cudaFuncSetAttribute(chol_inv_kernel<true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                             static_cast<int>(smem)) != cudaSuccess)
+                             static_cast<int>(need)) != cudaSuccess)
       return SHG_ERR_CUDA;
-    chol_inv_kernel<true><<<1, threads, smem, st>>>(static_cast<int>(k), G, Rinv, scratch, flags);
-  } else {
-    chol_inv_kernel<false><<<1, threads, 0, st>>>(static_cast<int>(k), G, Rinv, scratch, flags);
+    chol_inv_kernel<true><<<1, threads, need, st>>>(kk, G, Rinv, scratch, flags, nullptr);
+    return cuda_status(cudaGetLastError());
   }
+  // matrix in global memory: scale, then panels of kCholPanel columns (one
+  // CTA each) with their trailing updates over the whole GPU, then R^-1
+  float2* a = reinterpret_cast<float2*>(scratch);
+  float2* dinv_g = reinterpret_cast<float2*>(scratch + 2 * k * k);
+  const int sms = sm_count();
+  if (sms <= 0) return SHG_ERR_CUDA;
+  const long long cells = k * k;
+  chol_scale_kernel<<<static_cast<unsigned>(std::min<long long>((cells + 255) / 256, 4LL * sms)), 256, 0, st>>>(kk, G,
+                                                                                                               a);
+  if (cudaGetLastError() != cudaSuccess) return SHG_ERR_CUDA;
+  for (int j0 = 0; j0 < kk; j0 += kCholPanel) {
+    const int j1 = std::min(j0 + kCholPanel, kk);
+    chol_panel_kernel<<<1, 1024, 0, st>>>(kk, j0, j1, a, dinv_g, flags);
+    if (cudaGetLastError() != cudaSuccess) return SHG_ERR_CUDA;
+    if (j1 < kk) {
+      const int t = (kk - j1 + 31) / 32;
+      chol_trail_kernel<<<static_cast<unsigned>(t * (t + 1) / 2), 256, 0, st>>>(kk, j0, j1, a, dinv_g);
+      if (cudaGetLastError() != cudaSuccess) return SHG_ERR_CUDA;
+    }
+  }
+  chol_inv_kernel<false><<<1, threads, 0, st>>>(kk, G, Rinv, scratch, flags, dinv_g);
   return cuda_status(cudaGetLastError());
 }
 

@@ -12,7 +12,7 @@ size_t cholqr_small_bytes(int64_t k);
 // Pieces of that scratch (base must be 256-byte aligned).
 struct SmallWs {
   double* G;     // k x k FP64 Gram matrix (upper triangle)
-  double* chol;  // 2 k^2 doubles: Cholesky factor and inverse when not in shared memory
+  double* chol;  // 2 k^2 + k doubles: Cholesky factor, inverse, pivots when not in shared memory
   float* Rf;     // k x k FP32 R^-1
   float* jac;    // Jacobi matrices when not in shared memory
 };
