@@ -537,6 +537,7 @@ __device__ __forceinline__ float jac_elem_sym(const float* A, int ld, int p1, in
 // Shared layout: (c, s)[2][h], then the two A buffers (kp x (kp + 1) floats
 // each, upper triangles).
 constexpr int kJacSweeps = 40;
+constexpr int kJacGridThreads = 128;  // CTA size of the grid solver (more SMs per round)
 constexpr int kJacLogMaxK = 288;  // largest kp whose rotations are logged (13 MB at 40 sweeps)
 constexpr int kJacItems = 6;  // most blocks (or V pieces) one thread owns
 
@@ -791,7 +792,7 @@ __global__ void __launch_bounds__(512) jac_apply_v_kernel(int k, const float2* _
 // without it V^T is rotated in every round here.  Layout of `scratch`: A
 // buffers (2 kp (kp + 1) floats), V^T (kp x ldv), the rotations (c, s)[2][h],
 // last_rot.
-__global__ void __launch_bounds__(256) jacobi_grid_kernel(int k, const double* __restrict__ G,
+__global__ void __launch_bounds__(kJacGridThreads) jacobi_grid_kernel(int k, const double* __restrict__ G,
                                                          float* __restrict__ Vout, float* scratch,
                                                          float2* __restrict__ log, int* __restrict__ rounds_out) {
   namespace cg = cooperative_groups;
@@ -1184,13 +1185,14 @@ int jacobi_eig(int64_t k, const double* G, float* V, float* scratch, void* eig, 
     // launch); h rotation threads plus the block threads
     static int blocks_per_sm = 0;
     if (blocks_per_sm == 0 &&
-        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&blocks_per_sm, jacobi_grid_kernel, 256, 0) != cudaSuccess)
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&blocks_per_sm, jacobi_grid_kernel, kJacGridThreads, 0) !=
+            cudaSuccess)
       return SHG_ERR_CUDA;
     const int sms = sm_count();
     if (sms <= 0 || blocks_per_sm <= 0) return SHG_ERR_CUDA;
-    long long want = (static_cast<long long>(nblk) + h + 255) / 256;
+    long long want = (static_cast<long long>(nblk) + h + kJacGridThreads - 1) / kJacGridThreads;
     if (want > static_cast<long long>(sms) * blocks_per_sm) want = static_cast<long long>(sms) * blocks_per_sm;
-    if (want * 256 < h + 32) return SHG_ERR_UNSUPPORTED;
+    if (want * kJacGridThreads < h + 32) return SHG_ERR_UNSUPPORTED;
     const bool defer = eig && jacobi_log_bytes(k) > 0;
     int kk = static_cast<int>(k);
     const double* g = G;
@@ -1200,7 +1202,7 @@ int jacobi_eig(int64_t k, const double* G, float* V, float* scratch, void* eig, 
     float2* log = defer ? reinterpret_cast<float2*>(static_cast<uint8_t*>(eig) + 256) : nullptr;
     void* argv[] = {&kk, &g, &v, &sc, &log, &rounds};
     if (cudaLaunchCooperativeKernel(reinterpret_cast<const void*>(jacobi_grid_kernel), dim3(static_cast<unsigned>(want)),
-                                    dim3(256), argv, 0, st) != cudaSuccess)
+                                    dim3(kJacGridThreads), argv, 0, st) != cudaSuccess)
       return SHG_ERR_CUDA;
     if (defer) {
       constexpr int rb = 8;
