@@ -119,6 +119,24 @@ def dist_env():
     return ws, rank, local
 
 
+def max_over_ranks(x: float, ws: int, device) -> float:
+    """The largest of the ranks' values (a MAX all-reduce over the process
+    group); a single rank's own value."""
+    if ws == 1:
+        return x
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([x], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def whole_job_tflops(flop_per_step: float, steps: int, ws: int, ms_total: float) -> float:
+    """Rate of ws replicas that each ran `steps` steps of `flop_per_step`,
+    over the slowest replica's time."""
+    return flop_per_step * steps * ws / (ms_total * 1e-3) / 1e12
+
+
 def oracle_rate(A_host, Om_host, budget_s=10.0, ks=KS):
     """Oracle (FP64 CPU) throughput on a bounded row sample of the sweep."""
     from oracle import shgemm as OS
@@ -246,15 +264,13 @@ def main():
             ev[k].append(e[k])
     t1.record(stream)
     torch.cuda.synchronize()
-    ms_total = t0.elapsed_time(t1)
     if ws > 1:
-        tt = torch.tensor([ms_total], device=dev)
-        torch.distributed.all_reduce(tt, op=torch.distributed.ReduceOp.MAX)
-        ms_total = float(tt.item())
+        torch.distributed.barrier()
+    ms_total = max_over_ranks(t0.elapsed_time(t1), ws, dev)
     clk = clocks.stop()
     ms_step = ms_total / args.steps
     flop_step = sum(2.0 * M * N * k for k in KS)
-    value = flop_step * args.steps * ws / (ms_total * 1e-3) / 1e12
+    value = whole_job_tflops(flop_step, args.steps, ws, ms_total)
     per_k_ms = {k: float(np.mean([a.elapsed_time(b) for a, b in ev[k]])) for k in KS}
     shg.check_flags(flags, "timed steps")
 

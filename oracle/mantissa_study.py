@@ -1,6 +1,6 @@
 """CPU study of the accuracy of the random projection with low-precision
 Gaussian test matrices (the numerical experiment closing the analysis of
-Sec. 3; the survey's "next" list, item 3).  Test infrastructure only.
+Sec. 3).  Test infrastructure only.
 
 The Gaussian matrix G (n x k) is drawn in FP32 and rounded RN to a shorter
 mantissa (an eXmY format of `oracle.lowp`), then A and G are taken to FP64
