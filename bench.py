@@ -193,9 +193,10 @@ def main():
     ap.add_argument("--case", type=int, nargs=2, metavar=("MN", "K"),
                     help="profiling case: only W + K launches of one m=n=MN, k=K SHGEMM (no JSON contract line)")
     ap.add_argument("--variant", default="f16", help="variant for --case")
-    ap.add_argument("--factor", choices=["rsvd", "hosvd", "rsvd4096"],
-                    help="profiling case: W + K calls of the randomized SVD of the 1024^2 planted matrix "
-                         "or of RP-HOSVD of the 512^3 Tucker tensor (no JSON contract line)")
+    ap.add_argument("--factor", choices=["rsvd", "hosvd", "rsvd4096", "batched"],
+                    help="profiling case: W + K calls of the randomized SVD of the 1024^2 planted matrix, "
+                         "of the 4096^2 p = 256 matrix, of RP-HOSVD of the 512^3 Tucker tensor or of the "
+                         "256-problem batched randomized SVD on the stream pool (no JSON contract line)")
     args = ap.parse_args()
     if args.impl == "reference":
         run_reference(args)
@@ -366,6 +367,11 @@ def run_factor(args):
         A, Om = torch.from_numpy(A_h).to(dev), torch.from_numpy(Om_h).to(dev)
         ws = torch.empty(shg.rsvd_workspace_size(1024, 1024, 32, 32, 0), dtype=torch.uint8, device=dev)
         fn = lambda: shg.shg_rsvd(A, Om, 32, 32, 0, args.variant, workspace=ws, flags=fl, check=False)
+    elif args.factor == "batched":
+        As, ranks, s_, q_, ws, out = batched_problems(shg, torch, dev, dct_bases=True)
+        # on the stream pool without the graph: launches in enqueue order, problem by problem
+        fn = lambda: shg.shg_rsvd_batched(As, ranks, s_, q_, omegas=None, seed=4, use_graph=False, out=out,
+                                          workspace=ws, flags=fl, check=False)
     else:
         dims, J = (512, 512, 512), (48, 48, 48)
         X_h, _, _ = tucker(dims, (32, 32, 32), seed=3, noise_std=1e-4)
@@ -624,26 +630,43 @@ def sketch_times(shg, torch, dev, stream, n_train=4096, n_test=512, k=96):
             "estimator_keeps_learned_of_64": used}
 
 
-def batched_times(shg, torch, dev, stream):
+def batched_problems(shg, torch, dev, dct_bases=False):
     """256 uneven randomized SVDs (m in [256, 4096], n in [256, 2048], rank in
     {16, 32, 64, 128}, s = 16, q = 1, sigma_i = 2^(-i/rate), rate in [8, 64]).
-    The matrices are built on the GPU from seeded Gaussians as
-    Q1 diag(sigma) Q2^T with Q1, Q2 orthonormal bases of 256 columns (the
-    spectrum beyond 256 is below 2^-4 at the slowest decay and is dropped):
-    input generation only, outside every timed region."""
+    The matrices are Q1 diag(sigma) Q2^T with Q1, Q2 orthonormal bases of 256
+    columns (the spectrum beyond 256 is below 2^-4 at the slowest decay and is
+    dropped): by default the Q factors of seeded Gaussians, built on the GPU;
+    with dct_bases, randomly chosen and signed columns of the orthonormal
+    DCT-II matrix, built on the host (no torch.linalg, whose lazily loaded
+    library does not load under the profiler).  Input generation only,
+    outside every timed region.  Returns the matrices, ranks, s, q, a
+    workspace and the output tensors."""
     from synth import batch_specs
     specs = batch_specs(256, seed=4)
     g = torch.Generator(device=dev).manual_seed(4)
+    rng = np.random.default_rng(4)
+
+    def dct_basis(m, r):
+        from scipy.fft import dct
+        E = np.zeros((m, r), dtype=np.float32)
+        E[rng.choice(m, r, replace=False), np.arange(r)] = 1.0
+        Q = dct(E, axis=0, norm="ortho").astype(np.float32)
+        return Q * rng.choice(np.array([-1.0, 1.0], dtype=np.float32), size=(m, 1))
+
     As, ranks = [], []
     for sp in specs:
         m, n = sp["m"], sp["n"]
         r = min(m, n, 256)
-        sig = torch.pow(2.0, -torch.arange(1, r + 1, device=dev, dtype=torch.float32) / sp["rate"])
-        q1 = torch.linalg.qr(torch.randn(m, r, device=dev, generator=g))[0]
-        q2 = torch.linalg.qr(torch.randn(n, r, device=dev, generator=g))[0]
         ld = (n + 3) // 4 * 4
         buf = torch.zeros(m, ld, device=dev)
-        buf[:, :n] = (q1 * sig) @ q2.T
+        if dct_bases:
+            sig = (2.0 ** (-np.arange(1, r + 1) / sp["rate"])).astype(np.float32)
+            buf[:, :n] = torch.from_numpy((dct_basis(m, r) * sig) @ dct_basis(n, r).T).to(dev)
+        else:
+            sig = torch.pow(2.0, -torch.arange(1, r + 1, device=dev, dtype=torch.float32) / sp["rate"])
+            q1 = torch.linalg.qr(torch.randn(m, r, device=dev, generator=g))[0]
+            q2 = torch.linalg.qr(torch.randn(n, r, device=dev, generator=g))[0]
+            buf[:, :n] = (q1 * sig) @ q2.T
         As.append(buf[:, :n])
         ranks.append(sp["rank"])
     s, q = 16, 1
@@ -651,6 +674,14 @@ def batched_times(shg, torch, dev, stream):
     ws = torch.empty(shg.rsvd_batched_workspace_size(ms_, ns_, ranks, s, q), dtype=torch.uint8, device=dev)
     out = ([torch.empty(m, r, device=dev) for m, r in zip(ms_, ranks)], [torch.empty(r, device=dev) for r in ranks],
            [torch.empty(n, r, device=dev) for n, r in zip(ns_, ranks)])
+    return As, ranks, s, q, ws, out
+
+
+def batched_times(shg, torch, dev, stream):
+    """The 256-problem batch of `batched_problems` as one CUDA graph, on the
+    stream pool without the graph, and one problem after another."""
+    As, ranks, s, q, ws, out = batched_problems(shg, torch, dev)
+    ms_, ns_ = [A.shape[0] for A in As], [A.shape[1] for A in As]
     fl = shg.new_flags(dev)
     res = {"problems": 256, "bytes_of_A": int(sum(4 * m * n for m, n in zip(ms_, ns_)))}
     for mode, use_graph in (("graph", True), ("streams", False)):
