@@ -432,12 +432,6 @@ __global__ void __launch_bounds__(256) chol_trail_kernel(int k, int j0, int j1, 
 }
 
 // --------------------------------------------------------------- Jacobi FP32
-// One pair of a round: rows/columns p < q rotated by (c, s).
-struct __align__(16) JPair {
-  int p, q;
-  float c, s;
-};
-
 // The 2 x 2 block of J^T A J at pair rows (c, s) and pair columns
 // (c2, s2) from the old block m: rows first (new p = c p - s q,
 // new q = s p + c q), then columns the same way.  The products are rounded
@@ -452,17 +446,6 @@ __device__ __forceinline__ void jac_block(float m00, float m01, float m10, float
   n01 = __fmaf_rn(s2, l00, __fmul_rn(c2, l01));
   n10 = __fmaf_rn(-s2, l11, __fmul_rn(c2, l10));
   n11 = __fmaf_rn(s2, l10, __fmul_rn(c2, l11));
-}
-
-// Element (x, y) of J^T A J where x is side sx of pair P1 and y side sy of
-// pair P2 (P1 == P2 allowed: the rotated pair's off-diagonal is exactly 0).
-__device__ __forceinline__ float jac_elem(const float* A, int ld, const JPair& P1, int sx, const JPair& P2, int sy,
-                                          bool same) {
-  float n00, n01, n10, n11;
-  jac_block(A[P1.p * ld + P2.p], A[P1.p * ld + P2.q], A[P1.q * ld + P2.p], A[P1.q * ld + P2.q], P1.c, P1.s, P2.c,
-            P2.s, n00, n01, n10, n11);
-  if (same && sx != sy && P1.s != 0.0f) return 0.0f;
-  return sx ? (sy ? n11 : n10) : (sy ? n01 : n00);
 }
 
 // Rotation annihilating a_pq of the 2 x 2 block [[app, apq], [apq, aqq]]
@@ -494,18 +477,6 @@ __device__ __forceinline__ void circle_ab(int t, int r, int n1, int& a, int& b) 
 
 // Element (x, y) of a symmetric matrix kept as its upper triangle.
 __device__ __forceinline__ int sym_at(int x, int y, int ld) { return min(x, y) * ld + max(x, y); }
-
-// Element (x, y) of J^T A J (A symmetric, upper triangle) where x is side sx
-// of pair (p1, q1, c1, s1) and y side sy of pair (p2, q2, c2, s2); same:
-// both are the same pair, whose rotated off-diagonal is exactly 0.
-__device__ __forceinline__ float jac_elem_sym(const float* A, int ld, int p1, int q1, float2 r1, int sx, int p2,
-                                              int q2, float2 r2, int sy, bool same) {
-  float n00, n01, n10, n11;
-  jac_block(A[sym_at(p1, p2, ld)], A[sym_at(p1, q2, ld)], A[sym_at(q1, p2, ld)], A[sym_at(q1, q2, ld)], r1.x, r1.y,
-            r2.x, r2.y, n00, n01, n10, n11);
-  if (same && sx != sy && r1.y != 0.0f) return 0.0f;
-  return sx ? (sy ? n11 : n10) : (sy ? n01 : n00);
-}
 
 // Eigenvalues of the symmetric k x k matrix whose upper triangle is in G
 // (FP64), by the parallel cyclic Jacobi method: A = sigma G in FP32 (sigma a
