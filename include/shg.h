@@ -298,6 +298,11 @@ int shg_rp_hosvd(int ndim, const int64_t* dims, const int64_t* ranks, const floa
  * captures this fork/join into a CUDA graph, later calls with identical
  * arguments (same pointers and sizes) replay it with one graph launch; up to
  * 16 graphs are kept per process.  Calls are serialised by a mutex.
+ * Each problem's multi-CTA launches (projections, Gram matrices, GEMMs) size
+ * their grids for 16 SMs instead of the whole GPU, so that the problems in
+ * flight share the GPU; the environment variable SHG_BATCHED_GRID_SMS
+ * (0 = the whole GPU) overrides the share.  Results are the same up to the
+ * order of floating-point sums.
  * Device flags: as shg_rsvd (OR-ed over all problems).
  */
 int shg_rsvd_batched_workspace_size(int batch, const int64_t* m, const int64_t* n, const int64_t* rank,

@@ -20,6 +20,16 @@ int sm_count() {
   return n;
 }
 
+thread_local int g_grid_share = 0;
+
+int grid_sms() {
+  const int n = sm_count();
+  return (n > 0 && g_grid_share > 0 && g_grid_share < n) ? g_grid_share : n;
+}
+
+GridShare::GridShare(int sms) : prev_(g_grid_share) { g_grid_share = sms > 0 ? sms : 0; }
+GridShare::~GridShare() { g_grid_share = prev_; }
+
 int ceil_div_i(int64_t a, int64_t b) { return static_cast<int>((a + b - 1) / b); }
 
 namespace {

@@ -7,6 +7,7 @@
 // small projections fill the GPU together).  With use_graph the whole
 // fork/join is captured once into a CUDA graph, cached by the call's
 // arguments, and replayed with one graph launch on the caller's stream.
+#include <cstdlib>
 #include <cstring>
 #include <mutex>
 #include <vector>
@@ -62,6 +63,20 @@ int pool_for_device(Pool** out, int* dev_out) {
 
 int branches_for(int batch) { return batch < kMaxBranches ? batch : kMaxBranches; }
 
+// SMs over which each problem's multi-CTA launches (projections, Gram
+// matrices, GEMMs) size their grids; 0 = the whole GPU.  With many problems
+// in flight on the branch streams a share keeps one problem's few-
+// microsecond launch from occupying every SM: 256 uneven problems as one
+// graph took 29.3 ms with whole-GPU grids, 22.1 / 22.4 / 23.5 / 25.5 ms with
+// shares of 8 / 16 / 38 / 76 SMs (16 also keeps the graph-less stream pool
+// at its whole-GPU speed).  SHG_BATCHED_GRID_SMS overrides it (tuning
+// experiments).
+constexpr int kBatchedGridSms = 16;
+int batched_grid_sms() {
+  if (const char* e = std::getenv("SHG_BATCHED_GRID_SMS")) return std::atoi(e);
+  return kBatchedGridSms;
+}
+
 // Largest per-problem need: the shg_rsvd workspace plus an FP16 Omega
 // (n x round8(k)) for problems whose Omega is generated.
 int branch_bytes(int batch, const int64_t* m, const int64_t* n, const int64_t* rank, int64_t s, int q,
@@ -104,9 +119,10 @@ struct Args {
   int32_t* flags;
 };
 
-std::vector<uint8_t> make_key(const Args& a, int dev) {
+std::vector<uint8_t> make_key(const Args& a, int dev, int grid_share) {
   std::vector<uint8_t> key;
   put(key, dev);
+  put(key, grid_share);
   put(key, a.batch);
   put(key, a.s);
   put(key, a.q);
@@ -132,8 +148,9 @@ std::vector<uint8_t> make_key(const Args& a, int dev) {
 }
 
 // The fork/join itself: problems on branch streams, joined back to `st`.
-int enqueue(const Args& a, Pool& p, size_t per_branch, cudaStream_t st) {
+int enqueue(const Args& a, Pool& p, size_t per_branch, int grid_share, cudaStream_t st) {
   const int nb = branches_for(a.batch);
+  GridShare share(grid_share);
   if (cudaEventRecord(p.fork, st) != cudaSuccess) return SHG_ERR_CUDA;
   for (int b = 0; b < nb; ++b)
     if (cudaStreamWaitEvent(p.s[b], p.fork, 0) != cudaSuccess) return SHG_ERR_CUDA;
@@ -207,9 +224,10 @@ extern "C" int shg_rsvd_batched(int batch, const int64_t* m, const int64_t* n, c
   if ((rc = pool_for_device(&p, &dev)) != SHG_OK) return rc;
   cudaStreamCaptureStatus cap = cudaStreamCaptureStatusNone;
   if (cudaStreamIsCapturing(st, &cap) != cudaSuccess) return SHG_ERR_CUDA;
-  if (!use_graph || cap != cudaStreamCaptureStatusNone) return enqueue(a, *p, per, st);
+  const int grid_share = batched_grid_sms();
+  if (!use_graph || cap != cudaStreamCaptureStatusNone) return enqueue(a, *p, per, grid_share, st);
 
-  std::vector<uint8_t> key = make_key(a, dev);
+  std::vector<uint8_t> key = make_key(a, dev, grid_share);
   for (GraphEntry& e : g_graphs) {
     if (e.dev == dev && e.key == key) {
       e.last_use = ++g_tick;
@@ -220,7 +238,7 @@ extern "C" int shg_rsvd_batched(int batch, const int64_t* m, const int64_t* n, c
   // stream may be the legacy default stream, which cannot be captured); the
   // graph launch then orders it after the caller's earlier work
   if (cudaStreamBeginCapture(p->capture, cudaStreamCaptureModeRelaxed) != cudaSuccess) return SHG_ERR_CUDA;
-  rc = enqueue(a, *p, per, p->capture);
+  rc = enqueue(a, *p, per, grid_share, p->capture);
   cudaGraph_t graph = nullptr;
   const cudaError_t end = cudaStreamEndCapture(p->capture, &graph);
   if (rc != SHG_OK) {

@@ -61,6 +61,21 @@ int simt_gemm(int64_t M, int64_t N, int64_t K, const float* A, int64_t lda, int 
               int64_t stride_a, int64_t stride_b, int64_t stride_c, cudaStream_t stream);
 
 int sm_count();
+// SMs that a launch sized for the whole GPU spreads its grid over: all of
+// them, or the share that a GridShare in scope on the calling host thread
+// sets (the batched path, where many small problems run at once and each
+// problem's launches leave room for the others').
+int grid_sms();
+class GridShare {
+ public:
+  explicit GridShare(int sms);  // sms <= 0: the whole GPU
+  ~GridShare();
+  GridShare(const GridShare&) = delete;
+  GridShare& operator=(const GridShare&) = delete;
+
+ private:
+  int prev_;
+};
 int ceil_div_i(int64_t a, int64_t b);
 inline int cuda_status(cudaError_t e) { return e == cudaSuccess ? SHG_OK : SHG_ERR_CUDA; }
 

@@ -1072,7 +1072,8 @@ int gram_f64(int64_t m, int64_t k, const float* X, int64_t ldx, double* G, cudaS
   if (cudaMemsetAsync(G, 0, k * k * sizeof(double), st) != cudaSuccess) return SHG_ERR_CUDA;
   const int t = static_cast<int>((k + 31) / 32);
   const long long tiles = static_cast<long long>(t) * (t + 1) / 2;
-  const int sms = sm_count();
+  const int sms = grid_sms();
+  if (sms <= 0) return SHG_ERR_CUDA;
   // enough row chunks that about four CTAs per SM share the work
   long long chunks = (4ll * sms + tiles - 1) / tiles;
   long long rows = (m + chunks - 1) / chunks;

@@ -953,12 +953,13 @@ int tc_gemm_impl(int amaj, int bmode, int pieces, int64_t M, int64_t N, int64_t 
   if (bmode != B_SPLIT_PRE) tb2 = tb;  // unused by the other instances
 
   // stream-K grid: at most one CTA per SM, at least one unit per CTA
-  const int sms = sm_count();
+  const int sms = grid_sms();
   if (sms <= 0) return SHG_ERR_CUDA;
   // one CTA group per N tile when there are few N tiles (see cta_range)
   a.groups = (a.n_tiles > 1 && a.n_tiles <= 8 && cfg.groups != 0) ? a.n_tiles : 1;
   const long long per_group = a.units / a.groups;
-  const int grid = static_cast<int>(std::min<long long>(sms / a.groups, per_group)) * a.groups;
+  const long long ctas_per_group = std::max(1, sms / a.groups);
+  const int grid = static_cast<int>(std::min<long long>(ctas_per_group, per_group)) * a.groups;
   const int per_cta = grid / a.groups;
   bool split = false;
   for (int c = 1; c < per_cta && !split; ++c)

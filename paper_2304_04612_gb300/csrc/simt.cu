@@ -132,7 +132,7 @@ int simt_gemm(int64_t M, int64_t N, int64_t K, const float* A, int64_t lda, int 
   int splits = 1;
   if (batch == 1) {
     const long long tiles = static_cast<long long>(gx) * gy;
-    const long long want = 4ll * sm_count();
+    const long long want = 4ll * grid_sms();
     while (tiles * splits < want && K / (splits * 2) >= 256) splits *= 2;
   }
   const int kc = static_cast<int>(((K + splits - 1) / splits + BK - 1) / BK * BK);
