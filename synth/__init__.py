@@ -24,9 +24,12 @@ uniform(m, n, seed, lo, hi) i.i.d. U[lo, hi) FP32 (the SHGEMM accuracy inputs
 tucker(dims, core, seed, noise_std)
                            core N(0,1), factors Haar, plus i.i.d. N(0,
                            noise_std^2) noise; the RP-HOSVD test tensor.
-batch_specs(count, seed)   (m, n, r, rank) of a batch of uneven matrices.
-sketch_family(...)         matrices U_i diag(sigma) (V0 R_i)^T + E for the
-                           learned sketch.
+hosvd_omegas(dims, J, seed) one FP16 Gaussian per mode of a 3-way tensor.
+batch_specs(count, seed)   (m, n, rate, rank, seed) of a batch of uneven
+                           matrices; batch_matrix(spec) builds one of them.
+sketch_basis(n, r, seed), sketch_matrix(V0, m, sigma, theta_max, noise_rel, seed)
+                           matrices U diag(sigma) (V0 cos T + W sin T)^T + E of
+                           the learned-sketch family.
 """
 from __future__ import annotations
 
