@@ -14,11 +14,16 @@ shg_sparse_sign_f16  sparse {-1, 0, +1} test matrix (Sec. 3.4), same Philox stre
 shgemm_project     Y = op(A) Omega by SHGEMM (or the BF16 / FP32 SIMT variants)
 shg_gemm_split3    FP32-accurate op(A) B of two FP32 matrices (TCEC split)
 shg_sgemm          plain FP32 SIMT GEMM (the single-precision baseline)
+shg_gram           G = X^T X in FP64 (compensated FP32 sums), the CholeskyQR Gram step
 shg_cholqr2        CholeskyQR2 orthonormalisation (in place)
 shg_cholqr2_static the same on the library's static scratch (allocates nothing)
 shg_rsvd           randomized SVD (Algorithm 1, power scheme of Sec. 2.1)
 shg_rp_hosvd       random-projection HOSVD of a 3-way tensor (Algorithm 2)
 shg_rsvd_batched   many uneven randomized SVDs at once (concurrent branches, CUDA graph)
+shg_autotune_project, shg_autotune_lookup, shg_autotune_clear, shg_rsvd_batched_autotune
+                   launch configuration of the tensor-core projection per shape class
+rsvd_workspace_size, rp_hosvd_workspace_size, rsvd_batched_workspace_size
+                   workspace bytes of the factorizations (caller-allocated)
 shg_alpha_y_f16    variance of an FP16-rounded N(0,1) value (alpha_Y, Sec. 3.2)
 shg_round_f16      RN_fp16 of an FP32 matrix
 shg_residual_estimate   a-posteriori range-finder residual with FP16 probes (Thms. 1, 3)
