@@ -20,7 +20,7 @@ int sm_count() {
   return n;
 }
 
-thread_local int g_grid_share = 0;
+static thread_local int g_grid_share = 0;  // SMs of the current GridShare (0: none)
 
 int grid_sms() {
   const int n = sm_count();
