@@ -39,3 +39,10 @@ def test_peaks_and_traffic_gate():
     for k, b in bench.TRAFFIC["bytes_per_launch"].items():
         alg = 4.0 * M * N + 2.0 * N * int(k) + 4.0 * M * int(k)
         assert 0.99 * alg <= b <= 1.1 * alg          # within 10 % of the algorithmic bytes
+
+
+def test_clock_sampler_without_nvidia_smi(monkeypatch):
+    monkeypatch.setenv("PATH", "/nonexistent")
+    cs = bench.ClockSampler(0)
+    cs.start()
+    assert cs.stop()["reasons"] == ["nvidia-smi unavailable"]
