@@ -174,9 +174,8 @@ int shgemm_project(int64_t m, int64_t n, int64_t k, const float* A, int64_t lda,
                      d_flags, st);
     case SHG_SPLIT_BF16X3:
     case SHG_SPLIT_BF16X2:
-      if (trans_a) return SHG_ERR_UNSUPPORTED;
-      return tc_gemm(A_KMAJ, B_BF16, variant == SHG_SPLIT_BF16X3 ? 3 : 2, m, k, n, 1, A, lda, 0, omega, ldo, Y,
-                     ldy, 0, d_flags, st);
+      return tc_gemm(trans_a ? A_MNMAJ : A_KMAJ, B_BF16, variant == SHG_SPLIT_BF16X3 ? 3 : 2, m, k, n, 1, A, lda,
+                     0, omega, ldo, Y, ldy, 0, d_flags, st);
     case SHG_FP32_SIMT:
       return simt_gemm(m, k, n, A, lda, trans_a, omega, ldo, 1, Y, ldy, 0, 1, 0, 0, 0, st);
     default:
@@ -192,7 +191,7 @@ static bool tc_layout(int variant, int trans_a, int* amaj, int* bmode, int* piec
     *pieces = 2;
     return true;
   }
-  if ((variant == SHG_SPLIT_BF16X3 || variant == SHG_SPLIT_BF16X2) && !trans_a) {
+  if (variant == SHG_SPLIT_BF16X3 || variant == SHG_SPLIT_BF16X2) {
     *bmode = B_BF16;
     *pieces = variant == SHG_SPLIT_BF16X3 ? 3 : 2;
     return true;

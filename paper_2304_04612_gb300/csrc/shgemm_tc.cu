@@ -869,7 +869,7 @@ int tc_gemm_impl(int amaj, int bmode, int pieces, int64_t M, int64_t N, int64_t 
   if ((bmode == B_SPLIT || bmode == B_SPLIT_PRE) && pieces != 2) return SHG_ERR_INVALID_ARG;
   if (bmode == B_SPLIT_PRE && (!B_lo || (reinterpret_cast<uintptr_t>(B_lo) & 15))) return SHG_ERR_INVALID_ARG;
   if (bmode == B_F16 && pieces != 2) return SHG_ERR_INVALID_ARG;
-  if (bmode == B_BF16 && (pieces < 2 || pieces > 3 || amaj != A_KMAJ)) return SHG_ERR_UNSUPPORTED;
+  if (bmode == B_BF16 && (pieces < 2 || pieces > 3)) return SHG_ERR_UNSUPPORTED;
   const size_t bsz = (bmode == B_SPLIT) ? 4 : 2;
   if ((reinterpret_cast<uintptr_t>(A) & 15) || (reinterpret_cast<uintptr_t>(B) & 15)) return SHG_ERR_INVALID_ARG;
   if ((lda * 4) % 16 || (ldb * bsz) % 16 || (P > 1 && (p_stride * 4) % 16)) return SHG_ERR_INVALID_ARG;
@@ -977,6 +977,8 @@ int tc_gemm_impl(int amaj, int bmode, int pieces, int64_t M, int64_t N, int64_t 
     return launch<A_KMAJ, B_SPLIT, 2>(ta, tb, tb2, a, grid, smem, stream);
   }
   if (bmode == B_F16) return launch<A_MNMAJ, B_F16, 2>(ta, tb, tb2, a, grid, smem, stream);
+  if (bmode == B_BF16 && pieces == 2) return launch<A_MNMAJ, B_BF16, 2>(ta, tb, tb2, a, grid, smem, stream);
+  if (bmode == B_BF16 && pieces == 3) return launch<A_MNMAJ, B_BF16, 3>(ta, tb, tb2, a, grid, smem, stream);
   if (bmode == B_SPLIT) return launch<A_MNMAJ, B_SPLIT, 2>(ta, tb, tb2, a, grid, smem, stream);
   if (bmode == B_SPLIT_PRE) return launch<A_MNMAJ, B_SPLIT_PRE, 2>(ta, tb, tb2, a, grid, smem, stream);
   return SHG_ERR_UNSUPPORTED;

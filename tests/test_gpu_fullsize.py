@@ -92,7 +92,12 @@ def test_batched_256_sampled_problems(shg):
     s, q, seed = 16, 1, 4
     Us, Ss, Vs = shg.shg_rsvd_batched(As, ranks, s, q, omegas=None, seed=seed, use_graph=True)
     big = int(np.argmax([A.shape[0] * A.shape[1] for A in As]))
-    pick = [big] + list(np.random.default_rng(5).choice(256, size=2, replace=False))
+    # the worst-conditioned sketches: sigma_1 / sigma_k = 2^(k / rate) is
+    # largest for k = 144 at the fastest decay (about 2^18), where the
+    # compensated-FP32 Gram matrix of CholeskyQR is under the most strain
+    cond_log2 = [(r + s) / sp["rate"] for r, sp in zip(ranks, specs)]
+    worst = [int(i) for i in np.argsort(cond_log2)[::-1][:2]]
+    pick = [big] + worst + list(np.random.default_rng(5).choice(256, size=2, replace=False))
     for i in pick:
         A = As[i].cpu().numpy()
         n, k = A.shape[1], ranks[i] + s

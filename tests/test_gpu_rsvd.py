@@ -35,6 +35,32 @@ def residual(A, U, S, V):
     return np.linalg.norm(A - (U.astype(np.float64) * S.astype(np.float64)) @ V.astype(np.float64).T) / np.linalg.norm(A)
 
 
+def check_vectors(U, V, ref, eps=1e-5):
+    """Singular vectors against the oracle's (same A, same Omega), up to the
+    sign each pair (u_i, v_i) may take.  Wedin's theorem bounds the angle
+    between a computed and an exact singular vector pair by ||E|| / delta_i,
+    delta_i the distance of sigma_i to the other singular values of B; with
+    the backward error ||E|| <= 1e-6 ||A|| of the FP32 pipeline (the level
+    at which the singular values agree) and a factor 10 of slack, each
+    vector is within eps sigma_1 / delta_i of the oracle's (eps = 1e-5).
+    The pair's sign is unique: u_i and v_i must flip together."""
+    S_all = np.asarray(ref["S_all"], dtype=np.float64)
+    U = U.astype(np.float64)
+    V = V.astype(np.float64)
+    p = U.shape[1]
+    for i in range(p):
+        gaps = [S_all[i] - S_all[i + 1]] if i + 1 < len(S_all) else []
+        if i > 0:
+            gaps.append(S_all[i - 1] - S_all[i])
+        tol = min(1.0, eps * S_all[0] / min(gaps))
+        su = np.sign(U[:, i] @ ref["U"][:, i])
+        sv = np.sign(V[:, i] @ ref["V"][:, i])
+        assert su == sv, (i, su, sv)
+        eu = np.linalg.norm(su * U[:, i] - ref["U"][:, i])
+        ev = np.linalg.norm(sv * V[:, i] - ref["V"][:, i])
+        assert eu <= tol and ev <= tol, (i, eu, ev, tol)
+
+
 def test_cholqr2_orthonormal_and_matches_householder(shg):
     rng = np.random.default_rng(0)
     m, k = 3000, 72
@@ -72,9 +98,10 @@ def test_rsvd_planted_1024(shg, variant):
     # basis: perturbation bound cond(Y) * ||dY|| / ||Y|| with ||dY||/||Y|| <= 1e-5
     condY = np.linalg.cond(ref["Y"])
     assert np.linalg.norm(Q64 - ref["Q"]) <= 10 * condY * 1e-6 * np.sqrt(64)
-    # U, V orthonormal columns
+    # U, V orthonormal columns, and the oracle's vectors
     assert np.linalg.norm(U.T.astype(np.float64) @ U - np.eye(32)) < 1e-4
     assert np.linalg.norm(V.T.astype(np.float64) @ V - np.eye(32)) < 1e-4
+    check_vectors(U, V, ref)
 
 
 def test_rsvd_shgemm_no_worse_than_fp32(shg):
@@ -99,6 +126,7 @@ def test_rsvd_shapes_and_power_scheme(shg, m, n, rank, s, q):
     assert rel_s.max() <= 1e-5, rel_s.max()
     r_p = residual(A, U, S, V)
     assert abs(r_p - ref["r_p"]) <= 0.01 * ref["r_p"]
+    check_vectors(U, V, ref)
 
 
 def test_rsvd_bf16_variant(shg):
@@ -157,19 +185,49 @@ def test_rsvd_large_k_grid_eigensolver(shg):
     r_p = residual(A, U, S, V)
     assert abs(r_p - ref["r_p"]) <= 0.01 * ref["r_p"], (r_p, ref["r_p"])
     assert np.linalg.norm(U.T.astype(np.float64) @ U - np.eye(rank)) < 1e-4
+    check_vectors(U, V, ref)
 
 
 def test_rsvd_k_beyond_rotation_log(shg):
     """k = 296 is beyond the size whose rotations the eigensolver logs: the
-    grid solver then rotates V in every round itself.  Same tolerances."""
+    grid solver then rotates V in every round itself.  Same tolerances, on
+    all 280 singular values and vectors."""
     m, n, rank, s = 900, 800, 280, 16
     A = planted_svd(m, n, sigma_exp(min(m, n), 64.0), seed=12)
     Om = omega_f16(n, rank + s, seed=13)
     U, S, V = shg.shg_rsvd(dev(A), dev(Om), rank=rank, oversampling=s)
     U, S, V = (t.cpu().numpy() for t in (U, S, V))
     ref = OR.rsvd(A, Om, p=rank)
-    lead = slice(0, 64)
     rel_s = np.abs(S.astype(np.float64) - ref["S"]) / ref["S"]
-    assert rel_s[lead].max() <= 1e-5, rel_s[lead].max()
+    assert rel_s.max() <= 1e-5, (int(rel_s.argmax()), rel_s.max())
     r_p = residual(A, U, S, V)
     assert abs(r_p - ref["r_p"]) <= 0.01 * ref["r_p"], (r_p, ref["r_p"])
+    check_vectors(U, V, ref)
+
+
+@pytest.mark.parametrize("m,n,rank,s,rate", [
+    (700, 600, 17, 16, 8.0),      # k = 33: one-CTA Cholesky, one-CTA Jacobi
+    (900, 700, 129, 16, 48.0),    # k = 145: panel Cholesky (k > 113), one-CTA Jacobi (k <= 158)
+    (900, 800, 145, 16, 48.0),    # k = 161: grid Jacobi, V from the rotation log
+    (1000, 900, 281, 16, 96.0),   # k = 297: grid Jacobi rotating V in every round
+])
+def test_rsvd_odd_k(shg, m, n, rank, s, rate):
+    """An odd k = rank + s reaches every k x k kernel (Cholesky, eigensolver,
+    V from the rotation log, Rayleigh quotients, selection) padded to an even
+    size with a zero row and column; all p singular values and vectors
+    against the oracle, the rank-p residual within 1 %."""
+    A = planted_svd(m, n, sigma_exp(min(m, n), rate), seed=20 + rank)
+    Om = omega_f16(n, rank + s, seed=21 + rank)
+    U, S, V, Q = shg.shg_rsvd(dev(A), dev(Om), rank=rank, oversampling=s, want_q=True)
+    U, S, V, Q = (t.cpu().numpy() for t in (U, S, V, Q))
+    ref = OR.rsvd(A, Om, p=rank)
+    rel_s = np.abs(S.astype(np.float64) - ref["S"]) / ref["S"]
+    assert rel_s.max() <= 1e-5, (int(rel_s.argmax()), rel_s.max())
+    r_p = residual(A, U, S, V)
+    assert abs(r_p - ref["r_p"]) <= 0.01 * ref["r_p"], (r_p, ref["r_p"])
+    k = rank + s
+    Q64 = Q.astype(np.float64)
+    assert np.linalg.norm(Q64.T @ Q64 - np.eye(k)) <= 1e-5
+    condY = np.linalg.cond(ref["Y"])
+    assert np.linalg.norm(Q64 - ref["Q"]) <= 10 * condY * 1e-6 * np.sqrt(k)
+    check_vectors(U, V, ref)

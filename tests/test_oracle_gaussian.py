@@ -101,3 +101,41 @@ def test_gaussian_stream_layout_and_offset():
     assert np.array_equal(a[12:24], b)
     c = G.gaussian_f64(seed=10, offset=0, rows=8, cols=6).ravel()
     assert not np.allclose(a, c)
+
+
+def test_box_muller_inverse_map():
+    # Box-Muller maps (u1, u2) to polar coordinates: radius^2 = -2 ln u1 and
+    # angle = 2 pi u2.  Invert the output with exp and atan2 (not the
+    # forward formula) and recover the inputs: a swapped cos / sin, a
+    # missing factor 2 or a wrong logarithm changes them.
+    rng = np.random.default_rng(3)
+    u1 = rng.uniform(1e-9, 1.0, size=20000)
+    u2 = rng.uniform(0.0, 1.0, size=20000)
+    z0, z1 = G.box_muller(u1, u2)
+    assert np.allclose(np.exp(-(z0 * z0 + z1 * z1) / 2.0), u1, rtol=1e-12, atol=0)
+    ang = np.mod(np.arctan2(z1, z0) / (2.0 * np.pi), 1.0)
+    d = np.abs(ang - u2)
+    assert np.all(np.minimum(d, 1.0 - d) < 1e-12)
+    # fixed points: u2 = 0 puts the whole radius on z0, u2 = 1/4 on z1
+    r = np.sqrt(-2.0 * np.log(0.25))
+    a, b = G.box_muller(np.array([0.25]), np.array([0.0]))
+    assert a[0] == pytest.approx(r, rel=1e-15) and abs(b[0]) < 1e-15
+    a, b = G.box_muller(np.array([0.25]), np.array([0.25]))
+    assert abs(a[0]) < 1e-15 and b[0] == pytest.approx(r, rel=1e-15)
+
+
+def test_gaussian_stream_quantiles():
+    # empirical quantiles of 10^6 draws of the stream against the normal
+    # quantile function (scipy's ndtri, independent of the Box-Muller code);
+    # the standard error of the q-quantile is sqrt(q (1 - q) / n) / phi(x_q)
+    from scipy.special import ndtri
+    z = np.sort(G.gaussian_f64(seed=77, offset=0, rows=1000, cols=1000).ravel())
+    n = z.size
+    for q in (0.001, 0.01, 0.1, 0.25, 0.5, 0.75, 0.9, 0.99, 0.999):
+        xq = float(ndtri(q))
+        se = np.sqrt(q * (1 - q) / n) / (np.exp(-xq * xq / 2) / np.sqrt(2 * np.pi))
+        assert abs(z[int(q * n)] - xq) < 5 * se, (q, z[int(q * n)], xq, se)
+    # both outputs of a pair are standard normal and uncorrelated
+    zz = G.gaussian_f64(seed=78, offset=0, rows=250000, cols=4)
+    c = np.corrcoef(zz[:, 0], zz[:, 1])[0, 1]
+    assert abs(c) < 5 / np.sqrt(zz.shape[0])

@@ -96,3 +96,22 @@ def test_fp16_basis_reading_is_close():
     b = R.rsvd(A, Om, p=6, q=1, fp16_basis=True)
     assert abs(a["r_p"] - b["r_p"]) < 0.01 * a["r_p"]
     assert np.allclose(a["S"], b["S"], rtol=1e-3)
+
+
+def test_canonical_signs_hand_built():
+    # column 0: largest |.| is -0.5 (row 1) -> flipped; column 1: largest is
+    # +0.9 (row 0) -> kept; column 2: largest is -0.7 -> flipped.  V's
+    # columns flip with U's, so U diag(s) V^T is unchanged.
+    U = np.array([[0.1, 0.9, 0.2], [-0.5, 0.3, -0.7], [0.2, -0.1, 0.1]])
+    V = np.array([[1.0, 2.0, 3.0], [-4.0, 5.0, -6.0]])
+    Uc, Vc = R.canonical_signs(U, V)
+    assert np.array_equal(Uc, U * np.array([-1.0, 1.0, -1.0]))
+    assert np.array_equal(Vc, V * np.array([-1.0, 1.0, -1.0]))
+    S = np.array([3.0, 2.0, 1.0])
+    assert np.allclose((Uc * S) @ Vc.T, (U * S) @ V.T, rtol=0, atol=0)
+    # already canonical columns are left alone; V may be omitted
+    Uc2, none = R.canonical_signs(Uc)
+    assert none is None and np.array_equal(Uc2, Uc)
+    # a zero column keeps its sign (no NaN from sign(0))
+    Z, _ = R.canonical_signs(np.zeros((3, 1)))
+    assert np.array_equal(Z, np.zeros((3, 1)))

@@ -20,6 +20,22 @@ def test_project_exact_integer_brute_force():
     assert np.array_equal(hi, A.astype(np.float64)) and not lo.any()
 
 
+def test_project_exact_t_integer_brute_force():
+    # the transposed projection A^T B (power scheme, TN products) on a
+    # non-square integer case: C[i, j] = sum_r A[r, i] B[r, j] with Python
+    # integers; a transposed operand or a swapped index gives another matrix
+    rng = np.random.default_rng(1)
+    A = rng.integers(-40, 40, size=(9, 5)).astype(np.float32)     # n x m, contracted over n
+    B = rng.integers(-30, 30, size=(9, 3)).astype(np.float16)     # n x k
+    C = S.project_exact_t(A, B)
+    assert C.shape == (5, 3)
+    ref = [[sum(int(A[r, i]) * int(B[r, j]) for r in range(9)) for j in range(3)] for i in range(5)]
+    assert np.array_equal(C, np.array(ref, dtype=np.float64))
+    # FP32 values that are not integers are taken exactly (24-bit significands)
+    a = np.float32(1.0 + 2.0 ** -23)
+    assert S.project_exact_t(np.array([[a]], np.float32), np.array([[3.0]]))[0, 0] == 3.0 * (1.0 + 2.0 ** -23)
+
+
 def test_project_exact_uses_fp16_bits():
     W = omega_f16(64, 5, 1)
     A = uniform(7, 64, 2)
