@@ -61,6 +61,35 @@ typedef enum shg_variant {
   SHG_FP32_SIMT = 3     /* plain FP32 SIMT SGEMM with FP16 Omega widened exactly to FP32 (the single-precision baseline) */
 } shg_variant;
 
+/*
+ * Diagnostics of one randomized SVD (shg_rsvd with a non-NULL report).
+ * Phases of Algorithm 1 (Sec. 2.2) whose device time goes to phase_ms:
+ */
+#define SHG_PHASE_OMEGA    0  /* Omega generated from the seed (about 0 when the caller passes Omega) */
+#define SHG_PHASE_PROJECT  1  /* Y = A Omega */
+#define SHG_PHASE_ORTH     2  /* Q = orth(Y) by CholeskyQR2 */
+#define SHG_PHASE_POWER    3  /* the power scheme of Sec. 2.1 (about 0 when power_iters = 0) */
+#define SHG_PHASE_B        4  /* B = Q^T A */
+#define SHG_PHASE_SVD      5  /* small SVD of B (Gram matrix, eigensolver, Rayleigh quotients) */
+#define SHG_PHASE_LIFT     6  /* U = Q U', V = B^T U' Sigma^-1 */
+#define SHG_PHASE_ESTIMATE 7  /* the a-posteriori residual estimate below */
+#define SHG_NUM_PHASES     8
+#define SHG_REPORT_PROBES  8  /* FP16 Gaussian probes of the residual estimate */
+
+typedef struct shg_report {
+  int32_t flags;        /* *d_flags after the call (SHG_FLAG_* bits) */
+  int32_t status;       /* shg_flags_status(flags) */
+  double min_pivot;     /* smallest Cholesky pivot ratio R_jj^2 / G_jj over every CholeskyQR2
+                           factorisation of the call: the squared sine of the angle between a
+                           column and the span of the columns before it (1: orthogonal columns;
+                           near 0: close to breakdown; the first pass of the basis sees about
+                           1 / cond(Y)^2) */
+  double est_residual;  /* estimate of ||A - Q Q^T A||_F / ||A||_F from SHG_REPORT_PROBES FP16
+                           Gaussian probes (Theorems 1 and 3), -1 when A's alignment does not
+                           allow the tensor-core product of the estimate */
+  float phase_ms[SHG_NUM_PHASES]; /* CUDA-event time between the phase boundaries */
+} shg_report;
+
 /* Human-readable name of a shg_status value. Never NULL. */
 const char* shg_status_string(int status);
 
@@ -99,16 +128,19 @@ int shg_sparse_sign_f16(uint64_t seed, uint64_t offset, int64_t rows, int64_t co
 
 /*
  * A2-A4. Random projection Y = op(A) * Omega (Eq. rp-vec) by SHGEMM
- * (Sec. 4.1, Eqs. shgemm-1..3): A is split in shared memory into
- * hi = RN_fp16(a) and lo = RN_fp16((a - hi) * 2^11), both multiplied with the
- * FP16 Omega on tcgen05 tensor cores into FP32 TMEM accumulators, and
- * recombined as Y = acc_hi + 2^-11 acc_lo in FP32.
+ * (Sec. 4.1, Eqs. shgemm-1..3): each FP32 tile of A, staged by TMA in shared
+ * memory, is split by SIMT warps into hi = RN_fp16(a) and
+ * lo = RN_fp16((a - hi) * 2^11), written to tensor memory (the A operand of
+ * the MMA); both are multiplied with the FP16 Omega on tcgen05 tensor cores
+ * into FP32 TMEM accumulators (the hi product drained round-to-nearest into
+ * an FP32 register sum every few K blocks, Sec. 4.3), and recombined as
+ * Y = acc_hi + 2^-11 acc_lo in FP32.
  *
  *   trans_a = 0: A is m x n (lda >= n), Y = A * Omega.
  *   trans_a = 1: A is n x m (lda >= m), Y = A^T * Omega.
  *   Omega: n x k (ldo >= k), FP16 bits (BF16 bits for SHG_SPLIT_BF16X*).
  *   Y: m x k FP32 (ldy >= k), overwritten.
- * variant: shg_variant.  SHG_SPLIT_BF16X* support trans_a = 0 only.
+ * variant: shg_variant (every variant takes trans_a = 0 or 1).
  * Device flags: SHG_FLAG_RANGE when some |a| >= 65520 under SHG_SPLIT_F16
  * (its hi piece overflows to infinity; the kernel detects the non-finite
  * output row, so a NaN or infinite input raises the flag as well).
@@ -202,9 +234,11 @@ int shg_gram(int64_t m, int64_t k, const float* X, int64_t ldx, double* G, void*
 /*
  * CholeskyQR2 (the orthonormal basis of Algorithms 1 and 2):
  * twice { G = X^T X (compensated FP32 sums, FP64 result, as shg_gram),
- * G = R^T R (FP64 Cholesky),
- * X <- X R^-1 }.  X: m x k FP32 (ldx >= k), overwritten by Q with
- * Q^T Q = I and X_in = Q R, diag(R) > 0.  k <= m, k <= 1024.
+ * G = R^T R (Cholesky elimination in double-float arithmetic, pairs of FP32
+ * values with about 44 significant bits, on the power-of-4-scaled FP64 Gram
+ * matrix), X <- X R^-1 (R^-1 in FP32) }.  X: m x k FP32 (ldx >= k),
+ * overwritten by Q with Q^T Q = I and X_in = Q R, diag(R) > 0.
+ * k <= m < 2^31, k <= 1024.
  * Device flags: SHG_FLAG_NOT_SPD on a non-positive pivot.
  */
 int shg_cholqr2_workspace_size(int64_t m, int64_t k, size_t* bytes);
@@ -223,8 +257,11 @@ int shg_cholqr2(int64_t m, int64_t k, float* X, int64_t ldx,
  *   SHG_ERR_WORKSPACE before any launch.
  *   d_flags: a device word that must be zero on entry (as for shg_cholqr2),
  *   or NULL, in which case a word inside the static scratch is cleared on
- *   the stream and the device flags are not reported.  Everything else the
- *   call needs zeroed it clears itself on the stream.
+ *   the stream and the device flags are not reported: a Cholesky breakdown
+ *   (a rank-deficient X) then goes undetected, the call returns SHG_OK and X
+ *   holds no orthonormal basis.  Pass a flags word whenever X may be
+ *   rank-deficient.  Everything else the call needs zeroed it clears itself
+ *   on the stream.
  *   The scratch address is resolved on the first call on each device, with
  *   that device current: make that first call before any stream capture on
  *   the device begins.
@@ -238,35 +275,70 @@ int shg_cholqr2_static(int64_t m, int64_t k, float* X, int64_t ldx, int32_t* d_f
  * Randomized SVD, Algorithm 1 with the power scheme of Sec. 2.1:
  *   Y = A Omega; Q = orth(Y); q times { Z = orth(A^T fp16(Q)); Q = orth(A fp16(Z)) };
  *   B = Q^T A; U' S V'^T = tSVD(B, rank); U = Q U'.
- * k = rank + oversampling (p-hat of Sec. 2.2), 1 <= rank, k <= min(m, n), k <= 1024.
+ * The problem is stated as in Sec. 2.2: target rank, oversampling s (Eq.
+ * qqta-acc) and power iterations q.
+ * k = rank + oversampling (p-hat of Sec. 2.2), 1 <= rank, k <= min(m, n), k <= 1024,
+ * m, n < 2^31.
  *   A: m x n FP32 (lda >= n).  omega: n x k FP16 bits (BF16 bits for the BF16
- *   variants), ldo >= k.
+ *   variants), ldo >= k; or NULL: Omega is generated in the workspace as
+ *   shg_gaussian_f16(seed, 0, n, k) generates it (rounded on to BF16 for the
+ *   BF16 variants).  `seed` is also the key of the report's probes.
  *   U: m x rank (ld rank), S: rank (descending), V: n x rank (ld rank), all FP32,
  *   A ~= U diag(S) V^T.  Q_out: NULL or m x k FP32 (ld k), receives Q.
  * variant selects how the projections (Y = A Omega and the power-scheme
  * products) are computed: SHG_SPLIT_F16 / BF16X* (tensor cores, B = Q^T A by
  * the TCEC split) or SHG_FP32_SIMT (every GEMM in FP32 SIMT: the
- * single-precision baseline).  Gram matrices and Cholesky are FP64, the
- * k x k eigensolver of B B^T is FP32 Jacobi refined by FP64 Rayleigh
- * quotients.
+ * single-precision baseline).  Gram matrices are compensated FP32 sums
+ * delivered in FP64, the Cholesky factorisations double-float (see
+ * shg_cholqr2); the k x k eigensolver of B B^T is FP32 Jacobi refined by
+ * FP64 Rayleigh quotients.
+ * report (host pointer, nullable): when given, the call records CUDA events
+ * between the phases of Algorithm 1, tracks the smallest Cholesky pivot
+ * ratio, estimates the residual of the basis Q, synchronises `stream` and
+ * fills *report (see shg_report).  It may not be given while `stream` is
+ * being captured (SHG_ERR_UNSUPPORTED).  Without a report the call stays
+ * asynchronous.
  * Device flags: RANGE, NOT_SPD, TIMEOUT.
  */
 int shg_rsvd_workspace_size(int64_t m, int64_t n, int64_t rank, int64_t oversampling,
                             int power_iters, size_t* bytes);
 int shg_rsvd(int64_t m, int64_t n, int64_t rank, int64_t oversampling, int power_iters,
-             const float* A, int64_t lda, const uint16_t* omega, int64_t ldo,
+             const float* A, int64_t lda, const uint16_t* omega, int64_t ldo, uint64_t seed,
              float* U, float* S, float* V, float* Q_out,
-             void* workspace, size_t ws_bytes, int variant, int32_t* d_flags, void* stream);
+             void* workspace, size_t ws_bytes, int variant, int32_t* d_flags, void* stream,
+             shg_report* report);
 
 /*
- * Random-projection HOSVD, Algorithm 2 (Sec. 5.2), for a 3-way tensor
- * X[i0][i1][i2] (row-major, last index fastest, dims[0..2]).
- *   ranks[i] = J_i (target rank plus oversampling), 1 <= J_i <= dims[i], J_i <= 256.
- *   omegas[i]: FP16 bits, (prod_{j != i} dims[j]) x J_i with leading dimension
- *   omega_lds[i] (omega_lds NULL: J_i; the tensor-core path needs
- *   omega_lds[i] % 8 == 0); its row index is the row-major linear index of the
- *   other modes (i0*I2 + i2 for mode 1).  The tensor-core path also needs
- *   dims[2] % 4 == 0 (TMA row stride).
+ * Mode-i projection of Algorithm 2 (Sec. 5.2), W = X_(i) Omega, for a 3-way
+ * tensor X[i0][i1][i2] (row-major, last index fastest, dims[0..2]) without
+ * forming the unfolding: X_(i) has the mode-i index as its row and the
+ * row-major linear index of the other two modes as its column (i0*I2 + i2
+ * for mode 1).
+ *   mode: 0, 1 or 2.  omega: FP16 bits, (prod_{j != mode} dims[j]) x J,
+ *   ldo >= J.  W: dims[mode] x J FP32 (ldw >= J), overwritten.
+ *   variant: SHG_SPLIT_F16 (SHGEMM: mode 0 as an I0 x (I1 I2) matrix, mode 1
+ *   through a 3-D tensor map, mode 2 as the transposed (I0 I1) x I2 matrix)
+ *   or SHG_FP32_SIMT.  The tensor-core path needs X 16-byte aligned,
+ *   dims[2] % 4 == 0 (and for mode 0 (dims[1] dims[2]) % 4 == 0) and ldo % 8 == 0.
+ * Device flags: RANGE.
+ */
+int shg_mode_project(int ndim, const int64_t* dims, int mode, int64_t J, const float* X,
+                     const uint16_t* omega, int64_t ldo, float* W, int64_t ldw, int variant,
+                     int32_t* d_flags, void* stream);
+
+/*
+ * Random-projection HOSVD, Algorithm 2 (Sec. 5.2), of a 3-way tensor
+ * X[i0][i1][i2] (row-major, last index fastest, dims[0..2]), stated as the
+ * paper states the problem: the target rank of each mode and the
+ * oversampling s; J_i = ranks[i] + s columns are kept per mode (Algorithm 3
+ * pads the ranks the same way).  1 <= ranks[i], J_i <= dims[i], J_i <= 1024.
+ *   omegas: NULL, or per mode an FP16 (prod_{j != i} dims[j]) x J_i test
+ *   matrix (leading dimension omega_lds[i], or J_i when omega_lds is NULL;
+ *   the tensor-core path needs omega_lds[i] % 8 == 0) or NULL; a NULL
+ *   Omega_i is generated in the workspace as shg_gaussian_f16(seed, i * 2^32,
+ *   prod_{j != i} dims[j], J_i) generates it.  Its row index is the row-major
+ *   linear index of the other modes (see shg_mode_project).  The
+ *   tensor-core path also needs dims[2] % 4 == 0 (TMA row stride).
  *   W_i = X_(i) Omega_i; Q_i = CholeskyQR2(W_i) -> factors[i] (dims[i] x J_i, ld J_i).
  *   core (J0 x J1 x J2, row-major) = X x_0 Q_0^T x_1 Q_1^T x_2 Q_2^T.
  * variant: SHG_SPLIT_F16 (SHGEMM projections, TCEC-split first core
@@ -276,10 +348,12 @@ int shg_rsvd(int64_t m, int64_t n, int64_t rank, int64_t oversampling, int power
  * joined back to `stream`; the call stays asynchronous and ordered on
  * `stream`, also under stream capture.
  */
-int shg_rp_hosvd_workspace_size(int ndim, const int64_t* dims, const int64_t* ranks, size_t* bytes);
-int shg_rp_hosvd(int ndim, const int64_t* dims, const int64_t* ranks, const float* X,
-                 const uint16_t* const* omegas, const int64_t* omega_lds, float* core, float* const* factors,
-                 void* workspace, size_t ws_bytes, int variant, int32_t* d_flags, void* stream);
+int shg_rp_hosvd_workspace_size(int ndim, const int64_t* dims, const int64_t* ranks, int64_t oversampling,
+                                size_t* bytes);
+int shg_rp_hosvd(int ndim, const int64_t* dims, const int64_t* ranks, int64_t oversampling, const float* X,
+                 const uint16_t* const* omegas, const int64_t* omega_lds, uint64_t seed, float* core,
+                 float* const* factors, void* workspace, size_t ws_bytes, int variant, int32_t* d_flags,
+                 void* stream);
 
 /*
  * A12. Batched randomized SVD: problem i (0 <= i < batch) is Algorithm 1 on

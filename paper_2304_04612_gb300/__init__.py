@@ -18,6 +18,7 @@ shg_gram           G = X^T X in FP64 (compensated FP32 sums), the CholeskyQR Gra
 shg_cholqr2        CholeskyQR2 orthonormalisation (in place)
 shg_cholqr2_static the same on the library's static scratch (allocates nothing)
 shg_rsvd           randomized SVD (Algorithm 1, power scheme of Sec. 2.1)
+shg_mode_project   mode-i projection W = X_(i) Omega of a 3-way tensor (Algorithm 2)
 shg_rp_hosvd       random-projection HOSVD of a 3-way tensor (Algorithm 2)
 shg_rsvd_batched   many uneven randomized SVDs at once (concurrent branches, CUDA graph)
 shg_autotune_project, shg_autotune_lookup, shg_autotune_clear, shg_rsvd_batched_autotune
@@ -396,17 +397,25 @@ def rsvd_workspace_size(m: int, n: int, rank: int, oversampling: int, power_iter
     return need.value
 
 
-def shg_rsvd(A: torch.Tensor, omega: torch.Tensor, rank: int, oversampling: int, power_iters: int = 0,
+def shg_rsvd(A: torch.Tensor, omega: torch.Tensor | None, rank: int, oversampling: int, power_iters: int = 0,
              variant="f16", want_q: bool = False, workspace: torch.Tensor | None = None,
-             out=None, flags: torch.Tensor | None = None, check: bool = True, stream=None):
-    """Randomized SVD (Algorithm 1).  Returns (U, S, V[, Q]) with A ~= U diag(S) V^T."""
+             out=None, flags: torch.Tensor | None = None, check: bool = True, stream=None, seed: int = 0,
+             report: bool = False):
+    """Randomized SVD (Algorithm 1).  Returns (U, S, V[, Q][, report]) with
+    A ~= U diag(S) V^T.  omega=None generates the test matrix from ``seed``
+    (shg_gaussian_f16(seed, 0, n, k)).  report=True synchronises and adds
+    the shg_report as a dict (phase times of Algorithm 1, smallest Cholesky
+    pivot ratio, a-posteriori residual estimate)."""
     v = _variant(variant)
     lda = _mat(A, "A", (torch.float32,))
-    ldo = _mat(omega, "omega", (torch.bfloat16,) if v in (1, 2) else (torch.float16,))
     m, n = A.shape
     k = rank + oversampling
-    if omega.shape != (n, k):
-        raise ValueError(f"omega must be {n} x {k}")
+    if omega is not None:
+        ldo = _mat(omega, "omega", (torch.bfloat16,) if v in (1, 2) else (torch.float16,))
+        if omega.shape != (n, k):
+            raise ValueError(f"omega must be {n} x {k}")
+    else:
+        ldo = 0
     dev = A.device
     if out is None:
         U = torch.empty(m, rank, dtype=torch.float32, device=dev)
@@ -418,53 +427,92 @@ def shg_rsvd(A: torch.Tensor, omega: torch.Tensor, rank: int, oversampling: int,
     need = rsvd_workspace_size(m, n, rank, oversampling, power_iters)
     ws = workspace if workspace is not None else torch.empty(need, dtype=torch.uint8, device=dev)
     fl = flags if flags is not None else new_flags(dev)
-    _check(_lib.load().shg_rsvd(m, n, rank, oversampling, power_iters, _ptr(A), lda, _ptr(omega), ldo,
+    rep = _lib.Report() if report else None
+    _check(_lib.load().shg_rsvd(m, n, rank, oversampling, power_iters, _ptr(A), lda, _ptr(omega), ldo, seed,
                                 _ptr(U), _ptr(S), _ptr(V), _ptr(Q), _ptr(ws), ws.numel(), v, _ptr(fl),
-                                _stream(stream)), "shg_rsvd")
+                                _stream(stream), ctypes.byref(rep) if rep is not None else None), "shg_rsvd")
     if check:
         check_flags(fl, "shg_rsvd")
-    return (U, S, V, Q) if want_q else (U, S, V)
+    res = (U, S, V, Q) if want_q else (U, S, V)
+    return res + (rep.as_dict(),) if report else res
 
 
-def rp_hosvd_workspace_size(dims, ranks) -> int:
+def rp_hosvd_workspace_size(dims, ranks, oversampling: int = 0) -> int:
     d = (ctypes.c_int64 * 3)(*dims)
     r = (ctypes.c_int64 * 3)(*ranks)
     need = ctypes.c_size_t()
-    _check(_lib.load().shg_rp_hosvd_workspace_size(3, d, r, ctypes.byref(need)), "shg_rp_hosvd_workspace_size")
+    _check(_lib.load().shg_rp_hosvd_workspace_size(3, d, r, oversampling, ctypes.byref(need)),
+           "shg_rp_hosvd_workspace_size")
     return need.value
 
 
+def _omega_rows(dims, i):
+    rows = 1
+    for j, d in enumerate(dims):
+        if j != i:
+            rows *= d
+    return rows
+
+
+def shg_mode_project(X: torch.Tensor, omega: torch.Tensor, mode: int, variant="f16", out: torch.Tensor | None = None,
+                     flags: torch.Tensor | None = None, check: bool = True, stream=None) -> torch.Tensor:
+    """W = X_(mode) @ omega for a contiguous 3-way float32 tensor (the mode
+    projection of Algorithm 2); omega is (prod of the other dims) x J FP16."""
+    if X.dim() != 3 or not X.is_contiguous() or X.dtype != torch.float32 or not X.is_cuda:
+        raise ValueError("X must be a contiguous 3-way float32 CUDA tensor")
+    dims = list(X.shape)
+    ldo = _mat(omega, "omega", (torch.float16,))
+    J = omega.shape[1]
+    if omega.shape[0] != _omega_rows(dims, mode):
+        raise ValueError(f"omega must have {_omega_rows(dims, mode)} rows")
+    if out is None:
+        out = torch.empty(dims[mode], J, dtype=torch.float32, device=X.device)
+    ldw = _mat(out, "out", (torch.float32,))
+    fl = flags if flags is not None else new_flags(X.device)
+    d = (ctypes.c_int64 * 3)(*dims)
+    _check(_lib.load().shg_mode_project(3, d, int(mode), J, _ptr(X), _ptr(omega), ldo, _ptr(out), ldw,
+                                        _variant(variant), _ptr(fl), _stream(stream)), "shg_mode_project")
+    if check:
+        check_flags(fl, "shg_mode_project")
+    return out
+
+
 def shg_rp_hosvd(X: torch.Tensor, omegas, ranks, variant="f16", workspace: torch.Tensor | None = None,
-                 out=None, flags: torch.Tensor | None = None, check: bool = True, stream=None):
-    """RP-HOSVD (Algorithm 2) of a contiguous 3-way float32 tensor.  Returns
-    (core J0 x J1 x J2, [Q_0, Q_1, Q_2])."""
+                 out=None, flags: torch.Tensor | None = None, check: bool = True, stream=None,
+                 oversampling: int = 0, seed: int = 0):
+    """RP-HOSVD (Algorithm 2) of a contiguous 3-way float32 tensor with target
+    ranks r_i and oversampling s (J_i = r_i + s columns per mode).  omegas:
+    None (all generated from ``seed``) or a list of FP16 tensors / None.
+    Returns (core J0 x J1 x J2, [Q_0, Q_1, Q_2])."""
     if X.dim() != 3 or not X.is_contiguous() or X.dtype != torch.float32 or not X.is_cuda:
         raise ValueError("X must be a contiguous 3-way float32 CUDA tensor")
     dims = list(X.shape)
     ranks = [int(r) for r in ranks]
-    for i, om in enumerate(omegas):
-        rows = 1
-        for j, d in enumerate(dims):
-            if j != i:
-                rows *= d
-        if om.dtype != torch.float16 or tuple(om.shape) != (rows, ranks[i]) or om.stride(1) != 1:
-            raise ValueError(f"omega {i} must be a row-major float16 {rows} x {ranks[i]} tensor")
+    J = [r + oversampling for r in ranks]
+    oms = list(omegas) if omegas is not None else [None, None, None]
+    for i, om in enumerate(oms):
+        if om is None:
+            continue
+        rows = _omega_rows(dims, i)
+        if om.dtype != torch.float16 or tuple(om.shape) != (rows, J[i]) or om.stride(1) != 1:
+            raise ValueError(f"omega {i} must be a row-major float16 {rows} x {J[i]} tensor")
     dev = X.device
     if out is None:
-        core = torch.empty(*ranks, dtype=torch.float32, device=dev)
-        facs = [torch.empty(dims[i], ranks[i], dtype=torch.float32, device=dev) for i in range(3)]
+        core = torch.empty(*J, dtype=torch.float32, device=dev)
+        facs = [torch.empty(dims[i], J[i], dtype=torch.float32, device=dev) for i in range(3)]
     else:
         core, facs = out
-    need = rp_hosvd_workspace_size(dims, ranks)
+    need = rp_hosvd_workspace_size(dims, ranks, oversampling)
     ws = workspace if workspace is not None else torch.empty(need, dtype=torch.uint8, device=dev)
     fl = flags if flags is not None else new_flags(dev)
     d = (ctypes.c_int64 * 3)(*dims)
     r = (ctypes.c_int64 * 3)(*ranks)
-    om_ptrs = (ctypes.c_void_p * 3)(*[o.data_ptr() for o in omegas])
-    om_lds = (ctypes.c_int64 * 3)(*[o.stride(0) for o in omegas])
+    om_ptrs = (ctypes.c_void_p * 3)(*[o.data_ptr() if o is not None else 0 for o in oms])
+    om_lds = (ctypes.c_int64 * 3)(*[o.stride(0) if o is not None else 0 for o in oms])
     f_ptrs = (ctypes.c_void_p * 3)(*[f.data_ptr() for f in facs])
-    _check(_lib.load().shg_rp_hosvd(3, d, r, _ptr(X), om_ptrs, om_lds, _ptr(core), f_ptrs, _ptr(ws), ws.numel(),
-                                    _variant(variant), _ptr(fl), _stream(stream)), "shg_rp_hosvd")
+    _check(_lib.load().shg_rp_hosvd(3, d, r, oversampling, _ptr(X), om_ptrs, om_lds, seed, _ptr(core), f_ptrs,
+                                    _ptr(ws), ws.numel(), _variant(variant), _ptr(fl), _stream(stream)),
+           "shg_rp_hosvd")
     if check:
         check_flags(fl, "shg_rp_hosvd")
     return core, facs

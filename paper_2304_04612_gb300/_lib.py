@@ -54,14 +54,29 @@ SIGNATURES = {
     "shg_sketch_loss_grad": (c_int, [c_i64, c_i64, c_i64, c_vp, c_i64, c_vp, c_i64, c_int, c_vp, c_i64, c_vp,
                                      c_vp, c_sz, c_vp, c_vp]),
     "shg_rsvd_workspace_size": (c_int, [c_i64, c_i64, c_i64, c_i64, c_int, ctypes.POINTER(c_sz)]),
-    "shg_rsvd": (c_int, [c_i64, c_i64, c_i64, c_i64, c_int, c_vp, c_i64, c_vp, c_i64, c_vp, c_vp, c_vp,
-                         c_vp, c_vp, c_sz, c_int, c_vp, c_vp]),
-    "shg_rp_hosvd_workspace_size": (c_int, [c_int, ctypes.POINTER(c_i64), ctypes.POINTER(c_i64),
+    "shg_rsvd": (c_int, [c_i64, c_i64, c_i64, c_i64, c_int, c_vp, c_i64, c_vp, c_i64, c_u64, c_vp, c_vp, c_vp,
+                         c_vp, c_vp, c_sz, c_int, c_vp, c_vp, c_vp]),
+    "shg_mode_project": (c_int, [c_int, ctypes.POINTER(c_i64), c_int, c_i64, c_vp, c_vp, c_i64, c_vp, c_i64, c_int,
+                                 c_vp, c_vp]),
+    "shg_rp_hosvd_workspace_size": (c_int, [c_int, ctypes.POINTER(c_i64), ctypes.POINTER(c_i64), c_i64,
                                             ctypes.POINTER(c_sz)]),
-    "shg_rp_hosvd": (c_int, [c_int, ctypes.POINTER(c_i64), ctypes.POINTER(c_i64), c_vp,
-                             ctypes.POINTER(c_vp), ctypes.POINTER(c_i64), c_vp, ctypes.POINTER(c_vp), c_vp, c_sz,
+    "shg_rp_hosvd": (c_int, [c_int, ctypes.POINTER(c_i64), ctypes.POINTER(c_i64), c_i64, c_vp,
+                             c_vp, c_vp, c_u64, c_vp, ctypes.POINTER(c_vp), c_vp, c_sz,
                              c_int, c_vp, c_vp]),
 }
+
+PHASES = ("omega", "project", "orth", "power", "B", "svd", "lift", "estimate")
+
+
+class Report(ctypes.Structure):
+    """struct shg_report of include/shg.h."""
+    _fields_ = [("flags", ctypes.c_int32), ("status", ctypes.c_int32), ("min_pivot", ctypes.c_double),
+                ("est_residual", ctypes.c_double), ("phase_ms", ctypes.c_float * len(PHASES))]
+
+    def as_dict(self) -> dict:
+        return {"flags": self.flags, "status": self.status, "min_pivot": self.min_pivot,
+                "est_residual": self.est_residual,
+                "phase_ms": {name: float(self.phase_ms[i]) for i, name in enumerate(PHASES)}}
 
 _lib = None
 

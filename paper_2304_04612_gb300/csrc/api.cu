@@ -38,9 +38,12 @@ inline int64_t round8(int64_t x) { return (x + 7) / 8 * 8; }
 
 bool tc_variant(int v) { return v == SHG_SPLIT_F16 || v == SHG_SPLIT_BF16X3 || v == SHG_SPLIT_BF16X2; }
 
-// Workspace layout of shg_rsvd.
+constexpr int64_t kReportProbes = SHG_REPORT_PROBES;
+
+// Workspace layout of shg_rsvd (the estimator's pieces and the report
+// scalars are used only when a report is asked for).
 struct RsvdLayout {
-  size_t Y, T, Z, H, Hlo, Bt, small, eig, Vk, lam, Up, Ups, total;
+  size_t Y, T, Z, H, Hlo, Bt, small, eig, Vk, lam, Up, Ups, Om, est, piv, eout, total;
 };
 RsvdLayout rsvd_layout(int64_t m, int64_t n, int64_t k, int64_t rank) {
   const int64_t ldk = round8(k), mx = m > n ? m : n;
@@ -63,6 +66,12 @@ RsvdLayout rsvd_layout(int64_t m, int64_t n, int64_t k, int64_t rank) {
   L.lam = take(2 * k * 8);
   L.Up = take(k * rank * 4);
   L.Ups = take(k * rank * 4);
+  L.Om = take(n * ldk * 2);  // Omega generated from the seed
+  size_t est = 0;
+  shg_residual_estimate_workspace_size(m, n, k, kReportProbes, &est);
+  L.est = take(est);
+  L.piv = take(sizeof(double));
+  L.eout = take(3 * sizeof(double));
   L.total = off;
   return L;
 }
@@ -97,7 +106,7 @@ int mode_pool(ModePool** out) {
 }
 
 struct HosvdLayout {
-  size_t W[3], T[3], T1, T2, small[3], Bhi, Blo, total;
+  size_t W[3], T[3], T1, T2, small[3], Bhi, Blo, Om[3], total;
   int64_t ld[3];
 };
 HosvdLayout hosvd_layout(const int64_t* d, const int64_t* J) {
@@ -122,9 +131,53 @@ HosvdLayout hosvd_layout(const int64_t* d, const int64_t* J) {
   for (int i = 0; i < 3; ++i) L.small[i] = take(cholqr_small_bytes(maxJ));
   L.Bhi = take(d[2] * L.ld[2] * 2);  // Q_2 split into FP16 hi / lo for the first core contraction
   L.Blo = take(d[2] * L.ld[2] * 2);
+  for (int i = 0; i < 3; ++i) L.Om[i] = take(d[0] * d[1] * d[2] / d[i] * L.ld[i] * 2);  // generated Omega_i
   L.total = off;
   return L;
 }
+
+// Mode-i projection of Algorithm 2, W = X_(i) Omega (dims[i] x J, ld ldw),
+// with no unfolding materialised: mode 0 reads X as an I0 x (I1 I2)
+// matrix, mode 1 through a 3-D tensor map (K index (i0, i2), batched over
+// i0 on the SIMT path), mode 2 as the transposed (I0 I1) x I2 matrix.
+int mode_project(int i, const int64_t* d, int64_t J, const float* X, const uint16_t* omega, int64_t ldo, float* W,
+                 int64_t ldw, bool tc, int32_t* d_flags, cudaStream_t st) {
+  const int64_t I0 = d[0], I1 = d[1], I2 = d[2];
+  if (i == 0) {
+    if (tc) return tc_gemm(A_KMAJ, B_F16, 2, I0, J, I1 * I2, 1, X, I1 * I2, 0, omega, ldo, W, ldw, 0, d_flags, st);
+    return simt_gemm(I0, J, I1 * I2, X, I1 * I2, 0, omega, ldo, 1, W, ldw, 0, 1, 0, 0, 0, st);
+  }
+  if (i == 1) {
+    if (tc) return tc_gemm(A_KMAJ, B_F16, 2, I1, J, I2, I0, X, I2, I1 * I2, omega, ldo, W, ldw, 0, d_flags, st);
+    if (cudaMemset2DAsync(W, ldw * 4, 0, J * 4, I1, st) != cudaSuccess) return SHG_ERR_CUDA;
+    return simt_gemm(I1, J, I2, X, I2, 0, omega, ldo, 1, W, ldw, 1, I0, I1 * I2, I2 * ldo, 0, st);
+  }
+  if (tc) return tc_gemm(A_MNMAJ, B_F16, 2, I2, J, I0 * I1, 1, X, I2, 0, omega, ldo, W, ldw, 0, d_flags, st);
+  return simt_gemm(I2, J, I0 * I1, X, I2, 1, omega, ldo, 1, W, ldw, 0, 1, 0, 0, 0, st);
+}
+
+__global__ void fill_f64_kernel(double* p, double v) { *p = v; }
+
+// CUDA events of a report: one per phase boundary, created and destroyed
+// by the call that fills the report.
+struct PhaseEvents {
+  cudaEvent_t e[SHG_NUM_PHASES + 1] = {};
+  bool on = false;
+  int init() {
+    on = true;
+    for (auto& x : e)
+      if (cudaEventCreate(&x) != cudaSuccess) return SHG_ERR_CUDA;
+    return SHG_OK;
+  }
+  int mark(int i, cudaStream_t st) {
+    if (!on) return SHG_OK;
+    return cudaEventRecord(e[i], st) == cudaSuccess ? SHG_OK : SHG_ERR_CUDA;
+  }
+  ~PhaseEvents() {
+    for (auto& x : e)
+      if (x) cudaEventDestroy(x);
+  }
+};
 
 #define SHG_TRY(x)            \
   do {                        \
@@ -153,7 +206,7 @@ const char* shg_status_string(int s) {
   }
 }
 
-int shg_version(void) { return 100; }
+int shg_version(void) { return 200; }
 
 int shg_flags_status(int32_t f) {
   if (f & SHG_FLAG_TIMEOUT) return SHG_ERR_TIMEOUT;
@@ -272,7 +325,8 @@ int shg_gram(int64_t m, int64_t k, const float* X, int64_t ldx, double* G, void*
 }
 
 int shg_cholqr2_workspace_size(int64_t m, int64_t k, size_t* bytes) {
-  if (!bytes || k < 1 || m < k || k > 1024) return SHG_ERR_INVALID_ARG;
+  // the Gram and GEMM kernels index rows with 32-bit integers
+  if (!bytes || k < 1 || m < k || k > 1024 || m >= (1ll << 31)) return SHG_ERR_INVALID_ARG;
   *bytes = align256(static_cast<size_t>(m) * k * 4) + cholqr_small_bytes(k);
   return SHG_OK;
 }
@@ -293,117 +347,78 @@ int shg_rsvd_workspace_size(int64_t m, int64_t n, int64_t rank, int64_t oversamp
                             size_t* bytes) {
   if (!bytes || m < 1 || n < 1 || rank < 1 || oversampling < 0 || power_iters < 0) return SHG_ERR_INVALID_ARG;
   const int64_t k = rank + oversampling;
-  if (k > m || k > n || k > 1024) return SHG_ERR_INVALID_ARG;
+  if (k > m || k > n || k > 1024 || m >= (1ll << 31) || n >= (1ll << 31)) return SHG_ERR_INVALID_ARG;
   *bytes = rsvd_layout(m, n, k, rank).total;
   return SHG_OK;
 }
 
 int shg_rsvd(int64_t m, int64_t n, int64_t rank, int64_t oversampling, int power_iters, const float* A,
-             int64_t lda, const uint16_t* omega, int64_t ldo, float* U, float* S, float* V, float* Q_out,
-             void* ws, size_t ws_bytes, int variant, int32_t* d_flags, void* stream) {
-  size_t need = 0;
-  if (shg_rsvd_workspace_size(m, n, rank, oversampling, power_iters, &need) != SHG_OK) return SHG_ERR_INVALID_ARG;
-  if (!A || !omega || !U || !S || !V || !ws || !d_flags || lda < n) return SHG_ERR_INVALID_ARG;
-  if (variant < SHG_SPLIT_F16 || variant > SHG_FP32_SIMT) return SHG_ERR_INVALID_ARG;
-  const int64_t k = rank + oversampling;
-  if (ldo < k) return SHG_ERR_INVALID_ARG;
-  if (ws_bytes < need) return SHG_ERR_WORKSPACE;
-  cudaStream_t st = static_cast<cudaStream_t>(stream);
-  const RsvdLayout L = rsvd_layout(m, n, k, rank);
-  uint8_t* w = static_cast<uint8_t*>(ws);
-  float* Y = reinterpret_cast<float*>(w + L.Y);
-  float* T = reinterpret_cast<float*>(w + L.T);
-  float* Z = reinterpret_cast<float*>(w + L.Z);
-  uint16_t* H = reinterpret_cast<uint16_t*>(w + L.H);
-  float* Bt = reinterpret_cast<float*>(w + L.Bt);
-  void* small = w + L.small;
-  float* Vk = reinterpret_cast<float*>(w + L.Vk);
-  double* lam = reinterpret_cast<double*>(w + L.lam);
-  float* Up = reinterpret_cast<float*>(w + L.Up);
-  float* Ups = reinterpret_cast<float*>(w + L.Ups);
-  const int64_t ldk = round8(k);
-  const bool tc = tc_variant(variant);
-
-  // projection: Y = A Omega
-  SHG_TRY(shgemm_project(m, n, k, A, lda, 0, omega, ldo, Y, ldk, variant, d_flags, stream));
-  // orthonormal basis: Q = orth(Y)
-  SHG_TRY(cholqr2(m, k, Y, ldk, T, ldk, small, d_flags, st));
-  // power scheme (Sec. 2.1): the FP16-rounded basis is the next test matrix
-  for (int it = 0; it < power_iters; ++it) {
-    if (tc) {
-      SHG_TRY(to_f16(m, k, Y, ldk, H, ldk, st));
-      SHG_TRY(tc_gemm(A_MNMAJ, B_F16, 2, n, k, m, 1, A, lda, 0, H, ldk, Z, ldk, 0, d_flags, st));
-    } else {
-      SHG_TRY(simt_gemm(n, k, m, A, lda, 1, Y, ldk, 0, Z, ldk, 0, 1, 0, 0, 0, st));
-    }
-    SHG_TRY(cholqr2(n, k, Z, ldk, T, ldk, small, d_flags, st));
-    if (tc) {
-      SHG_TRY(to_f16(n, k, Z, ldk, H, ldk, st));
-      SHG_TRY(tc_gemm(A_KMAJ, B_F16, 2, m, k, n, 1, A, lda, 0, H, ldk, Y, ldk, 0, d_flags, st));
-    } else {
-      SHG_TRY(simt_gemm(m, k, n, A, lda, 0, Z, ldk, 0, Y, ldk, 0, 1, 0, 0, 0, st));
-    }
-    SHG_TRY(cholqr2(m, k, Y, ldk, T, ldk, small, d_flags, st));
-  }
-  // B^T = A^T Q (FP32-accurate)
-  if (tc) {
-    // Q split into FP16 hi / lo once (the TCEC B operand), then the TN product
-    uint16_t* Hlo = reinterpret_cast<uint16_t*>(w + L.Hlo);
-    SHG_TRY(split_f16(m, k, Y, ldk, H, Hlo, ldk, d_flags, st));
-    SHG_TRY(tc_gemm(A_MNMAJ, B_SPLIT_PRE, 2, n, k, m, 1, A, lda, 0, H, ldk, Bt, ldk, 0, d_flags, st, nullptr, nullptr,
-                    Hlo));
-  }
-  else
-    SHG_TRY(simt_gemm(n, k, m, A, lda, 1, Y, ldk, 0, Bt, ldk, 0, 1, 0, 0, 0, st));
-  // small SVD of B through the eigendecomposition of B B^T = Bt^T Bt
-  const SmallWs sw = small_ws(small, k);
-  double* G = sw.G;
-  SHG_TRY(gram_f64(n, k, Bt, ldk, G, st));
-  SHG_TRY(jacobi_eig(k, G, Vk, sw.jac, jacobi_log_bytes(k) ? w + L.eig : nullptr, st));
-  SHG_TRY(rayleigh_sort(k, rank, G, Vk, lam, S, Up, Ups, st));
-  // lift: U = Q U'; V = B^T U' Sigma^-1
-  SHG_TRY(simt_gemm(m, rank, k, Y, ldk, 0, Up, rank, 0, U, rank, 0, 1, 0, 0, 0, st));
-  SHG_TRY(simt_gemm(n, rank, k, Bt, ldk, 0, Ups, rank, 0, V, rank, 0, 1, 0, 0, 0, st));
-  if (Q_out) {
-    if (cudaMemcpy2DAsync(Q_out, k * 4, Y, ldk * 4, k * 4, m, cudaMemcpyDeviceToDevice, st) != cudaSuccess)
-      return SHG_ERR_CUDA;
-  }
-  return SHG_OK;
+             int64_t lda, const uint16_t* omega, int64_t ldo, uint64_t seed, float* U, float* S, float* V,
+             float* Q_out, void* ws, size_t ws_bytes, int variant, int32_t* d_flags, void* stream,
+             shg_report* report) {
+  return rsvd_impl(m, n, rank, oversampling, power_iters, A, lda, omega, ldo, seed, 0, U, S, V, Q_out, ws, ws_bytes,
+                   variant, d_flags, static_cast<cudaStream_t>(stream), report);
 }
 
-int shg_rp_hosvd_workspace_size(int ndim, const int64_t* dims, const int64_t* ranks, size_t* bytes) {
-  if (!bytes || !dims || !ranks) return SHG_ERR_INVALID_ARG;
+int shg_mode_project(int ndim, const int64_t* dims, int mode, int64_t J, const float* X, const uint16_t* omega,
+                     int64_t ldo, float* W, int64_t ldw, int variant, int32_t* d_flags, void* stream) {
+  if (!dims || !X || !omega || !W || !d_flags) return SHG_ERR_INVALID_ARG;
   if (ndim != 3) return SHG_ERR_UNSUPPORTED;
   for (int i = 0; i < 3; ++i)
-    if (dims[i] < 1 || ranks[i] < 1 || ranks[i] > dims[i] || ranks[i] > 1024) return SHG_ERR_INVALID_ARG;
-  *bytes = hosvd_layout(dims, ranks).total;
+    if (dims[i] < 1) return SHG_ERR_INVALID_ARG;
+  if (mode < 0 || mode > 2 || J < 1 || ldo < J || ldw < J) return SHG_ERR_INVALID_ARG;
+  if (variant != SHG_SPLIT_F16 && variant != SHG_FP32_SIMT) return SHG_ERR_UNSUPPORTED;
+  return mode_project(mode, dims, J, X, omega, ldo, W, ldw, variant == SHG_SPLIT_F16, d_flags,
+                      static_cast<cudaStream_t>(stream));
+}
+
+static bool hosvd_ranks(int ndim, const int64_t* dims, const int64_t* ranks, int64_t s, int64_t J[3]) {
+  if (!dims || !ranks || ndim != 3 || s < 0) return false;
+  for (int i = 0; i < 3; ++i) {
+    J[i] = ranks[i] + s;
+    if (dims[i] < 1 || ranks[i] < 1 || J[i] > dims[i] || J[i] > 1024) return false;
+  }
+  return true;
+}
+
+int shg_rp_hosvd_workspace_size(int ndim, const int64_t* dims, const int64_t* ranks, int64_t oversampling,
+                                size_t* bytes) {
+  if (!bytes) return SHG_ERR_INVALID_ARG;
+  if (ndim != 3) return SHG_ERR_UNSUPPORTED;
+  int64_t J[3];
+  if (!hosvd_ranks(ndim, dims, ranks, oversampling, J)) return SHG_ERR_INVALID_ARG;
+  *bytes = hosvd_layout(dims, J).total;
   return SHG_OK;
 }
 
-int shg_rp_hosvd(int ndim, const int64_t* dims, const int64_t* ranks, const float* X,
-                 const uint16_t* const* omegas, const int64_t* omega_lds, float* core, float* const* factors,
-                 void* ws, size_t ws_bytes, int variant, int32_t* d_flags, void* stream) {
+int shg_rp_hosvd(int ndim, const int64_t* dims, const int64_t* ranks, int64_t oversampling, const float* X,
+                 const uint16_t* const* omegas, const int64_t* omega_lds, uint64_t seed, float* core,
+                 float* const* factors, void* ws, size_t ws_bytes, int variant, int32_t* d_flags, void* stream) {
   size_t need = 0;
-  const int rc0 = shg_rp_hosvd_workspace_size(ndim, dims, ranks, &need);
+  const int rc0 = shg_rp_hosvd_workspace_size(ndim, dims, ranks, oversampling, &need);
   if (rc0 != SHG_OK) return rc0;
-  if (!X || !omegas || !core || !factors || !ws || !d_flags) return SHG_ERR_INVALID_ARG;
+  if (!X || !core || !factors || !ws || !d_flags) return SHG_ERR_INVALID_ARG;
+  int64_t J[3];
+  hosvd_ranks(ndim, dims, ranks, oversampling, J);
+  const HosvdLayout L = hosvd_layout(dims, J);
+  uint8_t* w = static_cast<uint8_t*>(ws);
+  const uint16_t* om[3];
   int64_t ldo[3];
   for (int i = 0; i < 3; ++i) {
-    if (!omegas[i] || !factors[i]) return SHG_ERR_INVALID_ARG;
-    ldo[i] = omega_lds ? omega_lds[i] : ranks[i];
-    if (ldo[i] < ranks[i]) return SHG_ERR_INVALID_ARG;
+    if (!factors[i]) return SHG_ERR_INVALID_ARG;
+    om[i] = omegas ? omegas[i] : nullptr;
+    ldo[i] = om[i] ? (omega_lds ? omega_lds[i] : J[i]) : L.ld[i];
+    if (ldo[i] < J[i]) return SHG_ERR_INVALID_ARG;
   }
   if (variant != SHG_SPLIT_F16 && variant != SHG_FP32_SIMT) return SHG_ERR_UNSUPPORTED;
   if (ws_bytes < need) return SHG_ERR_WORKSPACE;
   cudaStream_t st = static_cast<cudaStream_t>(stream);
-  const HosvdLayout L = hosvd_layout(dims, ranks);
-  uint8_t* w = static_cast<uint8_t*>(ws);
   float* W[3];
   for (int i = 0; i < 3; ++i) W[i] = reinterpret_cast<float*>(w + L.W[i]);
   float* T1 = reinterpret_cast<float*>(w + L.T1);
   float* T2 = reinterpret_cast<float*>(w + L.T2);
   const int64_t I0 = dims[0], I1 = dims[1], I2 = dims[2];
-  const int64_t J0 = ranks[0], J1 = ranks[1], J2 = ranks[2];
+  const int64_t J0 = J[0], J1 = J[1], J2 = J[2];
   const bool tc = (variant == SHG_SPLIT_F16);
 
   // per mode: W_i = X_(i) Omega_(i), Q_i = orth(W_i).  The three modes are
@@ -416,32 +431,17 @@ int shg_rp_hosvd(int ndim, const int64_t* dims, const int64_t* ranks, const floa
   for (int i = 0; i < 3; ++i) {
     cudaStream_t ms = mp->s[i];
     if (cudaStreamWaitEvent(ms, mp->fork, 0) != cudaSuccess) return SHG_ERR_CUDA;
-    if (i == 0) {
-      if (tc)
-        SHG_TRY(tc_gemm(A_KMAJ, B_F16, 2, I0, J0, I1 * I2, 1, X, I1 * I2, 0, omegas[0], ldo[0], W[0], L.ld[0], 0,
-                        d_flags, ms));
-      else
-        SHG_TRY(simt_gemm(I0, J0, I1 * I2, X, I1 * I2, 0, omegas[0], ldo[0], 1, W[0], L.ld[0], 0, 1, 0, 0, 0, ms));
-    } else if (i == 1) {
-      if (tc) {
-        SHG_TRY(tc_gemm(A_KMAJ, B_F16, 2, I1, J1, I2, I0, X, I2, I1 * I2, omegas[1], ldo[1], W[1], L.ld[1], 0,
-                        d_flags, ms));
-      } else {
-        if (cudaMemsetAsync(W[1], 0, I1 * L.ld[1] * 4, ms) != cudaSuccess) return SHG_ERR_CUDA;
-        SHG_TRY(simt_gemm(I1, J1, I2, X, I2, 0, omegas[1], ldo[1], 1, W[1], L.ld[1], 1, I0, I1 * I2, I2 * ldo[1], 0,
-                          ms));
-      }
-    } else {
-      if (tc)
-        SHG_TRY(tc_gemm(A_MNMAJ, B_F16, 2, I2, J2, I0 * I1, 1, X, I2, 0, omegas[2], ldo[2], W[2], L.ld[2], 0,
-                        d_flags, ms));
-      else
-        SHG_TRY(simt_gemm(I2, J2, I0 * I1, X, I2, 1, omegas[2], ldo[2], 1, W[2], L.ld[2], 0, 1, 0, 0, 0, ms));
+    if (!om[i]) {
+      // Omega_i: the Philox stream (seed, i * 2^32), rounded to FP16
+      uint16_t* gen = reinterpret_cast<uint16_t*>(w + L.Om[i]);
+      SHG_TRY(shg_gaussian_f16(seed, static_cast<uint64_t>(i) << 32, I0 * I1 * I2 / dims[i], J[i], gen, L.ld[i], ms));
+      om[i] = gen;
     }
+    SHG_TRY(mode_project(i, dims, J[i], X, om[i], ldo[i], W[i], L.ld[i], tc, d_flags, ms));
     float* T = reinterpret_cast<float*>(w + L.T[i]);
-    SHG_TRY(cholqr2(dims[i], ranks[i], W[i], L.ld[i], T, L.ld[i], w + L.small[i], d_flags, ms));
-    if (cudaMemcpy2DAsync(factors[i], ranks[i] * 4, W[i], L.ld[i] * 4, ranks[i] * 4, dims[i],
-                          cudaMemcpyDeviceToDevice, ms) != cudaSuccess)
+    SHG_TRY(cholqr2(dims[i], J[i], W[i], L.ld[i], T, L.ld[i], w + L.small[i], d_flags, ms));
+    if (cudaMemcpy2DAsync(factors[i], J[i] * 4, W[i], L.ld[i] * 4, J[i] * 4, dims[i], cudaMemcpyDeviceToDevice,
+                          ms) != cudaSuccess)
       return SHG_ERR_CUDA;
     if (cudaEventRecord(mp->done[i], ms) != cudaSuccess) return SHG_ERR_CUDA;
     if (cudaStreamWaitEvent(st, mp->done[i], 0) != cudaSuccess) return SHG_ERR_CUDA;
@@ -454,12 +454,145 @@ int shg_rp_hosvd(int ndim, const int64_t* dims, const int64_t* ranks, const floa
     SHG_TRY(split_f16(I2, J2, W[2], L.ld[2], Bhi, Blo, L.ld[2], d_flags, st));
     SHG_TRY(tc_gemm(A_KMAJ, B_SPLIT_PRE, 2, I0 * I1, J2, I2, 1, X, I2, 0, Bhi, L.ld[2], T1, L.ld[2], 0, d_flags, st,
                     nullptr, nullptr, Blo));
-  }
-  else
+  } else {
     SHG_TRY(simt_gemm(I0 * I1, J2, I2, X, I2, 0, W[2], L.ld[2], 0, T1, L.ld[2], 0, 1, 0, 0, 0, st));
+  }
   SHG_TRY(simt_gemm(J1, J2, I1, W[1], L.ld[1], 1, T1, L.ld[2], 0, T2, J2, 0, I0, 0, I1 * L.ld[2], J1 * J2, st));
   SHG_TRY(simt_gemm(J0, J1 * J2, I0, W[0], L.ld[0], 1, T2, J1 * J2, 0, core, J1 * J2, 0, 1, 0, 0, 0, st));
   return SHG_OK;
 }
 
 }  // extern "C"
+
+namespace shg {
+
+int rsvd_impl(int64_t m, int64_t n, int64_t rank, int64_t oversampling, int power_iters, const float* A,
+              int64_t lda, const uint16_t* omega, int64_t ldo, uint64_t seed, uint64_t omega_offset, float* U,
+              float* S, float* V, float* Q_out, void* ws, size_t ws_bytes, int variant, int32_t* d_flags,
+              cudaStream_t st, shg_report* report) {
+  size_t need = 0;
+  if (shg_rsvd_workspace_size(m, n, rank, oversampling, power_iters, &need) != SHG_OK) return SHG_ERR_INVALID_ARG;
+  if (!A || !U || !S || !V || !ws || !d_flags || lda < n) return SHG_ERR_INVALID_ARG;
+  if (variant < SHG_SPLIT_F16 || variant > SHG_FP32_SIMT) return SHG_ERR_INVALID_ARG;
+  const int64_t k = rank + oversampling;
+  if (omega && ldo < k) return SHG_ERR_INVALID_ARG;
+  if (ws_bytes < need) return SHG_ERR_WORKSPACE;
+  if (report) {
+    // the report synchronises the stream and times it with events
+    cudaStreamCaptureStatus cap = cudaStreamCaptureStatusNone;
+    if (cudaStreamIsCapturing(st, &cap) != cudaSuccess) return SHG_ERR_CUDA;
+    if (cap != cudaStreamCaptureStatusNone) return SHG_ERR_UNSUPPORTED;
+  }
+  const RsvdLayout L = rsvd_layout(m, n, k, rank);
+  uint8_t* w = static_cast<uint8_t*>(ws);
+  float* Y = reinterpret_cast<float*>(w + L.Y);
+  float* T = reinterpret_cast<float*>(w + L.T);
+  float* Z = reinterpret_cast<float*>(w + L.Z);
+  uint16_t* H = reinterpret_cast<uint16_t*>(w + L.H);
+  float* Bt = reinterpret_cast<float*>(w + L.Bt);
+  void* small = w + L.small;
+  float* Vk = reinterpret_cast<float*>(w + L.Vk);
+  double* lam = reinterpret_cast<double*>(w + L.lam);
+  float* Up = reinterpret_cast<float*>(w + L.Up);
+  float* Ups = reinterpret_cast<float*>(w + L.Ups);
+  double* piv = report ? reinterpret_cast<double*>(w + L.piv) : nullptr;
+  const int64_t ldk = round8(k);
+  const bool tc = tc_variant(variant);
+  PhaseEvents ev;
+  if (report) {
+    SHG_TRY(ev.init());
+    fill_f64_kernel<<<1, 1, 0, st>>>(piv, 1.0);
+    SHG_TRY(cuda_status(cudaGetLastError()));
+  }
+  SHG_TRY(ev.mark(SHG_PHASE_OMEGA, st));
+  // test matrix: the caller's, or the Philox stream (seed, omega_offset)
+  if (!omega) {
+    uint16_t* gen = reinterpret_cast<uint16_t*>(w + L.Om);
+    SHG_TRY(shg_gaussian_f16(seed, omega_offset, n, k, gen, ldk, st));
+    if (variant == SHG_SPLIT_BF16X3 || variant == SHG_SPLIT_BF16X2) SHG_TRY(f16_to_bf16(n, k, gen, ldk, gen, ldk, st));
+    omega = gen;
+    ldo = ldk;
+  }
+  SHG_TRY(ev.mark(SHG_PHASE_PROJECT, st));
+  // projection: Y = A Omega
+  SHG_TRY(shgemm_project(m, n, k, A, lda, 0, omega, ldo, Y, ldk, variant, d_flags, st));
+  SHG_TRY(ev.mark(SHG_PHASE_ORTH, st));
+  // orthonormal basis: Q = orth(Y)
+  SHG_TRY(cholqr2(m, k, Y, ldk, T, ldk, small, d_flags, st, piv));
+  SHG_TRY(ev.mark(SHG_PHASE_POWER, st));
+  // power scheme (Sec. 2.1): the FP16-rounded basis is the next test matrix
+  for (int it = 0; it < power_iters; ++it) {
+    if (tc) {
+      SHG_TRY(to_f16(m, k, Y, ldk, H, ldk, st));
+      SHG_TRY(tc_gemm(A_MNMAJ, B_F16, 2, n, k, m, 1, A, lda, 0, H, ldk, Z, ldk, 0, d_flags, st));
+    } else {
+      SHG_TRY(simt_gemm(n, k, m, A, lda, 1, Y, ldk, 0, Z, ldk, 0, 1, 0, 0, 0, st));
+    }
+    SHG_TRY(cholqr2(n, k, Z, ldk, T, ldk, small, d_flags, st, piv));
+    if (tc) {
+      SHG_TRY(to_f16(n, k, Z, ldk, H, ldk, st));
+      SHG_TRY(tc_gemm(A_KMAJ, B_F16, 2, m, k, n, 1, A, lda, 0, H, ldk, Y, ldk, 0, d_flags, st));
+    } else {
+      SHG_TRY(simt_gemm(m, k, n, A, lda, 0, Z, ldk, 0, Y, ldk, 0, 1, 0, 0, 0, st));
+    }
+    SHG_TRY(cholqr2(m, k, Y, ldk, T, ldk, small, d_flags, st, piv));
+  }
+  SHG_TRY(ev.mark(SHG_PHASE_B, st));
+  // B^T = A^T Q (FP32-accurate)
+  if (tc) {
+    // Q split into FP16 hi / lo once (the TCEC B operand), then the TN product
+    uint16_t* Hlo = reinterpret_cast<uint16_t*>(w + L.Hlo);
+    SHG_TRY(split_f16(m, k, Y, ldk, H, Hlo, ldk, d_flags, st));
+    SHG_TRY(tc_gemm(A_MNMAJ, B_SPLIT_PRE, 2, n, k, m, 1, A, lda, 0, H, ldk, Bt, ldk, 0, d_flags, st, nullptr, nullptr,
+                    Hlo));
+  } else {
+    SHG_TRY(simt_gemm(n, k, m, A, lda, 1, Y, ldk, 0, Bt, ldk, 0, 1, 0, 0, 0, st));
+  }
+  SHG_TRY(ev.mark(SHG_PHASE_SVD, st));
+  // small SVD of B through the eigendecomposition of B B^T = Bt^T Bt
+  const SmallWs sw = small_ws(small, k);
+  double* G = sw.G;
+  SHG_TRY(gram_f64(n, k, Bt, ldk, G, st));
+  SHG_TRY(jacobi_eig(k, G, Vk, sw.jac, jacobi_log_bytes(k) ? w + L.eig : nullptr, st));
+  SHG_TRY(rayleigh_sort(k, rank, G, Vk, lam, S, Up, Ups, st));
+  SHG_TRY(ev.mark(SHG_PHASE_LIFT, st));
+  // lift: U = Q U'; V = B^T U' Sigma^-1
+  SHG_TRY(simt_gemm(m, rank, k, Y, ldk, 0, Up, rank, 0, U, rank, 0, 1, 0, 0, 0, st));
+  SHG_TRY(simt_gemm(n, rank, k, Bt, ldk, 0, Ups, rank, 0, V, rank, 0, 1, 0, 0, 0, st));
+  if (Q_out) {
+    if (cudaMemcpy2DAsync(Q_out, k * 4, Y, ldk * 4, k * 4, m, cudaMemcpyDeviceToDevice, st) != cudaSuccess)
+      return SHG_ERR_CUDA;
+  }
+  SHG_TRY(ev.mark(SHG_PHASE_ESTIMATE, st));
+  if (!report) return SHG_OK;
+  // a-posteriori residual of the basis Q (Theorems 1 and 3), probes from the
+  // seed's Philox stream far from Omega's counter blocks
+  double* eout = reinterpret_cast<double*>(w + L.eout);
+  const bool est_ok = (lda % 4 == 0) && ((reinterpret_cast<uintptr_t>(A) & 15) == 0);
+  if (est_ok) {
+    size_t est_bytes = 0;
+    SHG_TRY(shg_residual_estimate_workspace_size(m, n, k, kReportProbes, &est_bytes));
+    SHG_TRY(shg_residual_estimate(m, n, k, kReportProbes, A, lda, Y, ldk, seed, 1ull << 62, 0.0, eout,
+                                  w + L.est, est_bytes, d_flags, st));
+  }
+  SHG_TRY(ev.mark(SHG_NUM_PHASES, st));
+  if (cudaStreamSynchronize(st) != cudaSuccess) return SHG_ERR_CUDA;
+  shg_report r{};
+  int32_t fl = 0;
+  double host[2] = {0.0, -1.0};
+  if (cudaMemcpy(&fl, d_flags, sizeof(fl), cudaMemcpyDeviceToHost) != cudaSuccess ||
+      cudaMemcpy(&host[0], piv, sizeof(double), cudaMemcpyDeviceToHost) != cudaSuccess)
+    return SHG_ERR_CUDA;
+  if (est_ok && cudaMemcpy(&host[1], eout, sizeof(double), cudaMemcpyDeviceToHost) != cudaSuccess)
+    return SHG_ERR_CUDA;
+  r.flags = fl;
+  r.status = shg_flags_status(fl);
+  r.min_pivot = host[0];
+  r.est_residual = host[1];
+  for (int i = 0; i < SHG_NUM_PHASES; ++i)
+    if (cudaEventElapsedTime(&r.phase_ms[i], ev.e[i], ev.e[i + 1]) != cudaSuccess) return SHG_ERR_CUDA;
+  *report = r;
+  return SHG_OK;
+}
+
+}  // namespace shg

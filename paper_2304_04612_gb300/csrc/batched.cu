@@ -77,8 +77,8 @@ int batched_grid_sms() {
   return kBatchedGridSms;
 }
 
-// Largest per-problem need: the shg_rsvd workspace plus an FP16 Omega
-// (n x round8(k)) for problems whose Omega is generated.
+// Largest per-problem need: the shg_rsvd workspace (which has room for a
+// generated FP16 Omega).
 int branch_bytes(int batch, const int64_t* m, const int64_t* n, const int64_t* rank, int64_t s, int q,
                  size_t* out) {
   size_t mx = 0;
@@ -87,7 +87,6 @@ int branch_bytes(int batch, const int64_t* m, const int64_t* n, const int64_t* r
     const int rc = shg_rsvd_workspace_size(m[i], n[i], rank[i], s, q, &b);
     if (rc != SHG_OK) return rc;
     b = (b + 255) & ~size_t(255);
-    b += (static_cast<size_t>(n[i]) * round8(rank[i] + s) * 2 + 255) & ~size_t(255);
     if (b > mx) mx = b;
   }
   *out = mx;
@@ -123,6 +122,7 @@ std::vector<uint8_t> make_key(const Args& a, int dev, int grid_share) {
   std::vector<uint8_t> key;
   put(key, dev);
   put(key, grid_share);
+  put(key, tc_tune_generation());  // a graph keeps the launch configurations it was captured with
   put(key, a.batch);
   put(key, a.s);
   put(key, a.q);
@@ -157,22 +157,12 @@ int enqueue(const Args& a, Pool& p, size_t per_branch, int grid_share, cudaStrea
   for (int i = 0; i < a.batch; ++i) {
     const int b = i % nb;
     uint8_t* w = a.ws + static_cast<size_t>(b) * per_branch;
-    const int64_t k = a.rank[i] + a.s;
     const uint16_t* om = a.omegas ? a.omegas[i] : nullptr;
-    int64_t ldo = om ? a.ldo[i] : round8(k);
-    size_t need = 0;
-    int rc = shg_rsvd_workspace_size(a.m[i], a.n[i], a.rank[i], a.s, a.q, &need);
-    if (rc != SHG_OK) return rc;
-    need = (need + 255) & ~size_t(255);
-    if (!om) {
-      uint16_t* gen = reinterpret_cast<uint16_t*>(w + need);
-      // Philox stream of problem i: counter blocks from i * 2^32 on
-      rc = shg_gaussian_f16(a.seed, static_cast<uint64_t>(i) << 32, a.n[i], k, gen, ldo, p.s[b]);
-      if (rc != SHG_OK) return rc;
-      om = gen;
-    }
-    rc = shg_rsvd(a.m[i], a.n[i], a.rank[i], a.s, a.q, a.A[i], a.lda[i], om, ldo, a.U[i], a.S[i], a.V[i], nullptr,
-                  w, need, a.variant, a.flags, p.s[b]);
+    const int64_t ldo = om ? a.ldo[i] : 0;
+    // a NULL Omega is problem i's Philox stream: counter blocks from i * 2^32 on
+    const int rc = rsvd_impl(a.m[i], a.n[i], a.rank[i], a.s, a.q, a.A[i], a.lda[i], om, ldo, a.seed,
+                             static_cast<uint64_t>(i) << 32, a.U[i], a.S[i], a.V[i], nullptr, w, per_branch,
+                             a.variant, a.flags, p.s[b], nullptr);
     if (rc != SHG_OK) return rc;
   }
   for (int b = 0; b < nb; ++b) {

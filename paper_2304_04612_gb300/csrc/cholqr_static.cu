@@ -45,7 +45,9 @@ int scratch_for_current_device(void** out) {
 
 extern "C" int shg_cholqr2_static(int64_t m, int64_t k, float* X, int64_t ldx, int32_t* d_flags, void* stream) {
   using namespace shg;
-  if (k < 1 || m < k || k > 1024 || !X || ldx < k) return SHG_ERR_INVALID_ARG;
+  if (k < 1 || m < k || k > 1024 || !X || ldx < k || m >= (1ll << 31)) return SHG_ERR_INVALID_ARG;
+  // m k floats must fit before the product is formed (no wrap-around)
+  if (static_cast<uint64_t>(m) > kStaticScratchBytes / 4 / static_cast<uint64_t>(k)) return SHG_ERR_WORKSPACE;
   const size_t t_bytes = align256(static_cast<size_t>(m) * k * 4);
   const size_t small = cholqr_small_bytes(k);
   if (t_bytes + small + 256 > kStaticScratchBytes) return SHG_ERR_WORKSPACE;

@@ -7,6 +7,7 @@
 // the element's logical index, never on the launch shape.  The sparse sign
 // matrix of Sec. 3.4 uses the raw 32-bit words of the same stream.
 #include <cmath>
+#include <cuda_bf16.h>
 #include <cuda_fp16.h>
 
 #include "internal.h"
@@ -92,7 +93,33 @@ __global__ void sparse_sign_f16_kernel(uint2 key, unsigned long long offset, lon
   }
 }
 
+// y = RN_bf16(x) of FP16 values (the BF16 test matrix of the BF16 split
+// variants is the FP16 one rounded to nearest even in BF16).
+__global__ void f16_to_bf16_kernel(long long rows, long long cols, const __half* __restrict__ x, long long ldx,
+                                   __nv_bfloat16* __restrict__ y, long long ldy) {
+  const long long n = rows * cols;
+  for (long long e = blockIdx.x * static_cast<long long>(blockDim.x) + threadIdx.x; e < n;
+       e += static_cast<long long>(gridDim.x) * blockDim.x) {
+    const long long r = e / cols, c = e - r * cols;
+    y[r * ldy + c] = __float2bfloat16_rn(__half2float(x[r * ldx + c]));  // FP16 -> FP32 is exact
+  }
+}
+
 }  // namespace
+
+int f16_to_bf16(int64_t rows, int64_t cols, const uint16_t* x, int64_t ldx, uint16_t* y, int64_t ldy,
+                cudaStream_t st) {
+  const long long n = rows * cols;
+  if (n <= 0) return SHG_OK;
+  const int sms = sm_count();
+  if (sms <= 0) return SHG_ERR_CUDA;
+  const long long want = (n + 255) / 256;
+  const int grid = static_cast<int>(want < 8ll * sms ? want : 8ll * sms);
+  f16_to_bf16_kernel<<<grid, 256, 0, st>>>(rows, cols, reinterpret_cast<const __half*>(x), ldx,
+                                           reinterpret_cast<__nv_bfloat16*>(y), ldy);
+  return cuda_status(cudaGetLastError());
+}
+
 }  // namespace shg
 
 extern "C" int shg_sparse_sign_f16(uint64_t seed, uint64_t offset, int64_t rows, int64_t cols, double s,

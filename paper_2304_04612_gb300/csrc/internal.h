@@ -54,11 +54,26 @@ int tc_autotune(int amaj, int bmode, int pieces, int64_t M, int64_t N, int64_t S
 // Cached configuration of a shape class (returns false when untuned).
 bool tc_tuned(int amaj, int bmode, int pieces, int64_t M, int64_t N, int64_t K, int64_t P, TcConfig* out);
 void tc_tune_clear();
+// Bumped whenever the tuner's cache changes (a new entry or a clear), so that
+// a cached CUDA graph captured under other launch configurations is not replayed.
+unsigned long long tc_tune_generation();
 
 // FP32 SIMT GEMM, batched over gridDim.z with element strides.
 int simt_gemm(int64_t M, int64_t N, int64_t K, const float* A, int64_t lda, int trans_a, const void* B,
               int64_t ldb, int b_f16, float* C, int64_t ldc, int accumulate, int64_t batch,
               int64_t stride_a, int64_t stride_b, int64_t stride_c, cudaStream_t stream);
+
+// y = RN_bf16(x) element-wise for an FP16 matrix (BF16 test matrices from
+// the FP16 Gaussian stream).
+int f16_to_bf16(int64_t rows, int64_t cols, const uint16_t* x, int64_t ldx, uint16_t* y, int64_t ldy,
+                cudaStream_t st);
+
+// Algorithm 1 as shg_rsvd computes it, with the counter offset of the
+// generated Omega (the batched path gives problem i offset i * 2^32).
+int rsvd_impl(int64_t m, int64_t n, int64_t rank, int64_t oversampling, int power_iters, const float* A,
+              int64_t lda, const uint16_t* omega, int64_t ldo, uint64_t seed, uint64_t omega_offset, float* U,
+              float* S, float* V, float* Q_out, void* ws, size_t ws_bytes, int variant, int32_t* d_flags,
+              cudaStream_t st, shg_report* report);
 
 int sm_count();
 // SMs that a launch sized for the whole GPU spreads its grid over: all of

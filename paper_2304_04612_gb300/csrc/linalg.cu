@@ -12,6 +12,7 @@
 // The eigensolver is a parallel cyclic Jacobi method (round-robin pairing)
 // in FP32 on the scaled Gram matrix; eigenvalues are then refined as FP64
 // Rayleigh quotients v^T G v / v^T v with the FP64 Gram matrix.
+#include <atomic>
 #include <cooperative_groups.h>
 #include <cuda_fp16.h>
 
@@ -1155,11 +1156,16 @@ int jacobi_eig(int64_t k, const double* G, float* V, float* scratch, void* eig, 
   } else {
     // too large for one SM: the whole grid works on every round (cooperative
     // launch); h rotation threads plus the block threads
-    static int blocks_per_sm = 0;
-    if (blocks_per_sm == 0 &&
-        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&blocks_per_sm, jacobi_grid_kernel, kJacGridThreads, 0) !=
-            cudaSuccess)
-      return SHG_ERR_CUDA;
+    // occupancy of the grid kernel, queried once (host threads may race to
+    // it; every one of them stores the same value)
+    static std::atomic<int> cached_bps{0};
+    int blocks_per_sm = cached_bps.load(std::memory_order_relaxed);
+    if (blocks_per_sm == 0) {
+      if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&blocks_per_sm, jacobi_grid_kernel, kJacGridThreads, 0) !=
+          cudaSuccess)
+        return SHG_ERR_CUDA;
+      cached_bps.store(blocks_per_sm, std::memory_order_relaxed);
+    }
     const int sms = sm_count();
     if (sms <= 0 || blocks_per_sm <= 0) return SHG_ERR_CUDA;
     long long want = (static_cast<long long>(nblk) + h + kJacGridThreads - 1) / kJacGridThreads;
@@ -1205,10 +1211,31 @@ int to_f16(int64_t rows, int64_t cols, const float* x, int64_t ldx, uint16_t* y,
   return cuda_status(cudaGetLastError());
 }
 
+namespace {
+// Pivot ratios of one Cholesky factorization G = R^T R: r_j = R_jj^2 / G_jj,
+// the squared sine of the angle between column j of X and the span of the
+// columns before it (1 for orthogonal columns, near 0 close to breakdown),
+// from R^-1's diagonal (Rinv_jj = 1 / R_jj); the minimum over j is folded
+// into *out with an integer atomicMin on the bits of the non-negative
+// doubles (their order is that of the values).
+__global__ void pivot_ratio_kernel(int k, const double* __restrict__ G, const float* __restrict__ Rinv,
+                                   unsigned long long* out) {
+  for (int j = threadIdx.x; j < k; j += blockDim.x) {
+    const double x = static_cast<double>(Rinv[static_cast<size_t>(j) * k + j]);
+    const double g = G[static_cast<size_t>(j) * k + j];
+    double r = (x > 0.0 && g > 0.0) ? 1.0 / (x * x * g) : 0.0;
+    if (!(r >= 0.0)) r = 0.0;
+    atomicMin(out, static_cast<unsigned long long>(__double_as_longlong(r)));
+  }
+}
+}  // namespace
+
 // X (m x k) -> Q with X = Q R; T (m x k, leading dimension ldt) is scratch;
-// small = cholqr_small_bytes(k).
+// small = cholqr_small_bytes(k).  min_pivot (device double, nullable): the
+// smallest pivot ratio R_jj^2 / G_jj of both factorizations is folded into
+// it (the caller initialises it, e.g. to 1).
 int cholqr2(int64_t m, int64_t k, float* X, int64_t ldx, float* T, int64_t ldt, void* small, int32_t* flags,
-            cudaStream_t st) {
+            cudaStream_t st, double* min_pivot) {
   const SmallWs w = small_ws(small, k);
   int rc;
   float* src = X;
@@ -1218,6 +1245,11 @@ int cholqr2(int64_t m, int64_t k, float* X, int64_t ldx, float* T, int64_t ldt, 
     const int64_t ldd = (pass == 0) ? ldt : ldx;
     if ((rc = gram_f64(m, k, src, lds, w.G, st))) return rc;
     if ((rc = chol_inv(k, w.G, w.Rf, w.chol, flags, st))) return rc;
+    if (min_pivot) {
+      pivot_ratio_kernel<<<1, 256, 0, st>>>(static_cast<int>(k), w.G, w.Rf,
+                                            reinterpret_cast<unsigned long long*>(min_pivot));
+      if ((rc = cuda_status(cudaGetLastError()))) return rc;
+    }
     if ((rc = simt_gemm(m, k, k, src, lds, 0, w.Rf, k, 0, dst, ldd, 0, 1, 0, 0, 0, st))) return rc;
     src = dst;
     lds = ldd;

@@ -31,6 +31,6 @@ int rayleigh_sort(int64_t k, int64_t p, const double* G, const float* V, double*
                   float* Ups, cudaStream_t st);
 int to_f16(int64_t rows, int64_t cols, const float* x, int64_t ldx, uint16_t* y, int64_t ldy, cudaStream_t st);
 int cholqr2(int64_t m, int64_t k, float* X, int64_t ldx, float* T, int64_t ldt, void* small, int32_t* flags,
-            cudaStream_t st);
+            cudaStream_t st, double* min_pivot = nullptr);
 
 }  // namespace shg

@@ -41,6 +41,7 @@
 #include <cuda_fp16.h>
 
 #include <algorithm>
+#include <atomic>
 #include <cstdlib>
 #include <mutex>
 #include <vector>
@@ -727,6 +728,7 @@ struct TuneKey {
 };
 std::mutex g_tune_mu;
 std::vector<std::pair<TuneKey, TcConfig>> g_tune;
+std::atomic<unsigned long long> g_tune_gen{0};
 
 int floor_log2(int64_t x) {
   int l = 0;
@@ -764,7 +766,9 @@ TcConfig default_config() {
   TcConfig c;
   c.sa = env_int("SHG_A_STAGES", 4);
   c.sb = env_int("SHG_B_STAGES", 4);
-  c.kc = env_int("SHG_DRAIN_KBLOCKS", 4);
+  // drain interval: 2..8 K blocks (whole-range TMEM accumulation, or drains
+  // every 16 blocks and more, lose too many low bits of the hi product)
+  c.kc = std::max(2, std::min(env_int("SHG_DRAIN_KBLOCKS", 4), 8));
   c.groups = env_int("SHG_NGROUPS", 1) != 0 ? 1 : 0;
   return c;
 }
@@ -785,7 +789,10 @@ bool tc_tuned(int amaj, int bmode, int pieces, int64_t M, int64_t N, int64_t K, 
 void tc_tune_clear() {
   std::lock_guard<std::mutex> lock(g_tune_mu);
   g_tune.clear();
+  ++g_tune_gen;
 }
+
+unsigned long long tc_tune_generation() { return g_tune_gen.load(); }
 
 int tc_autotune(int amaj, int bmode, int pieces, int64_t M, int64_t N, int64_t S_k, int64_t P, const float* A,
                 int64_t lda, int64_t p_stride, const void* B, int64_t ldb, float* C, int64_t ldc,
@@ -851,7 +858,10 @@ int tc_autotune(int amaj, int bmode, int pieces, int64_t M, int64_t N, int64_t S
     std::lock_guard<std::mutex> lock(g_tune_mu);
     bool have = false;
     for (const auto& e : g_tune) have = have || (e.first == key);
-    if (!have) g_tune.emplace_back(key, win);
+    if (!have) {
+      g_tune.emplace_back(key, win);
+      ++g_tune_gen;
+    }
   }
   if (best) *best = win;
   return SHG_OK;
@@ -911,7 +921,7 @@ int tc_gemm_impl(int amaj, int bmode, int pieces, int64_t M, int64_t N, int64_t 
     else if (a.sa > 2) --a.sa;
     else return SHG_ERR_UNSUPPORTED;
   }
-  a.kc = cfg.kc > 0 ? cfg.kc : a.kblocks;  // 0: accumulate a whole segment in TMEM
+  a.kc = std::max(1, std::min(cfg.kc, 8));
   TcTestHooks h;
   if (hooks) h = *hooks;
   a.wait_ns = h.wait_ns;

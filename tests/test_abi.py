@@ -26,8 +26,8 @@ def lib():
 
 def test_header_declares_the_paper_entry_points():
     names = declared_functions()
-    for want in ("shgemm_project", "shg_rsvd", "shg_rp_hosvd", "shg_gaussian_f16", "shg_gemm_split3",
-                 "shg_sgemm", "shg_cholqr2"):
+    for want in ("shgemm_project", "shg_rsvd", "shg_rp_hosvd", "shg_mode_project", "shg_gaussian_f16",
+                 "shg_gemm_split3", "shg_sgemm", "shg_cholqr2"):
         assert want in names
 
 
@@ -61,10 +61,37 @@ def test_host_argument_validation(lib):
     assert lib.shg_rsvd_workspace_size(100, 100, 90, 20, 0, ctypes.byref(sz)) == 1   # k > min(m, n)
     assert lib.shg_rsvd_workspace_size(1024, 1024, 32, 32, 0, ctypes.byref(sz)) == 0
     assert sz.value > 1024 * 64 * 4
+    assert lib.shg_rsvd_workspace_size(1 << 31, 1024, 32, 32, 0, ctypes.byref(sz)) == 1   # m >= 2^31
     d = (ctypes.c_int64 * 3)(8, 8, 8)
     r = (ctypes.c_int64 * 3)(4, 9, 4)                                 # J > I
-    assert lib.shg_rp_hosvd_workspace_size(3, d, r, ctypes.byref(sz)) == 1
-    assert lib.shg_rp_hosvd_workspace_size(4, d, r, ctypes.byref(sz)) == 7
+    assert lib.shg_rp_hosvd_workspace_size(3, d, r, 0, ctypes.byref(sz)) == 1
+    assert lib.shg_rp_hosvd_workspace_size(4, d, r, 0, ctypes.byref(sz)) == 7
+    r = (ctypes.c_int64 * 3)(4, 4, 4)
+    assert lib.shg_rp_hosvd_workspace_size(3, d, r, 5, ctypes.byref(sz)) == 1     # rank + s > I
+    assert lib.shg_rp_hosvd_workspace_size(3, d, r, -1, ctypes.byref(sz)) == 1
+    assert lib.shg_rp_hosvd_workspace_size(3, d, r, 4, ctypes.byref(sz)) == 0
+    # room for the three generated test matrices (64 x 8 FP16 each)
+    assert sz.value >= 3 * 64 * 8 * 2
+    # mode projection: bad mode, J > ld, NULL tensor, unsupported variant
+    assert lib.shg_mode_project(3, d, 3, 4, one, one, 8, one, 8, 0, one, null) == 1
+    assert lib.shg_mode_project(3, d, 0, 9, one, one, 8, one, 8, 0, one, null) == 1
+    assert lib.shg_mode_project(3, d, 0, 4, null, one, 8, one, 8, 0, one, null) == 1
+    assert lib.shg_mode_project(3, d, 0, 4, one, one, 8, one, 8, 1, one, null) == 7
+    # CholeskyQR2: m >= 2^31 rejected by the workspace query and the static entry
+    assert lib.shg_cholqr2_workspace_size(1 << 31, 16, ctypes.byref(sz)) == 1
+    assert lib.shg_cholqr2_static(1 << 31, 16, one, 16, null, null) == 1
+    # m k beyond the static scratch, with m k * 4 wrapping 64 bits: no wrap-around
+    assert lib.shg_cholqr2_static((1 << 31) - 1, 1024, one, 1024, null, null) == 4
+    # randomized SVD: NULL A, bad variant, short workspace (host checks only)
+    assert lib.shg_rsvd(64, 64, 8, 8, 0, null, 64, null, 0, 0, one, one, one, null, one, 1 << 30, 0, one, null,
+                        null) == 1
+    assert lib.shg_rsvd(64, 64, 8, 8, 0, one, 64, null, 0, 0, one, one, one, null, one, 1 << 30, 9, one, null,
+                        null) == 1
+    assert lib.shg_rsvd(64, 64, 8, 8, 0, one, 64, null, 0, 0, one, one, one, null, one, 16, 0, one, null,
+                        null) == 4
+    # a passed Omega needs ldo >= k; a NULL Omega ignores ldo
+    assert lib.shg_rsvd(64, 64, 8, 8, 0, one, 64, one, 8, 0, one, one, one, null, one, 1 << 30, 0, one, null,
+                        null) == 1
     # autotuner: bad shapes, reps out of range and the SIMT variant (nothing
     # to tune) are rejected before any launch; lookup of an untuned class
     cfg = (ctypes.c_int32 * 5)()
@@ -126,3 +153,15 @@ def test_batched_workspace_host_validation(lib):
     # diagnostic entry: out-of-range wait limit rejected on the host
     assert lib.shg_diag_wait_timeout(8, 8, 8, ctypes.c_void_p(16), 8, ctypes.c_void_p(16), 8, ctypes.c_void_p(16), 8,
                                      10, ctypes.c_void_p(16), null) == 1
+
+
+def test_report_struct_layout():
+    # the ctypes mirror of struct shg_report: two int32, two doubles, the
+    # phase times (no padding surprises between the int32 pair and the doubles)
+    from paper_2304_04612_gb300 import _lib
+    R = _lib.Report
+    assert R.flags.offset == 0 and R.status.offset == 4
+    assert R.min_pivot.offset == 8 and R.est_residual.offset == 16
+    assert R.phase_ms.offset == 24 and ctypes.sizeof(R) == 24 + 4 * len(_lib.PHASES)
+    src = open(HEADER).read()
+    assert f"#define SHG_NUM_PHASES     {len(_lib.PHASES)}" in src
