@@ -195,8 +195,12 @@ int shg_sgemm(int64_t m, int64_t n, int64_t kk,
  *   projections of shg_rsvd and shg_rsvd_batched) use it.  A class that is
  *   already cached is not timed again.  It may not run while `stream` is
  *   being captured (SHG_ERR_UNSUPPORTED), nor for SHG_FP32_SIMT.
- *   config_out (host, nullable): {A stages, B stages, drain K blocks,
- *   grouping, 1 if the class was cached before the call}.
+ *   config_out (host, nullable, 6 entries): {A stages, B stages, drain K
+ *   blocks, grouping, 1 if the class was cached before the call, wide tiles}.
+ *   "Wide tiles" (K-major A with an FP16 Omega and k > 128): output tiles
+ *   of up to 256 columns whose A operand is split in shared memory (one A
+ *   pass per 256 columns) instead of 128-column tiles split into tensor
+ *   memory; the tuner times both.
  *   shg_autotune_lookup reports the cached configuration of a class
  *   (config_out[4] = 0 when it has none; the other entries are then the
  *   built-in defaults).  shg_autotune_clear empties the cache.

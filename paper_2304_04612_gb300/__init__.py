@@ -139,7 +139,7 @@ def shgemm_project(A: torch.Tensor, omega: torch.Tensor, variant="f16", trans_a:
 
 def _config(arr) -> dict:
     return {"a_stages": arr[0], "b_stages": arr[1], "drain_kblocks": arr[2], "n_groups": bool(arr[3]),
-            "cached": bool(arr[4])}
+            "cached": bool(arr[4]), "wide": bool(arr[5])}
 
 
 def shg_autotune_project(A: torch.Tensor, omega: torch.Tensor, variant="f16", trans_a: bool = False, reps: int = 3,
@@ -158,14 +158,14 @@ def shg_autotune_project(A: torch.Tensor, omega: torch.Tensor, variant="f16", tr
         out = torch.empty(m, k, dtype=torch.float32, device=A.device)
     ldy = _mat(out, "out", (torch.float32,))
     fl = flags if flags is not None else new_flags(A.device)
-    cfg = (ctypes.c_int32 * 5)()
+    cfg = (ctypes.c_int32 * 6)()
     _check(_lib.load().shg_autotune_project(m, n, k, _ptr(A), lda, int(trans_a), _ptr(omega), ldo, _ptr(out), ldy,
                                             v, reps, _ptr(fl), _stream(stream), cfg), "shg_autotune_project")
     return _config(cfg)
 
 
 def shg_autotune_lookup(m: int, n: int, k: int, trans_a: bool = False, variant="f16") -> dict:
-    cfg = (ctypes.c_int32 * 5)()
+    cfg = (ctypes.c_int32 * 6)()
     _check(_lib.load().shg_autotune_lookup(m, n, k, int(trans_a), _variant(variant), cfg), "shg_autotune_lookup")
     return _config(cfg)
 

@@ -259,6 +259,7 @@ static void put_config(const TcConfig& c, int found, int32_t* out) {
   out[2] = c.kc;
   out[3] = c.groups;
   out[4] = found;
+  out[5] = c.wide;
 }
 
 int shg_autotune_project(int64_t m, int64_t n, int64_t k, const float* A, int64_t lda, int trans_a,

@@ -34,6 +34,7 @@ struct TcConfig {
   int sb = 4;      // depth of the B tile ring
   int kc = 4;      // K blocks per RN drain of the hi product
   int groups = 1;  // 1: one CTA group per N tile when there are 2..8 N tiles; 0: a single group
+  int wide = 1;    // 1: N tiles of up to 256 columns (K-major A, FP16 B, N > 128); 0: tiles of 128
 };
 int tc_gemm(int amaj, int bmode, int pieces, int64_t M, int64_t N, int64_t S_k, int64_t P,
             const float* A, int64_t lda, int64_t p_stride, const void* B, int64_t ldb, float* C,

@@ -651,6 +651,357 @@ __global__ void __launch_bounds__(kThreads, 1)
   }
 }
 
+// ------------------------------------------------------------ wide N tiles
+// The same product for N tiles of up to 256 columns (K-major A, FP16 B):
+// one A tile then feeds twice the MMA work, so a 256-column output streams
+// A through the SMs once (a 512-column output twice) and splits each A
+// element once per 256 columns instead of once per 128.
+//
+// The two accumulators of 256 columns fill tensor memory (hi product D,
+// single-buffered, and lo product L), so the A operand is read from shared
+// memory: the split warps convert each staged FP32 tile in place into the
+// K-major FP16 operand layout (thread r owns row r: its FP32 bytes, K 0..31
+// in the first box and K 32..63 in the second, become its hi row and its lo
+// row, in the same 128-byte swizzle).  The MMA issuer waits for the drain
+// of D before each chunk's first MMA.
+//
+// 16 warps: 0 A producer, 1 MMA issuer and TMEM owner, 2 B producer, 3 idle,
+// 4..7 split (one row per thread), 8..15 epilogue (TMEM lane quadrant
+// warp % 4, column half (warp - 8) / 4, 128 running sums per thread).
+// Registers are rebalanced per warpgroup with setmaxnreg: 128 at launch
+// (512 x 128 = 65536), then 56 / 120 / 168 / 168, which again sum to
+// 128 x (56 + 120) + 256 x 168 = 65536.
+constexpr int kWideThreads = 512;
+constexpr int kWideMaxN = 256;
+constexpr int kWideSplitWarp0 = 4;
+constexpr int kWideEpiWarp0 = 8;
+
+__device__ __forceinline__ void regs_dec_56() { asm volatile("setmaxnreg.dec.sync.aligned.u32 56;\n" ::: "memory"); }
+__device__ __forceinline__ void regs_dec_120() { asm volatile("setmaxnreg.dec.sync.aligned.u32 120;\n" ::: "memory"); }
+__device__ __forceinline__ void regs_inc_168() { asm volatile("setmaxnreg.inc.sync.aligned.u32 168;\n" ::: "memory"); }
+
+// Row r of a staged K-major FP32 tile (two 128-row x 32-float boxes, 128B
+// swizzle) split in place: hi = RN_f16(a) over the row's bytes of the first
+// box, lo = RN_f16((a - hi) 2^11) over those of the second, as K-major FP16
+// rows of 64 values with the same swizzle (logical 16-byte chunk g of row r
+// at physical chunk g ^ (r mod 8)).
+__device__ __forceinline__ void split_row_to_smem(uint8_t* tile, int r) {
+  float a[64];
+  read_row<A_KMAJ>(tile, r, a);
+  const int sw = r & 7;
+  uint8_t* hrow = tile + r * 128;
+  uint8_t* lrow = tile + 16384 + r * 128;
+#pragma unroll
+  for (int g = 0; g < 8; ++g) {
+    uint32_t hp[4], lp[4];
+#pragma unroll
+    for (int j = 0; j < 4; ++j) {
+      const float x0 = a[8 * g + 2 * j], x1 = a[8 * g + 2 * j + 1];
+      const __half2 hi = __floats2half2_rn(x0, x1);
+      const float2 hf = __half22float2(hi);
+      const __half2 lo = __floats2half2_rn((x0 - hf.x) * 2048.0f, (x1 - hf.y) * 2048.0f);
+      hp[j] = h2_as_u32(hi);
+      lp[j] = h2_as_u32(lo);
+    }
+    *reinterpret_cast<uint4*>(hrow + ((g ^ sw) << 4)) = make_uint4(hp[0], hp[1], hp[2], hp[3]);
+    *reinterpret_cast<uint4*>(lrow + ((g ^ sw) << 4)) = make_uint4(lp[0], lp[1], lp[2], lp[3]);
+  }
+}
+
+__global__ void __launch_bounds__(kWideThreads, 1)
+    tc_wide_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmB,
+                   const TcArgs args) {
+  extern __shared__ uint8_t smem_raw[];
+  uint8_t* smem = reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
+  const int SA = args.sa, SB = args.sb;
+  uint8_t* a_ring = smem;
+  uint8_t* b_ring = smem + SA * kABytes;
+  uint64_t* bars = reinterpret_cast<uint64_t*>(b_ring + SB * args.b_bytes);
+  const uint32_t bar_afull = smem_u32(bars);
+  const uint32_t bar_asplit = smem_u32(bars + SA);
+  const uint32_t bar_aempty = smem_u32(bars + 2 * SA);
+  const uint32_t bar_bfull = smem_u32(bars + 3 * SA);
+  const uint32_t bar_bempty = smem_u32(bars + 3 * SA + SB);
+  const int nb = 3 * SA + 2 * SB;
+  const uint32_t bar_dfull = smem_u32(bars + nb);
+  const uint32_t bar_dempty = smem_u32(bars + nb + 1);
+  const uint32_t bar_lempty = smem_u32(bars + nb + 2);
+  const uint32_t bar_drain = smem_u32(bars + nb + 3);
+  uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(bars + nb + 4);
+  volatile int* abort_flag = reinterpret_cast<volatile int*>(tmem_slot + 1);
+
+  const int warp = threadIdx.x >> 5;
+  const int lane = threadIdx.x & 31;
+  const int N = args.n_tile;
+
+  if (threadIdx.x == 0) {
+    for (int s = 0; s < SA; ++s) {
+      mbar_init(bar_afull + 8 * s, 1);
+      mbar_init(bar_asplit + 8 * s, 4);
+      mbar_init(bar_aempty + 8 * s, 1);
+    }
+    for (int s = 0; s < SB; ++s) {
+      mbar_init(bar_bfull + 8 * s, 1);
+      mbar_init(bar_bempty + 8 * s, 1);
+    }
+    mbar_init(bar_dfull, 1);
+    mbar_init(bar_dempty, 8);
+    mbar_init(bar_lempty, 8);
+    mbar_init(bar_drain, 1);
+    *abort_flag = 0;
+    fence_mbar_init();
+  }
+  if (warp == 0 && lane == 0) {
+    tma_prefetch_desc(&tmA);
+    tma_prefetch_desc(&tmB);
+  }
+  if (warp == 1) {
+    tmem_alloc(smem_u32(tmem_slot), args.tmem_cols);
+    tmem_relinquish();
+  }
+  tc_fence_before();
+  __syncthreads();
+  tc_fence_after();
+  const uint32_t tmem_base = *tmem_slot;
+  const uint32_t tm_d = tmem_base;
+  const uint32_t tm_l = tmem_base + kWideMaxN;
+
+  long long u0, u1;
+  cta_range(args, u0, u1);
+  const uint64_t lim = args.wait_ns;
+  long long issued_a = 0, issued_b = 0;
+
+  // Registers are rebalanced per warpgroup (setmaxnreg, executed by all four
+  // warps of a group) at the head of each group's branch, so that the
+  // group's code is compiled for its own count.
+  const int wg = warp >> 2;
+  if (wg == 0) {
+    regs_dec_56();
+    if (warp == 0) {
+      // ---------------------------------------------------------- A producer
+      if (lane == 0) {
+        Ring ra;
+        UnitWalk w;
+        w.init(u0, args);
+        long long i = 0;
+        for (long long u = u0; u < u1; ++u, ++i, ra.next(SA), w.next(args)) {
+          if (!mbar_wait(bar_aempty + 8 * ra.s, ra.ph ^ 1u, abort_flag, lim)) break;
+          const uint32_t afull = bar_afull + 8 * ra.s;
+          const uint32_t adst = smem_u32(a_ring + ra.s * kABytes);
+          mbar_expect_tx(afull, kABytes);
+          tma_load_3d(adst, &tmA, afull, w.sk * kBK, w.mt * kBM, w.pp);
+          tma_load_3d(adst + 16384, &tmA, afull, w.sk * kBK + 32, w.mt * kBM, w.pp);
+          issued_a = i + 1;
+        }
+      }
+      __syncwarp();
+    } else if (warp == 2) {
+      // ---------------------------------------------------------- B producer
+      if (lane == 0) {
+        const uint32_t b_tx = N * 128u;
+        Ring rb;
+        UnitWalk w;
+        w.init(u0, args);
+        long long i = 0;
+        for (long long u = u0; u < u1; ++u, ++i, rb.next(SB), w.next(args)) {
+          if (!mbar_wait(bar_bempty + 8 * rb.s, rb.ph ^ 1u, abort_flag, lim)) break;
+          const uint32_t bfull = bar_bfull + 8 * rb.s;
+          const uint32_t bdst = smem_u32(b_ring + rb.s * args.b_bytes);
+          const int brow = w.pp * args.S_k + w.sk * kBK;
+          mbar_expect_tx(bfull, b_tx);
+          for (int j = 0; j < N / 64; ++j) tma_load_2d(bdst + j * 8192, &tmB, bfull, w.nt * N + 64 * j, brow);
+          issued_b = i + 1;
+        }
+      }
+      __syncwarp();
+    } else if (warp == 1) {
+      // ---------------------------------------------------------- MMA issuer
+      if (lane == 0) {
+        const uint32_t idesc = idesc_f16(0u, 0u, 1u, kBM, N);
+        long long u = u0, cc = 0;
+        Ring ra, rb;
+        int seg = 0;
+        bool ok = true;
+        while (ok && u < u1) {
+          const UnitPos p0 = decode(u, args);
+          const long long seg_end = min_ll(u1, u + (args.kblocks - p0.kb));
+          if (!mbar_wait(bar_lempty, static_cast<uint32_t>((seg & 1) ^ 1), abort_flag, lim)) break;
+          bool first_in_seg = true;
+          while (u < seg_end) {
+            const long long chunk_end = min_ll(seg_end, u + args.kc);
+            // single-buffered D: the previous chunk must have been drained
+            if (!mbar_wait(bar_dempty, static_cast<uint32_t>((cc & 1) ^ 1), abort_flag, lim)) {
+              ok = false;
+              break;
+            }
+            tc_fence_after();
+            const long long chunk_start = u;
+            for (; u < chunk_end; ++u, ra.next(SA), rb.next(SB)) {
+              if (!mbar_wait(bar_asplit + 8 * ra.s, ra.ph, abort_flag, lim) ||
+                  !mbar_wait(bar_bfull + 8 * rb.s, rb.ph, abort_flag, lim)) {
+                ok = false;
+                break;
+              }
+              tc_fence_after();
+              const uint32_t abase = smem_u32(a_ring + ra.s * kABytes);
+              const uint32_t bbase = smem_u32(b_ring + rb.s * args.b_bytes);
+              // K-major A: 128-byte rows in 1024-byte 8-row atoms (SBO); a
+              // 16-deep K step moves the start address by 32 bytes (2 in the
+              // >> 4 field).  MN-major B: as in the narrow kernel.
+              const uint64_t ah0 = smem_desc_sw128(abase, 16, 1024);
+              const uint64_t al0 = smem_desc_sw128(abase + 16384, 16, 1024);
+              const uint64_t b0 = smem_desc_sw128(bbase, 8192, 1024);
+  #pragma unroll
+              for (int ks = 0; ks < kBK / 16; ++ks) {
+                const uint32_t acc_d = (u == chunk_start && ks == 0) ? 0u : 1u;
+                const uint32_t acc_l = (first_in_seg && ks == 0) ? 0u : 1u;
+                const uint64_t bk = b0 + static_cast<uint64_t>(ks * 128);
+                tc_mma_f16(tm_d, ah0 + static_cast<uint64_t>(ks * 2), bk, idesc, acc_d);
+                tc_mma_f16(tm_l, al0 + static_cast<uint64_t>(ks * 2), bk, idesc, acc_l);
+              }
+              first_in_seg = false;
+              tc_commit(bar_aempty + 8 * ra.s);
+              tc_commit(bar_bempty + 8 * rb.s);
+            }
+            if (!ok) break;
+            if (!args.drop_commit) tc_commit(bar_dfull);
+            ++cc;
+          }
+          ++seg;
+        }
+      }
+      __syncwarp();
+    }
+  } else if (wg == 1) {
+    regs_dec_120();
+    // ---------------------------------------------------------- split warps
+    const int r = threadIdx.x - kWideSplitWarp0 * 32;  // tile row of this thread
+    Ring ra;
+    for (long long u = u0; u < u1; ++u, ra.next(SA)) {
+      if (!warp_wait(bar_afull + 8 * ra.s, ra.ph, abort_flag, lim, lane)) {
+        *abort_flag = 1;
+        break;
+      }
+      split_row_to_smem(a_ring + ra.s * kABytes, r);
+      fence_proxy_async_smem();  // the generic-proxy stores, before the MMA reads them
+      __syncwarp();
+      if (lane == 0) mbar_arrive(bar_asplit + 8 * ra.s);
+    }
+  } else {
+    regs_inc_168();
+    // ---------------------------------------------------------- epilogue
+    const int q = warp & 3;                     // TMEM lane quadrant of this warp
+    const int cb = ((warp - kWideEpiWarp0) >> 2) * 128;  // column half
+    const int ncols = N - cb < 128 ? N - cb : 128;
+    const uint32_t lane_off = static_cast<uint32_t>(32 * q) << 16;
+    long long u = u0, cc = 0;
+    bool ok = true;
+    float nonfinite = 0.0f;
+    float S[128];
+    while (ok && u < u1) {
+      const UnitPos p0 = decode(u, args);
+      const long long seg_end = min_ll(u1, u + (args.kblocks - p0.kb));
+      const bool whole = (p0.kb == 0) && (seg_end - u == args.kblocks);
+      const long long nch = (seg_end - u + args.kc - 1) / args.kc;
+      const int row = p0.mt * kBM + 32 * q + lane;
+      for (long long c = 0; c < nch; ++c, ++cc) {
+        if (!warp_wait(bar_dfull, static_cast<uint32_t>(cc & 1), abort_flag, lim, lane)) {
+          ok = false;
+          break;
+        }
+        tc_fence_after();
+#pragma unroll
+        for (int c0 = 0; c0 < 128; c0 += 16) {
+          if (c0 < ncols) {
+            uint32_t rd[16];
+            tc_ld_32x32b_x16(tm_d + lane_off + cb + c0, rd);
+            tc_wait_ld();
+#pragma unroll
+            for (int j = 0; j < 16; ++j)
+              S[c0 + j] = (c == 0) ? __uint_as_float(rd[j]) : S[c0 + j] + __uint_as_float(rd[j]);
+          }
+        }
+        tc_fence_before();
+        __syncwarp();
+        if (lane == 0) mbar_arrive(bar_dempty);
+      }
+      if (!ok) break;
+      // segment done: Y = S + 2^-11 L
+      tc_fence_after();
+      const bool row_ok = row < args.M;
+      float* crow = args.C + static_cast<long long>(row) * args.ldc;
+      const bool vec = ((args.ldc & 3) == 0) && ((reinterpret_cast<uintptr_t>(args.C) & 15) == 0);
+      const bool plain = whole && !args.accumulate;
+#pragma unroll
+      for (int c0 = 0; c0 < 128; c0 += 16) {
+        if (c0 < ncols) {
+          uint32_t rl[16];
+          tc_ld_32x32b_x16(tm_l + lane_off + cb + c0, rl);
+          tc_wait_ld();
+          float v[16];
+#pragma unroll
+          for (int j = 0; j < 16; ++j) v[j] = fmaf(__uint_as_float(rl[j]), 0.00048828125f, S[c0 + j]);
+          if (cb == 0 && c0 == 0) nonfinite = __fmaf_rn(v[0], 0.0f, nonfinite);
+          const int col0 = p0.nt * N + cb + c0;
+          if (row_ok && col0 < args.N) {
+            if (vec && col0 + 16 <= args.N) {
+#pragma unroll
+              for (int j = 0; j < 16; j += 4) {
+                const float4 w4 = make_float4(v[j], v[j + 1], v[j + 2], v[j + 3]);
+                float4* dst = reinterpret_cast<float4*>(crow + col0 + j);
+                if (plain)
+                  *dst = w4;
+                else
+                  atomicAdd(dst, w4);
+              }
+            } else {
+#pragma unroll
+              for (int j = 0; j < 16; ++j) {
+                if (col0 + j < args.N) {
+                  if (plain)
+                    crow[col0 + j] = v[j];
+                  else
+                    atomicAdd(crow + col0 + j, v[j]);
+                }
+              }
+            }
+          }
+        }
+      }
+      tc_fence_before();
+      __syncwarp();
+      if (lane == 0) mbar_arrive(bar_lempty);
+      u = seg_end;
+    }
+    if (!ok) *abort_flag = 1;
+    if (nonfinite != 0.0f) atomicOr(args.flags, SHG_FLAG_RANGE);
+  
+  }
+
+  __syncthreads();
+  if (*abort_flag) {
+    // wait (bounded) for this CTA's TMA copies still in flight
+    if (warp == 0 && lane == 0) {
+      for (long long j = (issued_a > SA ? issued_a - SA : 0); j < issued_a; ++j)
+        wait_time_only(bar_afull + 8 * static_cast<int>(j % SA), static_cast<uint32_t>((j / SA) & 1), lim);
+    }
+    if (warp == 2 && lane == 0) {
+      for (long long j = (issued_b > SB ? issued_b - SB : 0); j < issued_b; ++j)
+        wait_time_only(bar_bfull + 8 * static_cast<int>(j % SB), static_cast<uint32_t>((j / SB) & 1), lim);
+    }
+    if (warp == 1 && lane == 0) {
+      tc_commit(bar_drain);
+      wait_time_only(bar_drain, 0, lim);
+    }
+    if (threadIdx.x == 0) atomicOr(args.flags, SHG_FLAG_TIMEOUT);
+  }
+  __syncthreads();
+  if (warp == 1) {
+    tc_fence_after();
+    tmem_dealloc(tmem_base, args.tmem_cols);
+  }
+}
+
 // ---------------------------------------------------------------- host side
 using EncodeTiled = CUresult (*)(CUtensorMap*, CUtensorMapDataType, cuuint32_t, void*, const cuuint64_t*,
                                  const cuuint64_t*, const cuuint32_t*, const cuuint32_t*,
@@ -716,6 +1067,23 @@ int launch(const CUtensorMap& ta, const CUtensorMap& tb, const CUtensorMap& tb2,
 }
 
 
+int launch_wide(const CUtensorMap& ta, const CUtensorMap& tb, const TcArgs& a, int grid, size_t smem,
+                cudaStream_t st) {
+  static size_t configured[64] = {};
+  int dev = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 64) return SHG_ERR_CUDA;
+  if (configured[dev] != smem) {
+    const int carve = static_cast<int>((smem * 100 + kMaxSmem - 1) / kMaxSmem);
+    if (cudaFuncSetAttribute(tc_wide_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, static_cast<int>(smem)) !=
+            cudaSuccess ||
+        cudaFuncSetAttribute(tc_wide_kernel, cudaFuncAttributePreferredSharedMemoryCarveout, carve) != cudaSuccess)
+      return SHG_ERR_CUDA;
+    configured[dev] = smem;
+  }
+  tc_wide_kernel<<<grid, kWideThreads, smem, st>>>(ta, tb, a);
+  return cuda_status(cudaGetLastError());
+}
+
 // ------------------------------------------------------------ autotuner
 // Shape class: operand layout and piece type, the N tiling, and M and K to
 // within a factor of two.  The cache is small (one entry per class seen).
@@ -770,7 +1138,13 @@ TcConfig default_config() {
   // every 16 blocks and more, lose too many low bits of the hi product)
   c.kc = std::max(2, std::min(env_int("SHG_DRAIN_KBLOCKS", 4), 8));
   c.groups = env_int("SHG_NGROUPS", 1) != 0 ? 1 : 0;
+  c.wide = env_int("SHG_WIDE", 1) != 0 ? 1 : 0;
   return c;
+}
+
+// Whether a call runs the wide-tile kernel under configuration c.
+bool use_wide(int amaj, int bmode, int pieces, int64_t N, const TcConfig& c) {
+  return amaj == A_KMAJ && bmode == B_F16 && pieces == 2 && N > 128 && c.wide != 0;
 }
 
 }  // namespace
@@ -821,8 +1195,26 @@ int tc_autotune(int amaj, int bmode, int pieces, int64_t M, int64_t N, int64_t S
           c.sb = sb;
           c.kc = kc;
           c.groups = g;
+          c.wide = 0;
           cand.push_back(c);
         }
+  {
+    // the wide-tile kernel: 2-4 A stages and 2-3 B stages of 32 KB fit in
+    // shared memory; its single-buffered hi accumulator favours long chunks
+    TcConfig probe;
+    if (use_wide(amaj, bmode, pieces, N, probe))
+      for (int sa : {2, 3, 4})
+        for (int sb : {2, 3})
+          for (int kc : {4, 8}) {
+            TcConfig c;
+            c.sa = sa;
+            c.sb = sb;
+            c.kc = kc;
+            c.groups = 1;
+            c.wide = 1;
+            cand.push_back(c);
+          }
+  }
   cudaEvent_t e0 = nullptr, e1 = nullptr;
   if (cudaEventCreate(&e0) != cudaSuccess || cudaEventCreate(&e1) != cudaSuccess) {
     if (e0) cudaEventDestroy(e0);
@@ -889,13 +1281,23 @@ int tc_gemm_impl(int amaj, int bmode, int pieces, int64_t M, int64_t N, int64_t 
   a.M = static_cast<int>(M);
   a.N = static_cast<int>(N);
   const int n_lo = (bmode == B_SPLIT || bmode == B_SPLIT_PRE) ? 1 : pieces - 1;
+  TcConfig cfg = default_config();
+  bool tuned = false;
+  if (force) cfg = *force;
+  else tuned = tc_tuned(amaj, bmode, pieces, M, N, K, P, &cfg);
+  const bool wide = use_wide(amaj, bmode, pieces, N, cfg);
+  // the wide kernel's single-buffered hi accumulator: drain every 8 K
+  // blocks unless a tuned or forced configuration says otherwise
+  if (wide && !force && !tuned && std::getenv("SHG_DRAIN_KBLOCKS") == nullptr) cfg.kc = 8;
   // TMEM: D0, D1, lo accumulator(s), then at least two A stages of pieces x 32 columns
   int nt = 0;
   n_tiling(bmode, pieces, N, &nt, &a.n_tiles);
+  if (wide) {
+    // tiles of up to 256 columns, multiples of 64
+    a.n_tiles = static_cast<int>((N + kWideMaxN - 1) / kWideMaxN);
+    nt = static_cast<int>(((N + a.n_tiles - 1) / a.n_tiles + 63) / 64 * 64);
+  }
   a.n_tile = nt;
-  TcConfig cfg = default_config();
-  if (force) cfg = *force;
-  else tc_tuned(amaj, bmode, pieces, M, N, K, P, &cfg);
   a.m_tiles = static_cast<int>((M + kBM - 1) / kBM);
   a.kb_per_p = static_cast<int>((S_k + kBK - 1) / kBK);
   a.kblocks = a.kb_per_p * static_cast<int>(P);
@@ -905,12 +1307,17 @@ int tc_gemm_impl(int amaj, int bmode, int pieces, int64_t M, int64_t N, int64_t 
   a.ldc = ldc;
   a.accumulate = accumulate;
   a.flags = d_flags;
-  const int acc_cols = (2 + n_lo) * nt;
-  a.st = std::min(4, (512 - acc_cols) / (pieces * 32));
-  if (a.st < 2) return SHG_ERR_UNSUPPORTED;
-  uint32_t cols = 32;
-  while (cols < static_cast<uint32_t>(acc_cols + a.st * pieces * 32)) cols <<= 1;
-  a.tmem_cols = cols;
+  if (wide) {
+    a.st = 0;  // A is read from shared memory
+    a.tmem_cols = 512;
+  } else {
+    const int acc_cols = (2 + n_lo) * nt;
+    a.st = std::min(4, (512 - acc_cols) / (pieces * 32));
+    if (a.st < 2) return SHG_ERR_UNSUPPORTED;
+    uint32_t cols = 32;
+    while (cols < static_cast<uint32_t>(acc_cols + a.st * pieces * 32)) cols <<= 1;
+    a.tmem_cols = cols;
+  }
   a.b_bytes = (bmode == B_SPLIT || bmode == B_SPLIT_PRE) ? static_cast<uint32_t>(nt) * 256u
                                                         : static_cast<uint32_t>(nt) * 128u;
   const uint32_t bar_bytes = 1024;
@@ -979,6 +1386,7 @@ int tc_gemm_impl(int amaj, int bmode, int pieces, int64_t M, int64_t N, int64_t 
       return SHG_ERR_CUDA;
   }
 
+  if (wide) return launch_wide(ta, tb, a, grid, smem, stream);
   if (amaj == A_KMAJ) {
     if (bmode == B_F16) return launch<A_KMAJ, B_F16, 2>(ta, tb, tb2, a, grid, smem, stream);
     if (bmode == B_BF16 && pieces == 2) return launch<A_KMAJ, B_BF16, 2>(ta, tb, tb2, a, grid, smem, stream);

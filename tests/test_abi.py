@@ -94,7 +94,7 @@ def test_host_argument_validation(lib):
                         null) == 1
     # autotuner: bad shapes, reps out of range and the SIMT variant (nothing
     # to tune) are rejected before any launch; lookup of an untuned class
-    cfg = (ctypes.c_int32 * 5)()
+    cfg = (ctypes.c_int32 * 6)()
     assert lib.shg_autotune_project(0, 8, 8, one, 8, 0, one, 8, one, 8, 0, 3, one, null, cfg) == 1
     assert lib.shg_autotune_project(8, 8, 8, one, 8, 0, one, 8, one, 8, 0, 0, one, null, cfg) == 1
     assert lib.shg_autotune_project(8, 8, 8, one, 8, 0, one, 8, one, 8, 3, 3, one, null, cfg) == 7

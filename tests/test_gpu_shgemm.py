@@ -77,6 +77,30 @@ def test_shgemm_f16_parity(shg, m, n, k, trans):
     assert not viol.any(), f"{viol.sum()} elements exceed the Sec. 4.3 bound"
 
 
+@pytest.mark.parametrize("m,n,k", [(256, 512, 200), (1000, 300, 256), (200, 640, 512), (77, 1536, 144),
+                                   (513, 2048, 160), (300, 1000, 320)])
+@pytest.mark.parametrize("wide", ["1", "0"])
+def test_shgemm_f16_tile_widths(shg, monkeypatch, m, n, k, wide):
+    """k > 128 runs on output tiles of up to 256 columns whose A operand is
+    split in shared memory (the default) or on 128-column tiles split into
+    tensor memory (SHG_WIDE=0); both against the exact product with the
+    same tolerances as above."""
+    monkeypatch.setenv("SHG_WIDE", wide)
+    A = uniform(m, n, seed=12)
+    Om = omega_f16(n, k, seed=13)
+    Y = shg.shgemm_project(padded_f32(A), padded_omega(Om, (k + 7) // 8 * 8), "f16").cpu().numpy()
+    ref = OS.project_exact(A, Om)
+    err = OS.rel_fro_error(Y, ref)
+    Ys = shg.shgemm_project(padded_f32(A), padded_omega(Om, (k + 7) // 8 * 8), "fp32").cpu().numpy()
+    err_simt = OS.rel_fro_error(Ys, ref)
+    err_repr = OS.rel_fro_error(OS.shgemm_emulated(A, Om), ref)
+    assert err <= 1e-5, (err, err_simt)
+    assert err <= max(2.0 * err_simt, 2.0 * err_repr), (err, err_simt, err_repr)
+    bound = OS.elementwise_bound(A, Om) + \
+        OS.U_FP16 ** 2 * (np.abs(A.astype(np.float64)) @ np.abs(Om.astype(np.float64)))
+    assert not (np.abs(Y - ref) > bound * (1 + 1e-6) + 1e-30).any()
+
+
 def test_shgemm_ld_and_offsets(shg):
     """Leading dimensions larger than the row length on A, Omega and Y."""
     m, n, k = 200, 700, 40
