@@ -663,7 +663,8 @@ __global__ void __launch_bounds__(kThreads, 1)
 // K-major FP16 operand layout (thread r owns row r: its FP32 bytes, K 0..31
 // in the first box and K 32..63 in the second, become its hi row and its lo
 // row, in the same 128-byte swizzle).  The MMA issuer waits for the drain
-// of D before each chunk's first MMA.
+// of D before each chunk's first hi MMA, after it has queued that unit's lo
+// MMAs, which keep the tensor pipe busy meanwhile.
 //
 // 16 warps: 0 A producer, 1 MMA issuer and TMEM owner, 2 B producer, 3 idle,
 // 4..7 split (one row per thread), 8..15 epilogue (TMEM lane quadrant
@@ -829,12 +830,6 @@ __global__ void __launch_bounds__(kWideThreads, 1)
           bool first_in_seg = true;
           while (u < seg_end) {
             const long long chunk_end = min_ll(seg_end, u + args.kc);
-            // single-buffered D: the previous chunk must have been drained
-            if (!mbar_wait(bar_dempty, static_cast<uint32_t>((cc & 1) ^ 1), abort_flag, lim)) {
-              ok = false;
-              break;
-            }
-            tc_fence_after();
             const long long chunk_start = u;
             for (; u < chunk_end; ++u, ra.next(SA), rb.next(SB)) {
               if (!mbar_wait(bar_asplit + 8 * ra.s, ra.ph, abort_flag, lim) ||
@@ -851,14 +846,25 @@ __global__ void __launch_bounds__(kWideThreads, 1)
               const uint64_t ah0 = smem_desc_sw128(abase, 16, 1024);
               const uint64_t al0 = smem_desc_sw128(abase + 16384, 16, 1024);
               const uint64_t b0 = smem_desc_sw128(bbase, 8192, 1024);
-  #pragma unroll
-              for (int ks = 0; ks < kBK / 16; ++ks) {
-                const uint32_t acc_d = (u == chunk_start && ks == 0) ? 0u : 1u;
-                const uint32_t acc_l = (first_in_seg && ks == 0) ? 0u : 1u;
-                const uint64_t bk = b0 + static_cast<uint64_t>(ks * 128);
-                tc_mma_f16(tm_d, ah0 + static_cast<uint64_t>(ks * 2), bk, idesc, acc_d);
-                tc_mma_f16(tm_l, al0 + static_cast<uint64_t>(ks * 2), bk, idesc, acc_l);
+              // the lo product first: L is not drained within a segment, so
+              // these MMAs keep the tensor pipe busy while the epilogue drains
+              // D at a chunk boundary
+#pragma unroll
+              for (int ks = 0; ks < kBK / 16; ++ks)
+                tc_mma_f16(tm_l, al0 + static_cast<uint64_t>(ks * 2), b0 + static_cast<uint64_t>(ks * 128), idesc,
+                           (first_in_seg && ks == 0) ? 0u : 1u);
+              if (u == chunk_start) {
+                // single-buffered D: the previous chunk must have been drained
+                if (!mbar_wait(bar_dempty, static_cast<uint32_t>((cc & 1) ^ 1), abort_flag, lim)) {
+                  ok = false;
+                  break;
+                }
+                tc_fence_after();
               }
+#pragma unroll
+              for (int ks = 0; ks < kBK / 16; ++ks)
+                tc_mma_f16(tm_d, ah0 + static_cast<uint64_t>(ks * 2), b0 + static_cast<uint64_t>(ks * 128), idesc,
+                           (u == chunk_start && ks == 0) ? 0u : 1u);
               first_in_seg = false;
               tc_commit(bar_aempty + 8 * ra.s);
               tc_commit(bar_bempty + 8 * rb.s);
