@@ -36,15 +36,13 @@ M = N = 16384
 
 # DRAM bytes (dram__bytes_read.sum + dram__bytes_write.sum) of one SHGEMM-FP16
 # launch at m = n = 16384, from one-pass ncu captures of
-# `bench.py --case 16384 K`, with the SHA-256 of the kernel sources they
-# apply to; reported only while the sources are unchanged.  (Captured on
-# sources 25998ac9...; the one later change is host-side grid sizing inside
-# the batched path's SM share, which leaves the device code and this
-# benchmark's launches as they were.)
+# `bench.py --case 16384 K` (128-column tiles for k = 64, 128; 256-column tiles
+# for k = 256, 512), with the SHA-256 of the kernel sources they apply to;
+# reported only while the sources are unchanged.
 TRAFFIC = {
     "sources": ["paper_2304_04612_gb300/csrc/shgemm_tc.cu", "paper_2304_04612_gb300/csrc/ptx.cuh"],
-    "sha256": "9c0e39d7442a151981bb30748cc06f42027db7c4c9eca5981cf7d5e529750f10",
-    "bytes_per_launch": {"64": 1093532416, "128": 1111054336, "256": 1123832320, "512": 1153206016},
+    "sha256": "5aed4d0cb5032d7657ceeb7cc9855cb916f30f604ab954472c42058527c88cca",
+    "bytes_per_launch": {"64": 1093736704, "128": 1109490688, "256": 1148108800, "512": 1170169344},
 }
 
 
@@ -315,7 +313,8 @@ def main():
                     "unit": "TFLOP/s", "frac": f0 / t0s / 1e12 / pk["bf16_tflops"], "traffic": traffic,
                     "peak_source": f"{src} bf16_tflops (burst; FP16 and BF16 dense rates are equal)"}
     roofline.update({
-        "kernel": f"tc_gemm_kernel<K-major A, FP16 Omega> (SHGEMM-FP16), m=n={M}, k={k0}",
+        "kernel": (f"tc_wide_kernel (SHGEMM-FP16, 256-column tiles), m=n={M}, k={k0}" if tuned[str(k0)].get("wide")
+                   else f"tc_gemm_kernel<K-major A, FP16 Omega> (SHGEMM-FP16, 128-column tiles), m=n={M}, k={k0}"),
         "share_of_step": per_k_ms[k0] / sum(per_k_ms.values()),
         "algorithmic": {"bytes": b0, "tensor_flops_4mnk": f0},
         "per_k": {str(k): roof[k] for k in KS}})
