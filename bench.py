@@ -330,7 +330,8 @@ def main():
             "gpu_launches": len(KS) * args.steps, "clocks": clk, "roofline": roofline}
 
     if rank == 0 and not args.quick:
-        side = side_measurements(shg, OS, torch, dev, A, A_host, Om, Om_host, Ys, flags, stream, pk)
+        side = side_measurements(shg, OS, torch, dev, A, A_host, Om, Om_host, Ys, flags, stream, pk,
+                                 clk_mhz=clk.get("sm_mhz"))
         line.update(side)
     if rank == 0:
         print(json.dumps(line), flush=True)
@@ -446,7 +447,7 @@ def time_ms(torch, stream, fn, reps=5, flush=None):
     return float(np.median(ts))
 
 
-def side_measurements(shg, OS, torch, dev, A, A_host, Om, Om_host, Ys, flags, stream, pk):
+def side_measurements(shg, OS, torch, dev, A, A_host, Om, Om_host, Ys, flags, stream, pk, clk_mhz=None):
     out = {}
     flush_buf = torch.empty(512 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)
 
@@ -457,7 +458,7 @@ def side_measurements(shg, OS, torch, dev, A, A_host, Om, Om_host, Ys, flags, st
     from oracle.lowp import encode_bf16
     cmp = {}
     Omb = torch.from_numpy(encode_bf16(OS.bf16_omega(Om_host)).view(np.int16)).to(dev).view(torch.bfloat16)
-    for variant, om in (("fp32", Om), ("bf16x3", Omb), ("f16", Om)):
+    for variant, om in (("fp32", Om), ("bf16x3", Omb), ("tf32", Om), ("f16", Om)):
         per = {}
         for k in KS:
             reps = 2 if variant == "fp32" else 5
@@ -467,11 +468,32 @@ def side_measurements(shg, OS, torch, dev, A, A_host, Om, Om_host, Ys, flags, st
         cmp[variant] = per
     out["sweep_16384"] = cmp
     out["speedup_vs_fp32_simt"] = {str(k): cmp["fp32"][str(k)]["ms"] / cmp["f16"][str(k)]["ms"] for k in KS}
+    # SHGEMM-TF32 (full exponent range) against its own floor: A's bytes at the
+    # measured HBM rate or 4mnk at half the FP16 tensor rate (TF32 runs at half)
+    tf = {}
+    for k in KS:
+        t = cmp["tf32"][str(k)]["ms"] * 1e-3
+        byts = 4.0 * M * N + 2.0 * N * k + 4.0 * M * k
+        floor = max(byts / (pk["hbm_gbs"] * 1e9), 4.0 * M * N * k / (0.5 * pk["bf16_tflops"] * 1e12))
+        tf[str(k)] = {"frac_of_floor": floor / t,
+                      "bound": "hbm" if byts / (pk["hbm_gbs"] * 1e9) >= 4.0 * M * N * k / (0.5 * pk["bf16_tflops"] * 1e12)
+                      else "tensor (TF32 = half the FP16 rate)"}
+    out["tf32_roofline"] = tf
+    # the FP32 SIMT path against the FFMA peak: 128 FP32 FMA per clock per SM
+    # (4 sub-partitions x 32 lanes) x 2 flop x SMs x the SM clock under load
+    sms = torch.cuda.get_device_properties(dev).multi_processor_count
+    mhz = clk_mhz if clk_mhz else pk.get("sm_max_mhz", 2070.0)
+    ffma_peak = 128 * 2 * sms * mhz * 1e6 / 1e12
+    out["fp32_simt_roofline"] = {"bound": "alu", "peak": ffma_peak, "unit": "TFLOP/s",
+                                 "peak_derivation": f"128 FFMA/clk/SM x 2 x {sms} SMs x {mhz:.0f} MHz",
+                                 "per_k": {str(k): {"achieved": cmp["fp32"][str(k)]["tflops_2mnk"],
+                                                    "frac": cmp["fp32"][str(k)]["tflops_2mnk"] / ffma_peak}
+                                           for k in KS}}
 
     # sampled-row error vs the FP64 oracle (same inputs), per variant
     rows = np.random.default_rng(0).choice(M, 128, replace=False)
     errs = {}
-    for variant, om in (("f16", Om), ("fp32", Om), ("bf16x3", Omb)):
+    for variant, om in (("f16", Om), ("fp32", Om), ("bf16x3", Omb), ("tf32", Om)):
         e = {}
         for k in KS:
             Y = shg.shgemm_project(A, om[:, :k], variant, out=Ys[k], flags=flags, check=True, stream=stream)
@@ -495,23 +517,59 @@ def side_measurements(shg, OS, torch, dev, A, A_host, Om, Om_host, Ys, flags, st
         small[str(mm)] = per
     out["sweep_small"] = small
 
-    # end to end through host buffers: H2D of A and Omega, the sweep, D2H of Y
+    # end to end through host buffers: H2D of A and Omega, the sweep, D2H of Y.
+    # A crosses in row blocks on four copy streams; the four projections of a
+    # block start as soon as its copy has landed and its rows of every Y go
+    # back on a fifth stream, so the copies of later blocks overlap the
+    # projections of earlier ones.
     A_pin = torch.from_numpy(A_host).pin_memory()
     Om_pin = torch.from_numpy(Om_host).pin_memory()
     Yh = {k: torch.empty(M, k, dtype=torch.float32).pin_memory() for k in KS}
+    nblk, ncs = 8, 4
+    rows_per = M // nblk
+    cstreams = [torch.cuda.Stream(dev) for _ in range(ncs)]
+    dstream = torch.cuda.Stream(dev)
 
     def e2e_step():
-        A.copy_(A_pin, non_blocking=True)
-        Om.copy_(Om_pin, non_blocking=True)
-        for k in KS:
-            shg.shgemm_project(A, Om[:, :k], "f16", out=Ys[k], flags=flags, check=False, stream=stream)
-            Yh[k].copy_(Ys[k], non_blocking=True)
+        with torch.cuda.stream(cstreams[0]):
+            Om.copy_(Om_pin, non_blocking=True)
+        om_ready = torch.cuda.Event()
+        om_ready.record(cstreams[0])
+        stream.wait_event(om_ready)
+        for b in range(nblk):
+            r0, r1 = b * rows_per, (b + 1) * rows_per
+            cs = cstreams[b % ncs]
+            with torch.cuda.stream(cs):
+                A[r0:r1].copy_(A_pin[r0:r1], non_blocking=True)
+            landed = torch.cuda.Event()
+            landed.record(cs)
+            stream.wait_event(landed)
+            for k in KS:
+                shg.shgemm_project(A[r0:r1], Om[:, :k], "f16", out=Ys[k][r0:r1], flags=flags, check=False,
+                                   stream=stream)
+            done = torch.cuda.Event()
+            done.record(stream)
+            dstream.wait_event(done)
+            with torch.cuda.stream(dstream):
+                for k in KS:
+                    Yh[k][r0:r1].copy_(Ys[k][r0:r1], non_blocking=True)
+        back = torch.cuda.Event()
+        back.record(dstream)
+        stream.wait_event(back)
     e2e_step()
-    ms = time_ms(torch, stream, e2e_step, reps=3)
+    torch.cuda.synchronize()
+    ms = time_ms(torch, stream, e2e_step, reps=10)
+    shg.check_flags(flags, "e2e")
+    ok_rows = np.random.default_rng(1).choice(M, 16, replace=False)
+    e2e_err = OS.rel_fro_error(Yh[512][ok_rows].numpy(), OS.project_exact(A_host[ok_rows], Om_host))
     h2d = A_host.nbytes + Om_host.nbytes
     d2h = sum(M * k * 4 for k in KS)
     out["e2e"] = {"value": sum(2.0 * M * N * k for k in KS) / (ms * 1e-3) / 1e12, "unit": "TFLOP/s",
-                  "ms_per_step": ms, "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h}
+                  "ms_per_step": ms, "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h,
+                  "h2d_gbs_if_copy_bound": h2d / (ms * 1e-3) / 1e9, "reps": 10,
+                  "pipeline": f"A in {nblk} row blocks on {ncs} copy streams, projections per block, Y rows "
+                              "back on a fifth stream",
+                  "check_rel_err_sampled_rows_k512": e2e_err}
 
     # randomized SVD of the planted 1024^2 matrix and RP-HOSVD of the 512^3 tensor
     out["rsvd_1024"] = rsvd_times(shg, torch, dev, stream)

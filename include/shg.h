@@ -58,7 +58,13 @@ typedef enum shg_variant {
   SHG_SPLIT_F16 = 0,    /* SHGEMM-FP16: A -> FP16 hi + 2^11-scaled FP16 lo, two tensor-core products (Eqs. shgemm-1..3) */
   SHG_SPLIT_BF16X3 = 1, /* A -> three BF16 pieces at 2^0, 2^-8, 2^-16; Omega must be BF16 (RN of the FP16 Omega) */
   SHG_SPLIT_BF16X2 = 2, /* A -> two BF16 pieces; Omega BF16 */
-  SHG_FP32_SIMT = 3     /* plain FP32 SIMT SGEMM with FP16 Omega widened exactly to FP32 (the single-precision baseline) */
+  SHG_FP32_SIMT = 3,    /* plain FP32 SIMT SGEMM with FP16 Omega widened exactly to FP32 (the single-precision baseline) */
+  SHG_SPLIT_TF32 = 4,   /* SHGEMM-TF32 (Sec. 4.2): A -> TF32 hi + 2^11-scaled TF32 lo, FP16 Omega widened exactly to TF32;
+                           the full FP32 exponent range of A at half the FP16 tensor rate */
+  SHG_SPLIT_AUTO = 5    /* SHGEMM-FP16, and when its range check trips (some |a| >= 65520, Sec. 4.2 / Sec. 5.1's
+                           Cauchy matrices) the call is redone in the full exponent range (SHGEMM-TF32 for A Omega,
+                           FP32 SIMT for products whose A operand is transposed or FP32 on both sides); the choice
+                           is made on the host after synchronising the stream */
 } shg_variant;
 
 /*
@@ -140,10 +146,17 @@ int shg_sparse_sign_f16(uint64_t seed, uint64_t offset, int64_t rows, int64_t co
  *   trans_a = 1: A is n x m (lda >= m), Y = A^T * Omega.
  *   Omega: n x k (ldo >= k), FP16 bits (BF16 bits for SHG_SPLIT_BF16X*).
  *   Y: m x k FP32 (ldy >= k), overwritten.
- * variant: shg_variant (every variant takes trans_a = 0 or 1).
+ * variant: shg_variant.  Every variant takes trans_a = 0 or 1; SHG_SPLIT_TF32
+ * with trans_a = 1 computes in FP32 SIMT (the TF32 kernel reads A K-major).
+ * SHG_SPLIT_AUTO runs SHGEMM-FP16 and, when the range flag trips, redoes
+ * the product with SHG_SPLIT_TF32 and restores *d_flags to its value on
+ * entry; it synchronises `stream` (to read the flag) and may not be used
+ * while the stream is being captured (SHG_ERR_UNSUPPORTED).
  * Device flags: SHG_FLAG_RANGE when some |a| >= 65520 under SHG_SPLIT_F16
  * (its hi piece overflows to infinity; the kernel detects the non-finite
- * output row, so a NaN or infinite input raises the flag as well).
+ * output row, so a NaN or infinite input raises the flag as well); under
+ * SHG_SPLIT_TF32 only for non-finite A or values that round past the
+ * largest finite TF32 number.
  * m, n, k >= 1 and < 2^31.
  */
 int shgemm_project(int64_t m, int64_t n, int64_t k,
@@ -291,8 +304,12 @@ int shg_cholqr2_static(int64_t m, int64_t k, float* X, int64_t ldx, int32_t* d_f
  *   A ~= U diag(S) V^T.  Q_out: NULL or m x k FP32 (ld k), receives Q.
  * variant selects how the projections (Y = A Omega and the power-scheme
  * products) are computed: SHG_SPLIT_F16 / BF16X* (tensor cores, B = Q^T A by
- * the TCEC split) or SHG_FP32_SIMT (every GEMM in FP32 SIMT: the
- * single-precision baseline).  Gram matrices are compensated FP32 sums
+ * the TCEC split), SHG_SPLIT_TF32 (full exponent range: A Omega and
+ * A fp16(Z) by SHGEMM-TF32; A^T fp16(Q) and B = Q^T A in FP32 SIMT),
+ * SHG_SPLIT_AUTO (SHG_SPLIT_F16, switched to SHG_SPLIT_TF32 for the whole
+ * call when the first projection's range check trips; synchronises the
+ * stream once, not under capture) or SHG_FP32_SIMT (every GEMM in FP32
+ * SIMT: the single-precision baseline).  Gram matrices are compensated FP32 sums
  * delivered in FP64, the Cholesky factorisations double-float (see
  * shg_cholqr2); the k x k eigensolver of B B^T is FP32 Jacobi refined by
  * FP64 Rayleigh quotients.

@@ -9,6 +9,8 @@ project_exact       the plain definition: A (FP32 values) times Omega (FP16
                     in Sec. 4.4.1.
 split_f16           the split of Eqs. shgemm-1 and shgemm-2: hi = toLow(a),
                     lo = toLow((a - toF32(hi)) * 2^11), toLow = FP16 RN-even.
+split_tf32          the same split with toLow = TF32 (SHGEMM-TF32, Sec. 4.2:
+                    the full FP32 exponent range).
 shgemm_emulated     hi*Omega + 2^-11 * lo*Omega (Eq. shgemm-3) in float64,
                     i.e. SHGEMM without any accumulation rounding.
 split3_emulated     TCEC-SGEMM (Eq. tcec-5) for two FP32 operands:
@@ -27,7 +29,7 @@ from __future__ import annotations
 
 import numpy as np
 
-from .lowp import FP16, BF16, round_rn, f16_to_f64
+from .lowp import FP16, BF16, TF32, round_rn, f16_to_f64
 
 U_FP32 = 2.0 ** -24      # unit roundoff of FP32 (Eq. rounding-error)
 U_FP16 = 2.0 ** -11      # unit roundoff of FP16 (after Eq. split-matrix-ineq)
@@ -55,6 +57,25 @@ def split_f16(A32: np.ndarray):
     hi = round_rn(a, FP16)
     lo = round_rn((a - hi) * 2.0 ** 11, FP16)
     return hi, lo
+
+
+def split_tf32(A32: np.ndarray):
+    """(hi, lo) of Eqs. shgemm-1 and shgemm-2 with toLow = TF32 (e8m10, RN-even),
+    the SHGEMM-TF32 of Sec. 4.2: hi = RN_tf32(a); lo = RN_tf32((a - hi) * 2^11).
+    TF32 keeps FP32's exponent range, so no |a| is out of range (only values
+    that round past the largest finite TF32 number become infinite)."""
+    a = np.asarray(A32, dtype=np.float32).astype(np.float64)
+    hi = round_rn(a, TF32)
+    lo = round_rn((a - hi) * 2.0 ** 11, TF32)
+    return hi, lo
+
+
+def shgemm_tf32_emulated(A32: np.ndarray, omega_f16: np.ndarray) -> np.ndarray:
+    """hi*Omega + 2^-11 * lo*Omega with the TF32 split, float64 (Eq. shgemm-3;
+    FP16 Omega values are exact in TF32)."""
+    hi, lo = split_tf32(A32)
+    W = f16_to_f64(omega_f16)
+    return hi @ W + (lo @ W) * 2.0 ** -11
 
 
 def shgemm_emulated(A32: np.ndarray, omega_f16: np.ndarray) -> np.ndarray:

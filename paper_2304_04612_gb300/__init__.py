@@ -39,7 +39,7 @@ import torch
 
 from . import _lib
 
-VARIANTS = {"f16": 0, "bf16x3": 1, "bf16x2": 2, "fp32": 3}
+VARIANTS = {"f16": 0, "bf16x3": 1, "bf16x2": 2, "fp32": 3, "tf32": 4, "auto": 5}
 FLAG_RANGE, FLAG_NOT_SPD, FLAG_TIMEOUT = 1, 2, 4
 
 

@@ -140,19 +140,27 @@ HosvdLayout hosvd_layout(const int64_t* d, const int64_t* J) {
 // with no unfolding materialised: mode 0 reads X as an I0 x (I1 I2)
 // matrix, mode 1 through a 3-D tensor map (K index (i0, i2), batched over
 // i0 on the SIMT path), mode 2 as the transposed (I0 I1) x I2 matrix.
+// How a mode projection is computed: SHGEMM-FP16, SHGEMM-TF32 (the
+// transposed mode 2 then in FP32 SIMT) or FP32 SIMT.
+enum ModeProj : int { MP_F16 = 0, MP_TF32 = 1, MP_SIMT = 2 };
+
 int mode_project(int i, const int64_t* d, int64_t J, const float* X, const uint16_t* omega, int64_t ldo, float* W,
-                 int64_t ldw, bool tc, int32_t* d_flags, cudaStream_t st) {
+                 int64_t ldw, int mp, int32_t* d_flags, cudaStream_t st) {
   const int64_t I0 = d[0], I1 = d[1], I2 = d[2];
   if (i == 0) {
-    if (tc) return tc_gemm(A_KMAJ, B_F16, 2, I0, J, I1 * I2, 1, X, I1 * I2, 0, omega, ldo, W, ldw, 0, d_flags, st);
+    if (mp == MP_F16)
+      return tc_gemm(A_KMAJ, B_F16, 2, I0, J, I1 * I2, 1, X, I1 * I2, 0, omega, ldo, W, ldw, 0, d_flags, st);
+    if (mp == MP_TF32) return tc_tf32_gemm(I0, J, I1 * I2, 1, X, I1 * I2, 0, omega, ldo, W, ldw, d_flags, st);
     return simt_gemm(I0, J, I1 * I2, X, I1 * I2, 0, omega, ldo, 1, W, ldw, 0, 1, 0, 0, 0, st);
   }
   if (i == 1) {
-    if (tc) return tc_gemm(A_KMAJ, B_F16, 2, I1, J, I2, I0, X, I2, I1 * I2, omega, ldo, W, ldw, 0, d_flags, st);
+    if (mp == MP_F16)
+      return tc_gemm(A_KMAJ, B_F16, 2, I1, J, I2, I0, X, I2, I1 * I2, omega, ldo, W, ldw, 0, d_flags, st);
+    if (mp == MP_TF32) return tc_tf32_gemm(I1, J, I2, I0, X, I2, I1 * I2, omega, ldo, W, ldw, d_flags, st);
     if (cudaMemset2DAsync(W, ldw * 4, 0, J * 4, I1, st) != cudaSuccess) return SHG_ERR_CUDA;
     return simt_gemm(I1, J, I2, X, I2, 0, omega, ldo, 1, W, ldw, 1, I0, I1 * I2, I2 * ldo, 0, st);
   }
-  if (tc) return tc_gemm(A_MNMAJ, B_F16, 2, I2, J, I0 * I1, 1, X, I2, 0, omega, ldo, W, ldw, 0, d_flags, st);
+  if (mp == MP_F16) return tc_gemm(A_MNMAJ, B_F16, 2, I2, J, I0 * I1, 1, X, I2, 0, omega, ldo, W, ldw, 0, d_flags, st);
   return simt_gemm(I2, J, I0 * I1, X, I2, 1, omega, ldo, 1, W, ldw, 0, 1, 0, 0, 0, st);
 }
 
@@ -178,6 +186,31 @@ struct PhaseEvents {
       if (x) cudaEventDestroy(x);
   }
 };
+
+// The automatic fallback of SHG_SPLIT_AUTO: the device flags word is read
+// before and after the FP16 attempt (synchronising the stream); when the
+// attempt raised SHG_FLAG_RANGE the word is put back as it was and the
+// caller redoes the work in the full exponent range.
+int range_probe_begin(int32_t* d_flags, cudaStream_t st, int32_t* before) {
+  cudaStreamCaptureStatus cap = cudaStreamCaptureStatusNone;
+  if (cudaStreamIsCapturing(st, &cap) != cudaSuccess) return SHG_ERR_CUDA;
+  if (cap != cudaStreamCaptureStatusNone) return SHG_ERR_UNSUPPORTED;
+  if (cudaMemcpyAsync(before, d_flags, sizeof(int32_t), cudaMemcpyDeviceToHost, st) != cudaSuccess ||
+      cudaStreamSynchronize(st) != cudaSuccess)
+    return SHG_ERR_CUDA;
+  return SHG_OK;
+}
+int range_probe_end(int32_t* d_flags, cudaStream_t st, int32_t before, bool* tripped) {
+  int32_t after = 0;
+  if (cudaMemcpyAsync(&after, d_flags, sizeof(int32_t), cudaMemcpyDeviceToHost, st) != cudaSuccess ||
+      cudaStreamSynchronize(st) != cudaSuccess)
+    return SHG_ERR_CUDA;
+  *tripped = (after & SHG_FLAG_RANGE) && !(before & SHG_FLAG_RANGE);
+  if (*tripped && (cudaMemcpyAsync(d_flags, &before, sizeof(int32_t), cudaMemcpyHostToDevice, st) != cudaSuccess ||
+                   cudaStreamSynchronize(st) != cudaSuccess))
+    return SHG_ERR_CUDA;
+  return SHG_OK;
+}
 
 #define SHG_TRY(x)            \
   do {                        \
@@ -231,6 +264,21 @@ int shgemm_project(int64_t m, int64_t n, int64_t k, const float* A, int64_t lda,
                      0, omega, ldo, Y, ldy, 0, d_flags, st);
     case SHG_FP32_SIMT:
       return simt_gemm(m, k, n, A, lda, trans_a, omega, ldo, 1, Y, ldy, 0, 1, 0, 0, 0, st);
+    case SHG_SPLIT_TF32:
+      // the TF32 kernel reads A K-major; the transposed product keeps the
+      // full range in FP32 SIMT
+      if (trans_a) return simt_gemm(m, k, n, A, lda, 1, omega, ldo, 1, Y, ldy, 0, 1, 0, 0, 0, st);
+      return tc_tf32_gemm(m, k, n, 1, A, lda, 0, omega, ldo, Y, ldy, d_flags, st);
+    case SHG_SPLIT_AUTO: {
+      // SHGEMM-FP16, redone in the full exponent range when its range check trips
+      bool tripped = false;
+      int32_t before = 0;
+      SHG_TRY(range_probe_begin(d_flags, st, &before));
+      SHG_TRY(shgemm_project(m, n, k, A, lda, trans_a, omega, ldo, Y, ldy, SHG_SPLIT_F16, d_flags, stream));
+      SHG_TRY(range_probe_end(d_flags, st, before, &tripped));
+      if (!tripped) return SHG_OK;
+      return shgemm_project(m, n, k, A, lda, trans_a, omega, ldo, Y, ldy, SHG_SPLIT_TF32, d_flags, stream);
+    }
     default:
       return SHG_ERR_INVALID_ARG;
   }
@@ -368,8 +416,9 @@ int shg_mode_project(int ndim, const int64_t* dims, int mode, int64_t J, const f
   for (int i = 0; i < 3; ++i)
     if (dims[i] < 1) return SHG_ERR_INVALID_ARG;
   if (mode < 0 || mode > 2 || J < 1 || ldo < J || ldw < J) return SHG_ERR_INVALID_ARG;
-  if (variant != SHG_SPLIT_F16 && variant != SHG_FP32_SIMT) return SHG_ERR_UNSUPPORTED;
-  return mode_project(mode, dims, J, X, omega, ldo, W, ldw, variant == SHG_SPLIT_F16, d_flags,
+  if (variant != SHG_SPLIT_F16 && variant != SHG_FP32_SIMT && variant != SHG_SPLIT_TF32) return SHG_ERR_UNSUPPORTED;
+  return mode_project(mode, dims, J, X, omega, ldo, W, ldw,
+                      variant == SHG_SPLIT_F16 ? MP_F16 : variant == SHG_SPLIT_TF32 ? MP_TF32 : MP_SIMT, d_flags,
                       static_cast<cudaStream_t>(stream));
 }
 
@@ -411,7 +460,8 @@ int shg_rp_hosvd(int ndim, const int64_t* dims, const int64_t* ranks, int64_t ov
     ldo[i] = om[i] ? (omega_lds ? omega_lds[i] : J[i]) : L.ld[i];
     if (ldo[i] < J[i]) return SHG_ERR_INVALID_ARG;
   }
-  if (variant != SHG_SPLIT_F16 && variant != SHG_FP32_SIMT) return SHG_ERR_UNSUPPORTED;
+  if (variant != SHG_SPLIT_F16 && variant != SHG_FP32_SIMT && variant != SHG_SPLIT_TF32 && variant != SHG_SPLIT_AUTO)
+    return SHG_ERR_UNSUPPORTED;
   if (ws_bytes < need) return SHG_ERR_WORKSPACE;
   cudaStream_t st = static_cast<cudaStream_t>(stream);
   float* W[3];
@@ -420,7 +470,25 @@ int shg_rp_hosvd(int ndim, const int64_t* dims, const int64_t* ranks, int64_t ov
   float* T2 = reinterpret_cast<float*>(w + L.T2);
   const int64_t I0 = dims[0], I1 = dims[1], I2 = dims[2];
   const int64_t J0 = J[0], J1 = J[1], J2 = J[2];
-  const bool tc = (variant == SHG_SPLIT_F16);
+  int var = variant;
+  bool w0_done = false;  // the probe's mode-0 projection stands when it did not trip
+  if (variant == SHG_SPLIT_AUTO) {
+    // the range of X decides for every mode: probe with the mode-0 projection
+    bool tripped = false;
+    int32_t before = 0;
+    if (!om[0]) {
+      uint16_t* gen = reinterpret_cast<uint16_t*>(w + L.Om[0]);
+      SHG_TRY(shg_gaussian_f16(seed, 0, I1 * I2, J[0], gen, L.ld[0], st));
+      om[0] = gen;
+    }
+    SHG_TRY(range_probe_begin(d_flags, st, &before));
+    SHG_TRY(mode_project(0, dims, J[0], X, om[0], ldo[0], W[0], L.ld[0], MP_F16, d_flags, st));
+    SHG_TRY(range_probe_end(d_flags, st, before, &tripped));
+    var = tripped ? SHG_SPLIT_TF32 : SHG_SPLIT_F16;
+    w0_done = !tripped;
+  }
+  const bool tc = (var == SHG_SPLIT_F16);
+  const int how = var == SHG_SPLIT_F16 ? MP_F16 : var == SHG_SPLIT_TF32 ? MP_TF32 : MP_SIMT;
 
   // per mode: W_i = X_(i) Omega_(i), Q_i = orth(W_i).  The three modes are
   // independent: they run on three library streams forked from and joined
@@ -438,7 +506,7 @@ int shg_rp_hosvd(int ndim, const int64_t* dims, const int64_t* ranks, int64_t ov
       SHG_TRY(shg_gaussian_f16(seed, static_cast<uint64_t>(i) << 32, I0 * I1 * I2 / dims[i], J[i], gen, L.ld[i], ms));
       om[i] = gen;
     }
-    SHG_TRY(mode_project(i, dims, J[i], X, om[i], ldo[i], W[i], L.ld[i], tc, d_flags, ms));
+    if (!(i == 0 && w0_done)) SHG_TRY(mode_project(i, dims, J[i], X, om[i], ldo[i], W[i], L.ld[i], how, d_flags, ms));
     float* T = reinterpret_cast<float*>(w + L.T[i]);
     SHG_TRY(cholqr2(dims[i], J[i], W[i], L.ld[i], T, L.ld[i], w + L.small[i], d_flags, ms));
     if (cudaMemcpy2DAsync(factors[i], J[i] * 4, W[i], L.ld[i] * 4, J[i] * 4, dims[i], cudaMemcpyDeviceToDevice,
@@ -474,7 +542,7 @@ int rsvd_impl(int64_t m, int64_t n, int64_t rank, int64_t oversampling, int powe
   size_t need = 0;
   if (shg_rsvd_workspace_size(m, n, rank, oversampling, power_iters, &need) != SHG_OK) return SHG_ERR_INVALID_ARG;
   if (!A || !U || !S || !V || !ws || !d_flags || lda < n) return SHG_ERR_INVALID_ARG;
-  if (variant < SHG_SPLIT_F16 || variant > SHG_FP32_SIMT) return SHG_ERR_INVALID_ARG;
+  if (variant < SHG_SPLIT_F16 || variant > SHG_SPLIT_AUTO) return SHG_ERR_INVALID_ARG;
   const int64_t k = rank + oversampling;
   if (omega && ldo < k) return SHG_ERR_INVALID_ARG;
   if (ws_bytes < need) return SHG_ERR_WORKSPACE;
@@ -498,7 +566,6 @@ int rsvd_impl(int64_t m, int64_t n, int64_t rank, int64_t oversampling, int powe
   float* Ups = reinterpret_cast<float*>(w + L.Ups);
   double* piv = report ? reinterpret_cast<double*>(w + L.piv) : nullptr;
   const int64_t ldk = round8(k);
-  const bool tc = tc_variant(variant);
   PhaseEvents ev;
   if (report) {
     SHG_TRY(ev.init());
@@ -515,8 +582,22 @@ int rsvd_impl(int64_t m, int64_t n, int64_t rank, int64_t oversampling, int powe
     ldo = ldk;
   }
   SHG_TRY(ev.mark(SHG_PHASE_PROJECT, st));
-  // projection: Y = A Omega
-  SHG_TRY(shgemm_project(m, n, k, A, lda, 0, omega, ldo, Y, ldk, variant, d_flags, st));
+  // projection: Y = A Omega.  SHG_SPLIT_AUTO tries SHGEMM-FP16 and moves the
+  // whole call to the full exponent range when the range check trips.
+  int var = variant;
+  if (variant == SHG_SPLIT_AUTO) {
+    bool tripped = false;
+    int32_t before = 0;
+    SHG_TRY(range_probe_begin(d_flags, st, &before));
+    SHG_TRY(shgemm_project(m, n, k, A, lda, 0, omega, ldo, Y, ldk, SHG_SPLIT_F16, d_flags, st));
+    SHG_TRY(range_probe_end(d_flags, st, before, &tripped));
+    var = tripped ? SHG_SPLIT_TF32 : SHG_SPLIT_F16;
+    if (tripped) SHG_TRY(shgemm_project(m, n, k, A, lda, 0, omega, ldo, Y, ldk, var, d_flags, st));
+  } else {
+    SHG_TRY(shgemm_project(m, n, k, A, lda, 0, omega, ldo, Y, ldk, var, d_flags, st));
+  }
+  const bool tc = tc_variant(var);        // FP16 / BF16 splits: every product on the tensor cores
+  const bool tf = var == SHG_SPLIT_TF32;  // full range: A fp16(Z) by SHGEMM-TF32, the rest in FP32 SIMT
   SHG_TRY(ev.mark(SHG_PHASE_ORTH, st));
   // orthonormal basis: Q = orth(Y)
   SHG_TRY(cholqr2(m, k, Y, ldk, T, ldk, small, d_flags, st, piv));
@@ -533,6 +614,9 @@ int rsvd_impl(int64_t m, int64_t n, int64_t rank, int64_t oversampling, int powe
     if (tc) {
       SHG_TRY(to_f16(n, k, Z, ldk, H, ldk, st));
       SHG_TRY(tc_gemm(A_KMAJ, B_F16, 2, m, k, n, 1, A, lda, 0, H, ldk, Y, ldk, 0, d_flags, st));
+    } else if (tf) {
+      SHG_TRY(to_f16(n, k, Z, ldk, H, ldk, st));
+      SHG_TRY(tc_tf32_gemm(m, k, n, 1, A, lda, 0, H, ldk, Y, ldk, d_flags, st));
     } else {
       SHG_TRY(simt_gemm(m, k, n, A, lda, 0, Z, ldk, 0, Y, ldk, 0, 1, 0, 0, 0, st));
     }

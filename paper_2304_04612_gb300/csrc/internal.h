@@ -45,6 +45,11 @@ int tc_gemm(int amaj, int bmode, int pieces, int64_t M, int64_t N, int64_t S_k, 
 // SHG_FLAG_RANGE when some |b| >= 65520.
 int split_f16(int64_t rows, int64_t cols, const float* B, int64_t ldb, uint16_t* hi, uint16_t* lo, int64_t ldo,
               int32_t* d_flags, cudaStream_t stream);
+// SHGEMM-TF32 (Sec. 4.2): C = A * B with A (K-major, as tc_gemm's A_KMAJ,
+// P pieces of S_k) split into TF32 hi / 2^11-scaled lo and B FP16 widened
+// exactly to TF32; the full FP32 exponent range of A.
+int tc_tf32_gemm(int64_t M, int64_t N, int64_t S_k, int64_t P, const float* A, int64_t lda, int64_t p_stride,
+                 const uint16_t* B, int64_t ldb, float* C, int64_t ldc, int32_t* d_flags, cudaStream_t stream);
 // Times the candidate configurations of this tc_gemm call (C is
 // overwritten; synchronises `stream`) and caches the fastest for the call's
 // shape class.  *best receives it; *found_before tells whether the class was

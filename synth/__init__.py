@@ -30,6 +30,8 @@ batch_specs(count, seed)   (m, n, rate, rank, seed) of a batch of uneven
 sketch_basis(n, r, seed), sketch_matrix(V0, m, sigma, theta_max, noise_rel, seed)
                            matrices U diag(sigma) (V0 cos T + W sin T)^T + E of
                            the learned-sketch family.
+cauchy_family(n, seed)     Cauchy matrix after one orthogonal-iteration step,
+                           entries beyond the FP16 range (SHGEMM-TF32 inputs).
 """
 from __future__ import annotations
 
@@ -153,3 +155,17 @@ def sketch_matrix(V0: np.ndarray, m: int, sigma: np.ndarray, theta_max: float,
     E = rng.standard_normal((m, n))
     E *= noise_rel * np.linalg.norm(S) / np.linalg.norm(E)
     return (S + E).astype(np.float32)
+
+
+def cauchy_family(n: int, seed: int, gamma: float = 1e-3, spread: float = 1e-3) -> np.ndarray:
+    """Stand-in for the Cauchy matrices of the randomized-SVD experiments:
+    C_ij = 1 / (|x_i - y_j| + gamma) with x, y uniform in (-spread, spread)
+    (x drawn first), followed by one step of the orthogonal iteration applied
+    to the matrix, A = (C C^T) C, formed in float64 and rounded to FP32.  Its
+    entries (about n^2 10^9) exceed the FP16 range, the case SHGEMM-TF32 is
+    for."""
+    rng = np.random.default_rng(seed)
+    x = rng.uniform(-spread, spread, size=n)
+    y = rng.uniform(-spread, spread, size=n)
+    C = 1.0 / (np.abs(x[:, None] - y[None, :]) + gamma)
+    return ((C @ C.T) @ C).astype(np.float32)

@@ -145,3 +145,45 @@ def test_range_flag():
     assert S.f16_range_ok(np.array([65519.0], dtype=np.float32))
     assert not S.f16_range_ok(np.array([65520.0], dtype=np.float32))
     assert not S.f16_range_ok(np.array([-1e6], dtype=np.float32))
+
+
+def test_tf32_split_full_exponent_range():
+    # SHGEMM-TF32 (Sec. 4.2): values far outside the FP16 range split and
+    # reconstruct to within u^2 |a| (u = 2^-11, the TF32 unit roundoff), and
+    # each piece has at most 11 significant bits
+    rng = np.random.default_rng(21)
+    e = rng.integers(-120, 120, size=4000)
+    a = (rng.uniform(1.0, 2.0, size=4000) * np.exp2(e.astype(np.float64)) *
+         rng.choice([-1.0, 1.0], size=4000)).astype(np.float32)
+    hi, lo = S.split_tf32(a)
+    a64 = a.astype(np.float64)
+    assert np.all(np.isfinite(hi)) and np.all(np.isfinite(lo))
+    rest = a64 - hi - lo * 2.0 ** -11
+    assert np.all(np.abs(rest) <= (2.0 ** -11) ** 2 * np.abs(a64))
+    for x in (hi, lo):
+        nz = x != 0
+        m, _ = np.frexp(x[nz])
+        assert np.all(np.ldexp(m, 11) == np.rint(np.ldexp(m, 11)))   # <= 11 significant bits
+    # the FP16 split cannot represent the large ones
+    big = a[np.abs(a) >= 65520.0]
+    assert big.size > 0 and not S.f16_range_ok(big)
+
+
+def test_tf32_split_equals_fp16_split_where_both_are_exact():
+    # TF32 and FP16 both carry 10 explicit mantissa bits: for a in [1, 2)
+    # (hi and the scaled lo are FP16 normals) the two splits are the same
+    rng = np.random.default_rng(22)
+    a = rng.uniform(1.0, 2.0, size=5000).astype(np.float32)
+    h16, l16 = S.split_f16(a)
+    h32, l32 = S.split_tf32(a)
+    keep = np.abs(l16) >= 2.0 ** -14          # lo an FP16 normal as well
+    assert np.array_equal(h16, h32)
+    assert np.array_equal(l16[keep], l32[keep])
+
+
+def test_shgemm_tf32_emulated_integer_brute_force():
+    rng = np.random.default_rng(23)
+    A = rng.integers(-1000, 1000, size=(6, 9)).astype(np.float32)
+    W = rng.integers(-30, 30, size=(9, 4)).astype(np.float16)
+    ref = [[sum(int(A[i, l]) * int(W[l, j]) for l in range(9)) for j in range(4)] for i in range(6)]
+    assert np.array_equal(S.shgemm_tf32_emulated(A, W), np.array(ref, dtype=np.float64))
