@@ -751,12 +751,18 @@ def batched_times(shg, torch, dev, stream):
     ms_, ns_ = [A.shape[0] for A in As], [A.shape[1] for A in As]
     fl = shg.new_flags(dev)
     res = {"problems": 256, "bytes_of_A": int(sum(4 * m * n for m, n in zip(ms_, ns_)))}
-    for mode, use_graph in (("graph", True), ("streams", False)):
+    # grouped launches (one per step of Algorithm 1 for the whole batch), as
+    # a graph and enqueued directly; then the per-problem launches on the
+    # library's stream pool (SHG_BATCHED_GROUPED=0), as a graph and directly
+    for mode, use_graph, grouped in (("graph", True, "1"), ("grouped_direct", False, "1"),
+                                     ("stream_pool_graph", True, "0"), ("streams", False, "0")):
+        os.environ["SHG_BATCHED_GROUPED"] = grouped
         fn = lambda: shg.shg_rsvd_batched(As, ranks, s, q, omegas=None, seed=4, use_graph=use_graph, out=out,
                                           workspace=ws, flags=fl, check=False, stream=stream)
         fn()
         ms = time_ms(torch, stream, fn, reps=5)
         res[mode] = {"ms": ms, "problems_per_s": 256 / (ms * 1e-3)}
+    os.environ.pop("SHG_BATCHED_GROUPED", None)
     # the same problems one after another through shg_rsvd on one stream
     oms = [shg.shg_gaussian_f16(4, i << 32, n, r + s,
                                 out=torch.empty(n, (r + s + 7) // 8 * 8, dtype=torch.float16, device=dev)[:, :r + s])

@@ -387,17 +387,23 @@ int shg_rp_hosvd(int ndim, const int64_t* dims, const int64_t* ranks, int64_t ov
  *   All arrays of sizes and pointers are HOST arrays of `batch` entries; the
  *   pointers in them are device pointers.  Workspace from
  *   shg_rsvd_batched_workspace_size (one slice per concurrent branch).
- * Problems run concurrently on up to 128 streams owned by the library
- * (created on the first call on a device), forked from and joined back to
- * `stream`.  use_graph != 0: the first call with a given set of arguments
- * captures this fork/join into a CUDA graph, later calls with identical
- * arguments (same pointers and sizes) replay it with one graph launch; up to
- * 16 graphs are kept per process.  Calls are serialised by a mutex.
- * Each problem's multi-CTA launches (projections, Gram matrices, GEMMs) size
- * their grids for 16 SMs instead of the whole GPU, so that the problems in
- * flight share the GPU; the environment variable SHG_BATCHED_GRID_SMS
- * (0 = the whole GPU) overrides the share.  Results are the same up to the
- * order of floating-point sums.
+ * Execution: with SHG_SPLIT_F16, k_i <= 158 for every problem (one-CTA
+ * eigensolver) and TMA-aligned A_i / Omega_i, every step of Algorithm 1 runs
+ * as one grouped launch for the whole batch (the projections of all
+ * problems in one persistent tensor-core launch over a list of all their
+ * tiles; one CTA per problem for the k x k steps).  The call then first
+ * copies the steps' argument tables into the workspace, synchronising
+ * `stream`; it takes this path only when `stream` is not being captured.
+ * Otherwise (or with SHG_BATCHED_GROUPED=0 in the environment) problems run
+ * concurrently on up to 128 streams owned by the library (created on the
+ * first call on a device), forked from and joined back to `stream`; each
+ * problem's multi-CTA launches size their grids for 16 SMs
+ * (SHG_BATCHED_GRID_SMS, 0 = the whole GPU, overrides the share).
+ * use_graph != 0: the first call with a given set of arguments captures the
+ * launches into a CUDA graph, later calls with identical arguments (same
+ * pointers and sizes, workspace untouched in between) replay it with one
+ * graph launch; up to 16 graphs are kept per process.  Calls are serialised
+ * by a mutex.  Results are the same up to the order of floating-point sums.
  * Device flags: as shg_rsvd (OR-ed over all problems).
  */
 int shg_rsvd_batched_workspace_size(int batch, const int64_t* m, const int64_t* n, const int64_t* rank,

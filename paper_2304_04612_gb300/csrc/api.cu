@@ -32,21 +32,12 @@ GridShare::~GridShare() { g_grid_share = prev_; }
 
 int ceil_div_i(int64_t a, int64_t b) { return static_cast<int>((a + b - 1) / b); }
 
-namespace {
-
-inline int64_t round8(int64_t x) { return (x + 7) / 8 * 8; }
-
-bool tc_variant(int v) { return v == SHG_SPLIT_F16 || v == SHG_SPLIT_BF16X3 || v == SHG_SPLIT_BF16X2; }
-
 constexpr int64_t kReportProbes = SHG_REPORT_PROBES;
 
 // Workspace layout of shg_rsvd (the estimator's pieces and the report
 // scalars are used only when a report is asked for).
-struct RsvdLayout {
-  size_t Y, T, Z, H, Hlo, Bt, small, eig, Vk, lam, Up, Ups, Om, est, piv, eout, total;
-};
 RsvdLayout rsvd_layout(int64_t m, int64_t n, int64_t k, int64_t rank) {
-  const int64_t ldk = round8(k), mx = m > n ? m : n;
+  const int64_t ldk = (k + 7) / 8 * 8, mx = m > n ? m : n;
   RsvdLayout L{};
   size_t off = 0;
   auto take = [&](size_t bytes) {
@@ -75,6 +66,13 @@ RsvdLayout rsvd_layout(int64_t m, int64_t n, int64_t k, int64_t rank) {
   L.total = off;
   return L;
 }
+
+
+namespace {
+
+inline int64_t round8(int64_t x) { return (x + 7) / 8 * 8; }
+
+bool tc_variant(int v) { return v == SHG_SPLIT_F16 || v == SHG_SPLIT_BF16X3 || v == SHG_SPLIT_BF16X2; }
 
 // Three library streams per device for the independent per-mode work of
 // RP-HOSVD, with fork / join events; created on first use.

@@ -7,6 +7,7 @@
 // small projections fill the GPU together).  With use_graph the whole
 // fork/join is captured once into a CUDA graph, cached by the call's
 // arguments, and replayed with one graph launch on the caller's stream.
+#include <algorithm>
 #include <cstdlib>
 #include <cstring>
 #include <mutex>
@@ -183,7 +184,11 @@ extern "C" int shg_rsvd_batched_workspace_size(int batch, const int64_t* m, cons
   size_t per = 0;
   const int rc = branch_bytes(batch, m, n, rank, oversampling, power_iters, &per);
   if (rc != SHG_OK) return rc;
-  *bytes = per * branches_for(batch);
+  // room for either path: one slice per branch of the stream pool, or one
+  // slice per problem plus the argument tables of the grouped launches
+  BatchCall c{batch, m, n, rank, oversampling, power_iters, nullptr, nullptr, nullptr, nullptr, 0, nullptr, nullptr,
+              nullptr};
+  *bytes = std::max(per * branches_for(batch), grouped_batch_bytes(c));
   return SHG_OK;
 }
 
@@ -215,20 +220,34 @@ extern "C" int shg_rsvd_batched(int batch, const int64_t* m, const int64_t* n, c
   cudaStreamCaptureStatus cap = cudaStreamCaptureStatusNone;
   if (cudaStreamIsCapturing(st, &cap) != cudaSuccess) return SHG_ERR_CUDA;
   const int grid_share = batched_grid_sms();
+  // the grouped launches (one per step for the whole batch) when every
+  // problem fits them; they need a synchronous upload of their argument
+  // tables first, so not while the caller's stream is being captured
+  BatchCall bc{batch, m, n, rank, oversampling, power_iters, A, lda, omegas, ldo, seed, U, S, V};
+  const char* ge = std::getenv("SHG_BATCHED_GROUPED");
+  const bool grouped = (!ge || std::atoi(ge) != 0) && cap == cudaStreamCaptureStatusNone &&
+                       grouped_batch_eligible(bc, variant);
+  if (grouped && !use_graph) {
+    if ((rc = grouped_batch_prepare(bc, ws, ws_bytes, st)) != SHG_OK) return rc;
+    return grouped_batch_enqueue(bc, ws, d_flags, st);
+  }
   if (!use_graph || cap != cudaStreamCaptureStatusNone) return enqueue(a, *p, per, grid_share, st);
 
   std::vector<uint8_t> key = make_key(a, dev, grid_share);
+  put(key, grouped);
   for (GraphEntry& e : g_graphs) {
     if (e.dev == dev && e.key == key) {
       e.last_use = ++g_tick;
       return cuda_status(cudaGraphLaunch(e.exec, st));
     }
   }
-  // capture the fork/join once on the library's capture stream (the caller's
-  // stream may be the legacy default stream, which cannot be captured); the
-  // graph launch then orders it after the caller's earlier work
+  // capture the fork/join (or the grouped steps) once on the library's
+  // capture stream (the caller's stream may be the legacy default stream,
+  // which cannot be captured); the graph launch then orders it after the
+  // caller's earlier work
+  if (grouped && (rc = grouped_batch_prepare(bc, ws, ws_bytes, st)) != SHG_OK) return rc;
   if (cudaStreamBeginCapture(p->capture, cudaStreamCaptureModeRelaxed) != cudaSuccess) return SHG_ERR_CUDA;
-  rc = enqueue(a, *p, per, grid_share, p->capture);
+  rc = grouped ? grouped_batch_enqueue(bc, ws, d_flags, p->capture) : enqueue(a, *p, per, grid_share, p->capture);
   cudaGraph_t graph = nullptr;
   const cudaError_t end = cudaStreamEndCapture(p->capture, &graph);
   if (rc != SHG_OK) {

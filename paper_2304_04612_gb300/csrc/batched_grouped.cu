@@ -1,0 +1,321 @@
+// The batched randomized SVD as grouped launches: every step of Algorithm 1
+// (with the power scheme of Sec. 2.1) runs for the whole batch in one launch
+// (or, for the Cholesky factorisations beyond shared memory, one launch per
+// 32-column panel), instead of a chain of launches per problem.
+//
+// The host builds, once per set of arguments, the per-problem argument
+// arrays of every step (device pointers into one workspace slice per
+// problem, laid out as shg_rsvd lays out its workspace), the projections'
+// problem tables with their TMA tensor maps and the projections' unit lists,
+// and copies them into the workspace after the slices.  The step sequence
+// then refers to them only through device pointers, so it can be captured
+// into a CUDA graph and replayed.
+//
+// Per problem the arithmetic is exactly that of shg_rsvd with SHG_SPLIT_F16:
+// the same kernels' bodies on the same data; only the projections run on the
+// grouped tensor-core kernel (grouped_tc.cu), whose 128-column tiles and
+// drain interval match the 128-column kernel's defaults.
+#include <algorithm>
+#include <cstring>
+#include <vector>
+
+#include "grouped.h"
+#include "internal.h"
+#include "linalg.h"
+
+namespace shg {
+namespace {
+
+inline int64_t round8(int64_t x) { return (x + 7) / 8 * 8; }
+
+// Section offsets (bytes from the start of the table region) and sizes.
+struct Plan {
+  int n = 0, q = 0;
+  std::vector<size_t> slice;  // per-problem slice offset from the workspace base
+  size_t slices_bytes = 0, table_bytes = 0;
+  // argument arrays
+  size_t gen = 0, zY = 0, zZ = 0, zB = 0, zG = 0;
+  size_t gramY1 = 0, gramY2 = 0, gramZ1 = 0, gramZ2 = 0, gramB = 0;
+  size_t cholS = 0, cholP = 0;
+  size_t simtY1 = 0, simtY2 = 0, simtZ1 = 0, simtZ2 = 0, liftU = 0, liftV = 0;
+  size_t convY = 0, convZ = 0, splitY = 0, eig = 0;
+  size_t pNN = 0, uNN = 0, pNH = 0, uNH = 0, pTN = 0, uTN = 0, pB = 0, uB = 0;
+  int n_gen = 0, n_cholS = 0, n_cholP = 0;
+  long long units_NN = 0, units_NH = 0, units_TN = 0, units_B = 0;
+  int kmax = 0, kmax_small = 0, kmax_panel = 0, mmax = 0, nmax = 0, rmax = 0, tbmax = 0;
+  long long max_mk = 0, max_nk = 0, max_kk = 0;
+};
+
+struct Tables {
+  std::vector<uint8_t> buf;
+  size_t off = 0;
+  template <typename T>
+  size_t add(const std::vector<T>& v) {
+    const size_t o = off;
+    off = align256(off + v.size() * sizeof(T));
+    buf.resize(off);
+    if (!v.empty()) std::memcpy(buf.data() + o, v.data(), v.size() * sizeof(T));
+    return o;
+  }
+};
+
+// The plan of call c; with ws != nullptr also the argument tables (device
+// pointers into ws) in *t.  Returns SHG_OK or an error.
+int build(const BatchCall& c, uint8_t* ws, Plan* P, Tables* t) {
+  const int n = c.batch;
+  P->n = n;
+  P->q = c.q;
+  P->slice.resize(n);
+  size_t off = 0;
+  for (int i = 0; i < n; ++i) {
+    const int64_t k = c.rank[i] + c.s;
+    P->slice[i] = off;
+    off += align256(rsvd_layout(c.m[i], c.n[i], k, c.rank[i]).total);
+  }
+  P->slices_bytes = off;
+  std::vector<ZeroArg> zY, zZ, zB, zG;
+  std::vector<GaussArg> gen;
+  std::vector<GramArg> gY1, gY2, gZ1, gZ2, gB;
+  std::vector<CholArg> cS, cP;
+  std::vector<SimtArg> sY1, sY2, sZ1, sZ2, lU, lV;
+  std::vector<ConvArg> cvY, cvZ, spY;
+  std::vector<EigArg> eg;
+  std::vector<GemmProblem> pNN, pNH, pTN, pB;
+  for (int i = 0; i < n; ++i) {
+    const int m = static_cast<int>(c.m[i]), nn = static_cast<int>(c.n[i]), r = static_cast<int>(c.rank[i]);
+    const int k = r + static_cast<int>(c.s);
+    const int64_t ldk = round8(k);
+    const RsvdLayout L = rsvd_layout(m, nn, k, r);
+    uint8_t* w = ws ? ws + P->slice[i] : nullptr;
+    auto F = [&](size_t o) { return reinterpret_cast<float*>(w ? w + o : nullptr); };
+    auto H16 = [&](size_t o) { return reinterpret_cast<uint16_t*>(w ? w + o : nullptr); };
+    float *Y = F(L.Y), *T = F(L.T), *Z = F(L.Z), *Bt = F(L.Bt), *Vk = F(L.Vk), *Up = F(L.Up), *Ups = F(L.Ups);
+    uint16_t *H = H16(L.H), *Hlo = H16(L.Hlo);
+    const SmallWs sw = w ? small_ws(w + L.small, k) : SmallWs{};
+    P->kmax = std::max(P->kmax, k);
+    P->mmax = std::max(P->mmax, m);
+    P->nmax = std::max(P->nmax, nn);
+    P->rmax = std::max(P->rmax, r);
+    P->max_mk = std::max<long long>(P->max_mk, static_cast<long long>(m) * ldk * 4);
+    P->max_nk = std::max<long long>(P->max_nk, static_cast<long long>(nn) * ldk * 4);
+    P->max_kk = std::max<long long>(P->max_kk, static_cast<long long>(k) * k * 8);
+    const int tb = jacobi_cta_tb(k);
+    if (tb <= 0) return SHG_ERR_UNSUPPORTED;
+    P->tbmax = std::max(P->tbmax, tb);
+    // the test matrix: the caller's or the Philox stream (seed, i 2^32); every
+    // problem has an entry in the generation step (no rows when Omega is
+    // given), so that the tables' layout does not depend on the pointers
+    const uint16_t* om = (ws && c.omegas) ? c.omegas[i] : nullptr;
+    const int64_t ldo = om ? c.ldo[i] : ldk;
+    const bool generate = !om;
+    if (generate) om = H16(L.Om);
+    gen.push_back(GaussArg{H16(L.Om), ldk, static_cast<unsigned long long>(i) << 32, generate ? nn : 0, k});
+    zY.push_back(ZeroArg{Y, ldk * 4, static_cast<long long>(k) * 4, m});
+    zZ.push_back(ZeroArg{Z, ldk * 4, static_cast<long long>(k) * 4, nn});
+    zB.push_back(ZeroArg{Bt, ldk * 4, static_cast<long long>(k) * 4, nn});
+    zG.push_back(ZeroArg{sw.G, static_cast<long long>(k) * 8, static_cast<long long>(k) * 8, k});
+    gY1.push_back(GramArg{Y, ldk, sw.G, m, k});
+    gY2.push_back(GramArg{T, ldk, sw.G, m, k});
+    gZ1.push_back(GramArg{Z, ldk, sw.G, nn, k});
+    gZ2.push_back(GramArg{T, ldk, sw.G, nn, k});
+    gB.push_back(GramArg{Bt, ldk, sw.G, nn, k});
+    (k <= chol_smem_kmax() ? cS : cP).push_back(CholArg{sw.G, sw.Rf, sw.chol, k});
+    if (k <= chol_smem_kmax()) P->kmax_small = std::max(P->kmax_small, k);
+    else P->kmax_panel = std::max(P->kmax_panel, k);
+    sY1.push_back(SimtArg{Y, ldk, sw.Rf, k, T, ldk, m, k, k});
+    sY2.push_back(SimtArg{T, ldk, sw.Rf, k, Y, ldk, m, k, k});
+    sZ1.push_back(SimtArg{Z, ldk, sw.Rf, k, T, ldk, nn, k, k});
+    sZ2.push_back(SimtArg{T, ldk, sw.Rf, k, Z, ldk, nn, k, k});
+    // (a size-only plan, ws == nullptr, has no pointer arrays to read)
+    lU.push_back(SimtArg{Y, ldk, Up, r, ws ? c.U[i] : nullptr, r, m, r, k});
+    lV.push_back(SimtArg{Bt, ldk, Ups, r, ws ? c.V[i] : nullptr, r, nn, r, k});
+    cvY.push_back(ConvArg{Y, ldk, H, nullptr, ldk, m, k});
+    cvZ.push_back(ConvArg{Z, ldk, H, nullptr, ldk, nn, k});
+    spY.push_back(ConvArg{Y, ldk, H, Hlo, ldk, m, k});
+    uint8_t* eigb = w ? w + L.eig : nullptr;
+    eg.push_back(EigArg{sw.G, reinterpret_cast<float2*>(eigb ? eigb + 256 : nullptr), reinterpret_cast<int*>(eigb),
+                        Vk, reinterpret_cast<double*>(w ? w + L.lam : nullptr), ws ? c.S[i] : nullptr, Up, Ups, k, r,
+                        tb});
+    GemmProblem g{};
+    if (ws) {
+      int rc = grouped_problem(A_KMAJ, false, m, k, nn, c.A[i], c.lda[i], om, nullptr, ldo, Y, ldk, &g);
+      if (rc != SHG_OK) return rc;
+    } else {
+      grouped_tiling(k, &g.n_tile, &g.n_tiles);
+      g.m_tiles = (m + 127) / 128;
+      g.kblocks = (nn + 63) / 64;
+    }
+    pNN.push_back(g);
+    P->units_NN += static_cast<long long>(g.n_tiles) * g.m_tiles * g.kblocks;
+    if (ws) {
+      int rc = grouped_problem(A_KMAJ, false, m, k, nn, c.A[i], c.lda[i], H, nullptr, ldk, Y, ldk, &g);
+      if (rc != SHG_OK) return rc;
+    }
+    pNH.push_back(g);
+    P->units_NH += static_cast<long long>(g.n_tiles) * g.m_tiles * g.kblocks;
+    GemmProblem gt{};
+    if (ws) {
+      int rc = grouped_problem(A_MNMAJ, false, nn, k, m, c.A[i], c.lda[i], H, nullptr, ldk, Z, ldk, &gt);
+      if (rc != SHG_OK) return rc;
+    } else {
+      grouped_tiling(k, &gt.n_tile, &gt.n_tiles);
+      gt.m_tiles = (nn + 127) / 128;
+      gt.kblocks = (m + 63) / 64;
+    }
+    pTN.push_back(gt);
+    P->units_TN += static_cast<long long>(gt.n_tiles) * gt.m_tiles * gt.kblocks;
+    if (ws) {
+      int rc = grouped_problem(A_MNMAJ, true, nn, k, m, c.A[i], c.lda[i], H, Hlo, ldk, Bt, ldk, &gt);
+      if (rc != SHG_OK) return rc;
+    }
+    pB.push_back(gt);
+    P->units_B += static_cast<long long>(gt.n_tiles) * gt.m_tiles * gt.kblocks;
+  }
+  P->n_gen = static_cast<int>(gen.size());
+  P->n_cholS = static_cast<int>(cS.size());
+  P->n_cholP = static_cast<int>(cP.size());
+  Tables local;
+  Tables& T = t ? *t : local;
+  T.buf.clear();
+  T.off = 0;
+  P->gen = T.add(gen);
+  P->zY = T.add(zY);
+  P->zZ = T.add(zZ);
+  P->zB = T.add(zB);
+  P->zG = T.add(zG);
+  P->gramY1 = T.add(gY1);
+  P->gramY2 = T.add(gY2);
+  P->gramZ1 = T.add(gZ1);
+  P->gramZ2 = T.add(gZ2);
+  P->gramB = T.add(gB);
+  P->cholS = T.add(cS);
+  P->cholP = T.add(cP);
+  P->simtY1 = T.add(sY1);
+  P->simtY2 = T.add(sY2);
+  P->simtZ1 = T.add(sZ1);
+  P->simtZ2 = T.add(sZ2);
+  P->liftU = T.add(lU);
+  P->liftV = T.add(lV);
+  P->convY = T.add(cvY);
+  P->convZ = T.add(cvZ);
+  P->splitY = T.add(spY);
+  P->eig = T.add(eg);
+  P->pNN = T.add(pNN);
+  P->pNH = T.add(pNH);
+  P->pTN = T.add(pTN);
+  P->pB = T.add(pB);
+  std::vector<int4> u;
+  grouped_units(pNN.data(), n, &u);
+  P->uNN = T.add(u);
+  grouped_units(pNH.data(), n, &u);
+  P->uNH = T.add(u);
+  grouped_units(pTN.data(), n, &u);
+  P->uTN = T.add(u);
+  grouped_units(pB.data(), n, &u);
+  P->uB = T.add(u);
+  P->table_bytes = T.off;
+  return SHG_OK;
+}
+
+// CholeskyQR2 of every problem's X (m_i or n_i rows): gram / chol / X R^-1 twice.
+int cholqr2_grouped(const Plan& P, uint8_t* tb, size_t gram1, size_t simt1, size_t gram2, size_t simt2, int rows_max,
+                    int32_t* flags, cudaStream_t st) {
+  const int n = P.n;
+  for (int pass = 0; pass < 2; ++pass) {
+    int rc = zero_grouped(reinterpret_cast<const ZeroArg*>(tb + P.zG), n, P.max_kk, st);
+    if (rc != SHG_OK) return rc;
+    rc = gram_grouped(reinterpret_cast<const GramArg*>(tb + (pass == 0 ? gram1 : gram2)), n, P.kmax, rows_max, st);
+    if (rc != SHG_OK) return rc;
+    rc = chol_small_grouped(reinterpret_cast<const CholArg*>(tb + P.cholS), P.n_cholS, P.kmax_small, flags, st);
+    if (rc != SHG_OK) return rc;
+    rc = chol_panel_grouped(reinterpret_cast<const CholArg*>(tb + P.cholP), P.n_cholP, P.kmax_panel, flags, st);
+    if (rc != SHG_OK) return rc;
+    rc = simt_grouped(reinterpret_cast<const SimtArg*>(tb + (pass == 0 ? simt1 : simt2)), n, rows_max, P.kmax, st);
+    if (rc != SHG_OK) return rc;
+  }
+  return SHG_OK;
+}
+
+}  // namespace
+
+bool grouped_batch_eligible(const BatchCall& c, int variant) {
+  if (variant != SHG_SPLIT_F16) return false;
+  for (int i = 0; i < c.batch; ++i) {
+    const int64_t k = c.rank[i] + c.s;
+    if (k > jacobi_cta_kmax() || jacobi_cta_tb(k) <= 0) return false;
+    if ((reinterpret_cast<uintptr_t>(c.A[i]) & 15) || (c.lda[i] & 3)) return false;
+    if (c.omegas && c.omegas[i] && ((reinterpret_cast<uintptr_t>(c.omegas[i]) & 15) || (c.ldo[i] & 7))) return false;
+  }
+  return true;
+}
+
+size_t grouped_batch_bytes(const BatchCall& c) {
+  Plan P;
+  if (build(c, nullptr, &P, nullptr) != SHG_OK) return 0;
+  return P.slices_bytes + P.table_bytes;
+}
+
+int grouped_batch_prepare(const BatchCall& c, void* ws, size_t ws_bytes, cudaStream_t upload_stream) {
+  Plan P;
+  Tables T;
+  uint8_t* w = static_cast<uint8_t*>(ws);
+  int rc = build(c, w, &P, &T);
+  if (rc != SHG_OK) return rc;
+  if (P.slices_bytes + P.table_bytes > ws_bytes) return SHG_ERR_WORKSPACE;
+  if (cudaMemcpyAsync(w + P.slices_bytes, T.buf.data(), P.table_bytes, cudaMemcpyHostToDevice, upload_stream) !=
+          cudaSuccess ||
+      cudaStreamSynchronize(upload_stream) != cudaSuccess)
+    return SHG_ERR_CUDA;
+  return SHG_OK;
+}
+
+int grouped_batch_enqueue(const BatchCall& c, void* ws, int32_t* flags, cudaStream_t st) {
+  Plan P;
+  int rc = build(c, nullptr, &P, nullptr);
+  if (rc != SHG_OK) return rc;
+  uint8_t* tb = static_cast<uint8_t*>(ws) + P.slices_bytes;
+  const int n = P.n;
+  auto zero = [&](size_t o, long long mx) { return zero_grouped(reinterpret_cast<const ZeroArg*>(tb + o), n, mx, st); };
+#define SHG_G(x)                 \
+  do {                           \
+    const int rc_ = (x);         \
+    if (rc_ != SHG_OK) return rc_; \
+  } while (0)
+  // Omega
+  SHG_G(gaussian_grouped(c.seed, reinterpret_cast<const GaussArg*>(tb + P.gen), P.n_gen,
+                         static_cast<long long>(P.nmax) * P.kmax, st));
+  // Y = A Omega; Q = orth(Y)
+  SHG_G(zero(P.zY, P.max_mk));
+  SHG_G(tc_gemm_grouped(A_KMAJ, false, reinterpret_cast<const GemmProblem*>(tb + P.pNN),
+                        reinterpret_cast<const int4*>(tb + P.uNN), P.units_NN, flags, st));
+  SHG_G(cholqr2_grouped(P, tb, P.gramY1, P.simtY1, P.gramY2, P.simtY2, P.mmax, flags, st));
+  // power scheme: the FP16-rounded basis is the next test matrix
+  for (int it = 0; it < P.q; ++it) {
+    SHG_G(convert_grouped(reinterpret_cast<const ConvArg*>(tb + P.convY), n, P.max_mk / 4, false, flags, st));
+    SHG_G(zero(P.zZ, P.max_nk));
+    SHG_G(tc_gemm_grouped(A_MNMAJ, false, reinterpret_cast<const GemmProblem*>(tb + P.pTN),
+                          reinterpret_cast<const int4*>(tb + P.uTN), P.units_TN, flags, st));
+    SHG_G(cholqr2_grouped(P, tb, P.gramZ1, P.simtZ1, P.gramZ2, P.simtZ2, P.nmax, flags, st));
+    SHG_G(convert_grouped(reinterpret_cast<const ConvArg*>(tb + P.convZ), n, P.max_nk / 4, false, flags, st));
+    SHG_G(zero(P.zY, P.max_mk));
+    SHG_G(tc_gemm_grouped(A_KMAJ, false, reinterpret_cast<const GemmProblem*>(tb + P.pNH),
+                          reinterpret_cast<const int4*>(tb + P.uNH), P.units_NH, flags, st));
+    SHG_G(cholqr2_grouped(P, tb, P.gramY1, P.simtY1, P.gramY2, P.simtY2, P.mmax, flags, st));
+  }
+  // B^T = A^T Q by the TCEC split (Q split once)
+  SHG_G(convert_grouped(reinterpret_cast<const ConvArg*>(tb + P.splitY), n, P.max_mk / 4, true, flags, st));
+  SHG_G(zero(P.zB, P.max_nk));
+  SHG_G(tc_gemm_grouped(A_MNMAJ, true, reinterpret_cast<const GemmProblem*>(tb + P.pB),
+                        reinterpret_cast<const int4*>(tb + P.uB), P.units_B, flags, st));
+  // small SVD of B through the eigendecomposition of B B^T
+  SHG_G(zero(P.zG, P.max_kk));
+  SHG_G(gram_grouped(reinterpret_cast<const GramArg*>(tb + P.gramB), n, P.kmax, P.nmax, st));
+  SHG_G(eig_grouped(reinterpret_cast<const EigArg*>(tb + P.eig), n, P.kmax, P.rmax, P.tbmax, st));
+  // lift: U = Q U'; V = B^T U' Sigma^-1
+  SHG_G(simt_grouped(reinterpret_cast<const SimtArg*>(tb + P.liftU), n, P.mmax, P.rmax, st));
+  SHG_G(simt_grouped(reinterpret_cast<const SimtArg*>(tb + P.liftV), n, P.nmax, P.rmax, st));
+#undef SHG_G
+  return SHG_OK;
+}
+
+}  // namespace shg

@@ -10,6 +10,7 @@
 #include <cuda_bf16.h>
 #include <cuda_fp16.h>
 
+#include "grouped.h"
 #include "internal.h"
 
 namespace shg {
@@ -34,12 +35,12 @@ __device__ __forceinline__ float to_unit(uint32_t x) {
   return fmaf(static_cast<float>(x), 2.3283064365386963e-10f, 1.1641532182693481e-10f);
 }
 
-__global__ void gaussian_f16_kernel(uint2 key, unsigned long long offset, long long rows, long long cols,
-                                    __half* out, long long ld) {
+__device__ __forceinline__ void gaussian_f16_body(uint2 key, unsigned long long offset, long long rows, long long cols,
+                                                  __half* out, long long ld, int bx, int gdx) {
   const long long n = rows * cols;
   const long long nblk = (n + 3) / 4;
-  for (long long b = blockIdx.x * static_cast<long long>(blockDim.x) + threadIdx.x; b < nblk;
-       b += static_cast<long long>(gridDim.x) * blockDim.x) {
+  for (long long b = bx * static_cast<long long>(blockDim.x) + threadIdx.x; b < nblk;
+       b += static_cast<long long>(gdx) * blockDim.x) {
     const unsigned long long ctr = b + offset;
     const uint4 x = philox4x32_10(make_uint4(static_cast<uint32_t>(ctr), static_cast<uint32_t>(ctr >> 32), 0u, 0u), key);
     float z[4];
@@ -66,6 +67,17 @@ __global__ void gaussian_f16_kernel(uint2 key, unsigned long long offset, long l
       }
     }
   }
+}
+
+__global__ void gaussian_f16_kernel(uint2 key, unsigned long long offset, long long rows, long long cols,
+                                    __half* out, long long ld) {
+  gaussian_f16_body(key, offset, rows, cols, out, ld, blockIdx.x, gridDim.x);
+}
+
+// The test matrices of a batch, one problem per blockIdx.y.
+__global__ void gaussian_grouped_kernel(uint2 key, const GaussArg* __restrict__ args) {
+  const GaussArg a = args[blockIdx.y];
+  gaussian_f16_body(key, a.offset, a.rows, a.cols, reinterpret_cast<__half*>(a.out), a.ld, blockIdx.x, gridDim.x);
 }
 
 // Sparse sign test matrix (Sec. 3.4): element e takes 32-bit word e mod 4 of
@@ -106,6 +118,17 @@ __global__ void f16_to_bf16_kernel(long long rows, long long cols, const __half*
 }
 
 }  // namespace
+
+int gaussian_grouped(uint64_t seed, const GaussArg* d, int n, long long max_elems, cudaStream_t st) {
+  if (n <= 0) return SHG_OK;
+  const int sms = sm_count();
+  if (sms <= 0) return SHG_ERR_CUDA;
+  const long long want = ((max_elems + 3) / 4 + 255) / 256;
+  const int gx = static_cast<int>(want < 2ll * sms ? (want < 1 ? 1 : want) : 2ll * sms);
+  const uint2 key = make_uint2(static_cast<uint32_t>(seed), static_cast<uint32_t>(seed >> 32));
+  gaussian_grouped_kernel<<<dim3(gx, n), 256, 0, st>>>(key, d);
+  return cuda_status(cudaGetLastError());
+}
 
 int f16_to_bf16(int64_t rows, int64_t cols, const uint16_t* x, int64_t ldx, uint16_t* y, int64_t ldy,
                 cudaStream_t st) {

@@ -74,6 +74,35 @@ int simt_gemm(int64_t M, int64_t N, int64_t K, const float* A, int64_t lda, int 
 int f16_to_bf16(int64_t rows, int64_t cols, const uint16_t* x, int64_t ldx, uint16_t* y, int64_t ldy,
                 cudaStream_t st);
 
+// Byte offsets of the pieces of shg_rsvd's workspace (each 256-aligned).
+struct RsvdLayout {
+  size_t Y, T, Z, H, Hlo, Bt, small, eig, Vk, lam, Up, Ups, Om, est, piv, eout, total;
+};
+RsvdLayout rsvd_layout(int64_t m, int64_t n, int64_t k, int64_t rank);
+// The batched randomized SVD as grouped launches (one per step of
+// Algorithm 1 for the whole batch); see batched_grouped.cu.
+struct BatchCall {
+  int batch;
+  const int64_t *m, *n, *rank;
+  int64_t s;
+  int q;
+  const float* const* A;
+  const int64_t* lda;
+  const uint16_t* const* omegas;
+  const int64_t* ldo;
+  uint64_t seed;
+  float* const* U;
+  float* const* S;
+  float* const* V;
+};
+// Whether every problem of the call can take the grouped path, and the
+// workspace it needs.
+bool grouped_batch_eligible(const BatchCall& c, int variant);
+size_t grouped_batch_bytes(const BatchCall& c);
+// Builds the step arguments in the workspace (synchronising `upload_stream`)
+// and enqueues the grouped launches on `st`.
+int grouped_batch_prepare(const BatchCall& c, void* ws, size_t ws_bytes, cudaStream_t upload_stream);
+int grouped_batch_enqueue(const BatchCall& c, void* ws, int32_t* d_flags, cudaStream_t st);
 // Algorithm 1 as shg_rsvd computes it, with the counter offset of the
 // generated Omega (the batched path gives problem i offset i * 2^32).
 int rsvd_impl(int64_t m, int64_t n, int64_t rank, int64_t oversampling, int power_iters, const float* A,

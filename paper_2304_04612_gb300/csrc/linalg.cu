@@ -16,6 +16,7 @@
 #include <cooperative_groups.h>
 #include <cuda_fp16.h>
 
+#include "grouped.h"
 #include "internal.h"
 #include "linalg.h"
 
@@ -48,9 +49,8 @@ __device__ __forceinline__ void dot2_step(float x, float y, float& s, float& c) 
   c = __fadd_rn(c, __fadd_rn(r, e));
 }
 
-__global__ void __launch_bounds__(256) gram_kernel(int m, int k, const float* __restrict__ X, long long ldx,
-                                                   double* __restrict__ G, int rows_per_chunk) {
-  const int ti = blockIdx.y, tj = blockIdx.x;
+__device__ __forceinline__ void gram_body(int m, int k, const float* __restrict__ X, long long ldx,
+                                          double* __restrict__ G, int rows_per_chunk, int ti, int tj, int chunk) {
   if (ti > tj) return;
   __shared__ float Xi[32][33], Xj[32][33];
   const int tid = threadIdx.x;
@@ -60,7 +60,7 @@ __global__ void __launch_bounds__(256) gram_kernel(int m, int k, const float* __
   const int lr = tid >> 5;  // this thread loads rows lr, lr + 8, lr + 16, lr + 24 of a 32-row slab
   double acc[4] = {0, 0, 0, 0};
   float s[4] = {0, 0, 0, 0}, c[4] = {0, 0, 0, 0};
-  const int r0 = blockIdx.z * rows_per_chunk;
+  const int r0 = chunk * rows_per_chunk;
   const int r1 = min(m, r0 + rows_per_chunk);
   float pi[4], pj[4];
   auto fetch = [&](int rb) {
@@ -107,6 +107,11 @@ __global__ void __launch_bounds__(256) gram_kernel(int m, int k, const float* __
     if (gj < k && gj >= gi)
       atomicAdd(&G[gi * k + gj], acc[q] + (static_cast<double>(s[q]) + static_cast<double>(c[q])));
   }
+}
+
+__global__ void __launch_bounds__(256) gram_kernel(int m, int k, const float* __restrict__ X, long long ldx,
+                                                   double* __restrict__ G, int rows_per_chunk) {
+  gram_body(m, k, X, ldx, G, rows_per_chunk, blockIdx.y, blockIdx.x, blockIdx.z);
 }
 
 // ------------------------------------------------ Cholesky + inverse
@@ -203,9 +208,8 @@ __device__ __forceinline__ float2 df_recip(float2 d) {
 // SMEM selects the shared-memory layout at compile time, so that the
 // accesses compile to shared loads and stores rather than generic ones.
 template <bool SMEM>
-__global__ void __launch_bounds__(1024) chol_inv_kernel(int k, const double* __restrict__ G, float* __restrict__ Xf,
-                                                       double* scratch, int* flags,
-                                                       const float2* __restrict__ pre_dinv) {
+__device__ __forceinline__ void chol_inv_body(int k, const double* __restrict__ G, float* __restrict__ Xf,
+                                              double* scratch, int* flags, const float2* __restrict__ pre_dinv) {
   extern __shared__ __align__(16) float2 smd[];
   float2* a = SMEM ? smd : reinterpret_cast<float2*>(scratch);
   float* rf = reinterpret_cast<float*>(a + k * k);
@@ -339,6 +343,13 @@ __global__ void __launch_bounds__(1024) chol_inv_kernel(int k, const double* __r
   }
 }
 
+template <bool SMEM>
+__global__ void __launch_bounds__(1024) chol_inv_kernel(int k, const double* __restrict__ G, float* __restrict__ Xf,
+                                                       double* scratch, int* flags,
+                                                       const float2* __restrict__ pre_dinv) {
+  chol_inv_body<SMEM>(k, G, Xf, scratch, flags, pre_dinv);
+}
+
 // The same elimination for k too large for shared memory, in panels of
 // kCholPanel columns over the whole GPU (the matrix stays in L2):
 // chol_scale_kernel writes the scaled double-float upper triangle,
@@ -350,14 +361,15 @@ __global__ void __launch_bounds__(1024) chol_inv_kernel(int k, const double* __r
 // chol_inv_kernel<false> with pre_dinv then forms R^-1.
 constexpr int kCholPanel = 32;
 
-__global__ void __launch_bounds__(256) chol_scale_kernel(int k, const double* __restrict__ G, float2* __restrict__ a) {
+__device__ __forceinline__ void chol_scale_body(int k, const double* __restrict__ G, float2* __restrict__ a, int bx,
+                                                int gdx) {
   __shared__ double red[32];
   __shared__ double dmax;
   diag_max(k, G, red, &dmax);  // every block forms the scale itself
   __syncthreads();
   const int e2 = (dmax > 0.0) ? (ilogb(dmax) >> 1) : 0;
   const double sigma = ldexp(1.0, -2 * e2);
-  for (long long e = blockIdx.x * 256LL + threadIdx.x; e < static_cast<long long>(k) * k; e += gridDim.x * 256LL) {
+  for (long long e = bx * 256LL + threadIdx.x; e < static_cast<long long>(k) * k; e += gdx * 256LL) {
     const int i = static_cast<int>(e / k), j = static_cast<int>(e - static_cast<long long>(i) * k);
     float2 v = make_float2(0.0f, 0.0f);
     if (j >= i) {
@@ -369,8 +381,11 @@ __global__ void __launch_bounds__(256) chol_scale_kernel(int k, const double* __
   }
 }
 
-__global__ void __launch_bounds__(1024) chol_panel_kernel(int k, int j0, int j1, float2* a, float2* dinv_g,
-                                                         int* flags) {
+__global__ void __launch_bounds__(256) chol_scale_kernel(int k, const double* __restrict__ G, float2* __restrict__ a) {
+  chol_scale_body(k, G, a, blockIdx.x, gridDim.x);
+}
+
+__device__ __forceinline__ void chol_panel_body(int k, int j0, int j1, float2* a, float2* dinv_g, int* flags) {
   __shared__ float2 dj_s;
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5, nw = blockDim.x >> 5;
   for (int j = j0; j < j1; ++j) {
@@ -396,11 +411,16 @@ __global__ void __launch_bounds__(1024) chol_panel_kernel(int k, int j0, int j1,
   }
 }
 
-__global__ void __launch_bounds__(256) chol_trail_kernel(int k, int j0, int j1, float2* a,
-                                                        const float2* __restrict__ dinv_g) {
+__global__ void __launch_bounds__(1024) chol_panel_kernel(int k, int j0, int j1, float2* a, float2* dinv_g,
+                                                         int* flags) {
+  chol_panel_body(k, j0, j1, a, dinv_g, flags);
+}
+
+__device__ __forceinline__ void chol_trail_body(int k, int j0, int j1, float2* a, const float2* __restrict__ dinv_g,
+                                                int tile) {
   // tile (ti, tj), ti <= tj, of the trailing triangle rows / columns [j1, k)
   const int t = (k - j1 + 31) / 32;
-  int ti = 0, rem = blockIdx.x;
+  int ti = 0, rem = tile;
   while (rem >= t - ti) {
     rem -= t - ti;
     ++ti;
@@ -430,6 +450,11 @@ __global__ void __launch_bounds__(256) chol_trail_kernel(int k, int j0, int j1, 
       a[static_cast<size_t>(l) * k + lp] = v;
     }
   }
+}
+
+__global__ void __launch_bounds__(256) chol_trail_kernel(int k, int j0, int j1, float2* a,
+                                                        const float2* __restrict__ dinv_g) {
+  chol_trail_body(k, j0, j1, a, dinv_g, blockIdx.x);
 }
 
 // --------------------------------------------------------------- Jacobi FP32
@@ -517,8 +542,8 @@ __host__ __device__ inline size_t jac_cta_floats(int kp) {
   return static_cast<size_t>(2 * kp) + 2 * static_cast<size_t>(kp) * (kp + 1);
 }
 
-__global__ void __launch_bounds__(768) jacobi_kernel(int k, const double* __restrict__ G, float2* __restrict__ log,
-                                                    int* __restrict__ rounds_out, int TB) {
+__device__ __forceinline__ void jacobi_body(int k, const double* __restrict__ G, float2* __restrict__ log,
+                                            int* __restrict__ rounds_out, int TB) {
   extern __shared__ __align__(16) float smf[];
   const int kp = k + (k & 1);
   const int h = kp / 2, n1 = kp - 1;
@@ -684,6 +709,11 @@ __global__ void __launch_bounds__(768) jacobi_kernel(int k, const double* __rest
   if (tid == 0) *rounds_out = sweeps * n1;
 }
 
+__global__ void __launch_bounds__(768) jacobi_kernel(int k, const double* __restrict__ G, float2* __restrict__ log,
+                                                    int* __restrict__ rounds_out, int TB) {
+  jacobi_body(k, G, log, rounds_out, TB);
+}
+
 // V = J_0 J_1 ... J_{R-1} from the rotation log of jacobi_kernel (round rho
 // rotates, in every slot t, columns (p, q) of V by (c, s) of log[rho h + t]).
 // Rows of V are independent under V <- V J, so CTA b builds rows
@@ -692,11 +722,11 @@ __global__ void __launch_bounds__(768) jacobi_kernel(int k, const double* __rest
 // warp barrier when one warp covers the slots).  The log is read eight
 // rounds ahead.  Writes Vout (k x k, row-major, columns = eigenvectors).
 template <int RB>
-__global__ void __launch_bounds__(512) jac_apply_v_kernel(int k, const float2* __restrict__ log,
-                                                          const int* __restrict__ rounds, float* __restrict__ Vout) {
+__device__ __forceinline__ void jac_apply_v_body(int k, const float2* __restrict__ log, const int* __restrict__ rounds,
+                                                 float* __restrict__ Vout, int block) {
   extern __shared__ float vs[];  // RB x kp
   const int kp = k + (k & 1), h = kp / 2, n1 = kp - 1;
-  const int row0 = blockIdx.x * RB;
+  const int row0 = block * RB;
   const int t = threadIdx.x, nt = blockDim.x;
   const bool one_warp = nt == 32;
   for (int e = t; e < RB * kp; e += nt) {
@@ -750,6 +780,12 @@ __global__ void __launch_bounds__(512) jac_apply_v_kernel(int k, const float2* _
     const int i = e / k, j = e - i * k;
     if (row0 + i < k) Vout[static_cast<size_t>(row0 + i) * k + j] = vs[i * kp + j];
   }
+}
+
+template <int RB>
+__global__ void __launch_bounds__(512) jac_apply_v_kernel(int k, const float2* __restrict__ log,
+                                                          const int* __restrict__ rounds, float* __restrict__ Vout) {
+  jac_apply_v_body<RB>(k, log, rounds, Vout, blockIdx.x);
 }
 
 // The same Jacobi method for k too large for one SM's shared memory: A (two
@@ -930,9 +966,8 @@ __global__ void __launch_bounds__(kJacGridThreads) jacobi_grid_kernel(int k, con
 // lambda_i = v_i^T G v_i / v_i^T v_i (FP64 Rayleigh quotient, G symmetric
 // from its upper triangle; the FP32 rotations leave |v_i| = 1 only to
 // ~1e-5); one CTA per i.  nrm[i] = |v_i| (FP64).
-__global__ void rayleigh_kernel(int k, const double* __restrict__ G, const float* __restrict__ V,
-                                double* __restrict__ lam, double* __restrict__ nrm) {
-  const int i = blockIdx.x;
+__device__ __forceinline__ void rayleigh_body(int k, const double* __restrict__ G, const float* __restrict__ V,
+                                              double* __restrict__ lam, double* __restrict__ nrm, int i) {
   __shared__ double red[2][32];
   double s = 0.0, q = 0.0;
   for (int e = threadIdx.x; e < k * k; e += blockDim.x) {
@@ -965,13 +1000,18 @@ __global__ void rayleigh_kernel(int k, const double* __restrict__ G, const float
   }
 }
 
+__global__ void rayleigh_kernel(int k, const double* __restrict__ G, const float* __restrict__ V,
+                                double* __restrict__ lam, double* __restrict__ nrm) {
+  rayleigh_body(k, G, V, lam, nrm, blockIdx.x);
+}
+
 // Sort eigenvalues descending (ties by index), S[j] = sqrt(lambda) for the
 // top p, Up = V[:, perm[:p]] normalised to unit length and Ups = Up / S
 // (k x p, FP32).  Ranks by counting (thread per eigenvalue), then all
 // threads write Up and Ups element by element.
-__global__ void sort_select_kernel(int k, int p, const double* __restrict__ lam, const double* __restrict__ nrm,
-                                   const float* __restrict__ V, float* __restrict__ S, float* __restrict__ Up,
-                                   float* __restrict__ Ups) {
+__device__ __forceinline__ void sort_select_body(int k, int p, const double* __restrict__ lam,
+                                                 const double* __restrict__ nrm, const float* __restrict__ V,
+                                                 float* __restrict__ S, float* __restrict__ Up, float* __restrict__ Ups) {
   extern __shared__ double sel[];          // [p] 1 / ||v||, [p] 1 / (||v|| sigma)
   int* perm = reinterpret_cast<int*>(sel + 2 * p);  // [p] column of rank r
   for (int i = threadIdx.x; i < k; i += blockDim.x) {
@@ -997,6 +1037,12 @@ __global__ void sort_select_kernel(int k, int p, const double* __restrict__ lam,
     Up[e] = static_cast<float>(v * sel[r]);
     Ups[e] = static_cast<float>(v * sel[p + r]);
   }
+}
+
+__global__ void sort_select_kernel(int k, int p, const double* __restrict__ lam, const double* __restrict__ nrm,
+                                   const float* __restrict__ V, float* __restrict__ S, float* __restrict__ Up,
+                                   float* __restrict__ Ups) {
+  sort_select_body(k, p, lam, nrm, V, S, Up, Ups);
 }
 
 __global__ void f32_to_f16_kernel(long long rows, long long cols, const float* __restrict__ x, long long ldx,
@@ -1255,6 +1301,204 @@ int cholqr2(int64_t m, int64_t k, float* X, int64_t ldx, float* T, int64_t ldt, 
     lds = ldd;
   }
   return SHG_OK;
+}
+
+
+// ------------------------------------------------------------ grouped steps
+// One launch per step for many problems (the batched randomized SVD): each
+// kernel reads its problem's arguments from a device array and runs the
+// body of the single-problem kernel above on them.
+namespace {
+
+constexpr int kGramChunkRows = 512;  // rows per Gram CTA (a multiple of the FP64 flush interval)
+
+__global__ void zero_grouped_kernel(const ZeroArg* __restrict__ args) {
+  const ZeroArg a = args[blockIdx.y];
+  const long long words = a.width_bytes / 4, n = words * a.rows;
+  for (long long e = blockIdx.x * static_cast<long long>(blockDim.x) + threadIdx.x; e < n;
+       e += static_cast<long long>(gridDim.x) * blockDim.x) {
+    const long long r = e / words, c = e - r * words;
+    reinterpret_cast<uint32_t*>(static_cast<uint8_t*>(a.p) + r * a.ld_bytes)[c] = 0u;
+  }
+}
+
+__global__ void __launch_bounds__(256) gram_grouped_kernel(const GramArg* __restrict__ args, int cmax) {
+  const int p = blockIdx.z / cmax, chunk = blockIdx.z - p * cmax;
+  const GramArg a = args[p];
+  const int t = (a.k + 31) / 32;
+  if (static_cast<int>(blockIdx.x) >= t || static_cast<int>(blockIdx.y) >= t || chunk * kGramChunkRows >= a.m) return;
+  gram_body(a.m, a.k, a.X, a.ldx, a.G, kGramChunkRows, blockIdx.y, blockIdx.x, chunk);
+}
+
+__global__ void __launch_bounds__(1024) chol_small_grouped_kernel(const CholArg* __restrict__ args, int* flags) {
+  const CholArg a = args[blockIdx.x];
+  chol_inv_body<true>(a.k, a.G, a.Rf, a.scratch, flags, nullptr);
+}
+
+__global__ void __launch_bounds__(256) chol_scale_grouped_kernel(const CholArg* __restrict__ args) {
+  const CholArg a = args[blockIdx.y];
+  chol_scale_body(a.k, a.G, reinterpret_cast<float2*>(a.scratch), blockIdx.x, gridDim.x);
+}
+
+__global__ void __launch_bounds__(1024) chol_panel_grouped_kernel(const CholArg* __restrict__ args, int j0,
+                                                                 int* flags) {
+  const CholArg a = args[blockIdx.x];
+  if (j0 >= a.k) return;
+  chol_panel_body(a.k, j0, min(j0 + kCholPanel, a.k), reinterpret_cast<float2*>(a.scratch),
+                  reinterpret_cast<float2*>(a.scratch + 2 * a.k * a.k), flags);
+}
+
+__global__ void __launch_bounds__(256) chol_trail_grouped_kernel(const CholArg* __restrict__ args, int j0) {
+  const CholArg a = args[blockIdx.y];
+  const int j1 = j0 + kCholPanel;
+  if (j1 >= a.k) return;
+  const int t = (a.k - j1 + 31) / 32;
+  if (static_cast<int>(blockIdx.x) >= t * (t + 1) / 2) return;
+  chol_trail_body(a.k, j0, j1, reinterpret_cast<float2*>(a.scratch),
+                  reinterpret_cast<const float2*>(a.scratch + 2 * a.k * a.k), blockIdx.x);
+}
+
+__global__ void __launch_bounds__(1024) chol_inv_grouped_kernel(const CholArg* __restrict__ args, int* flags) {
+  const CholArg a = args[blockIdx.x];
+  chol_inv_body<false>(a.k, a.G, a.Rf, a.scratch, flags, reinterpret_cast<const float2*>(a.scratch + 2 * a.k * a.k));
+}
+
+__global__ void convert_grouped_kernel(const ConvArg* __restrict__ args, int* flags) {
+  const ConvArg a = args[blockIdx.y];
+  const long long n = static_cast<long long>(a.rows) * a.cols;
+  bool big = false;
+  for (long long e = blockIdx.x * static_cast<long long>(blockDim.x) + threadIdx.x; e < n;
+       e += static_cast<long long>(gridDim.x) * blockDim.x) {
+    const long long r = e / a.cols, c = e - r * a.cols;
+    const float x = a.x[r * a.ldx + c];
+    const __half h = __float2half_rn(x);
+    reinterpret_cast<__half*>(a.y)[r * a.ldy + c] = h;
+    if (a.ylo) {
+      // the TCEC split of an FP32 operand: x - hi and the scaling are exact
+      reinterpret_cast<__half*>(a.ylo)[r * a.ldy + c] = __float2half_rn((x - __half2float(h)) * 2048.0f);
+      big |= fabsf(x) >= 65520.0f;
+    }
+  }
+  if (big) atomicOr(flags, SHG_FLAG_RANGE);
+}
+
+__global__ void __launch_bounds__(768) jacobi_grouped_kernel(const EigArg* __restrict__ args) {
+  const EigArg a = args[blockIdx.x];
+  jacobi_body(a.k, a.G, a.log, a.rounds, a.TB);
+}
+
+__global__ void __launch_bounds__(512) apply_v_grouped_kernel(const EigArg* __restrict__ args) {
+  const EigArg a = args[blockIdx.y];
+  if (static_cast<int>(blockIdx.x) * 8 >= a.k) return;
+  jac_apply_v_body<8>(a.k, a.log, a.rounds, a.V, blockIdx.x);
+}
+
+__global__ void rayleigh_grouped_kernel(const EigArg* __restrict__ args) {
+  const EigArg a = args[blockIdx.y];
+  if (static_cast<int>(blockIdx.x) >= a.k) return;
+  rayleigh_body(a.k, a.G, a.V, a.lam, a.lam + a.k, blockIdx.x);
+}
+
+__global__ void sort_select_grouped_kernel(const EigArg* __restrict__ args) {
+  const EigArg a = args[blockIdx.x];
+  sort_select_body(a.k, a.p, a.lam, a.lam + a.k, a.V, a.S, a.Up, a.Ups);
+}
+
+int grid_for(long long work, int per_block) {
+  const long long b = (work + per_block - 1) / per_block;
+  const int sms = sm_count();
+  const long long cap = sms > 0 ? 4ll * sms : 512;
+  return static_cast<int>(b < 1 ? 1 : (b > cap ? cap : b));
+}
+
+}  // namespace
+
+int zero_grouped(const ZeroArg* d, int n, long long max_bytes, cudaStream_t st) {
+  if (n <= 0) return SHG_OK;
+  zero_grouped_kernel<<<dim3(grid_for(max_bytes / 4, 256 * 8), n), 256, 0, st>>>(d);
+  return cuda_status(cudaGetLastError());
+}
+
+int gram_grouped(const GramArg* d, int n, int kmax, int mmax, cudaStream_t st) {
+  if (n <= 0) return SHG_OK;
+  const int t = (kmax + 31) / 32, cmax = (mmax + kGramChunkRows - 1) / kGramChunkRows;
+  gram_grouped_kernel<<<dim3(t, t, n * cmax), 256, 0, st>>>(d, cmax);
+  return cuda_status(cudaGetLastError());
+}
+
+int chol_smem_kmax() { return 113; }
+
+int chol_small_grouped(const CholArg* d, int n, int kmax, int32_t* flags, cudaStream_t st) {
+  if (n <= 0) return SHG_OK;
+  const size_t need = static_cast<size_t>(2 * kmax * kmax) * sizeof(double);
+  if (!smem_fits(need)) return SHG_ERR_UNSUPPORTED;
+  if (cudaFuncSetAttribute(chol_small_grouped_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                           static_cast<int>(need)) != cudaSuccess)
+    return SHG_ERR_CUDA;
+  chol_small_grouped_kernel<<<n, block_threads(static_cast<int64_t>(kmax) * kmax / 4), need, st>>>(d, flags);
+  return cuda_status(cudaGetLastError());
+}
+
+int chol_panel_grouped(const CholArg* d, int n, int kmax, int32_t* flags, cudaStream_t st) {
+  if (n <= 0) return SHG_OK;
+  chol_scale_grouped_kernel<<<dim3(grid_for(static_cast<long long>(kmax) * kmax, 256), n), 256, 0, st>>>(d);
+  if (cudaGetLastError() != cudaSuccess) return SHG_ERR_CUDA;
+  for (int j0 = 0; j0 < kmax; j0 += kCholPanel) {
+    chol_panel_grouped_kernel<<<n, 1024, 0, st>>>(d, j0, flags);
+    if (cudaGetLastError() != cudaSuccess) return SHG_ERR_CUDA;
+    const int j1 = j0 + kCholPanel;
+    if (j1 < kmax) {
+      const int t = (kmax - j1 + 31) / 32;
+      chol_trail_grouped_kernel<<<dim3(t * (t + 1) / 2, n), 256, 0, st>>>(d, j0);
+      if (cudaGetLastError() != cudaSuccess) return SHG_ERR_CUDA;
+    }
+  }
+  chol_inv_grouped_kernel<<<n, block_threads(static_cast<int64_t>(kmax) * kmax / 4), 0, st>>>(d, flags);
+  return cuda_status(cudaGetLastError());
+}
+
+int convert_grouped(const ConvArg* d, int n, long long max_elems, bool split, int32_t* flags, cudaStream_t st) {
+  (void)split;
+  if (n <= 0) return SHG_OK;
+  convert_grouped_kernel<<<dim3(grid_for(max_elems, 256 * 4), n), 256, 0, st>>>(d, flags);
+  return cuda_status(cudaGetLastError());
+}
+
+int jacobi_cta_kmax() { return 158; }
+
+int jacobi_cta_tb(int64_t k) {
+  const int64_t kp = k + (k & 1);
+  const int h = static_cast<int>(kp / 2);
+  const int nblk = h * (h + 1) / 2;
+  int TB = 0;
+  for (int per = 1; per <= kJacItems; ++per) {
+    TB = ((nblk + per - 1) / per + 31) / 32 * 32;
+    if (TB <= 18 * 32) break;
+  }
+  const size_t smem = jac_cta_floats(static_cast<int>(kp)) * sizeof(float);
+  if (!smem_fits(smem) || h > 128 || TB > 18 * 32 || (nblk + TB - 1) / TB > kJacItems) return 0;
+  return TB;
+}
+
+int eig_grouped(const EigArg* d, int n, int kmax, int pmax, int tbmax, cudaStream_t st) {
+  if (n <= 0) return SHG_OK;
+  const int kp = kmax + (kmax & 1), h = kp / 2;
+  const size_t smem = jac_cta_floats(kp) * sizeof(float);
+  const int rot_warps = (h + 31) / 32;
+  const int groups = std::max(rot_warps, tbmax / 32 / 3 + ((tbmax / 32) % 3 ? 1 : 0));
+  if (groups * 128 > 768) return SHG_ERR_UNSUPPORTED;
+  if (cudaFuncSetAttribute(jacobi_grouped_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                           static_cast<int>(smem)) != cudaSuccess)
+    return SHG_ERR_CUDA;
+  jacobi_grouped_kernel<<<n, groups * 128, smem, st>>>(d);
+  if (cudaGetLastError() != cudaSuccess) return SHG_ERR_CUDA;
+  constexpr int rb = 8;
+  apply_v_grouped_kernel<<<dim3((kmax + rb - 1) / rb, n), (h + 31) / 32 * 32, rb * kp * sizeof(float), st>>>(d);
+  if (cudaGetLastError() != cudaSuccess) return SHG_ERR_CUDA;
+  rayleigh_grouped_kernel<<<dim3(kmax, n), 256, 0, st>>>(d);
+  if (cudaGetLastError() != cudaSuccess) return SHG_ERR_CUDA;
+  sort_select_grouped_kernel<<<n, 1024, pmax * (2 * sizeof(double) + sizeof(int)), st>>>(d);
+  return cuda_status(cudaGetLastError());
 }
 
 }  // namespace shg

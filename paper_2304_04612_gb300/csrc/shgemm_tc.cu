@@ -58,44 +58,6 @@ constexpr int kThreads = 352;
 constexpr int kFirstSplitWarp = 2;
 constexpr int kFirstEpiWarp = 6;
 constexpr int kBProducerWarp = 10;
-// Split 64 values into PIECES 16-bit pieces (FP16: hi, 2^11-scaled lo; BF16:
-// pieces at 2^0, 2^8, 2^16 scales), two per 32-bit TMEM column (even K in
-// the lower half), and store them at TMEM columns taddr + 32 * piece of this
-// thread's lane.
-template <bool BF16, int PIECES>
-__device__ __forceinline__ void split_to_tmem(const float (&a)[64], uint32_t taddr) {
-#pragma unroll
-  for (int h = 0; h < 4; ++h) {  // 8 columns (16 values) per store
-    uint32_t out[PIECES][8];
-#pragma unroll
-    for (int j = 0; j < 8; ++j) {
-      const float x0 = a[16 * h + 2 * j], x1 = a[16 * h + 2 * j + 1];
-      if constexpr (!BF16) {
-        // hi = RN_f16(a); lo = RN_f16((a - hi) * 2^11): a - hi and the scaling are exact
-        const __half2 hi = __floats2half2_rn(x0, x1);
-        const float2 hf = __half22float2(hi);
-        const __half2 lo = __floats2half2_rn((x0 - hf.x) * 2048.0f, (x1 - hf.y) * 2048.0f);
-        out[0][j] = h2_as_u32(hi);
-        out[1][j] = h2_as_u32(lo);
-      } else {
-        // p0 = RN_bf16(a); p_j = RN_bf16(r_j), r_j = (r_{j-1} - p_{j-1}) * 2^8 (exact)
-        float r0 = x0, r1 = x1;
-#pragma unroll
-        for (int pc = 0; pc < PIECES; ++pc) {
-          const __nv_bfloat162 b = __floats2bfloat162_rn(r0, r1);
-          const float2 bf = __bfloat1622float2(b);
-          out[pc][j] = b2_as_u32(b);
-          r0 = (r0 - bf.x) * 256.0f;
-          r1 = (r1 - bf.y) * 256.0f;
-        }
-      }
-    }
-    // columns 8h .. 8h+7 of each piece
-#pragma unroll
-    for (int pc = 0; pc < PIECES; ++pc) tc_st_32x32b_x8(taddr + pc * 32 + 8 * h, out[pc]);
-  }
-}
-
 // In-place split of the TMA-staged FP32 B tile of the TCEC product: 64 rows
 // of G groups of 8 floats as G/4 boxes of 64 rows x 128 B (swizzled); hi / lo
 // are written as G/8 blocks of 64 rows x 128 B at offsets 0 and 64*G*16 (the

@@ -7,6 +7,7 @@
 // gridDim.z (partials added with FP32 atomics into a pre-zeroed C).
 #include <cuda_fp16.h>
 
+#include "grouped.h"
 #include "internal.h"
 
 namespace shg {
@@ -15,17 +16,16 @@ namespace {
 constexpr int BM = 128, BN = 64, BK = 16;
 
 template <bool TA, bool BH>
-__global__ void __launch_bounds__(256) simt_gemm_kernel(int M, int N, int K, const float* __restrict__ A,
-                                                       long long lda, const void* __restrict__ Bv, long long ldb,
-                                                       float* __restrict__ C, long long ldc, int k_chunk,
-                                                       int splits, int atomic, long long sa, long long sb,
-                                                       long long sc) {
+__device__ __forceinline__ void simt_gemm_body(int M, int N, int K, const float* __restrict__ A, long long lda,
+                                               const void* __restrict__ Bv, long long ldb, float* __restrict__ C,
+                                               long long ldc, int k_chunk, int splits, int atomic, long long sa,
+                                               long long sb, long long sc, int bx, int by, int bz) {
   __shared__ float As[2][BK][BM + 4];
   __shared__ float Bs[2][BK][BN];
   const int tid = threadIdx.x;
   const int ty = tid >> 4, tx = tid & 15;
-  const int m0 = blockIdx.y * BM, n0 = blockIdx.x * BN;
-  const int batch = blockIdx.z / splits, split = blockIdx.z % splits;
+  const int m0 = by * BM, n0 = bx * BN;
+  const int batch = bz / splits, split = bz % splits;
   const int kbeg = split * k_chunk;
   const int kend = min(K, kbeg + k_chunk);
   A += batch * sa;
@@ -119,7 +119,31 @@ __global__ void __launch_bounds__(256) simt_gemm_kernel(int M, int N, int K, con
   }
 }
 
+template <bool TA, bool BH>
+__global__ void __launch_bounds__(256) simt_gemm_kernel(int M, int N, int K, const float* __restrict__ A,
+                                                       long long lda, const void* __restrict__ Bv, long long ldb,
+                                                       float* __restrict__ C, long long ldc, int k_chunk,
+                                                       int splits, int atomic, long long sa, long long sb,
+                                                       long long sc) {
+  simt_gemm_body<TA, BH>(M, N, K, A, lda, Bv, ldb, C, ldc, k_chunk, splits, atomic, sa, sb, sc, blockIdx.x, blockIdx.y,
+                         blockIdx.z);
+}
+
+// One GEMM C = A B per problem of a batch (blockIdx.z), FP32 operands.
+__global__ void __launch_bounds__(256) simt_grouped_kernel(const SimtArg* __restrict__ args) {
+  const SimtArg a = args[blockIdx.z];
+  if (static_cast<int>(blockIdx.x) * BN >= a.N || static_cast<int>(blockIdx.y) * BM >= a.M) return;
+  simt_gemm_body<false, false>(a.M, a.N, a.K, a.A, a.lda, a.B, a.ldb, a.C, a.ldc, a.K, 1, 0, 0, 0, 0, blockIdx.x,
+                               blockIdx.y, 0);
+}
+
 }  // namespace
+
+int simt_grouped(const SimtArg* d, int n, int mmax, int nmax, cudaStream_t st) {
+  if (n <= 0) return SHG_OK;
+  simt_grouped_kernel<<<dim3((nmax + BN - 1) / BN, (mmax + BM - 1) / BM, n), 256, 0, st>>>(d);
+  return cuda_status(cudaGetLastError());
+}
 
 int simt_gemm(int64_t M, int64_t N, int64_t K, const float* A, int64_t lda, int trans_a, const void* B,
               int64_t ldb, int b_f16, float* C, int64_t ldc, int accumulate, int64_t batch, int64_t stride_a,

@@ -48,7 +48,12 @@ def batch():
 
 
 @pytest.mark.parametrize("q", [0, 1])
-def test_batched_matches_oracle(shg, batch, q):
+@pytest.mark.parametrize("grouped", ["1", "0"])
+def test_batched_matches_oracle(shg, batch, q, grouped, monkeypatch):
+    """Both execution paths: one grouped launch per step for the whole batch
+    (the default), and the per-problem launches on the library's streams
+    (SHG_BATCHED_GROUPED=0)."""
+    monkeypatch.setenv("SHG_BATCHED_GROUPED", grouped)
     specs, As = batch
     s = 16
     ranks = [sp["rank"] for sp in specs]
@@ -64,7 +69,9 @@ def test_batched_matches_oracle(shg, batch, q):
         assert abs(r_p - ref["r_p"]) <= 0.01 * ref["r_p"], (i, r_p, ref["r_p"])
 
 
-def test_generated_omegas_and_graph_replay(shg, batch):
+@pytest.mark.parametrize("grouped", ["1", "0"])
+def test_generated_omegas_and_graph_replay(shg, batch, grouped, monkeypatch):
+    monkeypatch.setenv("SHG_BATCHED_GROUPED", grouped)
     specs, As = batch
     s = 16
     ranks = [sp["rank"] for sp in specs]
@@ -91,3 +98,23 @@ def test_generated_omegas_and_graph_replay(shg, batch):
                              flags=flags)
         for a, b in zip(S1, out[1]):
             assert torch.allclose(a, b, rtol=1e-6, atol=0), rep
+
+
+def test_batched_odd_k_and_large_k_grouped(shg):
+    """The grouped path with odd k (padded k x k kernels) and k = 144 (the
+    panel Cholesky beyond shared memory) in one batch; all singular values
+    against the oracle."""
+    specs = [dict(m=700, n=600, rate=10.0, rank=17, seed=31), dict(m=900, n=800, rate=20.0, rank=128, seed=32),
+             dict(m=513, n=767, rate=8.0, rank=31, seed=33), dict(m=300, n=1000, rate=12.0, rank=64, seed=34)]
+    As = [batch_matrix(sp) for sp in specs]
+    ranks = [sp["rank"] for sp in specs]
+    s = 16
+    Oms = [omega_f16(A.shape[1], r + s, seed=200 + i) for i, (A, r) in enumerate(zip(As, ranks))]
+    Us, Ss, Vs = shg.shg_rsvd_batched([padded_f32(A) for A in As], ranks, s, 1,
+                                      omegas=[padded_f16(O) for O in Oms], use_graph=False)
+    for i, (A, O, r) in enumerate(zip(As, Oms, ranks)):
+        ref = OR.rsvd(A, O, p=r, q=1, fp16_basis=True)
+        S = Ss[i].cpu().numpy().astype(np.float64)
+        assert np.max(np.abs(S - ref["S"]) / ref["S"]) <= 1e-5, i
+        r_p = residual(A, Us[i].cpu().numpy(), Ss[i].cpu().numpy(), Vs[i].cpu().numpy())
+        assert abs(r_p - ref["r_p"]) <= 0.01 * ref["r_p"], (i, r_p, ref["r_p"])
