@@ -250,8 +250,9 @@ int shg_gram(int64_t m, int64_t k, const float* X, int64_t ldx, double* G, void*
 
 /*
  * CholeskyQR2 (the orthonormal basis of Algorithms 1 and 2):
- * twice { G = X^T X (compensated FP32 sums, FP64 result, as shg_gram),
- * G = R^T R (Cholesky elimination in double-float arithmetic, pairs of FP32
+ * twice { G = X^T X (FP64 result; the first pass with compensated FP32
+ * sums as shg_gram, the second, on the well-conditioned X R^-1, with FP32
+ * sums of 32-row slabs), G = R^T R (Cholesky elimination in double-float arithmetic, pairs of FP32
  * values with about 44 significant bits, on the power-of-4-scaled FP64 Gram
  * matrix), X <- X R^-1 (R^-1 in FP32) }.  X: m x k FP32 (ldx >= k),
  * overwritten by Q with Q^T Q = I and X_in = Q R, diag(R) > 0.
@@ -309,8 +310,8 @@ int shg_cholqr2_static(int64_t m, int64_t k, float* X, int64_t ldx, int32_t* d_f
  * SHG_SPLIT_AUTO (SHG_SPLIT_F16, switched to SHG_SPLIT_TF32 for the whole
  * call when the first projection's range check trips; synchronises the
  * stream once, not under capture) or SHG_FP32_SIMT (every GEMM in FP32
- * SIMT: the single-precision baseline).  Gram matrices are compensated FP32 sums
- * delivered in FP64, the Cholesky factorisations double-float (see
+ * SIMT: the single-precision baseline).  Gram matrices are FP32 sums
+ * delivered in FP64 (compensated, but for the second CholeskyQR pass), the Cholesky factorisations double-float (see
  * shg_cholqr2); the k x k eigensolver of B B^T is FP32 Jacobi refined by
  * FP64 Rayleigh quotients.
  * report (host pointer, nullable): when given, the call records CUDA events

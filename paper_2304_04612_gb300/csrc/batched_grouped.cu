@@ -122,13 +122,13 @@ int build(const BatchCall& c, uint8_t* ws, Plan* P, Tables* t) {
     (k <= chol_smem_kmax() ? cS : cP).push_back(CholArg{sw.G, sw.Rf, sw.chol, k});
     if (k <= chol_smem_kmax()) P->kmax_small = std::max(P->kmax_small, k);
     else P->kmax_panel = std::max(P->kmax_panel, k);
-    sY1.push_back(SimtArg{Y, ldk, sw.Rf, k, T, ldk, m, k, k});
-    sY2.push_back(SimtArg{T, ldk, sw.Rf, k, Y, ldk, m, k, k});
-    sZ1.push_back(SimtArg{Z, ldk, sw.Rf, k, T, ldk, nn, k, k});
-    sZ2.push_back(SimtArg{T, ldk, sw.Rf, k, Z, ldk, nn, k, k});
+    sY1.push_back(SimtArg{Y, ldk, sw.Rf, k, T, ldk, m, k, k, 1});
+    sY2.push_back(SimtArg{T, ldk, sw.Rf, k, Y, ldk, m, k, k, 1});
+    sZ1.push_back(SimtArg{Z, ldk, sw.Rf, k, T, ldk, nn, k, k, 1});
+    sZ2.push_back(SimtArg{T, ldk, sw.Rf, k, Z, ldk, nn, k, k, 1});
     // (a size-only plan, ws == nullptr, has no pointer arrays to read)
-    lU.push_back(SimtArg{Y, ldk, Up, r, ws ? c.U[i] : nullptr, r, m, r, k});
-    lV.push_back(SimtArg{Bt, ldk, Ups, r, ws ? c.V[i] : nullptr, r, nn, r, k});
+    lU.push_back(SimtArg{Y, ldk, Up, r, ws ? c.U[i] : nullptr, r, m, r, k, 0});
+    lV.push_back(SimtArg{Bt, ldk, Ups, r, ws ? c.V[i] : nullptr, r, nn, r, k, 0});
     cvY.push_back(ConvArg{Y, ldk, H, nullptr, ldk, m, k});
     cvZ.push_back(ConvArg{Z, ldk, H, nullptr, ldk, nn, k});
     spY.push_back(ConvArg{Y, ldk, H, Hlo, ldk, m, k});
@@ -224,7 +224,8 @@ int cholqr2_grouped(const Plan& P, uint8_t* tb, size_t gram1, size_t simt1, size
   for (int pass = 0; pass < 2; ++pass) {
     int rc = zero_grouped(reinterpret_cast<const ZeroArg*>(tb + P.zG), n, P.max_kk, st);
     if (rc != SHG_OK) return rc;
-    rc = gram_grouped(reinterpret_cast<const GramArg*>(tb + (pass == 0 ? gram1 : gram2)), n, P.kmax, rows_max, st);
+    rc = gram_grouped(reinterpret_cast<const GramArg*>(tb + (pass == 0 ? gram1 : gram2)), n, P.kmax, rows_max, st,
+                      pass == 1);
     if (rc != SHG_OK) return rc;
     rc = chol_small_grouped(reinterpret_cast<const CholArg*>(tb + P.cholS), P.n_cholS, P.kmax_small, flags, st);
     if (rc != SHG_OK) return rc;

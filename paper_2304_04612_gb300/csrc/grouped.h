@@ -60,14 +60,14 @@ struct CholArg {      // Rf = FP32(R^-1), G = R^T R; scratch as chol_inv's (2 k^
   double* scratch;
   int k;
 };
-struct SimtArg {      // C = A B (FP32, row-major, no transposes)
+struct SimtArg {      // C = A B (FP32, row-major, no transposes); upper_b: B upper triangular
   const float* A;
   long long lda;
   const float* B;
   long long ldb;
   float* C;
   long long ldc;
-  int M, N, K;
+  int M, N, K, upper_b;
 };
 struct ConvArg {      // y = RN_f16(x), and with ylo the TCEC split (y hi, ylo lo)
   const float* x;
@@ -91,7 +91,7 @@ struct EigArg {       // eigenvectors of G by one-CTA Jacobi, then Rayleigh quot
 
 int zero_grouped(const ZeroArg* d, int n, long long max_bytes, cudaStream_t st);
 int gaussian_grouped(uint64_t seed, const GaussArg* d, int n, long long max_elems, cudaStream_t st);
-int gram_grouped(const GramArg* d, int n, int kmax, int mmax, cudaStream_t st);
+int gram_grouped(const GramArg* d, int n, int kmax, int mmax, cudaStream_t st, bool plain = false);
 // Cholesky + R^-1 of n problems with k <= chol_smem_kmax() (one CTA each).
 int chol_small_grouped(const CholArg* d, int n, int kmax, int32_t* flags, cudaStream_t st);
 // The same beyond shared memory, in 32-column panels (all panels of all problems).

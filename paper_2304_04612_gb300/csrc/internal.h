@@ -64,10 +64,12 @@ void tc_tune_clear();
 // a cached CUDA graph captured under other launch configurations is not replayed.
 unsigned long long tc_tune_generation();
 
-// FP32 SIMT GEMM, batched over gridDim.z with element strides.
+// FP32 SIMT GEMM, batched over gridDim.z with element strides.  upper_b:
+// B is upper triangular (zeros stored below the diagonal), whose zero terms
+// are skipped.
 int simt_gemm(int64_t M, int64_t N, int64_t K, const float* A, int64_t lda, int trans_a, const void* B,
               int64_t ldb, int b_f16, float* C, int64_t ldc, int accumulate, int64_t batch,
-              int64_t stride_a, int64_t stride_b, int64_t stride_c, cudaStream_t stream);
+              int64_t stride_a, int64_t stride_b, int64_t stride_c, cudaStream_t stream, int upper_b = 0);
 
 // y = RN_bf16(x) element-wise for an FP16 matrix (BF16 test matrices from
 // the FP16 Gaussian stream).

@@ -12,6 +12,7 @@
 // The eigensolver is a parallel cyclic Jacobi method (round-robin pairing)
 // in FP32 on the scaled Gram matrix; eigenvalues are then refined as FP64
 // Rayleigh quotients v^T G v / v^T v with the FP64 Gram matrix.
+#include <algorithm>
 #include <atomic>
 #include <cooperative_groups.h>
 #include <cuda_fp16.h>
@@ -37,7 +38,23 @@ namespace {
 // by gamma_128^2 sum |x_ri x_rj| (about 6e-11 of it, 4e-14 for random signs);
 // the chunk sums meet in FP64 atomics.  The _rn intrinsics keep the compiler
 // from contracting the transformations into FMAs.
+//
+// The second pass of CholeskyQR2 factors X R^-1, whose condition number is
+// near 1 whatever X's was, so its Gram needs only working precision (the
+// mixed-precision CholeskyQR2 of Yamazaki, Tomov and Dongarra, 2015: the
+// doubled precision goes to the first Gram only).  The plain variant
+// accumulates each 32-row slab with FP32 FMAs and adds the slab sums into
+// the (s, c) pair with TwoSum, which bounds the error of an entry by about
+// gamma_32 sum |x_ri x_rj| + O(u^2): one FMA per product instead of the ten
+// operations of the compensated step.
 constexpr int kFlushRows = 128;
+
+__device__ __forceinline__ void two_sum_into(float p, float& s, float& c) {
+  const float t = __fadd_rn(s, p);
+  const float z = __fsub_rn(t, s);
+  c = __fadd_rn(c, __fadd_rn(__fsub_rn(s, __fsub_rn(t, z)), __fsub_rn(p, z)));
+  s = t;
+}
 
 __device__ __forceinline__ void dot2_step(float x, float y, float& s, float& c) {
   const float p = __fmul_rn(x, y);
@@ -49,14 +66,23 @@ __device__ __forceinline__ void dot2_step(float x, float y, float& s, float& c) 
   c = __fadd_rn(c, __fadd_rn(r, e));
 }
 
+template <bool PLAIN>
 __device__ __forceinline__ void gram_body(int m, int k, const float* __restrict__ X, long long ldx,
                                           double* __restrict__ G, int rows_per_chunk, int ti, int tj, int chunk) {
   if (ti > tj) return;
-  __shared__ float Xi[32][33], Xj[32][33];
+  // Xj rows 16-byte aligned: a thread reads its four columns as one float4
+  __shared__ float Xi[32][33];
+  __shared__ __align__(16) float Xj[32][36];
   const int tid = threadIdx.x;
-  const int a = tid >> 3;        // 0..31: row of the G tile
-  const int b4 = (tid & 7) * 4;  // 4 columns
-  const int ci = ti * 32 + (tid & 31), cj = tj * 32 + (tid & 31);
+  const int warp = tid >> 5, lane = tid & 31;
+  // warp w owns rows 8 (w >> 1) .. + 8 and columns 16 (w & 1) .. + 16 of the
+  // G tile (a thread: row a, columns b4 .. b4 + 3); a warp whose part lies
+  // wholly in the padding beyond k or below the diagonal skips the sums
+  const int a = 8 * (warp >> 1) + (lane >> 2);
+  const int b4 = 16 * (warp & 1) + (lane & 3) * 4;
+  const bool live = ti * 32 + 8 * (warp >> 1) < k && tj * 32 + 16 * (warp & 1) < k &&
+                    !(ti == tj && 16 * (warp & 1) + 15 < 8 * (warp >> 1));
+  const int ci = ti * 32 + lane, cj = tj * 32 + lane;
   const int lr = tid >> 5;  // this thread loads rows lr, lr + 8, lr + 16, lr + 24 of a 32-row slab
   double acc[4] = {0, 0, 0, 0};
   float s[4] = {0, 0, 0, 0}, c[4] = {0, 0, 0, 0};
@@ -82,11 +108,25 @@ __device__ __forceinline__ void gram_body(int m, int k, const float* __restrict_
     }
     __syncthreads();
     if (rb + 32 < r1) fetch(rb + 32);  // the next slab's loads overlap this slab's sums
+    if (live) {
+      float p[4] = {0.0f, 0.0f, 0.0f, 0.0f};
 #pragma unroll 4
-    for (int rr = 0; rr < 32; ++rr) {
-      const float xa = Xi[rr][a];
+      for (int rr = 0; rr < 32; ++rr) {
+        const float xa = Xi[rr][a];
+        const float4 xb4 = *reinterpret_cast<const float4*>(&Xj[rr][b4]);
+        const float xb[4] = {xb4.x, xb4.y, xb4.z, xb4.w};
 #pragma unroll
-      for (int q = 0; q < 4; ++q) dot2_step(xa, Xj[rr][b4 + q], s[q], c[q]);
+        for (int q = 0; q < 4; ++q) {
+          if (PLAIN)
+            p[q] = __fmaf_rn(xa, xb[q], p[q]);
+          else
+            dot2_step(xa, xb[q], s[q], c[q]);
+        }
+      }
+      if (PLAIN) {
+#pragma unroll
+        for (int q = 0; q < 4; ++q) two_sum_into(p[q], s[q], c[q]);
+      }
     }
     __syncthreads();
     since += 32;
@@ -109,9 +149,10 @@ __device__ __forceinline__ void gram_body(int m, int k, const float* __restrict_
   }
 }
 
+template <bool PLAIN>
 __global__ void __launch_bounds__(256) gram_kernel(int m, int k, const float* __restrict__ X, long long ldx,
                                                    double* __restrict__ G, int rows_per_chunk) {
-  gram_body(m, k, X, ldx, G, rows_per_chunk, blockIdx.y, blockIdx.x, blockIdx.z);
+  gram_body<PLAIN>(m, k, X, ldx, G, rows_per_chunk, blockIdx.y, blockIdx.x, blockIdx.z);
 }
 
 // ------------------------------------------------ Cholesky + inverse
@@ -965,45 +1006,79 @@ __global__ void __launch_bounds__(kJacGridThreads) jacobi_grid_kernel(int k, con
 
 // lambda_i = v_i^T G v_i / v_i^T v_i (FP64 Rayleigh quotient, G symmetric
 // from its upper triangle; the FP32 rotations leave |v_i| = 1 only to
-// ~1e-5); one CTA per i.  nrm[i] = |v_i| (FP64).
+// ~1e-5) for the kRayVecs vectors i0 .. i0 + kRayVecs - 1 of one CTA, which
+// share every load of G.  By symmetry v^T G v = sum_b v_b (g_bb v_b +
+// 2 sum_{a<b} g_ab v_a): a thread per column b (consecutive threads read
+// consecutive elements of a row of G), one FP64 FMA per element of the
+// strict upper triangle and vector.  nrm[i] = |v_i| (FP64).  Dynamic shared
+// memory: kRayVecs * k doubles.
+constexpr int kRayVecs = 4;
+
 __device__ __forceinline__ void rayleigh_body(int k, const double* __restrict__ G, const float* __restrict__ V,
-                                              double* __restrict__ lam, double* __restrict__ nrm, int i) {
-  __shared__ double red[2][32];
-  double s = 0.0, q = 0.0;
-  for (int e = threadIdx.x; e < k * k; e += blockDim.x) {
-    const int a = e / k, b = e - a * k;
-    const double g = G[min(a, b) * k + max(a, b)];
-    s = fma(static_cast<double>(V[a * k + i]) * g, static_cast<double>(V[b * k + i]), s);
-  }
-  for (int a = threadIdx.x; a < k; a += blockDim.x) {
-    const double v = V[a * k + i];
-    q = fma(v, v, q);
-  }
-#pragma unroll
-  for (int o = 16; o > 0; o >>= 1) {
-    s += __shfl_xor_sync(0xffffffffu, s, o);
-    q += __shfl_xor_sync(0xffffffffu, q, o);
-  }
-  if ((threadIdx.x & 31) == 0) {
-    red[0][threadIdx.x >> 5] = s;
-    red[1][threadIdx.x >> 5] = q;
+                                              double* __restrict__ lam, double* __restrict__ nrm, int i0) {
+  extern __shared__ double rv[];  // [kRayVecs][k]: the vectors in FP64
+  __shared__ double red[2 * kRayVecs][32];
+  const int nv = min(kRayVecs, k - i0);
+  for (int e = threadIdx.x; e < kRayVecs * k; e += blockDim.x) {
+    const int v = e / k, a = e - v * k;
+    rv[e] = (v < nv) ? static_cast<double>(V[a * k + i0 + v]) : 0.0;
   }
   __syncthreads();
-  if (threadIdx.x == 0) {
-    double t = 0.0, u = 0.0;
-    for (int w = 0; w < (blockDim.x + 31) / 32; ++w) {
-      t += red[0][w];
-      u += red[1][w];
+  double s[kRayVecs], q[kRayVecs];
+#pragma unroll
+  for (int v = 0; v < kRayVecs; ++v) s[v] = q[v] = 0.0;
+  for (int b = threadIdx.x; b < k; b += blockDim.x) {
+    double u[kRayVecs];
+#pragma unroll
+    for (int v = 0; v < kRayVecs; ++v) u[v] = 0.0;
+    for (int a = 0; a < b; ++a) {
+      const double g = G[a * k + b];
+#pragma unroll
+      for (int v = 0; v < kRayVecs; ++v) u[v] = fma(g, rv[v * k + a], u[v]);
     }
-    lam[i] = t / u;
-    nrm[i] = sqrt(u);
+    const double gbb = G[b * k + b];
+#pragma unroll
+    for (int v = 0; v < kRayVecs; ++v) {
+      const double vb = rv[v * k + b];
+      s[v] = fma(vb, fma(gbb, vb, 2.0 * u[v]), s[v]);
+      q[v] = fma(vb, vb, q[v]);
+    }
+  }
+#pragma unroll
+  for (int v = 0; v < kRayVecs; ++v) {
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+      s[v] += __shfl_xor_sync(0xffffffffu, s[v], o);
+      q[v] += __shfl_xor_sync(0xffffffffu, q[v], o);
+    }
+  }
+  if ((threadIdx.x & 31) == 0) {
+#pragma unroll
+    for (int v = 0; v < kRayVecs; ++v) {
+      red[v][threadIdx.x >> 5] = s[v];
+      red[kRayVecs + v][threadIdx.x >> 5] = q[v];
+    }
+  }
+  __syncthreads();
+  if (static_cast<int>(threadIdx.x) < nv) {
+    const int v = threadIdx.x;
+    double t = 0.0, w = 0.0;
+    for (int x = 0; x < (blockDim.x + 31) / 32; ++x) {
+      t += red[v][x];
+      w += red[kRayVecs + v][x];
+    }
+    lam[i0 + v] = t / w;
+    nrm[i0 + v] = sqrt(w);
   }
 }
 
 __global__ void rayleigh_kernel(int k, const double* __restrict__ G, const float* __restrict__ V,
                                 double* __restrict__ lam, double* __restrict__ nrm) {
-  rayleigh_body(k, G, V, lam, nrm, blockIdx.x);
+  rayleigh_body(k, G, V, lam, nrm, blockIdx.x * kRayVecs);
 }
+
+// Threads of a Rayleigh CTA: a thread per column, in whole warps, at most 256.
+inline int rayleigh_threads(int k) { return std::min(256, (k + 31) / 32 * 32); }
 
 // Sort eigenvalues descending (ties by index), S[j] = sqrt(lambda) for the
 // top p, Up = V[:, perm[:p]] normalised to unit length and Ups = Up / S
@@ -1115,7 +1190,7 @@ size_t cholqr_small_bytes(int64_t k) {
   return off[4];
 }
 
-int gram_f64(int64_t m, int64_t k, const float* X, int64_t ldx, double* G, cudaStream_t st) {
+int gram_f64(int64_t m, int64_t k, const float* X, int64_t ldx, double* G, cudaStream_t st, bool plain) {
   if (cudaMemsetAsync(G, 0, k * k * sizeof(double), st) != cudaSuccess) return SHG_ERR_CUDA;
   const int t = static_cast<int>((k + 31) / 32);
   const long long tiles = static_cast<long long>(t) * (t + 1) / 2;
@@ -1129,7 +1204,10 @@ int gram_f64(int64_t m, int64_t k, const float* X, int64_t ldx, double* G, cudaS
   chunks = (m + rows - 1) / rows;
   if (chunks > 65535) return SHG_ERR_UNSUPPORTED;
   dim3 grid(t, t, static_cast<unsigned>(chunks));
-  gram_kernel<<<grid, 256, 0, st>>>(static_cast<int>(m), static_cast<int>(k), X, ldx, G, static_cast<int>(rows));
+  if (plain)
+    gram_kernel<true><<<grid, 256, 0, st>>>(static_cast<int>(m), static_cast<int>(k), X, ldx, G, static_cast<int>(rows));
+  else
+    gram_kernel<false><<<grid, 256, 0, st>>>(static_cast<int>(m), static_cast<int>(k), X, ldx, G, static_cast<int>(rows));
   return cuda_status(cudaGetLastError());
 }
 
@@ -1241,7 +1319,13 @@ int jacobi_eig(int64_t k, const double* G, float* V, float* scratch, void* eig, 
 int rayleigh_sort(int64_t k, int64_t p, const double* G, const float* V, double* lam, float* S, float* Up,
                   float* Ups, cudaStream_t st) {
   double* nrm = lam + k;  // lam holds 2k doubles
-  rayleigh_kernel<<<static_cast<unsigned>(k), 256, 0, st>>>(static_cast<int>(k), G, V, lam, nrm);
+  const size_t rsm = kRayVecs * static_cast<size_t>(k) * sizeof(double);
+  if (!smem_fits(rsm)) return SHG_ERR_UNSUPPORTED;
+  if (rsm > 48 * 1024 && cudaFuncSetAttribute(rayleigh_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                              static_cast<int>(rsm)) != cudaSuccess)
+    return SHG_ERR_CUDA;
+  rayleigh_kernel<<<static_cast<unsigned>((k + kRayVecs - 1) / kRayVecs), rayleigh_threads(static_cast<int>(k)), rsm,
+                    st>>>(static_cast<int>(k), G, V, lam, nrm);
   if (cudaGetLastError() != cudaSuccess) return SHG_ERR_CUDA;
   sort_select_kernel<<<1, 1024, p * (2 * sizeof(double) + sizeof(int)), st>>>(static_cast<int>(k), static_cast<int>(p),
                                                                               lam, nrm, V, S, Up, Ups);
@@ -1289,14 +1373,15 @@ int cholqr2(int64_t m, int64_t k, float* X, int64_t ldx, float* T, int64_t ldt, 
   for (int pass = 0; pass < 2; ++pass) {
     float* dst = (pass == 0) ? T : X;
     const int64_t ldd = (pass == 0) ? ldt : ldx;
-    if ((rc = gram_f64(m, k, src, lds, w.G, st))) return rc;
+    // the first pass in doubled precision, the second in working precision
+    if ((rc = gram_f64(m, k, src, lds, w.G, st, pass == 1))) return rc;
     if ((rc = chol_inv(k, w.G, w.Rf, w.chol, flags, st))) return rc;
     if (min_pivot) {
       pivot_ratio_kernel<<<1, 256, 0, st>>>(static_cast<int>(k), w.G, w.Rf,
                                             reinterpret_cast<unsigned long long*>(min_pivot));
       if ((rc = cuda_status(cudaGetLastError()))) return rc;
     }
-    if ((rc = simt_gemm(m, k, k, src, lds, 0, w.Rf, k, 0, dst, ldd, 0, 1, 0, 0, 0, st))) return rc;
+    if ((rc = simt_gemm(m, k, k, src, lds, 0, w.Rf, k, 0, dst, ldd, 0, 1, 0, 0, 0, st, 1))) return rc;
     src = dst;
     lds = ldd;
   }
@@ -1322,12 +1407,13 @@ __global__ void zero_grouped_kernel(const ZeroArg* __restrict__ args) {
   }
 }
 
+template <bool PLAIN>
 __global__ void __launch_bounds__(256) gram_grouped_kernel(const GramArg* __restrict__ args, int cmax) {
   const int p = blockIdx.z / cmax, chunk = blockIdx.z - p * cmax;
   const GramArg a = args[p];
   const int t = (a.k + 31) / 32;
   if (static_cast<int>(blockIdx.x) >= t || static_cast<int>(blockIdx.y) >= t || chunk * kGramChunkRows >= a.m) return;
-  gram_body(a.m, a.k, a.X, a.ldx, a.G, kGramChunkRows, blockIdx.y, blockIdx.x, chunk);
+  gram_body<PLAIN>(a.m, a.k, a.X, a.ldx, a.G, kGramChunkRows, blockIdx.y, blockIdx.x, chunk);
 }
 
 __global__ void __launch_bounds__(1024) chol_small_grouped_kernel(const CholArg* __restrict__ args, int* flags) {
@@ -1395,8 +1481,8 @@ __global__ void __launch_bounds__(512) apply_v_grouped_kernel(const EigArg* __re
 
 __global__ void rayleigh_grouped_kernel(const EigArg* __restrict__ args) {
   const EigArg a = args[blockIdx.y];
-  if (static_cast<int>(blockIdx.x) >= a.k) return;
-  rayleigh_body(a.k, a.G, a.V, a.lam, a.lam + a.k, blockIdx.x);
+  if (static_cast<int>(blockIdx.x) * kRayVecs >= a.k) return;
+  rayleigh_body(a.k, a.G, a.V, a.lam, a.lam + a.k, blockIdx.x * kRayVecs);
 }
 
 __global__ void sort_select_grouped_kernel(const EigArg* __restrict__ args) {
@@ -1419,10 +1505,13 @@ int zero_grouped(const ZeroArg* d, int n, long long max_bytes, cudaStream_t st) 
   return cuda_status(cudaGetLastError());
 }
 
-int gram_grouped(const GramArg* d, int n, int kmax, int mmax, cudaStream_t st) {
+int gram_grouped(const GramArg* d, int n, int kmax, int mmax, cudaStream_t st, bool plain) {
   if (n <= 0) return SHG_OK;
   const int t = (kmax + 31) / 32, cmax = (mmax + kGramChunkRows - 1) / kGramChunkRows;
-  gram_grouped_kernel<<<dim3(t, t, n * cmax), 256, 0, st>>>(d, cmax);
+  if (plain)
+    gram_grouped_kernel<true><<<dim3(t, t, n * cmax), 256, 0, st>>>(d, cmax);
+  else
+    gram_grouped_kernel<false><<<dim3(t, t, n * cmax), 256, 0, st>>>(d, cmax);
   return cuda_status(cudaGetLastError());
 }
 
@@ -1495,7 +1584,8 @@ int eig_grouped(const EigArg* d, int n, int kmax, int pmax, int tbmax, cudaStrea
   constexpr int rb = 8;
   apply_v_grouped_kernel<<<dim3((kmax + rb - 1) / rb, n), (h + 31) / 32 * 32, rb * kp * sizeof(float), st>>>(d);
   if (cudaGetLastError() != cudaSuccess) return SHG_ERR_CUDA;
-  rayleigh_grouped_kernel<<<dim3(kmax, n), 256, 0, st>>>(d);
+  rayleigh_grouped_kernel<<<dim3((kmax + kRayVecs - 1) / kRayVecs, n), rayleigh_threads(kmax),
+                            kRayVecs * kmax * sizeof(double), st>>>(d);
   if (cudaGetLastError() != cudaSuccess) return SHG_ERR_CUDA;
   sort_select_grouped_kernel<<<n, 1024, pmax * (2 * sizeof(double) + sizeof(int)), st>>>(d);
   return cuda_status(cudaGetLastError());

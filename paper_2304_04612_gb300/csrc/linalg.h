@@ -18,7 +18,10 @@ struct SmallWs {
 };
 SmallWs small_ws(void* base, int64_t k);
 
-int gram_f64(int64_t m, int64_t k, const float* X, int64_t ldx, double* G, cudaStream_t st);
+// G = X^T X (upper triangle, FP64, zeroed first): compensated FP32 sums
+// (about 2^-48 relative error), or with `plain` FP32 sums of 32-row slabs
+// (working precision: the second CholeskyQR pass).
+int gram_f64(int64_t m, int64_t k, const float* X, int64_t ldx, double* G, cudaStream_t st, bool plain = false);
 // Rinv = FP32(R^-1) with G = R^T R (FP64, upper Cholesky).
 int chol_inv(int64_t k, const double* G, float* Rinv, double* scratch, int32_t* flags, cudaStream_t st);
 // Eigenvectors V (k x k FP32, columns) of the symmetric matrix whose upper

@@ -4,7 +4,10 @@
 //
 // C[b] (+)= op(A[b]) * B[b], 128 x 64 output tile per 256-thread CTA (8 x 4
 // per thread), 16-deep K tiles double-buffered in shared memory, split-K over
-// gridDim.z (partials added with FP32 atomics into a pre-zeroed C).
+// gridDim.z (partials added with FP32 atomics into a pre-zeroed C).  With
+// upper_b, B is upper triangular (its zero rows below the diagonal are
+// stored), and a tile's K range stops at the tile's last column: the terms
+// skipped are exact zeros, so C is the same to the bit.
 #include <cuda_fp16.h>
 
 #include "grouped.h"
@@ -19,7 +22,7 @@ template <bool TA, bool BH>
 __device__ __forceinline__ void simt_gemm_body(int M, int N, int K, const float* __restrict__ A, long long lda,
                                                const void* __restrict__ Bv, long long ldb, float* __restrict__ C,
                                                long long ldc, int k_chunk, int splits, int atomic, long long sa,
-                                               long long sb, long long sc, int bx, int by, int bz) {
+                                               long long sb, long long sc, int bx, int by, int bz, int upper_b) {
   __shared__ float As[2][BK][BM + 4];
   __shared__ float Bs[2][BK][BN];
   const int tid = threadIdx.x;
@@ -27,7 +30,7 @@ __device__ __forceinline__ void simt_gemm_body(int M, int N, int K, const float*
   const int m0 = by * BM, n0 = bx * BN;
   const int batch = bz / splits, split = bz % splits;
   const int kbeg = split * k_chunk;
-  const int kend = min(K, kbeg + k_chunk);
+  const int kend = min(min(K, kbeg + k_chunk), upper_b ? n0 + BN : K);
   A += batch * sa;
   C += batch * sc;
   const float* Bf = reinterpret_cast<const float*>(Bv) + (BH ? 0 : batch * sb);
@@ -124,9 +127,9 @@ __global__ void __launch_bounds__(256) simt_gemm_kernel(int M, int N, int K, con
                                                        long long lda, const void* __restrict__ Bv, long long ldb,
                                                        float* __restrict__ C, long long ldc, int k_chunk,
                                                        int splits, int atomic, long long sa, long long sb,
-                                                       long long sc) {
+                                                       long long sc, int upper_b) {
   simt_gemm_body<TA, BH>(M, N, K, A, lda, Bv, ldb, C, ldc, k_chunk, splits, atomic, sa, sb, sc, blockIdx.x, blockIdx.y,
-                         blockIdx.z);
+                         blockIdx.z, upper_b);
 }
 
 // One GEMM C = A B per problem of a batch (blockIdx.z), FP32 operands.
@@ -134,7 +137,7 @@ __global__ void __launch_bounds__(256) simt_grouped_kernel(const SimtArg* __rest
   const SimtArg a = args[blockIdx.z];
   if (static_cast<int>(blockIdx.x) * BN >= a.N || static_cast<int>(blockIdx.y) * BM >= a.M) return;
   simt_gemm_body<false, false>(a.M, a.N, a.K, a.A, a.lda, a.B, a.ldb, a.C, a.ldc, a.K, 1, 0, 0, 0, 0, blockIdx.x,
-                               blockIdx.y, 0);
+                               blockIdx.y, 0, a.upper_b);
 }
 
 }  // namespace
@@ -147,7 +150,7 @@ int simt_grouped(const SimtArg* d, int n, int mmax, int nmax, cudaStream_t st) {
 
 int simt_gemm(int64_t M, int64_t N, int64_t K, const float* A, int64_t lda, int trans_a, const void* B,
               int64_t ldb, int b_f16, float* C, int64_t ldc, int accumulate, int64_t batch, int64_t stride_a,
-              int64_t stride_b, int64_t stride_c, cudaStream_t stream) {
+              int64_t stride_b, int64_t stride_c, cudaStream_t stream, int upper_b) {
   if (M <= 0 || N <= 0 || K <= 0 || batch <= 0) return SHG_ERR_INVALID_ARG;
   if (M >= (1ll << 31) || N >= (1ll << 31) || K >= (1ll << 31)) return SHG_ERR_INVALID_ARG;
   const int gx = static_cast<int>((N + BN - 1) / BN), gy = static_cast<int>((M + BM - 1) / BM);
@@ -171,7 +174,7 @@ int simt_gemm(int64_t M, int64_t N, int64_t K, const float* A, int64_t lda, int 
 #define SHG_SIMT(TA, BH)                                                                                  \
   simt_gemm_kernel<TA, BH><<<grid, 256, 0, stream>>>(static_cast<int>(M), static_cast<int>(N),             \
                                                      static_cast<int>(K), A, lda, B, ldb, C, ldc, kc,       \
-                                                     splits, atomic, stride_a, stride_b, stride_c)
+                                                     splits, atomic, stride_a, stride_b, stride_c, upper_b)
   if (trans_a) {
     if (b_f16) SHG_SIMT(true, true); else SHG_SIMT(true, false);
   } else {
