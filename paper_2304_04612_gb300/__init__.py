@@ -306,8 +306,10 @@ def shg_rsvd_batched(As, ranks, oversampling: int, power_iters: int = 0, omegas=
     else:
         Us, Ss, Vs = out
     lib = _lib.load()
-    need = rsvd_batched_workspace_size(ms, ns, ranks, oversampling, power_iters)
-    ws = workspace if workspace is not None else torch.empty(need, dtype=torch.uint8, device=dev_)
+    if workspace is None:   # (a caller's workspace is checked against the need by the library)
+        need = rsvd_batched_workspace_size(ms, ns, ranks, oversampling, power_iters)
+        workspace = torch.empty(need, dtype=torch.uint8, device=dev_)
+    ws = workspace
     fl = flags if flags is not None else new_flags(dev_)
     if omegas is None:
         om_arr, ldo_arr = None, None

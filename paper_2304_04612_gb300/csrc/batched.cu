@@ -229,12 +229,13 @@ extern "C" int shg_rsvd_batched(int batch, const int64_t* m, const int64_t* n, c
                        grouped_batch_eligible(bc, variant);
   if (grouped && !use_graph) {
     if ((rc = grouped_batch_prepare(bc, ws, ws_bytes, st)) != SHG_OK) return rc;
-    return grouped_batch_enqueue(bc, ws, d_flags, st);
+    return grouped_batch_enqueue(bc, ws, d_flags, st, p->s, p->done, p->fork);
   }
   if (!use_graph || cap != cudaStreamCaptureStatusNone) return enqueue(a, *p, per, grid_share, st);
 
   std::vector<uint8_t> key = make_key(a, dev, grid_share);
   put(key, grouped);
+  put(key, grouped ? grouped_lane_limit() : 0);
   for (GraphEntry& e : g_graphs) {
     if (e.dev == dev && e.key == key) {
       e.last_use = ++g_tick;
@@ -247,7 +248,8 @@ extern "C" int shg_rsvd_batched(int batch, const int64_t* m, const int64_t* n, c
   // caller's earlier work
   if (grouped && (rc = grouped_batch_prepare(bc, ws, ws_bytes, st)) != SHG_OK) return rc;
   if (cudaStreamBeginCapture(p->capture, cudaStreamCaptureModeRelaxed) != cudaSuccess) return SHG_ERR_CUDA;
-  rc = grouped ? grouped_batch_enqueue(bc, ws, d_flags, p->capture) : enqueue(a, *p, per, grid_share, p->capture);
+  rc = grouped ? grouped_batch_enqueue(bc, ws, d_flags, p->capture, p->s, p->done, p->fork)
+               : enqueue(a, *p, per, grid_share, p->capture);
   cudaGraph_t graph = nullptr;
   const cudaError_t end = cudaStreamEndCapture(p->capture, &graph);
   if (rc != SHG_OK) {

@@ -6,8 +6,8 @@
 // The host builds, once per set of arguments, the per-problem argument
 // arrays of every step (device pointers into one workspace slice per
 // problem, laid out as shg_rsvd lays out its workspace), the projections'
-// problem tables with their TMA tensor maps and the projections' unit lists,
-// and copies them into the workspace after the slices.  The step sequence
+// problem tables with their TMA tensor maps and the numbering of their work
+// units, and copies them into the workspace after the slices.  The step sequence
 // then refers to them only through device pointers, so it can be captured
 // into a CUDA graph and replayed.
 //
@@ -16,7 +16,9 @@
 // grouped tensor-core kernel (grouped_tc.cu), whose 128-column tiles and
 // drain interval match the 128-column kernel's defaults.
 #include <algorithm>
+#include <cstdlib>
 #include <cstring>
+#include <initializer_list>
 #include <vector>
 
 #include "grouped.h"
@@ -39,37 +41,45 @@ struct Plan {
   size_t cholS = 0, cholP = 0;
   size_t simtY1 = 0, simtY2 = 0, simtZ1 = 0, simtZ2 = 0, liftU = 0, liftV = 0;
   size_t convY = 0, convZ = 0, splitY = 0, eig = 0;
-  size_t pNN = 0, uNN = 0, pNH = 0, uNH = 0, pTN = 0, uTN = 0, pB = 0, uB = 0;
+  size_t pNN = 0, pNH = 0, pTN = 0, pB = 0;
   int n_gen = 0, n_cholS = 0, n_cholP = 0;
   long long units_NN = 0, units_NH = 0, units_TN = 0, units_B = 0;
   int kmax = 0, kmax_small = 0, kmax_panel = 0, mmax = 0, nmax = 0, rmax = 0, tbmax = 0;
   long long max_mk = 0, max_nk = 0, max_kk = 0;
 };
 
+// The argument tables, packed at 256-byte offsets; without `copy` only the
+// offsets are worked out (the size-only plan of a workspace query).
 struct Tables {
   std::vector<uint8_t> buf;
   size_t off = 0;
+  bool copy = true;
   template <typename T>
   size_t add(const std::vector<T>& v) {
     const size_t o = off;
     off = align256(off + v.size() * sizeof(T));
-    buf.resize(off);
-    if (!v.empty()) std::memcpy(buf.data() + o, v.data(), v.size() * sizeof(T));
+    if (copy) {
+      if (buf.capacity() < off) buf.reserve(2 * off);
+      buf.resize(off);
+      if (!v.empty()) std::memcpy(buf.data() + o, v.data(), v.size() * sizeof(T));
+    }
     return o;
   }
 };
 
-// The plan of call c; with ws != nullptr also the argument tables (device
-// pointers into ws) in *t.  Returns SHG_OK or an error.
-int build(const BatchCall& c, uint8_t* ws, Plan* P, Tables* t) {
-  const int n = c.batch;
+// The plan of the problems idx of call c (a lane); with ws != nullptr (the
+// lane's region of the workspace) also the argument tables (device pointers
+// into ws) in *t.  Returns SHG_OK or an error.
+int build(const BatchCall& c, const std::vector<int>& idx, uint8_t* ws, Plan* P, Tables* t) {
+  const int n = static_cast<int>(idx.size());
   P->n = n;
   P->q = c.q;
   P->slice.resize(n);
   size_t off = 0;
-  for (int i = 0; i < n; ++i) {
+  for (int j = 0; j < n; ++j) {
+    const int i = idx[j];
     const int64_t k = c.rank[i] + c.s;
-    P->slice[i] = off;
+    P->slice[j] = off;
     off += align256(rsvd_layout(c.m[i], c.n[i], k, c.rank[i]).total);
   }
   P->slices_bytes = off;
@@ -81,12 +91,21 @@ int build(const BatchCall& c, uint8_t* ws, Plan* P, Tables* t) {
   std::vector<ConvArg> cvY, cvZ, spY;
   std::vector<EigArg> eg;
   std::vector<GemmProblem> pNN, pNH, pTN, pB;
-  for (int i = 0; i < n; ++i) {
+  for (auto* v : {&zY, &zZ, &zB, &zG}) v->reserve(n);
+  gen.reserve(n);
+  for (auto* v : {&gY1, &gY2, &gZ1, &gZ2, &gB}) v->reserve(n);
+  for (auto* v : {&cS, &cP}) v->reserve(n);
+  for (auto* v : {&sY1, &sY2, &sZ1, &sZ2, &lU, &lV}) v->reserve(n);
+  for (auto* v : {&cvY, &cvZ, &spY}) v->reserve(n);
+  eg.reserve(n);
+  for (auto* v : {&pNN, &pNH, &pTN, &pB}) v->reserve(n);
+  for (int j = 0; j < n; ++j) {
+    const int i = idx[j];
     const int m = static_cast<int>(c.m[i]), nn = static_cast<int>(c.n[i]), r = static_cast<int>(c.rank[i]);
     const int k = r + static_cast<int>(c.s);
     const int64_t ldk = round8(k);
     const RsvdLayout L = rsvd_layout(m, nn, k, r);
-    uint8_t* w = ws ? ws + P->slice[i] : nullptr;
+    uint8_t* w = ws ? ws + P->slice[j] : nullptr;
     auto F = [&](size_t o) { return reinterpret_cast<float*>(w ? w + o : nullptr); };
     auto H16 = [&](size_t o) { return reinterpret_cast<uint16_t*>(w ? w + o : nullptr); };
     float *Y = F(L.Y), *T = F(L.T), *Z = F(L.Z), *Bt = F(L.Bt), *Vk = F(L.Vk), *Up = F(L.Up), *Ups = F(L.Ups);
@@ -146,13 +165,11 @@ int build(const BatchCall& c, uint8_t* ws, Plan* P, Tables* t) {
       g.kblocks = (nn + 63) / 64;
     }
     pNN.push_back(g);
-    P->units_NN += static_cast<long long>(g.n_tiles) * g.m_tiles * g.kblocks;
     if (ws) {
       int rc = grouped_problem(A_KMAJ, false, m, k, nn, c.A[i], c.lda[i], H, nullptr, ldk, Y, ldk, &g);
       if (rc != SHG_OK) return rc;
     }
     pNH.push_back(g);
-    P->units_NH += static_cast<long long>(g.n_tiles) * g.m_tiles * g.kblocks;
     GemmProblem gt{};
     if (ws) {
       int rc = grouped_problem(A_MNMAJ, false, nn, k, m, c.A[i], c.lda[i], H, nullptr, ldk, Z, ldk, &gt);
@@ -163,18 +180,17 @@ int build(const BatchCall& c, uint8_t* ws, Plan* P, Tables* t) {
       gt.kblocks = (m + 63) / 64;
     }
     pTN.push_back(gt);
-    P->units_TN += static_cast<long long>(gt.n_tiles) * gt.m_tiles * gt.kblocks;
     if (ws) {
       int rc = grouped_problem(A_MNMAJ, true, nn, k, m, c.A[i], c.lda[i], H, Hlo, ldk, Bt, ldk, &gt);
       if (rc != SHG_OK) return rc;
     }
     pB.push_back(gt);
-    P->units_B += static_cast<long long>(gt.n_tiles) * gt.m_tiles * gt.kblocks;
   }
   P->n_gen = static_cast<int>(gen.size());
   P->n_cholS = static_cast<int>(cS.size());
   P->n_cholP = static_cast<int>(cP.size());
   Tables local;
+  local.copy = false;
   Tables& T = t ? *t : local;
   T.buf.clear();
   T.off = 0;
@@ -200,19 +216,14 @@ int build(const BatchCall& c, uint8_t* ws, Plan* P, Tables* t) {
   P->convZ = T.add(cvZ);
   P->splitY = T.add(spY);
   P->eig = T.add(eg);
+  P->units_NN = grouped_assign_units(pNN.data(), n);
+  P->units_NH = grouped_assign_units(pNH.data(), n);
+  P->units_TN = grouped_assign_units(pTN.data(), n);
+  P->units_B = grouped_assign_units(pB.data(), n);
   P->pNN = T.add(pNN);
   P->pNH = T.add(pNH);
   P->pTN = T.add(pTN);
   P->pB = T.add(pB);
-  std::vector<int4> u;
-  grouped_units(pNN.data(), n, &u);
-  P->uNN = T.add(u);
-  grouped_units(pNH.data(), n, &u);
-  P->uNH = T.add(u);
-  grouped_units(pTN.data(), n, &u);
-  P->uTN = T.add(u);
-  grouped_units(pB.data(), n, &u);
-  P->uB = T.add(u);
   P->table_bytes = T.off;
   return SHG_OK;
 }
@@ -237,7 +248,88 @@ int cholqr2_grouped(const Plan& P, uint8_t* tb, size_t gram1, size_t simt1, size
   return SHG_OK;
 }
 
+// The steps of one lane (its plan P, region ws) on stream st.
+int enqueue_lane(const BatchCall& c, const Plan& P, uint8_t* ws, int32_t* flags, cudaStream_t st) {
+  uint8_t* tb = ws + P.slices_bytes;
+  const int n = P.n;
+  auto zero = [&](size_t o, long long mx) { return zero_grouped(reinterpret_cast<const ZeroArg*>(tb + o), n, mx, st); };
+#define SHG_G(x)                 \
+  do {                           \
+    const int rc_ = (x);         \
+    if (rc_ != SHG_OK) return rc_; \
+  } while (0)
+  // Omega
+  SHG_G(gaussian_grouped(c.seed, reinterpret_cast<const GaussArg*>(tb + P.gen), P.n_gen,
+                         static_cast<long long>(P.nmax) * P.kmax, st));
+  // Y = A Omega; Q = orth(Y)
+  SHG_G(zero(P.zY, P.max_mk));
+  SHG_G(tc_gemm_grouped(A_KMAJ, false, reinterpret_cast<const GemmProblem*>(tb + P.pNN), n,
+                        P.units_NN, flags, st));
+  SHG_G(cholqr2_grouped(P, tb, P.gramY1, P.simtY1, P.gramY2, P.simtY2, P.mmax, flags, st));
+  // power scheme: the FP16-rounded basis is the next test matrix
+  for (int it = 0; it < P.q; ++it) {
+    SHG_G(convert_grouped(reinterpret_cast<const ConvArg*>(tb + P.convY), n, P.max_mk / 4, false, flags, st));
+    SHG_G(zero(P.zZ, P.max_nk));
+    SHG_G(tc_gemm_grouped(A_MNMAJ, false, reinterpret_cast<const GemmProblem*>(tb + P.pTN), n,
+                          P.units_TN, flags, st));
+    SHG_G(cholqr2_grouped(P, tb, P.gramZ1, P.simtZ1, P.gramZ2, P.simtZ2, P.nmax, flags, st));
+    SHG_G(convert_grouped(reinterpret_cast<const ConvArg*>(tb + P.convZ), n, P.max_nk / 4, false, flags, st));
+    SHG_G(zero(P.zY, P.max_mk));
+    SHG_G(tc_gemm_grouped(A_KMAJ, false, reinterpret_cast<const GemmProblem*>(tb + P.pNH), n,
+                          P.units_NH, flags, st));
+    SHG_G(cholqr2_grouped(P, tb, P.gramY1, P.simtY1, P.gramY2, P.simtY2, P.mmax, flags, st));
+  }
+  // B^T = A^T Q by the TCEC split (Q split once)
+  SHG_G(convert_grouped(reinterpret_cast<const ConvArg*>(tb + P.splitY), n, P.max_mk / 4, true, flags, st));
+  SHG_G(zero(P.zB, P.max_nk));
+  SHG_G(tc_gemm_grouped(A_MNMAJ, true, reinterpret_cast<const GemmProblem*>(tb + P.pB), n,
+                        P.units_B, flags, st));
+  // small SVD of B through the eigendecomposition of B B^T
+  SHG_G(zero(P.zG, P.max_kk));
+  SHG_G(gram_grouped(reinterpret_cast<const GramArg*>(tb + P.gramB), n, P.kmax, P.nmax, st));
+  SHG_G(eig_grouped(reinterpret_cast<const EigArg*>(tb + P.eig), n, P.kmax, P.rmax, P.tbmax, st));
+  // lift: U = Q U'; V = B^T U' Sigma^-1
+  SHG_G(simt_grouped(reinterpret_cast<const SimtArg*>(tb + P.liftU), n, P.mmax, P.rmax, st));
+  SHG_G(simt_grouped(reinterpret_cast<const SimtArg*>(tb + P.liftV), n, P.nmax, P.rmax, st));
+#undef SHG_G
+  return SHG_OK;
+}
+
+
+// Lanes: the problems grouped by k = rank + s, largest k first, at most
+// kMaxLanes groups (SHG_BATCHED_LANES, 1 .. kMaxLanes, sets the limit; with
+// more distinct k than lanes neighbouring classes share a lane).  Every
+// lane runs its own sequence of grouped steps on its own stream, so that
+// the one-CTA k x k chains of the large-k lanes run beside the bandwidth-
+// bound steps of the others.  A problem keeps its index in the call (its
+// Philox stream, its outputs).
+constexpr int kMaxLanes = 4;
+
+int lane_limit() {
+  int l = kMaxLanes;
+  if (const char* e = std::getenv("SHG_BATCHED_LANES")) l = std::atoi(e);
+  return std::max(1, std::min(l, kMaxLanes));
+}
+
+std::vector<std::vector<int>> lanes_of(const BatchCall& c) {
+  std::vector<int64_t> ks;
+  for (int i = 0; i < c.batch; ++i) ks.push_back(c.rank[i] + c.s);
+  std::sort(ks.begin(), ks.end(), [](int64_t a, int64_t b) { return a > b; });
+  ks.erase(std::unique(ks.begin(), ks.end()), ks.end());
+  const int nk = static_cast<int>(ks.size());
+  const int nl = std::min(lane_limit(), nk);
+  std::vector<std::vector<int>> lanes(nl);
+  for (int i = 0; i < c.batch; ++i) {
+    const int64_t k = c.rank[i] + c.s;
+    const int pos = static_cast<int>(std::find(ks.begin(), ks.end(), k) - ks.begin());
+    lanes[static_cast<size_t>(pos) * nl / nk].push_back(i);
+  }
+  return lanes;
+}
+
 }  // namespace
+
+int grouped_lane_limit() { return lane_limit(); }
 
 bool grouped_batch_eligible(const BatchCall& c, int variant) {
   if (variant != SHG_SPLIT_F16) return false;
@@ -251,71 +343,55 @@ bool grouped_batch_eligible(const BatchCall& c, int variant) {
 }
 
 size_t grouped_batch_bytes(const BatchCall& c) {
-  Plan P;
-  if (build(c, nullptr, &P, nullptr) != SHG_OK) return 0;
-  return P.slices_bytes + P.table_bytes;
+  size_t total = 0;
+  for (const std::vector<int>& idx : lanes_of(c)) {
+    Plan P;
+    if (build(c, idx, nullptr, &P, nullptr) != SHG_OK) return 0;
+    total += align256(P.slices_bytes + P.table_bytes);
+  }
+  return total;
 }
 
 int grouped_batch_prepare(const BatchCall& c, void* ws, size_t ws_bytes, cudaStream_t upload_stream) {
-  Plan P;
-  Tables T;
+  const std::vector<std::vector<int>> lanes = lanes_of(c);
+  std::vector<Tables> tabs(lanes.size());
   uint8_t* w = static_cast<uint8_t*>(ws);
-  int rc = build(c, w, &P, &T);
-  if (rc != SHG_OK) return rc;
-  if (P.slices_bytes + P.table_bytes > ws_bytes) return SHG_ERR_WORKSPACE;
-  if (cudaMemcpyAsync(w + P.slices_bytes, T.buf.data(), P.table_bytes, cudaMemcpyHostToDevice, upload_stream) !=
-          cudaSuccess ||
-      cudaStreamSynchronize(upload_stream) != cudaSuccess)
-    return SHG_ERR_CUDA;
-  return SHG_OK;
+  size_t base = 0;
+  for (size_t l = 0; l < lanes.size(); ++l) {
+    Plan P;
+    int rc = build(c, lanes[l], w + base, &P, &tabs[l]);
+    if (rc != SHG_OK) return rc;
+    if (base + P.slices_bytes + P.table_bytes > ws_bytes) return SHG_ERR_WORKSPACE;
+    if (cudaMemcpyAsync(w + base + P.slices_bytes, tabs[l].buf.data(), P.table_bytes, cudaMemcpyHostToDevice,
+                        upload_stream) != cudaSuccess)
+      return SHG_ERR_CUDA;
+    base += align256(P.slices_bytes + P.table_bytes);
+  }
+  return cuda_status(cudaStreamSynchronize(upload_stream));
 }
 
-int grouped_batch_enqueue(const BatchCall& c, void* ws, int32_t* flags, cudaStream_t st) {
-  Plan P;
-  int rc = build(c, nullptr, &P, nullptr);
-  if (rc != SHG_OK) return rc;
-  uint8_t* tb = static_cast<uint8_t*>(ws) + P.slices_bytes;
-  const int n = P.n;
-  auto zero = [&](size_t o, long long mx) { return zero_grouped(reinterpret_cast<const ZeroArg*>(tb + o), n, mx, st); };
-#define SHG_G(x)                 \
-  do {                           \
-    const int rc_ = (x);         \
-    if (rc_ != SHG_OK) return rc_; \
-  } while (0)
-  // Omega
-  SHG_G(gaussian_grouped(c.seed, reinterpret_cast<const GaussArg*>(tb + P.gen), P.n_gen,
-                         static_cast<long long>(P.nmax) * P.kmax, st));
-  // Y = A Omega; Q = orth(Y)
-  SHG_G(zero(P.zY, P.max_mk));
-  SHG_G(tc_gemm_grouped(A_KMAJ, false, reinterpret_cast<const GemmProblem*>(tb + P.pNN),
-                        reinterpret_cast<const int4*>(tb + P.uNN), P.units_NN, flags, st));
-  SHG_G(cholqr2_grouped(P, tb, P.gramY1, P.simtY1, P.gramY2, P.simtY2, P.mmax, flags, st));
-  // power scheme: the FP16-rounded basis is the next test matrix
-  for (int it = 0; it < P.q; ++it) {
-    SHG_G(convert_grouped(reinterpret_cast<const ConvArg*>(tb + P.convY), n, P.max_mk / 4, false, flags, st));
-    SHG_G(zero(P.zZ, P.max_nk));
-    SHG_G(tc_gemm_grouped(A_MNMAJ, false, reinterpret_cast<const GemmProblem*>(tb + P.pTN),
-                          reinterpret_cast<const int4*>(tb + P.uTN), P.units_TN, flags, st));
-    SHG_G(cholqr2_grouped(P, tb, P.gramZ1, P.simtZ1, P.gramZ2, P.simtZ2, P.nmax, flags, st));
-    SHG_G(convert_grouped(reinterpret_cast<const ConvArg*>(tb + P.convZ), n, P.max_nk / 4, false, flags, st));
-    SHG_G(zero(P.zY, P.max_mk));
-    SHG_G(tc_gemm_grouped(A_KMAJ, false, reinterpret_cast<const GemmProblem*>(tb + P.pNH),
-                          reinterpret_cast<const int4*>(tb + P.uNH), P.units_NH, flags, st));
-    SHG_G(cholqr2_grouped(P, tb, P.gramY1, P.simtY1, P.gramY2, P.simtY2, P.mmax, flags, st));
+int grouped_batch_enqueue(const BatchCall& c, void* ws, int32_t* flags, cudaStream_t st, const cudaStream_t* lane_st,
+                          const cudaEvent_t* lane_done, cudaEvent_t fork) {
+  const std::vector<std::vector<int>> lanes = lanes_of(c);
+  const int nl = static_cast<int>(lanes.size());
+  if (nl > 1 && cudaEventRecord(fork, st) != cudaSuccess) return SHG_ERR_CUDA;
+  size_t base = 0;
+  for (int l = 0; l < nl; ++l) {
+    Plan P;
+    int rc = build(c, lanes[l], nullptr, &P, nullptr);
+    if (rc != SHG_OK) return rc;
+    cudaStream_t ls = st;
+    if (nl > 1) {
+      ls = lane_st[l];
+      if (cudaStreamWaitEvent(ls, fork, 0) != cudaSuccess) return SHG_ERR_CUDA;
+    }
+    rc = enqueue_lane(c, P, static_cast<uint8_t*>(ws) + base, flags, ls);
+    if (rc != SHG_OK) return rc;
+    if (nl > 1 && (cudaEventRecord(lane_done[l], ls) != cudaSuccess || cudaStreamWaitEvent(st, lane_done[l], 0) !=
+                                                                          cudaSuccess))
+      return SHG_ERR_CUDA;
+    base += align256(P.slices_bytes + P.table_bytes);
   }
-  // B^T = A^T Q by the TCEC split (Q split once)
-  SHG_G(convert_grouped(reinterpret_cast<const ConvArg*>(tb + P.splitY), n, P.max_mk / 4, true, flags, st));
-  SHG_G(zero(P.zB, P.max_nk));
-  SHG_G(tc_gemm_grouped(A_MNMAJ, true, reinterpret_cast<const GemmProblem*>(tb + P.pB),
-                        reinterpret_cast<const int4*>(tb + P.uB), P.units_B, flags, st));
-  // small SVD of B through the eigendecomposition of B B^T
-  SHG_G(zero(P.zG, P.max_kk));
-  SHG_G(gram_grouped(reinterpret_cast<const GramArg*>(tb + P.gramB), n, P.kmax, P.nmax, st));
-  SHG_G(eig_grouped(reinterpret_cast<const EigArg*>(tb + P.eig), n, P.kmax, P.rmax, P.tbmax, st));
-  // lift: U = Q U'; V = B^T U' Sigma^-1
-  SHG_G(simt_grouped(reinterpret_cast<const SimtArg*>(tb + P.liftU), n, P.mmax, P.rmax, st));
-  SHG_G(simt_grouped(reinterpret_cast<const SimtArg*>(tb + P.liftV), n, P.nmax, P.rmax, st));
-#undef SHG_G
   return SHG_OK;
 }
 

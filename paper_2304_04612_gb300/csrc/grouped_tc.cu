@@ -2,10 +2,12 @@
 // m, n and k in one persistent launch (the batching pattern of the batched
 // randomized SVD: Algorithm 1 applied to every matrix of a batch).
 //
-// The work of all problems is one list of units (problem p, N tile nt, M
-// tile mt, 64-deep K block kb), built on the host and read from device
-// memory; each CTA takes a contiguous range of it (stream-K over the whole
-// batch), so the SMs stay balanced however uneven the problems are.  Each
+// The work of all problems is one numbered sequence of units (problem p, N
+// tile nt, M tile mt, 64-deep K block kb, K block fastest); each problem
+// records the number of its first unit, from which a warp finds a unit's
+// position (a binary search over the problems, then stepping); each CTA
+// takes a contiguous range of the sequence (stream-K over the whole batch),
+// so the SMs stay balanced however uneven the problems are.  Each
 // problem carries its own sizes, output pointer and TMA tensor maps (in
 // global memory).  The data path is that of the 128-column kernel
 // (tc_gemm_kernel in shgemm_tc.cu): A tile by TMA, split by SIMT warps into
@@ -35,6 +37,7 @@ constexpr int kGTmemStages = 2;
 
 struct GArgs {
   long long units;  // units of all problems
+  int nprob;
   int* flags;
   int sa, sb;       // A staging and B ring depths
   uint32_t b_bytes; // B ring stage bytes (the largest tile of the batch)
@@ -42,9 +45,43 @@ struct GArgs {
   unsigned long long wait_ns;
 };
 
+__device__ __forceinline__ long long units_of(const GemmProblem* P) {
+  return static_cast<long long>(P->n_tiles) * P->m_tiles * P->kblocks;
+}
+
+// Position (problem, N tile, M tile, K block) of unit u: the problem is the
+// last one whose first unit is at most u.
+__device__ __forceinline__ int4 unit_at(const GemmProblem* __restrict__ probs, int nprob, long long u) {
+  int lo = 0, hi = nprob - 1;
+  while (lo < hi) {
+    const int mid = (lo + hi + 1) >> 1;
+    if (probs[mid].u_begin <= u) lo = mid;
+    else hi = mid - 1;
+  }
+  const GemmProblem* P = probs + lo;
+  const long long local = u - P->u_begin;
+  const long long seg = local / P->kblocks;
+  return make_int4(lo, static_cast<int>(seg / P->m_tiles), static_cast<int>(seg % P->m_tiles),
+                   static_cast<int>(local % P->kblocks));
+}
+
+// The position of the unit after w.
+__device__ __forceinline__ void unit_step(const GemmProblem* __restrict__ probs, int nprob, int4& w) {
+  const GemmProblem* P = probs + w.x;
+  if (++w.w < P->kblocks) return;
+  w.w = 0;
+  if (++w.z < P->m_tiles) return;
+  w.z = 0;
+  if (++w.y < P->n_tiles) return;
+  w.y = 0;
+  do {
+    ++w.x;
+  } while (w.x < nprob - 1 && units_of(probs + w.x) == 0);
+}
+
 template <int AMAJ, bool PRE_B>
 __global__ void __launch_bounds__(kGThreads, 1)
-    tc_grouped_kernel(const GemmProblem* __restrict__ probs, const int4* __restrict__ units, const GArgs g) {
+    tc_grouped_kernel(const GemmProblem* __restrict__ probs, const GArgs g) {
   extern __shared__ uint8_t smem_raw[];
   uint8_t* smem = reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
   const int SA = g.sa, SB = g.sb, ST = kGTmemStages;
@@ -111,8 +148,8 @@ __global__ void __launch_bounds__(kGThreads, 1)
     if (lane == 0) {
       Ring ra;
       long long i = 0;
-      for (long long u = u0; u < u1; ++u, ++i, ra.next(SA)) {
-        const int4 w = units[u];  // (problem, N tile, M tile, K block)
+      int4 w = unit_at(probs, g.nprob, u0);  // (problem, N tile, M tile, K block)
+      for (long long u = u0; u < u1; ++u, ++i, ra.next(SA), unit_step(probs, g.nprob, w)) {
         const CUtensorMap* map = &probs[w.x].tmA;
         if (!mbar_wait(bar_aempty + 8 * ra.s, ra.ph ^ 1u, abort_flag, lim)) break;
         const uint32_t afull = bar_afull + 8 * ra.s;
@@ -133,8 +170,8 @@ __global__ void __launch_bounds__(kGThreads, 1)
     if (lane == 0) {
       Ring rb;
       long long i = 0;
-      for (long long u = u0; u < u1; ++u, ++i, rb.next(SB)) {
-        const int4 w = units[u];
+      int4 w = unit_at(probs, g.nprob, u0);
+      for (long long u = u0; u < u1; ++u, ++i, rb.next(SB), unit_step(probs, g.nprob, w)) {
         const GemmProblem* P = probs + w.x;
         const int nt = P->n_tile;
         if (!mbar_wait(bar_bempty + 8 * rb.s, rb.ph ^ 1u, abort_flag, lim)) break;
@@ -157,7 +194,7 @@ __global__ void __launch_bounds__(kGThreads, 1)
       int seg = 0;
       bool ok = true;
       while (ok && u < u1) {
-        const int4 w0 = units[u];
+        const int4 w0 = unit_at(probs, g.nprob, u);
         const GemmProblem* P = probs + w0.x;
         const int nt = P->n_tile;
         const uint32_t idesc = idesc_f16(0u, 0u, 1u, kBM, nt);
@@ -244,7 +281,7 @@ __global__ void __launch_bounds__(kGThreads, 1)
     float nonfinite = 0.0f;
     float S[kGMaxN];
     while (ok && u < u1) {
-      const int4 w0 = units[u];
+      const int4 w0 = unit_at(probs, g.nprob, u);
       const GemmProblem* P = probs + w0.x;
       const int nt = P->n_tile;
       const long long seg_end = min_ll(u1, u + (P->kblocks - w0.w));
@@ -348,8 +385,7 @@ __global__ void __launch_bounds__(kGThreads, 1)
 }
 
 template <int AMAJ, bool PRE_B>
-int launch_grouped(const GemmProblem* d_probs, const int4* d_units, const GArgs& g, int grid, size_t smem,
-                   cudaStream_t st) {
+int launch_grouped(const GemmProblem* d_probs, const GArgs& g, int grid, size_t smem, cudaStream_t st) {
   auto k = tc_grouped_kernel<AMAJ, PRE_B>;
   static size_t configured[64] = {};
   int dev = 0;
@@ -361,7 +397,7 @@ int launch_grouped(const GemmProblem* d_probs, const int4* d_units, const GArgs&
       return SHG_ERR_CUDA;
     configured[dev] = smem;
   }
-  k<<<grid, kGThreads, smem, st>>>(d_probs, d_units, g);
+  k<<<grid, kGThreads, smem, st>>>(d_probs, g);
   return cuda_status(cudaGetLastError());
 }
 
@@ -416,19 +452,21 @@ int grouped_problem(int amaj, bool pre_b, int64_t M, int64_t N, int64_t K, const
   return SHG_OK;
 }
 
-void grouped_units(const GemmProblem* probs, int nprob, std::vector<int4>* units) {
-  units->clear();
-  for (int p = 0; p < nprob; ++p)
-    for (int nt = 0; nt < probs[p].n_tiles; ++nt)
-      for (int mt = 0; mt < probs[p].m_tiles; ++mt)
-        for (int kb = 0; kb < probs[p].kblocks; ++kb) units->push_back(make_int4(p, nt, mt, kb));
+long long grouped_assign_units(GemmProblem* probs, int nprob) {
+  long long u = 0;
+  for (int p = 0; p < nprob; ++p) {
+    probs[p].u_begin = u;
+    u += static_cast<long long>(probs[p].n_tiles) * probs[p].m_tiles * probs[p].kblocks;
+  }
+  return u;
 }
 
-int tc_gemm_grouped(int amaj, bool pre_b, const GemmProblem* d_probs, const int4* d_units, long long n_units,
+int tc_gemm_grouped(int amaj, bool pre_b, const GemmProblem* d_probs, int nprob, long long n_units,
                     int32_t* d_flags, cudaStream_t st) {
-  if (n_units <= 0) return SHG_OK;
+  if (n_units <= 0 || nprob <= 0) return SHG_OK;
   GArgs g{};
   g.units = n_units;
+  g.nprob = nprob;
   g.flags = d_flags;
   g.sa = 4;
   g.sb = 4;
@@ -441,9 +479,9 @@ int tc_gemm_grouped(int amaj, bool pre_b, const GemmProblem* d_probs, const int4
   const int sms = sm_count();
   if (sms <= 0) return SHG_ERR_CUDA;
   const int grid = static_cast<int>(std::min<long long>(sms, n_units));
-  if (amaj == A_KMAJ && !pre_b) return launch_grouped<A_KMAJ, false>(d_probs, d_units, g, grid, smem, st);
-  if (amaj == A_MNMAJ && !pre_b) return launch_grouped<A_MNMAJ, false>(d_probs, d_units, g, grid, smem, st);
-  if (amaj == A_MNMAJ && pre_b) return launch_grouped<A_MNMAJ, true>(d_probs, d_units, g, grid, smem, st);
+  if (amaj == A_KMAJ && !pre_b) return launch_grouped<A_KMAJ, false>(d_probs, g, grid, smem, st);
+  if (amaj == A_MNMAJ && !pre_b) return launch_grouped<A_MNMAJ, false>(d_probs, g, grid, smem, st);
+  if (amaj == A_MNMAJ && pre_b) return launch_grouped<A_MNMAJ, true>(d_probs, g, grid, smem, st);
   return SHG_ERR_UNSUPPORTED;
 }
 

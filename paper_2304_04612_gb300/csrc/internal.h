@@ -104,7 +104,12 @@ size_t grouped_batch_bytes(const BatchCall& c);
 // Builds the step arguments in the workspace (synchronising `upload_stream`)
 // and enqueues the grouped launches on `st`.
 int grouped_batch_prepare(const BatchCall& c, void* ws, size_t ws_bytes, cudaStream_t upload_stream);
-int grouped_batch_enqueue(const BatchCall& c, void* ws, int32_t* d_flags, cudaStream_t st);
+// With more than one lane (problems grouped by k) each lane's steps go to
+// lane_st[l] (forked from and joined back to st with the events given).
+int grouped_batch_enqueue(const BatchCall& c, void* ws, int32_t* d_flags, cudaStream_t st, const cudaStream_t* lane_st,
+                          const cudaEvent_t* lane_done, cudaEvent_t fork);
+// The most lanes a grouped call uses (part of a cached graph's identity).
+int grouped_lane_limit();
 // Algorithm 1 as shg_rsvd computes it, with the counter offset of the
 // generated Omega (the batched path gives problem i offset i * 2^32).
 int rsvd_impl(int64_t m, int64_t n, int64_t rank, int64_t oversampling, int power_iters, const float* A,
