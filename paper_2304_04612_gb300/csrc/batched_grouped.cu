@@ -6,8 +6,8 @@
 // The host builds, once per set of arguments, the per-problem argument
 // arrays of every step (device pointers into one workspace slice per
 // problem, laid out as shg_rsvd lays out its workspace), the projections'
-// problem tables with their TMA tensor maps and the numbering of their work
-// units, and copies them into the workspace after the slices.  The step sequence
+// problem tables with their TMA tensor maps and the numbering of their
+// output tiles, and copies them into the workspace after the slices.  The step sequence
 // then refers to them only through device pointers, so it can be captured
 // into a CUDA graph and replayed.
 //
@@ -36,14 +36,14 @@ struct Plan {
   std::vector<size_t> slice;  // per-problem slice offset from the workspace base
   size_t slices_bytes = 0, table_bytes = 0;
   // argument arrays
-  size_t gen = 0, zY = 0, zZ = 0, zB = 0, zG = 0;
+  size_t gen = 0, zG = 0, sched = 0;
   size_t gramY1 = 0, gramY2 = 0, gramZ1 = 0, gramZ2 = 0, gramB = 0;
   size_t cholS = 0, cholP = 0;
   size_t simtY1 = 0, simtY2 = 0, simtZ1 = 0, simtZ2 = 0, liftU = 0, liftV = 0;
   size_t convY = 0, convZ = 0, splitY = 0, eig = 0;
   size_t pNN = 0, pNH = 0, pTN = 0, pB = 0;
   int n_gen = 0, n_cholS = 0, n_cholP = 0;
-  long long units_NN = 0, units_NH = 0, units_TN = 0, units_B = 0;
+  long long tiles_NN = 0, tiles_NH = 0, tiles_TN = 0, tiles_B = 0;
   int kmax = 0, kmax_small = 0, kmax_panel = 0, mmax = 0, nmax = 0, rmax = 0, tbmax = 0;
   long long max_mk = 0, max_nk = 0, max_kk = 0;
 };
@@ -83,7 +83,7 @@ int build(const BatchCall& c, const std::vector<int>& idx, uint8_t* ws, Plan* P,
     off += align256(rsvd_layout(c.m[i], c.n[i], k, c.rank[i]).total);
   }
   P->slices_bytes = off;
-  std::vector<ZeroArg> zY, zZ, zB, zG;
+  std::vector<ZeroArg> zG;
   std::vector<GaussArg> gen;
   std::vector<GramArg> gY1, gY2, gZ1, gZ2, gB;
   std::vector<CholArg> cS, cP;
@@ -91,7 +91,7 @@ int build(const BatchCall& c, const std::vector<int>& idx, uint8_t* ws, Plan* P,
   std::vector<ConvArg> cvY, cvZ, spY;
   std::vector<EigArg> eg;
   std::vector<GemmProblem> pNN, pNH, pTN, pB;
-  for (auto* v : {&zY, &zZ, &zB, &zG}) v->reserve(n);
+  zG.reserve(n);
   gen.reserve(n);
   for (auto* v : {&gY1, &gY2, &gZ1, &gZ2, &gB}) v->reserve(n);
   for (auto* v : {&cS, &cP}) v->reserve(n);
@@ -129,9 +129,6 @@ int build(const BatchCall& c, const std::vector<int>& idx, uint8_t* ws, Plan* P,
     const bool generate = !om;
     if (generate) om = H16(L.Om);
     gen.push_back(GaussArg{H16(L.Om), ldk, static_cast<unsigned long long>(i) << 32, generate ? nn : 0, k});
-    zY.push_back(ZeroArg{Y, ldk * 4, static_cast<long long>(k) * 4, m});
-    zZ.push_back(ZeroArg{Z, ldk * 4, static_cast<long long>(k) * 4, nn});
-    zB.push_back(ZeroArg{Bt, ldk * 4, static_cast<long long>(k) * 4, nn});
     zG.push_back(ZeroArg{sw.G, static_cast<long long>(k) * 8, static_cast<long long>(k) * 8, k});
     gY1.push_back(GramArg{Y, ldk, sw.G, m, k});
     gY2.push_back(GramArg{T, ldk, sw.G, m, k});
@@ -195,9 +192,6 @@ int build(const BatchCall& c, const std::vector<int>& idx, uint8_t* ws, Plan* P,
   T.buf.clear();
   T.off = 0;
   P->gen = T.add(gen);
-  P->zY = T.add(zY);
-  P->zZ = T.add(zZ);
-  P->zB = T.add(zB);
   P->zG = T.add(zG);
   P->gramY1 = T.add(gY1);
   P->gramY2 = T.add(gY2);
@@ -216,10 +210,17 @@ int build(const BatchCall& c, const std::vector<int>& idx, uint8_t* ws, Plan* P,
   P->convZ = T.add(cvZ);
   P->splitY = T.add(spY);
   P->eig = T.add(eg);
-  P->units_NN = grouped_assign_units(pNN.data(), n);
-  P->units_NH = grouped_assign_units(pNH.data(), n);
-  P->units_TN = grouped_assign_units(pTN.data(), n);
-  P->units_B = grouped_assign_units(pB.data(), n);
+  // the projections' problems with the longest tiles first (the tail of
+  // each launch is then the shortest tiles)
+  for (auto* v : {&pNN, &pNH, &pTN, &pB})
+    std::stable_sort(v->begin(), v->end(),
+                     [](const GemmProblem& a, const GemmProblem& b) { return a.kblocks > b.kblocks; });
+  P->tiles_NN = grouped_assign_tiles(pNN.data(), n);
+  P->tiles_NH = grouped_assign_tiles(pNH.data(), n);
+  P->tiles_TN = grouped_assign_tiles(pTN.data(), n);
+  P->tiles_B = grouped_assign_tiles(pB.data(), n);
+  // tile schedulers of the four projections (two zeroed words each)
+  P->sched = T.add(std::vector<uint32_t>(8, 0u));
   P->pNN = T.add(pNN);
   P->pNH = T.add(pNH);
   P->pTN = T.add(pTN);
@@ -251,6 +252,7 @@ int cholqr2_grouped(const Plan& P, uint8_t* tb, size_t gram1, size_t simt1, size
 // The steps of one lane (its plan P, region ws) on stream st.
 int enqueue_lane(const BatchCall& c, const Plan& P, uint8_t* ws, int32_t* flags, cudaStream_t st) {
   uint8_t* tb = ws + P.slices_bytes;
+  unsigned int* sched = reinterpret_cast<unsigned int*>(tb + P.sched);
   const int n = P.n;
   auto zero = [&](size_t o, long long mx) { return zero_grouped(reinterpret_cast<const ZeroArg*>(tb + o), n, mx, st); };
 #define SHG_G(x)                 \
@@ -262,28 +264,24 @@ int enqueue_lane(const BatchCall& c, const Plan& P, uint8_t* ws, int32_t* flags,
   SHG_G(gaussian_grouped(c.seed, reinterpret_cast<const GaussArg*>(tb + P.gen), P.n_gen,
                          static_cast<long long>(P.nmax) * P.kmax, st));
   // Y = A Omega; Q = orth(Y)
-  SHG_G(zero(P.zY, P.max_mk));
-  SHG_G(tc_gemm_grouped(A_KMAJ, false, reinterpret_cast<const GemmProblem*>(tb + P.pNN), n,
-                        P.units_NN, flags, st));
+  SHG_G(tc_gemm_grouped(A_KMAJ, false, reinterpret_cast<const GemmProblem*>(tb + P.pNN), n, P.tiles_NN,
+                        sched + 0, flags, st));
   SHG_G(cholqr2_grouped(P, tb, P.gramY1, P.simtY1, P.gramY2, P.simtY2, P.mmax, flags, st));
   // power scheme: the FP16-rounded basis is the next test matrix
   for (int it = 0; it < P.q; ++it) {
     SHG_G(convert_grouped(reinterpret_cast<const ConvArg*>(tb + P.convY), n, P.max_mk / 4, false, flags, st));
-    SHG_G(zero(P.zZ, P.max_nk));
-    SHG_G(tc_gemm_grouped(A_MNMAJ, false, reinterpret_cast<const GemmProblem*>(tb + P.pTN), n,
-                          P.units_TN, flags, st));
+    SHG_G(tc_gemm_grouped(A_MNMAJ, false, reinterpret_cast<const GemmProblem*>(tb + P.pTN), n, P.tiles_TN,
+                          sched + 2, flags, st));
     SHG_G(cholqr2_grouped(P, tb, P.gramZ1, P.simtZ1, P.gramZ2, P.simtZ2, P.nmax, flags, st));
     SHG_G(convert_grouped(reinterpret_cast<const ConvArg*>(tb + P.convZ), n, P.max_nk / 4, false, flags, st));
-    SHG_G(zero(P.zY, P.max_mk));
-    SHG_G(tc_gemm_grouped(A_KMAJ, false, reinterpret_cast<const GemmProblem*>(tb + P.pNH), n,
-                          P.units_NH, flags, st));
+    SHG_G(tc_gemm_grouped(A_KMAJ, false, reinterpret_cast<const GemmProblem*>(tb + P.pNH), n, P.tiles_NH,
+                          sched + 4, flags, st));
     SHG_G(cholqr2_grouped(P, tb, P.gramY1, P.simtY1, P.gramY2, P.simtY2, P.mmax, flags, st));
   }
   // B^T = A^T Q by the TCEC split (Q split once)
   SHG_G(convert_grouped(reinterpret_cast<const ConvArg*>(tb + P.splitY), n, P.max_mk / 4, true, flags, st));
-  SHG_G(zero(P.zB, P.max_nk));
-  SHG_G(tc_gemm_grouped(A_MNMAJ, true, reinterpret_cast<const GemmProblem*>(tb + P.pB), n,
-                        P.units_B, flags, st));
+  SHG_G(tc_gemm_grouped(A_MNMAJ, true, reinterpret_cast<const GemmProblem*>(tb + P.pB), n, P.tiles_B,
+                        sched + 6, flags, st));
   // small SVD of B through the eigendecomposition of B B^T
   SHG_G(zero(P.zG, P.max_kk));
   SHG_G(gram_grouped(reinterpret_cast<const GramArg*>(tb + P.gramB), n, P.kmax, P.nmax, st));

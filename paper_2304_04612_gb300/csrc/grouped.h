@@ -20,7 +20,7 @@ struct alignas(64) GemmProblem {
   CUtensorMap tmA, tmB, tmB2;
   float* C;
   long long ldc;
-  long long u_begin;  // index of the problem's first unit in the launch
+  long long t_begin;  // number of the problem's first output tile in the launch
   int M, N, n_tile, n_tiles, m_tiles, kblocks;
 };
 // N tiling of the grouped kernel: tiles of at most 128 columns, multiples of 64.
@@ -30,14 +30,16 @@ int grouped_tiling(int64_t N, int* n_tile, int* n_tiles);
 // when pre_b) K x N FP16, ldb.  Host only (encodes the tensor maps).
 int grouped_problem(int amaj, bool pre_b, int64_t M, int64_t N, int64_t K, const float* A, int64_t lda,
                     const uint16_t* B, const uint16_t* B_lo, int64_t ldb, float* C, int64_t ldc, GemmProblem* out);
-// Numbers the work units (problem, N tile, M tile, 64-deep K block) of the
-// problems in that order (K block fastest): sets every u_begin and returns
-// the number of units.  The kernel decodes a unit's position from them.
-long long grouped_assign_units(GemmProblem* probs, int nprob);
-// One launch over the n_units units of nprob problems; every C must be zero
-// where tiles are split across CTAs (the caller zeroes all of them).
-int tc_gemm_grouped(int amaj, bool pre_b, const GemmProblem* d_probs, int nprob, long long n_units,
-                    int32_t* d_flags, cudaStream_t st);
+// Numbers the output tiles (problem, N tile, M tile) of the problems in
+// that order (M tile fastest): sets every t_begin and returns the number
+// of tiles.  The kernel decodes a tile's position from them.
+long long grouped_assign_tiles(GemmProblem* probs, int nprob);
+// One launch over the n_tiles tiles of nprob problems, each tile written
+// whole.  d_sched: two zeroed words (the tile counter and the count of
+// finished CTAs; the launch leaves them zero again), one pair per launch
+// that may run at the same time.
+int tc_gemm_grouped(int amaj, bool pre_b, const GemmProblem* d_probs, int nprob, long long n_tiles,
+                    unsigned int* d_sched, int32_t* d_flags, cudaStream_t st);
 
 // ------------------------------------------------------ other grouped steps
 struct ZeroArg {      // rows x width_bytes at p, rows ld_bytes apart

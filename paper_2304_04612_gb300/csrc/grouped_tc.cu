@@ -2,13 +2,18 @@
 // m, n and k in one persistent launch (the batching pattern of the batched
 // randomized SVD: Algorithm 1 applied to every matrix of a batch).
 //
-// The work of all problems is one numbered sequence of units (problem p, N
-// tile nt, M tile mt, 64-deep K block kb, K block fastest); each problem
-// records the number of its first unit, from which a warp finds a unit's
-// position (a binary search over the problems, then stepping); each CTA
-// takes a contiguous range of the sequence (stream-K over the whole batch),
-// so the SMs stay balanced however uneven the problems are.  Each
-// problem carries its own sizes, output pointer and TMA tensor maps (in
+// The work of all problems is one numbered sequence of output tiles
+// (problem p, N tile nt, M tile mt; M tile fastest), each with all its
+// 64-deep K blocks; each problem records the number of its first tile, from
+// which a warp finds a tile's position (a binary search over the problems).
+// CTAs take tiles one at a time from a counter in global memory (its A
+// producer fetches the next number and passes it to the other roles through
+// a small queue in shared memory), so the SMs stay balanced however uneven
+// the problems are, a CTA that starts late (its SM held by another lane's
+// kernel) takes whatever is left, and every tile is written whole by one
+// CTA (no partial sums, no zeroed output).  The last CTA to finish resets
+// the counter for the next launch.  Each problem carries its own sizes,
+// output pointer and TMA tensor maps (in
 // global memory).  The data path is that of the 128-column kernel
 // (tc_gemm_kernel in shgemm_tc.cu): A tile by TMA, split by SIMT warps into
 // FP16 hi / 2^11-scaled lo in tensor memory, two tcgen05 products per K
@@ -35,9 +40,13 @@ constexpr int kGMaxN = 128;
 constexpr uint32_t kGTmemCols = 512;
 constexpr int kGTmemStages = 2;
 
+constexpr int kGQueue = 4;         // tile queue depth
+constexpr int kGQueueReaders = 10; // B producer, MMA issuer, four split and four epilogue warps
+
 struct GArgs {
-  long long units;  // units of all problems
+  long long tiles;      // tiles of all problems
   int nprob;
+  unsigned int* sched;  // [0] next tile, [1] CTAs done (zero at launch, reset by the last CTA)
   int* flags;
   int sa, sb;       // A staging and B ring depths
   uint32_t b_bytes; // B ring stage bytes (the largest tile of the batch)
@@ -45,38 +54,18 @@ struct GArgs {
   unsigned long long wait_ns;
 };
 
-__device__ __forceinline__ long long units_of(const GemmProblem* P) {
-  return static_cast<long long>(P->n_tiles) * P->m_tiles * P->kblocks;
-}
-
-// Position (problem, N tile, M tile, K block) of unit u: the problem is the
-// last one whose first unit is at most u.
-__device__ __forceinline__ int4 unit_at(const GemmProblem* __restrict__ probs, int nprob, long long u) {
+// Position (problem, N tile, M tile) of tile t: the problem is the last
+// one whose first tile is at most t.
+__device__ __forceinline__ int3 tile_at(const GemmProblem* __restrict__ probs, int nprob, long long t) {
   int lo = 0, hi = nprob - 1;
   while (lo < hi) {
     const int mid = (lo + hi + 1) >> 1;
-    if (probs[mid].u_begin <= u) lo = mid;
+    if (probs[mid].t_begin <= t) lo = mid;
     else hi = mid - 1;
   }
   const GemmProblem* P = probs + lo;
-  const long long local = u - P->u_begin;
-  const long long seg = local / P->kblocks;
-  return make_int4(lo, static_cast<int>(seg / P->m_tiles), static_cast<int>(seg % P->m_tiles),
-                   static_cast<int>(local % P->kblocks));
-}
-
-// The position of the unit after w.
-__device__ __forceinline__ void unit_step(const GemmProblem* __restrict__ probs, int nprob, int4& w) {
-  const GemmProblem* P = probs + w.x;
-  if (++w.w < P->kblocks) return;
-  w.w = 0;
-  if (++w.z < P->m_tiles) return;
-  w.z = 0;
-  if (++w.y < P->n_tiles) return;
-  w.y = 0;
-  do {
-    ++w.x;
-  } while (w.x < nprob - 1 && units_of(probs + w.x) == 0);
+  const int local = static_cast<int>(t - P->t_begin);
+  return make_int3(lo, local / P->m_tiles, local % P->m_tiles);
 }
 
 template <int AMAJ, bool PRE_B>
@@ -99,8 +88,11 @@ __global__ void __launch_bounds__(kGThreads, 1)
   const uint32_t bar_dempty = smem_u32(bars + nb + 2);  // [2]
   const uint32_t bar_lempty = smem_u32(bars + nb + 4);
   const uint32_t bar_drain = smem_u32(bars + nb + 5);
-  uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(bars + nb + 6);
+  const uint32_t bar_qfull = smem_u32(bars + nb + 6);              // [kGQueue]
+  const uint32_t bar_qempty = smem_u32(bars + nb + 6 + kGQueue);   // [kGQueue]
+  uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(bars + nb + 6 + 2 * kGQueue);
   volatile int* abort_flag = reinterpret_cast<volatile int*>(tmem_slot + 1);
+  volatile int* tile_q = reinterpret_cast<volatile int*>(tmem_slot + 2);  // [kGQueue]: tile numbers, -1 = no more
 
   const int warp = threadIdx.x >> 5;
   const int lane = threadIdx.x & 31;
@@ -124,6 +116,10 @@ __global__ void __launch_bounds__(kGThreads, 1)
     }
     mbar_init(bar_lempty, 4);
     mbar_init(bar_drain, 1);
+    for (int s = 0; s < kGQueue; ++s) {
+      mbar_init(bar_qfull + 8 * s, 1);
+      mbar_init(bar_qempty + 8 * s, kGQueueReaders);
+    }
     *abort_flag = 0;
     fence_mbar_init();
   }
@@ -138,72 +134,100 @@ __global__ void __launch_bounds__(kGThreads, 1)
   const uint32_t tm_l = tmem_base + 2 * kGMaxN;
   const uint32_t tm_a = tmem_base + 3 * kGMaxN;
 
-  const long long u0 = static_cast<long long>(blockIdx.x) * g.units / gridDim.x;
-  const long long u1 = static_cast<long long>(blockIdx.x + 1) * g.units / gridDim.x;
   const uint64_t lim = g.wait_ns;
   long long issued_a = 0, issued_b = 0;
 
   if (warp == 0) {
     // ---------------------------------------------------------- A producer
+    // (also the tile scheduler: fetches tile numbers into the queue)
     if (lane == 0) {
-      Ring ra;
+      Ring ra, rq;
       long long i = 0;
-      int4 w = unit_at(probs, g.nprob, u0);  // (problem, N tile, M tile, K block)
-      for (long long u = u0; u < u1; ++u, ++i, ra.next(SA), unit_step(probs, g.nprob, w)) {
-        const CUtensorMap* map = &probs[w.x].tmA;
-        if (!mbar_wait(bar_aempty + 8 * ra.s, ra.ph ^ 1u, abort_flag, lim)) break;
-        const uint32_t afull = bar_afull + 8 * ra.s;
-        const uint32_t adst = smem_u32(a_ring + ra.s * kABytes);
-        mbar_expect_tx(afull, kABytes);
-        if (AMAJ == A_KMAJ) {
-          tma_load_3d(adst, map, afull, w.w * kBK, w.z * kBM, 0);
-          tma_load_3d(adst + 16384, map, afull, w.w * kBK + 32, w.z * kBM, 0);
-        } else {
-          for (int j = 0; j < 4; ++j) tma_load_2d(adst + j * 8192, map, afull, w.z * kBM + 32 * j, w.w * kBK);
+      bool ok = true;
+      while (ok) {
+        if (!mbar_wait(bar_qempty + 8 * rq.s, rq.ph ^ 1u, abort_flag, lim)) break;
+        const unsigned int t = atomicAdd(g.sched, 1u);
+        const int tile = (static_cast<long long>(t) < g.tiles) ? static_cast<int>(t) : -1;
+        tile_q[rq.s] = tile;
+        mbar_arrive(bar_qfull + 8 * rq.s);
+        rq.next(kGQueue);
+        if (tile < 0) break;
+        const int3 w = tile_at(probs, g.nprob, tile);  // (problem, N tile, M tile)
+        const GemmProblem* P = probs + w.x;
+        const CUtensorMap* map = &P->tmA;
+        for (int kb = 0; kb < P->kblocks; ++kb, ++i, ra.next(SA)) {
+          if (!mbar_wait(bar_aempty + 8 * ra.s, ra.ph ^ 1u, abort_flag, lim)) {
+            ok = false;
+            break;
+          }
+          const uint32_t afull = bar_afull + 8 * ra.s;
+          const uint32_t adst = smem_u32(a_ring + ra.s * kABytes);
+          mbar_expect_tx(afull, kABytes);
+          if (AMAJ == A_KMAJ) {
+            tma_load_3d(adst, map, afull, kb * kBK, w.z * kBM, 0);
+            tma_load_3d(adst + 16384, map, afull, kb * kBK + 32, w.z * kBM, 0);
+          } else {
+            for (int j = 0; j < 4; ++j) tma_load_2d(adst + j * 8192, map, afull, w.z * kBM + 32 * j, kb * kBK);
+          }
+          issued_a = i + 1;
         }
-        issued_a = i + 1;
       }
     }
     __syncwarp();
   } else if (warp == kGBProducerWarp) {
     // ---------------------------------------------------------- B producer
     if (lane == 0) {
-      Ring rb;
+      Ring rb, rq;
       long long i = 0;
-      int4 w = unit_at(probs, g.nprob, u0);
-      for (long long u = u0; u < u1; ++u, ++i, rb.next(SB), unit_step(probs, g.nprob, w)) {
+      bool ok = true;
+      while (ok) {
+        if (!mbar_wait(bar_qfull + 8 * rq.s, rq.ph, abort_flag, lim)) break;
+        const int tile = tile_q[rq.s];
+        mbar_arrive(bar_qempty + 8 * rq.s);
+        rq.next(kGQueue);
+        if (tile < 0) break;
+        const int3 w = tile_at(probs, g.nprob, tile);
         const GemmProblem* P = probs + w.x;
         const int nt = P->n_tile;
-        if (!mbar_wait(bar_bempty + 8 * rb.s, rb.ph ^ 1u, abort_flag, lim)) break;
-        const uint32_t bfull = bar_bfull + 8 * rb.s;
-        const uint32_t bdst = smem_u32(b_ring + rb.s * g.b_bytes);
-        mbar_expect_tx(bfull, (PRE_B ? 256u : 128u) * nt);
-        for (int j = 0; j < nt / 64; ++j) {
-          tma_load_2d(bdst + j * 8192, &P->tmB, bfull, w.y * nt + 64 * j, w.w * kBK);
-          if (PRE_B) tma_load_2d(bdst + nt * 128 + j * 8192, &P->tmB2, bfull, w.y * nt + 64 * j, w.w * kBK);
+        for (int kb = 0; kb < P->kblocks; ++kb, ++i, rb.next(SB)) {
+          if (!mbar_wait(bar_bempty + 8 * rb.s, rb.ph ^ 1u, abort_flag, lim)) {
+            ok = false;
+            break;
+          }
+          const uint32_t bfull = bar_bfull + 8 * rb.s;
+          const uint32_t bdst = smem_u32(b_ring + rb.s * g.b_bytes);
+          mbar_expect_tx(bfull, (PRE_B ? 256u : 128u) * nt);
+          for (int j = 0; j < nt / 64; ++j) {
+            tma_load_2d(bdst + j * 8192, &P->tmB, bfull, w.y * nt + 64 * j, kb * kBK);
+            if (PRE_B) tma_load_2d(bdst + nt * 128 + j * 8192, &P->tmB2, bfull, w.y * nt + 64 * j, kb * kBK);
+          }
+          issued_b = i + 1;
         }
-        issued_b = i + 1;
       }
     }
     __syncwarp();
   } else if (warp == 1) {
     // ---------------------------------------------------------- MMA issuer
     if (lane == 0) {
-      long long u = u0, cc = 0;
-      Ring rt, rb;
+      long long cc = 0;
+      Ring rt, rb, rq;
       int seg = 0;
       bool ok = true;
-      while (ok && u < u1) {
-        const int4 w0 = unit_at(probs, g.nprob, u);
-        const GemmProblem* P = probs + w0.x;
+      while (ok) {
+        if (!mbar_wait(bar_qfull + 8 * rq.s, rq.ph, abort_flag, lim)) break;
+        const int tile = tile_q[rq.s];
+        mbar_arrive(bar_qempty + 8 * rq.s);
+        rq.next(kGQueue);
+        if (tile < 0) break;
+        const GemmProblem* P = probs + tile_at(probs, g.nprob, tile).x;
         const int nt = P->n_tile;
+        const int K = P->kblocks;
         const uint32_t idesc = idesc_f16(0u, 0u, 1u, kBM, nt);
         const uint32_t b_piece = static_cast<uint32_t>(nt / 64) * 8192u;
-        const long long seg_end = min_ll(u1, u + (P->kblocks - w0.w));
         if (!mbar_wait(bar_lempty, static_cast<uint32_t>((seg & 1) ^ 1), abort_flag, lim)) break;
         bool first_in_seg = true;
-        while (u < seg_end) {
-          const long long chunk_end = min_ll(seg_end, u + g.kc);
+        for (int kb0 = 0; kb0 < K; kb0 += g.kc) {
+          const int kend = min(K, kb0 + g.kc);
           const int d = static_cast<int>(cc & 1);
           if (!mbar_wait(bar_dempty + 8 * d, static_cast<uint32_t>(((cc >> 1) & 1) ^ 1), abort_flag, lim)) {
             ok = false;
@@ -211,8 +235,7 @@ __global__ void __launch_bounds__(kGThreads, 1)
           }
           tc_fence_after();
           const uint32_t tm_d = tmem_base + d * kGMaxN;
-          const long long chunk_start = u;
-          for (; u < chunk_end; ++u, rt.next(ST), rb.next(SB)) {
+          for (int kb = kb0; kb < kend; ++kb, rt.next(ST), rb.next(SB)) {
             const int st = rt.s, sb = rb.s;
             if (!mbar_wait(bar_tfull + 8 * st, rt.ph, abort_flag, lim) ||
                 !mbar_wait(bar_bfull + 8 * sb, rb.ph, abort_flag, lim)) {
@@ -226,7 +249,7 @@ __global__ void __launch_bounds__(kGThreads, 1)
             const uint64_t bl0 = smem_desc_sw128(sbm + b_piece, 8192, 1024);
 #pragma unroll
             for (int ks = 0; ks < kBK / 16; ++ks) {
-              const uint32_t acc_d = (u == chunk_start && ks == 0) ? 0u : 1u;
+              const uint32_t acc_d = (kb == kb0 && ks == 0) ? 0u : 1u;
               const uint32_t acc_l = (first_in_seg && ks == 0) ? 0u : 1u;
               const uint64_t bh = bh0 + static_cast<uint64_t>(ks * 128);
               tc_mma_f16_tmem_a(tm_d, ta + ks * 8, bh, idesc, acc_d);
@@ -251,44 +274,64 @@ __global__ void __launch_bounds__(kGThreads, 1)
     const int q = warp & 3;
     const int r = 32 * q + lane;
     const uint32_t lane_off = static_cast<uint32_t>(32 * q) << 16;
-    Ring ra, rt;
-    for (long long u = u0; u < u1; ++u, ra.next(SA), rt.next(ST)) {
-      if (!warp_wait(bar_afull + 8 * ra.s, ra.ph, abort_flag, lim, lane)) {
-        *abort_flag = 1;
-        break;
-      }
-      float a[64];
-      read_row<AMAJ>(a_ring + ra.s * kABytes, r, a);
+    Ring ra, rt, rq;
+    bool ok = true;
+    while (ok) {
+      if (!warp_wait(bar_qfull + 8 * rq.s, rq.ph, abort_flag, lim, lane)) break;
+      const int tile = tile_q[rq.s];
       __syncwarp();
-      if (lane == 0) mbar_arrive(bar_aempty + 8 * ra.s);
-      if (!warp_wait(bar_tempty + 8 * rt.s, rt.ph ^ 1u, abort_flag, lim, lane)) {
-        *abort_flag = 1;
-        break;
+      if (lane == 0) mbar_arrive(bar_qempty + 8 * rq.s);
+      rq.next(kGQueue);
+      if (tile < 0) break;
+      const int K = probs[tile_at(probs, g.nprob, tile).x].kblocks;
+      for (int kb = 0; kb < K; ++kb, ra.next(SA), rt.next(ST)) {
+        if (!warp_wait(bar_afull + 8 * ra.s, ra.ph, abort_flag, lim, lane)) {
+          *abort_flag = 1;
+          ok = false;
+          break;
+        }
+        float a[64];
+        read_row<AMAJ>(a_ring + ra.s * kABytes, r, a);
+        __syncwarp();
+        if (lane == 0) mbar_arrive(bar_aempty + 8 * ra.s);
+        if (!warp_wait(bar_tempty + 8 * rt.s, rt.ph ^ 1u, abort_flag, lim, lane)) {
+          *abort_flag = 1;
+          ok = false;
+          break;
+        }
+        tc_fence_after();
+        split_to_tmem<false, 2>(a, tm_a + lane_off + rt.s * 64);
+        tc_wait_st();
+        tc_fence_before();
+        __syncwarp();
+        if (lane == 0) mbar_arrive(bar_tfull + 8 * rt.s);
       }
-      tc_fence_after();
-      split_to_tmem<false, 2>(a, tm_a + lane_off + rt.s * 64);
-      tc_wait_st();
-      tc_fence_before();
-      __syncwarp();
-      if (lane == 0) mbar_arrive(bar_tfull + 8 * rt.s);
     }
   } else {
     // ---------------------------------------------------------- epilogue
     const int q = warp & 3;
     const uint32_t lane_off = static_cast<uint32_t>(32 * q) << 16;
-    long long u = u0, cc = 0;
+    long long cc = 0;
     bool ok = true;
     float nonfinite = 0.0f;
     float S[kGMaxN];
-    while (ok && u < u1) {
-      const int4 w0 = unit_at(probs, g.nprob, u);
-      const GemmProblem* P = probs + w0.x;
+    Ring rq;
+    while (ok) {
+      if (!warp_wait(bar_qfull + 8 * rq.s, rq.ph, abort_flag, lim, lane)) {
+        ok = false;
+        break;
+      }
+      const int tile = tile_q[rq.s];
+      __syncwarp();
+      if (lane == 0) mbar_arrive(bar_qempty + 8 * rq.s);
+      rq.next(kGQueue);
+      if (tile < 0) break;
+      const int3 w = tile_at(probs, g.nprob, tile);
+      const GemmProblem* P = probs + w.x;
       const int nt = P->n_tile;
-      const long long seg_end = min_ll(u1, u + (P->kblocks - w0.w));
-      const bool whole = (w0.w == 0) && (seg_end - u == P->kblocks);
-      const long long nch = (seg_end - u + g.kc - 1) / g.kc;
-      const int row = w0.z * kBM + 32 * q + lane;
-      for (long long c = 0; c < nch; ++c, ++cc) {
+      const int nch = (P->kblocks + g.kc - 1) / g.kc;
+      const int row = w.z * kBM + 32 * q + lane;
+      for (int c = 0; c < nch; ++c, ++cc) {
         const int d = static_cast<int>(cc & 1);
         if (!warp_wait(bar_dfull + 8 * d, static_cast<uint32_t>((cc >> 1) & 1), abort_flag, lim, lane)) {
           ok = false;
@@ -311,7 +354,7 @@ __global__ void __launch_bounds__(kGThreads, 1)
         if (lane == 0) mbar_arrive(bar_dempty + 8 * d);
       }
       if (!ok) break;
-      // segment done: C = S + 2^-11 L
+      // tile done: C = S + 2^-11 L, stored whole
       tc_fence_after();
       const bool row_ok = row < P->M;
       float* crow = P->C + static_cast<long long>(row) * P->ldc;
@@ -326,28 +369,16 @@ __global__ void __launch_bounds__(kGThreads, 1)
 #pragma unroll
           for (int j = 0; j < 16; ++j) v[j] = fmaf(__uint_as_float(rl[j]), 0.00048828125f, S[c0 + j]);
           if (c0 == 0) nonfinite = __fmaf_rn(v[0], 0.0f, nonfinite);
-          const int col0 = w0.y * nt + c0;
+          const int col0 = w.y * nt + c0;
           if (row_ok && col0 < P->N) {
             if (vec && col0 + 16 <= P->N) {
 #pragma unroll
-              for (int j = 0; j < 16; j += 4) {
-                const float4 w4 = make_float4(v[j], v[j + 1], v[j + 2], v[j + 3]);
-                float4* dst = reinterpret_cast<float4*>(crow + col0 + j);
-                if (whole)
-                  *dst = w4;
-                else
-                  atomicAdd(dst, w4);
-              }
+              for (int j = 0; j < 16; j += 4)
+                *reinterpret_cast<float4*>(crow + col0 + j) = make_float4(v[j], v[j + 1], v[j + 2], v[j + 3]);
             } else {
 #pragma unroll
-              for (int j = 0; j < 16; ++j) {
-                if (col0 + j < P->N) {
-                  if (whole)
-                    crow[col0 + j] = v[j];
-                  else
-                    atomicAdd(crow + col0 + j, v[j]);
-                }
-              }
+              for (int j = 0; j < 16; ++j)
+                if (col0 + j < P->N) crow[col0 + j] = v[j];
             }
           }
         }
@@ -355,7 +386,6 @@ __global__ void __launch_bounds__(kGThreads, 1)
       tc_fence_before();
       __syncwarp();
       if (lane == 0) mbar_arrive(bar_lempty);
-      u = seg_end;
     }
     if (!ok) *abort_flag = 1;
     if (nonfinite != 0.0f) atomicOr(g.flags, SHG_FLAG_RANGE);
@@ -381,6 +411,16 @@ __global__ void __launch_bounds__(kGThreads, 1)
   if (warp == 1) {
     tc_fence_after();
     tmem_dealloc(tmem_base, kGTmemCols);
+  }
+  // every CTA has fetched its last tile number: the last one to get here
+  // resets the scheduler for the next launch
+  if (threadIdx.x == 0) {
+    __threadfence();
+    if (atomicAdd(g.sched + 1, 1u) == gridDim.x - 1) {
+      atomicExch(g.sched, 0u);
+      atomicExch(g.sched + 1, 0u);
+      __threadfence();
+    }
   }
 }
 
@@ -452,21 +492,23 @@ int grouped_problem(int amaj, bool pre_b, int64_t M, int64_t N, int64_t K, const
   return SHG_OK;
 }
 
-long long grouped_assign_units(GemmProblem* probs, int nprob) {
-  long long u = 0;
+long long grouped_assign_tiles(GemmProblem* probs, int nprob) {
+  long long t = 0;
   for (int p = 0; p < nprob; ++p) {
-    probs[p].u_begin = u;
-    u += static_cast<long long>(probs[p].n_tiles) * probs[p].m_tiles * probs[p].kblocks;
+    probs[p].t_begin = t;
+    t += static_cast<long long>(probs[p].n_tiles) * probs[p].m_tiles;
   }
-  return u;
+  return t;
 }
 
-int tc_gemm_grouped(int amaj, bool pre_b, const GemmProblem* d_probs, int nprob, long long n_units,
-                    int32_t* d_flags, cudaStream_t st) {
-  if (n_units <= 0 || nprob <= 0) return SHG_OK;
+int tc_gemm_grouped(int amaj, bool pre_b, const GemmProblem* d_probs, int nprob, long long n_tiles,
+                    unsigned int* d_sched, int32_t* d_flags, cudaStream_t st) {
+  if (n_tiles <= 0 || nprob <= 0) return SHG_OK;
+  if (n_tiles >= (1ll << 31) || !d_sched) return SHG_ERR_INVALID_ARG;
   GArgs g{};
-  g.units = n_units;
+  g.tiles = n_tiles;
   g.nprob = nprob;
+  g.sched = d_sched;
   g.flags = d_flags;
   g.sa = 4;
   g.sb = 4;
@@ -478,7 +520,7 @@ int tc_gemm_grouped(int amaj, bool pre_b, const GemmProblem* d_probs, int nprob,
   const size_t smem = 1024 + static_cast<size_t>(g.sa) * kABytes + static_cast<size_t>(g.sb) * g.b_bytes + bar_bytes;
   const int sms = sm_count();
   if (sms <= 0) return SHG_ERR_CUDA;
-  const int grid = static_cast<int>(std::min<long long>(sms, n_units));
+  const int grid = static_cast<int>(std::min<long long>(sms, n_tiles));
   if (amaj == A_KMAJ && !pre_b) return launch_grouped<A_KMAJ, false>(d_probs, g, grid, smem, st);
   if (amaj == A_MNMAJ && !pre_b) return launch_grouped<A_MNMAJ, false>(d_probs, g, grid, smem, st);
   if (amaj == A_MNMAJ && pre_b) return launch_grouped<A_MNMAJ, true>(d_probs, g, grid, smem, st);
