@@ -40,9 +40,10 @@ M = N = 16384
 # for k = 256, 512), with the SHA-256 of the kernel sources they apply to;
 # reported only while the sources are unchanged.
 TRAFFIC = {
-    "sources": ["paper_2304_04612_gb300/csrc/shgemm_tc.cu", "paper_2304_04612_gb300/csrc/ptx.cuh"],
-    "sha256": "5aed4d0cb5032d7657ceeb7cc9855cb916f30f604ab954472c42058527c88cca",
-    "bytes_per_launch": {"64": 1093736704, "128": 1109490688, "256": 1148108800, "512": 1170169344},
+    "sources": ["paper_2304_04612_gb300/csrc/shgemm_tc.cu", "paper_2304_04612_gb300/csrc/ptx.cuh",
+                "paper_2304_04612_gb300/csrc/tc_common.cuh"],
+    "sha256": "83f4d226dca51fb44f78064868d24dad8d14d069152376b7f258befc826ebaf1",
+    "bytes_per_launch": {"64": 1094153472, "128": 1109935360, "256": 1150388736, "512": 1174635520},
 }
 
 
@@ -751,18 +752,23 @@ def batched_times(shg, torch, dev, stream):
     ms_, ns_ = [A.shape[0] for A in As], [A.shape[1] for A in As]
     fl = shg.new_flags(dev)
     res = {"problems": 256, "bytes_of_A": int(sum(4 * m * n for m, n in zip(ms_, ns_)))}
-    # grouped launches (one per step of Algorithm 1 for the whole batch), as
-    # a graph and enqueued directly; then the per-problem launches on the
-    # library's stream pool (SHG_BATCHED_GROUPED=0), as a graph and directly
-    for mode, use_graph, grouped in (("graph", True, "1"), ("grouped_direct", False, "1"),
-                                     ("stream_pool_graph", True, "0"), ("streams", False, "0")):
+    # grouped launches (one per step of Algorithm 1 for each lane of
+    # problems of one k class, the lanes on their own streams), as a graph,
+    # as a graph with all problems in one lane, and enqueued directly; then
+    # the per-problem launches on the library's stream pool
+    # (SHG_BATCHED_GROUPED=0), as a graph and directly
+    for mode, use_graph, grouped, lanes in (("graph", True, "1", "4"), ("graph_one_lane", True, "1", "1"),
+                                            ("grouped_direct", False, "1", "4"),
+                                            ("stream_pool_graph", True, "0", "4"), ("streams", False, "0", "4")):
         os.environ["SHG_BATCHED_GROUPED"] = grouped
+        os.environ["SHG_BATCHED_LANES"] = lanes
         fn = lambda: shg.shg_rsvd_batched(As, ranks, s, q, omegas=None, seed=4, use_graph=use_graph, out=out,
                                           workspace=ws, flags=fl, check=False, stream=stream)
         fn()
         ms = time_ms(torch, stream, fn, reps=5)
         res[mode] = {"ms": ms, "problems_per_s": 256 / (ms * 1e-3)}
     os.environ.pop("SHG_BATCHED_GROUPED", None)
+    os.environ.pop("SHG_BATCHED_LANES", None)
     # the same problems one after another through shg_rsvd on one stream
     oms = [shg.shg_gaussian_f16(4, i << 32, n, r + s,
                                 out=torch.empty(n, (r + s + 7) // 8 * 8, dtype=torch.float16, device=dev)[:, :r + s])

@@ -67,6 +67,13 @@ typedef enum shg_variant {
                            is made on the host after synchronising the stream */
 } shg_variant;
 
+/* OR'ed into the variant of shgemm_project: every output tile is summed by
+ * one CTA in K order (each element by one thread on the SIMT paths) instead
+ * of splitting tiles across CTAs with FP32 atomic partial sums, so Y is
+ * reproducible bit for bit from run to run.  It costs load balance when
+ * there are fewer output tiles than SMs. */
+#define SHG_DETERMINISTIC 0x100
+
 /*
  * Diagnostics of one randomized SVD (shg_rsvd with a non-NULL report).
  * Phases of Algorithm 1 (Sec. 2.2) whose device time goes to phase_ms:
@@ -146,8 +153,11 @@ int shg_sparse_sign_f16(uint64_t seed, uint64_t offset, int64_t rows, int64_t co
  *   trans_a = 1: A is n x m (lda >= m), Y = A^T * Omega.
  *   Omega: n x k (ldo >= k), FP16 bits (BF16 bits for SHG_SPLIT_BF16X*).
  *   Y: m x k FP32 (ldy >= k), overwritten.
- * variant: shg_variant.  Every variant takes trans_a = 0 or 1; SHG_SPLIT_TF32
- * with trans_a = 1 computes in FP32 SIMT (the TF32 kernel reads A K-major).
+ * variant: shg_variant, optionally | SHG_DETERMINISTIC.  Every variant
+ * takes trans_a = 0 or 1; SHG_SPLIT_TF32 with trans_a = 1 computes in FP32
+ * SIMT (the TF32 kernel reads A K-major).  Without SHG_DETERMINISTIC the
+ * stream-K schedule sums the parts of a split tile with FP32 atomics, so the
+ * last bits of Y may differ between runs (within the same error bound).
  * SHG_SPLIT_AUTO runs SHGEMM-FP16 and, when the range flag trips, redoes
  * the product with SHG_SPLIT_TF32 and restores *d_flags to its value on
  * entry; it synchronises `stream` (to read the flag) and may not be used

@@ -39,6 +39,8 @@ import torch
 
 from . import _lib
 
+SHG_DETERMINISTIC = 0x100  # OR'ed into a projection's variant: bitwise reproducible Y
+
 VARIANTS = {"f16": 0, "bf16x3": 1, "bf16x2": 2, "fp32": 3, "tf32": 4, "auto": 5}
 FLAG_RANGE, FLAG_NOT_SPD, FLAG_TIMEOUT = 1, 2, 4
 
@@ -114,10 +116,11 @@ def shg_sparse_sign_f16(seed: int, offset: int, rows: int, cols: int, s: float =
 
 def shgemm_project(A: torch.Tensor, omega: torch.Tensor, variant="f16", trans_a: bool = False,
                    out: torch.Tensor | None = None, flags: torch.Tensor | None = None,
-                   check: bool = True, stream=None) -> torch.Tensor:
+                   check: bool = True, stream=None, deterministic: bool = False) -> torch.Tensor:
     """Y = A @ omega (trans_a: A.T @ omega).  omega: float16 (bfloat16 for the
     BF16 variants).  With check=True the call synchronises and raises on a
-    device flag (e.g. SHG_ERR_RANGE)."""
+    device flag (e.g. SHG_ERR_RANGE).  deterministic: every output tile summed
+    by one CTA in K order (SHG_DETERMINISTIC), Y reproducible bit for bit."""
     v = _variant(variant)
     lda = _mat(A, "A", (torch.float32,))
     ldo = _mat(omega, "omega", (torch.bfloat16,) if v in (1, 2) else (torch.float16,))
@@ -131,7 +134,8 @@ def shgemm_project(A: torch.Tensor, omega: torch.Tensor, variant="f16", trans_a:
     ldy = _mat(out, "out", (torch.float32,))
     fl = flags if flags is not None else new_flags(A.device)
     _check(_lib.load().shgemm_project(m, n, k, _ptr(A), lda, int(trans_a), _ptr(omega), ldo, _ptr(out), ldy,
-                                      v, _ptr(fl), _stream(stream)), "shgemm_project")
+                                      v | (SHG_DETERMINISTIC if deterministic else 0), _ptr(fl), _stream(stream)),
+           "shgemm_project")
     if check:
         check_flags(fl, "shgemm_project")
     return out

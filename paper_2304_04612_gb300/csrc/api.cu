@@ -252,30 +252,34 @@ int shgemm_project(int64_t m, int64_t n, int64_t k, const float* A, int64_t lda,
   if (m < 1 || n < 1 || k < 1 || !A || !omega || !Y || !d_flags) return SHG_ERR_INVALID_ARG;
   if (lda < (trans_a ? m : n) || ldo < k || ldy < k) return SHG_ERR_INVALID_ARG;
   cudaStream_t st = static_cast<cudaStream_t>(stream);
+  // SHG_DETERMINISTIC: every output tile (element, on the SIMT path) summed
+  // by one CTA (thread) in K order, no split-K partial sums
+  const int det = variant & SHG_DETERMINISTIC;
+  variant &= ~SHG_DETERMINISTIC;
   switch (variant) {
     case SHG_SPLIT_F16:
       return tc_gemm(trans_a ? A_MNMAJ : A_KMAJ, B_F16, 2, m, k, n, 1, A, lda, 0, omega, ldo, Y, ldy, 0,
-                     d_flags, st);
+                     d_flags, st, nullptr, nullptr, nullptr, det != 0);
     case SHG_SPLIT_BF16X3:
     case SHG_SPLIT_BF16X2:
       return tc_gemm(trans_a ? A_MNMAJ : A_KMAJ, B_BF16, variant == SHG_SPLIT_BF16X3 ? 3 : 2, m, k, n, 1, A, lda,
-                     0, omega, ldo, Y, ldy, 0, d_flags, st);
+                     0, omega, ldo, Y, ldy, 0, d_flags, st, nullptr, nullptr, nullptr, det != 0);
     case SHG_FP32_SIMT:
-      return simt_gemm(m, k, n, A, lda, trans_a, omega, ldo, 1, Y, ldy, 0, 1, 0, 0, 0, st);
+      return simt_gemm(m, k, n, A, lda, trans_a, omega, ldo, 1, Y, ldy, 0, 1, 0, 0, 0, st, 0, det != 0);
     case SHG_SPLIT_TF32:
       // the TF32 kernel reads A K-major; the transposed product keeps the
       // full range in FP32 SIMT
-      if (trans_a) return simt_gemm(m, k, n, A, lda, 1, omega, ldo, 1, Y, ldy, 0, 1, 0, 0, 0, st);
-      return tc_tf32_gemm(m, k, n, 1, A, lda, 0, omega, ldo, Y, ldy, d_flags, st);
+      if (trans_a) return simt_gemm(m, k, n, A, lda, 1, omega, ldo, 1, Y, ldy, 0, 1, 0, 0, 0, st, 0, det != 0);
+      return tc_tf32_gemm(m, k, n, 1, A, lda, 0, omega, ldo, Y, ldy, d_flags, st, det != 0);
     case SHG_SPLIT_AUTO: {
       // SHGEMM-FP16, redone in the full exponent range when its range check trips
       bool tripped = false;
       int32_t before = 0;
       SHG_TRY(range_probe_begin(d_flags, st, &before));
-      SHG_TRY(shgemm_project(m, n, k, A, lda, trans_a, omega, ldo, Y, ldy, SHG_SPLIT_F16, d_flags, stream));
+      SHG_TRY(shgemm_project(m, n, k, A, lda, trans_a, omega, ldo, Y, ldy, SHG_SPLIT_F16 | det, d_flags, stream));
       SHG_TRY(range_probe_end(d_flags, st, before, &tripped));
       if (!tripped) return SHG_OK;
-      return shgemm_project(m, n, k, A, lda, trans_a, omega, ldo, Y, ldy, SHG_SPLIT_TF32, d_flags, stream);
+      return shgemm_project(m, n, k, A, lda, trans_a, omega, ldo, Y, ldy, SHG_SPLIT_TF32 | det, d_flags, stream);
     }
     default:
       return SHG_ERR_INVALID_ARG;

@@ -39,7 +39,8 @@ struct TcConfig {
 int tc_gemm(int amaj, int bmode, int pieces, int64_t M, int64_t N, int64_t S_k, int64_t P,
             const float* A, int64_t lda, int64_t p_stride, const void* B, int64_t ldb, float* C,
             int64_t ldc, int accumulate, int32_t* d_flags, cudaStream_t stream,
-            const TcTestHooks* hooks = nullptr, const TcConfig* force = nullptr, const void* B_lo = nullptr);
+            const TcTestHooks* hooks = nullptr, const TcConfig* force = nullptr, const void* B_lo = nullptr,
+            bool tile_ranges = false);
 // hi = RN_f16(b), lo = RN_f16((b - hi) 2^11) of a rows x cols FP32 matrix
 // (the TCEC split of the B operand, done once per call); raises
 // SHG_FLAG_RANGE when some |b| >= 65520.
@@ -49,7 +50,8 @@ int split_f16(int64_t rows, int64_t cols, const float* B, int64_t ldb, uint16_t*
 // P pieces of S_k) split into TF32 hi / 2^11-scaled lo and B FP16 widened
 // exactly to TF32; the full FP32 exponent range of A.
 int tc_tf32_gemm(int64_t M, int64_t N, int64_t S_k, int64_t P, const float* A, int64_t lda, int64_t p_stride,
-                 const uint16_t* B, int64_t ldb, float* C, int64_t ldc, int32_t* d_flags, cudaStream_t stream);
+                 const uint16_t* B, int64_t ldb, float* C, int64_t ldc, int32_t* d_flags, cudaStream_t stream,
+                 bool tile_ranges = false);
 // Times the candidate configurations of this tc_gemm call (C is
 // overwritten; synchronises `stream`) and caches the fastest for the call's
 // shape class.  *best receives it; *found_before tells whether the class was
@@ -66,10 +68,12 @@ unsigned long long tc_tune_generation();
 
 // FP32 SIMT GEMM, batched over gridDim.z with element strides.  upper_b:
 // B is upper triangular (zeros stored below the diagonal), whose zero terms
-// are skipped.
+// are skipped.  no_split: no split-K (each element summed by one thread in
+// K order, so C is bitwise reproducible).
 int simt_gemm(int64_t M, int64_t N, int64_t K, const float* A, int64_t lda, int trans_a, const void* B,
               int64_t ldb, int b_f16, float* C, int64_t ldc, int accumulate, int64_t batch,
-              int64_t stride_a, int64_t stride_b, int64_t stride_c, cudaStream_t stream, int upper_b = 0);
+              int64_t stride_a, int64_t stride_b, int64_t stride_c, cudaStream_t stream, int upper_b = 0,
+              bool no_split = false);
 
 // y = RN_bf16(x) element-wise for an FP16 matrix (BF16 test matrices from
 // the FP16 Gaussian stream).

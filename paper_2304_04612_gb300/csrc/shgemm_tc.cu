@@ -1045,7 +1045,7 @@ namespace {
 int tc_gemm_impl(int amaj, int bmode, int pieces, int64_t M, int64_t N, int64_t S_k, int64_t P, const float* A,
                  int64_t lda, int64_t p_stride, const void* B, int64_t ldb, float* C, int64_t ldc, int accumulate,
                  int32_t* d_flags, cudaStream_t stream, const TcTestHooks* hooks, const TcConfig* force,
-                 const void* B_lo) {
+                 const void* B_lo, bool tile_ranges) {
   if (M <= 0 || N <= 0 || S_k <= 0 || P <= 0) return SHG_ERR_INVALID_ARG;
   if (M >= (1ll << 31) || N >= (1ll << 31) || S_k * P >= (1ll << 31)) return SHG_ERR_INVALID_ARG;
   if (amaj == A_MNMAJ && P != 1) return SHG_ERR_INVALID_ARG;
@@ -1087,6 +1087,7 @@ int tc_gemm_impl(int amaj, int bmode, int pieces, int64_t M, int64_t N, int64_t 
   a.C = C;
   a.ldc = ldc;
   a.accumulate = accumulate;
+  a.tile_ranges = tile_ranges ? 1 : 0;
   a.flags = d_flags;
   if (wide) {
     a.st = 0;  // A is read from shared memory
@@ -1157,10 +1158,12 @@ int tc_gemm_impl(int amaj, int bmode, int pieces, int64_t M, int64_t N, int64_t 
   a.groups = (a.n_tiles > 1 && a.n_tiles <= 8 && cfg.groups != 0) ? a.n_tiles : 1;
   const long long per_group = a.units / a.groups;
   const long long ctas_per_group = std::max(1, sms / a.groups);
-  const int grid = static_cast<int>(std::min<long long>(ctas_per_group, per_group)) * a.groups;
+  const int grid = static_cast<int>(std::min<long long>(ctas_per_group, tile_ranges ? per_group / a.kblocks
+                                                                                         : per_group)) *
+                   a.groups;
   const int per_cta = grid / a.groups;
   bool split = false;
-  for (int c = 1; c < per_cta && !split; ++c)
+  for (int c = 1; c < per_cta && !split && !tile_ranges; ++c)
     if ((static_cast<long long>(c) * per_group / per_cta) % a.kblocks != 0) split = true;
   if (split && !accumulate) {
     if (cudaMemset2DAsync(C, ldc * sizeof(float), 0, N * sizeof(float), M, stream) != cudaSuccess)
@@ -1188,9 +1191,9 @@ int tc_gemm_impl(int amaj, int bmode, int pieces, int64_t M, int64_t N, int64_t 
 int tc_gemm(int amaj, int bmode, int pieces, int64_t M, int64_t N, int64_t S_k, int64_t P, const float* A,
             int64_t lda, int64_t p_stride, const void* B, int64_t ldb, float* C, int64_t ldc, int accumulate,
             int32_t* d_flags, cudaStream_t stream, const TcTestHooks* hooks, const TcConfig* force,
-            const void* B_lo) {
+            const void* B_lo, bool tile_ranges) {
   return tc_gemm_impl(amaj, bmode, pieces, M, N, S_k, P, A, lda, p_stride, B, ldb, C, ldc, accumulate, d_flags,
-                      stream, hooks, force, B_lo);
+                      stream, hooks, force, B_lo, tile_ranges);
 }
 
 // ------------------------------------------------------ B split, once

@@ -425,7 +425,8 @@ __global__ void __launch_bounds__(kTfThreads, 1)
 }  // namespace
 
 int tc_tf32_gemm(int64_t M, int64_t N, int64_t S_k, int64_t P, const float* A, int64_t lda, int64_t p_stride,
-                 const uint16_t* B, int64_t ldb, float* C, int64_t ldc, int32_t* d_flags, cudaStream_t stream) {
+                 const uint16_t* B, int64_t ldb, float* C, int64_t ldc, int32_t* d_flags, cudaStream_t stream,
+                 bool tile_ranges) {
   if (M <= 0 || N <= 0 || S_k <= 0 || P <= 0) return SHG_ERR_INVALID_ARG;
   if (M >= (1ll << 31) || N >= (1ll << 31) || S_k * P >= (1ll << 31)) return SHG_ERR_INVALID_ARG;
   if ((reinterpret_cast<uintptr_t>(A) & 15) || (reinterpret_cast<uintptr_t>(B) & 15)) return SHG_ERR_INVALID_ARG;
@@ -446,6 +447,7 @@ int tc_tf32_gemm(int64_t M, int64_t N, int64_t S_k, int64_t P, const float* A, i
   a.C = C;
   a.ldc = ldc;
   a.accumulate = 0;
+  a.tile_ranges = tile_ranges ? 1 : 0;
   a.flags = d_flags;
   a.st = 0;
   a.tmem_cols = 3 * nt <= 256 ? 256 : 512;
@@ -479,10 +481,12 @@ int tc_tf32_gemm(int64_t M, int64_t N, int64_t S_k, int64_t P, const float* A, i
   a.groups = (a.n_tiles > 1 && a.n_tiles <= 8) ? a.n_tiles : 1;
   const long long per_group = a.units / a.groups;
   const long long ctas_per_group = std::max(1, sms / a.groups);
-  const int grid = static_cast<int>(std::min<long long>(ctas_per_group, per_group)) * a.groups;
+  const int grid = static_cast<int>(std::min<long long>(ctas_per_group, tile_ranges ? per_group / a.kblocks
+                                                                                         : per_group)) *
+                   a.groups;
   const int per_cta = grid / a.groups;
   bool split = false;
-  for (int c = 1; c < per_cta && !split; ++c)
+  for (int c = 1; c < per_cta && !split && !tile_ranges; ++c)
     if ((static_cast<long long>(c) * per_group / per_cta) % a.kblocks != 0) split = true;
   if (split && cudaMemset2DAsync(C, ldc * sizeof(float), 0, N * sizeof(float), M, stream) != cudaSuccess)
     return SHG_ERR_CUDA;

@@ -150,14 +150,14 @@ int simt_grouped(const SimtArg* d, int n, int mmax, int nmax, cudaStream_t st) {
 
 int simt_gemm(int64_t M, int64_t N, int64_t K, const float* A, int64_t lda, int trans_a, const void* B,
               int64_t ldb, int b_f16, float* C, int64_t ldc, int accumulate, int64_t batch, int64_t stride_a,
-              int64_t stride_b, int64_t stride_c, cudaStream_t stream, int upper_b) {
+              int64_t stride_b, int64_t stride_c, cudaStream_t stream, int upper_b, bool no_split) {
   if (M <= 0 || N <= 0 || K <= 0 || batch <= 0) return SHG_ERR_INVALID_ARG;
   if (M >= (1ll << 31) || N >= (1ll << 31) || K >= (1ll << 31)) return SHG_ERR_INVALID_ARG;
   const int gx = static_cast<int>((N + BN - 1) / BN), gy = static_cast<int>((M + BM - 1) / BM);
   if (gy > 65535) return SHG_ERR_UNSUPPORTED;
   // split K so that the grid covers the GPU a few times over (single batch only)
   int splits = 1;
-  if (batch == 1) {
+  if (batch == 1 && !no_split) {
     const long long tiles = static_cast<long long>(gx) * gy;
     const long long want = 4ll * grid_sms();
     while (tiles * splits < want && K / (splits * 2) >= 256) splits *= 2;

@@ -37,6 +37,7 @@ struct TcArgs {
   uint32_t tmem_cols, b_bytes;
   int kc;
   int groups;    // CTA groups, one per run of N tiles (divides n_tiles and gridDim.x)
+  int tile_ranges;  // CTA ranges hold whole output tiles (each summed in K order by one CTA)
   unsigned long long wait_ns;
   int drop_commit;
 };
@@ -186,7 +187,8 @@ struct UnitWalk {
   }
 };
 
-// Units of this CTA.  The grid is split into `groups` equal groups, group g
+// Units of this CTA (with tile_ranges rounded to whole output tiles, so
+// that no tile is summed by two CTAs).  The grid is split into `groups` equal groups, group g
 // owning N tiles [g, g + 1) x n_tiles / groups; the i-th CTAs of all groups
 // cover the same (M tile, K block) range, so the groups read the same A
 // tiles at about the same time and all but the first read come from L2:
@@ -196,6 +198,12 @@ __device__ __forceinline__ void cta_range(const TcArgs& a, long long& u0, long l
   const int g = static_cast<int>(blockIdx.x) % G, i = static_cast<int>(blockIdx.x) / G;
   const int C = static_cast<int>(gridDim.x) / G;
   const long long per = a.units / G;
+  if (a.tile_ranges) {
+    const long long tiles = per / a.kblocks;
+    u0 = g * per + (static_cast<long long>(i) * tiles / C) * a.kblocks;
+    u1 = g * per + (static_cast<long long>(i + 1) * tiles / C) * a.kblocks;
+    return;
+  }
   u0 = g * per + static_cast<long long>(i) * per / C;
   u1 = g * per + static_cast<long long>(i + 1) * per / C;
 }

@@ -165,3 +165,11 @@ def test_report_struct_layout():
     assert R.phase_ms.offset == 24 and ctypes.sizeof(R) == 24 + 4 * len(_lib.PHASES)
     src = open(HEADER).read()
     assert f"#define SHG_NUM_PHASES     {len(_lib.PHASES)}" in src
+
+
+def test_deterministic_flag_matches_header():
+    import paper_2304_04612_gb300 as shg
+    src = open(HEADER).read()
+    assert f"#define SHG_DETERMINISTIC 0x{shg.SHG_DETERMINISTIC:x}" in src
+    # it lies above every variant number, so OR-ing it in never changes the variant
+    assert all(v < shg.SHG_DETERMINISTIC for v in shg.VARIANTS.values())

@@ -212,3 +212,21 @@ def test_gaussian_generator_layout_independent(shg):
     shg.shg_gaussian_f16(7, 0, 40, 30, out=buf[:, :30])
     assert torch.equal(a, buf[:, :30].cpu())
     assert torch.count_nonzero(buf[:, 30:]) == 0
+
+
+@pytest.mark.parametrize("variant,k", [("f16", 64), ("f16", 512), ("tf32", 96), ("fp32", 64)])
+def test_deterministic_projection_is_bitwise_reproducible(shg, variant, k):
+    """SHG_DETERMINISTIC: each output tile summed by one CTA in K order, so two
+    runs give the same bits; the result still meets the projection bound.  The
+    shape (40 tiles of 128 rows, fewer than the SMs, and a long K range) is one
+    where the default stream-K schedule splits every tile across CTAs."""
+    m, n = 5000, 6144
+    A_h = uniform(m, n, seed=41)
+    Om_h = omega_f16(n, k, seed=42)
+    A, Om = dev(A_h), dev(Om_h)
+    ys = [shg.shgemm_project(A, Om, variant, deterministic=True) for _ in range(3)]
+    for y in ys[1:]:
+        assert torch.equal(y, ys[0])
+    ref = OS.project_exact(A_h, Om_h)
+    err = np.linalg.norm(ys[0].cpu().numpy() - ref) / np.linalg.norm(ref)
+    assert err <= 1e-5, err
