@@ -5,7 +5,7 @@
 // C[b] (+)= op(A[b]) * B[b] in register-blocked tiles: 256 threads, each
 // with 8 x 8 outputs (two 4 x 4 quadrants in each direction, so that its
 // shared-memory reads are 128-bit and conflict free), a 128 x 128 output tile
-// (256 x 64 when N <= 64), 8-deep K tiles double-buffered in shared memory
+// (256 x 64 when N <= 64), 16-deep K tiles double-buffered in shared memory
 // (the next tile's global loads in registers while the current one is
 // multiplied; B in FP16 widened exactly to FP32 on the way in), split-K
 // over gridDim.z when the tiles alone would not cover the GPU (partials
@@ -137,7 +137,7 @@ __global__ void __launch_bounds__(256) simt_grouped_kernel(const SimtArg* __rest
 }
 
 // ---------------------------------------------------------------- 8 x 8 tiles
-constexpr int TK = 8;  // K depth of a shared-memory tile
+constexpr int TK = 16;  // K depth of a shared-memory tile
 
 template <bool TA, bool BH, int TBM, int TBN>
 __global__ void __launch_bounds__(256, 2)
@@ -148,8 +148,8 @@ __global__ void __launch_bounds__(256, 2)
   __shared__ __align__(16) float As[2][TK][TBM + 4];
   __shared__ __align__(16) float Bs[2][TK][TBN + 4];
   constexpr int TX = TBN / 8;           // threads along N
-  constexpr int A_VEC = TBM * TK / 4;   // float4 pieces of an A tile (2 TBM)
-  constexpr int B_VEC = BH ? TBN : TBN * TK / 4;  // 8-half (FP16) or float4 (FP32) pieces of a B tile
+  constexpr int A_VEC = TBM * TK / 4;   // float4 pieces of an A tile
+  constexpr int B_VEC = TBN * TK / (BH ? 8 : 4);  // 8-half (FP16) or float4 (FP32) pieces of a B tile
   const int tid = threadIdx.x;
   const int tx = tid % TX, ty = tid / TX;
   const int m0 = blockIdx.y * TBM, n0 = blockIdx.x * TBN;
