@@ -380,7 +380,7 @@ def run_factor(args):
         fn = lambda: shg.shg_rsvd(A, Om, 32, 32, 0, args.variant, workspace=ws, flags=fl, check=False)
     elif args.factor == "batched":
         As, ranks, s_, q_, ws, out = batched_problems(shg, torch, dev, dct_bases=True)
-        # on the stream pool without the graph: launches in enqueue order, problem by problem
+        # the grouped launches in lanes, enqueued directly (no graph)
         fn = lambda: shg.shg_rsvd_batched(As, ranks, s_, q_, omegas=None, seed=4, use_graph=False, out=out,
                                           workspace=ws, flags=fl, check=False)
     else:

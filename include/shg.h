@@ -372,9 +372,13 @@ int shg_mode_project(int ndim, const int64_t* dims, int mode, int64_t J, const f
  *   linear index of the other modes (see shg_mode_project).  The
  *   tensor-core path also needs dims[2] % 4 == 0 (TMA row stride).
  *   W_i = X_(i) Omega_i; Q_i = CholeskyQR2(W_i) -> factors[i] (dims[i] x J_i, ld J_i).
- *   core (J0 x J1 x J2, row-major) = X x_0 Q_0^T x_1 Q_1^T x_2 Q_2^T.
- * variant: SHG_SPLIT_F16 (SHGEMM projections, TCEC-split first core
- * contraction) or SHG_FP32_SIMT (FP32 baseline).
+ *   core (J0 x J1 x J2, row-major) = X x_0 Q_0^T x_1 Q_1^T x_2 Q_2^T,
+ *   contracted in the order mode 2, mode 0, mode 1 (the first two as single
+ *   products over all of X and of X x_2 Q_2^T).
+ * variant: SHG_SPLIT_F16 (SHGEMM projections; the mode-2 and mode-0 core
+ * contractions as FP32-accurate TCEC products on the tensor cores, the last
+ * mode as J0 small FP32 products), SHG_SPLIT_TF32, SHG_SPLIT_AUTO or
+ * SHG_FP32_SIMT (FP32 baseline).
  * The three modes' projections and CholeskyQR2 run on three streams owned
  * by the library (created on the first call on a device), forked from and
  * joined back to `stream`; the call stays asynchronous and ordered on

@@ -124,8 +124,8 @@ HosvdLayout hosvd_layout(const int64_t* d, const int64_t* J) {
     maxJ = J[i] > maxJ ? J[i] : maxJ;
   }
   for (int i = 0; i < 3; ++i) L.T[i] = take(maxI * maxL * 4);  // one per mode: the modes run concurrently
-  L.T1 = take(d[0] * d[1] * L.ld[2] * 4);
-  L.T2 = take(d[0] * J[1] * J[2] * 4);
+  L.T1 = take(d[0] * d[1] * J[2] * 4);  // X x_2 Q_2^T, (I0 I1) x J2, leading dimension J2
+  L.T2 = take(J[0] * d[1] * J[2] * 4);  // then x_0 Q_0^T: J0 x (I1 J2)
   for (int i = 0; i < 3; ++i) L.small[i] = take(cholqr_small_bytes(maxJ));
   L.Bhi = take(d[2] * L.ld[2] * 2);  // Q_2 split into FP16 hi / lo for the first core contraction
   L.Blo = take(d[2] * L.ld[2] * 2);
@@ -518,18 +518,29 @@ int shg_rp_hosvd(int ndim, const int64_t* dims, const int64_t* ranks, int64_t ov
     if (cudaStreamWaitEvent(st, mp->done[i], 0) != cudaSuccess) return SHG_ERR_CUDA;
   }
   pool_lock.unlock();
-  // core = X x_2 Q_2^T x_1 Q_1^T x_0 Q_0^T
+  // core = X x_2 Q_2^T x_0 Q_0^T x_1 Q_1^T: the two large contractions as
+  // single products on the tensor cores (X is read once), then J0 small
+  // products for the last mode
+  //   T1 = X_(01) Q_2                 (I0 I1) x J2, K = I2
+  //   T2[j0] = sum_i0 Q_0[i0, j0] T1[i0]   J0 x (I1 J2), K = I0
+  //   core[j0] = Q_1^T T2[j0]            J1 x J2 each, K = I1
   if (tc) {
     uint16_t* Bhi = reinterpret_cast<uint16_t*>(w + L.Bhi);
     uint16_t* Blo = reinterpret_cast<uint16_t*>(w + L.Blo);
     SHG_TRY(split_f16(I2, J2, W[2], L.ld[2], Bhi, Blo, L.ld[2], d_flags, st));
-    SHG_TRY(tc_gemm(A_KMAJ, B_SPLIT_PRE, 2, I0 * I1, J2, I2, 1, X, I2, 0, Bhi, L.ld[2], T1, L.ld[2], 0, d_flags, st,
+    SHG_TRY(tc_gemm(A_KMAJ, B_SPLIT_PRE, 2, I0 * I1, J2, I2, 1, X, I2, 0, Bhi, L.ld[2], T1, J2, 0, d_flags, st,
                     nullptr, nullptr, Blo));
   } else {
-    SHG_TRY(simt_gemm(I0 * I1, J2, I2, X, I2, 0, W[2], L.ld[2], 0, T1, L.ld[2], 0, 1, 0, 0, 0, st));
+    SHG_TRY(simt_gemm(I0 * I1, J2, I2, X, I2, 0, W[2], L.ld[2], 0, T1, J2, 0, 1, 0, 0, 0, st));
   }
-  SHG_TRY(simt_gemm(J1, J2, I1, W[1], L.ld[1], 1, T1, L.ld[2], 0, T2, J2, 0, I0, 0, I1 * L.ld[2], J1 * J2, st));
-  SHG_TRY(simt_gemm(J0, J1 * J2, I0, W[0], L.ld[0], 1, T2, J1 * J2, 0, core, J1 * J2, 0, 1, 0, 0, 0, st));
+  if (tc && (I1 * J2) % 4 == 0) {
+    // FP32-accurate TCEC product, both operands split on chip
+    SHG_TRY(tc_gemm(A_MNMAJ, B_SPLIT, 2, J0, I1 * J2, I0, 1, W[0], L.ld[0], 0, T1, I1 * J2, T2, I1 * J2, 0, d_flags,
+                    st));
+  } else {
+    SHG_TRY(simt_gemm(J0, I1 * J2, I0, W[0], L.ld[0], 1, T1, I1 * J2, 0, T2, I1 * J2, 0, 1, 0, 0, 0, st));
+  }
+  SHG_TRY(simt_gemm(J1, J2, I1, W[1], L.ld[1], 1, T2, J2, 0, core, J2, 0, J0, 0, I1 * J2, J1 * J2, st));
   return SHG_OK;
 }
 

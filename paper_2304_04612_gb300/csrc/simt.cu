@@ -128,6 +128,18 @@ __device__ __forceinline__ void simt_gemm_body(int M, int N, int K, const float*
   }
 }
 
+// The 128 x 64 tile as a batched / split-K launch (small outputs, where the
+// 8 x 8 tiles would be mostly padding).
+template <bool TA, bool BH>
+__global__ void __launch_bounds__(256) simt_small_kernel(int M, int N, int K, const float* __restrict__ A,
+                                                        long long lda, const void* __restrict__ Bv, long long ldb,
+                                                        float* __restrict__ C, long long ldc, int k_chunk,
+                                                        int splits, int atomic, long long sa, long long sb,
+                                                        long long sc, int upper_b) {
+  simt_gemm_body<TA, BH>(M, N, K, A, lda, Bv, ldb, C, ldc, k_chunk, splits, atomic, sa, sb, sc, blockIdx.x, blockIdx.y,
+                         blockIdx.z, upper_b);
+}
+
 // One GEMM C = A B per problem of a batch (blockIdx.z), FP32 operands.
 __global__ void __launch_bounds__(256) simt_grouped_kernel(const SimtArg* __restrict__ args) {
   const SimtArg a = args[blockIdx.z];
@@ -327,24 +339,39 @@ int simt_gemm(int64_t M, int64_t N, int64_t K, const float* A, int64_t lda, int 
               int64_t stride_b, int64_t stride_c, cudaStream_t stream, int upper_b, bool no_split) {
   if (M <= 0 || N <= 0 || K <= 0 || batch <= 0) return SHG_ERR_INVALID_ARG;
   if (M >= (1ll << 31) || N >= (1ll << 31) || K >= (1ll << 31)) return SHG_ERR_INVALID_ARG;
-  // 128 x 128 output tiles, or 256 x 64 for narrow products
+  // 128 x 128 output tiles, or 256 x 64 for narrow products; the 128 x 64
+  // tile (8 x 4 per thread, about 0.8 of the larger tiles' rate) when the
+  // larger tiles would be mostly padding (e.g. many 48 x 48 outputs)
   const bool narrow = N <= 64;
-  const int tbm = narrow ? 256 : 128, tbn = narrow ? 64 : 128;
+  int tbm = narrow ? 256 : 128, tbn = narrow ? 64 : 128;
+  const auto padded = [&](int bm, int bn) {
+    return static_cast<double>((M + bm - 1) / bm * bm) * static_cast<double>((N + bn - 1) / bn * bn);
+  };
+  const bool small = padded(BM, BN) / 0.8 < padded(tbm, tbn);
+  if (small) {
+    tbm = BM;
+    tbn = BN;
+  }
   const int gx = static_cast<int>((N + tbn - 1) / tbn), gy = static_cast<int>((M + tbm - 1) / tbm);
   if (gy > 65535) return SHG_ERR_UNSUPPORTED;
-  // split K so that the grid covers the GPU a few times over (single batch only)
+  // split K so that the grid covers the GPU a few times over: one product
+  // while each part keeps at least 256 of K; a batch whose outputs are
+  // contiguous (one zeroing covers them) while each part keeps 64
   int splits = 1;
-  if (batch == 1 && !no_split) {
-    const long long tiles = static_cast<long long>(gx) * gy;
+  const bool contiguous = batch == 1 || stride_c == M * ldc;
+  if (!no_split && contiguous) {
+    const long long tiles = static_cast<long long>(gx) * gy * batch;
     const long long want = 4ll * grid_sms();
-    while (tiles * splits < want && K / (splits * 2) >= 256) splits *= 2;
+    const int64_t min_part = batch == 1 ? 256 : 64;
+    while (tiles * splits < want && K / (splits * 2) >= min_part) splits *= 2;
   }
-  const int kc = static_cast<int>(((K + splits - 1) / splits + TK - 1) / TK * TK);
+  const int kstep = small ? BK : TK;
+  const int kc = static_cast<int>(((K + splits - 1) / splits + kstep - 1) / kstep * kstep);
   splits = static_cast<int>((K + kc - 1) / kc);
   if (batch * splits > 65535) return SHG_ERR_UNSUPPORTED;
   const int atomic = (splits > 1 || accumulate) ? 1 : 0;
   if (splits > 1 && !accumulate) {
-    if (cudaMemset2DAsync(C, ldc * sizeof(float), 0, N * sizeof(float), M, stream) != cudaSuccess)
+    if (cudaMemset2DAsync(C, ldc * sizeof(float), 0, N * sizeof(float), M * batch, stream) != cudaSuccess)
       return SHG_ERR_CUDA;
   }
   // 128-bit global accesses where every row (and batch entry) starts on 16 bytes
@@ -358,7 +385,18 @@ int simt_gemm(int64_t M, int64_t N, int64_t K, const float* A, int64_t lda, int 
   simt_tile_kernel<TA, BH, TBM, TBN><<<grid, 256, 0, stream>>>(                                               \
       static_cast<int>(M), static_cast<int>(N), static_cast<int>(K), A, lda, B, ldb, C, ldc, kc, splits, atomic, \
       stride_a, stride_b, stride_c, upper_b, vec_a, vec_b, vec_c)
-  if (narrow) {
+  if (small) {
+#define SHG_SMALL(TA, BH)                                                                                     \
+  simt_small_kernel<TA, BH><<<grid, 256, 0, stream>>>(static_cast<int>(M), static_cast<int>(N),               \
+                                                      static_cast<int>(K), A, lda, B, ldb, C, ldc, kc, splits, \
+                                                      atomic, stride_a, stride_b, stride_c, upper_b)
+    if (trans_a) {
+      if (b_f16) SHG_SMALL(true, true); else SHG_SMALL(true, false);
+    } else {
+      if (b_f16) SHG_SMALL(false, true); else SHG_SMALL(false, false);
+    }
+#undef SHG_SMALL
+  } else if (narrow) {
     if (trans_a) {
       if (b_f16) SHG_SIMT(true, true, 256, 64); else SHG_SIMT(true, false, 256, 64);
     } else {
