@@ -557,6 +557,8 @@ def side_measurements(shg, OS, torch, dev, A, A_host, Om, Om_host, Ys, flags, st
         back = torch.cuda.Event()
         back.record(dstream)
         stream.wait_event(back)
+    # the host link's own rate: one whole-A copy from the same pinned buffer
+    link_ms = time_ms(torch, stream, lambda: A.copy_(A_pin, non_blocking=True), reps=5)
     e2e_step()
     torch.cuda.synchronize()
     ms = time_ms(torch, stream, e2e_step, reps=10)
@@ -568,6 +570,8 @@ def side_measurements(shg, OS, torch, dev, A, A_host, Om, Om_host, Ys, flags, st
     out["e2e"] = {"value": sum(2.0 * M * N * k for k in KS) / (ms * 1e-3) / 1e12, "unit": "TFLOP/s",
                   "ms_per_step": ms, "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h,
                   "h2d_gbs_if_copy_bound": h2d / (ms * 1e-3) / 1e9, "reps": 10,
+                  "h2d_link_gbs": A_host.nbytes / (link_ms * 1e-3) / 1e9,
+                  "fraction_of_copy_floor": (h2d / (A_host.nbytes / (link_ms * 1e-3))) / (ms * 1e-3),
                   "pipeline": f"A in {nblk} row blocks on {ncs} copy streams, projections per block, Y rows "
                               "back on a fifth stream",
                   "check_rel_err_sampled_rows_k512": e2e_err}
