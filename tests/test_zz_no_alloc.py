@@ -58,3 +58,38 @@ def test_static_null_flags_and_size_limit():
     rc = lib.shg_cholqr2_static(1 << 20, 64, ctypes.c_void_p(big.data_ptr()), 64, ctypes.c_void_p(0),
                                 ctypes.c_void_p(0))
     assert rc == 4  # SHG_ERR_WORKSPACE
+
+
+def test_static_allocates_nothing():
+    """Observed, not only read: device free memory is the same before and
+    after a call, and the call can be captured into a CUDA graph in global
+    capture mode, under which any device allocation (or other call that is
+    unsafe during capture) from any thread makes the capture fail; the
+    replayed graph gives the workspace entry point's result."""
+    import paper_2304_04612_gb300 as shg
+    from paper_2304_04612_gb300 import _lib
+    lib = _lib.load()
+    dev = torch.device("cuda", 0)
+    rng = np.random.default_rng(11)
+    X0 = torch.from_numpy(rng.standard_normal((3000, 40)).astype(np.float32)).to(dev)
+    ref = shg.shg_cholqr2(X0.clone())
+    flags = shg.new_flags(dev)
+    X = X0.clone()
+    assert _call_static(lib, X, flags) == 0  # first call: the scratch's address is looked up once
+    torch.cuda.synchronize()
+    free0 = torch.cuda.mem_get_info(dev)[0]
+    X.copy_(X0)
+    assert _call_static(lib, X, flags) == 0
+    torch.cuda.synchronize()
+    assert torch.cuda.mem_get_info(dev)[0] == free0
+    g = torch.cuda.CUDAGraph()
+    Xg = X0.clone()
+    torch.cuda.synchronize()
+    with torch.cuda.graph(g, capture_error_mode="global"):
+        rc = _call_static(lib, Xg, flags)
+    assert rc == 0
+    Xg.copy_(X0)
+    g.replay()
+    torch.cuda.synchronize()
+    assert int(flags.item()) == 0
+    assert (Xg - ref).abs().max().item() <= 1e-6
