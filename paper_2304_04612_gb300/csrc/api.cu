@@ -1,6 +1,7 @@
 // extern "C" entry points of libshg.so (declared in include/shg.h):
 // argument validation on the host, then the launches of Algorithm 1
 // (randomized SVD) and Algorithm 2 (RP-HOSVD) on the caller's stream.
+#include <atomic>
 #include <cstring>
 #include <mutex>
 
@@ -10,13 +11,17 @@
 namespace shg {
 
 int sm_count() {
-  static int cache[64] = {0};
+  // per-device cache; host threads may fill an entry at the same time (same value)
+  static std::atomic<int> cache[64];
   int dev = 0;
   if (cudaGetDevice(&dev) != cudaSuccess || dev < 0) return -1;
-  if (dev < 64 && cache[dev] > 0) return cache[dev];
+  if (dev < 64) {
+    const int c = cache[dev].load(std::memory_order_relaxed);
+    if (c > 0) return c;
+  }
   int n = 0;
   if (cudaDeviceGetAttribute(&n, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess) return -1;
-  if (dev < 64) cache[dev] = n;
+  if (dev < 64) cache[dev].store(n, std::memory_order_relaxed);
   return n;
 }
 
