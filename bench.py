@@ -581,6 +581,7 @@ def side_measurements(shg, OS, torch, dev, A, A_host, Om, Om_host, Ys, flags, st
     out["rp_hosvd_512"] = hosvd_times(shg, torch, dev, stream)
     out["rsvd_batched_256"] = batched_times(shg, torch, dev, stream)
     out["rsvd_4096_p256"] = rsvd4096_times(shg, torch, dev, stream)
+    out["rsvd_16384_k64"] = rsvd16384_times(shg, torch, dev, stream)
     out["learned_sketch_2048"] = sketch_times(shg, torch, dev, stream)
 
     # CPU baseline: the oracle on a bounded row sample of the same sweep
@@ -638,6 +639,44 @@ def rsvd4096_times(shg, torch, dev, stream):
     sig = 2.0 ** (-np.arange(1, 513) * (np.log2(1e3) / p))
     res["optimal_residual"] = float(np.sqrt(np.sum(sig[p:] ** 2) / np.sum(sig ** 2)))
     res["l2"] = "A (64 MiB) stays in L2 between calls; the k x k steps dominate"
+    return res
+
+
+def rsvd16384_times(shg, torch, dev, stream):
+    """Randomized SVD where the passes over A dominate: A 16384 x 16384 FP32
+    (1 GiB, larger than L2) = U diag(sigma) V^T with sigma_i = 2^(-i/8) on 512
+    planted directions (U, V orthonormal Q factors of seeded Gaussians, built on
+    the GPU outside the timed calls), rank 32, oversampling 32 (k = 64), q = 0
+    and q = 1; SHGEMM path vs FP32 path, residual ||A - U S V^T||_F / ||A||_F
+    against the optimal rank-32 residual of the planted spectrum."""
+    N, r, p, s = 16384, 512, 32, 32
+    g = torch.Generator(device=dev).manual_seed(6)
+    U0 = torch.linalg.qr(torch.randn(N, r, device=dev, generator=g))[0]
+    V0 = torch.linalg.qr(torch.randn(N, r, device=dev, generator=g))[0]
+    sig = torch.pow(2.0, -torch.arange(1, r + 1, device=dev, dtype=torch.float32) / 8.0)
+    A = ((U0 * sig) @ V0.T).contiguous()
+    del U0, V0
+    Om = torch.randn(N, p + s, device=dev, generator=g).half()
+    nA = torch.linalg.norm(A)
+    fl = shg.new_flags(dev)
+    sig_h = 2.0 ** (-np.arange(1, r + 1) / 8.0)
+    res = {"config": "A 16384x16384 FP32, sigma_i = 2^(-i/8) (512 planted), rank 32, s = 32",
+           "optimal_residual": float(np.sqrt(np.sum(sig_h[p:] ** 2) / np.sum(sig_h ** 2)))}
+    for q in (0, 1):
+        ws = torch.empty(shg.rsvd_workspace_size(N, N, p, s, q), dtype=torch.uint8, device=dev)
+        row = {}
+        for v in ("f16", "fp32"):
+            outs = (torch.empty(N, p, device=dev), torch.empty(p, device=dev), torch.empty(N, p, device=dev), None)
+            fn = lambda: shg.shg_rsvd(A, Om, p, s, q, v, workspace=ws, out=outs, flags=fl, check=False,
+                                      stream=stream)
+            fn()
+            ms = time_ms(torch, stream, fn, reps=5)
+            U, S, V = outs[:3]
+            row[v] = {"ms": ms, "residual": float(torch.linalg.norm(A - (U * S) @ V.T) / nA)}
+        row["speedup_f16_vs_fp32"] = row["fp32"]["ms"] / row["f16"]["ms"]
+        res[f"q{q}"] = row
+        del ws
+    shg.check_flags(fl, "rsvd_16384")
     return res
 
 

@@ -219,11 +219,13 @@ int shg_sgemm(int64_t m, int64_t n, int64_t kk,
  *   already cached is not timed again.  It may not run while `stream` is
  *   being captured (SHG_ERR_UNSUPPORTED), nor for SHG_FP32_SIMT.
  *   config_out (host, nullable, 6 entries): {A stages, B stages, drain K
- *   blocks, grouping, 1 if the class was cached before the call, wide tiles}.
- *   "Wide tiles" (K-major A with an FP16 Omega and k > 128): output tiles
- *   of up to 256 columns whose A operand is split in shared memory (one A
- *   pass per 256 columns) instead of 128-column tiles split into tensor
- *   memory; the tuner times both.
+ *   blocks, grouping, 1 if the class was cached before the call, tiles}.
+ *   Tiles (K-major A with an FP16 Omega and k > 128): 1 = output tiles of
+ *   up to 256 columns per CTA whose A operand is split in shared memory (one
+ *   A pass per 256 columns), 2 = 256 x 256 tiles on pairs of CTAs (one
+ *   tensor-core MMA of 256 rows over two SMs, each SM holding half of the
+ *   Omega tile), 0 = 128-column tiles split into tensor memory; the tuner
+ *   times all three.
  *   shg_autotune_lookup reports the cached configuration of a class
  *   (config_out[4] = 0 when it has none; the other entries are then the
  *   built-in defaults).  shg_autotune_clear empties the cache.
@@ -238,6 +240,24 @@ int shg_autotune_project(int64_t m, int64_t n, int64_t k, const float* A, int64_
                          int32_t* d_flags, void* stream, int32_t* config_out);
 int shg_autotune_lookup(int64_t m, int64_t n, int64_t k, int trans_a, int variant, int32_t* config_out);
 int shg_autotune_clear(void);
+/*
+ * The autotuner's cache as plain records, so that a caller can keep it
+ * across processes (the Python binding stores it as JSON together with the
+ * GPU's name and SM count, and loads it only on the same kind of GPU).  No
+ * counterpart in the paper.  A record is SHG_TUNE_RECORD int32 values:
+ *   {A layout (0 K-major, 1 MN-major), Omega / B mode, pieces, N tile,
+ *    N tiles, floor(log2 m), floor(log2 K), more than one K piece,
+ *    A stages, B stages, drain K blocks, grouping, wide tiles, CTA pairs}.
+ * shg_autotune_export writes min(capacity, entries) records to `records`
+ * (host memory, capacity * SHG_TUNE_RECORD values; NULL when capacity = 0)
+ * and the number of entries to *count.  shg_autotune_import checks every
+ * record (SHG_ERR_INVALID_ARG, nothing added, when one is out of range) and
+ * adds those whose shape class is not cached yet; *added (nullable)
+ * receives how many.  Neither touches the GPU.
+ */
+#define SHG_TUNE_RECORD 14
+int shg_autotune_export(int32_t* records, int32_t capacity, int32_t* count);
+int shg_autotune_import(const int32_t* records, int32_t count, int32_t* added);
 int shg_rsvd_batched_autotune(int batch, const int64_t* m, const int64_t* n, const int64_t* rank,
                               int64_t oversampling, const float* const* A, const int64_t* lda, uint64_t seed,
                               void* workspace, size_t ws_bytes, int reps, int32_t* d_flags, void* stream,

@@ -23,6 +23,8 @@ shg_rp_hosvd       random-projection HOSVD of a 3-way tensor (Algorithm 2)
 shg_rsvd_batched   many uneven randomized SVDs at once (concurrent branches, CUDA graph)
 shg_autotune_project, shg_autotune_lookup, shg_autotune_clear, shg_rsvd_batched_autotune
                    launch configuration of the tensor-core projection per shape class
+shg_autotune_export, shg_autotune_import, save_autotune, load_autotune
+                   the tuner's cache as records / as JSON keyed by GPU name and SM count
 rsvd_workspace_size, rp_hosvd_workspace_size, rsvd_batched_workspace_size
                    workspace bytes of the factorizations (caller-allocated)
 shg_alpha_y_f16    variance of an FP16-rounded N(0,1) value (alpha_Y, Sec. 3.2)
@@ -34,6 +36,7 @@ sketch.SketchFn    torch.autograd.Function over the two above; sketch.choose_ske
 from __future__ import annotations
 
 import ctypes
+import os
 
 import torch
 
@@ -143,7 +146,7 @@ def shgemm_project(A: torch.Tensor, omega: torch.Tensor, variant="f16", trans_a:
 
 def _config(arr) -> dict:
     return {"a_stages": arr[0], "b_stages": arr[1], "drain_kblocks": arr[2], "n_groups": bool(arr[3]),
-            "cached": bool(arr[4]), "wide": bool(arr[5])}
+            "cached": bool(arr[4]), "wide": bool(arr[5]), "pair": arr[5] == 2}
 
 
 def shg_autotune_project(A: torch.Tensor, omega: torch.Tensor, variant="f16", trans_a: bool = False, reps: int = 3,
@@ -176,6 +179,69 @@ def shg_autotune_lookup(m: int, n: int, k: int, trans_a: bool = False, variant="
 
 def shg_autotune_clear() -> None:
     _check(_lib.load().shg_autotune_clear(), "shg_autotune_clear")
+
+
+TUNE_RECORD = 14
+_TUNE_FIELDS = ("a_layout", "b_mode", "pieces", "n_tile", "n_tiles", "m_log2", "k_log2", "k_pieces",
+                "a_stages", "b_stages", "drain_kblocks", "n_groups", "wide", "pair")
+
+
+def shg_autotune_export() -> list[dict]:
+    """The autotuner's cache, one dict per shape class."""
+    lib = _lib.load()
+    n = ctypes.c_int32(0)
+    _check(lib.shg_autotune_export(None, 0, ctypes.byref(n)), "shg_autotune_export")
+    buf = (ctypes.c_int32 * max(1, n.value * TUNE_RECORD))()
+    _check(lib.shg_autotune_export(buf, n.value, ctypes.byref(n)), "shg_autotune_export")
+    return [dict(zip(_TUNE_FIELDS, buf[i * TUNE_RECORD:(i + 1) * TUNE_RECORD])) for i in range(n.value)]
+
+
+def shg_autotune_import(entries: list[dict]) -> int:
+    """Add cache entries (as shg_autotune_export gives them) for the classes
+    not cached yet; returns how many were added."""
+    vals = [int(e[f]) for e in entries for f in _TUNE_FIELDS]
+    buf = (ctypes.c_int32 * max(1, len(vals)))(*vals)
+    added = ctypes.c_int32(0)
+    _check(_lib.load().shg_autotune_import(buf, len(entries), ctypes.byref(added)), "shg_autotune_import")
+    return added.value
+
+
+def save_autotune(path: str, gpu_name: str | None = None, sm_count: int | None = None) -> int:
+    """Write the autotuner's cache to a JSON file keyed by the GPU's name and
+    SM count (those of the current CUDA device unless given); returns the
+    number of entries written."""
+    import json
+    if gpu_name is None or sm_count is None:
+        props = torch.cuda.get_device_properties(torch.cuda.current_device())
+        gpu_name = props.name if gpu_name is None else gpu_name
+        sm_count = props.multi_processor_count if sm_count is None else sm_count
+    entries = shg_autotune_export()
+    tmp = path + ".tmp"
+    with open(tmp, "w") as f:
+        json.dump({"format": "shg-autotune-1", "gpu": gpu_name, "sm_count": int(sm_count), "entries": entries}, f,
+                  indent=1)
+    os.replace(tmp, path)
+    return len(entries)
+
+
+def load_autotune(path: str, gpu_name: str | None = None, sm_count: int | None = None) -> int:
+    """Load a cache written by save_autotune when it was made on the same kind
+    of GPU (name and SM count); returns the number of entries added (0 for a
+    missing file or another GPU)."""
+    import json
+    if not os.path.exists(path):
+        return 0
+    with open(path) as f:
+        d = json.load(f)
+    if d.get("format") != "shg-autotune-1":
+        raise ValueError(f"{path}: not an autotune cache")
+    if gpu_name is None or sm_count is None:
+        props = torch.cuda.get_device_properties(torch.cuda.current_device())
+        gpu_name = props.name if gpu_name is None else gpu_name
+        sm_count = props.multi_processor_count if sm_count is None else sm_count
+    if d.get("gpu") != gpu_name or int(d.get("sm_count", -1)) != int(sm_count):
+        return 0
+    return shg_autotune_import(d["entries"])
 
 
 def shg_rsvd_batched_autotune(As, ranks, oversampling: int, seed: int = 0, reps: int = 3,

@@ -42,6 +42,8 @@ SIGNATURES = {
                                      c_int, c_vp, c_vp, c_vp]),
     "shg_autotune_lookup": (c_int, [c_i64, c_i64, c_i64, c_int, c_int, c_vp]),
     "shg_autotune_clear": (c_int, []),
+    "shg_autotune_export": (c_int, [c_vp, ctypes.c_int32, c_vp]),
+    "shg_autotune_import": (c_int, [c_vp, ctypes.c_int32, c_vp]),
     "shg_rsvd_batched_autotune": (c_int, [c_int, c_vp, c_vp, c_vp, c_i64, c_vp, c_vp, c_u64, c_vp, c_sz, c_int,
                                           c_vp, c_vp, c_vp]),
     "shg_rsvd_batched": (c_int, [c_int, c_vp, c_vp, c_vp, c_i64, c_int, c_vp, c_vp, c_vp, c_vp, c_u64, c_vp, c_vp,

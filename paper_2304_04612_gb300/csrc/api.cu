@@ -314,7 +314,7 @@ static void put_config(const TcConfig& c, int found, int32_t* out) {
   out[2] = c.kc;
   out[3] = c.groups;
   out[4] = found;
-  out[5] = c.wide;
+  out[5] = c.wide ? (c.pair ? 2 : 1) : 0;
 }
 
 int shg_autotune_project(int64_t m, int64_t n, int64_t k, const float* A, int64_t lda, int trans_a,
@@ -344,6 +344,19 @@ int shg_autotune_lookup(int64_t m, int64_t n, int64_t k, int trans_a, int varian
 
 int shg_autotune_clear(void) {
   tc_tune_clear();
+  return SHG_OK;
+}
+
+int shg_autotune_export(int32_t* records, int32_t capacity, int32_t* count) {
+  if (capacity < 0 || !count || (capacity > 0 && !records)) return SHG_ERR_INVALID_ARG;
+  *count = tc_tune_export(records, capacity);
+  return SHG_OK;
+}
+
+int shg_autotune_import(const int32_t* records, int32_t count, int32_t* added) {
+  const int n = tc_tune_import(records, count);
+  if (n < 0) return SHG_ERR_INVALID_ARG;
+  if (added) *added = n;
   return SHG_OK;
 }
 

@@ -823,6 +823,8 @@ __global__ void __launch_bounds__(kWideThreads, 1)
   }
 }
 
+#include "shgemm_pair.cuh"
+
 // ---------------------------------------------------------------- host side
 template <int AMAJ, int BMODE, int PIECES>
 int launch(const CUtensorMap& ta, const CUtensorMap& tb, const CUtensorMap& tb2, const TcArgs& a, int grid,
@@ -920,6 +922,7 @@ TcConfig default_config() {
   c.kc = std::max(2, std::min(env_int("SHG_DRAIN_KBLOCKS", 4), 8));
   c.groups = env_int("SHG_NGROUPS", 1) != 0 ? 1 : 0;
   c.wide = env_int("SHG_WIDE", 1) != 0 ? 1 : 0;
+  c.pair = env_int("SHG_PAIR", 0) != 0 ? 1 : 0;
   return c;
 }
 
@@ -949,6 +952,53 @@ void tc_tune_clear() {
 
 unsigned long long tc_tune_generation() { return g_tune_gen.load(); }
 
+int tc_tune_export(int32_t* rec, int cap) {
+  std::lock_guard<std::mutex> lock(g_tune_mu);
+  const int n = static_cast<int>(g_tune.size());
+  for (int i = 0; i < n && i < cap && rec; ++i) {
+    const TuneKey& k = g_tune[i].first;
+    const TcConfig& c = g_tune[i].second;
+    const int32_t v[kTuneRecord] = {k.amaj, k.bmode, k.pieces, k.nt, k.n_tiles, k.mlog, k.klog, k.pmulti,
+                                    c.sa, c.sb, c.kc, c.groups, c.wide, c.pair};
+    for (int j = 0; j < kTuneRecord; ++j) rec[i * kTuneRecord + j] = v[j];
+  }
+  return n;
+}
+
+int tc_tune_import(const int32_t* rec, int count) {
+  if (count < 0 || (count > 0 && !rec)) return -1;
+  // every record is checked before any is added
+  for (int i = 0; i < count; ++i) {
+    const int32_t* v = rec + i * kTuneRecord;
+    const bool ok = (v[0] == A_KMAJ || v[0] == A_MNMAJ) && v[1] >= 0 && v[1] <= B_SPLIT_PRE && v[2] >= 2 &&
+                    v[2] <= 3 && v[3] >= 64 && v[3] <= 256 && v[3] % 64 == 0 && v[4] >= 1 && v[5] >= 0 &&
+                    v[5] < 63 && v[6] >= 0 && v[6] < 63 && (v[7] == 0 || v[7] == 1) && v[8] >= 2 && v[8] <= 6 &&
+                    v[9] >= 2 && v[9] <= 6 && v[10] >= 2 && v[10] <= 8 && (v[11] == 0 || v[11] == 1) &&
+                    (v[12] == 0 || v[12] == 1) && (v[13] == 0 || v[13] == 1);
+    if (!ok) return -1;
+  }
+  std::lock_guard<std::mutex> lock(g_tune_mu);
+  int added = 0;
+  for (int i = 0; i < count; ++i) {
+    const int32_t* v = rec + i * kTuneRecord;
+    TuneKey k{v[0], v[1], v[2], v[3], v[4], v[5], v[6], v[7]};
+    bool have = false;
+    for (const auto& e : g_tune) have = have || (e.first == k);
+    if (have) continue;
+    TcConfig c;
+    c.sa = v[8];
+    c.sb = v[9];
+    c.kc = v[10];
+    c.groups = v[11];
+    c.wide = v[12];
+    c.pair = v[13];
+    g_tune.emplace_back(k, c);
+    ++added;
+  }
+  if (added) ++g_tune_gen;
+  return added;
+}
+
 int tc_autotune(int amaj, int bmode, int pieces, int64_t M, int64_t N, int64_t S_k, int64_t P, const float* A,
                 int64_t lda, int64_t p_stride, const void* B, int64_t ldb, float* C, int64_t ldc,
                 int32_t* d_flags, cudaStream_t stream, int reps, TcConfig* best, int* found_before) {
@@ -977,6 +1027,7 @@ int tc_autotune(int amaj, int bmode, int pieces, int64_t M, int64_t N, int64_t S
           c.kc = kc;
           c.groups = g;
           c.wide = 0;
+          c.pair = 0;
           cand.push_back(c);
         }
   {
@@ -993,6 +1044,21 @@ int tc_autotune(int amaj, int bmode, int pieces, int64_t M, int64_t N, int64_t S
             c.kc = kc;
             c.groups = 1;
             c.wide = 1;
+            c.pair = 0;
+            cand.push_back(c);
+          }
+    // the CTA-pair kernel: Omega stages are half as large
+    if (use_wide(amaj, bmode, pieces, N, probe) && env_int("SHG_TUNE_PAIR", 1) != 0)
+      for (int sa : {3, 4, 5})
+        for (int sb : {3, 4, 6})
+          for (int kc : {4, 8}) {
+            TcConfig c;
+            c.sa = sa;
+            c.sb = sb;
+            c.kc = kc;
+            c.groups = 1;
+            c.wide = 1;
+            c.pair = 1;
             cand.push_back(c);
           }
   }
@@ -1067,6 +1133,7 @@ int tc_gemm_impl(int amaj, int bmode, int pieces, int64_t M, int64_t N, int64_t 
   if (force) cfg = *force;
   else tuned = tc_tuned(amaj, bmode, pieces, M, N, K, P, &cfg);
   const bool wide = use_wide(amaj, bmode, pieces, N, cfg);
+  bool pair = wide && cfg.pair != 0;
   // the wide kernel's single-buffered hi accumulator: drain every 8 K
   // blocks unless a tuned or forced configuration says otherwise
   if (wide && !force && !tuned && std::getenv("SHG_DRAIN_KBLOCKS") == nullptr) cfg.kc = 8;
@@ -1078,8 +1145,25 @@ int tc_gemm_impl(int amaj, int bmode, int pieces, int64_t M, int64_t N, int64_t 
     a.n_tiles = static_cast<int>((N + kWideMaxN - 1) / kWideMaxN);
     nt = static_cast<int>(((N + a.n_tiles - 1) / a.n_tiles + 63) / 64 * 64);
   }
+  // CTA pairs: 256 x 256 tiles (columns beyond N are computed from
+  // zero-filled Omega columns and not stored); one wave of resident pairs
+  int pair_slots = 0;
+  if (pair) {
+    // the ring depths and shared memory that the fitting below arrives at
+    int sa = std::max(2, std::min(cfg.sa, 6)), sb = std::max(2, std::min(cfg.sb, 6));
+    while (sa * kABytes + sb * kPairBBytes + 2048 > kMaxSmem) {
+      if (sb > 2 && sb >= sa) --sb;
+      else --sa;
+    }
+    pair_slots = pair_capacity(1024 + static_cast<size_t>(sa) * kABytes + static_cast<size_t>(sb) * kPairBBytes + 1024);
+    if (pair_slots < 1) pair = false;
+  }
+  if (pair) {
+    a.n_tiles = static_cast<int>((N + kPairN - 1) / kPairN);
+    nt = kPairN;
+  }
   a.n_tile = nt;
-  a.m_tiles = static_cast<int>((M + kBM - 1) / kBM);
+  a.m_tiles = static_cast<int>((M + (pair ? kPairBM : kBM) - 1) / (pair ? kPairBM : kBM));
   a.kb_per_p = static_cast<int>((S_k + kBK - 1) / kBK);
   a.kblocks = a.kb_per_p * static_cast<int>(P);
   a.S_k = static_cast<int>(S_k);
@@ -1102,6 +1186,7 @@ int tc_gemm_impl(int amaj, int bmode, int pieces, int64_t M, int64_t N, int64_t 
   }
   a.b_bytes = (bmode == B_SPLIT || bmode == B_SPLIT_PRE) ? static_cast<uint32_t>(nt) * 256u
                                                         : static_cast<uint32_t>(nt) * 128u;
+  if (pair) a.b_bytes = kPairBBytes;
   const uint32_t bar_bytes = 1024;
   a.sa = std::max(2, std::min(cfg.sa, 6));
   a.sb = std::max(2, std::min(cfg.sb, 6));
@@ -1161,7 +1246,15 @@ int tc_gemm_impl(int amaj, int bmode, int pieces, int64_t M, int64_t N, int64_t 
   const int grid = static_cast<int>(std::min<long long>(ctas_per_group, tile_ranges ? per_group / a.kblocks
                                                                                          : per_group)) *
                    a.groups;
-  const int per_cta = grid / a.groups;
+  int launch_grid = grid;
+  int per_cta = grid / a.groups;
+  if (pair) {
+    // the stream-K grid counts pairs, two CTAs each
+    const long long pairs = std::min<long long>(pair_slots, std::max(1, sms / 2));
+    const long long pairs_per_group = std::max<long long>(1, pairs / a.groups);
+    per_cta = static_cast<int>(std::min<long long>(pairs_per_group, tile_ranges ? per_group / a.kblocks : per_group));
+    launch_grid = 2 * per_cta * a.groups;
+  }
   bool split = false;
   for (int c = 1; c < per_cta && !split && !tile_ranges; ++c)
     if ((static_cast<long long>(c) * per_group / per_cta) % a.kblocks != 0) split = true;
@@ -1170,6 +1263,7 @@ int tc_gemm_impl(int amaj, int bmode, int pieces, int64_t M, int64_t N, int64_t 
       return SHG_ERR_CUDA;
   }
 
+  if (pair) return launch_pair(ta, tb, a, launch_grid, smem, stream);
   if (wide) return launch_wide(ta, tb, a, grid, smem, stream);
   if (amaj == A_KMAJ) {
     if (bmode == B_F16) return launch<A_KMAJ, B_F16, 2>(ta, tb, tb2, a, grid, smem, stream);

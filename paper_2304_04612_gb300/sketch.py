@@ -74,3 +74,66 @@ def choose_sketch(A: torch.Tensor, omega_learned: torch.Tensor, seed: int, probe
     el, eg = float(est_l[0].item()), float(est_g[0].item())
     use_learned = el <= eg
     return (om_l if use_learned else om_g), el, eg, use_learned
+
+
+# ---------------------------------------------------------------- checkpoint
+def save_sketch(path: str, omega: torch.Tensor, optimizer: torch.optim.Optimizer | None = None, step: int = 0) -> None:
+    """Checkpoint of a learned sketch as an .npz file (plain arrays, no pickled
+    objects): the FP32 master weights, their FP16 rounding (the sketch the
+    projection uses), the training step, and, when ``optimizer`` is an Adam
+    optimizer holding ``omega``, its moment estimates and step count so that
+    training resumes where it stopped.  Written to a temporary file and
+    renamed, so an interrupted save leaves the previous checkpoint intact."""
+    import numpy as np
+    import os
+    w = omega.detach().to("cpu", torch.float32).contiguous()
+    arrays = {"format": np.array("shg-sketch-1"), "omega_fp32": w.numpy(),
+              "omega_fp16": w.half().view(torch.int16).numpy(), "step": np.array(int(step), dtype=np.int64)}
+    if optimizer is not None:
+        st = optimizer.state.get(omega, {})
+        if st:
+            group = next(g for g in optimizer.param_groups if any(p is omega for p in g["params"]))
+            arrays["adam_exp_avg"] = st["exp_avg"].detach().cpu().numpy()
+            arrays["adam_exp_avg_sq"] = st["exp_avg_sq"].detach().cpu().numpy()
+            arrays["adam_step"] = np.array(float(st["step"]), dtype=np.float64)
+            arrays["adam_hyper"] = np.array([group["lr"], group["betas"][0], group["betas"][1], group["eps"],
+                                             group["weight_decay"]], dtype=np.float64)
+    tmp = path + ".tmp.npz"
+    np.savez(tmp, **arrays)
+    os.replace(tmp, path)
+
+
+def load_sketch(path: str, device="cpu"):
+    """Read a checkpoint written by save_sketch.  Returns (omega, step, adam):
+    omega the FP32 master weights on ``device`` as a leaf tensor that requires
+    a gradient, step the saved training step, adam the saved optimizer state
+    (a dict) or None.  The stored FP16 copy is checked against the rounding of
+    the master weights."""
+    import numpy as np
+    with np.load(path, allow_pickle=False) as z:
+        if str(z["format"]) != "shg-sketch-1":
+            raise ValueError(f"{path}: not a sketch checkpoint")
+        w = torch.from_numpy(z["omega_fp32"].copy())
+        if not torch.equal(w.half().view(torch.int16), torch.from_numpy(z["omega_fp16"].copy())):
+            raise ValueError(f"{path}: the FP16 copy does not match the FP32 master weights")
+        step = int(z["step"])
+        adam = None
+        if "adam_exp_avg" in z.files:
+            adam = {"exp_avg": torch.from_numpy(z["adam_exp_avg"].copy()),
+                    "exp_avg_sq": torch.from_numpy(z["adam_exp_avg_sq"].copy()),
+                    "step": float(z["adam_step"]), "hyper": [float(x) for x in z["adam_hyper"]]}
+    omega = w.to(device).requires_grad_(True)
+    return omega, step, adam
+
+
+def restore_adam(optimizer: torch.optim.Adam, omega: torch.Tensor, adam: dict | None) -> None:
+    """Put the moment estimates and step count of a checkpoint back into an
+    Adam optimizer built over ``omega`` (the tensor load_sketch returned)."""
+    if adam is None:
+        return
+    group = next(g for g in optimizer.param_groups if any(p is omega for p in g["params"]))
+    lr, b1, b2, eps, wd = adam["hyper"]
+    group.update(lr=lr, betas=(b1, b2), eps=eps, weight_decay=wd)
+    optimizer.state[omega] = {"step": torch.tensor(adam["step"], dtype=torch.float32),
+                              "exp_avg": adam["exp_avg"].to(omega.device),
+                              "exp_avg_sq": adam["exp_avg_sq"].to(omega.device)}

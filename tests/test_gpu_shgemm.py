@@ -79,13 +79,15 @@ def test_shgemm_f16_parity(shg, m, n, k, trans):
 
 @pytest.mark.parametrize("m,n,k", [(256, 512, 200), (1000, 300, 256), (200, 640, 512), (77, 1536, 144),
                                    (513, 2048, 160), (300, 1000, 320)])
-@pytest.mark.parametrize("wide", ["1", "0"])
-def test_shgemm_f16_tile_widths(shg, monkeypatch, m, n, k, wide):
-    """k > 128 runs on output tiles of up to 256 columns whose A operand is
-    split in shared memory (the default) or on 128-column tiles split into
-    tensor memory (SHG_WIDE=0); both against the exact product with the
-    same tolerances as above."""
-    monkeypatch.setenv("SHG_WIDE", wide)
+@pytest.mark.parametrize("tiles", ["pair", "wide", "narrow"])
+def test_shgemm_f16_tile_widths(shg, monkeypatch, m, n, k, tiles):
+    """k > 128 runs on 256 x 256 output tiles computed by pairs of CTAs
+    (SHG_PAIR=1), on 128 x 256 tiles per CTA whose A operand is split in
+    shared memory (SHG_PAIR=0), or on 128-column tiles split into tensor
+    memory (SHG_WIDE=0); each against the exact product with the same
+    tolerances as above."""
+    monkeypatch.setenv("SHG_WIDE", "0" if tiles == "narrow" else "1")
+    monkeypatch.setenv("SHG_PAIR", "1" if tiles == "pair" else "0")
     A = uniform(m, n, seed=12)
     Om = omega_f16(n, k, seed=13)
     Y = shg.shgemm_project(padded_f32(A), padded_omega(Om, (k + 7) // 8 * 8), "f16").cpu().numpy()
@@ -230,3 +232,23 @@ def test_deterministic_projection_is_bitwise_reproducible(shg, variant, k):
     ref = OS.project_exact(A_h, Om_h)
     err = np.linalg.norm(ys[0].cpu().numpy() - ref) / np.linalg.norm(ref)
     assert err <= 1e-5, err
+
+
+@pytest.mark.parametrize("tiles", ["pair", "wide"])
+def test_deterministic_wide_tiles(shg, monkeypatch, tiles):
+    """SHG_DETERMINISTIC on the two kernels of k > 128 (256 x 256 tiles on CTA
+    pairs, 128 x 256 tiles per CTA): whole output tiles per CTA range, the
+    same bits on every run, within the projection tolerance."""
+    monkeypatch.setenv("SHG_PAIR", "1" if tiles == "pair" else "0")
+    m, n, k = 3000, 4096, 384
+    A_h = uniform(m, n, seed=43)
+    Om_h = omega_f16(n, k, seed=44)
+    A, Om = dev(A_h), dev(Om_h)
+    ys = [shg.shgemm_project(A, Om, "f16", deterministic=True) for _ in range(3)]
+    for y in ys[1:]:
+        assert torch.equal(y, ys[0])
+    ref = OS.project_exact(A_h, Om_h)
+    err = OS.rel_fro_error(ys[0].cpu().numpy(), ref)
+    assert err <= 1e-5, err
+    Yd = shg.shgemm_project(A, Om, "f16").cpu().numpy()   # the stream-K schedule, same tolerance
+    assert OS.rel_fro_error(Yd, ref) <= 1e-5
