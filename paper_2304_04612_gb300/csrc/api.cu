@@ -5,6 +5,8 @@
 #include <cstring>
 #include <mutex>
 
+#include <nvtx3/nvToolsExt.h>
+
 #include "internal.h"
 #include "linalg.h"
 
@@ -169,11 +171,18 @@ int mode_project(int i, const int64_t* d, int64_t J, const float* X, const uint1
 
 __global__ void fill_f64_kernel(double* p, double v) { *p = v; }
 
-// CUDA events of a report: one per phase boundary, created and destroyed
-// by the call that fills the report.
+// Phases of a randomized SVD call (Algorithm 1 and the power scheme), as
+// NVTX ranges on the host thread (visible to a profiler attached to the
+// process; without one an NVTX call costs a pointer test) and, when a
+// report is asked for, as CUDA events at each boundary, created and
+// destroyed by the call that fills the report.
+constexpr const char* kPhaseNames[SHG_NUM_PHASES] = {
+    "shg_rsvd: Omega", "shg_rsvd: Y = A Omega", "shg_rsvd: Q = orth(Y)", "shg_rsvd: power scheme",
+    "shg_rsvd: B = Q^T A", "shg_rsvd: small SVD of B", "shg_rsvd: U = Q U', V", "shg_rsvd: residual estimate"};
 struct PhaseEvents {
   cudaEvent_t e[SHG_NUM_PHASES + 1] = {};
   bool on = false;
+  bool range_open = false;
   int init() {
     on = true;
     for (auto& x : e)
@@ -181,10 +190,14 @@ struct PhaseEvents {
     return SHG_OK;
   }
   int mark(int i, cudaStream_t st) {
+    if (range_open) nvtxRangePop();
+    range_open = i < SHG_NUM_PHASES;
+    if (range_open) nvtxRangePushA(kPhaseNames[i]);
     if (!on) return SHG_OK;
     return cudaEventRecord(e[i], st) == cudaSuccess ? SHG_OK : SHG_ERR_CUDA;
   }
   ~PhaseEvents() {
+    if (range_open) nvtxRangePop();
     for (auto& x : e)
       if (x) cudaEventDestroy(x);
   }
