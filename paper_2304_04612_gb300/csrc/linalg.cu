@@ -1248,6 +1248,29 @@ int chol_inv(int64_t k, const double* G, float* Rinv, double* scratch, int32_t* 
   return cuda_status(cudaGetLastError());
 }
 
+// V from the rotation log: RB rows of V per CTA, RB the smallest power of
+// two that keeps the grid within one CTA per SM (a round's latency grows
+// with the rows each slot thread rotates, and the rows are independent).
+int apply_v_log(int64_t k, const float2* log, const int* rounds, float* V, cudaStream_t st) {
+  const int64_t kp = k + (k & 1);
+  const int h = static_cast<int>(kp / 2);
+  const int threads = (h + 31) / 32 * 32;
+  const int sms = sm_count();
+  if (sms <= 0) return SHG_ERR_CUDA;
+  int rb = 1;
+  while (rb < 8 && (k + rb - 1) / rb > sms) rb *= 2;
+  const unsigned grid = static_cast<unsigned>((k + rb - 1) / rb);
+  const size_t smem = static_cast<size_t>(rb) * kp * sizeof(float);
+  const int kk = static_cast<int>(k);
+  switch (rb) {
+    case 1: jac_apply_v_kernel<1><<<grid, threads, smem, st>>>(kk, log, rounds, V); break;
+    case 2: jac_apply_v_kernel<2><<<grid, threads, smem, st>>>(kk, log, rounds, V); break;
+    case 4: jac_apply_v_kernel<4><<<grid, threads, smem, st>>>(kk, log, rounds, V); break;
+    default: jac_apply_v_kernel<8><<<grid, threads, smem, st>>>(kk, log, rounds, V); break;
+  }
+  return cuda_status(cudaGetLastError());
+}
+
 int jacobi_eig(int64_t k, const double* G, float* V, float* scratch, void* eig, cudaStream_t st) {
   if (k > 1024) return SHG_ERR_UNSUPPORTED;
   const int64_t kp = k + (k & 1);
@@ -1272,11 +1295,7 @@ int jacobi_eig(int64_t k, const double* G, float* V, float* scratch, void* eig, 
       return SHG_ERR_CUDA;
     jacobi_kernel<<<1, groups * 128, smem, st>>>(static_cast<int>(k), G, log, rounds, TB);
     if (cudaGetLastError() != cudaSuccess) return SHG_ERR_CUDA;
-    // V: eight rows per CTA, one thread per slot
-    constexpr int rb = 8;
-    const int threads = (h + 31) / 32 * 32;
-    jac_apply_v_kernel<rb><<<static_cast<unsigned>((k + rb - 1) / rb), threads, rb * kp * sizeof(float), st>>>(
-        static_cast<int>(k), log, rounds, V);
+    return apply_v_log(k, log, rounds, V, st);
   } else {
     // too large for one SM: the whole grid works on every round (cooperative
     // launch); h rotation threads plus the block threads
@@ -1306,12 +1325,7 @@ int jacobi_eig(int64_t k, const double* G, float* V, float* scratch, void* eig, 
     if (cudaLaunchCooperativeKernel(reinterpret_cast<const void*>(jacobi_grid_kernel), dim3(static_cast<unsigned>(want)),
                                     dim3(kJacGridThreads), argv, 0, st) != cudaSuccess)
       return SHG_ERR_CUDA;
-    if (defer) {
-      constexpr int rb = 8;
-      const int threads = (h + 31) / 32 * 32;
-      jac_apply_v_kernel<rb><<<static_cast<unsigned>((k + rb - 1) / rb), threads, rb * kp * sizeof(float), st>>>(
-          static_cast<int>(k), log, rounds, V);
-    }
+    if (defer) return apply_v_log(k, log, rounds, V, st);
   }
   return cuda_status(cudaGetLastError());
 }
