@@ -1089,12 +1089,17 @@ __device__ __forceinline__ void sort_select_body(int k, int p, const double* __r
                                                  float* __restrict__ S, float* __restrict__ Up, float* __restrict__ Ups) {
   extern __shared__ double sel[];          // [p] 1 / ||v||, [p] 1 / (||v|| sigma)
   int* perm = reinterpret_cast<int*>(sel + 2 * p);  // [p] column of rank r
+  // Ranks by a strict total order (a NaN counts as -inf, ties go by index),
+  // so that they are a permutation of 0 .. k - 1 and every rank below p is
+  // filled, whatever the values (a non-finite Y gives NaN eigenvalues).
+  auto key = [](double x) { return x == x ? x : -INFINITY; };
   for (int i = threadIdx.x; i < k; i += blockDim.x) {
     const double li = lam[i];
+    const double ki = key(li);
     int r = 0;
     for (int j = 0; j < k; ++j) {
-      const double lj = lam[j];
-      r += (lj > li) || (lj == li && j < i);
+      const double kj = key(lam[j]);
+      r += (kj > ki) || (kj == ki && j < i);
     }
     if (r < p) {
       const double sg = sqrt(fmax(li, 0.0));

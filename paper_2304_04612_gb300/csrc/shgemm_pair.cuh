@@ -371,6 +371,7 @@ std::mutex g_pair_mu;
 bool pair_set_smem(int dev, size_t smem) {
   static size_t configured[64] = {};
   if (configured[dev] == smem) return true;
+  if (!regs_at_launch_ok(tc_pair_kernel)) return false;
   const int carve = static_cast<int>((smem * 100 + kMaxSmem - 1) / kMaxSmem);
   if (cudaFuncSetAttribute(tc_pair_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, static_cast<int>(smem)) !=
           cudaSuccess ||

@@ -1,24 +1,28 @@
 // SHGEMM on tcgen05 tensor cores (Sec. 4.1, Eqs. shgemm-1..3), its BF16
 // analogue, and the TCEC split product (Eq. tcec-5) for two FP32 operands.
 //
-// One CTA = 11 warps, one CTA per SM, persistent over a contiguous range of
+// One CTA = 16 warps, one CTA per SM, persistent over a contiguous range of
 // work units (stream-K).  A unit is one (N tile <= 128, 128-row M tile,
 // 64-deep K block).
 //   warp 0      TMA producer of A: FP32 tile (128 x 64, 32 KB) into a shared-
 //               memory staging ring, running ahead independently of B
-//   warp 10     TMA producer of B: 16-bit Omega tile (or the FP32 B tile of
+//   warp 2      TMA producer of B: 16-bit Omega tile (or the FP32 B tile of
 //               the TCEC product) into a second ring, freed by the MMAs
 //   warp 1      TMEM owner + single-thread tcgen05.mma issuer; the A operand
 //               is read from tensor memory, B from shared memory
-//   warps 2..5  split warps: thread r of the CTA's 128 reads row r of the
-//               staged FP32 tile, splits hi = RN_f16(a),
-//               lo = RN_f16((a - hi) * 2^11) (or BF16 pieces) and writes
-//               the pieces into TMEM lane r with tcgen05.st (the A operand)
-//               (an FP16 overflow, |a| >= 65520, makes hi infinite; the
-//               epilogue sees it as a non-finite Y and raises the range flag)
-//   warps 6..9  epilogue: drains the hi product every `kc` K blocks from
+//   warps 4..7, 8..11
+//               two groups of split warps taking alternate units: thread r
+//               of a group reads row r of the staged FP32 tile, splits
+//               hi = RN_f16(a), lo = RN_f16((a - hi) * 2^11) (or BF16
+//               pieces) and writes the pieces into TMEM lane r with
+//               tcgen05.st (the A operand) (an FP16 overflow, |a| >= 65520,
+//               makes hi infinite; the epilogue sees it as a non-finite Y
+//               and raises the range flag)
+//   warps 12..15 epilogue: drains the hi product every `kc` K blocks from
 //               TMEM into an FP32 running sum held in registers (RN adds);
 //               at the end of a segment Y = sum + 2^-11 acc_lo
+// Registers per warpgroup (setmaxnreg): 56 for warps 0..3, 128 for the two
+// split groups, 200 for the epilogue.
 //
 // Rounding: the tensor core's accumulation is not round-to-nearest (Sec.
 // 4.3 describes RZ on A100; TMEM accumulation over a long K range loses
@@ -54,10 +58,10 @@ namespace shg {
 
 namespace {
 
-constexpr int kThreads = 352;
-constexpr int kFirstSplitWarp = 2;
-constexpr int kFirstEpiWarp = 6;
-constexpr int kBProducerWarp = 10;
+constexpr int kThreads = 512;
+constexpr int kFirstSplitWarp = 4;  // two split groups: warps 4..7 and 8..11
+constexpr int kFirstEpiWarp = 12;
+constexpr int kBProducerWarp = 2;
 // In-place split of the TMA-staged FP32 B tile of the TCEC product: 64 rows
 // of G groups of 8 floats as G/4 boxes of 64 rows x 128 B (swizzled); hi / lo
 // are written as G/8 blocks of 64 rows x 128 B at offsets 0 and 64*G*16 (the
@@ -183,6 +187,13 @@ __global__ void __launch_bounds__(kThreads, 1)
   const uint64_t lim = args.wait_ns;
   long long issued_a = 0, issued_b = 0;
 
+  // Registers are rebalanced per warpgroup (setmaxnreg): 128 at launch
+  // (512 x 128 = 65536), then 56 for the producers and the MMA thread, 128
+  // (unchanged) for each split group and 200 for the epilogue, which again
+  // sum to 128 x 56 + 256 x 128 + 128 x 200 = 65536.
+  const int wg = warp >> 2;
+  if (wg == 0) {
+  regs_dec_56();
   if (warp == 0) {
     // ---------------------------------------------------------- A producer
     // The A stream runs ahead on its own: loaded TMA latency is several
@@ -305,14 +316,24 @@ __global__ void __launch_bounds__(kThreads, 1)
       }
     }
     __syncwarp();
-  } else if (warp < kFirstEpiWarp) {
+  }
+  } else if (wg <= 2) {
     // ---------------------------------------------------------- split warps
+    // Two groups of four warps take alternate units (group g the units
+    // u0 + g, u0 + g + 2, ...), so that one group's waits and stores
+    // overlap the other's loads and arithmetic.
+    const int g = wg - 1;
     const int q = warp & 3;
     const int r = 32 * q + lane;  // tile row == TMEM lane of this thread
     const uint32_t lane_off = static_cast<uint32_t>(32 * q) << 16;
     float vmax = 0.0f;
     Ring ra, rb, rt;
-    for (long long u = u0; u < u1; ++u, ra.next(SA), rb.next(SB), rt.next(ST)) {
+    if (g == 1) {
+      ra.next(SA);
+      rb.next(SB);
+      rt.next(ST);
+    }
+    for (long long u = u0 + g; u < u1; u += 2) {
       const int sa = ra.s, sb = rb.s, st = rt.s;
       const uint32_t pa = ra.ph, pb = rb.ph, pt = rt.ph;
       if (kInplaceB) {
@@ -320,7 +341,7 @@ __global__ void __launch_bounds__(kThreads, 1)
           *abort_flag = 1;
           break;
         }
-        split_inplace_b(b_ring + sb * args.b_bytes, N / 8, threadIdx.x - kFirstSplitWarp * 32, vmax);
+        split_inplace_b(b_ring + sb * args.b_bytes, N / 8, threadIdx.x - (kFirstSplitWarp + 4 * g) * 32, vmax);
         fence_proxy_async_smem();
         __syncwarp();
         if (lane == 0) mbar_arrive(bar_bready + 8 * sb);
@@ -343,9 +364,15 @@ __global__ void __launch_bounds__(kThreads, 1)
       tc_fence_before();
       __syncwarp();
       if (lane == 0) mbar_arrive(bar_tfull + 8 * st);
+      for (int t = 0; t < 2; ++t) {
+        ra.next(SA);
+        rb.next(SB);
+        rt.next(ST);
+      }
     }
     if (kInplaceB && vmax >= 65520.0f) atomicOr(args.flags, SHG_FLAG_RANGE);  // the FP32 B operand
   } else {
+    regs_inc_200();
     // ---------------------------------------------------------- epilogue
     const int q = warp & 3;  // TMEM lane quadrant this warp may access
     const uint32_t lane_off = static_cast<uint32_t>(32 * q) << 16;
@@ -837,6 +864,7 @@ int launch(const CUtensorMap& ta, const CUtensorMap& tb, const CUtensorMap& tb2,
   int dev = 0;
   if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 64) return SHG_ERR_CUDA;
   if (configured[dev] != smem) {
+    if (!regs_at_launch_ok(k)) return SHG_ERR_UNSUPPORTED;
     const int carve = static_cast<int>((smem * 100 + kMaxSmem - 1) / kMaxSmem);
     if (cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, static_cast<int>(smem)) !=
             cudaSuccess ||
@@ -856,6 +884,7 @@ int launch_wide(const CUtensorMap& ta, const CUtensorMap& tb, const TcArgs& a, i
   int dev = 0;
   if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 64) return SHG_ERR_CUDA;
   if (configured[dev] != smem) {
+    if (!regs_at_launch_ok(tc_wide_kernel)) return SHG_ERR_UNSUPPORTED;
     const int carve = static_cast<int>((smem * 100 + kMaxSmem - 1) / kMaxSmem);
     if (cudaFuncSetAttribute(tc_wide_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, static_cast<int>(smem)) !=
             cudaSuccess ||

@@ -208,9 +208,20 @@ __device__ __forceinline__ void cta_range(const TcArgs& a, long long& u0, long l
   u1 = g * per + static_cast<long long>(i + 1) * per / C;
 }
 
+// The per-warpgroup register budgets (setmaxnreg) of the tensor-core kernels
+// add up to 512 threads x 128 registers: a kernel that setmaxnreg.inc's a
+// warpgroup is launched only when it was built with exactly 128 registers
+// per thread (otherwise the increase could never be granted).
+template <typename Kernel>
+bool regs_at_launch_ok(Kernel kernel) {
+  cudaFuncAttributes fa;
+  return cudaFuncGetAttributes(&fa, kernel) == cudaSuccess && fa.numRegs == 128;
+}
+
 __device__ __forceinline__ void regs_dec_56() { asm volatile("setmaxnreg.dec.sync.aligned.u32 56;\n" ::: "memory"); }
 __device__ __forceinline__ void regs_dec_120() { asm volatile("setmaxnreg.dec.sync.aligned.u32 120;\n" ::: "memory"); }
 __device__ __forceinline__ void regs_inc_168() { asm volatile("setmaxnreg.inc.sync.aligned.u32 168;\n" ::: "memory"); }
+__device__ __forceinline__ void regs_inc_200() { asm volatile("setmaxnreg.inc.sync.aligned.u32 200;\n" ::: "memory"); }
 
 // ---------------------------------------------------------------- host side
 using EncodeTiled = CUresult (*)(CUtensorMap*, CUtensorMapDataType, cuuint32_t, void*, const cuuint64_t*,
