@@ -13,17 +13,20 @@
 //               128B swizzle): the staged tile is already a K-major TF32
 //               operand layout (128-byte rows of 32 values)
 //   warp 1      TMEM owner and single-thread tcgen05.mma kind::tf32 issuer
-//               (A and B from shared memory, M = 128, N = N tile, K = 8)
+//               (hi A and B from shared memory, lo A from tensor memory,
+//               M = 128, N = N tile, K = 8)
 //   warp 2      TMA producer of the FP16 Omega tile (64 x N, MN-major)
 //   warps 4..7  split: thread r rounds row r of the staged tile in place to
-//               hi and writes lo to the stage's second half (same layout)
+//               hi and writes lo to tensor memory lane r (the lo product
+//               reads its A operand from there), so an A stage is the 32 KB
+//               FP32 tile alone and four of them fit beside the Omega ring
 //   warps 8..11 widen the FP16 Omega tile to FP32 and transpose it into the
 //               K-major operand layout (TF32 operands are read K-major)
 //   warps 12..15 epilogue: the hi product is drained from a double-buffered
 //               TMEM accumulator every kc K blocks and added RN into an FP32
 //               register sum (Sec. 4.3); at a segment's end
 //               Y = sum + 2^-11 (lo accumulator)
-// Registers per warpgroup (setmaxnreg): 56, 120, 56, 232 (128 at launch).
+// Registers per warpgroup (setmaxnreg): 56, 128, 56, 232 (128 at launch).
 // Partial segments of the stream-K split add into a pre-zeroed Y with FP32
 // atomics.  Every wait is bounded; on a timeout the CTA raises
 // SHG_FLAG_TIMEOUT, lets its copies and MMAs finish, frees TMEM and returns.
@@ -38,10 +41,9 @@ namespace {
 
 constexpr int kTfThreads = 512;
 constexpr int kTfMaxN = 128;
-constexpr uint32_t kTfABytes = 65536;  // FP32 / hi tile (32 KB) + lo tile (32 KB)
+constexpr uint32_t kTfABytes = 32768;  // FP32 tile, rounded to hi in place (lo goes to tensor memory)
 
 __device__ __forceinline__ void regs_dec_56_tf() { asm volatile("setmaxnreg.dec.sync.aligned.u32 56;\n" ::: "memory"); }
-__device__ __forceinline__ void regs_dec_120_tf() { asm volatile("setmaxnreg.dec.sync.aligned.u32 120;\n" ::: "memory"); }
 __device__ __forceinline__ void regs_inc_232_tf() { asm volatile("setmaxnreg.inc.sync.aligned.u32 232;\n" ::: "memory"); }
 
 // D[tmem] (+)= A[smem] * B[smem], kind::tf32 (32-bit operands whose low 13
@@ -56,38 +58,56 @@ __device__ __forceinline__ void tc_mma_tf32(uint32_t d_tmem, uint64_t adesc, uin
       : "memory");
 }
 
-// Round to nearest even at 10 explicit mantissa bits (TF32), as an FP32 bit
-// pattern with the low 13 bits clear; infinities and NaNs pass unchanged, a
-// value that rounds past the largest finite one becomes infinite.
+// Round to nearest even at 10 explicit mantissa bits (TF32) by the
+// conversion instruction, as an FP32 bit pattern with the low 13 bits
+// clear; infinities and NaNs pass unchanged, a value that rounds past the
+// largest finite one becomes infinite.
 __device__ __forceinline__ float rn_tf32(float x) {
-  uint32_t u = __float_as_uint(x);
-  if ((u & 0x7f800000u) == 0x7f800000u) return x;
-  u += 0xfffu + ((u >> 13) & 1u);
+  uint32_t u;
+  asm("cvt.rn.tf32.f32 %0, %1;" : "=r"(u) : "f"(x));
   return __uint_as_float(u & 0xffffe000u);
 }
 
-// Row r of a staged K-major FP32 tile: hi written in place, lo at +32 KB in
-// the same layout (logical 16-byte chunk c of box b, row r, at physical
-// chunk c ^ (r mod 8)).  Every byte a thread writes is one it read itself.
-__device__ __forceinline__ void split_row_tf32(uint8_t* tile, int r) {
+// Row r of a staged K-major FP32 tile: hi written in place (logical 16-byte
+// chunk c of box b, row r, at physical chunk c ^ (r mod 8); every byte a
+// thread writes is one it read itself), lo to tensor memory lane r, K value
+// j in column taddr + j (the A operand of the lo product, one 32-bit value
+// per column).
+__device__ __forceinline__ void split_row_tf32(uint8_t* tile, int r, uint32_t taddr) {
   float a[64];
   read_row<A_KMAJ>(tile, r, a);
   const int sw = r & 7;
 #pragma unroll
-  for (int g = 0; g < 8; ++g) {
-    float h[8], l[8];
+  for (int q = 0; q < 4; ++q) {  // K values 16 q .. 16 q + 15
+    uint32_t lo[16];
 #pragma unroll
-    for (int j = 0; j < 8; ++j) {
-      h[j] = rn_tf32(a[8 * g + j]);
-      l[j] = rn_tf32((a[8 * g + j] - h[j]) * 2048.0f);  // a - hi and the scaling are exact
+    for (int gg = 0; gg < 2; ++gg) {
+      const int g = 2 * q + gg;
+      float h[8];
+#pragma unroll
+      for (int j = 0; j < 8; ++j) {
+        h[j] = rn_tf32(a[8 * g + j]);
+        lo[8 * gg + j] = __float_as_uint(rn_tf32((a[8 * g + j] - h[j]) * 2048.0f));  // a - hi and the scaling are exact
+      }
+      uint8_t* bx = tile + (g >> 2) * 16384 + r * 128;
+      const int c0 = ((2 * (g & 3)) ^ sw) << 4, c1 = ((2 * (g & 3) + 1) ^ sw) << 4;
+      *reinterpret_cast<float4*>(bx + c0) = make_float4(h[0], h[1], h[2], h[3]);
+      *reinterpret_cast<float4*>(bx + c1) = make_float4(h[4], h[5], h[6], h[7]);
     }
-    uint8_t* bx = tile + (g >> 2) * 16384 + r * 128;
-    const int c0 = ((2 * (g & 3)) ^ sw) << 4, c1 = ((2 * (g & 3) + 1) ^ sw) << 4;
-    *reinterpret_cast<float4*>(bx + c0) = make_float4(h[0], h[1], h[2], h[3]);
-    *reinterpret_cast<float4*>(bx + c1) = make_float4(h[4], h[5], h[6], h[7]);
-    *reinterpret_cast<float4*>(bx + 32768 + c0) = make_float4(l[0], l[1], l[2], l[3]);
-    *reinterpret_cast<float4*>(bx + 32768 + c1) = make_float4(l[4], l[5], l[6], l[7]);
+    tc_st_32x32b_x16(taddr + 16 * q, lo);
   }
+}
+
+// D[tmem] (+)= A[tmem] * B[smem], kind::tf32: the A operand (M = 128 rows on
+// the 128 TMEM lanes, one 32-bit value per column along K) from tensor memory.
+__device__ __forceinline__ void tc_mma_tf32_tmem_a(uint32_t d_tmem, uint32_t a_tmem, uint64_t bdesc, uint32_t idesc,
+                                                   uint32_t accumulate) {
+  asm volatile(
+      "{\n\t.reg .pred p;\n\t"
+      "setp.ne.b32 p, %4, 0;\n\t"
+      "tcgen05.mma.cta_group::1.kind::tf32 [%0], [%1], %2, %3, p;\n\t}\n" ::"r"(d_tmem),
+      "r"(a_tmem), "l"(bdesc), "r"(idesc), "r"(accumulate)
+      : "memory");
 }
 
 // FP16 Omega tile (64 K-rows x N, N / 64 boxes of 64 x 64 halves, 128B
@@ -119,7 +139,7 @@ __global__ void __launch_bounds__(kTfThreads, 1)
                    const TcArgs args) {
   extern __shared__ uint8_t smem_raw[];
   uint8_t* smem = reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
-  const int SA = args.sa, SB = args.sb;
+  const int SA = args.sa, SB = args.sb, ST = args.st;
   const int N = args.n_tile;
   const uint32_t b_f32 = static_cast<uint32_t>(N) * 256u;  // FP32 Omega tile bytes, then the FP16 landing tile
   uint8_t* a_ring = smem;
@@ -131,7 +151,8 @@ __global__ void __launch_bounds__(kTfThreads, 1)
   const uint32_t bar_bfull = smem_u32(bars + 3 * SA);
   const uint32_t bar_bconv = smem_u32(bars + 3 * SA + SB);
   const uint32_t bar_bempty = smem_u32(bars + 3 * SA + 2 * SB);
-  const int nb = 3 * SA + 3 * SB;
+  const uint32_t bar_tempty = smem_u32(bars + 3 * SA + 3 * SB);  // [ST] lo stages in tensor memory
+  const int nb = 3 * SA + 3 * SB + ST;
   const uint32_t bar_dfull = smem_u32(bars + nb);       // [2]
   const uint32_t bar_dempty = smem_u32(bars + nb + 2);  // [2]
   const uint32_t bar_lempty = smem_u32(bars + nb + 4);
@@ -153,6 +174,7 @@ __global__ void __launch_bounds__(kTfThreads, 1)
       mbar_init(bar_bconv + 8 * s, 4);
       mbar_init(bar_bempty + 8 * s, 1);
     }
+    for (int s = 0; s < ST; ++s) mbar_init(bar_tempty + 8 * s, 1);
     for (int d = 0; d < 2; ++d) {
       mbar_init(bar_dfull + 8 * d, 1);
       mbar_init(bar_dempty + 8 * d, 4);
@@ -173,8 +195,9 @@ __global__ void __launch_bounds__(kTfThreads, 1)
   tc_fence_before();
   __syncthreads();
   tc_fence_after();
-  const uint32_t tmem_base = *tmem_slot;  // D0 at 0, D1 at N, lo accumulator at 2N
+  const uint32_t tmem_base = *tmem_slot;  // D0 at 0, D1 at N, lo accumulator at 2N, lo A stages from 3N
   const uint32_t tm_l = tmem_base + 2 * N;
+  const uint32_t tm_lo = tmem_base + 3 * N;
 
   long long u0, u1;
   cta_range(args, u0, u1);
@@ -226,7 +249,7 @@ __global__ void __launch_bounds__(kTfThreads, 1)
       if (lane == 0) {
         const uint32_t idesc = idesc_f16(2u, 0u, 0u, kBM, N);  // TF32 A and B, both K-major
         long long u = u0, cc = 0;
-        Ring ra, rb;
+        Ring ra, rb, rt;
         int seg = 0;
         bool ok = true;
         while (ok && u < u1) {
@@ -244,7 +267,7 @@ __global__ void __launch_bounds__(kTfThreads, 1)
             tc_fence_after();
             const uint32_t tm_d = tmem_base + d * N;
             const long long chunk_start = u;
-            for (; u < chunk_end; ++u, ra.next(SA), rb.next(SB)) {
+            for (; u < chunk_end; ++u, ra.next(SA), rb.next(SB), rt.next(ST)) {
               if (!mbar_wait(bar_asplit + 8 * ra.s, ra.ph, abort_flag, lim) ||
                   !mbar_wait(bar_bconv + 8 * rb.s, rb.ph, abort_flag, lim)) {
                 ok = false;
@@ -253,22 +276,25 @@ __global__ void __launch_bounds__(kTfThreads, 1)
               tc_fence_after();
               const uint32_t abase = smem_u32(a_ring + ra.s * kTfABytes);
               const uint32_t bbase = smem_u32(b_ring + rb.s * args.b_bytes);
-              // K-major A and B: a K step of 8 values is 32 bytes along the
-              // 128-byte rows (2 in the >> 4 address field); K 32..63 sit in
-              // the second box (16 KB on for A's 128 rows, N x 128 bytes for B)
+              // K-major A (hi, shared memory) and B: a K step of 8 values is
+              // 32 bytes along the 128-byte rows (2 in the >> 4 address
+              // field); K 32..63 sit in the second box (16 KB on for A's 128
+              // rows, N x 128 bytes for B).  The lo piece of A: 8 TMEM
+              // columns per K step.
               const uint64_t ah0 = smem_desc_sw128(abase, 16, 1024);
-              const uint64_t al0 = smem_desc_sw128(abase + 32768, 16, 1024);
               const uint64_t b0 = smem_desc_sw128(bbase, 16, 1024);
+              const uint32_t ta = tm_lo + rt.s * 64;
 #pragma unroll
               for (int ks = 0; ks < kBK / 8; ++ks) {
                 const uint64_t aoff = static_cast<uint64_t>((ks >> 2) * 1024 + (ks & 3) * 2);
                 const uint64_t bk = b0 + static_cast<uint64_t>((ks >> 2) * (N * 8) + (ks & 3) * 2);
                 tc_mma_tf32(tm_d, ah0 + aoff, bk, idesc, (u == chunk_start && ks == 0) ? 0u : 1u);
-                tc_mma_tf32(tm_l, al0 + aoff, bk, idesc, (first_in_seg && ks == 0) ? 0u : 1u);
+                tc_mma_tf32_tmem_a(tm_l, ta + ks * 8, bk, idesc, (first_in_seg && ks == 0) ? 0u : 1u);
               }
               first_in_seg = false;
               tc_commit(bar_aempty + 8 * ra.s);
               tc_commit(bar_bempty + 8 * rb.s);
+              tc_commit(bar_tempty + 8 * rt.s);
             }
             if (!ok) break;
             if (!args.drop_commit) tc_commit(bar_dfull + 8 * d);
@@ -280,17 +306,21 @@ __global__ void __launch_bounds__(kTfThreads, 1)
       __syncwarp();
     }
   } else if (wg == 1) {
-    regs_dec_120_tf();
     // ------------------------------------------------------------ split warps
-    const int r = threadIdx.x - 128;
-    Ring ra;
-    for (long long u = u0; u < u1; ++u, ra.next(SA)) {
-      if (!warp_wait(bar_afull + 8 * ra.s, ra.ph, abort_flag, lim, lane)) {
+    const int r = threadIdx.x - 128;  // tile row == TMEM lane of this thread
+    const uint32_t lane_off = static_cast<uint32_t>(32 * (warp & 3)) << 16;
+    Ring ra, rt;
+    for (long long u = u0; u < u1; ++u, ra.next(SA), rt.next(ST)) {
+      if (!warp_wait(bar_afull + 8 * ra.s, ra.ph, abort_flag, lim, lane) ||
+          !warp_wait(bar_tempty + 8 * rt.s, rt.ph ^ 1u, abort_flag, lim, lane)) {
         *abort_flag = 1;
         break;
       }
-      split_row_tf32(a_ring + ra.s * kTfABytes, r);
+      tc_fence_after();
+      split_row_tf32(a_ring + ra.s * kTfABytes, r, tm_lo + lane_off + rt.s * 64);
+      tc_wait_st();
       fence_proxy_async_smem();
+      tc_fence_before();
       __syncwarp();
       if (lane == 0) mbar_arrive(bar_asplit + 8 * ra.s);
     }
@@ -449,17 +479,20 @@ int tc_tf32_gemm(int64_t M, int64_t N, int64_t S_k, int64_t P, const float* A, i
   a.accumulate = 0;
   a.tile_ranges = tile_ranges ? 1 : 0;
   a.flags = d_flags;
-  a.st = 0;
-  a.tmem_cols = 3 * nt <= 256 ? 256 : 512;
+  // TMEM: D0, D1, the lo accumulator, then lo A stages of 64 columns
+  a.st = std::min(4, (512 - 3 * nt) / 64);
+  if (a.st < 2) return SHG_ERR_UNSUPPORTED;
+  a.tmem_cols = 512;
   a.b_bytes = static_cast<uint32_t>(nt) * 384u;  // FP32 tile + FP16 landing tile
   a.kc = std::max(2, std::min(env_int("SHG_DRAIN_KBLOCKS", 4), 8));
   TcTestHooks h;
   a.wait_ns = h.wait_ns;
   a.drop_commit = 0;
   const uint32_t bar_bytes = 1024;
-  a.sa = 2;
+  a.sa = std::max(2, std::min(env_int("SHG_TF32_A_STAGES", 4), 6));
   a.sb = 3;
   while (a.sa * kTfABytes + a.sb * a.b_bytes + 1024 + bar_bytes > kMaxSmem && a.sb > 2) --a.sb;
+  while (a.sa * kTfABytes + a.sb * a.b_bytes + 1024 + bar_bytes > kMaxSmem && a.sa > 2) --a.sa;
   if (a.sa * kTfABytes + a.sb * a.b_bytes + 1024 + bar_bytes > kMaxSmem) return SHG_ERR_UNSUPPORTED;
   const size_t smem = 1024 + static_cast<size_t>(a.sa) * kTfABytes + static_cast<size_t>(a.sb) * a.b_bytes + bar_bytes;
 
@@ -495,6 +528,7 @@ int tc_tf32_gemm(int64_t M, int64_t N, int64_t S_k, int64_t P, const float* A, i
   int dev = 0;
   if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 64) return SHG_ERR_CUDA;
   if (configured[dev] != smem) {
+    if (!regs_at_launch_ok(tc_tf32_kernel)) return SHG_ERR_UNSUPPORTED;
     const int carve = static_cast<int>((smem * 100 + kMaxSmem - 1) / kMaxSmem);
     if (cudaFuncSetAttribute(tc_tf32_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, static_cast<int>(smem)) !=
             cudaSuccess ||
