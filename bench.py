@@ -252,6 +252,11 @@ def main():
     # launch configuration per shape class, timed once before the warm-up
     tuned = {str(k): shg.shg_autotune_project(A, Om[:, :k], "f16", reps=3, out=Ys[k], flags=flags, stream=stream)
              for k in KS}
+    # whether each class kept stream-K ranges or whole output tiles per CTA
+    # (a class's N tiling: n_tile x n_tiles = k for these k)
+    for e in shg.shg_autotune_export():
+        if e["a_layout"] == 0 and e["b_mode"] == 0 and str(e["n_tile"] * e["n_tiles"]) in tuned:
+            tuned[str(e["n_tile"] * e["n_tiles"])]["whole_tiles"] = bool(e["whole_tiles"])
     for _ in range(args.warmup):
         step()
     torch.cuda.synchronize()

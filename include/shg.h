@@ -225,7 +225,9 @@ int shg_sgemm(int64_t m, int64_t n, int64_t kk,
  *   A pass per 256 columns), 2 = 256 x 256 tiles on pairs of CTAs (one
  *   tensor-core MMA of 256 rows over two SMs, each SM holding half of the
  *   Omega tile), 0 = 128-column tiles split into tensor memory; the tuner
- *   times all three.
+ *   times all three, then the winner once more with CTA ranges of whole
+ *   output tiles instead of stream-K ranges (kept when faster; such a class
+ *   then gives bitwise-reproducible Y as SHG_DETERMINISTIC does).
  *   shg_autotune_lookup reports the cached configuration of a class
  *   (config_out[4] = 0 when it has none; the other entries are then the
  *   built-in defaults).  shg_autotune_clear empties the cache.
@@ -247,7 +249,8 @@ int shg_autotune_clear(void);
  * counterpart in the paper.  A record is SHG_TUNE_RECORD int32 values:
  *   {A layout (0 K-major, 1 MN-major), Omega / B mode, pieces, N tile,
  *    N tiles, floor(log2 m), floor(log2 K), more than one K piece,
- *    A stages, B stages, drain K blocks, grouping, wide tiles, CTA pairs}.
+ *    A stages, B stages, drain K blocks, grouping, wide tiles, CTA pairs,
+ *    whole output tiles per CTA (no split-K)}.
  * shg_autotune_export writes min(capacity, entries) records to `records`
  * (host memory, capacity * SHG_TUNE_RECORD values; NULL when capacity = 0)
  * and the number of entries to *count.  shg_autotune_import checks every
@@ -255,7 +258,7 @@ int shg_autotune_clear(void);
  * adds those whose shape class is not cached yet; *added (nullable)
  * receives how many.  Neither touches the GPU.
  */
-#define SHG_TUNE_RECORD 14
+#define SHG_TUNE_RECORD 15
 int shg_autotune_export(int32_t* records, int32_t capacity, int32_t* count);
 int shg_autotune_import(const int32_t* records, int32_t count, int32_t* added);
 int shg_rsvd_batched_autotune(int batch, const int64_t* m, const int64_t* n, const int64_t* rank,

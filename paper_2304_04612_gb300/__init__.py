@@ -181,9 +181,9 @@ def shg_autotune_clear() -> None:
     _check(_lib.load().shg_autotune_clear(), "shg_autotune_clear")
 
 
-TUNE_RECORD = 14
+TUNE_RECORD = 15
 _TUNE_FIELDS = ("a_layout", "b_mode", "pieces", "n_tile", "n_tiles", "m_log2", "k_log2", "k_pieces",
-                "a_stages", "b_stages", "drain_kblocks", "n_groups", "wide", "pair")
+                "a_stages", "b_stages", "drain_kblocks", "n_groups", "wide", "pair", "whole_tiles")
 
 
 def shg_autotune_export() -> list[dict]:

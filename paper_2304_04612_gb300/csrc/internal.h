@@ -36,6 +36,7 @@ struct TcConfig {
   int groups = 1;  // 1: one CTA group per N tile when there are 2..8 N tiles; 0: a single group
   int wide = 1;    // 1: N tiles of up to 256 columns (K-major A, FP16 B, N > 128); 0: tiles of 128
   int pair = 1;    // with wide: 256 x 256 tiles on CTA pairs (cta_group::2); 0: 128 x 256 tiles per CTA
+  int whole = 0;   // 1: CTA ranges of whole output tiles (no split-K); 0: stream-K ranges
 };
 int tc_gemm(int amaj, int bmode, int pieces, int64_t M, int64_t N, int64_t S_k, int64_t P,
             const float* A, int64_t lda, int64_t p_stride, const void* B, int64_t ldb, float* C,
@@ -67,7 +68,7 @@ void tc_tune_clear();
 // the configuration); export returns the number of entries (writing at most
 // `cap`), import adds entries whose class is not cached yet and returns how
 // many it added, or -1 on a malformed record.
-constexpr int kTuneRecord = 14;
+constexpr int kTuneRecord = 15;
 int tc_tune_export(int32_t* rec, int cap);
 int tc_tune_import(const int32_t* rec, int count);
 // Bumped whenever the tuner's cache changes (a new entry or a clear), so that

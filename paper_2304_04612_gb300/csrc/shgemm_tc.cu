@@ -988,7 +988,7 @@ int tc_tune_export(int32_t* rec, int cap) {
     const TuneKey& k = g_tune[i].first;
     const TcConfig& c = g_tune[i].second;
     const int32_t v[kTuneRecord] = {k.amaj, k.bmode, k.pieces, k.nt, k.n_tiles, k.mlog, k.klog, k.pmulti,
-                                    c.sa, c.sb, c.kc, c.groups, c.wide, c.pair};
+                                    c.sa, c.sb, c.kc, c.groups, c.wide, c.pair, c.whole};
     for (int j = 0; j < kTuneRecord; ++j) rec[i * kTuneRecord + j] = v[j];
   }
   return n;
@@ -1003,7 +1003,8 @@ int tc_tune_import(const int32_t* rec, int count) {
                     v[2] <= 3 && v[3] >= 64 && v[3] <= 256 && v[3] % 64 == 0 && v[4] >= 1 && v[5] >= 0 &&
                     v[5] < 63 && v[6] >= 0 && v[6] < 63 && (v[7] == 0 || v[7] == 1) && v[8] >= 2 && v[8] <= 6 &&
                     v[9] >= 2 && v[9] <= 6 && v[10] >= 2 && v[10] <= 8 && (v[11] == 0 || v[11] == 1) &&
-                    (v[12] == 0 || v[12] == 1) && (v[13] == 0 || v[13] == 1);
+                    (v[12] == 0 || v[12] == 1) && (v[13] == 0 || v[13] == 1) &&
+                    (v[14] == 0 || v[14] == 1);
     if (!ok) return -1;
   }
   std::lock_guard<std::mutex> lock(g_tune_mu);
@@ -1021,6 +1022,7 @@ int tc_tune_import(const int32_t* rec, int count) {
     c.groups = v[11];
     c.wide = v[12];
     c.pair = v[13];
+    c.whole = v[14];
     g_tune.emplace_back(k, c);
     ++added;
   }
@@ -1119,6 +1121,26 @@ int tc_autotune(int amaj, int bmode, int pieces, int64_t M, int64_t N, int64_t S
       win = c;
     }
   }
+  if (rc == SHG_OK) {
+    // the winner once more with CTA ranges of whole output tiles (no split-K
+    // partial tiles, no zeroing of Y; fewer CTAs when tiles are few)
+    TcConfig c = win;
+    c.whole = 1;
+    rc = tc_gemm(amaj, bmode, pieces, M, N, S_k, P, A, lda, p_stride, B, ldb, C, ldc, 0, d_flags, stream, nullptr,
+                 &c);
+    if (rc == SHG_OK && cudaEventRecord(e0, stream) != cudaSuccess) rc = SHG_ERR_CUDA;
+    for (int r = 0; r < reps && rc == SHG_OK; ++r)
+      rc = tc_gemm(amaj, bmode, pieces, M, N, S_k, P, A, lda, p_stride, B, ldb, C, ldc, 0, d_flags, stream,
+                   nullptr, &c);
+    float ms = 0.0f;
+    if (rc == SHG_OK && (cudaEventRecord(e1, stream) != cudaSuccess || cudaEventSynchronize(e1) != cudaSuccess ||
+                         cudaEventElapsedTime(&ms, e0, e1) != cudaSuccess))
+      rc = SHG_ERR_CUDA;
+    if (rc == SHG_OK && ms < best_ms) {
+      best_ms = ms;
+      win = c;
+    }
+  }
   cudaEventDestroy(e0);
   cudaEventDestroy(e1);
   if (rc != SHG_OK) return rc;
@@ -1140,7 +1162,7 @@ namespace {
 int tc_gemm_impl(int amaj, int bmode, int pieces, int64_t M, int64_t N, int64_t S_k, int64_t P, const float* A,
                  int64_t lda, int64_t p_stride, const void* B, int64_t ldb, float* C, int64_t ldc, int accumulate,
                  int32_t* d_flags, cudaStream_t stream, const TcTestHooks* hooks, const TcConfig* force,
-                 const void* B_lo, bool tile_ranges) {
+                 const void* B_lo, bool deterministic) {
   if (M <= 0 || N <= 0 || S_k <= 0 || P <= 0) return SHG_ERR_INVALID_ARG;
   if (M >= (1ll << 31) || N >= (1ll << 31) || S_k * P >= (1ll << 31)) return SHG_ERR_INVALID_ARG;
   if (amaj == A_MNMAJ && P != 1) return SHG_ERR_INVALID_ARG;
@@ -1163,6 +1185,8 @@ int tc_gemm_impl(int amaj, int bmode, int pieces, int64_t M, int64_t N, int64_t 
   else tuned = tc_tuned(amaj, bmode, pieces, M, N, K, P, &cfg);
   const bool wide = use_wide(amaj, bmode, pieces, N, cfg);
   bool pair = wide && cfg.pair != 0;
+  // whole output tiles per CTA range: asked for (bitwise-reproducible Y) or tuned
+  const bool tile_ranges = deterministic || cfg.whole != 0;
   // the wide kernel's single-buffered hi accumulator: drain every 8 K
   // blocks unless a tuned or forced configuration says otherwise
   if (wide && !force && !tuned && std::getenv("SHG_DRAIN_KBLOCKS") == nullptr) cfg.kc = 8;

@@ -67,7 +67,7 @@ def test_autotune_cache_round_trip(tmp_path):
     import paper_2304_04612_gb300 as shg
     shg.shg_autotune_clear()
     e = {"a_layout": 0, "b_mode": 0, "pieces": 2, "n_tile": 128, "n_tiles": 2, "m_log2": 14, "k_log2": 14,
-         "k_pieces": 0, "a_stages": 4, "b_stages": 3, "drain_kblocks": 8, "n_groups": 1, "wide": 1, "pair": 1}
+         "k_pieces": 0, "a_stages": 4, "b_stages": 3, "drain_kblocks": 8, "n_groups": 1, "wide": 1, "pair": 1, "whole_tiles": 0}
     assert shg.shg_autotune_import([e]) == 1
     assert shg.shg_autotune_import([e]) == 0                # the class is cached already
     assert shg.shg_autotune_export() == [e]
@@ -85,3 +85,12 @@ def test_autotune_cache_round_trip(tmp_path):
     with pytest.raises(RuntimeError):
         shg.shg_autotune_import([dict(e, a_stages=9)])
     assert shg.shg_autotune_export() == []
+
+
+def test_tune_record_size_matches_header():
+    import os
+    import re
+    import paper_2304_04612_gb300 as shg
+    hdr = open(os.path.join(os.path.dirname(__file__), "..", "include", "shg.h")).read()
+    n = int(re.search(r"#define SHG_TUNE_RECORD (\d+)", hdr).group(1))
+    assert n == shg.TUNE_RECORD == len(shg._TUNE_FIELDS)
