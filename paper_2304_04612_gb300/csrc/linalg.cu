@@ -517,17 +517,34 @@ __device__ __forceinline__ void jac_block(float m00, float m01, float m10, float
 
 // Rotation annihilating a_pq of the 2 x 2 block [[app, apq], [apq, aqq]]
 // (t = tan of the angle, the smaller root); skipped (c = 1, s = 0) when
-// |a_pq| <= 2^-23 sqrt(|a_pp a_qq|).  c = 1/sqrt(1 + t^2) and s = t c keep
-// c^2 + s^2 = 1 to rounding whatever the accuracy of t.
+// |a_pq| <= 2^-23 sqrt(|a_pp a_qq|), compared as squares.  The rotation
+// maps (p, q) to (c p - s q, s p + c q).  sqrt(1 + tau^2) is formed as
+// x rsqrt(x) (no rounding-exact square root is needed: any t gives an
+// orthogonal rotation, and one that leaves a tiny a_pq is caught by later
+// sweeps); beyond |tau| = 2^20 t = 1 / (2 tau).  c = 1/sqrt(1 + t^2) and
+// s = t c keep c^2 + s^2 = 1 to rounding whatever the accuracy of t.
 __device__ __forceinline__ bool jac_rot(float app, float aqq, float apq, float& c, float& s) {
   c = 1.0f;
   s = 0.0f;
-  if (!(fabsf(apq) > 1.1920929e-7f * sqrtf(fabsf(app * aqq))) || !(fabsf(apq) > 1e-30f)) return false;
+  if (!(apq * apq > 0x1p-46f * fabsf(app * aqq)) || !(fabsf(apq) > 1e-30f)) return false;
   const float tau = __fdividef(aqq - app, 2.0f * apq);
-  const float t = __fdividef(tau >= 0.0f ? 1.0f : -1.0f, fabsf(tau) + sqrtf(fmaf(tau, tau, 1.0f)));
+  const float w = fabsf(tau);
+  const float x = fmaf(w, w, 1.0f);
+  const float t = (w < 0x1p20f) ? __fdividef(1.0f, w + x * rsqrtf(x)) : __fdividef(0.5f, w);
   c = rsqrtf(fmaf(t, t, 1.0f));
-  s = t * c;
+  s = copysignf(t, tau) * c;
   return true;
+}
+
+// A rotation counts as large when |a_pq| > 2^-12 sqrt(|a_pp a_qq|) and
+// |a_pq| > 2^-40 (the matrix is scaled to a largest diagonal in [1, 2)).
+// Cyclic Jacobi converges quadratically: after a sweep whose rotations were
+// all small, the off-diagonal ratios are of order 2^-24, at the level of the
+// FP32 entries themselves, so the sweep that would only confirm this is
+// skipped.  Pairs below 2^-40 belong to eigenvalues under 2^-40 of the
+// largest, whose FP32 rotations stay at noise level and never settle.
+__device__ __forceinline__ bool jac_big(float app, float aqq, float apq) {
+  return fabsf(apq) > 0x1p-40f && apq * apq > 0x1p-24f * fabsf(app * aqq);
 }
 
 // Indices (a, b) of slot t at round r of the round-robin ("circle")
@@ -545,39 +562,74 @@ __device__ __forceinline__ void circle_ab(int t, int r, int n1, int& a, int& b) 
 // Element (x, y) of a symmetric matrix kept as its upper triangle.
 __device__ __forceinline__ int sym_at(int x, int y, int ld) { return min(x, y) * ld + max(x, y); }
 
+// Positions of the circle order: position 2t holds the a-index of slot t,
+// position 2t + 1 its b-index.  From one round to the next every index
+// moves along a fixed map of positions (h = kp / 2 slots): a_1 -> b_0,
+// a_j -> a_{j-1} (j >= 2), b_j -> b_{j+1} (j < h - 1), b_{h-1} -> a_{h-1},
+// and position 0 (index 0) stays.  circ_next gives where the index at
+// position x goes, circ_prev where the index at position y came from.
+__device__ __forceinline__ int circ_next(int x, int h) {
+  if (h < 2) return x;
+  const int j = x >> 1;
+  if ((x & 1) == 0) return (j == 0) ? 0 : (j == 1) ? 1 : 2 * (j - 1);
+  return (j == h - 1) ? 2 * (h - 1) : 2 * (j + 1) + 1;
+}
+__device__ __forceinline__ int circ_prev(int y, int h) {
+  if (h < 2) return y;
+  const int j = y >> 1;
+  if ((y & 1) == 0) return (j == 0) ? 0 : (j == h - 1) ? 2 * h - 1 : 2 * (j + 1);
+  return (j == 0) ? 2 : 2 * j - 1;
+}
+// Index held by position x at round r.
+__device__ __forceinline__ int circ_index(int x, int r, int n1) {
+  int a, b;
+  circle_ab(x >> 1, r, n1, a, b);
+  return (x & 1) ? b : a;
+}
+
 // Eigenvalues of the symmetric k x k matrix whose upper triangle is in G
 // (FP64), by the parallel cyclic Jacobi method: A = sigma G in FP32 (sigma a
 // power of two near 1 / max diag), then sweeps until a sweep applies no
-// rotation (at most kJacSweeps).  One CTA; A lives in shared memory, and a
-// round is bound by shared-memory traffic, which the layout keeps low.  The
-// eigenvectors are not accumulated here: every round's rotations (c, s) go
-// to `log` (round rho, slot t at rho * h + t) and *rounds_out receives the
-// number of rounds that count; jac_apply_v_kernel multiplies them out.
+// rotation, or until one sweep's rotations were all small (jac_big), at most
+// kJacSweeps.  One CTA; A lives in shared memory, and a round is bound by
+// instruction issue and shared-memory traffic, which the layout keeps low.
+// The eigenvectors are not accumulated here: every round's rotations (c, s)
+// go to `log` (round rho, slot t at rho * h + t; the rotation maps the
+// slot's (a, b) indices of circle_ab to (c a - s b, s a + c b)) and
+// *rounds_out receives the number of rounds that count; jac_apply_v_kernel
+// multiplies them out.
 //   Pairing: the circle order of circle_ab (kp = k rounded up to even,
-//   h = kp / 2 slots, n1 = kp - 1).  Between rounds a_i <- a_{i+1}
-//   (1 <= i < h - 1), a_{h-1} <- b_{h-1}, b_i <- b_{i-1} (i >= 1) and
-//   b_0 <- a_1, so the slot of round r that each index of round r + 1 comes
-//   from is fixed; every thread computes slot indices, and only the
-//   rotations (c, s) go through shared memory.
-//   A is kept as its upper triangle (each element read and written once per
-//   round).
+//   h = kp / 2 slots, n1 = kp - 1).  A is stored by position (circ_next):
+//   row and column 2t hold slot t's a-index, 2t + 1 its b-index, so a pair
+//   block (t, u) always sits at rows 2t, 2t + 1 and columns 2u, 2u + 1, and
+//   its rotated 2 x 2 block goes to the fixed positions its indices hold in
+//   the next round.  Every address a thread touches is fixed over the
+//   rounds and computed once.  A is kept as the upper triangle of the
+//   position matrix (each element read and written once per round).
 //   Roles (whole warps): block threads own fixed pair blocks (t, u), t <= u,
 //   in folded-triangle order (rows i and h - 1 - i of the triangle form one
 //   row of h + 1 blocks) and write each 2 x 2 block of J^T A J to the second
 //   buffer; rotation threads (one per slot) build round r + 1's rotations
-//   from the old A at the same time.  The rotation chain (about 200
-//   dependent instructions) sets the length of a round, so the rotation
-//   warps get a warp scheduler to themselves: warp w issues from scheduler
-//   w mod 4, the rotation warps are warps 0, 4, 8, ... and the other warps
-//   on that scheduler only wait at the barrier.  One barrier per round.
-//   last_rot holds the latest sweep that applies a rotation; sweep s ends
-//   the loop when last_rot < s, and the rounds of sweeps 0 .. s - 1 count.
+//   from the old A at the same time: the next-round diagonal block of slot
+//   rt gathers positions circ_prev(2 rt) and circ_prev(2 rt + 1), whose
+//   rotated values the rotation thread forms itself with the same
+//   arithmetic (jac_block) the block threads use, so they are bit-identical.
+//   The rotation chain sets the length of a round, so the rotation warps get
+//   a warp scheduler to themselves: warp w issues from scheduler w mod 4,
+//   the rotation warps are warps 0, 4, 8, ... and the other warps on that
+//   scheduler only wait at the barrier.  One barrier per round.
+//   last_rot holds the latest sweep that applies a rotation and big_rot[s %
+//   4] whether sweep s applied a large one; after sweep s the loop ends with
+//   the rounds of sweeps 0 .. s - 1 when last_rot < s, or with those of
+//   sweeps 0 .. s when big_rot is clear (slot (s + 3) % 4 is cleared for
+//   sweep s + 3 once every thread has passed its last read).
 // Shared layout: (c, s)[2][h], then the two A buffers (kp x (kp + 1) floats
-// each, upper triangles).
+// each, upper triangles).  kp (kp + 1) < 2^16 (the smem_fits limit), so two
+// offsets pack into one word.
 constexpr int kJacSweeps = 40;
 constexpr int kJacGridThreads = 128;  // CTA size of the grid solver (more SMs per round)
 constexpr int kJacLogMaxK = 288;  // largest kp whose rotations are logged (13 MB at 40 sweeps)
-constexpr int kJacItems = 6;  // most blocks (or V pieces) one thread owns
+constexpr int kJacItems = 6;  // most blocks one thread owns
 
 __host__ __device__ inline size_t jac_cta_floats(int kp) {
   return static_cast<size_t>(2 * kp) + 2 * static_cast<size_t>(kp) * (kp + 1);
@@ -592,16 +644,23 @@ __device__ __forceinline__ void jacobi_body(int k, const double* __restrict__ G,
   float2* rots = reinterpret_cast<float2*>(smf);  // [2][h]
   float* const M0 = smf + 4 * h;
   __shared__ int last_rot;
+  __shared__ int big_rot[4];
   __shared__ double red[32];
   __shared__ double dmax;
   const int tid = threadIdx.x, nt = blockDim.x;
   diag_max(k, G, red, &dmax);
-  if (tid == 0) last_rot = -1;
+  if (tid == 0) {
+    last_rot = -1;
+    big_rot[0] = big_rot[1] = big_rot[2] = big_rot[3] = 0;
+  }
   __syncthreads();
   const double sigma = ldexp(1.0, -((dmax > 0.0) ? ilogb(dmax) : 0));
   for (int e = tid; e < kp * kp; e += nt) {
-    const int i = e / kp, j = e - i * kp;
-    if (j >= i) M0[i * ld + j] = (j < k) ? static_cast<float>(G[i * k + j] * sigma) : 0.0f;
+    const int x = e / kp, y = e - x * kp;
+    if (y >= x) {
+      const int i = circ_index(x, 0, n1), j = circ_index(y, 0, n1);
+      M0[x * ld + y] = (i < k && j < k) ? static_cast<float>(G[min(i, j) * k + max(i, j)] * sigma) : 0.0f;
+    }
   }
   const int nblk = h * (h + 1) / 2;
   // warps 0, 4, 8, ...: rotation warps (then idle); the others: block warps
@@ -611,62 +670,60 @@ __device__ __forceinline__ void jacobi_body(int k, const double* __restrict__ G,
   const bool is_blk = !sched0 && wt < TB;
   const int rt = sched0 ? (warp >> 2) * 32 + lane : -1;
   const bool rotor = rt >= 0 && rt < h;
-  // fixed blocks (t, u) in folded-triangle order
-  int it[kJacItems];  // t | u << 16, or -1
+  // fixed blocks (t, u) in folded-triangle order: it = t | u << 16 (or -1),
+  // src = offset of element (2t, 2u) (bit 30: diagonal block), dst0 / dst1 =
+  // the next-round offsets of rows 2t / 2t + 1 at columns 2u (low half) and
+  // 2u + 1 (high half)
+  int it[kJacItems], src[kJacItems];
+  uint32_t dst0[kJacItems], dst1[kJacItems];
 #pragma unroll
   for (int c = 0; c < kJacItems; ++c) {
     it[c] = -1;
+    src[c] = 0;
+    dst0[c] = dst1[c] = 0u;
     const int bi = wt + c * TB;
     if (is_blk && bi < nblk) {
       const int i = bi / (h + 1), j = bi - i * (h + 1);
-      it[c] = (j < h - i) ? (i | ((i + j) << 16)) : ((h - 1 - i) | ((j - 1) << 16));
+      const int t = (j < h - i) ? i : h - 1 - i, u = (j < h - i) ? i + j : j - 1;
+      it[c] = t | (u << 16);
+      src[c] = (2 * t * ld + 2 * u) | ((t == u) ? (1 << 30) : 0);
+      const int pa = circ_next(2 * t, h), pb = circ_next(2 * t + 1, h);
+      const int qa = circ_next(2 * u, h), qb = circ_next(2 * u + 1, h);
+      dst0[c] = static_cast<uint32_t>(sym_at(pa, qa, ld)) | (static_cast<uint32_t>(sym_at(pa, qb, ld)) << 16);
+      dst1[c] = static_cast<uint32_t>(sym_at(pb, qa, ld)) | (static_cast<uint32_t>(sym_at(pb, qb, ld)) << 16);
     }
   }
-  // the slots of the previous round that slot rt's a- and b-index come from
-  const int srcA = (rt <= 0) ? 0 : min(rt + 1, h - 1);
-  const int srcB = (rt >= 1) ? rt - 1 : (h >= 2 ? 1 : 0);
+  // rotation thread rt: the next-round positions 2 rt, 2 rt + 1 come from
+  // positions sa, sb (slots Sa, Sb); their diagonal blocks start at rd0 /
+  // rd1, and the block holding (sa, sb) (slots T1 <= T2) at rdx.  rfl: sides
+  // of sa and sb within their slots, the row and column sides of (sa, sb) in
+  // block (T1, T2), and T1 == T2.
+  int rd0 = 0, rd1 = 0, rdx = 0, rfl = 0, rSa = 0, rSb = 0, rT1 = 0, rT2 = 0;
+  if (rotor) {
+    const int sa = circ_prev(2 * rt, h), sb = circ_prev(2 * rt + 1, h);
+    rSa = sa >> 1;
+    rSb = sb >> 1;
+    rT1 = min(rSa, rSb);
+    rT2 = max(rSa, rSb);
+    rd0 = 2 * rSa * (ld + 1);
+    rd1 = 2 * rSb * (ld + 1);
+    rdx = 2 * rT1 * ld + 2 * rT2;
+    const int rs = (rSa <= rSb) ? (sa & 1) : (sb & 1), cs = (rSa <= rSb) ? (sb & 1) : (sa & 1);
+    rfl = (sa & 1) | ((sb & 1) << 1) | (rs << 2) | (cs << 3) | ((rT1 == rT2) ? 16 : 0);
+  }
   __syncthreads();
   if (rotor) {
-    int pa, pb;
-    circle_ab(rt, 0, n1, pa, pb);
-    const int p = min(pa, pb), q = max(pa, pb);
+    const int d = 2 * rt * (ld + 1);
+    const float app = M0[d], aqq = M0[d + ld + 1], apq = M0[d + 1];
     float c, s;
-    if (jac_rot(M0[p * ld + p], M0[q * ld + q], M0[p * ld + q], c, s)) last_rot = 0;
+    if (jac_rot(app, aqq, apq, c, s)) {
+      last_rot = 0;
+      if (jac_big(app, aqq, apq)) big_rot[0] = 1;
+    }
     rots[rt] = make_float2(c, s);
     log[rt] = make_float2(c, s);
   }
   __syncthreads();
-  // Rotation thread: the ten elements of the old A its next rotation needs
-  // (the diagonal 2 x 2 blocks of its two source slots and their common
-  // block) are addressed one round ahead, so that its loads are the first
-  // in the shared-memory queue when the round starts.
-  int rix[10], rfl = 0;
-  auto plan = [&](int r) {
-    int pa, pb, aA, bA, aB, bB;
-    circle_ab(rt, r + 1, n1, pa, pb);
-    circle_ab(srcA, r, n1, aA, bA);
-    circle_ab(srcB, r, n1, aB, bB);
-    const int pA = min(aA, bA), qA = max(aA, bA), pB = min(aB, bB), qB = max(aB, bB);
-    const int sxa = (pa == pA) ? 0 : 1, sxb = (pb == pB) ? 0 : 1;
-    const bool a_low = pa < pb;
-    const int tp = a_low ? srcA : srcB, tq = a_low ? srcB : srcA;
-    const int pp = a_low ? pA : pB, qp = a_low ? qA : qB, pq = a_low ? pB : pA, qq = a_low ? qB : qA;
-    const int sp = a_low ? sxa : sxb, sq = a_low ? sxb : sxa;
-    const bool pfirst = tp <= tq;
-    const int p1 = pfirst ? pp : pq, q1 = pfirst ? qp : qq, p2 = pfirst ? pq : pp, q2 = pfirst ? qq : qp;
-    rix[0] = pp * ld + pp;
-    rix[1] = pp * ld + qp;
-    rix[2] = qp * ld + qp;
-    rix[3] = pq * ld + pq;
-    rix[4] = pq * ld + qq;
-    rix[5] = qq * ld + qq;
-    rix[6] = sym_at(p1, p2, ld);
-    rix[7] = sym_at(p1, q2, ld);
-    rix[8] = sym_at(q1, p2, ld);
-    rix[9] = sym_at(q1, q2, ld);
-    rfl = sp | (sq << 1) | (pfirst ? 4 : 0) | (tp == tq ? 8 : 0) | (a_low ? 16 : 0);
-  };
-  if (rotor) plan(0);
   int buf = 0;
   int sweeps = kJacSweeps;
   for (int sweep = 0; sweep < kJacSweeps; ++sweep) {
@@ -678,25 +735,19 @@ __device__ __forceinline__ void jacobi_body(int k, const double* __restrict__ G,
         // two blocks at a time: all loads, then all arithmetic and stores
 #pragma unroll
         for (int g = 0; g < kJacItems; g += 2) {
-          int ix[2][4];
           float v[2][4];
           float2 R1[2], R2[2];
 #pragma unroll
           for (int e = 0; e < 2; ++e) {
             if (it[g + e] >= 0) {
-              const int t = it[g + e] & 0xffff, u = it[g + e] >> 16;
-              int a1, b1, a2, b2;
-              circle_ab(t, r, n1, a1, b1);
-              circle_ab(u, r, n1, a2, b2);
-              const int p1 = min(a1, b1), q1 = max(a1, b1), p2 = min(a2, b2), q2 = max(a2, b2);
-              ix[e][0] = sym_at(p1, p2, ld);
-              ix[e][1] = sym_at(p1, q2, ld);
-              ix[e][2] = sym_at(q1, p2, ld);
-              ix[e][3] = sym_at(q1, q2, ld);
-              R1[e] = cur[t];
-              R2[e] = cur[u];
-#pragma unroll
-              for (int z = 0; z < 4; ++z) v[e][z] = A[ix[e][z]];
+              const int s0 = src[g + e] & 0xffff;
+              const bool dg = (src[g + e] >> 30) != 0;
+              R1[e] = cur[it[g + e] & 0xffff];
+              R2[e] = cur[it[g + e] >> 16];
+              v[e][0] = A[s0];
+              v[e][1] = A[s0 + 1];
+              v[e][2] = A[dg ? s0 + 1 : s0 + ld];
+              v[e][3] = A[s0 + ld + 1];
             }
           }
 #pragma unroll
@@ -704,40 +755,40 @@ __device__ __forceinline__ void jacobi_body(int k, const double* __restrict__ G,
             if (it[g + e] >= 0) {
               float n00, n01, n10, n11;
               jac_block(v[e][0], v[e][1], v[e][2], v[e][3], R1[e].x, R1[e].y, R2[e].x, R2[e].y, n00, n01, n10, n11);
-              if ((it[g + e] & 0xffff) == (it[g + e] >> 16)) {
+              if ((src[g + e] >> 30) != 0) {
                 if (R1[e].y != 0.0f) n01 = 0.0f;
                 n10 = n01;  // the same element as n01 on the diagonal block
               }
-              B[ix[e][0]] = n00;
-              B[ix[e][1]] = n01;
-              B[ix[e][2]] = n10;
-              B[ix[e][3]] = n11;
+              B[dst0[g + e] & 0xffffu] = n00;
+              B[dst0[g + e] >> 16] = n01;
+              B[dst1[g + e] & 0xffffu] = n10;
+              B[dst1[g + e] >> 16] = n11;
             }
           }
         }
       } else if (rotor) {
         // rotation of slot rt for round r + 1 from the same old A
-        float ev[10];
-#pragma unroll
-        for (int z = 0; z < 10; ++z) ev[z] = A[rix[z]];
-        const float2 RA = cur[srcA], RB = cur[srcB];
-        const int sp = rfl & 1, sq = (rfl >> 1) & 1;
-        const bool pfirst = (rfl & 4) != 0, same = (rfl & 8) != 0, a_low = (rfl & 16) != 0;
-        const float2 Rp = a_low ? RA : RB, Rq = a_low ? RB : RA;
+        const bool same = (rfl & 16) != 0;
+        const float d00 = A[rd0], d01 = A[rd0 + 1], d11 = A[rd0 + ld + 1];
+        const float e00 = A[rd1], e01 = A[rd1 + 1], e11 = A[rd1 + ld + 1];
+        const float x00 = A[rdx], x01 = A[rdx + 1], x10 = A[same ? rdx + 1 : rdx + ld], x11 = A[rdx + ld + 1];
+        const float2 RA = cur[rSa], RB = cur[rSb], R1 = cur[rT1], R2 = cur[rT2];
         float n00, n01, n10, n11;
-        jac_block(ev[0], ev[1], ev[1], ev[2], Rp.x, Rp.y, Rp.x, Rp.y, n00, n01, n10, n11);
-        const float app = sp ? n11 : n00;
-        jac_block(ev[3], ev[4], ev[4], ev[5], Rq.x, Rq.y, Rq.x, Rq.y, n00, n01, n10, n11);
-        const float aqq = sq ? n11 : n00;
-        const float2 R1 = pfirst ? Rp : Rq, R2 = pfirst ? Rq : Rp;
-        const int sx = pfirst ? sp : sq, sy = pfirst ? sq : sp;
-        jac_block(ev[6], ev[7], ev[8], ev[9], R1.x, R1.y, R2.x, R2.y, n00, n01, n10, n11);
-        const float apq = (same && sx != sy && R1.y != 0.0f) ? 0.0f : (sx ? (sy ? n11 : n10) : (sy ? n01 : n00));
+        jac_block(d00, d01, d01, d11, RA.x, RA.y, RA.x, RA.y, n00, n01, n10, n11);
+        const float app = (rfl & 1) ? n11 : n00;
+        jac_block(e00, e01, e01, e11, RB.x, RB.y, RB.x, RB.y, n00, n01, n10, n11);
+        const float aqq = (rfl & 2) ? n11 : n00;
+        jac_block(x00, x01, x10, x11, R1.x, R1.y, R2.x, R2.y, n00, n01, n10, n11);
+        const int rs = (rfl >> 2) & 1, cs = (rfl >> 3) & 1;
+        const float apq = (same && rs != cs && R1.y != 0.0f) ? 0.0f : (rs ? (cs ? n11 : n10) : (cs ? n01 : n00));
+        const int swn = (r + 1 == n1) ? sweep + 1 : sweep;
         float c, s;
-        if (jac_rot(app, aqq, apq, c, s)) last_rot = (r + 1 == n1) ? sweep + 1 : sweep;
+        if (jac_rot(app, aqq, apq, c, s)) {
+          last_rot = swn;
+          if (jac_big(app, aqq, apq)) big_rot[swn & 3] = 1;
+        }
         rots[(buf ^ 1) * h + rt] = make_float2(c, s);
         if (sweep * n1 + r + 1 < kJacSweeps * n1) log[static_cast<size_t>(sweep * n1 + r + 1) * h + rt] = make_float2(c, s);
-        plan(r + 1 == n1 ? 0 : r + 1);
       }
       __syncthreads();
       buf ^= 1;
@@ -746,6 +797,11 @@ __device__ __forceinline__ void jacobi_body(int k, const double* __restrict__ G,
       sweeps = sweep;
       break;
     }
+    if (big_rot[sweep & 3] == 0) {
+      sweeps = sweep + 1;
+      break;
+    }
+    if (tid == 0) big_rot[(sweep + 3) & 3] = 0;
   }
   if (tid == 0) *rounds_out = sweeps * n1;
 }
@@ -755,78 +811,122 @@ __global__ void __launch_bounds__(768) jacobi_kernel(int k, const double* __rest
   jacobi_body(k, G, log, rounds_out, TB);
 }
 
-// V = J_0 J_1 ... J_{R-1} from the rotation log of jacobi_kernel (round rho
-// rotates, in every slot t, columns (p, q) of V by (c, s) of log[rho h + t]).
-// Rows of V are independent under V <- V J, so CTA b builds rows
-// [b RB, b RB + RB) in shared memory from identity rows, thread t applying
-// slot t's rotation to all of them (loads first), one barrier per round (a
-// warp barrier when one warp covers the slots).  The log is read eight
-// rounds ahead.  Writes Vout (k x k, row-major, columns = eigenvectors).
-template <int RB>
-__device__ __forceinline__ void jac_apply_v_body(int k, const float2* __restrict__ log, const int* __restrict__ rounds,
-                                                 float* __restrict__ Vout, int block) {
-  extern __shared__ float vs[];  // RB x kp
+// V = J_0 J_1 ... J_{R-1} from the rotation log (round rho rotates, in every
+// slot t, the columns of V at slot t's a- and b-index by (c, s) of
+// log[rho h + t]).  Rows of V are independent under V <- V J: one warp
+// builds one row, keeping its entries by position (circ_next) so that the
+// rotation of slot t always meets the entries at positions 2t and 2t + 1:
+// lane l holds slots l, l + 32, ... (NS of them), rotates them and passes
+// them to their next-round positions with warp shuffles (a-values one slot
+// down, b-values one slot up, with the wraps of the circle order).  The
+// warps of a CTA share the log, staged through shared memory in chunks of
+// C rounds by cp.async (the next chunk is in flight while the current one
+// is applied; one CTA barrier per chunk), so no round waits for L2.
+// Writes row `row` of Vout (k x k, row-major, columns = eigenvectors) when
+// `row` < k; every warp of the CTA takes part in the barriers.
+constexpr int kApplyVWarps = 4;           // rows (warps) per CTA of the V build
+constexpr int kApplyVStageBytes = 49152;  // two chunks of the log
+
+__host__ __device__ inline int apply_v_chunk(int h) {
+  int c = kApplyVStageBytes / (2 * 8 * h);
+  c = c > 64 ? 64 : c;
+  return c & ~3;
+}
+
+__device__ __forceinline__ void cp_async8(void* smem, const void* gmem) {
+  asm volatile("cp.async.ca.shared.global [%0], [%1], 8;" ::"r"(static_cast<uint32_t>(__cvta_generic_to_shared(smem))),
+               "l"(gmem)
+               : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
+__device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_group 0;" ::: "memory"); }
+
+template <int NS>
+__device__ __forceinline__ void jac_apply_v_warp(int k, const float2* __restrict__ log, int R,
+                                                 float* __restrict__ Vout, int row) {
+  extern __shared__ __align__(16) float2 vstage[];  // [2][C h]
   const int kp = k + (k & 1), h = kp / 2, n1 = kp - 1;
-  const int row0 = block * RB;
-  const int t = threadIdx.x, nt = blockDim.x;
-  const bool one_warp = nt == 32;
-  for (int e = t; e < RB * kp; e += nt) {
-    const int i = e / kp, j = e - i * kp;
-    vs[e] = (row0 + i == j) ? 1.0f : 0.0f;
+  const int lane = threadIdx.x & 31;
+  const int C = apply_v_chunk(h);
+  const bool live = row < k;
+  float wa[NS], wb[NS];
+  int tc[NS];
+#pragma unroll
+  for (int j = 0; j < NS; ++j) {
+    const int t = lane + 32 * j;
+    tc[j] = min(t, h - 1);
+    wa[j] = (t < h && circ_index(2 * t, 0, n1) == row) ? 1.0f : 0.0f;
+    wb[j] = (t < h && circ_index(2 * t + 1, 0, n1) == row) ? 1.0f : 0.0f;
   }
-  __syncthreads();
-  const int R = *rounds;
-  const bool on = t < h;
-  float2 cur[8], nxt[8];
+  auto stage = [&](int c0, int b) {
+    const int cnt = min(C, R - c0) * h;
+    const float2* src = log + static_cast<size_t>(c0) * h;
+    float2* dst = vstage + b * C * h;
+    for (int e = threadIdx.x; e < cnt; e += blockDim.x) cp_async8(dst + e, src + e);
+    cp_async_commit();
+  };
+  const int last_lane = (h - 1) & 31, last_j = (h - 1) >> 5;
+  int b = 0;
+  if (R > 0) stage(0, 0);
+  for (int c0 = 0; c0 < R; c0 += C, b ^= 1) {
+    cp_async_wait_all();
+    __syncthreads();  // chunk c0 visible to all warps; the other buffer is free
+    if (c0 + C < R) stage(c0 + C, b ^ 1);
+    const float2* cs = vstage + b * C * h;
+    const int cnt = min(C, R - c0);
+    for (int rr = 0; rr < cnt; ++rr) {
+      float na[NS], nb[NS];
 #pragma unroll
-  for (int u = 0; u < 8; ++u)
-    cur[u] = (on && u < R) ? log[static_cast<size_t>(u) * h + t] : make_float2(1.0f, 0.0f);
-  int rm = 0;  // round mod n1
-  for (int g = 0; g < R; g += 8) {
+      for (int j = 0; j < NS; ++j) {
+        const float2 r = cs[rr * h + tc[j]];
+        na[j] = __fmaf_rn(-r.y, wb[j], __fmul_rn(r.x, wa[j]));
+        nb[j] = __fmaf_rn(r.y, wa[j], __fmul_rn(r.x, wb[j]));
+      }
+      if (h >= 2) {
 #pragma unroll
-    for (int u = 0; u < 8; ++u)
-      nxt[u] = (on && g + 8 + u < R) ? log[static_cast<size_t>(g + 8 + u) * h + t] : make_float2(1.0f, 0.0f);
-#pragma unroll
-    for (int u = 0; u < 8; ++u) {
-      if (g + u < R) {
-        if (on) {
-          int a, b;
-          circle_ab(t, rm, n1, a, b);
-          const int p = min(a, b), q = max(a, b);
-          const float c = cur[u].x, sn = cur[u].y;
-          float x[RB], y[RB];
-#pragma unroll
-          for (int i = 0; i < RB; ++i) {
-            x[i] = vs[i * kp + p];
-            y[i] = vs[i * kp + q];
+        for (int j = 0; j < NS; ++j) {
+          const float dn = __shfl_down_sync(0xffffffffu, na[j], 1);
+          const float wrap_a = __shfl_sync(0xffffffffu, na[(j + 1 < NS) ? j + 1 : j], 0);
+          const float up = __shfl_up_sync(0xffffffffu, nb[j], 1);
+          const float wrap_b = __shfl_sync(0xffffffffu, nb[(j > 0) ? j - 1 : j], 31);
+          float a2 = (lane == 31) ? wrap_a : dn;  // a_t <- a_{t+1}
+          float b2 = (lane == 0) ? wrap_b : up;   // b_t <- b_{t-1}
+          if (j == 0 && lane == 0) {
+            a2 = na[0];  // position 0 stays
+            b2 = dn;     // b_0 <- a_1
           }
-#pragma unroll
-          for (int i = 0; i < RB; ++i) {
-            vs[i * kp + p] = __fmaf_rn(-sn, y[i], __fmul_rn(c, x[i]));
-            vs[i * kp + q] = __fmaf_rn(sn, x[i], __fmul_rn(c, y[i]));
-          }
+          if (j == last_j && lane == last_lane) a2 = nb[j];  // a_{h-1} <- b_{h-1}
+          wa[j] = a2;
+          wb[j] = b2;
         }
-        if (++rm == n1) rm = 0;
-        if (one_warp)
-          __syncwarp();
-        else
-          __syncthreads();
+      } else {
+#pragma unroll
+        for (int j = 0; j < NS; ++j) {
+          wa[j] = na[j];
+          wb[j] = nb[j];
+        }
       }
     }
-#pragma unroll
-    for (int u = 0; u < 8; ++u) cur[u] = nxt[u];
+    __syncthreads();  // every warp is done with buffer b before it is refilled
   }
-  __syncthreads();
-  for (int e = t; e < RB * k; e += nt) {
-    const int i = e / k, j = e - i * k;
-    if (row0 + i < k) Vout[static_cast<size_t>(row0 + i) * k + j] = vs[i * kp + j];
+  if (!live) return;
+  const int rf = (n1 > 0) ? R % n1 : 0;
+#pragma unroll
+  for (int j = 0; j < NS; ++j) {
+    const int t = lane + 32 * j;
+    if (t < h) {
+      const int ia = circ_index(2 * t, rf, n1), ib = circ_index(2 * t + 1, rf, n1);
+      if (ia < k) Vout[static_cast<size_t>(row) * k + ia] = wa[j];
+      if (ib < k) Vout[static_cast<size_t>(row) * k + ib] = wb[j];
+    }
   }
 }
 
-template <int RB>
-__global__ void __launch_bounds__(512) jac_apply_v_kernel(int k, const float2* __restrict__ log,
-                                                          const int* __restrict__ rounds, float* __restrict__ Vout) {
-  jac_apply_v_body<RB>(k, log, rounds, Vout, blockIdx.x);
+template <int NS>
+__global__ void __launch_bounds__(32 * kApplyVWarps) jac_apply_v_kernel(int k, const float2* __restrict__ log,
+                                                                       const int* __restrict__ rounds,
+                                                                       float* __restrict__ Vout) {
+  jac_apply_v_warp<NS>(k, log, *rounds, Vout, blockIdx.x * kApplyVWarps + (threadIdx.x >> 5));
 }
 
 // The same Jacobi method for k too large for one SM's shared memory: A (two
@@ -834,13 +934,16 @@ __global__ void __launch_bounds__(512) jac_apply_v_kernel(int k, const float2* _
 // global memory (they stay in L2); every round is spread over the whole grid
 // of a cooperative launch and ends with one grid barrier.  Shared data is
 // read with ld.global.cg (L2, never a stale L1 line written by another SM in
-// an earlier round).  The last h threads of the grid are the rotation
-// threads, addressing their loads a round ahead as in jacobi_kernel; the
-// others take the pair blocks in folded-triangle order.  With `log` the
-// rotations go there and V is multiplied out afterwards (jac_apply_v_kernel);
-// without it V^T is rotated in every round here.  Layout of `scratch`: A
-// buffers (2 kp (kp + 1) floats), V^T (kp x ldv), the rotations (c, s)[2][h],
-// last_rot.
+// an earlier round).  A is stored by index (the upper triangle of A itself)
+// and the slots' indices are recomputed every round.  The last h threads of
+// the grid are the rotation threads, addressing their loads a round ahead;
+// the others take the pair blocks in folded-triangle order.  The sweeps end
+// by the rules of jacobi_kernel (last_rot, big_rot).  With `log` the
+// rotations go there in the slots' (a, b) orientation and V is multiplied
+// out afterwards (jac_apply_v_kernel); without it V^T is rotated in every
+// round here.  Layout of `scratch`: A buffers (2 kp (kp + 1) floats), V^T
+// (kp x ldv), the rotations (c, s)[2][h] in (min, max) index orientation,
+// last_rot, big_rot[4].
 __global__ void __launch_bounds__(kJacGridThreads) jacobi_grid_kernel(int k, const double* __restrict__ G,
                                                          float* __restrict__ Vout, float* scratch,
                                                          float2* __restrict__ log, int* __restrict__ rounds_out) {
@@ -853,6 +956,7 @@ __global__ void __launch_bounds__(kJacGridThreads) jacobi_grid_kernel(int k, con
   float* const Vt = M0 + 2 * kp * ld;
   float2* const rots = reinterpret_cast<float2*>(Vt + kp * ldv);  // [2][h]; 8-byte aligned (offsets are even)
   volatile int* const last_rot = reinterpret_cast<int*>(rots + 2 * h);
+  volatile int* const big_rot = last_rot + 1;  // [4], as in jacobi_kernel
   const int gtid = static_cast<int>(blockIdx.x * blockDim.x + threadIdx.x);
   const int gnt = static_cast<int>(gridDim.x * blockDim.x);
   const bool defer = log != nullptr;
@@ -870,7 +974,10 @@ __global__ void __launch_bounds__(kJacGridThreads) jacobi_grid_kernel(int k, con
       const int i = e / ldv, j = e - i * ldv;
       Vt[e] = (i == j) ? 1.0f : 0.0f;
     }
-  if (gtid == 0) *last_rot = -1;
+  if (gtid == 0) {
+    *last_rot = -1;
+    big_rot[0] = big_rot[1] = big_rot[2] = big_rot[3] = 0;
+  }
   const int workers = gnt - h;  // the host launches at least h + 1 threads
   const int rt = gtid - workers;
   const bool rotor = rt >= 0;
@@ -882,9 +989,14 @@ __global__ void __launch_bounds__(kJacGridThreads) jacobi_grid_kernel(int k, con
     circle_ab(rt, 0, n1, pa, pb);
     const int p = min(pa, pb), q = max(pa, pb);
     float c, s;
-    if (jac_rot(__ldcg(M0 + p * ld + p), __ldcg(M0 + q * ld + q), __ldcg(M0 + p * ld + q), c, s)) *last_rot = 0;
+    const float app = __ldcg(M0 + p * ld + p), aqq = __ldcg(M0 + q * ld + q), apq = __ldcg(M0 + p * ld + q);
+    if (jac_rot(app, aqq, apq, c, s)) {
+      *last_rot = 0;
+      if (jac_big(app, aqq, apq)) big_rot[0] = 1;
+    }
     rots[rt] = make_float2(c, s);
-    if (defer) log[rt] = make_float2(c, s);
+    // the log takes the slot's (a, b) orientation: (c, -s) when a > b
+    if (defer) log[rt] = make_float2(c, (pa < pb) ? s : -s);
   }
   int rix[10], rfl = 0;
   auto plan = [&](int r) {
@@ -979,11 +1091,21 @@ __global__ void __launch_bounds__(kJacGridThreads) jacobi_grid_kernel(int k, con
         const int sx = pfirst ? sp : sq, sy = pfirst ? sq : sp;
         jac_block(ev[6], ev[7], ev[8], ev[9], R1.x, R1.y, R2.x, R2.y, n00, n01, n10, n11);
         const float apq = (same && sx != sy && R1.y != 0.0f) ? 0.0f : (sx ? (sy ? n11 : n10) : (sy ? n01 : n00));
+        const int swn = (r + 1 == n1) ? sweep + 1 : sweep;
         float c, s;
-        if (jac_rot(app, aqq, apq, c, s)) *last_rot = (r + 1 == n1) ? sweep + 1 : sweep;
+        const bool did = jac_rot(app, aqq, apq, c, s);
+        const bool large = did && jac_big(app, aqq, apq);
+        // one store per warp to the shared flags (stores of many threads to
+        // one L2 line queue up behind each other)
+        const unsigned am = __activemask();
+        const unsigned any_did = __ballot_sync(am, did), any_large = __ballot_sync(am, large);
+        if ((threadIdx.x & 31) == __ffs(am) - 1) {
+          if (any_did) *last_rot = swn;
+          if (any_large) big_rot[swn & 3] = 1;
+        }
         rots[(buf ^ 1) * h + rt] = make_float2(c, s);
         if (defer && sweep * n1 + r + 1 < kJacSweeps * n1)
-          log[static_cast<size_t>(sweep * n1 + r + 1) * h + rt] = make_float2(c, s);
+          log[static_cast<size_t>(sweep * n1 + r + 1) * h + rt] = make_float2(c, a_low ? s : -s);
         plan(r + 1 == n1 ? 0 : r + 1);
       }
       grid.sync();
@@ -993,6 +1115,11 @@ __global__ void __launch_bounds__(kJacGridThreads) jacobi_grid_kernel(int k, con
       sweeps = sweep;
       break;
     }
+    if (big_rot[sweep & 3] == 0) {
+      sweeps = sweep + 1;
+      break;
+    }
+    if (gtid == 0) big_rot[(sweep + 3) & 3] = 0;
   }
   if (defer) {
     if (gtid == 0) *rounds_out = sweeps * n1;
@@ -1253,27 +1380,27 @@ int chol_inv(int64_t k, const double* G, float* Rinv, double* scratch, int32_t* 
   return cuda_status(cudaGetLastError());
 }
 
-// V from the rotation log: RB rows of V per CTA, RB the smallest power of
-// two that keeps the grid within one CTA per SM (a round's latency grows
-// with the rows each slot thread rotates, and the rows are independent).
+// V from the rotation log: one warp per row of V, NS = ceil(h / 32) slots
+// per lane.
+template <int NS>
+int launch_apply_v(int k, const float2* log, const int* rounds, float* V, cudaStream_t st) {
+  const unsigned grid = static_cast<unsigned>((k + kApplyVWarps - 1) / kApplyVWarps);
+  jac_apply_v_kernel<NS><<<grid, 32 * kApplyVWarps, kApplyVStageBytes, st>>>(k, log, rounds, V);
+  return cuda_status(cudaGetLastError());
+}
+
 int apply_v_log(int64_t k, const float2* log, const int* rounds, float* V, cudaStream_t st) {
   const int64_t kp = k + (k & 1);
-  const int h = static_cast<int>(kp / 2);
-  const int threads = (h + 31) / 32 * 32;
-  const int sms = sm_count();
-  if (sms <= 0) return SHG_ERR_CUDA;
-  int rb = 1;
-  while (rb < 8 && (k + rb - 1) / rb > sms) rb *= 2;
-  const unsigned grid = static_cast<unsigned>((k + rb - 1) / rb);
-  const size_t smem = static_cast<size_t>(rb) * kp * sizeof(float);
+  const int ns = static_cast<int>((kp / 2 + 31) / 32);
   const int kk = static_cast<int>(k);
-  switch (rb) {
-    case 1: jac_apply_v_kernel<1><<<grid, threads, smem, st>>>(kk, log, rounds, V); break;
-    case 2: jac_apply_v_kernel<2><<<grid, threads, smem, st>>>(kk, log, rounds, V); break;
-    case 4: jac_apply_v_kernel<4><<<grid, threads, smem, st>>>(kk, log, rounds, V); break;
-    default: jac_apply_v_kernel<8><<<grid, threads, smem, st>>>(kk, log, rounds, V); break;
+  switch (ns) {
+    case 1: return launch_apply_v<1>(kk, log, rounds, V, st);
+    case 2: return launch_apply_v<2>(kk, log, rounds, V, st);
+    case 3: return launch_apply_v<3>(kk, log, rounds, V, st);
+    case 4: return launch_apply_v<4>(kk, log, rounds, V, st);
+    case 5: return launch_apply_v<5>(kk, log, rounds, V, st);
+    default: return SHG_ERR_UNSUPPORTED;
   }
-  return cuda_status(cudaGetLastError());
 }
 
 int jacobi_eig(int64_t k, const double* G, float* V, float* scratch, void* eig, cudaStream_t st) {
@@ -1492,10 +1619,11 @@ __global__ void __launch_bounds__(768) jacobi_grouped_kernel(const EigArg* __res
   jacobi_body(a.k, a.G, a.log, a.rounds, a.TB);
 }
 
-__global__ void __launch_bounds__(512) apply_v_grouped_kernel(const EigArg* __restrict__ args) {
+template <int NS>
+__global__ void __launch_bounds__(32 * kApplyVWarps) apply_v_grouped_kernel(const EigArg* __restrict__ args) {
   const EigArg a = args[blockIdx.y];
-  if (static_cast<int>(blockIdx.x) * 8 >= a.k) return;
-  jac_apply_v_body<8>(a.k, a.log, a.rounds, a.V, blockIdx.x);
+  if (static_cast<int>(blockIdx.x) * kApplyVWarps >= a.k) return;  // the whole CTA
+  jac_apply_v_warp<NS>(a.k, a.log, *a.rounds, a.V, blockIdx.x * kApplyVWarps + (threadIdx.x >> 5));
 }
 
 __global__ void rayleigh_grouped_kernel(const EigArg* __restrict__ args) {
@@ -1600,8 +1728,13 @@ int eig_grouped(const EigArg* d, int n, int kmax, int pmax, int tbmax, cudaStrea
     return SHG_ERR_CUDA;
   jacobi_grouped_kernel<<<n, groups * 128, smem, st>>>(d);
   if (cudaGetLastError() != cudaSuccess) return SHG_ERR_CUDA;
-  constexpr int rb = 8;
-  apply_v_grouped_kernel<<<dim3((kmax + rb - 1) / rb, n), (h + 31) / 32 * 32, rb * kp * sizeof(float), st>>>(d);
+  const dim3 vgrid((kmax + kApplyVWarps - 1) / kApplyVWarps, n);
+  switch ((h + 31) / 32) {
+    case 1: apply_v_grouped_kernel<1><<<vgrid, 32 * kApplyVWarps, kApplyVStageBytes, st>>>(d); break;
+    case 2: apply_v_grouped_kernel<2><<<vgrid, 32 * kApplyVWarps, kApplyVStageBytes, st>>>(d); break;
+    case 3: apply_v_grouped_kernel<3><<<vgrid, 32 * kApplyVWarps, kApplyVStageBytes, st>>>(d); break;
+    default: return SHG_ERR_UNSUPPORTED;
+  }
   if (cudaGetLastError() != cudaSuccess) return SHG_ERR_CUDA;
   rayleigh_grouped_kernel<<<dim3((kmax + kRayVecs - 1) / kRayVecs, n), rayleigh_threads(kmax),
                             kRayVecs * kmax * sizeof(double), st>>>(d);
