@@ -239,7 +239,8 @@ int cholqr2_grouped(const Plan& P, uint8_t* tb, size_t gram1, size_t simt1, size
     rc = gram_grouped(reinterpret_cast<const GramArg*>(tb + (pass == 0 ? gram1 : gram2)), n, P.kmax, rows_max, st,
                       pass == 1);
     if (rc != SHG_OK) return rc;
-    rc = chol_small_grouped(reinterpret_cast<const CholArg*>(tb + P.cholS), P.n_cholS, P.kmax_small, flags, st);
+    rc = chol_small_grouped(reinterpret_cast<const CholArg*>(tb + P.cholS), P.n_cholS, P.kmax_small, flags, st,
+                            pass == 1);
     if (rc != SHG_OK) return rc;
     rc = chol_panel_grouped(reinterpret_cast<const CholArg*>(tb + P.cholP), P.n_cholP, P.kmax_panel, flags, st);
     if (rc != SHG_OK) return rc;

@@ -98,7 +98,7 @@ int zero_grouped(const ZeroArg* d, int n, long long max_bytes, cudaStream_t st);
 int gaussian_grouped(uint64_t seed, const GaussArg* d, int n, long long max_elems, cudaStream_t st);
 int gram_grouped(const GramArg* d, int n, int kmax, int mmax, cudaStream_t st, bool plain = false);
 // Cholesky + R^-1 of n problems with k <= chol_smem_kmax() (one CTA each).
-int chol_small_grouped(const CholArg* d, int n, int kmax, int32_t* flags, cudaStream_t st);
+int chol_small_grouped(const CholArg* d, int n, int kmax, int32_t* flags, cudaStream_t st, bool working);
 // The same beyond shared memory, in 32-column panels (all panels of all problems).
 int chol_panel_grouped(const CholArg* d, int n, int kmax, int32_t* flags, cudaStream_t st);
 int chol_smem_kmax();

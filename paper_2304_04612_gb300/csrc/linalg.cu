@@ -208,10 +208,12 @@ __device__ __forceinline__ float2 df_sub_mul(float2 a, float2 t, float2 b) {
   const float2 s = two_sum(a.x, -p);
   return two_sum(s.x, __fadd_rn(s.y, __fsub_rn(a.y, pe)));
 }
-// 1 / d for d > 0: r = fl(1 / d.hi), e = 1 - d r in double-float (1 - p is
-// exact, p being within an ulp of 1), then r + r e
+// 1 / d for d > 0 (d.hi a normal float): r ~ 1 / d.hi (the hardware
+// approximation, relative error below 2^-22), e = 1 - d r in double-float
+// (1 - p is exact, p being within a few ulps of 1), then r + r e, whose
+// error is of order e^2
 __device__ __forceinline__ float2 df_recip(float2 d) {
-  const float r = 1.0f / d.x;
+  const float r = __fdividef(1.0f, d.x);
   const float p = __fmul_rn(d.x, r);
   float pe = __fmaf_rn(d.x, r, -p);
   pe = __fmaf_rn(d.y, r, pe);
@@ -248,9 +250,15 @@ __device__ __forceinline__ float2 df_recip(float2 d) {
 // positive normal float so that R stays finite.
 // SMEM selects the shared-memory layout at compile time, so that the
 // accesses compile to shared loads and stores rather than generic ones.
-template <bool SMEM>
+// F32 (shared-memory layout only): the elimination in working precision,
+// for a well-conditioned G (the second pass of CholeskyQR2, whose input
+// already has nearly orthonormal columns): the hi word of each pair alone,
+// one multiply and one FMA per element; the lo words stay zero, so the
+// inverse below reads the same layout.
+template <bool SMEM, bool F32 = false>
 __device__ __forceinline__ void chol_inv_body(int k, const double* __restrict__ G, float* __restrict__ Xf,
                                               double* scratch, int* flags, const float2* __restrict__ pre_dinv) {
+  static_assert(SMEM || !F32, "the working-precision elimination runs in shared memory");
   extern __shared__ __align__(16) float2 smd[];
   float2* a = SMEM ? smd : reinterpret_cast<float2*>(scratch);
   float* rf = reinterpret_cast<float*>(a + k * k);
@@ -276,7 +284,7 @@ __device__ __forceinline__ void chol_inv_body(int k, const double* __restrict__ 
     if (j >= i) {
       const double g = G[e] * sigma;
       v.x = static_cast<float>(g);
-      v.y = static_cast<float>(g - static_cast<double>(v.x));
+      v.y = F32 ? 0.0f : static_cast<float>(g - static_cast<double>(v.x));
     }
     a[e] = v;
   }
@@ -288,7 +296,7 @@ __device__ __forceinline__ void chol_inv_body(int k, const double* __restrict__ 
       d = make_float2(1.17549435e-38f, 0.0f);
       a[j * k + j] = d;
     }
-    dinv[j] = df_recip(d);
+    dinv[j] = F32 ? make_float2(1.0f / d.x, 0.0f) : df_recip(d);
   };
   if (tid == 0) pivot(0);
   __syncthreads();
@@ -306,12 +314,18 @@ __device__ __forceinline__ void chol_inv_body(int k, const double* __restrict__ 
           if (r == i) continue;  // odd n: the middle row has no second half
         }
         const int l = j + 1 + r, lp = j + 1 + cc;
-        const float2 t = df_mul(rowj[l], dj);
-        a[l * k + lp] = df_sub_mul(a[l * k + lp], t, rowj[lp]);
+        if (F32) {
+          float* el = reinterpret_cast<float*>(a + l * k + lp);
+          *el = __fmaf_rn(-__fmul_rn(rowj[l].x, dj.x), rowj[lp].x, *el);
+        } else {
+          const float2 t = df_mul(rowj[l], dj);
+          a[l * k + lp] = df_sub_mul(a[l * k + lp], t, rowj[lp]);
+        }
+        // thread 0 (folded row 0, element 0) owns a[j+1][j+1]: its pivot
+        // right away, ahead of the rest of its elements
+        if (tid == 0 && c == 0) pivot(j + 1);
       }
     }
-    // thread 0 (folded row 0, element 0) owns a[j+1][j+1]
-    if (tid == 0) pivot(j + 1);
     __syncthreads();
   }
   }
@@ -384,11 +398,11 @@ __device__ __forceinline__ void chol_inv_body(int k, const double* __restrict__ 
   }
 }
 
-template <bool SMEM>
+template <bool SMEM, bool F32>
 __global__ void __launch_bounds__(1024) chol_inv_kernel(int k, const double* __restrict__ G, float* __restrict__ Xf,
                                                        double* scratch, int* flags,
                                                        const float2* __restrict__ pre_dinv) {
-  chol_inv_body<SMEM>(k, G, Xf, scratch, flags, pre_dinv);
+  chol_inv_body<SMEM, F32>(k, G, Xf, scratch, flags, pre_dinv);
 }
 
 // The same elimination for k too large for shared memory, in panels of
@@ -635,33 +649,19 @@ __host__ __device__ inline size_t jac_cta_floats(int kp) {
   return static_cast<size_t>(2 * kp) + 2 * static_cast<size_t>(kp) * (kp + 1);
 }
 
-__device__ __forceinline__ void jacobi_body(int k, const double* __restrict__ G, float2* __restrict__ log,
-                                            int* __restrict__ rounds_out, int TB) {
-  extern __shared__ __align__(16) float smf[];
+// The rounds of jacobi_body for CTAs whose block threads own ITEMS pair
+// blocks each (the loops over the blocks unroll exactly, with no tests for
+// absent ones).  Returns the number of sweeps that count.
+template <int ITEMS>
+__device__ __forceinline__ int jacobi_sweeps(int k, float* smf, float2* __restrict__ log, int TB, int* last_rot_p,
+                                             int* big_rot) {
   const int kp = k + (k & 1);
   const int h = kp / 2, n1 = kp - 1;
   const int ld = kp + 1;
   float2* rots = reinterpret_cast<float2*>(smf);  // [2][h]
   float* const M0 = smf + 4 * h;
-  __shared__ int last_rot;
-  __shared__ int big_rot[4];
-  __shared__ double red[32];
-  __shared__ double dmax;
-  const int tid = threadIdx.x, nt = blockDim.x;
-  diag_max(k, G, red, &dmax);
-  if (tid == 0) {
-    last_rot = -1;
-    big_rot[0] = big_rot[1] = big_rot[2] = big_rot[3] = 0;
-  }
-  __syncthreads();
-  const double sigma = ldexp(1.0, -((dmax > 0.0) ? ilogb(dmax) : 0));
-  for (int e = tid; e < kp * kp; e += nt) {
-    const int x = e / kp, y = e - x * kp;
-    if (y >= x) {
-      const int i = circ_index(x, 0, n1), j = circ_index(y, 0, n1);
-      M0[x * ld + y] = (i < k && j < k) ? static_cast<float>(G[min(i, j) * k + max(i, j)] * sigma) : 0.0f;
-    }
-  }
+  int& last_rot = *last_rot_p;
+  const int tid = threadIdx.x;
   const int nblk = h * (h + 1) / 2;
   // warps 0, 4, 8, ...: rotation warps (then idle); the others: block warps
   const int warp = tid >> 5, lane = tid & 31;
@@ -674,10 +674,10 @@ __device__ __forceinline__ void jacobi_body(int k, const double* __restrict__ G,
   // src = offset of element (2t, 2u) (bit 30: diagonal block), dst0 / dst1 =
   // the next-round offsets of rows 2t / 2t + 1 at columns 2u (low half) and
   // 2u + 1 (high half)
-  int it[kJacItems], src[kJacItems];
-  uint32_t dst0[kJacItems], dst1[kJacItems];
+  int it[ITEMS], src[ITEMS];
+  uint32_t dst0[ITEMS], dst1[ITEMS];
 #pragma unroll
-  for (int c = 0; c < kJacItems; ++c) {
+  for (int c = 0; c < ITEMS; ++c) {
     it[c] = -1;
     src[c] = 0;
     dst0[c] = dst1[c] = 0u;
@@ -734,12 +734,12 @@ __device__ __forceinline__ void jacobi_body(int k, const double* __restrict__ G,
       if (is_blk) {
         // two blocks at a time: all loads, then all arithmetic and stores
 #pragma unroll
-        for (int g = 0; g < kJacItems; g += 2) {
+        for (int g = 0; g < ITEMS; g += 2) {
           float v[2][4];
           float2 R1[2], R2[2];
 #pragma unroll
           for (int e = 0; e < 2; ++e) {
-            if (it[g + e] >= 0) {
+            if (g + e < ITEMS && it[g + e] >= 0) {
               const int s0 = src[g + e] & 0xffff;
               const bool dg = (src[g + e] >> 30) != 0;
               R1[e] = cur[it[g + e] & 0xffff];
@@ -752,7 +752,7 @@ __device__ __forceinline__ void jacobi_body(int k, const double* __restrict__ G,
           }
 #pragma unroll
           for (int e = 0; e < 2; ++e) {
-            if (it[g + e] >= 0) {
+            if (g + e < ITEMS && it[g + e] >= 0) {
               float n00, n01, n10, n11;
               jac_block(v[e][0], v[e][1], v[e][2], v[e][3], R1[e].x, R1[e].y, R2[e].x, R2[e].y, n00, n01, n10, n11);
               if ((src[g + e] >> 30) != 0) {
@@ -802,6 +802,47 @@ __device__ __forceinline__ void jacobi_body(int k, const double* __restrict__ G,
       break;
     }
     if (tid == 0) big_rot[(sweep + 3) & 3] = 0;
+  }
+  return sweeps;
+}
+
+
+__device__ __forceinline__ void jacobi_body(int k, const double* __restrict__ G, float2* __restrict__ log,
+                                            int* __restrict__ rounds_out, int TB) {
+  extern __shared__ __align__(16) float smf[];
+  const int kp = k + (k & 1);
+  const int h = kp / 2, n1 = kp - 1;
+  const int ld = kp + 1;
+  float* const M0 = smf + 4 * h;
+  __shared__ int last_rot;
+  __shared__ int big_rot[4];
+  __shared__ double red[32];
+  __shared__ double dmax;
+  const int tid = threadIdx.x, nt = blockDim.x;
+  diag_max(k, G, red, &dmax);
+  if (tid == 0) {
+    last_rot = -1;
+    big_rot[0] = big_rot[1] = big_rot[2] = big_rot[3] = 0;
+  }
+  __syncthreads();
+  const double sigma = ldexp(1.0, -((dmax > 0.0) ? ilogb(dmax) : 0));
+  for (int e = tid; e < kp * kp; e += nt) {
+    const int x = e / kp, y = e - x * kp;
+    if (y >= x) {
+      const int i = circ_index(x, 0, n1), j = circ_index(y, 0, n1);
+      M0[x * ld + y] = (i < k && j < k) ? static_cast<float>(G[min(i, j) * k + max(i, j)] * sigma) : 0.0f;
+    }
+  }
+  __syncthreads();
+  const int nblk = h * (h + 1) / 2;
+  int sweeps = 0;
+  switch ((nblk + TB - 1) / TB) {
+    case 1: sweeps = jacobi_sweeps<1>(k, smf, log, TB, &last_rot, big_rot); break;
+    case 2: sweeps = jacobi_sweeps<2>(k, smf, log, TB, &last_rot, big_rot); break;
+    case 3: sweeps = jacobi_sweeps<3>(k, smf, log, TB, &last_rot, big_rot); break;
+    case 4: sweeps = jacobi_sweeps<4>(k, smf, log, TB, &last_rot, big_rot); break;
+    case 5: sweeps = jacobi_sweeps<5>(k, smf, log, TB, &last_rot, big_rot); break;
+    default: sweeps = jacobi_sweeps<kJacItems>(k, smf, log, TB, &last_rot, big_rot); break;
   }
   if (tid == 0) *rounds_out = sweeps * n1;
 }
@@ -1343,17 +1384,19 @@ int gram_f64(int64_t m, int64_t k, const float* X, int64_t ldx, double* G, cudaS
   return cuda_status(cudaGetLastError());
 }
 
-int chol_inv(int64_t k, const double* G, float* Rinv, double* scratch, int32_t* flags, cudaStream_t st) {
+int chol_inv(int64_t k, const double* G, float* Rinv, double* scratch, int32_t* flags, cudaStream_t st,
+             bool working) {
   if (k > 1024) return SHG_ERR_UNSUPPORTED;
   const size_t need = static_cast<size_t>(2 * k * k) * sizeof(double);
   const int in_smem = smem_fits(need);
   const int threads = block_threads(k * k / 4);
   const int kk = static_cast<int>(k);
   if (in_smem) {
-    if (cudaFuncSetAttribute(chol_inv_kernel<true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                             static_cast<int>(need)) != cudaSuccess)
+    auto kern = working ? chol_inv_kernel<true, true> : chol_inv_kernel<true, false>;
+    if (cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, static_cast<int>(need)) !=
+        cudaSuccess)
       return SHG_ERR_CUDA;
-    chol_inv_kernel<true><<<1, threads, need, st>>>(kk, G, Rinv, scratch, flags, nullptr);
+    kern<<<1, threads, need, st>>>(kk, G, Rinv, scratch, flags, nullptr);
     return cuda_status(cudaGetLastError());
   }
   // matrix in global memory: scale, then panels of kCholPanel columns (one
@@ -1376,7 +1419,7 @@ int chol_inv(int64_t k, const double* G, float* Rinv, double* scratch, int32_t* 
       if (cudaGetLastError() != cudaSuccess) return SHG_ERR_CUDA;
     }
   }
-  chol_inv_kernel<false><<<1, threads, 0, st>>>(kk, G, Rinv, scratch, flags, dinv_g);
+  chol_inv_kernel<false, false><<<1, threads, 0, st>>>(kk, G, Rinv, scratch, flags, dinv_g);
   return cuda_status(cudaGetLastError());
 }
 
@@ -1519,9 +1562,10 @@ int cholqr2(int64_t m, int64_t k, float* X, int64_t ldx, float* T, int64_t ldt, 
   for (int pass = 0; pass < 2; ++pass) {
     float* dst = (pass == 0) ? T : X;
     const int64_t ldd = (pass == 0) ? ldt : ldx;
-    // the first pass in doubled precision, the second in working precision
+    // the first pass in doubled precision, the second (on nearly
+    // orthonormal columns) in working precision
     if ((rc = gram_f64(m, k, src, lds, w.G, st, pass == 1))) return rc;
-    if ((rc = chol_inv(k, w.G, w.Rf, w.chol, flags, st))) return rc;
+    if ((rc = chol_inv(k, w.G, w.Rf, w.chol, flags, st, pass == 1))) return rc;
     if (min_pivot) {
       pivot_ratio_kernel<<<1, 256, 0, st>>>(static_cast<int>(k), w.G, w.Rf,
                                             reinterpret_cast<unsigned long long*>(min_pivot));
@@ -1562,9 +1606,10 @@ __global__ void __launch_bounds__(256) gram_grouped_kernel(const GramArg* __rest
   gram_body<PLAIN>(a.m, a.k, a.X, a.ldx, a.G, kGramChunkRows, blockIdx.y, blockIdx.x, chunk);
 }
 
+template <bool F32>
 __global__ void __launch_bounds__(1024) chol_small_grouped_kernel(const CholArg* __restrict__ args, int* flags) {
   const CholArg a = args[blockIdx.x];
-  chol_inv_body<true>(a.k, a.G, a.Rf, a.scratch, flags, nullptr);
+  chol_inv_body<true, F32>(a.k, a.G, a.Rf, a.scratch, flags, nullptr);
 }
 
 __global__ void __launch_bounds__(256) chol_scale_grouped_kernel(const CholArg* __restrict__ args) {
@@ -1664,14 +1709,15 @@ int gram_grouped(const GramArg* d, int n, int kmax, int mmax, cudaStream_t st, b
 
 int chol_smem_kmax() { return 113; }
 
-int chol_small_grouped(const CholArg* d, int n, int kmax, int32_t* flags, cudaStream_t st) {
+int chol_small_grouped(const CholArg* d, int n, int kmax, int32_t* flags, cudaStream_t st, bool working) {
   if (n <= 0) return SHG_OK;
   const size_t need = static_cast<size_t>(2 * kmax * kmax) * sizeof(double);
   if (!smem_fits(need)) return SHG_ERR_UNSUPPORTED;
-  if (cudaFuncSetAttribute(chol_small_grouped_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                           static_cast<int>(need)) != cudaSuccess)
+  auto kern = working ? chol_small_grouped_kernel<true> : chol_small_grouped_kernel<false>;
+  if (cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, static_cast<int>(need)) !=
+      cudaSuccess)
     return SHG_ERR_CUDA;
-  chol_small_grouped_kernel<<<n, block_threads(static_cast<int64_t>(kmax) * kmax / 4), need, st>>>(d, flags);
+  kern<<<n, block_threads(static_cast<int64_t>(kmax) * kmax / 4), need, st>>>(d, flags);
   return cuda_status(cudaGetLastError());
 }
 

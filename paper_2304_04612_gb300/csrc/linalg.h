@@ -22,8 +22,10 @@ SmallWs small_ws(void* base, int64_t k);
 // (about 2^-48 relative error), or with `plain` FP32 sums of 32-row slabs
 // (working precision: the second CholeskyQR pass).
 int gram_f64(int64_t m, int64_t k, const float* X, int64_t ldx, double* G, cudaStream_t st, bool plain = false);
-// Rinv = FP32(R^-1) with G = R^T R (FP64, upper Cholesky).
-int chol_inv(int64_t k, const double* G, float* Rinv, double* scratch, int32_t* flags, cudaStream_t st);
+// Rinv = FP32(R^-1) with G = R^T R (upper Cholesky), eliminated in
+// double-float, or with `working` (a well-conditioned G, k <= 113) in FP32.
+int chol_inv(int64_t k, const double* G, float* Rinv, double* scratch, int32_t* flags, cudaStream_t st,
+             bool working = false);
 // Eigenvectors V (k x k FP32, columns) of the symmetric matrix whose upper
 // triangle is G.  `scratch`: jacobi_scratch_floats(k) floats; `eig`:
 // jacobi_log_bytes(k) bytes (the rotation log of the single-CTA solver; it
