@@ -594,6 +594,31 @@ __device__ __forceinline__ int circ_prev(int y, int h) {
   if ((y & 1) == 0) return (j == 0) ? 0 : (j == h - 1) ? 2 * h - 1 : 2 * (j + 1);
   return (j == 0) ? 2 : 2 * j - 1;
 }
+// Slot and partner of index x at round r of circle_ab (the inverse of the
+// pairing): x = 0 is slot 0's a-index; otherwise x is the a-index of slot
+// (x - r) mod n1 when that lies in 1 .. h - 1, else the b-index of slot
+// (r - x) mod n1.
+__device__ __forceinline__ void circ_slot(int x, int r, int n1, int& slot, int& partner) {
+  const int h = (n1 + 1) >> 1;
+  int a, b;
+  if (x == 0) {
+    slot = 0;
+    circle_ab(0, r, n1, a, b);
+    partner = b;
+    return;
+  }
+  const int ta = (x - r + n1) % n1;
+  if (ta >= 1 && ta < h) {
+    slot = ta;
+    circle_ab(ta, r, n1, a, b);
+    partner = b;
+  } else {
+    slot = (r - x + n1) % n1;
+    circle_ab(slot, r, n1, a, b);
+    partner = a;
+  }
+}
+
 // Index held by position x at round r.
 __device__ __forceinline__ int circ_index(int x, int r, int n1) {
   int a, b;
@@ -641,8 +666,7 @@ __device__ __forceinline__ int circ_index(int x, int r, int n1) {
 // each, upper triangles).  kp (kp + 1) < 2^16 (the smem_fits limit), so two
 // offsets pack into one word.
 constexpr int kJacSweeps = 40;
-constexpr int kJacGridThreads = 128;  // CTA size of the grid solver (more SMs per round)
-constexpr int kJacLogMaxK = 288;  // largest kp whose rotations are logged (13 MB at 40 sweeps)
+constexpr int kJacLogMaxK = 158;  // largest kp whose rotations are logged (the one-CTA solver's; 4 MB at 40 sweeps)
 constexpr int kJacItems = 6;  // most blocks one thread owns
 
 __host__ __device__ inline size_t jac_cta_floats(int kp) {
@@ -970,205 +994,226 @@ __global__ void __launch_bounds__(32 * kApplyVWarps) jac_apply_v_kernel(int k, c
   jac_apply_v_warp<NS>(k, log, *rounds, Vout, blockIdx.x * kApplyVWarps + (threadIdx.x >> 5));
 }
 
-// The same Jacobi method for k too large for one SM's shared memory: A (two
-// buffers, upper triangles), the rotations and, without a log, V^T live in
-// global memory (they stay in L2); every round is spread over the whole grid
-// of a cooperative launch and ends with one grid barrier.  Shared data is
-// read with ld.global.cg (L2, never a stale L1 line written by another SM in
-// an earlier round).  A is stored by index (the upper triangle of A itself)
-// and the slots' indices are recomputed every round.  The last h threads of
-// the grid are the rotation threads, addressing their loads a round ahead;
-// the others take the pair blocks in folded-triangle order.  The sweeps end
-// by the rules of jacobi_kernel (last_rot, big_rot).  With `log` the
-// rotations go there in the slots' (a, b) orientation and V is multiplied
-// out afterwards (jac_apply_v_kernel); without it V^T is rotated in every
-// round here.  Layout of `scratch`: A buffers (2 kp (kp + 1) floats), V^T
-// (kp x ldv), the rotations (c, s)[2][h] in (min, max) index orientation,
-// last_rot, big_rot[4].
-__global__ void __launch_bounds__(kJacGridThreads) jacobi_grid_kernel(int k, const double* __restrict__ G,
-                                                         float* __restrict__ Vout, float* scratch,
-                                                         float2* __restrict__ log, int* __restrict__ rounds_out) {
+// ------------------------------------------------------------ block Jacobi
+// The eigensolver for k too large for one SM's shared memory: the parallel
+// cyclic Jacobi method on blocks (a two-level form of the same method).
+// The kpb x kpb matrix (kpb = k rounded up to a multiple of 16, zero
+// padding) is split into nb = kpb / 8 blocks of 8 indices, paired by the
+// circle order of circle_ab over blocks (nb - 1 rounds per sweep).  In a
+// round, every pair of blocks (16 indices) first gets one cyclic Jacobi
+// sweep of its own 16 x 16 diagonal tile (phase 1: 15 inner rounds of 8
+// disjoint rotations, the rotations multiplied into a 16 x 16 orthogonal
+// U_p), then the whole matrix and V are transformed by the block-diagonal
+// product of the U_p (phase 2: every 16 x 16 tile (p, q) of A becomes
+// U_p^T A_pq U_q, every 16 x 16 tile of V at the columns of pair p becomes
+// V U_p).  Every index pair meets in at least one rotation per sweep, as in
+// the scalar method, and the sweeps end by its rules (no rotation at all,
+// or none above 2^-12 of the diagonal, jac_big), but a grid barrier is paid
+// per block round (twice) instead of per index round: 2 (nb - 1) barriers
+// per sweep instead of kp - 1.
+//   The grid runs groups of 256 threads (one thread per element of a 16 x 16
+//   tile, a named barrier per group, four groups per CTA); groups take the
+//   pairs of phase 1 and the tiles of phase 2 in turn.  A, V and the U_p
+//   live in global memory (they stay in L2) and are read with ld.global.cg
+//   (never a stale L1 line written by another SM).  Each phase reads and
+//   writes only its own tile, so the updates are in place.
+//   scratch (floats): A (kpb x kpb, full symmetric), V (kpb x kpb), U
+//   (npairs x 256), then the flags (any[4], big[4] as ints).
+//   Writes Vout (k x k, row-major, columns = eigenvectors).
+constexpr int kBjBlock = 8;        // indices per block
+constexpr int kBjTile = 16;        // indices per pair of blocks
+constexpr int kBjGroup = 256;      // threads per group (one per tile element)
+constexpr int kBjThreads = 1024;   // four groups per CTA
+
+__host__ __device__ inline int bj_kpb(int k) { return (k + kBjTile - 1) / kBjTile * kBjTile; }
+__host__ __device__ inline size_t bj_scratch_floats(int k) {
+  const size_t kpb = static_cast<size_t>(bj_kpb(k));
+  return 2 * kpb * kpb + (kpb / kBjTile) * kBjGroup + 64;
+}
+
+__device__ __forceinline__ void bj_group_sync(int g) {
+  asm volatile("bar.sync %0, %1;" ::"r"(g + 1), "r"(kBjGroup) : "memory");
+}
+
+// global index of local index i (0..15) of the block pair (a, b)
+__device__ __forceinline__ int bj_index(int i, int a, int b) {
+  return (i < kBjBlock) ? a * kBjBlock + i : b * kBjBlock + (i - kBjBlock);
+}
+
+__global__ void __launch_bounds__(kBjThreads) bjac_grid_kernel(int k, const double* __restrict__ G,
+                                                                float* __restrict__ Vout, float* scratch) {
   namespace cg = cooperative_groups;
   cg::grid_group grid = cg::this_grid();
-  const int kp = k + (k & 1);
-  const int h = kp / 2, n1 = kp - 1;
-  const int ld = kp + 1, ldv = (kp + 3) & ~3;
-  float* const M0 = scratch;
-  float* const Vt = M0 + 2 * kp * ld;
-  float2* const rots = reinterpret_cast<float2*>(Vt + kp * ldv);  // [2][h]; 8-byte aligned (offsets are even)
-  volatile int* const last_rot = reinterpret_cast<int*>(rots + 2 * h);
-  volatile int* const big_rot = last_rot + 1;  // [4], as in jacobi_kernel
+  const int kpb = bj_kpb(k), nb = kpb / kBjBlock, np = nb / 2, n1 = nb - 1;
+  float* const A = scratch;
+  float* const V = A + static_cast<size_t>(kpb) * kpb;
+  float* const Ub = V + static_cast<size_t>(kpb) * kpb;
+  volatile int* const any_rot = reinterpret_cast<int*>(Ub + static_cast<size_t>(np) * kBjGroup);
+  volatile int* const big_rot = any_rot + 4;
+  const int g = threadIdx.x / kBjGroup, gt = threadIdx.x % kBjGroup;
+  const int ti = gt >> 4, tj = gt & 15;
+  const int gid = blockIdx.x * (kBjThreads / kBjGroup) + g;
+  const int ngroups = gridDim.x * (kBjThreads / kBjGroup);
   const int gtid = static_cast<int>(blockIdx.x * blockDim.x + threadIdx.x);
   const int gnt = static_cast<int>(gridDim.x * blockDim.x);
-  const bool defer = log != nullptr;
+  __shared__ float S[4][2][kBjTile][kBjTile + 1];  // tile (two buffers in phase 1)
+  __shared__ float U[4][2][kBjTile][kBjTile + 1];  // U_p (two buffers in phase 1), U_p and U_q in phase 2
+  __shared__ float2 rc[4][kBjTile / 2];            // inner rotations (c, s)
+  __shared__ int ptab[kBjTile - 1][kBjTile];       // inner round ir, index x: slot | partner << 4
+  __shared__ int pair_of[kBjTile - 1][kBjTile / 2];  // inner round ir, slot t: smaller | larger << 4
+  __shared__ int flag[4][2];                       // any, big of this group's pair
   __shared__ double red[32];
   __shared__ double dmax;
   diag_max(k, G, red, &dmax);  // every block forms the scale itself
   __syncthreads();
   const double sigma = ldexp(1.0, -((dmax > 0.0) ? ilogb(dmax) : 0));
-  for (int e = gtid; e < kp * kp; e += gnt) {
-    const int i = e / kp, j = e - i * kp;
-    if (j >= i) M0[i * ld + j] = (j < k) ? static_cast<float>(G[i * k + j] * sigma) : 0.0f;
+  for (long long e = gtid; e < static_cast<long long>(kpb) * kpb; e += gnt) {
+    const int i = static_cast<int>(e / kpb), j = static_cast<int>(e - static_cast<long long>(i) * kpb);
+    A[e] = (i < k && j < k) ? static_cast<float>(G[min(i, j) * k + max(i, j)] * sigma) : 0.0f;
+    V[e] = (i == j) ? 1.0f : 0.0f;
   }
-  if (!defer)
-    for (int e = gtid; e < kp * ldv; e += gnt) {
-      const int i = e / ldv, j = e - i * ldv;
-      Vt[e] = (i == j) ? 1.0f : 0.0f;
+  if (gtid < 8) any_rot[gtid] = 0;  // any_rot[0..3], big_rot[0..3]
+  // the fixed pairing of the inner rounds (circle order on 16 indices)
+  for (int e = threadIdx.x; e < (kBjTile - 1) * kBjTile; e += blockDim.x) {
+    const int ir = e / kBjTile, x = e % kBjTile;
+    int sl, pt;
+    circ_slot(x, ir, kBjTile - 1, sl, pt);
+    ptab[ir][x] = sl | (pt << 4);
+    if (x < kBjTile / 2) {
+      int a, b;
+      circle_ab(x, ir, kBjTile - 1, a, b);
+      pair_of[ir][x] = min(a, b) | (max(a, b) << 4);
     }
-  if (gtid == 0) {
-    *last_rot = -1;
-    big_rot[0] = big_rot[1] = big_rot[2] = big_rot[3] = 0;
   }
-  const int workers = gnt - h;  // the host launches at least h + 1 threads
-  const int rt = gtid - workers;
-  const bool rotor = rt >= 0;
-  const int srcA = (rt <= 0) ? 0 : min(rt + 1, h - 1);
-  const int srcB = (rt >= 1) ? rt - 1 : (h >= 2 ? 1 : 0);
   grid.sync();
-  if (rotor) {
-    int pa, pb;
-    circle_ab(rt, 0, n1, pa, pb);
-    const int p = min(pa, pb), q = max(pa, pb);
-    float c, s;
-    const float app = __ldcg(M0 + p * ld + p), aqq = __ldcg(M0 + q * ld + q), apq = __ldcg(M0 + p * ld + q);
-    if (jac_rot(app, aqq, apq, c, s)) {
-      *last_rot = 0;
-      if (jac_big(app, aqq, apq)) big_rot[0] = 1;
-    }
-    rots[rt] = make_float2(c, s);
-    // the log takes the slot's (a, b) orientation: (c, -s) when a > b
-    if (defer) log[rt] = make_float2(c, (pa < pb) ? s : -s);
-  }
-  int rix[10], rfl = 0;
-  auto plan = [&](int r) {
-    int pa, pb, aA, bA, aB, bB;
-    circle_ab(rt, r + 1, n1, pa, pb);
-    circle_ab(srcA, r, n1, aA, bA);
-    circle_ab(srcB, r, n1, aB, bB);
-    const int pA = min(aA, bA), qA = max(aA, bA), pB = min(aB, bB), qB = max(aB, bB);
-    const int sxa = (pa == pA) ? 0 : 1, sxb = (pb == pB) ? 0 : 1;
-    const bool a_low = pa < pb;
-    const int tp = a_low ? srcA : srcB, tq = a_low ? srcB : srcA;
-    const int pp = a_low ? pA : pB, qp = a_low ? qA : qB, pq = a_low ? pB : pA, qq = a_low ? qB : qA;
-    const int sp = a_low ? sxa : sxb, sq = a_low ? sxb : sxa;
-    const bool pfirst = tp <= tq;
-    const int p1 = pfirst ? pp : pq, q1 = pfirst ? qp : qq, p2 = pfirst ? pq : pp, q2 = pfirst ? qq : qp;
-    rix[0] = pp * ld + pp;
-    rix[1] = pp * ld + qp;
-    rix[2] = qp * ld + qp;
-    rix[3] = pq * ld + pq;
-    rix[4] = pq * ld + qq;
-    rix[5] = qq * ld + qq;
-    rix[6] = sym_at(p1, p2, ld);
-    rix[7] = sym_at(p1, q2, ld);
-    rix[8] = sym_at(q1, p2, ld);
-    rix[9] = sym_at(q1, q2, ld);
-    rfl = sp | (sq << 1) | (pfirst ? 4 : 0) | (tp == tq ? 8 : 0) | (a_low ? 16 : 0);
-  };
-  if (rotor) plan(0);
-  grid.sync();
-  const int nblk = h * (h + 1) / 2;
-  const int nv4 = ldv >> 2;
-  int buf = 0, sweeps = kJacSweeps;
+  int sweeps = kJacSweeps;
   for (int sweep = 0; sweep < kJacSweeps; ++sweep) {
     for (int r = 0; r < n1; ++r) {
-      const float* A = M0 + buf * (kp * ld);
-      float* B = M0 + (buf ^ 1) * (kp * ld);
-      const float2* cur = rots + buf * h;
-      if (!rotor) {
-        // J^T A J by pair blocks (t, u), u >= t, folded-triangle order
-        for (int bi = gtid; bi < nblk; bi += workers) {
-          const int i = bi / (h + 1), j = bi - i * (h + 1);
-          const int t = (j < h - i) ? i : h - 1 - i, u = (j < h - i) ? i + j : j - 1;
-          int a1, b1, a2, b2;
-          circle_ab(t, r, n1, a1, b1);
-          circle_ab(u, r, n1, a2, b2);
-          const int p1 = min(a1, b1), q1 = max(a1, b1), p2 = min(a2, b2), q2 = max(a2, b2);
-          const int i00 = sym_at(p1, p2, ld), i01 = sym_at(p1, q2, ld), i10 = sym_at(q1, p2, ld),
-                    i11 = sym_at(q1, q2, ld);
-          const float2 R1 = __ldcg(cur + t), R2 = __ldcg(cur + u);
-          float n00, n01, n10, n11;
-          jac_block(__ldcg(A + i00), __ldcg(A + i01), __ldcg(A + i10), __ldcg(A + i11), R1.x, R1.y, R2.x, R2.y, n00,
-                    n01, n10, n11);
-          if (t == u) {
-            if (R1.y != 0.0f) n01 = 0.0f;
-            n10 = n01;
+      // ---------------------------------------------- phase 1: pair tiles
+      // (one group per CTA, so that the pairs' groups have SMs to
+      // themselves: an inner round is a chain of dependent steps)
+      for (int p = (g == 0) ? static_cast<int>(blockIdx.x) : np; p < np; p += gridDim.x) {
+        int a, b;
+        circle_ab(p, r, n1, a, b);
+        const int gi = bj_index(ti, a, b), gj = bj_index(tj, a, b);
+        S[g][0][ti][tj] = __ldcg(A + static_cast<size_t>(gi) * kpb + gj);
+        U[g][0][ti][tj] = (ti == tj) ? 1.0f : 0.0f;
+        if (gt < 2) flag[g][gt] = 0;
+        bj_group_sync(g);
+        int cb = 0;
+        for (int ir = 0; ir < kBjTile - 1; ++ir) {
+          // the pairing of this inner round is fixed (circle order on the 16
+          // local indices): slots and partners of this thread's row and
+          // column, read while the rotations are computed
+          const int ei = ptab[ir][ti], ej = ptab[ir][tj];
+          const int si = ei & 15, pi = ei >> 4, sj = ej & 15, pj = ej >> 4;
+          if (gt < kBjTile / 2) {
+            const int pq = pair_of[ir][gt];
+            const int pp = pq & 15, qq = pq >> 4;
+            const float app = S[g][cb][pp][pp], aqq = S[g][cb][qq][qq], apq = S[g][cb][pp][qq];
+            float c, s;
+            if (jac_rot(app, aqq, apq, c, s)) {
+              flag[g][0] = 1;
+              if (jac_big(app, aqq, apq)) flag[g][1] = 1;
+            }
+            rc[g][gt] = make_float2(c, s);
           }
-          B[i00] = n00;
-          B[i01] = n01;
-          B[i10] = n10;
-          B[i11] = n11;
-        }
-        // V <- V J on the transposed rows p, q (when not deferred)
-        if (!defer)
-          for (int w = gtid; w < h * nv4; w += workers) {
-            const int t = w / nv4, c4 = (w - t * nv4) * 4;
-            int a1, b1;
-            circle_ab(t, r, n1, a1, b1);
-            const float2 R = __ldcg(cur + t);
-            float4* vp = reinterpret_cast<float4*>(Vt + min(a1, b1) * ldv + c4);
-            float4* vq = reinterpret_cast<float4*>(Vt + max(a1, b1) * ldv + c4);
-            const float4 x = __ldcg(vp), y = __ldcg(vq);
-            *vp = make_float4(__fmaf_rn(-R.y, y.x, __fmul_rn(R.x, x.x)), __fmaf_rn(-R.y, y.y, __fmul_rn(R.x, x.y)),
-                              __fmaf_rn(-R.y, y.z, __fmul_rn(R.x, x.z)), __fmaf_rn(-R.y, y.w, __fmul_rn(R.x, x.w)));
-            *vq = make_float4(__fmaf_rn(R.y, x.x, __fmul_rn(R.x, y.x)), __fmaf_rn(R.y, x.y, __fmul_rn(R.x, y.y)),
-                              __fmaf_rn(R.y, x.z, __fmul_rn(R.x, y.z)), __fmaf_rn(R.y, x.w, __fmul_rn(R.x, y.w)));
+          bj_group_sync(g);
+          {
+            // (ti, tj) of J^T S J and of U J: the smaller index x of a pair
+            // becomes c x - s y, the larger y becomes s x + c y
+            const float s00 = S[g][cb][ti][tj], s10 = S[g][cb][pi][tj];
+            const float s01 = S[g][cb][ti][pj], s11 = S[g][cb][pi][pj];
+            const float u0 = U[g][cb][ti][tj], u1 = U[g][cb][ti][pj];
+            const float2 Ri = rc[g][si], Rj = rc[g][sj];
+            const float sgi = (ti > pi) ? Ri.y : -Ri.y, sgj = (tj > pj) ? Rj.y : -Rj.y;
+            const float l0 = __fmaf_rn(sgi, s10, __fmul_rn(Ri.x, s00));
+            const float l1 = __fmaf_rn(sgi, s11, __fmul_rn(Ri.x, s01));
+            float v = __fmaf_rn(sgj, l1, __fmul_rn(Rj.x, l0));
+            if (pj == ti && Rj.y != 0.0f) v = 0.0f;  // the pair's own off-diagonal, annihilated
+            S[g][cb ^ 1][ti][tj] = v;
+            U[g][cb ^ 1][ti][tj] = __fmaf_rn(sgj, u1, __fmul_rn(Rj.x, u0));
           }
-      } else {
-        // rotation of slot rt for round r + 1 from the same old A
-        float ev[10];
-#pragma unroll
-        for (int z = 0; z < 10; ++z) ev[z] = __ldcg(A + rix[z]);
-        const float2 RA = __ldcg(cur + srcA), RB = __ldcg(cur + srcB);
-        const int sp = rfl & 1, sq = (rfl >> 1) & 1;
-        const bool pfirst = (rfl & 4) != 0, same = (rfl & 8) != 0, a_low = (rfl & 16) != 0;
-        const float2 Rp = a_low ? RA : RB, Rq = a_low ? RB : RA;
-        float n00, n01, n10, n11;
-        jac_block(ev[0], ev[1], ev[1], ev[2], Rp.x, Rp.y, Rp.x, Rp.y, n00, n01, n10, n11);
-        const float app = sp ? n11 : n00;
-        jac_block(ev[3], ev[4], ev[4], ev[5], Rq.x, Rq.y, Rq.x, Rq.y, n00, n01, n10, n11);
-        const float aqq = sq ? n11 : n00;
-        const float2 R1 = pfirst ? Rp : Rq, R2 = pfirst ? Rq : Rp;
-        const int sx = pfirst ? sp : sq, sy = pfirst ? sq : sp;
-        jac_block(ev[6], ev[7], ev[8], ev[9], R1.x, R1.y, R2.x, R2.y, n00, n01, n10, n11);
-        const float apq = (same && sx != sy && R1.y != 0.0f) ? 0.0f : (sx ? (sy ? n11 : n10) : (sy ? n01 : n00));
-        const int swn = (r + 1 == n1) ? sweep + 1 : sweep;
-        float c, s;
-        const bool did = jac_rot(app, aqq, apq, c, s);
-        const bool large = did && jac_big(app, aqq, apq);
-        // one store per warp to the shared flags (stores of many threads to
-        // one L2 line queue up behind each other)
-        const unsigned am = __activemask();
-        const unsigned any_did = __ballot_sync(am, did), any_large = __ballot_sync(am, large);
-        if ((threadIdx.x & 31) == __ffs(am) - 1) {
-          if (any_did) *last_rot = swn;
-          if (any_large) big_rot[swn & 3] = 1;
+          bj_group_sync(g);
+          cb ^= 1;
         }
-        rots[(buf ^ 1) * h + rt] = make_float2(c, s);
-        if (defer && sweep * n1 + r + 1 < kJacSweeps * n1)
-          log[static_cast<size_t>(sweep * n1 + r + 1) * h + rt] = make_float2(c, a_low ? s : -s);
-        plan(r + 1 == n1 ? 0 : r + 1);
+        Ub[static_cast<size_t>(p) * kBjGroup + gt] = U[g][cb][ti][tj];
+        A[static_cast<size_t>(gi) * kpb + gj] = S[g][cb][ti][tj];  // the pair's own tile, rotated
+        if (gt == 0) {
+          const int sw = sweep & 3;
+          if (flag[g][0]) any_rot[sw] = 1;
+          if (flag[g][1]) big_rot[sw] = 1;
+        }
+        bj_group_sync(g);
       }
       grid.sync();
-      buf ^= 1;
+      // ---------------------------------------------- phase 2: A and V tiles
+      const int nA = np * (np - 1) / 2, nV = (kpb / kBjTile) * np;
+      for (int w = gid; w < nA + nV; w += ngroups) {
+        if (w < nA) {
+          // tile (p, q), p < q, of the pairs' index sets: U_p^T A_pq U_q
+          // (the diagonal tiles came out of phase 1)
+          int p = 0, rem = w;
+          while (rem >= np - 1 - p) {
+            rem -= np - 1 - p;
+            ++p;
+          }
+          const int q = p + 1 + rem;
+          int pa, pb, qa, qb;
+          circle_ab(p, r, n1, pa, pb);
+          circle_ab(q, r, n1, qa, qb);
+          const int gi = bj_index(ti, pa, pb), gj = bj_index(tj, qa, qb);
+          S[g][0][ti][tj] = __ldcg(A + static_cast<size_t>(gi) * kpb + gj);
+          U[g][0][ti][tj] = __ldcg(Ub + static_cast<size_t>(p) * kBjGroup + gt);
+          U[g][1][ti][tj] = __ldcg(Ub + static_cast<size_t>(q) * kBjGroup + gt);
+          bj_group_sync(g);
+          float t = 0.0f;
+#pragma unroll
+          for (int z = 0; z < kBjTile; ++z) t = __fmaf_rn(S[g][0][ti][z], U[g][1][z][tj], t);
+          S[g][1][ti][tj] = t;
+          bj_group_sync(g);
+          float o = 0.0f;
+#pragma unroll
+          for (int z = 0; z < kBjTile; ++z) o = __fmaf_rn(U[g][0][z][ti], S[g][1][z][tj], o);
+          A[static_cast<size_t>(gi) * kpb + gj] = o;
+          A[static_cast<size_t>(gj) * kpb + gi] = o;
+        } else {
+          // V rows c0 .. c0 + 15 at the columns of pair p: V U_p
+          const int w2 = w - nA;
+          const int p = w2 % np, c0 = (w2 / np) * kBjTile;
+          int pa, pb;
+          circle_ab(p, r, n1, pa, pb);
+          const int row = c0 + ti;
+          S[g][0][ti][tj] = __ldcg(V + static_cast<size_t>(row) * kpb + bj_index(tj, pa, pb));
+          U[g][0][ti][tj] = __ldcg(Ub + static_cast<size_t>(p) * kBjGroup + gt);
+          bj_group_sync(g);
+          float o = 0.0f;
+#pragma unroll
+          for (int z = 0; z < kBjTile; ++z) o = __fmaf_rn(S[g][0][ti][z], U[g][0][z][tj], o);
+          V[static_cast<size_t>(row) * kpb + bj_index(tj, pa, pb)] = o;
+        }
+        bj_group_sync(g);
+      }
+      grid.sync();
     }
-    if (*last_rot < sweep) {
+    const int sw = sweep & 3;
+    if (!any_rot[sw]) {
       sweeps = sweep;
       break;
     }
-    if (big_rot[sweep & 3] == 0) {
+    if (!big_rot[sw]) {
       sweeps = sweep + 1;
       break;
     }
-    if (gtid == 0) big_rot[(sweep + 3) & 3] = 0;
-  }
-  if (defer) {
-    if (gtid == 0) *rounds_out = sweeps * n1;
-  } else {
-    for (int e = gtid; e < k * k; e += gnt) {
-      const int i = e / k, j = e - i * k;
-      Vout[e] = __ldcg(Vt + j * ldv + i);
+    if (gtid == 0) {
+      any_rot[(sweep + 3) & 3] = 0;
+      big_rot[(sweep + 3) & 3] = 0;
     }
+  }
+  (void)sweeps;
+  for (long long e = gtid; e < static_cast<long long>(k) * k; e += gnt) {
+    const int i = static_cast<int>(e / k), j = static_cast<int>(e - static_cast<long long>(i) * k);
+    Vout[e] = __ldcg(V + static_cast<size_t>(i) * kpb + j);
   }
 }
 
@@ -1309,8 +1354,9 @@ int smem_fits(size_t bytes) { return bytes <= 200 * 1024 ? 1 : 0; }
 // and V^T (kp x ldv).
 size_t jacobi_scratch_floats(int64_t k) {
   const int64_t kp = k + (k & 1), ldv = (kp + 3) & ~int64_t(3);
-  // matrices, then (grid version) the rotations (c, s)[2][kp/2] and the flag
-  return static_cast<size_t>(2 * kp * (kp + 1) + kp * ldv + 2 * kp + 64);
+  // one-CTA spill area (matrices, rotations, flags) or the block solver's
+  return std::max(static_cast<size_t>(2 * kp * (kp + 1) + kp * ldv + 2 * kp + 64),
+                  bj_scratch_floats(static_cast<int>(k)));
 }
 
 // One-CTA kernels: about `work` elements per barrier phase, a few per thread.
@@ -1472,35 +1518,33 @@ int jacobi_eig(int64_t k, const double* G, float* V, float* scratch, void* eig, 
     if (cudaGetLastError() != cudaSuccess) return SHG_ERR_CUDA;
     return apply_v_log(k, log, rounds, V, st);
   } else {
-    // too large for one SM: the whole grid works on every round (cooperative
-    // launch); h rotation threads plus the block threads
-    // occupancy of the grid kernel, queried once (host threads may race to
-    // it; every one of them stores the same value)
+    // too large for one SM: the block solver on the whole grid (cooperative
+    // launch), groups of 256 threads over the pair tiles and the tiles of A
+    // and V.  Occupancy queried once (host threads may race to it; every one
+    // of them stores the same value).
     static std::atomic<int> cached_bps{0};
     int blocks_per_sm = cached_bps.load(std::memory_order_relaxed);
     if (blocks_per_sm == 0) {
-      if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&blocks_per_sm, jacobi_grid_kernel, kJacGridThreads, 0) !=
+      if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&blocks_per_sm, bjac_grid_kernel, kBjThreads, 0) !=
           cudaSuccess)
         return SHG_ERR_CUDA;
       cached_bps.store(blocks_per_sm, std::memory_order_relaxed);
     }
     const int sms = sm_count();
     if (sms <= 0 || blocks_per_sm <= 0) return SHG_ERR_CUDA;
-    long long want = (static_cast<long long>(nblk) + h + kJacGridThreads - 1) / kJacGridThreads;
+    const long long kpb = bj_kpb(static_cast<int>(k)), np = kpb / kBjTile;
+    const long long units = std::max(np, np * (np - 1) / 2 + (kpb / kBjTile) * np);
+    const int per_cta = kBjThreads / kBjGroup;
+    long long want = (units + per_cta - 1) / per_cta;
     if (want > static_cast<long long>(sms) * blocks_per_sm) want = static_cast<long long>(sms) * blocks_per_sm;
-    if (want * kJacGridThreads < h + 32) return SHG_ERR_UNSUPPORTED;
-    const bool defer = eig && jacobi_log_bytes(k) > 0;
     int kk = static_cast<int>(k);
     const double* g = G;
     float* v = V;
     float* sc = scratch;
-    int* rounds = defer ? static_cast<int*>(eig) : nullptr;
-    float2* log = defer ? reinterpret_cast<float2*>(static_cast<uint8_t*>(eig) + 256) : nullptr;
-    void* argv[] = {&kk, &g, &v, &sc, &log, &rounds};
-    if (cudaLaunchCooperativeKernel(reinterpret_cast<const void*>(jacobi_grid_kernel), dim3(static_cast<unsigned>(want)),
-                                    dim3(kJacGridThreads), argv, 0, st) != cudaSuccess)
+    void* argv[] = {&kk, &g, &v, &sc};
+    if (cudaLaunchCooperativeKernel(reinterpret_cast<const void*>(bjac_grid_kernel), dim3(static_cast<unsigned>(want)),
+                                    dim3(kBjThreads), argv, 0, st) != cudaSuccess)
       return SHG_ERR_CUDA;
-    if (defer) return apply_v_log(k, log, rounds, V, st);
   }
   return cuda_status(cudaGetLastError());
 }

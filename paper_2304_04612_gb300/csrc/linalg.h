@@ -29,7 +29,8 @@ int chol_inv(int64_t k, const double* G, float* Rinv, double* scratch, int32_t* 
 // Eigenvectors V (k x k FP32, columns) of the symmetric matrix whose upper
 // triangle is G.  `scratch`: jacobi_scratch_floats(k) floats; `eig`:
 // jacobi_log_bytes(k) bytes (the rotation log of the single-CTA solver; it
-// is used when non-null and non-zero in size, else the grid solver runs).
+// is used when non-null and non-zero in size, else the block solver runs on
+// the whole grid).
 int jacobi_eig(int64_t k, const double* G, float* V, float* scratch, void* eig, cudaStream_t st);
 size_t jacobi_log_bytes(int64_t k);
 int rayleigh_sort(int64_t k, int64_t p, const double* G, const float* V, double* lam, float* S, float* Up,
