@@ -529,25 +529,28 @@ __device__ __forceinline__ void jac_block(float m00, float m01, float m10, float
   n11 = __fmaf_rn(s2, l10, __fmul_rn(c2, l11));
 }
 
-// Rotation annihilating a_pq of the 2 x 2 block [[app, apq], [apq, aqq]]
-// (t = tan of the angle, the smaller root); skipped (c = 1, s = 0) when
-// |a_pq| <= 2^-23 sqrt(|a_pp a_qq|), compared as squares.  The rotation
-// maps (p, q) to (c p - s q, s p + c q).  sqrt(1 + tau^2) is formed as
-// x rsqrt(x) (no rounding-exact square root is needed: any t gives an
-// orthogonal rotation, and one that leaves a tiny a_pq is caught by later
-// sweeps); beyond |tau| = 2^20 t = 1 / (2 tau).  c = 1/sqrt(1 + t^2) and
-// s = t c keep c^2 + s^2 = 1 to rounding whatever the accuracy of t.
+// Rotation annihilating a_pq of the 2 x 2 block [[app, apq], [apq, aqq]];
+// skipped (c = 1, s = 0) when |a_pq| <= 2^-23 sqrt(|a_pp a_qq|) (compared as
+// squares) or |a_pq| <= 2^-60.  The rotation maps (p, q) to
+// (c p - s q, s p + c q).  It is the rotation of the smaller angle,
+// t = tan = sign(tau) / (|tau| + sqrt(1 + tau^2)), tau = d / (2 a_pq),
+// d = a_qq - a_pp, written without tau: with r = sqrt(d^2 + 4 a_pq^2),
+// c = (r + |d|) / sqrt(2 r (r + |d|)) and |s| = 2 |a_pq| / sqrt(2 r (r + |d|)),
+// so that the dependent chain holds two reciprocal square roots (each about
+// forty cycles) and no division.  The inputs are entries of a matrix scaled
+// to a largest diagonal in [1, 2), so d^2 + 4 a_pq^2 neither overflows nor,
+// with |a_pq| > 2^-60, underflows.  c^2 + s^2 = 1 to rounding.
 __device__ __forceinline__ bool jac_rot(float app, float aqq, float apq, float& c, float& s) {
-  c = 1.0f;
-  s = 0.0f;
-  if (!(apq * apq > 0x1p-46f * fabsf(app * aqq)) || !(fabsf(apq) > 1e-30f)) return false;
-  const float tau = __fdividef(aqq - app, 2.0f * apq);
-  const float w = fabsf(tau);
-  const float x = fmaf(w, w, 1.0f);
-  const float t = (w < 0x1p20f) ? __fdividef(1.0f, w + x * rsqrtf(x)) : __fdividef(0.5f, w);
-  c = rsqrtf(fmaf(t, t, 1.0f));
-  s = copysignf(t, tau) * c;
-  return true;
+  const bool did = (apq * apq > 0x1p-46f * fabsf(app * aqq)) && (fabsf(apq) > 0x1p-60f);
+  const float d = aqq - app, a2 = 2.0f * apq;
+  const float h = fmaf(d, d, a2 * a2);
+  const float r = h * rsqrtf(h);
+  const float u = r + fabsf(d);
+  const float inv = rsqrtf(2.0f * r * u);
+  const float ss = fabsf(a2) * inv;
+  c = did ? u * inv : 1.0f;
+  s = did ? (((d < 0.0f) != (apq < 0.0f)) ? -ss : ss) : 0.0f;
+  return did;
 }
 
 // A rotation counts as large when |a_pq| > 2^-12 sqrt(|a_pp a_qq|) and
@@ -1058,7 +1061,7 @@ __global__ void __launch_bounds__(kBjThreads) bjac_grid_kernel(int k, const doub
   const int gnt = static_cast<int>(gridDim.x * blockDim.x);
   __shared__ float S[4][2][kBjTile][kBjTile + 1];  // tile (two buffers in phase 1)
   __shared__ float U[4][2][kBjTile][kBjTile + 1];  // U_p (two buffers in phase 1), U_p and U_q in phase 2
-  __shared__ float2 rc[4][kBjTile / 2];            // inner rotations (c, s)
+  __shared__ float2 rc[4][2][kBjTile / 2];         // inner rotations (c, s), two rounds
   __shared__ int ptab[kBjTile - 1][kBjTile];       // inner round ir, index x: slot | partner << 4
   __shared__ int pair_of[kBjTile - 1][kBjTile / 2];  // inner round ir, slot t: smaller | larger << 4
   __shared__ int flag[4][2];                       // any, big of this group's pair
@@ -1100,39 +1103,71 @@ __global__ void __launch_bounds__(kBjThreads) bjac_grid_kernel(int k, const doub
         U[g][0][ti][tj] = (ti == tj) ? 1.0f : 0.0f;
         if (gt < 2) flag[g][gt] = 0;
         bj_group_sync(g);
+        // rotation thread t (t < 8): the rotation of slot t for inner round
+        // 0 from the tile, then in every round the one for the next round
+        // from the current tile and the current rotations, forming the three
+        // elements it needs with the element threads' arithmetic (rotated).
+        // The pairing is fixed, so every thread reads its table entries for
+        // the next round during the current one: after a barrier only the
+        // tile and rotation loads stand before the arithmetic.
+        auto rotate = [&](float app, float aqq, float apq, float2* out) {
+          float c, s;
+          if (jac_rot(app, aqq, apq, c, s)) {
+            flag[g][0] = 1;
+            if (jac_big(app, aqq, apq)) flag[g][1] = 1;
+          }
+          *out = make_float2(c, s);
+        };
+        const bool rotor = gt < kBjTile / 2;
+        if (rotor) {
+          const int pq = pair_of[0][gt];
+          const int pp = pq & 15, qq = pq >> 4;
+          rotate(S[g][0][pp][pp], S[g][0][qq][qq], S[g][0][pp][qq], &rc[g][0][gt]);
+        }
+        bj_group_sync(g);
+        // element (x, y) of J^T S J given the round's table entries ex, ey of
+        // x and y (slot | partner << 4): the smaller index of a pair becomes
+        // c x - s y, the larger s x + c y; the pair's own off-diagonal is
+        // annihilated
+        auto rotated = [](const float (*Sc)[kBjTile + 1], const float2* R, int x, int y, int ex, int ey) {
+          const int px = ex >> 4, py = ey >> 4;
+          const float s00 = Sc[x][y], s10 = Sc[px][y], s01 = Sc[x][py], s11 = Sc[px][py];
+          const float2 Rx = R[ex & 15], Ry = R[ey & 15];
+          const float sgx = (x > px) ? Rx.y : -Rx.y, sgy = (y > py) ? Ry.y : -Ry.y;
+          const float l0 = __fmaf_rn(sgx, s10, __fmul_rn(Rx.x, s00));
+          const float l1 = __fmaf_rn(sgx, s11, __fmul_rn(Rx.x, s01));
+          const float v = __fmaf_rn(sgy, l1, __fmul_rn(Ry.x, l0));
+          return (py == x && Ry.y != 0.0f) ? 0.0f : v;
+        };
+        int eti = ptab[0][ti], etj = ptab[0][tj];
+        int rpq = rotor ? pair_of[1][gt] : 0;
+        int epp = rotor ? ptab[0][rpq & 15] : 0, eqq = rotor ? ptab[0][rpq >> 4] : 0;
         int cb = 0;
         for (int ir = 0; ir < kBjTile - 1; ++ir) {
-          // the pairing of this inner round is fixed (circle order on the 16
-          // local indices): slots and partners of this thread's row and
-          // column, read while the rotations are computed
-          const int ei = ptab[ir][ti], ej = ptab[ir][tj];
-          const int si = ei & 15, pi = ei >> 4, sj = ej & 15, pj = ej >> 4;
-          if (gt < kBjTile / 2) {
-            const int pq = pair_of[ir][gt];
-            const int pp = pq & 15, qq = pq >> 4;
-            const float app = S[g][cb][pp][pp], aqq = S[g][cb][qq][qq], apq = S[g][cb][pp][qq];
-            float c, s;
-            if (jac_rot(app, aqq, apq, c, s)) {
-              flag[g][0] = 1;
-              if (jac_big(app, aqq, apq)) flag[g][1] = 1;
-            }
-            rc[g][gt] = make_float2(c, s);
+          const float(*Sc)[kBjTile + 1] = S[g][cb];
+          const float2* R = rc[g][cb];
+          // the next round's entries (independent of this round's data)
+          const int nx = (ir + 1 < kBjTile - 1) ? ir + 1 : ir;
+          const int eti_n = ptab[nx][ti], etj_n = ptab[nx][tj];
+          const int rpq_n = (rotor && ir + 2 < kBjTile - 1) ? pair_of[ir + 2][gt] : 0;
+          if (rotor && ir + 1 < kBjTile - 1) {
+            const int pp = rpq & 15, qq = rpq >> 4;
+            rotate(rotated(Sc, R, pp, pp, epp, epp), rotated(Sc, R, qq, qq, eqq, eqq), rotated(Sc, R, pp, qq, epp, eqq),
+                   &rc[g][cb ^ 1][gt]);
           }
-          bj_group_sync(g);
+          S[g][cb ^ 1][ti][tj] = rotated(Sc, R, ti, tj, eti, etj);
           {
-            // (ti, tj) of J^T S J and of U J: the smaller index x of a pair
-            // becomes c x - s y, the larger y becomes s x + c y
-            const float s00 = S[g][cb][ti][tj], s10 = S[g][cb][pi][tj];
-            const float s01 = S[g][cb][ti][pj], s11 = S[g][cb][pi][pj];
-            const float u0 = U[g][cb][ti][tj], u1 = U[g][cb][ti][pj];
-            const float2 Ri = rc[g][si], Rj = rc[g][sj];
-            const float sgi = (ti > pi) ? Ri.y : -Ri.y, sgj = (tj > pj) ? Rj.y : -Rj.y;
-            const float l0 = __fmaf_rn(sgi, s10, __fmul_rn(Ri.x, s00));
-            const float l1 = __fmaf_rn(sgi, s11, __fmul_rn(Ri.x, s01));
-            float v = __fmaf_rn(sgj, l1, __fmul_rn(Rj.x, l0));
-            if (pj == ti && Rj.y != 0.0f) v = 0.0f;  // the pair's own off-diagonal, annihilated
-            S[g][cb ^ 1][ti][tj] = v;
-            U[g][cb ^ 1][ti][tj] = __fmaf_rn(sgj, u1, __fmul_rn(Rj.x, u0));
+            const float2 Rj = R[etj & 15];
+            const int pj = etj >> 4;
+            const float sgj = (tj > pj) ? Rj.y : -Rj.y;
+            U[g][cb ^ 1][ti][tj] = __fmaf_rn(sgj, U[g][cb][ti][pj], __fmul_rn(Rj.x, U[g][cb][ti][tj]));
+          }
+          eti = eti_n;
+          etj = etj_n;
+          if (rotor && ir + 2 < kBjTile - 1) {
+            rpq = rpq_n;
+            epp = ptab[ir + 1][rpq_n & 15];
+            eqq = ptab[ir + 1][rpq_n >> 4];
           }
           bj_group_sync(g);
           cb ^= 1;
