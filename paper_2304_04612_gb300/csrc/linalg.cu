@@ -1334,12 +1334,15 @@ inline int rayleigh_threads(int k) { return std::min(256, (k + 31) / 32 * 32); }
 // threads write Up and Ups element by element.
 __device__ __forceinline__ void sort_select_body(int k, int p, const double* __restrict__ lam,
                                                  const double* __restrict__ nrm, const float* __restrict__ V,
-                                                 float* __restrict__ S, float* __restrict__ Up, float* __restrict__ Ups) {
-  extern __shared__ double sel[];          // [p] 1 / ||v||, [p] 1 / (||v|| sigma)
+                                                 float* __restrict__ S, float* __restrict__ Up, float* __restrict__ Ups,
+                                                 int a0, int a1) {
+  extern __shared__ double sel_raw[];
+  float* sel = reinterpret_cast<float*>(sel_raw);  // [p] 1 / ||v||, [p] 1 / (||v|| sigma)
   int* perm = reinterpret_cast<int*>(sel + 2 * p);  // [p] column of rank r
   // Ranks by a strict total order (a NaN counts as -inf, ties go by index),
   // so that they are a permutation of 0 .. k - 1 and every rank below p is
   // filled, whatever the values (a non-finite Y gives NaN eigenvalues).
+  // Every CTA forms them (k^2 comparisons); the first one writes S.
   auto key = [](double x) { return x == x ? x : -INFINITY; };
   for (int i = threadIdx.x; i < k; i += blockDim.x) {
     const double li = lam[i];
@@ -1351,26 +1354,29 @@ __device__ __forceinline__ void sort_select_body(int k, int p, const double* __r
     }
     if (r < p) {
       const double sg = sqrt(fmax(li, 0.0));
-      S[r] = static_cast<float>(sg);
+      if (a0 == 0) S[r] = static_cast<float>(sg);
       const double inv_n = 1.0 / nrm[i];
-      sel[r] = inv_n;
-      sel[p + r] = sg > 0.0 ? inv_n / sg : 0.0;
+      sel[r] = static_cast<float>(inv_n);
+      sel[p + r] = static_cast<float>(sg > 0.0 ? inv_n / sg : 0.0);
       perm[r] = i;
     }
   }
   __syncthreads();
-  for (int e = threadIdx.x; e < k * p; e += blockDim.x) {
+  // rows a0 .. a1 - 1 of U' (normalised columns) and U' Sigma^-1
+  for (int e = a0 * p + threadIdx.x; e < a1 * p; e += blockDim.x) {
     const int a = e / p, r = e - a * p;
-    const double v = V[a * k + perm[r]];
-    Up[e] = static_cast<float>(v * sel[r]);
-    Ups[e] = static_cast<float>(v * sel[p + r]);
+    const float v = V[a * k + perm[r]];
+    Up[e] = v * sel[r];
+    Ups[e] = v * sel[p + r];
   }
 }
 
 __global__ void sort_select_kernel(int k, int p, const double* __restrict__ lam, const double* __restrict__ nrm,
                                    const float* __restrict__ V, float* __restrict__ S, float* __restrict__ Up,
                                    float* __restrict__ Ups) {
-  sort_select_body(k, p, lam, nrm, V, S, Up, Ups);
+  const int rows = (k + gridDim.x - 1) / gridDim.x;
+  const int a0 = blockIdx.x * rows, a1 = min(k, a0 + rows);
+  sort_select_body(k, p, lam, nrm, V, S, Up, Ups, a0, a1);
 }
 
 __global__ void f32_to_f16_kernel(long long rows, long long cols, const float* __restrict__ x, long long ldx,
@@ -1595,8 +1601,12 @@ int rayleigh_sort(int64_t k, int64_t p, const double* G, const float* V, double*
   rayleigh_kernel<<<static_cast<unsigned>((k + kRayVecs - 1) / kRayVecs), rayleigh_threads(static_cast<int>(k)), rsm,
                     st>>>(static_cast<int>(k), G, V, lam, nrm);
   if (cudaGetLastError() != cudaSuccess) return SHG_ERR_CUDA;
-  sort_select_kernel<<<1, 1024, p * (2 * sizeof(double) + sizeof(int)), st>>>(static_cast<int>(k), static_cast<int>(p),
-                                                                              lam, nrm, V, S, Up, Ups);
+  // the rows of U' over several CTAs (each forms the ranks itself), about
+  // 16 rows per CTA
+  const unsigned sgrid = static_cast<unsigned>(std::max<int64_t>(1, std::min<int64_t>((k + 15) / 16, 64)));
+  sort_select_kernel<<<sgrid, 1024, p * (2 * sizeof(float) + sizeof(int)), st>>>(static_cast<int>(k),
+                                                                                 static_cast<int>(p), lam, nrm, V, S,
+                                                                                 Up, Ups);
   return cuda_status(cudaGetLastError());
 }
 
@@ -1758,7 +1768,7 @@ __global__ void rayleigh_grouped_kernel(const EigArg* __restrict__ args) {
 
 __global__ void sort_select_grouped_kernel(const EigArg* __restrict__ args) {
   const EigArg a = args[blockIdx.x];
-  sort_select_body(a.k, a.p, a.lam, a.lam + a.k, a.V, a.S, a.Up, a.Ups);
+  sort_select_body(a.k, a.p, a.lam, a.lam + a.k, a.V, a.S, a.Up, a.Ups, 0, a.k);
 }
 
 int grid_for(long long work, int per_block) {
@@ -1864,7 +1874,7 @@ int eig_grouped(const EigArg* d, int n, int kmax, int pmax, int tbmax, cudaStrea
   rayleigh_grouped_kernel<<<dim3((kmax + kRayVecs - 1) / kRayVecs, n), rayleigh_threads(kmax),
                             kRayVecs * kmax * sizeof(double), st>>>(d);
   if (cudaGetLastError() != cudaSuccess) return SHG_ERR_CUDA;
-  sort_select_grouped_kernel<<<n, 1024, pmax * (2 * sizeof(double) + sizeof(int)), st>>>(d);
+  sort_select_grouped_kernel<<<n, 1024, pmax * (2 * sizeof(float) + sizeof(int)), st>>>(d);
   return cuda_status(cudaGetLastError());
 }
 
