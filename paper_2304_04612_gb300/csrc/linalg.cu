@@ -405,6 +405,121 @@ __global__ void __launch_bounds__(1024) chol_inv_kernel(int k, const double* __r
   chol_inv_body<SMEM, F32>(k, G, Xf, scratch, flags, pre_dinv);
 }
 
+// R^-1 for k beyond shared memory (after the panel elimination), by 32 x 32
+// blocks over several CTAs instead of one CTA walking the whole matrix in
+// global memory:
+//   rinv_prep_kernel: R in FP32, padded to kb = 32 ceil(k / 32): the strict
+//     upper triangle R_il = a_il / R_ii from the unscaled rows, the diagonal
+//     holding 1 / R_ii (the square root of the pivot reciprocal), padding
+//     rows and columns those of the identity.
+//   rinv_diag_kernel: the inverse D_I of every diagonal block (a warp per
+//     block, a lane per column, back-substitution: X_cc = 1 / R_cc,
+//     X_ic = -(1 / R_ii) sum_{l = i+1 .. c} R_il X_lc).
+//   rinv_block_kernel: block column J of X = R^-1 (a CTA per block column, a
+//     thread per element of a 32 x 32 block): X_JJ = D_J, then for
+//     I = J - 1 .. 0, X_IJ = -D_I sum_{L = I+1 .. J} R_IL X_LJ, the R blocks
+//     of a step loaded together (up to kRinvStage at once).  Writes columns
+//     32 J .. 32 J + 31 of Xf (k x k, row-major) times 2^-e (the power-of-4
+//     scale of the factorisation), zero below the diagonal.
+// The rounding is that of the one-CTA inverse (blocks of 32 instead of 16).
+constexpr int kRinvB = 32;
+constexpr int kRinvStage = 8;
+
+__global__ void __launch_bounds__(256) rinv_prep_kernel(int k, int kb, const float2* __restrict__ a,
+                                                        const float2* __restrict__ dinv, float* __restrict__ R) {
+  __shared__ float rs;
+  const int i = blockIdx.y;
+  if (threadIdx.x == 0)
+    rs = (i < k) ? static_cast<float>(sqrt(static_cast<double>(dinv[i].x) + static_cast<double>(dinv[i].y))) : 1.0f;
+  __syncthreads();
+  const float r = rs;
+  for (int l = blockIdx.x * blockDim.x + threadIdx.x; l < kb; l += gridDim.x * blockDim.x) {
+    float v = 0.0f;
+    if (i < k && l < k) {
+      if (l > i) {
+        const float2 x = a[static_cast<size_t>(i) * k + l];
+        v = __fmaf_rn(x.y, r, __fmul_rn(x.x, r));
+      } else if (l == i) {
+        v = r;
+      }
+    } else if (l == i) {
+      v = 1.0f;
+    }
+    R[static_cast<size_t>(i) * kb + l] = v;
+  }
+}
+
+__global__ void __launch_bounds__(32) rinv_diag_kernel(int kb, const float* __restrict__ R, float* __restrict__ D) {
+  __shared__ float Rb[kRinvB][kRinvB + 1], Xb[kRinvB][kRinvB + 1];
+  const int I = blockIdx.x, c = threadIdx.x;
+  for (int r = 0; r < kRinvB; ++r) Rb[r][c] = R[static_cast<size_t>(I * kRinvB + r) * kb + I * kRinvB + c];
+  __syncwarp();
+  for (int i = kRinvB - 1; i >= 0; --i) {
+    float x = 0.0f;
+    if (c == i) {
+      x = Rb[i][i];
+    } else if (c > i) {
+      float s = 0.0f;
+      for (int l = i + 1; l <= c; ++l) s = fmaf(Rb[i][l], Xb[l][c], s);
+      x = -s * Rb[i][i];
+    }
+    Xb[i][c] = x;  // lane c reads only its own column of Xb
+  }
+  __syncwarp();
+  for (int r = 0; r < kRinvB; ++r) D[(static_cast<size_t>(I) * kRinvB + r) * kRinvB + c] = Xb[r][c];
+}
+
+__global__ void __launch_bounds__(1024) rinv_block_kernel(int k, int kb, const double* __restrict__ G,
+                                                          const float* __restrict__ R, const float* __restrict__ D,
+                                                          float* __restrict__ Xf) {
+  extern __shared__ float rsm[];
+  constexpr int P = kRinvB + 1;  // padded row of a staged block
+  const int J = blockIdx.x;
+  const int tid = threadIdx.x, r = tid / kRinvB, c = tid % kRinvB;
+  float* Xs = rsm;                              // (J + 1) blocks of 32 x P
+  float* Rst = Xs + (J + 1) * kRinvB * P;       // kRinvStage blocks
+  float* T = Rst + kRinvStage * kRinvB * P;     // 32 x P
+  float* Dst = T + kRinvB * P;                  // 32 x P
+  __shared__ double red[32];
+  __shared__ double dmax;
+  diag_max(k, G, red, &dmax);
+  Xs[(J * kRinvB + r) * P + c] = D[(static_cast<size_t>(J) * kRinvB + r) * kRinvB + c];
+  __syncthreads();
+  const int e2 = (dmax > 0.0) ? (ilogb(dmax) >> 1) : 0;
+  const float unscale = ldexpf(1.0f, -e2);
+  for (int I = J - 1; I >= 0; --I) {
+    float acc = 0.0f;
+    for (int L0 = I + 1; L0 <= J; L0 += kRinvStage) {
+      const int nl = min(kRinvStage, J - L0 + 1);
+      for (int q = 0; q < nl; ++q)
+        Rst[(q * kRinvB + r) * P + c] = R[static_cast<size_t>(I * kRinvB + r) * kb + (L0 + q) * kRinvB + c];
+      __syncthreads();
+      for (int q = 0; q < nl; ++q) {
+        const float* rb = Rst + (q * kRinvB + r) * P;
+        const float* xb = Xs + ((L0 + q) * kRinvB) * P + c;
+#pragma unroll 8
+        for (int m = 0; m < kRinvB; ++m) acc = fmaf(rb[m], xb[m * P], acc);
+      }
+      __syncthreads();
+    }
+    T[r * P + c] = acc;
+    Dst[r * P + c] = D[(static_cast<size_t>(I) * kRinvB + r) * kRinvB + c];
+    __syncthreads();
+    float x = 0.0f;
+#pragma unroll 8
+    for (int m = 0; m < kRinvB; ++m) x = fmaf(Dst[r * P + m], T[m * P + c], x);
+    Xs[(I * kRinvB + r) * P + c] = -x;
+    __syncthreads();
+  }
+  const int col = J * kRinvB + c;
+  if (col < k) {
+    for (int row = r; row < k; row += kRinvB) {
+      const float v = (row < (J + 1) * kRinvB) ? Xs[row * P + c] * unscale : 0.0f;
+      Xf[static_cast<size_t>(row) * k + col] = (row <= col) ? v : 0.0f;
+    }
+  }
+}
+
 // The same elimination for k too large for shared memory, in panels of
 // kCholPanel columns over the whole GPU (the matrix stays in L2):
 // chol_scale_kernel writes the scaled double-float upper triangle,
@@ -1505,6 +1620,26 @@ int chol_inv(int64_t k, const double* G, float* Rinv, double* scratch, int32_t* 
       chol_trail_kernel<<<static_cast<unsigned>(t * (t + 1) / 2), 256, 0, st>>>(kk, j0, j1, a, dinv_g);
       if (cudaGetLastError() != cudaSuccess) return SHG_ERR_CUDA;
     }
+  }
+  // R^-1 by 32 x 32 blocks (R padded to kb and the diagonal-block inverses
+  // in the scratch behind the eliminated matrix, 8 k^2 bytes, which they fit
+  // for k > 113); else in one CTA
+  const int kb = (kk + kRinvB - 1) / kRinvB * kRinvB, nbk = kb / kRinvB;
+  const size_t need_r = (static_cast<size_t>(kb) * kb + static_cast<size_t>(nbk) * kRinvB * kRinvB) * sizeof(float);
+  const size_t rsmem = (static_cast<size_t>(nbk + kRinvStage + 2) * kRinvB * (kRinvB + 1)) * sizeof(float);
+  if (need_r <= static_cast<size_t>(8) * k * k && smem_fits(rsmem)) {
+    float* Rp = reinterpret_cast<float*>(a + k * k);
+    float* Dg = Rp + static_cast<size_t>(kb) * kb;
+    rinv_prep_kernel<<<dim3(static_cast<unsigned>((kb + 255) / 256), static_cast<unsigned>(kb)), 256, 0, st>>>(
+        kk, kb, a, dinv_g, Rp);
+    if (cudaGetLastError() != cudaSuccess) return SHG_ERR_CUDA;
+    rinv_diag_kernel<<<nbk, kRinvB, 0, st>>>(kb, Rp, Dg);
+    if (cudaGetLastError() != cudaSuccess) return SHG_ERR_CUDA;
+    if (cudaFuncSetAttribute(rinv_block_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             static_cast<int>(rsmem)) != cudaSuccess)
+      return SHG_ERR_CUDA;
+    rinv_block_kernel<<<nbk, 1024, rsmem, st>>>(kk, kb, G, Rp, Dg, Rinv);
+    return cuda_status(cudaGetLastError());
   }
   chol_inv_kernel<false, false><<<1, threads, 0, st>>>(kk, G, Rinv, scratch, flags, dinv_g);
   return cuda_status(cudaGetLastError());
