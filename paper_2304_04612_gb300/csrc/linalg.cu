@@ -1152,6 +1152,8 @@ __host__ __device__ inline size_t bj_scratch_floats(int k) {
 __device__ __forceinline__ void bj_group_sync(int g) {
   asm volatile("bar.sync %0, %1;" ::"r"(g + 1), "r"(kBjGroup) : "memory");
 }
+// groups 0 and 1 together (a pair's tile in phase 1)
+__device__ __forceinline__ void bj_pair_sync() { asm volatile("bar.sync 5, %0;" ::"r"(2 * kBjGroup) : "memory"); }
 
 // global index of local index i (0..15) of the block pair (a, b)
 __device__ __forceinline__ int bj_index(int i, int a, int b) {
@@ -1208,93 +1210,109 @@ __global__ void __launch_bounds__(kBjThreads) bjac_grid_kernel(int k, const doub
   for (int sweep = 0; sweep < kJacSweeps; ++sweep) {
     for (int r = 0; r < n1; ++r) {
       // ---------------------------------------------- phase 1: pair tiles
-      // (one group per CTA, so that the pairs' groups have SMs to
-      // themselves: an inner round is a chain of dependent steps)
-      for (int p = (g == 0) ? static_cast<int>(blockIdx.x) : np; p < np; p += gridDim.x) {
-        int a, b;
-        circle_ab(p, r, n1, a, b);
-        const int gi = bj_index(ti, a, b), gj = bj_index(tj, a, b);
-        S[g][0][ti][tj] = __ldcg(A + static_cast<size_t>(gi) * kpb + gj);
-        U[g][0][ti][tj] = (ti == tj) ? 1.0f : 0.0f;
-        if (gt < 2) flag[g][gt] = 0;
-        bj_group_sync(g);
-        // rotation thread t (t < 8): the rotation of slot t for inner round
-        // 0 from the tile, then in every round the one for the next round
-        // from the current tile and the current rotations, forming the three
-        // elements it needs with the element threads' arithmetic (rotated).
-        // The pairing is fixed, so every thread reads its table entries for
-        // the next round during the current one: after a barrier only the
-        // tile and rotation loads stand before the arithmetic.
-        auto rotate = [&](float app, float aqq, float apq, float2* out) {
-          float c, s;
-          if (jac_rot(app, aqq, apq, c, s)) {
-            flag[g][0] = 1;
-            if (jac_big(app, aqq, apq)) flag[g][1] = 1;
+      // Two groups of one CTA per pair, so that the pair has an SM to itself
+      // (an inner round is a chain of dependent steps): group 0 holds the
+      // tile, a thread per element; the first 8 threads of group 1 are the
+      // rotation threads, so that their chain does not wait for element
+      // updates of their own.  One 512-thread barrier per inner round.
+      if (g < 2) {
+        const bool elem = (g == 0);
+        const int rt = (g == 1 && gt < kBjTile / 2) ? gt : -1;
+        for (int p = static_cast<int>(blockIdx.x); p < np; p += gridDim.x) {
+          int a, b;
+          circle_ab(p, r, n1, a, b);
+          const int gi = bj_index(ti, a, b), gj = bj_index(tj, a, b);
+          if (elem) {
+            S[0][0][ti][tj] = __ldcg(A + static_cast<size_t>(gi) * kpb + gj);
+            U[0][0][ti][tj] = (ti == tj) ? 1.0f : 0.0f;
+            if (gt < 2) flag[0][gt] = 0;
           }
-          *out = make_float2(c, s);
-        };
-        const bool rotor = gt < kBjTile / 2;
-        if (rotor) {
-          const int pq = pair_of[0][gt];
-          const int pp = pq & 15, qq = pq >> 4;
-          rotate(S[g][0][pp][pp], S[g][0][qq][qq], S[g][0][pp][qq], &rc[g][0][gt]);
+          bj_pair_sync();
+          // rotation thread t: the rotation of slot t for inner round 0
+          // from the tile, then in every round the one for the next round
+          // from the current tile and the current rotations, forming the
+          // three elements it needs with the element threads' arithmetic
+          // (rotated), so the values agree bit for bit.  The pairing is
+          // fixed: every thread reads its table entries one round ahead.
+          auto rotate = [&](float app, float aqq, float apq, float2* out) {
+            float c, s;
+            if (jac_rot(app, aqq, apq, c, s)) {
+              flag[0][0] = 1;
+              if (jac_big(app, aqq, apq)) flag[0][1] = 1;
+            }
+            *out = make_float2(c, s);
+          };
+          if (rt >= 0) {
+            const int pq = pair_of[0][rt];
+            const int pp = pq & 15, qq = pq >> 4;
+            rotate(S[0][0][pp][pp], S[0][0][qq][qq], S[0][0][pp][qq], &rc[0][0][rt]);
+          }
+          bj_pair_sync();
+          // element (x, y) of J^T S J given the round's table entries ex, ey
+          // of x and y (slot | partner << 4): the smaller index of a pair
+          // becomes c x - s y, the larger s x + c y; the pair's own
+          // off-diagonal is annihilated
+          auto rotated = [](const float (*Sc)[kBjTile + 1], const float2* R, int x, int y, int ex, int ey) {
+            const int px = ex >> 4, py = ey >> 4;
+            const float s00 = Sc[x][y], s10 = Sc[px][y], s01 = Sc[x][py], s11 = Sc[px][py];
+            const float2 Rx = R[ex & 15], Ry = R[ey & 15];
+            const float sgx = (x > px) ? Rx.y : -Rx.y, sgy = (y > py) ? Ry.y : -Ry.y;
+            const float l0 = __fmaf_rn(sgx, s10, __fmul_rn(Rx.x, s00));
+            const float l1 = __fmaf_rn(sgx, s11, __fmul_rn(Rx.x, s01));
+            const float v = __fmaf_rn(sgy, l1, __fmul_rn(Ry.x, l0));
+            return (py == x && Ry.y != 0.0f) ? 0.0f : v;
+          };
+          int eti = 0, etj = 0, rpq = 0, epp = 0, eqq = 0;
+          if (elem) {
+            eti = ptab[0][ti];
+            etj = ptab[0][tj];
+          } else if (rt >= 0) {
+            rpq = pair_of[1][rt];
+            epp = ptab[0][rpq & 15];
+            eqq = ptab[0][rpq >> 4];
+          }
+          int cb = 0;
+          for (int ir = 0; ir < kBjTile - 1; ++ir) {
+            const float(*Sc)[kBjTile + 1] = S[0][cb];
+            const float2* R = rc[0][cb];
+            if (rt >= 0) {
+              // the next round's entries first (independent of this round's data)
+              const bool more = ir + 2 < kBjTile - 1;
+              const int rpq_n = more ? pair_of[ir + 2][rt] : 0;
+              const int epp_n = more ? ptab[ir + 1][rpq_n & 15] : 0, eqq_n = more ? ptab[ir + 1][rpq_n >> 4] : 0;
+              if (ir + 1 < kBjTile - 1) {
+                const int pp = rpq & 15, qq = rpq >> 4;
+                rotate(rotated(Sc, R, pp, pp, epp, epp), rotated(Sc, R, qq, qq, eqq, eqq),
+                       rotated(Sc, R, pp, qq, epp, eqq), &rc[0][cb ^ 1][rt]);
+              }
+              rpq = rpq_n;
+              epp = epp_n;
+              eqq = eqq_n;
+            } else if (elem) {
+              const int nx = (ir + 1 < kBjTile - 1) ? ir + 1 : ir;
+              const int eti_n = ptab[nx][ti], etj_n = ptab[nx][tj];
+              S[0][cb ^ 1][ti][tj] = rotated(Sc, R, ti, tj, eti, etj);
+              const float2 Rj = R[etj & 15];
+              const int pj = etj >> 4;
+              const float sgj = (tj > pj) ? Rj.y : -Rj.y;
+              U[0][cb ^ 1][ti][tj] = __fmaf_rn(sgj, U[0][cb][ti][pj], __fmul_rn(Rj.x, U[0][cb][ti][tj]));
+              eti = eti_n;
+              etj = etj_n;
+            }
+            bj_pair_sync();
+            cb ^= 1;
+          }
+          if (elem) {
+            Ub[static_cast<size_t>(p) * kBjGroup + gt] = U[0][cb][ti][tj];
+            A[static_cast<size_t>(gi) * kpb + gj] = S[0][cb][ti][tj];  // the pair's own tile, rotated
+            if (gt == 0) {
+              const int sw = sweep & 3;
+              if (flag[0][0]) any_rot[sw] = 1;
+              if (flag[0][1]) big_rot[sw] = 1;
+            }
+          }
+          bj_pair_sync();
         }
-        bj_group_sync(g);
-        // element (x, y) of J^T S J given the round's table entries ex, ey of
-        // x and y (slot | partner << 4): the smaller index of a pair becomes
-        // c x - s y, the larger s x + c y; the pair's own off-diagonal is
-        // annihilated
-        auto rotated = [](const float (*Sc)[kBjTile + 1], const float2* R, int x, int y, int ex, int ey) {
-          const int px = ex >> 4, py = ey >> 4;
-          const float s00 = Sc[x][y], s10 = Sc[px][y], s01 = Sc[x][py], s11 = Sc[px][py];
-          const float2 Rx = R[ex & 15], Ry = R[ey & 15];
-          const float sgx = (x > px) ? Rx.y : -Rx.y, sgy = (y > py) ? Ry.y : -Ry.y;
-          const float l0 = __fmaf_rn(sgx, s10, __fmul_rn(Rx.x, s00));
-          const float l1 = __fmaf_rn(sgx, s11, __fmul_rn(Rx.x, s01));
-          const float v = __fmaf_rn(sgy, l1, __fmul_rn(Ry.x, l0));
-          return (py == x && Ry.y != 0.0f) ? 0.0f : v;
-        };
-        int eti = ptab[0][ti], etj = ptab[0][tj];
-        int rpq = rotor ? pair_of[1][gt] : 0;
-        int epp = rotor ? ptab[0][rpq & 15] : 0, eqq = rotor ? ptab[0][rpq >> 4] : 0;
-        int cb = 0;
-        for (int ir = 0; ir < kBjTile - 1; ++ir) {
-          const float(*Sc)[kBjTile + 1] = S[g][cb];
-          const float2* R = rc[g][cb];
-          // the next round's entries (independent of this round's data)
-          const int nx = (ir + 1 < kBjTile - 1) ? ir + 1 : ir;
-          const int eti_n = ptab[nx][ti], etj_n = ptab[nx][tj];
-          const int rpq_n = (rotor && ir + 2 < kBjTile - 1) ? pair_of[ir + 2][gt] : 0;
-          if (rotor && ir + 1 < kBjTile - 1) {
-            const int pp = rpq & 15, qq = rpq >> 4;
-            rotate(rotated(Sc, R, pp, pp, epp, epp), rotated(Sc, R, qq, qq, eqq, eqq), rotated(Sc, R, pp, qq, epp, eqq),
-                   &rc[g][cb ^ 1][gt]);
-          }
-          S[g][cb ^ 1][ti][tj] = rotated(Sc, R, ti, tj, eti, etj);
-          {
-            const float2 Rj = R[etj & 15];
-            const int pj = etj >> 4;
-            const float sgj = (tj > pj) ? Rj.y : -Rj.y;
-            U[g][cb ^ 1][ti][tj] = __fmaf_rn(sgj, U[g][cb][ti][pj], __fmul_rn(Rj.x, U[g][cb][ti][tj]));
-          }
-          eti = eti_n;
-          etj = etj_n;
-          if (rotor && ir + 2 < kBjTile - 1) {
-            rpq = rpq_n;
-            epp = ptab[ir + 1][rpq_n & 15];
-            eqq = ptab[ir + 1][rpq_n >> 4];
-          }
-          bj_group_sync(g);
-          cb ^= 1;
-        }
-        Ub[static_cast<size_t>(p) * kBjGroup + gt] = U[g][cb][ti][tj];
-        A[static_cast<size_t>(gi) * kpb + gj] = S[g][cb][ti][tj];  // the pair's own tile, rotated
-        if (gt == 0) {
-          const int sw = sweep & 3;
-          if (flag[g][0]) any_rot[sw] = 1;
-          if (flag[g][1]) big_rot[sw] = 1;
-        }
-        bj_group_sync(g);
       }
       grid.sync();
       // ---------------------------------------------- phase 2: A and V tiles
