@@ -1146,7 +1146,7 @@ constexpr int kBjThreads = 1024;   // four groups per CTA
 __host__ __device__ inline int bj_kpb(int k) { return (k + kBjTile - 1) / kBjTile * kBjTile; }
 __host__ __device__ inline size_t bj_scratch_floats(int k) {
   const size_t kpb = static_cast<size_t>(bj_kpb(k));
-  return 2 * kpb * kpb + (kpb / kBjTile) * kBjGroup + 64;
+  return 4 * kpb * kpb + 2 * (kpb / kBjTile) * kBjGroup + 64;
 }
 
 __device__ __forceinline__ void bj_group_sync(int g) {
@@ -1165,15 +1165,14 @@ __global__ void __launch_bounds__(kBjThreads) bjac_grid_kernel(int k, const doub
   namespace cg = cooperative_groups;
   cg::grid_group grid = cg::this_grid();
   const int kpb = bj_kpb(k), nb = kpb / kBjBlock, np = nb / 2, n1 = nb - 1;
-  float* const A = scratch;
-  float* const V = A + static_cast<size_t>(kpb) * kpb;
-  float* const Ub = V + static_cast<size_t>(kpb) * kpb;
-  volatile int* const any_rot = reinterpret_cast<int*>(Ub + static_cast<size_t>(np) * kBjGroup);
+  const size_t kpb2 = static_cast<size_t>(kpb) * kpb;
+  float* const A = scratch;  // three buffers of kpb^2
+  float* const V = A + 3 * kpb2;
+  float* const Ub = V + kpb2;  // two buffers of np x 256
+  volatile int* const any_rot = reinterpret_cast<int*>(Ub + 2 * static_cast<size_t>(np) * kBjGroup);
   volatile int* const big_rot = any_rot + 4;
   const int g = threadIdx.x / kBjGroup, gt = threadIdx.x % kBjGroup;
   const int ti = gt >> 4, tj = gt & 15;
-  const int gid = blockIdx.x * (kBjThreads / kBjGroup) + g;
-  const int ngroups = gridDim.x * (kBjThreads / kBjGroup);
   const int gtid = static_cast<int>(blockIdx.x * blockDim.x + threadIdx.x);
   const int gnt = static_cast<int>(gridDim.x * blockDim.x);
   __shared__ float S[4][2][kBjTile][kBjTile + 1];  // tile (two buffers in phase 1)
@@ -1206,121 +1205,29 @@ __global__ void __launch_bounds__(kBjThreads) bjac_grid_kernel(int k, const doub
     }
   }
   grid.sync();
+  // groups: the pair tiles on groups 0 and 1 of CTAs 0 .. np - 1 (one pair
+  // each), the tiles of A and V on every other group
+  const int nct = static_cast<int>(gridDim.x);
+  const bool pair_cta = static_cast<int>(blockIdx.x) < np;
+  const int nw2 = 2 * np + 4 * (nct - np);
+  const int w2id = pair_cta ? ((g >= 2) ? 2 * static_cast<int>(blockIdx.x) + (g - 2) : -1)
+                            : 2 * np + 4 * (static_cast<int>(blockIdx.x) - np) + g;
+  const int nA = np * (np - 1) / 2, nV = (kpb / kBjTile) * np;
   int sweeps = kJacSweeps;
-  for (int sweep = 0; sweep < kJacSweeps; ++sweep) {
-    for (int r = 0; r < n1; ++r) {
-      // ---------------------------------------------- phase 1: pair tiles
-      // Two groups of one CTA per pair, so that the pair has an SM to itself
-      // (an inner round is a chain of dependent steps): group 0 holds the
-      // tile, a thread per element; the first 8 threads of group 1 are the
-      // rotation threads, so that their chain does not wait for element
-      // updates of their own.  One 512-thread barrier per inner round.
-      if (g < 2) {
-        const bool elem = (g == 0);
-        const int rt = (g == 1 && gt < kBjTile / 2) ? gt : -1;
-        for (int p = static_cast<int>(blockIdx.x); p < np; p += gridDim.x) {
-          int a, b;
-          circle_ab(p, r, n1, a, b);
-          const int gi = bj_index(ti, a, b), gj = bj_index(tj, a, b);
-          if (elem) {
-            S[0][0][ti][tj] = __ldcg(A + static_cast<size_t>(gi) * kpb + gj);
-            U[0][0][ti][tj] = (ti == tj) ? 1.0f : 0.0f;
-            if (gt < 2) flag[0][gt] = 0;
-          }
-          bj_pair_sync();
-          // rotation thread t: the rotation of slot t for inner round 0
-          // from the tile, then in every round the one for the next round
-          // from the current tile and the current rotations, forming the
-          // three elements it needs with the element threads' arithmetic
-          // (rotated), so the values agree bit for bit.  The pairing is
-          // fixed: every thread reads its table entries one round ahead.
-          auto rotate = [&](float app, float aqq, float apq, float2* out) {
-            float c, s;
-            if (jac_rot(app, aqq, apq, c, s)) {
-              flag[0][0] = 1;
-              if (jac_big(app, aqq, apq)) flag[0][1] = 1;
-            }
-            *out = make_float2(c, s);
-          };
-          if (rt >= 0) {
-            const int pq = pair_of[0][rt];
-            const int pp = pq & 15, qq = pq >> 4;
-            rotate(S[0][0][pp][pp], S[0][0][qq][qq], S[0][0][pp][qq], &rc[0][0][rt]);
-          }
-          bj_pair_sync();
-          // element (x, y) of J^T S J given the round's table entries ex, ey
-          // of x and y (slot | partner << 4): the smaller index of a pair
-          // becomes c x - s y, the larger s x + c y; the pair's own
-          // off-diagonal is annihilated
-          auto rotated = [](const float (*Sc)[kBjTile + 1], const float2* R, int x, int y, int ex, int ey) {
-            const int px = ex >> 4, py = ey >> 4;
-            const float s00 = Sc[x][y], s10 = Sc[px][y], s01 = Sc[x][py], s11 = Sc[px][py];
-            const float2 Rx = R[ex & 15], Ry = R[ey & 15];
-            const float sgx = (x > px) ? Rx.y : -Rx.y, sgy = (y > py) ? Ry.y : -Ry.y;
-            const float l0 = __fmaf_rn(sgx, s10, __fmul_rn(Rx.x, s00));
-            const float l1 = __fmaf_rn(sgx, s11, __fmul_rn(Rx.x, s01));
-            const float v = __fmaf_rn(sgy, l1, __fmul_rn(Ry.x, l0));
-            return (py == x && Ry.y != 0.0f) ? 0.0f : v;
-          };
-          int eti = 0, etj = 0, rpq = 0, epp = 0, eqq = 0;
-          if (elem) {
-            eti = ptab[0][ti];
-            etj = ptab[0][tj];
-          } else if (rt >= 0) {
-            rpq = pair_of[1][rt];
-            epp = ptab[0][rpq & 15];
-            eqq = ptab[0][rpq >> 4];
-          }
-          int cb = 0;
-          for (int ir = 0; ir < kBjTile - 1; ++ir) {
-            const float(*Sc)[kBjTile + 1] = S[0][cb];
-            const float2* R = rc[0][cb];
-            if (rt >= 0) {
-              // the next round's entries first (independent of this round's data)
-              const bool more = ir + 2 < kBjTile - 1;
-              const int rpq_n = more ? pair_of[ir + 2][rt] : 0;
-              const int epp_n = more ? ptab[ir + 1][rpq_n & 15] : 0, eqq_n = more ? ptab[ir + 1][rpq_n >> 4] : 0;
-              if (ir + 1 < kBjTile - 1) {
-                const int pp = rpq & 15, qq = rpq >> 4;
-                rotate(rotated(Sc, R, pp, pp, epp, epp), rotated(Sc, R, qq, qq, eqq, eqq),
-                       rotated(Sc, R, pp, qq, epp, eqq), &rc[0][cb ^ 1][rt]);
-              }
-              rpq = rpq_n;
-              epp = epp_n;
-              eqq = eqq_n;
-            } else if (elem) {
-              const int nx = (ir + 1 < kBjTile - 1) ? ir + 1 : ir;
-              const int eti_n = ptab[nx][ti], etj_n = ptab[nx][tj];
-              S[0][cb ^ 1][ti][tj] = rotated(Sc, R, ti, tj, eti, etj);
-              const float2 Rj = R[etj & 15];
-              const int pj = etj >> 4;
-              const float sgj = (tj > pj) ? Rj.y : -Rj.y;
-              U[0][cb ^ 1][ti][tj] = __fmaf_rn(sgj, U[0][cb][ti][pj], __fmul_rn(Rj.x, U[0][cb][ti][tj]));
-              eti = eti_n;
-              etj = etj_n;
-            }
-            bj_pair_sync();
-            cb ^= 1;
-          }
-          if (elem) {
-            Ub[static_cast<size_t>(p) * kBjGroup + gt] = U[0][cb][ti][tj];
-            A[static_cast<size_t>(gi) * kpb + gj] = S[0][cb][ti][tj];  // the pair's own tile, rotated
-            if (gt == 0) {
-              const int sw = sweep & 3;
-              if (flag[0][0]) any_rot[sw] = 1;
-              if (flag[0][1]) big_rot[sw] = 1;
-            }
-          }
-          bj_pair_sync();
-        }
-      }
-      grid.sync();
-      // ---------------------------------------------- phase 2: A and V tiles
-      const int nA = np * (np - 1) / 2, nV = (kpb / kBjTile) * np;
-      for (int w = gid; w < nA + nV; w += ngroups) {
+  bool flush = false;
+  for (int s = 0;; ++s) {
+    const int rs = s % n1, rp = (s + n1 - 1) % n1;  // pairings of rounds s and s - 1
+    const float* const Aprev = A + static_cast<size_t>((s + 2) % 3) * kpb2;  // input of round s - 1
+    float* const Acur = A + static_cast<size_t>(s % 3) * kpb2;               // input of round s
+    float* const Anext = A + static_cast<size_t>((s + 1) % 3) * kpb2;        // input of round s + 1
+    const float* const Uprev = Ub + static_cast<size_t>((s + 1) & 1) * np * kBjGroup;
+    float* const Ucur = Ub + static_cast<size_t>(s & 1) * np * kBjGroup;
+    // ------------------------------------------ tiles of round s - 1
+    if (s >= 1 && w2id >= 0) {
+      for (int w = w2id; w < nA + nV; w += nw2) {
         if (w < nA) {
-          // tile (p, q), p < q, of the pairs' index sets: U_p^T A_pq U_q
-          // (the diagonal tiles came out of phase 1)
+          // tile (p, q), p < q, of round s - 1's pairs: U_p^T A_pq U_q (the
+          // diagonal tiles came out of that round's pair phase)
           int p = 0, rem = w;
           while (rem >= np - 1 - p) {
             rem -= np - 1 - p;
@@ -1328,12 +1235,12 @@ __global__ void __launch_bounds__(kBjThreads) bjac_grid_kernel(int k, const doub
           }
           const int q = p + 1 + rem;
           int pa, pb, qa, qb;
-          circle_ab(p, r, n1, pa, pb);
-          circle_ab(q, r, n1, qa, qb);
+          circle_ab(p, rp, n1, pa, pb);
+          circle_ab(q, rp, n1, qa, qb);
           const int gi = bj_index(ti, pa, pb), gj = bj_index(tj, qa, qb);
-          S[g][0][ti][tj] = __ldcg(A + static_cast<size_t>(gi) * kpb + gj);
-          U[g][0][ti][tj] = __ldcg(Ub + static_cast<size_t>(p) * kBjGroup + gt);
-          U[g][1][ti][tj] = __ldcg(Ub + static_cast<size_t>(q) * kBjGroup + gt);
+          S[g][0][ti][tj] = __ldcg(Aprev + static_cast<size_t>(gi) * kpb + gj);
+          U[g][0][ti][tj] = __ldcg(Uprev + static_cast<size_t>(p) * kBjGroup + gt);
+          U[g][1][ti][tj] = __ldcg(Uprev + static_cast<size_t>(q) * kBjGroup + gt);
           bj_group_sync(g);
           float t = 0.0f;
 #pragma unroll
@@ -1343,17 +1250,17 @@ __global__ void __launch_bounds__(kBjThreads) bjac_grid_kernel(int k, const doub
           float o = 0.0f;
 #pragma unroll
           for (int z = 0; z < kBjTile; ++z) o = __fmaf_rn(U[g][0][z][ti], S[g][1][z][tj], o);
-          A[static_cast<size_t>(gi) * kpb + gj] = o;
-          A[static_cast<size_t>(gj) * kpb + gi] = o;
+          Acur[static_cast<size_t>(gi) * kpb + gj] = o;
+          Acur[static_cast<size_t>(gj) * kpb + gi] = o;
         } else {
           // V rows c0 .. c0 + 15 at the columns of pair p: V U_p
           const int w2 = w - nA;
           const int p = w2 % np, c0 = (w2 / np) * kBjTile;
           int pa, pb;
-          circle_ab(p, r, n1, pa, pb);
+          circle_ab(p, rp, n1, pa, pb);
           const int row = c0 + ti;
           S[g][0][ti][tj] = __ldcg(V + static_cast<size_t>(row) * kpb + bj_index(tj, pa, pb));
-          U[g][0][ti][tj] = __ldcg(Ub + static_cast<size_t>(p) * kBjGroup + gt);
+          U[g][0][ti][tj] = __ldcg(Uprev + static_cast<size_t>(p) * kBjGroup + gt);
           bj_group_sync(g);
           float o = 0.0f;
 #pragma unroll
@@ -1362,20 +1269,175 @@ __global__ void __launch_bounds__(kBjThreads) bjac_grid_kernel(int k, const doub
         }
         bj_group_sync(g);
       }
-      grid.sync();
     }
-    const int sw = sweep & 3;
-    if (!any_rot[sw]) {
-      sweeps = sweep;
-      break;
+    // ------------------------------------------ pair tiles of round s
+    // Two groups of one CTA per pair, so that the pair has an SM to itself
+    // (an inner round is a chain of dependent steps): group 0 holds the
+    // tile, a thread per element; the first 8 threads of group 1 are the
+    // rotation threads, so that their chain does not wait for element
+    // updates of their own.  One 512-thread barrier per inner round.
+    if (!flush && pair_cta && g < 2) {
+      const bool elem = (g == 0);
+      const int rt = (g == 1 && gt < kBjTile / 2) ? gt : -1;
+      const int p = static_cast<int>(blockIdx.x);
+      int a, b;
+      circle_ab(p, rs, n1, a, b);
+      const int gi = bj_index(ti, a, b), gj = bj_index(tj, a, b);
+      // The tile of round s's input: its diagonal blocks are parts of round
+      // s - 1's pair tiles (written in the previous step); when a and b sat
+      // in different pairs Pa, Pb of round s - 1, the block (a, b) is part
+      // of round s - 1's tile (Pa, Pb), which the tile groups write in this
+      // very step, so it is formed here from round s - 1's input:
+      // (U_Pa^T A_PaPb U_Pb) at the rows of a and the columns of b.
+      int Pa = 0, Pb = 0, sa = 0, sb = 0;
+      if (s >= 1) {
+        int xa, ya;
+        circ_slot(a, rp, n1, Pa, xa);
+        circ_slot(b, rp, n1, Pb, ya);
+        int t0, t1;
+        circle_ab(Pa, rp, n1, t0, t1);
+        sa = (a == t0) ? 0 : 1;
+        circle_ab(Pb, rp, n1, t0, t1);
+        sb = (b == t0) ? 0 : 1;
+      }
+      const bool cross = (s >= 1) && (Pa != Pb);
+      if (elem) {
+        if (!cross || ((ti < kBjBlock) == (tj < kBjBlock)))
+          S[0][0][ti][tj] = __ldcg(Acur + static_cast<size_t>(gi) * kpb + gj);
+        U[0][0][ti][tj] = (ti == tj) ? 1.0f : 0.0f;
+        if (gt < 2) flag[0][gt] = 0;
+        if (cross) {
+          int qa0, qa1, qb0, qb1;
+          circle_ab(Pa, rp, n1, qa0, qa1);
+          circle_ab(Pb, rp, n1, qb0, qb1);
+          S[1][0][ti][tj] = __ldcg(Aprev + static_cast<size_t>(bj_index(ti, qa0, qa1)) * kpb + bj_index(tj, qb0, qb1));
+          U[1][0][ti][tj] = __ldcg(Uprev + static_cast<size_t>(Pa) * kBjGroup + gt);
+          U[1][1][ti][tj] = __ldcg(Uprev + static_cast<size_t>(Pb) * kBjGroup + gt);
+        }
+      }
+      bj_pair_sync();
+      if (cross) {
+        // W = T U_Pb (columns of b's half), then C = U_Pa^T W (rows of a's half)
+        if (elem && gt < kBjTile * kBjBlock) {
+          const int m = gt / kBjBlock, j = gt % kBjBlock;
+          float w = 0.0f;
+#pragma unroll
+          for (int z = 0; z < kBjTile; ++z) w = __fmaf_rn(S[1][0][m][z], U[1][1][z][kBjBlock * sb + j], w);
+          S[1][1][m][j] = w;
+        }
+        bj_pair_sync();
+        if (elem && gt < kBjBlock * kBjBlock) {
+          const int i = gt / kBjBlock, j = gt % kBjBlock;
+          float o = 0.0f;
+#pragma unroll
+          for (int z = 0; z < kBjTile; ++z) o = __fmaf_rn(U[1][0][z][kBjBlock * sa + i], S[1][1][z][j], o);
+          S[0][0][i][kBjBlock + j] = o;
+          S[0][0][kBjBlock + j][i] = o;
+        }
+        bj_pair_sync();
+      }
+      // rotation thread t: the rotation of slot t for inner round 0 from the
+      // tile, then in every round the one for the next round from the
+      // current tile and the current rotations, forming the three elements
+      // it needs with the element threads' arithmetic (rotated), so the
+      // values agree bit for bit.  The pairing is fixed: every thread reads
+      // its table entries one round ahead.
+      auto rotate = [&](float app, float aqq, float apq, float2* out) {
+        float c, sn;
+        if (jac_rot(app, aqq, apq, c, sn)) {
+          flag[0][0] = 1;
+          if (jac_big(app, aqq, apq)) flag[0][1] = 1;
+        }
+        *out = make_float2(c, sn);
+      };
+      if (rt >= 0) {
+        const int pq = pair_of[0][rt];
+        const int pp = pq & 15, qq = pq >> 4;
+        rotate(S[0][0][pp][pp], S[0][0][qq][qq], S[0][0][pp][qq], &rc[0][0][rt]);
+      }
+      bj_pair_sync();
+      // element (x, y) of J^T S J given the round's table entries ex, ey of
+      // x and y (slot | partner << 4): the smaller index of a pair becomes
+      // c x - s y, the larger s x + c y; the pair's own off-diagonal is
+      // annihilated
+      auto rotated = [](const float (*Sc)[kBjTile + 1], const float2* R, int x, int y, int ex, int ey) {
+        const int px = ex >> 4, py = ey >> 4;
+        const float s00 = Sc[x][y], s10 = Sc[px][y], s01 = Sc[x][py], s11 = Sc[px][py];
+        const float2 Rx = R[ex & 15], Ry = R[ey & 15];
+        const float sgx = (x > px) ? Rx.y : -Rx.y, sgy = (y > py) ? Ry.y : -Ry.y;
+        const float l0 = __fmaf_rn(sgx, s10, __fmul_rn(Rx.x, s00));
+        const float l1 = __fmaf_rn(sgx, s11, __fmul_rn(Rx.x, s01));
+        const float v = __fmaf_rn(sgy, l1, __fmul_rn(Ry.x, l0));
+        return (py == x && Ry.y != 0.0f) ? 0.0f : v;
+      };
+      int eti = 0, etj = 0, rpq = 0, epp = 0, eqq = 0;
+      if (elem) {
+        eti = ptab[0][ti];
+        etj = ptab[0][tj];
+      } else if (rt >= 0) {
+        rpq = pair_of[1][rt];
+        epp = ptab[0][rpq & 15];
+        eqq = ptab[0][rpq >> 4];
+      }
+      int cb = 0;
+      for (int ir = 0; ir < kBjTile - 1; ++ir) {
+        const float(*Sc)[kBjTile + 1] = S[0][cb];
+        const float2* R = rc[0][cb];
+        if (rt >= 0) {
+          // the next round's entries first (independent of this round's data)
+          const bool more = ir + 2 < kBjTile - 1;
+          const int rpq_n = more ? pair_of[ir + 2][rt] : 0;
+          const int epp_n = more ? ptab[ir + 1][rpq_n & 15] : 0, eqq_n = more ? ptab[ir + 1][rpq_n >> 4] : 0;
+          if (ir + 1 < kBjTile - 1) {
+            const int pp = rpq & 15, qq = rpq >> 4;
+            rotate(rotated(Sc, R, pp, pp, epp, epp), rotated(Sc, R, qq, qq, eqq, eqq), rotated(Sc, R, pp, qq, epp, eqq),
+                   &rc[0][cb ^ 1][rt]);
+          }
+          rpq = rpq_n;
+          epp = epp_n;
+          eqq = eqq_n;
+        } else if (elem) {
+          const int nx = (ir + 1 < kBjTile - 1) ? ir + 1 : ir;
+          const int eti_n = ptab[nx][ti], etj_n = ptab[nx][tj];
+          S[0][cb ^ 1][ti][tj] = rotated(Sc, R, ti, tj, eti, etj);
+          const float2 Rj = R[etj & 15];
+          const int pj = etj >> 4;
+          const float sgj = (tj > pj) ? Rj.y : -Rj.y;
+          U[0][cb ^ 1][ti][tj] = __fmaf_rn(sgj, U[0][cb][ti][pj], __fmul_rn(Rj.x, U[0][cb][ti][tj]));
+          eti = eti_n;
+          etj = etj_n;
+        }
+        bj_pair_sync();
+        cb ^= 1;
+      }
+      if (elem) {
+        Ucur[static_cast<size_t>(p) * kBjGroup + gt] = U[0][cb][ti][tj];
+        Anext[static_cast<size_t>(gi) * kpb + gj] = S[0][cb][ti][tj];  // the pair's own tile, rotated
+        if (gt == 0) {
+          const int sw = (s / n1) & 3;
+          if (flag[0][0]) any_rot[sw] = 1;
+          if (flag[0][1]) big_rot[sw] = 1;
+        }
+      }
+      bj_pair_sync();
     }
-    if (!big_rot[sw]) {
-      sweeps = sweep + 1;
-      break;
-    }
-    if (gtid == 0) {
-      any_rot[(sweep + 3) & 3] = 0;
-      big_rot[(sweep + 3) & 3] = 0;
+    grid.sync();
+    if (flush) break;
+    if (rs == n1 - 1) {
+      // sweep s / n1 is complete: its flags are final
+      const int sweep = s / n1, sw = sweep & 3;
+      if (!any_rot[sw]) {
+        sweeps = sweep;
+        flush = true;
+      } else if (!big_rot[sw]) {
+        sweeps = sweep + 1;
+        flush = true;
+      } else if (sweep + 1 >= kJacSweeps) {
+        flush = true;
+      } else if (gtid == 0) {
+        any_rot[(sweep + 3) & 3] = 0;
+        big_rot[(sweep + 3) & 3] = 0;
+      }
     }
   }
   (void)sweeps;
@@ -1726,11 +1788,14 @@ int jacobi_eig(int64_t k, const double* G, float* V, float* scratch, void* eig, 
     }
     const int sms = sm_count();
     if (sms <= 0 || blocks_per_sm <= 0) return SHG_ERR_CUDA;
+    // a CTA per pair (its groups 0 and 1 take the pair tile, 2 and 3 tiles of
+    // A and V), further CTAs for the rest of the tiles
     const long long kpb = bj_kpb(static_cast<int>(k)), np = kpb / kBjTile;
-    const long long units = std::max(np, np * (np - 1) / 2 + (kpb / kBjTile) * np);
+    const long long units = np * (np - 1) / 2 + (kpb / kBjTile) * np;
     const int per_cta = kBjThreads / kBjGroup;
-    long long want = (units + per_cta - 1) / per_cta;
+    long long want = np + std::max(0LL, (units - 2 * np + per_cta - 1) / per_cta);
     if (want > static_cast<long long>(sms) * blocks_per_sm) want = static_cast<long long>(sms) * blocks_per_sm;
+    if (want < np) return SHG_ERR_UNSUPPORTED;
     int kk = static_cast<int>(k);
     const double* g = G;
     float* v = V;
