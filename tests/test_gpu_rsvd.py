@@ -230,8 +230,9 @@ def test_rp_hosvd_small(shg):
 
 def test_rsvd_large_k_grid_eigensolver(shg):
     """k = rank + s = 160 exceeds one SM's shared memory: the eigensolver runs
-    on the whole grid (cooperative launch).  Same tolerances as the other
-    randomized-SVD cases (slower decay keeps sigma_128 / sigma_1 = 2^-4)."""
+    as block Jacobi on the whole grid (cooperative launch).  Same tolerances
+    as the other randomized-SVD cases (slower decay keeps sigma_128 / sigma_1
+    = 2^-4)."""
     m, n, rank, s = 1200, 1000, 128, 32
     A = planted_svd(m, n, sigma_exp(min(m, n), 32.0), seed=8)
     Om = omega_f16(n, rank + s, seed=9)
@@ -247,9 +248,9 @@ def test_rsvd_large_k_grid_eigensolver(shg):
 
 
 def test_rsvd_k_beyond_rotation_log(shg):
-    """k = 296 is beyond the size whose rotations the eigensolver logs: the
-    grid solver then rotates V in every round itself.  Same tolerances, on
-    all 280 singular values and vectors."""
+    """k = 296: the block solver on the whole grid, V transformed with A in
+    every block round.  Same tolerances, on all 280 singular values and
+    vectors."""
     m, n, rank, s = 900, 800, 280, 16
     A = planted_svd(m, n, sigma_exp(min(m, n), 64.0), seed=12)
     Om = omega_f16(n, rank + s, seed=13)
@@ -266,14 +267,16 @@ def test_rsvd_k_beyond_rotation_log(shg):
 @pytest.mark.parametrize("m,n,rank,s,rate", [
     (700, 600, 17, 16, 8.0),      # k = 33: one-CTA Cholesky, one-CTA Jacobi
     (900, 700, 129, 16, 48.0),    # k = 145: panel Cholesky (k > 113), one-CTA Jacobi (k <= 158)
-    (900, 800, 145, 16, 48.0),    # k = 161: grid Jacobi, V from the rotation log
-    (1000, 900, 281, 16, 96.0),   # k = 297: grid Jacobi rotating V in every round
+    (900, 800, 145, 16, 48.0),    # k = 161: block Jacobi on the grid (11 block pairs)
+    (1000, 900, 281, 16, 96.0),   # k = 297: block Jacobi (19 block pairs)
+    (1300, 1200, 561, 16, 192.0), # k = 577: block Jacobi (37 pairs), R^-1 by 32 x 32 blocks
 ])
 def test_rsvd_odd_k(shg, m, n, rank, s, rate):
     """An odd k = rank + s reaches every k x k kernel (Cholesky, eigensolver,
-    V from the rotation log, Rayleigh quotients, selection) padded to an even
-    size with a zero row and column; all p singular values and vectors
-    against the oracle, the rank-p residual within 1 %."""
+    V, Rayleigh quotients, selection) padded to an even size (the one-CTA
+    solver) or to a multiple of 16 (the block solver) with zero rows and
+    columns; all p singular values and vectors against the oracle, the
+    rank-p residual within 1 %."""
     A = planted_svd(m, n, sigma_exp(min(m, n), rate), seed=20 + rank)
     Om = omega_f16(n, rank + s, seed=21 + rank)
     U, S, V, Q = shg.shg_rsvd(dev(A), padded_omega(Om), rank=rank, oversampling=s, want_q=True)
