@@ -143,8 +143,9 @@ int shg_sparse_sign_f16(uint64_t seed, uint64_t offset, int64_t rows, int64_t co
  * A2-A4. Random projection Y = op(A) * Omega (Eq. rp-vec) by SHGEMM
  * (Sec. 4.1, Eqs. shgemm-1..3): each FP32 tile of A, staged by TMA in shared
  * memory, is split by SIMT warps into hi = RN_fp16(a) and
- * lo = RN_fp16((a - hi) * 2^11), written to tensor memory (the A operand of
- * the MMA); both are multiplied with the FP16 Omega on tcgen05 tensor cores
+ * lo = RN_fp16((a - hi) * 2^11), written to tensor memory (128-column output
+ * tiles) or back into shared memory in the MMA's operand layout (256-column
+ * tiles, N > 128); both are multiplied with the FP16 Omega on tcgen05 tensor cores
  * into FP32 TMEM accumulators (the hi product drained round-to-nearest into
  * an FP32 register sum every few K blocks, Sec. 4.3), and recombined as
  * Y = acc_hi + 2^-11 acc_lo in FP32.
@@ -285,9 +286,10 @@ int shg_gram(int64_t m, int64_t k, const float* X, int64_t ldx, double* G, void*
  * CholeskyQR2 (the orthonormal basis of Algorithms 1 and 2):
  * twice { G = X^T X (FP64 result; the first pass with compensated FP32
  * sums as shg_gram, the second, on the well-conditioned X R^-1, with FP32
- * sums of 32-row slabs), G = R^T R (Cholesky elimination in double-float arithmetic, pairs of FP32
- * values with about 44 significant bits, on the power-of-4-scaled FP64 Gram
- * matrix), X <- X R^-1 (R^-1 in FP32) }.  X: m x k FP32 (ldx >= k),
+ * sums of 32-row slabs), G = R^T R (Cholesky elimination on the
+ * power-of-4-scaled Gram matrix: in double-float arithmetic, pairs of FP32
+ * values with about 44 significant bits, for the first pass; in FP32 for the
+ * second up to k = 113), X <- X R^-1 (R^-1 in FP32) }.  X: m x k FP32 (ldx >= k),
  * overwritten by Q with Q^T Q = I and X_in = Q R, diag(R) > 0.
  * k <= m < 2^31, k <= 1024.
  * Device flags: SHG_FLAG_NOT_SPD on a non-positive pivot.
@@ -344,9 +346,10 @@ int shg_cholqr2_static(int64_t m, int64_t k, float* X, int64_t ldx, int32_t* d_f
  * call when the first projection's range check trips; synchronises the
  * stream once, not under capture) or SHG_FP32_SIMT (every GEMM in FP32
  * SIMT: the single-precision baseline).  Gram matrices are FP32 sums
- * delivered in FP64 (compensated, but for the second CholeskyQR pass), the Cholesky factorisations double-float (see
- * shg_cholqr2); the k x k eigensolver of B B^T is FP32 Jacobi refined by
- * FP64 Rayleigh quotients.
+ * delivered in FP64 (compensated, but for the second CholeskyQR pass), the
+ * Cholesky factorisations as in shg_cholqr2; the k x k eigensolver of B B^T
+ * is FP32 Jacobi (one CTA up to k = 158, block Jacobi on the whole grid
+ * beyond) refined by FP64 Rayleigh quotients.
  * report (host pointer, nullable): when given, the call records CUDA events
  * between the phases of Algorithm 1, tracks the smallest Cholesky pivot
  * ratio, estimates the residual of the basis Q, synchronises `stream` and

@@ -1,16 +1,19 @@
 // k x k linear algebra of the randomized factorizations (k = rank +
-// oversampling, small): FP64 Gram matrices, Cholesky factors and their
-// inverses, and the eigendecomposition of B B^T for the small SVD of
-// Algorithm 1.
+// oversampling, small): Gram matrices (delivered in FP64), Cholesky factors
+// and their inverses, and the eigendecomposition of B B^T for the small SVD
+// of Algorithm 1.
 //
 // CholeskyQR2 replaces the QR factorization of Algorithms 1 and 2:
-// twice { G = X^T X, G = R^T R, X <- X R^-1 }.  The Gram matrix is summed
-// from exact FP32 x FP32 products with compensated FP32 arithmetic (about
-// twice FP32's precision), delivered in FP64 and factored in FP64; R^-1 is
-// formed in FP32 from the FP64 factor and X R^-1 is an FP32 GEMM.
+// twice { G = X^T X, G = R^T R, X <- X R^-1 }.  The first pass's Gram matrix
+// is summed from exact FP32 x FP32 products with compensated FP32
+// arithmetic (about twice FP32's precision) and factored in double-float
+// arithmetic; the second pass, on the nearly orthonormal X R^-1, sums and
+// (up to k = 113) factors in FP32.  R^-1 is formed in FP32 and X R^-1 is an
+// FP32 GEMM.
 //
 // The eigensolver is a parallel cyclic Jacobi method (round-robin pairing)
-// in FP32 on the scaled Gram matrix; eigenvalues are then refined as FP64
+// in FP32 on the scaled Gram matrix, on one CTA up to k = 158 and as block
+// Jacobi on the whole grid beyond; eigenvalues are then refined as FP64
 // Rayleigh quotients v^T G v / v^T v with the FP64 Gram matrix.
 #include <algorithm>
 #include <atomic>
