@@ -496,6 +496,24 @@ def side_measurements(shg, OS, torch, dev, A, A_host, Om, Om_host, Ys, flags, st
                                                     "frac": cmp["fp32"][str(k)]["tflops_2mnk"] / ffma_peak}
                                            for k in KS}}
 
+    # context only (a library GEMM, not on the path): cuBLAS SGEMM of the same
+    # product with FP32 inputs (Omega widened exactly), TF32 off, beside the
+    # project's FP32 SIMT path
+    tf32_was = torch.backends.cuda.matmul.allow_tf32
+    torch.backends.cuda.matmul.allow_tf32 = False
+    ctx = {}
+    try:
+        Omf = Om.float()
+        for k in KS:
+            Bk = Omf[:, :k].contiguous()
+            torch.matmul(A, Bk, out=Ys[k])  # library set-up outside the timing
+            ms = time_ms(torch, stream, lambda: torch.matmul(A, Bk, out=Ys[k]), reps=3)
+            ctx[str(k)] = {"ms": ms, "tflops_2mnk": 2.0 * M * N * k / (ms * 1e-3) / 1e12,
+                           "shgemm_speedup": ms / cmp["f16"][str(k)]["ms"]}
+    finally:
+        torch.backends.cuda.matmul.allow_tf32 = tf32_was
+    out["context_cublas_sgemm"] = ctx
+
     # sampled-row error vs the FP64 oracle (same inputs), per variant
     rows = np.random.default_rng(0).choice(M, 128, replace=False)
     errs = {}

@@ -1473,21 +1473,27 @@ __device__ __forceinline__ void rayleigh_body(int k, const double* __restrict__ 
   double s[kRayVecs], q[kRayVecs];
 #pragma unroll
   for (int v = 0; v < kRayVecs; ++v) s[v] = q[v] = 0.0;
-  for (int b = threadIdx.x; b < k; b += blockDim.x) {
+  // `split` threads per column b share its a-range (a = part, part + split,
+  // ..), the loads of G unrolled so that several are in flight; the part-0
+  // thread adds the diagonal term and |v_b|^2
+  const int split = max(1, static_cast<int>(blockDim.x) / k);
+  const int part = static_cast<int>(threadIdx.x) % split;
+  for (int b = threadIdx.x / split; b < k; b += blockDim.x / split) {
     double u[kRayVecs];
 #pragma unroll
     for (int v = 0; v < kRayVecs; ++v) u[v] = 0.0;
-    for (int a = 0; a < b; ++a) {
+#pragma unroll 4
+    for (int a = part; a < b; a += split) {
       const double g = G[a * k + b];
 #pragma unroll
       for (int v = 0; v < kRayVecs; ++v) u[v] = fma(g, rv[v * k + a], u[v]);
     }
-    const double gbb = G[b * k + b];
+    const double gbb = (part == 0) ? G[b * k + b] : 0.0;
 #pragma unroll
     for (int v = 0; v < kRayVecs; ++v) {
       const double vb = rv[v * k + b];
       s[v] = fma(vb, fma(gbb, vb, 2.0 * u[v]), s[v]);
-      q[v] = fma(vb, vb, q[v]);
+      if (part == 0) q[v] = fma(vb, vb, q[v]);
     }
   }
 #pragma unroll
@@ -1524,7 +1530,10 @@ __global__ void rayleigh_kernel(int k, const double* __restrict__ G, const float
 }
 
 // Threads of a Rayleigh CTA: a thread per column, in whole warps, at most 256.
+// one thread per column (the batch: many CTAs), or 256 with several per
+// column for a single small problem
 inline int rayleigh_threads(int k) { return std::min(256, (k + 31) / 32 * 32); }
+inline int rayleigh_threads_single(int /*k*/) { return 256; }
 
 // Sort eigenvalues descending (ties by index), S[j] = sqrt(lambda) for the
 // top p, Up = V[:, perm[:p]] normalised to unit length and Ups = Up / S
@@ -1819,7 +1828,7 @@ int rayleigh_sort(int64_t k, int64_t p, const double* G, const float* V, double*
   if (rsm > 48 * 1024 && cudaFuncSetAttribute(rayleigh_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                               static_cast<int>(rsm)) != cudaSuccess)
     return SHG_ERR_CUDA;
-  rayleigh_kernel<<<static_cast<unsigned>((k + kRayVecs - 1) / kRayVecs), rayleigh_threads(static_cast<int>(k)), rsm,
+  rayleigh_kernel<<<static_cast<unsigned>((k + kRayVecs - 1) / kRayVecs), rayleigh_threads_single(static_cast<int>(k)), rsm,
                     st>>>(static_cast<int>(k), G, V, lam, nrm);
   if (cudaGetLastError() != cudaSuccess) return SHG_ERR_CUDA;
   // the rows of U' over several CTAs (each forms the ranks itself), about
