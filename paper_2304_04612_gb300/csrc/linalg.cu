@@ -1482,11 +1482,19 @@ __device__ __forceinline__ void rayleigh_body(int k, const double* __restrict__ 
     double u[kRayVecs];
 #pragma unroll
     for (int v = 0; v < kRayVecs; ++v) u[v] = 0.0;
-#pragma unroll 4
-    for (int a = part; a < b; a += split) {
-      const double g = G[a * k + b];
+    if (split == 1) {
+      for (int a = 0; a < b; ++a) {
+        const double g = G[a * k + b];
 #pragma unroll
-      for (int v = 0; v < kRayVecs; ++v) u[v] = fma(g, rv[v * k + a], u[v]);
+        for (int v = 0; v < kRayVecs; ++v) u[v] = fma(g, rv[v * k + a], u[v]);
+      }
+    } else {
+#pragma unroll 4
+      for (int a = part; a < b; a += split) {
+        const double g = G[a * k + b];
+#pragma unroll
+        for (int v = 0; v < kRayVecs; ++v) u[v] = fma(g, rv[v * k + a], u[v]);
+      }
     }
     const double gbb = (part == 0) ? G[b * k + b] : 0.0;
 #pragma unroll
