@@ -70,13 +70,17 @@ def check_vectors(U, V, ref, eps=1e-5):
         assert eu <= tol and ev <= tol, (i, eu, ev, tol)
 
 
-@pytest.mark.parametrize("m,k,cond", [(3000, 72, 1e4), (20000, 160, 1e6), (4096, 296, 2.6e5)])
+@pytest.mark.parametrize("m,k,cond", [(3000, 72, 1e4), (2000, 113, 1e4), (2000, 114, 1e4), (20000, 160, 1e6),
+                                      (4096, 296, 2.6e5)])
 def test_cholqr2_orthonormal_and_matches_householder(shg, m, k, cond):
     """CholeskyQR2 with the first Gram compensated and the second in working
     precision: orthonormal to a few FP32 units per entry whatever cond(X) up
     to ~1e6 (||Q^T Q - I||_F <= 2 k u, u = 2^-24: the second pass's Gram and
     triangular product each leave O(u) per entry), and the same factor as
-    Householder QR to first order (cond u sqrt(k), shown where it is small)."""
+    Householder QR to first order (cond u sqrt(k), shown where it is small).
+    k = 113 is the largest one-CTA factorisation (its second pass in FP32),
+    k = 114 the smallest on the panel path with R^-1 by 32 x 32 blocks (R
+    padded to 128)."""
     rng = np.random.default_rng(0)
     U = np.linalg.qr(rng.standard_normal((m, k)))[0]
     V = np.linalg.qr(rng.standard_normal((k, k)))[0]
