@@ -1216,7 +1216,6 @@ __global__ void __launch_bounds__(kBjThreads) bjac_grid_kernel(int k, const doub
   const int w2id = pair_cta ? ((g >= 2) ? 2 * static_cast<int>(blockIdx.x) + (g - 2) : -1)
                             : 2 * np + 4 * (static_cast<int>(blockIdx.x) - np) + g;
   const int nA = np * (np - 1) / 2, nV = (kpb / kBjTile) * np;
-  int sweeps = kJacSweeps;
   bool flush = false;
   for (int s = 0;; ++s) {
     const int rs = s % n1, rp = (s + n1 - 1) % n1;  // pairings of rounds s and s - 1
@@ -1428,12 +1427,9 @@ __global__ void __launch_bounds__(kBjThreads) bjac_grid_kernel(int k, const doub
     if (flush) break;
     if (rs == n1 - 1) {
       // sweep s / n1 is complete: its flags are final
+      // (no rotation at all, or none large: the sweep ends the solve)
       const int sweep = s / n1, sw = sweep & 3;
-      if (!any_rot[sw]) {
-        sweeps = sweep;
-        flush = true;
-      } else if (!big_rot[sw]) {
-        sweeps = sweep + 1;
+      if (!any_rot[sw] || !big_rot[sw]) {
         flush = true;
       } else if (sweep + 1 >= kJacSweeps) {
         flush = true;
@@ -1443,7 +1439,6 @@ __global__ void __launch_bounds__(kBjThreads) bjac_grid_kernel(int k, const doub
       }
     }
   }
-  (void)sweeps;
   for (long long e = gtid; e < static_cast<long long>(k) * k; e += gnt) {
     const int i = static_cast<int>(e / k), j = static_cast<int>(e - static_cast<long long>(i) * k);
     Vout[e] = __ldcg(V + static_cast<size_t>(i) * kpb + j);
