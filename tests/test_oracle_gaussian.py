@@ -139,3 +139,14 @@ def test_gaussian_stream_quantiles():
     zz = G.gaussian_f64(seed=78, offset=0, rows=250000, cols=4)
     c = np.corrcoef(zz[:, 0], zz[:, 1])[0, 1]
     assert abs(c) < 5 / np.sqrt(zz.shape[0])
+
+
+def test_gaussian_f16_is_the_half_rounding_of_the_stream():
+    # gaussian_f16 rounds the float64 stream RN-even to FP16: numpy's
+    # double -> half cast is an independent correctly rounded conversion
+    x = G.gaussian_f64(123, 7, 64, 97)
+    h = G.gaussian_f16(123, 7, 64, 97)
+    assert h.shape == (64, 97)
+    assert np.array_equal(h, x.astype(np.float16).astype(np.float64))
+    assert np.array_equal(round_rn(h, FP16), h)
+    assert np.all(np.abs(h - x) <= FP16.u * np.abs(x) + FP16.min_subnormal)

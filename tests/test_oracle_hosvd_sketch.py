@@ -93,3 +93,25 @@ def test_residual_estimator_unbiased():
     ests = [K.residual_estimate(A, Q, omega_f16(50, 16, 100 + s).astype(np.float64), al) ** 2
             for s in range(200)]
     assert abs(np.mean(ests) / true ** 2 - 1.0) < 0.05
+
+
+def test_sketch_gradient_in_y_finite_differences():
+    # dl/dY for a generic Y (not in the range of A, m > n so that A^T has a
+    # null space): central differences of l(Y) = 1 - ||Q^T A||^2 / ||A||^2,
+    # Q from the QR of Y, written out here.  grad_omega's own pin cannot see
+    # a slip in the part of dl/dY that A^T maps to zero
+    rng = np.random.default_rng(13)
+    A = planted_svd(25, 12, sigma_exp(12, 2.0), seed=14).astype(np.float64)
+    Y = rng.standard_normal((25, 4))
+    nA2 = np.sum(A * A)
+
+    def l(Yv):
+        Q, _ = np.linalg.qr(Yv)
+        return 1.0 - np.sum((Q.T @ A) ** 2) / nA2
+
+    g = K.grad_Y(A, Y)
+    h = 1e-6
+    for i, j in [(0, 0), (24, 3), (7, 1), (13, 2)]:
+        Yp = Y.copy(); Yp[i, j] += h
+        Ym = Y.copy(); Ym[i, j] -= h
+        assert np.isclose(g[i, j], (l(Yp) - l(Ym)) / (2 * h), rtol=1e-5, atol=1e-9)

@@ -80,3 +80,30 @@ def test_rn_error_bound(fmt):
     nz = (np.abs(r) >= fmt.min_normal) & np.isfinite(r)
     e = 2.0 ** np.floor(np.log2(np.abs(r[nz])))
     assert np.all(np.abs(r[nz] - g[nz]) <= e * fmt.u * (1 + 1e-15))
+
+
+def test_f16_to_f64_bits_and_half_inputs_agree_with_numpy():
+    # both input forms of f16_to_f64 (uint16 bit patterns and float16 data)
+    # against numpy's own half -> double widening, over every finite pattern
+    from oracle.lowp import f16_to_f64
+    bits = np.arange(1 << 16, dtype=np.uint16)
+    ref = bits.view(np.float16).astype(np.float64)
+    fin = np.isfinite(ref)
+    assert np.array_equal(f16_to_f64(bits)[fin], ref[fin])
+    assert np.array_equal(f16_to_f64(bits.view(np.float16))[fin], ref[fin])
+    # the sign of zero survives the bit-pattern path
+    assert np.signbit(f16_to_f64(np.array([0x8000], dtype=np.uint16)))[0]
+
+
+def test_bf16_decode_and_encode_against_torch():
+    # every BF16 bit pattern: the decoded value equals torch's bfloat16 ->
+    # float64 widening, and encoding the finite values returns the pattern
+    from oracle.lowp import bf16_to_f64, encode_bf16
+    bits = np.arange(1 << 16, dtype=np.uint16)
+    ref = torch.from_numpy(bits.view(np.int16)).view(torch.bfloat16).to(torch.float64).numpy()
+    got = bf16_to_f64(bits)
+    fin = np.isfinite(ref)
+    assert np.array_equal(got[fin], ref[fin])
+    assert np.array_equal(np.isnan(got), np.isnan(ref))
+    assert np.array_equal(got[np.isinf(ref)], ref[np.isinf(ref)])
+    assert np.array_equal(encode_bf16(got[fin]), bits[fin])

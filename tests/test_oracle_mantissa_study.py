@@ -36,3 +36,20 @@ def test_matrix_construction():
     # r eigenvalues near 1, the rest at the noise level xi * (eigenvalues of G G^T / n) <= 4e-4
     ev = np.sort(np.linalg.eigvalsh(A1))[::-1]
     assert np.all(ev[:r] > 0.99) and ev[r] < 1e-3
+
+
+def test_projection_error_eckart_young():
+    # with G the top-k right singular vectors of A (numpy's SVD), range(A G)
+    # is the top-k left singular subspace and the error is the tail of the
+    # singular values; with G spanning all of range(A^T) the error vanishes
+    # (an integer product: A is exactly rank 15 in FP32 as well)
+    rng = np.random.default_rng(4)
+    A = (rng.integers(-3, 4, (60, 15)) @ rng.integers(-3, 4, (15, 50))).astype(np.float32)
+    A64 = A.astype(np.float64)
+    _, s, Vt = np.linalg.svd(A64)
+    for k in (1, 5, 12):
+        assert s[k] > 1e-3 * s[0]
+        e = MS.projection_error(A, Vt[:k].T)
+        assert np.isclose(e, np.sqrt(np.sum(s[k:] ** 2)), rtol=1e-10)
+    G = rng.standard_normal((50, 20))
+    assert MS.projection_error(A, G) < 1e-10 * np.linalg.norm(A64)

@@ -187,3 +187,43 @@ def test_shgemm_tf32_emulated_integer_brute_force():
     W = rng.integers(-30, 30, size=(9, 4)).astype(np.float16)
     ref = [[sum(int(A[i, l]) * int(W[l, j]) for l in range(9)) for j in range(4)] for i in range(6)]
     assert np.array_equal(S.shgemm_tf32_emulated(A, W), np.array(ref, dtype=np.float64))
+
+
+def test_bf16_omega_matches_torch_cast_on_every_fp16_value():
+    # RN_bf16 of each finite FP16 value: FP16 values are exact in float32, and
+    # torch's float32 -> bfloat16 cast rounds to nearest even
+    import torch
+    from oracle.lowp import all_finite_values
+    v = all_finite_values(FP16)
+    got = S.bf16_omega(v.astype(np.float16))
+    ref = torch.from_numpy(v.astype(np.float32)).to(torch.bfloat16).to(torch.float64).numpy()
+    assert np.array_equal(got, ref)
+
+
+def test_shgemm_bf16_emulated_integer_brute_force():
+    # integer A (|a| < 256: one BF16 piece, the others zero) and integer
+    # Omega (|w| <= 256, exact in BF16) on a non-square case: the result is
+    # the integer product, summed with Python integers
+    rng = np.random.default_rng(5)
+    A = rng.integers(-255, 256, size=(7, 11)).astype(np.float32)
+    W = rng.integers(-256, 257, size=(11, 4)).astype(np.float16)
+    ref = [[sum(int(A[i, l]) * int(W[l, j]) for l in range(11)) for j in range(4)] for i in range(7)]
+    for pieces in (2, 3):
+        assert np.array_equal(S.shgemm_bf16_emulated(A, W, pieces), np.array(ref, dtype=np.float64))
+
+
+@pytest.mark.parametrize("pieces,u", [(3, 2.0 ** -24), (2, 2.0 ** -16)])
+def test_shgemm_bf16_emulated_against_exact_product(pieces, u):
+    # sum_j p_j 2^(-8j) reconstructs a within u |a| (the split's own pin), so
+    # the emulated product is within u |A| |Omega_bf16| of A Omega_bf16; a
+    # dropped piece or a missing 2^(-8j) scale is off by far more
+    A = uniform(40, 300, 21)
+    Om = omega_f16(300, 24, seed=22)
+    W = S.bf16_omega(Om)
+    ex = A.astype(np.float64) @ W
+    em = S.shgemm_bf16_emulated(A, Om, pieces)
+    bound = u * (1 + 2.0 ** -20) * (np.abs(A.astype(np.float64)) @ np.abs(W))
+    assert np.all(np.abs(em - ex) <= bound)
+    if pieces == 3:
+        two = S.shgemm_bf16_emulated(A, Om, 2)
+        assert np.max(np.abs(two - ex)) > 16 * np.max(np.abs(em - ex))
