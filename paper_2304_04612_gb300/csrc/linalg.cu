@@ -1129,17 +1129,25 @@ __global__ void __launch_bounds__(32 * kApplyVWarps) jac_apply_v_kernel(int k, c
 // U_p^T A_pq U_q, every 16 x 16 tile of V at the columns of pair p becomes
 // V U_p).  Every index pair meets in at least one rotation per sweep, as in
 // the scalar method, and the sweeps end by its rules (no rotation at all,
-// or none above 2^-12 of the diagonal, jac_big), but a grid barrier is paid
-// per block round (twice) instead of per index round: 2 (nb - 1) barriers
-// per sweep instead of kp - 1.
+// or none above 2^-12 of the diagonal, jac_big).
+//   Pipelined: step s runs phase 1 of block round s beside phase 2 of block
+//   round s - 1, with one grid barrier per step, so a sweep pays nb - 1 grid
+//   barriers instead of the scalar method's kp - 1.  Phase 1 of round s reads
+//   the input of round s, whose diagonal blocks phase 1 of round s - 1 wrote;
+//   where the two blocks of a pair sat in different pairs of round s - 1,
+//   their off-diagonal block is one that phase 2 writes in the same step, so
+//   the pair forms it itself from round s - 1's input and U factors.
 //   The grid runs groups of 256 threads (one thread per element of a 16 x 16
-//   tile, a named barrier per group, four groups per CTA); groups take the
-//   pairs of phase 1 and the tiles of phase 2 in turn.  A, V and the U_p
-//   live in global memory (they stay in L2) and are read with ld.global.cg
-//   (never a stale L1 line written by another SM).  Each phase reads and
-//   writes only its own tile, so the updates are in place.
-//   scratch (floats): A (kpb x kpb, full symmetric), V (kpb x kpb), U
-//   (npairs x 256), then the flags (any[4], big[4] as ints).
+//   tile, a named barrier per group, four groups per CTA).  Pair p of a round
+//   runs on groups 0 and 1 of CTA p (an SM to itself: group 0 holds the
+//   tile, eight threads of group 1 compute the rotations); every other group
+//   takes tiles of phase 2 in turn.  A, V and the U_p live in global memory
+//   (they stay in L2) and are read with ld.global.cg (never a stale L1 line
+//   written by another SM).  A rotates through three buffers (the inputs of
+//   rounds s - 1, s and s + 1) and U through two; V is updated in place
+//   (each phase-2 tile of V reads and writes only its own elements).
+//   scratch (floats): A (3 x kpb x kpb, full symmetric), V (kpb x kpb), U
+//   (2 x npairs x 256), then the flags (any[4], big[4] as ints).
 //   Writes Vout (k x k, row-major, columns = eigenvectors).
 constexpr int kBjBlock = 8;        // indices per block
 constexpr int kBjTile = 16;        // indices per pair of blocks
