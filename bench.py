@@ -318,6 +318,8 @@ def main():
         roofline = {"bound": "tensor", "achieved": f0 / t0s / 1e12, "peak": pk["bf16_tflops"],
                     "unit": "TFLOP/s", "frac": f0 / t0s / 1e12 / pk["bf16_tflops"], "traffic": traffic,
                     "peak_source": f"{src} bf16_tflops (burst; FP16 and BF16 dense rates are equal)"}
+        if pk.get("bf16_tflops_sustained"):
+            roofline["frac_of_sustained"] = f0 / t0s / 1e12 / pk["bf16_tflops_sustained"]
     roofline.update({
         "kernel": (f"tc_wide_kernel (SHGEMM-FP16, 256-column tiles), m=n={M}, k={k0}" if tuned[str(k0)].get("wide")
                    else f"tc_gemm_kernel<K-major A, FP16 Omega> (SHGEMM-FP16, 128-column tiles), m=n={M}, k={k0}"),
