@@ -173,3 +173,21 @@ def test_deterministic_flag_matches_header():
     assert f"#define SHG_DETERMINISTIC 0x{shg.SHG_DETERMINISTIC:x}" in src
     # it lies above every variant number, so OR-ing it in never changes the variant
     assert all(v < shg.SHG_DETERMINISTIC for v in shg.VARIANTS.values())
+
+
+def test_rsvd_workspace_covers_the_eigensolver_scratch(lib):
+    # host-side sizing only: the workspace of a randomized SVD holds the
+    # eigensolver's scratch on both sides of the one-CTA limit (k <= 158: the
+    # rotation log of 40 sweeps x (k - 1) rounds x k / 2 (c, s) pairs; beyond:
+    # three kpb x kpb buffers of A, V and two sets of 16 x 16 tile factors per
+    # block pair, kpb = k rounded up to 16), odd k included
+    sz = ctypes.c_size_t()
+    for k in (33, 158, 159, 160, 266, 577, 1024):
+        assert lib.shg_rsvd_workspace_size(2048, 2048, k - 16, 16, 0, ctypes.byref(sz)) == 0
+        kp = k + (k & 1)
+        kpb = (k + 15) // 16 * 16
+        if kp <= 158:
+            need = 40 * (kp - 1) * (kp // 2) * 8
+        else:
+            need = (4 * kpb * kpb + 2 * (kpb // 16) * 256) * 4
+        assert sz.value >= need + 2048 * k * 4, k
